@@ -1,0 +1,228 @@
+"""CPU oracle for the direction-reuse path tracer (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
+this package.  It wraps ``oracle.c`` (plain C, built with gcc) through ctypes and shares no
+code with the CUDA library; both sides only consume the arrays produced by
+``paper_2310_07182_gb300.scenes``.
+
+``render`` parallelises over tile ranges with Python threads: each thread calls the
+single-threaded C routine on a disjoint range of tiles (ctypes releases the GIL), so the
+result does not depend on the thread count.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+INDEPENDENT, MORTON_SORT, DIRECTION_REUSE, WORLD_REUSE = 0, 1, 2, 3
+CAT_EMPTY, CAT_DIFFUSE, CAT_GLOSSY, CAT_HYBRID = 0, 1, 2, 3
+CLS_NONE, CLS_DIFFUSE, CLS_GLOSSY = 0, 1, 2
+MODES = {"independent": INDEPENDENT, "morton_sort": MORTON_SORT,
+         "direction_reuse": DIRECTION_REUSE, "world_reuse": WORLD_REUSE}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, IEEE float, no FMA contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("spp", C.c_uint32), ("max_bounces", C.c_uint32), ("mode", C.c_uint32),
+                ("tile_w", C.c_uint32), ("tile_h", C.c_uint32), ("k", C.c_uint32),
+                ("interleave", C.c_uint32), ("frame_base", C.c_uint32), ("reuse_depth", C.c_uint32),
+                ("pad", C.c_uint32), ("seed", C.c_uint64)]
+
+
+class _Outputs(C.Structure):
+    _fields_ = [("accum", C.c_void_p), ("taint", C.c_void_p), ("dbg_prim", C.c_void_p),
+                ("dbg_cat", C.c_void_p), ("dbg_cls", C.c_void_p), ("dbg_flags", C.c_void_p),
+                ("dbg_local", C.c_void_p), ("dbg_world", C.c_void_p), ("counters", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        vp, u32, i32 = C.c_void_p, C.c_uint32, C.c_int
+        L.orc_philox4x32_10.argtypes = [u32, u32, vp, vp]
+        L.orc_lcg_sequence.argtypes = [u32, u32, u32, u32, vp]
+        L.orc_tile_sigma.argtypes = [u32, u32, u32, u32, C.c_uint64, i32, vp, vp]
+        L.orc_sincos.argtypes = [C.c_float, vp, vp]
+        L.orc_sample_cosine.argtypes = [C.c_float, C.c_float, vp]
+        L.orc_sample_ggx.argtypes = [vp, C.c_float, vp, C.c_float, C.c_float, vp, vp]
+        L.orc_sample_ggx.restype = i32
+        L.orc_frame.argtypes = [vp, vp, vp]
+        L.orc_scene_new.argtypes = [vp, u32, vp, vp, vp, u32, vp]
+        L.orc_scene_new.restype = vp
+        L.orc_scene_free.argtypes = [vp]
+        L.orc_scene_nodes.argtypes = [vp]
+        L.orc_scene_nodes.restype = u32
+        L.orc_trace.argtypes = [vp, vp, vp, u32, i32, vp, vp, vp]
+        L.orc_render_tiles.argtypes = [vp, C.POINTER(_Camera), C.POINTER(_Params), u32, u32,
+                                       C.POINTER(_Outputs)]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def philox(key: int, ctr) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(key & 0xFFFFFFFF, (key >> 32) & 0xFFFFFFFF, _p(c), _p(out))
+    return out
+
+
+def lcg_sequence(m, a, c, x0) -> np.ndarray:
+    out = np.zeros(m, dtype=np.uint32)
+    lib().orc_lcg_sequence(m, a, c, x0, _p(out))
+    return out
+
+
+def tile_sigma(tile_w, tile_h, tile, frame, seed, lcg=True):
+    out = np.zeros(tile_w * tile_h, dtype=np.uint32)
+    abc = np.zeros(3, dtype=np.uint32)
+    lib().orc_tile_sigma(tile_w, tile_h, tile, frame, seed, int(lcg), _p(out), _p(abc))
+    return out, abc
+
+
+def sincos(x: float):
+    s = np.zeros(1, dtype=np.float32)
+    c = np.zeros(1, dtype=np.float32)
+    lib().orc_sincos(float(np.float32(x)), _p(s), _p(c))
+    return s[0], c[0]
+
+
+def sample_cosine(u1, u2):
+    w = np.zeros(3, dtype=np.float32)
+    lib().orc_sample_cosine(float(np.float32(u1)), float(np.float32(u2)), _p(w))
+    return w
+
+
+def sample_ggx(wo, alpha, f0, u1, u2):
+    wo = np.ascontiguousarray(wo, dtype=np.float32)
+    f0 = np.ascontiguousarray(f0, dtype=np.float32)
+    wi = np.zeros(3, dtype=np.float32)
+    wt = np.zeros(3, dtype=np.float32)
+    ok = lib().orc_sample_ggx(_p(wo), float(np.float32(alpha)), _p(f0), float(np.float32(u1)),
+                              float(np.float32(u2)), _p(wi), _p(wt))
+    return bool(ok), wi, wt
+
+
+def frame(n):
+    n = np.ascontiguousarray(n, dtype=np.float32)
+    t = np.zeros(3, dtype=np.float32)
+    b = np.zeros(3, dtype=np.float32)
+    lib().orc_frame(_p(n), _p(t), _p(b))
+    return t, b
+
+
+class Scene:
+    """Oracle copy of a scene (its own FP64 median-split BVH)."""
+
+    def __init__(self, sc):
+        self.src = sc
+        self._arrays = (np.ascontiguousarray(sc.tri_xyz, dtype=np.float32),
+                        np.ascontiguousarray(sc.tri_mat, dtype=np.uint32),
+                        np.ascontiguousarray(sc.mat_type, dtype=np.uint32),
+                        np.ascontiguousarray(sc.mat_params, dtype=np.float32),
+                        np.ascontiguousarray(sc.env, dtype=np.float32))
+        tx, tm, mt, mp, env = self._arrays
+        self.h = lib().orc_scene_new(_p(tx), tx.shape[0], _p(tm), _p(mt), _p(mp), mt.shape[0], _p(env))
+
+    @property
+    def n_nodes(self):
+        return lib().orc_scene_nodes(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.orc_scene_free(self.h)
+            self.h = None
+
+
+def trace(scene: Scene, rays, skip=None, use_bvh=True):
+    """Closest hit of (n, 8) fp32 rays -> (prim int32, t float64, fragile uint8)."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32)
+    n = rays.shape[0]
+    sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.int32)
+    prim = np.zeros(n, dtype=np.int32)
+    t = np.zeros(n, dtype=np.float64)
+    fr = np.zeros(n, dtype=np.uint8)
+    lib().orc_trace(scene.h, _p(rays), _p(sk), n, int(use_bvh), _p(prim), _p(t), _p(fr))
+    return prim, t, fr
+
+
+def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=None,
+           interleave=True, seed=0, frame_base=0, reuse_depth=0, debug=False, threads=None,
+           tiles=None, accum=None):
+    """Run the oracle path tracer.  Returns a dict with ``rgb`` (mean radiance, float64 h x w x 3),
+    ``taint`` (h x w uint8), ``counters`` and, with debug=True (spp 1), per-bounce arrays.
+    ``tiles`` = (begin, end) restricts the work to a tile range (other pixels stay 0).
+    ``accum`` (npx x 3 float64) continues an earlier accumulation in place (progressive
+    rendering resumed at ``frame_base``)."""
+    W, H = tile
+    K = W * H if k is None else k
+    w, h = cam.width, cam.height
+    npx = w * h
+    B = max_bounces
+    ntiles = ((w + W - 1) // W) * ((h + H - 1) // H)
+    t0, t1 = (0, ntiles) if tiles is None else tiles
+    if accum is None:
+        accum = np.zeros((npx, 3), dtype=np.float64)
+    assert accum.shape == (npx, 3) and accum.dtype == np.float64 and accum.flags.c_contiguous
+    taint = np.zeros(npx, dtype=np.uint8)
+    dbg = {}
+    if debug:
+        dbg = dict(prim=np.full((B + 1, npx), -2, dtype=np.int32), cat=np.full((B, npx), 255, np.uint8),
+                   cls=np.zeros((B, npx), np.uint8), flags=np.zeros((B, npx), np.uint8),
+                   local=np.zeros((B, npx, 3), np.float32), world=np.zeros((B, npx, 3), np.float32))
+    camc = _Camera((C.c_float * 3)(*cam.pos), (C.c_float * 3)(*cam.look_at), (C.c_float * 3)(*cam.up),
+                   cam.vfov_deg, w, h)
+    par = _Params(spp, B, MODES[mode] if isinstance(mode, str) else mode, W, H, K, int(interleave),
+                  frame_base, reuse_depth, 0, seed)
+    nthreads = threads or max(1, min(os.cpu_count() or 1, t1 - t0))
+    bounds = np.linspace(t0, t1, nthreads + 1).astype(int)
+    counters = np.zeros((nthreads, 3), dtype=np.uint64)
+
+    def work(i):
+        o = _Outputs(_p(accum), _p(taint), _p(dbg.get("prim")), _p(dbg.get("cat")), _p(dbg.get("cls")),
+                     _p(dbg.get("flags")), _p(dbg.get("local")), _p(dbg.get("world")), _p(counters[i]))
+        lib().orc_render_tiles(scene.h, C.byref(camc), C.byref(par), int(bounds[i]), int(bounds[i + 1]),
+                               C.byref(o))
+
+    ths = [threading.Thread(target=work, args=(i,)) for i in range(nthreads) if bounds[i] < bounds[i + 1]]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    res = dict(rgb=(accum / spp).reshape(h, w, 3), accum=accum, taint=taint.reshape(h, w),
+               counters=counters.sum(axis=0), threads=len(ths))
+    for key, v in dbg.items():
+        res["dbg_" + key] = v
+    return res

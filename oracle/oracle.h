@@ -1,0 +1,103 @@
+/*
+ * oracle.h -- plain, slow CPU oracle for the direction-reuse path tracer of
+ * "Generate Coherent Rays Directly" (Liu et al., arXiv 2310.07182).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load this library.  It shares no code, header, table or constant
+ * generator with the CUDA library under paper_2310_07182_gb300/csrc; the two only meet
+ * on the seeded input arrays produced by paper_2310_07182_gb300/scenes.py.
+ *
+ * Precision: closest-hit intersection and radiance accumulation are FP64.  Direction
+ * sampling, tangent frames, reuse and throughput are computed in IEEE FP32 with a fixed
+ * operation order (no FMA contraction, correctly rounded division and square root, own
+ * polynomial sine/cosine), because ray directions must agree bit for bit with the GPU;
+ * the paper does not state a precision (Sec. 4-5).
+ *
+ * Parity pins for each function are listed in oracle/README.md.  The hybrid-group weight
+ * (Sec. 3.2, "Hybrid Tile") has no formula in the paper: parity unpinned beyond the
+ * invariants the tests check.
+ */
+#ifndef ORC_ORACLE_H
+#define ORC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): out = bijection_key(ctr). */
+void orc_philox4x32_10(uint32_t k0, uint32_t k1, const uint32_t ctr[4], uint32_t out[4]);
+
+/* Full-period LCG sequence x_{k+1} = (a x_k + c) mod m, x_0 given (Sec. 3.3). */
+void orc_lcg_sequence(uint32_t m, uint32_t a, uint32_t c, uint32_t x0, uint32_t* out);
+
+/* Interleaved grouping of one W*H tile (Sec. 3.3): sigma[i] = shuffled number of the
+ * tile's i-th pixel (row-major); group = sigma / K.  abc_x0 receives (a, c, x0). */
+void orc_tile_sigma(uint32_t tile_w, uint32_t tile_h, uint32_t tile, uint32_t frame,
+                    uint64_t seed, int lcg, uint32_t* sigma, uint32_t* abc_x0);
+
+/* FP32 sine/cosine for |x| <= pi/4 by Taylor polynomials (1/n! coefficients). */
+void orc_sincos(float x, float* s, float* c);
+
+/* Cosine-weighted hemisphere sample (Shirley-Chiu concentric map). */
+void orc_sample_cosine(float u1, float u2, float* w);
+
+/* GGX visible-normal-free sampling of D(m)(m.n) (Walter et al. 2007); returns 1 if the
+ * sample is valid.  weight = f cos / pdf per channel. */
+int orc_sample_ggx(const float* wo, float alpha, const float* f0, float u1, float u2,
+                   float* wi, float* weight);
+
+/* Tangent frame (t, b) of a unit normal n (Duff et al., JCGT 2017). */
+void orc_frame(const float* n, float* t, float* b);
+
+typedef struct orc_scene orc_scene;
+
+orc_scene* orc_scene_new(const float* tri_xyz, uint32_t n_tri, const uint32_t* tri_mat,
+                         const uint32_t* mat_type, const float* mat_params, uint32_t n_mat,
+                         const float* env);
+void orc_scene_free(orc_scene* s);
+uint32_t orc_scene_nodes(const orc_scene* s);
+
+/* Closest hit of n rays (rays: n x 8 fp32: o.xyz, unused, d.xyz, unused).
+ * prim = original triangle index or -1, t in units of |d|, fragile = decision too close
+ * to call in FP32 (near-tie, near an edge, near the origin). use_bvh=0: brute force. */
+void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
+               int use_bvh, int32_t* prim, double* t, uint8_t* fragile);
+
+typedef struct {
+    float pos[3], look_at[3], up[3];
+    float vfov_deg;
+    uint32_t width, height;
+} orc_camera;
+
+enum { ORC_INDEPENDENT = 0, ORC_MORTON_SORT = 1, ORC_DIRECTION_REUSE = 2, ORC_WORLD_REUSE = 3 };
+
+typedef struct {
+    uint32_t spp, max_bounces, mode;
+    uint32_t tile_w, tile_h, k, interleave;
+    uint32_t frame_base, reuse_depth; /* reuse at bounces b <= reuse_depth; 0 = all */
+    uint32_t pad;
+    uint64_t seed;
+} orc_params;
+
+typedef struct {
+    double* accum;      /* npx*3: += sum over samples of path radiance */
+    uint8_t* taint;     /* npx: 1 if the pixel's result depends on a fragile decision */
+    /* optional per-bounce debug (spp == 1), NULL to skip */
+    int32_t* dbg_prim;  /* (B+1)*npx: original id of the hit of trace b; -1 miss, -2 none */
+    uint8_t* dbg_cat;   /* B*npx: category of the pixel's group at reuse step b (1..B) */
+    uint8_t* dbg_cls;   /* B*npx: material class of the pixel at step b */
+    uint8_t* dbg_flags; /* B*npx: bit0 alive at step b, bit1 spawned a ray, bit2 tainted */
+    float* dbg_local;   /* B*npx*3: tangent-space exit direction */
+    float* dbg_world;   /* B*npx*3: world-space exit direction */
+    uint64_t* counters; /* [0] primary rays, [1] secondary rays, [2] fragile decisions */
+} orc_outputs;
+
+/* Render tiles [tile_begin, tile_end) of the image (Sec. 3, whole method). */
+void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_params* p,
+                      uint32_t tile_begin, uint32_t tile_end, orc_outputs* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
