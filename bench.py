@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the direction-reuse path tracer on the landscape workload.
+
+One step = one full render through the C ABI of the 1920x1080 fBm landscape (2,093,058
+triangles, 1 spp, 2 bounces, 8x8 tiles, K = 8, LCG-interleaved groups, FP32 BVH2): ray
+generation, primary trace, then per bounce shade + classify + reuse + spawn, group
+compaction and the secondary trace, then accumulation and output.  The headline value is
+secondary Mrays/s of direction reuse over the whole step (device CUDA events on the render
+stream); independent sampling and Morton-sorted reordering are measured the same way and
+reported beside it.  Inputs (scene, path state) are resident in HBM before timing and the
+L2 is flushed between steps.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under torchrun each
+rank renders its own frames of the same workload (weak scaling, no data-path collective).
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "secondary Mrays/s"
+WORKLOAD = ("landscape 1920x1080, fBm terrain 1024^2 grid (2,093,058 tris), 60/30/10 Lambert/GGX/mirror, "
+            "sky env, 1 spp, 2 bounces, 8x8 tiles, K=8, LCG interleave, FP32 BVH2")
+TILE, K, SPP, BOUNCES = (8, 8), 8, 1, 2
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def frame_of(rank: int, step: int, world: int) -> int:
+    """Frame index rendered by ``rank`` at ``step``: ranks render disjoint frames."""
+    return step * world + rank
+
+
+def aggregate(values, op="max"):
+    """Reduce a per-rank float over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(values)
+    backend = dist.get_backend()
+    dev = "cuda" if backend == "nccl" else "cpu"
+    t = torch.tensor([float(values)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_file: str):
+    """DRAM bytes per launch of the trace kernel from the committed ncu summary, or None if
+    the kernel source changed since that capture."""
+    summ = os.path.join(ROOT, "profiles", "k_trace_bvh2.landscape.txt")
+    src = os.path.join(ROOT, "paper_2310_07182_gb300", "csrc", kernel_file)
+    if not os.path.exists(summ):
+        return None
+    kv = {}
+    with open(summ) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha") != sha or "dram_bytes_per_launch_full" not in kv:
+        return None
+    return float(kv["dram_bytes_per_launch_full"])
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_oracle_rate(sc, target_s: float, max_tiles=None, mode="direction_reuse", frame_base=0):
+    """Time the CPU oracle (all host cores) on a bounded sample of the workload's tiles.
+    Returns (secondary Mrays/s, threads, sample description, seconds)."""
+    import oracle
+    O = oracle.Scene(sc)
+    cam = sc.camera
+    ntx = math.ceil(cam.width / TILE[0])
+    nty = math.ceil(cam.height / TILE[1])
+    ntiles = ntx * nty
+    threads = os.cpu_count() or 1
+    # probe, then size the sample for ~target_s
+    n = min(ntiles, 8 * threads)
+    t0 = time.perf_counter()
+    r = oracle.render(O, cam, spp=SPP, max_bounces=BOUNCES, mode=mode, tile=TILE, k=K, seed=0,
+                      frame_base=frame_base, tiles=(0, n), threads=threads)
+    dt = time.perf_counter() - t0
+    n2 = int(min(ntiles, max(n, n * target_s / max(dt, 1e-3))))
+    if max_tiles:
+        n2 = min(n2, max_tiles)
+    start = (ntiles - n2) // 2  # a band through the middle of the image
+    t0 = time.perf_counter()
+    r = oracle.render(O, cam, spp=SPP, max_bounces=BOUNCES, mode=mode, tile=TILE, k=K, seed=0,
+                      frame_base=frame_base, tiles=(start, start + n2), threads=threads)
+    dt = time.perf_counter() - t0
+    sec = int(r["counters"][1])
+    sample = f"{n2} of {ntiles} 8x8 tiles ({100.0 * n2 / ntiles:.1f}% of the image), {mode}, 1 spp, 2 bounces"
+    return sec / dt / 1e6, r["threads"], sample, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on the host cores."""
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from paper_2310_07182_gb300 import scenes
+    sc = scenes.landscape()
+    per_step = []
+    rays = []
+    import oracle
+    O = oracle.Scene(sc)
+    cam = sc.camera
+    ntiles = math.ceil(cam.width / TILE[0]) * math.ceil(cam.height / TILE[1])
+    threads = os.cpu_count() or 1
+    n = min(ntiles, 16 * threads)
+    for s in range(args.warmup + args.steps):
+        start = (s * 7919 * n) % (ntiles - n)
+        t0 = time.perf_counter()
+        r = oracle.render(O, cam, spp=SPP, max_bounces=BOUNCES, mode="direction_reuse", tile=TILE, k=K, seed=0,
+                          tiles=(start, start + n), threads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            per_step.append(dt)
+            rays.append(int(r["counters"][1]))
+    total_t = sum(per_step)
+    value = sum(rays) / total_t / 1e6
+    sample = f"{n} of {ntiles} 8x8 tiles per step, direction_reuse, 1 spp, 2 bounces"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mrays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * total_t / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2310_07182_gb300 import binding as cr
+    from paper_2310_07182_gb300 import build as crbuild
+    from paper_2310_07182_gb300 import scenes
+    crbuild.build()
+    t_setup = time.perf_counter()
+    sc = scenes.landscape()
+    S = cr.Scene(sc)
+    cam = sc.camera
+    out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream().cuda_stream
+    setup_s = time.perf_counter() - t_setup
+
+    def step(mode, frame, flags=0):
+        st = cr.cr_stats()
+        o = cr.make_opts(k=K, interleave=True, seed=0, frame_base=frame,
+                         flags=cr.CR_OPT_STATS | flags, stream=stream, stats=st)
+        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, mode, TILE[0], TILE[1], out, o)
+        return st.as_dict()
+
+    # counting pass (untimed): node visits and triangle tests of the secondary traces
+    modes = args.modes.split(",")
+    counts = {}
+    for mode in modes:
+        counts[mode] = step(mode, frame_of(rank, 0, world), flags=cr.CR_OPT_COUNT)
+
+    results = {}
+    clocks = None
+    for mode in modes:
+        for w in range(args.warmup):
+            step(mode, frame_of(rank, w, world))
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if mode == modes[0] else None
+        if sampler:
+            sampler.__enter__()
+        stats = []
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(float(s))  # evict the L2 between steps (outside the timed events)
+            stats.append(step(mode, frame_of(rank, args.warmup + s, world)))
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        if sampler:
+            sampler.__exit__()
+            clocks = sampler.summary()
+        ms = sum(x["ms_total"] for x in stats)
+        ms_max = aggregate(ms, "max")
+        sec = sum(x["secondary_rays"] for x in stats)
+        sec_all = aggregate(sec, "sum")
+        results[mode] = dict(
+            mrays=sec_all / (ms_max / 1e3) / 1e6,
+            ms_per_step=ms_max / args.steps,
+            trace_mrays=sec / (sum(x["ms_trace_secondary"] for x in stats) / 1e3) / 1e6,
+            ms_trace_secondary=sum(x["ms_trace_secondary"] for x in stats) / args.steps,
+            ms_shade=sum(x["ms_shade"] for x in stats) / args.steps,
+            ms_compact=sum(x["ms_compact"] for x in stats) / args.steps,
+            ms_sort=sum(x["ms_sort"] for x in stats) / args.steps,
+            ms_trace_primary=sum(x["ms_trace_primary"] for x in stats) / args.steps,
+            secondary_rays_per_step=sec / args.steps,
+            launches_per_step=stats[0]["kernel_launches"],
+            wall_s=wall,
+        )
+        c = counts[mode]
+        results[mode]["nodes_per_ray"] = c["node_visits"] / max(c["secondary_rays"], 1)
+        results[mode]["tris_per_ray"] = c["tri_tests"] / max(c["secondary_rays"], 1)
+
+    # end to end through the C ABI into pinned host memory
+    host = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, pin_memory=True)
+    for w in range(args.warmup):
+        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, modes[0], TILE[0], TILE[1], host,
+                        cr.make_opts(k=K, frame_base=frame_of(rank, w, world)))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, modes[0], TILE[0], TILE[1], host,
+                        cr.make_opts(k=K, frame_base=frame_of(rank, args.warmup + s, world)))
+    e2e_s = aggregate(time.perf_counter() - t0, "max")
+    e2e_rays = aggregate(results[modes[0]]["secondary_rays_per_step"] * args.steps, "sum")
+
+    if rank != 0:
+        return
+    R = results[modes[0]]
+    # roofline of the secondary trace kernel: algorithmic bytes per ray = ray (32) + queue
+    # index (4) + hit (8) + 64 per BVH2 node visited + 48 per triangle tested
+    bytes_per_ray = 32 + 4 + 8 + 64 * R["nodes_per_ray"] + 48 * R["tris_per_ray"]
+    launches = BOUNCES
+    rays_per_launch = R["secondary_rays_per_step"] / launches
+    ms_per_launch = R["ms_trace_secondary"] / launches
+    achieved = bytes_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e9
+    peak, peak_kind = load_peaks()
+    traffic = profile_traffic("trace.cu")
+    line = {
+        "metric": METRIC, "value": round(R["mrays"], 2), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(R["ms_per_step"], 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": modes[0], "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world} (frames per rank)", "timing": "CUDA events on the render stream"},
+        "clocks": clocks,
+        "e2e": {"value": round(e2e_rays / e2e_s / 1e6, 2), "unit": "Mrays/s",
+                "h2d_bytes_per_step": 48, "d2h_bytes_per_step": cam.width * cam.height * 12},
+        "gpu_launches": int(R["launches_per_step"] * args.steps),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_trace_bvh2 (secondary)", "bytes_per_ray": round(bytes_per_ray, 1),
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "trace_only_mrays": round(R["trace_mrays"], 2),
+        "stages_ms": {k: round(R[k], 4) for k in ("ms_trace_primary", "ms_trace_secondary", "ms_shade", "ms_compact",
+                                                   "ms_sort")},
+        "comparators": {m: {"mrays": round(results[m]["mrays"], 2), "trace_only_mrays": round(results[m]["trace_mrays"], 2),
+                            "ms_per_step": round(results[m]["ms_per_step"], 4),
+                            "nodes_per_ray": round(results[m]["nodes_per_ray"], 2),
+                            "tris_per_ray": round(results[m]["tris_per_ray"], 2),
+                            "ms_sort": round(results[m]["ms_sort"], 4)}
+                        for m in modes if m != "direction_reuse"},
+        "secondary_rays_per_step": int(R["secondary_rays_per_step"]),
+    }
+    if not args.no_cpu_baseline:
+        v, thr, sample, dt = cpu_oracle_rate(sc, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mrays/s", "cores": thr, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--modes", default="direction_reuse,independent,morton_sort",
+                    help="modes to time (the first is the headline); profiling runs use one")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * cr.h -- C ABI of libcr.so: a GB300 (sm_103a) direction-reuse path tracer after
+ * "Generate Coherent Rays Directly" (Liu et al., arXiv 2310.07182).
+ *
+ * The library renders triangle scenes by wavefront path tracing on one GPU.  Its
+ * secondary rays are generated in coherent form by the paper's method: pixels are
+ * gathered into interleaved reuse groups (Sec. 3.3), each group is classed as diffuse,
+ * glossy or hybrid from its shading points' materials, and shares a tangent-space exit
+ * direction accordingly (Sec. 3.2).  Two comparators run on the same kernels:
+ * independent sampling ("NoOpt", Table 1) and Morton-code ray sorting ("TwoPoint",
+ * Table 1 and Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a cr_status; CR_OK (0) on success.  On failure nothing the call
+ *     owns is leaked, output buffers may be partly written, and cr_last_error() returns a
+ *     message for the calling thread.  No call aborts, throws across the ABI or traps the
+ *     GPU.
+ *   - Pointers documented "host or device" may be either; the kind is found with
+ *     cudaPointerGetAttributes.  Host buffers are copied through library-owned device
+ *     memory; device buffers are used in place on the call's stream.
+ *   - Buffers passed in are owned by the caller and are not retained after the call
+ *     returns (device work on the call's stream may still read or write them until that
+ *     stream is synchronised; every call below synchronises its stream before returning
+ *     unless the description says otherwise).
+ *   - A cr_scene is not thread-safe: calls on one scene must be serialised by the caller.
+ */
+#ifndef CR_H
+#define CR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CR_OK = 0,
+    CR_ERR_INVALID_ARG = 1,    /* an argument is out of range; message says which */
+    CR_ERR_OOM = 2,            /* device or host allocation failed */
+    CR_ERR_CUDA = 3,           /* a CUDA runtime call failed; message has its text */
+    CR_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out */
+    CR_ERR_STACK_OVERFLOW = 5, /* BVH deeper than the traversal stack (never for built scenes) */
+    CR_ERR_BUSY = 6,           /* result not ready yet (server polling) */
+    CR_ERR_NOT_FOUND = 7       /* unknown handle or id */
+} cr_status;
+
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+const char* cr_last_error(void);
+/* Library version string, e.g. "cr 0.1 sm_103a". */
+const char* cr_version(void);
+
+/* ---------------------------------------------------------------------------------- */
+/* Scenes.  Material classes follow Sec. 3.2: Lambert is "diffuse", GGX and mirror are
+ * "glossy or specular"; emitters end a path and take no part in grouping. */
+typedef enum { CR_MAT_LAMBERT = 0, CR_MAT_GGX = 1, CR_MAT_MIRROR = 2, CR_MAT_EMITTER = 3 } cr_mat_type;
+
+typedef struct {
+    uint32_t type;     /* cr_mat_type */
+    float albedo[3];   /* Lambert albedo, GGX/mirror F0 (Schlick), each in [0, 1] */
+    float roughness;   /* GGX alpha, in (0, 1]; ignored by other types */
+    float emission[3]; /* emitter radiance; ignored by other types */
+} cr_material;         /* 32 bytes */
+
+typedef struct {
+    float radiance[3]; /* constant environment radiance seen by rays that miss */
+} cr_env;
+
+enum { CR_BVH2 = 1u, CR_BVH8Q = 2u };
+
+typedef struct cr_scene cr_scene;
+
+/* Build a device-resident scene: a binned-SAH BVH2 (32 bins, <= 4 triangles per leaf,
+ * depth <= 64) on the host, optionally collapsed into 8-wide nodes with 8-bit
+ * conservatively quantised child boxes (bvh_flags & CR_BVH8Q; Ylitie et al. 2017, cited
+ * in Sec. 2.3), then uploaded once.
+ *   tri_xyz  host, n_tri * 9 floats: v0.xyz v1.xyz v2.xyz per triangle; all finite.
+ *   tri_mat  host, n_tri material indices < n_mat.
+ *   mats     host, n_mat materials.
+ *   env      host, may be NULL (black).
+ *   bvh_flags CR_BVH2 (always built) | CR_BVH8Q.
+ *   out      receives the handle; destroy it with cr_scene_destroy.
+ * The inputs are copied; the caller may free them when the call returns.
+ * Errors: CR_ERR_INVALID_ARG (n_tri == 0 or > 2^28, NaN/Inf vertex, material index or
+ * type out of range, NULL pointer), CR_ERR_OOM, CR_ERR_CUDA. */
+cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const uint32_t* tri_mat,
+                          const cr_material* mats, uint32_t n_mat, const cr_env* env,
+                          uint32_t bvh_flags, cr_scene** out);
+
+/* Free the scene's device and host memory (waits for the device).  NULL is a no-op. */
+cr_status cr_scene_destroy(cr_scene* scene);
+
+typedef struct {
+    uint32_t n_tri, n_mat;
+    uint32_t n_nodes2, depth2; /* BVH2 inner nodes, maximum leaf depth */
+    uint32_t n_nodes8;         /* BVH8-Q nodes (0 if not built) */
+    uint32_t pad;
+    uint64_t device_bytes;     /* scene bytes resident on the device */
+    double build_ms;           /* host build time */
+    float bounds_lo[3], bounds_hi[3];
+} cr_scene_info;
+
+cr_status cr_scene_get_info(const cr_scene* scene, cr_scene_info* info);
+
+/* ---------------------------------------------------------------------------------- */
+/* Rendering. */
+typedef struct {
+    float pos[3], look_at[3], up[3];
+    float vfov_deg;          /* vertical field of view, in (0, 180) */
+    uint32_t width, height;  /* >= 1, width * height <= 2^26 */
+} cr_camera;
+
+typedef enum { CR_INDEPENDENT = 0, CR_MORTON_SORT = 1, CR_DIRECTION_REUSE = 2 } cr_reuse_mode;
+
+/* Per-call statistics (filled when cr_render_opts.stats != NULL).  Stage times are CUDA
+ * event times on the call's stream summed over samples and bounces. */
+typedef struct {
+    double ms_total;           /* first launch to last (events) */
+    double ms_raygen, ms_trace_primary, ms_trace_secondary, ms_shade, ms_compact, ms_sort, ms_accum;
+    uint64_t primary_rays;     /* rays of the primary trace (valid pixels x spp) */
+    uint64_t secondary_rays;   /* rays traced at bounces 1..B */
+    uint64_t secondary_rays_b1;/* rays traced at bounce 1 */
+    uint64_t kernel_launches;  /* library kernels launched by the call */
+    uint64_t node_visits, tri_tests; /* counting pass only (CR_OPT_COUNT) */
+} cr_stats;
+
+/* Optional per-bounce capture (device pointers, spp must be 1).  npx = width * height.
+ * Entries of rays that were not traced / pixels not alive are left untouched, so fill the
+ * buffers beforehand (e.g. prim with -2). */
+typedef struct {
+    int32_t* prim;   /* (B+1) * npx: original triangle index hit by trace b (0 = primary), -1 miss */
+    uint8_t* cat;    /* B * npx: category of the pixel's group at step b: 0 empty, 1 diffuse, 2 glossy, 3 hybrid */
+    uint8_t* cls;    /* B * npx: class of the pixel's shading point: 0 none, 1 diffuse, 2 glossy/specular */
+    uint8_t* flags;  /* B * npx: bit0 alive at step b, bit1 spawned a secondary ray */
+    float* local;    /* B * npx * 3: tangent-space exit direction */
+    float* world;    /* B * npx * 3: world-space exit direction */
+} cr_debug;
+
+enum {
+    CR_OPT_STATS = 1u,      /* record per-stage CUDA events (adds event records between launches) */
+    CR_OPT_COUNT = 2u,      /* counting pass: count node visits / triangle tests (slower) */
+    CR_OPT_NO_SYNC = 4u,    /* return without synchronising the stream (device out_rgb only) */
+    CR_OPT_PERSISTENT = 8u  /* persistent trace kernel with an atomic ray counter */
+};
+
+typedef struct {
+    uint32_t k;            /* pixels per reuse group K; 0 = W*H.  Power of two dividing W*H, <= 256 */
+    uint32_t interleave;   /* 1: LCG-shuffled groups (Sec. 3.3, default); 0: contiguous groups */
+    uint64_t seed;         /* Philox key */
+    uint32_t frame_base;   /* frame index of the first sample (progressive rendering) */
+    uint32_t reuse_depth;  /* reuse at bounces b <= reuse_depth; 0 = every bounce */
+    uint32_t bvh;          /* CR_BVH2 (default) or CR_BVH8Q (scene must have it) */
+    uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 */
+    uint32_t flags;        /* CR_OPT_* */
+    uint32_t pad;
+    void* stream;          /* cudaStream_t to run on; NULL = legacy default stream */
+    cr_stats* stats;       /* optional, host */
+    cr_debug* debug;       /* optional, host struct of device pointers */
+} cr_render_opts;
+
+/* Fill opts with the defaults: k = 0, interleave = 1, seed = 0, frame_base = 0,
+ * reuse_depth = 0, bvh = CR_BVH2, block = 0, flags = 0, stream = NULL, stats = debug = NULL. */
+cr_status cr_render_opts_default(cr_render_opts* opts);
+
+/* Render spp samples per pixel with paths of up to max_bounces secondary rays and write
+ * the mean radiance (linear fp32 RGB, row-major, top row first) to out_rgb.
+ *   scene        from cr_scene_create.
+ *   camera       host struct.
+ *   spp          >= 1 (Sec. 3.1: several samples = one sample in "smaller pixels").
+ *   max_bounces  1..16: number of secondary rays per path (no Russian roulette).
+ *   mode         CR_INDEPENDENT (each path samples its own BSDF), CR_MORTON_SORT (the same
+ *                paths, secondary rays sorted by a 30-bit TwoPoint Morton key before each
+ *                trace), CR_DIRECTION_REUSE (Sec. 3.2-3.3).
+ *   group_w, group_h  tile W x H of the reuse-domain partition (Sec. 3.3); W*H a power of
+ *                two <= 1024.  Rays of every mode are laid out tile by tile.
+ *   out_rgb      host or device, width*height*3 floats, written once at the end.
+ * With opts == NULL (cr_render) K = W*H.  The result depends only on (scene, camera, spp,
+ * bounces, mode, W, H, K, interleave, seed, frame_base, reuse_depth): random numbers are
+ * keyed by (pixel, frame, bounce), never by ray order, so CR_MORTON_SORT gives the same
+ * image as CR_INDEPENDENT bit for bit.
+ * Errors: CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA. */
+cr_status cr_render(cr_scene* scene, const cr_camera* camera, uint32_t spp, uint32_t max_bounces,
+                    cr_reuse_mode mode, uint32_t group_w, uint32_t group_h, float* out_rgb);
+
+cr_status cr_render_ex(cr_scene* scene, const cr_camera* camera, uint32_t spp, uint32_t max_bounces,
+                       cr_reuse_mode mode, uint32_t group_w, uint32_t group_h, float* out_rgb,
+                       const cr_render_opts* opts);
+
+/* ---------------------------------------------------------------------------------- */
+/* Parity / debug entry points (the same kernels as the render path). */
+
+/* Closest hit of n rays (Sec. 1: the intersection step).
+ *   rays      host or device, n * 8 floats: o.xyz, (unused), d.xyz, tmax (inf = unbounded).
+ *   skip_prim host or device or NULL: n original triangle indices the ray must ignore (-1 none).
+ *   prim      host or device, n int32: original index of the closest hit, -1 if none.
+ *   t         host or device, n floats: hit distance in units of |d| (inf if none).
+ * Hit rule: watertight test (Woop et al. 2013), t > 0, edges inclusive; equal t goes to the
+ * smaller original index.  opts may be NULL (bvh, block, stream, flags are read). */
+cr_status cr_trace_rays(cr_scene* scene, const float* rays, const int32_t* skip_prim, uint32_t n,
+                        int32_t* prim, float* t, const cr_render_opts* opts);
+
+/* Interleaved grouping (Sec. 3.3) of one frame: slot_of_pixel[p] = tile * W*H + sigma(i),
+ * where i is the pixel's row-major index within its tile; its group is slot / K.
+ * slot_of_pixel: host or device, width*height uint32. */
+cr_status cr_debug_groups(uint32_t width, uint32_t height, uint32_t group_w, uint32_t group_h,
+                          uint32_t interleave, uint64_t seed, uint32_t frame, uint32_t* slot_of_pixel);
+
+/* Philox4x32-10 of n counters under key = seed: out[4i..4i+3] = philox(seed, ctr[4i..4i+3]).
+ * ctr, out: host or device, n*4 uint32. */
+cr_status cr_debug_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out);
+
+/* The device BSDF samplers, one call per row (fp32, same code as the render path):
+ *   kind 0: cosine hemisphere from (u1, u2); kind 1: GGX with alpha = param[4i+0] and
+ *   F0 = param[4i+1..3] about wo; kind 2: mirror.  wo: n*3, u: n*2, param: n*4,
+ *   wi/weight: n*3, valid: n.  All host or device.  Also sincos: kind 3 writes
+ *   (sin x, cos x, 0) of x = u[2i] to wi. */
+cr_status cr_debug_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param,
+                          float* wi, float* weight, uint8_t* valid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libcr.so (include/cr.h).
+
+Each ``cr_*`` function here marshals its arguments and calls the C entry point of the same
+name; every step of the path runs in the library's CUDA kernels.  PyTorch is used only for
+device memory and streams: arrays may be numpy arrays (host) or torch tensors (host or
+CUDA); CUDA tensors are passed by ``data_ptr()`` and the call runs on torch's current
+stream unless a stream is given.
+
+The library must have been built (``python -m paper_2310_07182_gb300.build`` or
+``__graft_entry__.build()``); importing a function that needs it raises if libcr.so is
+missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcr.so")
+
+CR_OK, CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT, CR_ERR_STACK_OVERFLOW, CR_ERR_BUSY, \
+    CR_ERR_NOT_FOUND = range(8)
+CR_MAT_LAMBERT, CR_MAT_GGX, CR_MAT_MIRROR, CR_MAT_EMITTER = range(4)
+CR_BVH2, CR_BVH8Q = 1, 2
+CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE = 0, 1, 2
+CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT = 1, 2, 4, 8
+MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE}
+
+
+class CrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cr status {status}: {msg}")
+        self.status = status
+
+
+class cr_material(C.Structure):
+    _fields_ = [("type", C.c_uint32), ("albedo", C.c_float * 3), ("roughness", C.c_float),
+                ("emission", C.c_float * 3)]
+
+
+class cr_env(C.Structure):
+    _fields_ = [("radiance", C.c_float * 3)]
+
+
+class cr_scene_info(C.Structure):
+    _fields_ = [("n_tri", C.c_uint32), ("n_mat", C.c_uint32), ("n_nodes2", C.c_uint32), ("depth2", C.c_uint32),
+                ("n_nodes8", C.c_uint32), ("pad", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("build_ms", C.c_double), ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3)]
+
+
+class cr_camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class cr_stats(C.Structure):
+    _fields_ = [("ms_total", C.c_double), ("ms_raygen", C.c_double), ("ms_trace_primary", C.c_double),
+                ("ms_trace_secondary", C.c_double), ("ms_shade", C.c_double), ("ms_compact", C.c_double),
+                ("ms_sort", C.c_double), ("ms_accum", C.c_double), ("primary_rays", C.c_uint64),
+                ("secondary_rays", C.c_uint64), ("secondary_rays_b1", C.c_uint64),
+                ("kernel_launches", C.c_uint64), ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cr_debug(C.Structure):
+    _fields_ = [("prim", C.c_void_p), ("cat", C.c_void_p), ("cls", C.c_void_p), ("flags", C.c_void_p),
+                ("local", C.c_void_p), ("world", C.c_void_p)]
+
+
+class cr_render_opts(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("interleave", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
+                ("reuse_depth", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32),
+                ("pad", C.c_uint32), ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
+                ("debug", C.POINTER(cr_debug))]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("cr_last_error", C.c_char_p, []),
+    ("cr_version", C.c_char_p, []),
+    ("cr_scene_create", C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
+                                  C.c_uint32, C.POINTER(C.c_void_p)]),
+    ("cr_scene_destroy", C.c_int, [C.c_void_p]),
+    ("cr_scene_get_info", C.c_int, [C.c_void_p, C.POINTER(cr_scene_info)]),
+    ("cr_render_opts_default", C.c_int, [C.POINTER(cr_render_opts)]),
+    ("cr_render", C.c_int, [C.c_void_p, C.POINTER(cr_camera), C.c_uint32, C.c_uint32, C.c_int, C.c_uint32,
+                            C.c_uint32, C.c_void_p]),
+    ("cr_render_ex", C.c_int, [C.c_void_p, C.POINTER(cr_camera), C.c_uint32, C.c_uint32, C.c_int, C.c_uint32,
+                               C.c_uint32, C.c_void_p, C.POINTER(cr_render_opts)]),
+    ("cr_trace_rays", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
+                                C.POINTER(cr_render_opts)]),
+    ("cr_debug_groups", C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
+                                  C.c_uint32, C.c_void_p]),
+    ("cr_debug_philox", C.c_int, [C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p]),
+    ("cr_debug_sample", C.c_int, [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+]
+
+
+def exported_names():
+    return [n for n, _, _ in _SIGS]
+
+
+def lib():
+    """Load libcr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcr.so not built ({LIB_PATH}); run paper_2310_07182_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != CR_OK:
+        raise CrError(status, lib().cr_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(type(x))
+
+
+def _current_stream(tensors=()):
+    for t in tensors:
+        if hasattr(t, "is_cuda") and t.is_cuda:
+            import torch
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+# ---------------------------------------------------------------------------------------
+# Entry points with the ABI's names.
+def cr_version() -> str:
+    return lib().cr_version().decode()
+
+
+def cr_scene_create(tri_xyz, tri_mat, mat_type, mat_params, env=(0.0, 0.0, 0.0), bvh_flags=CR_BVH2):
+    """Build and upload a scene; returns the opaque handle (an int)."""
+    tri_xyz = np.ascontiguousarray(tri_xyz, dtype=np.float32).reshape(-1, 9)
+    tri_mat = np.ascontiguousarray(tri_mat, dtype=np.uint32)
+    mat_type = np.asarray(mat_type, dtype=np.uint32)
+    mat_params = np.asarray(mat_params, dtype=np.float32).reshape(-1, 7)
+    mats = (cr_material * len(mat_type))()
+    for i, (t, p) in enumerate(zip(mat_type, mat_params)):
+        mats[i].type = int(t)
+        mats[i].albedo[:] = [float(v) for v in p[0:3]]
+        mats[i].roughness = float(p[3])
+        mats[i].emission[:] = [float(v) for v in p[4:7]]
+    e = cr_env((C.c_float * 3)(*[float(v) for v in env]))
+    out = C.c_void_p()
+    _check(lib().cr_scene_create(_ptr(tri_xyz), tri_xyz.shape[0], _ptr(tri_mat), C.addressof(mats), len(mat_type),
+                                 C.addressof(e), bvh_flags, C.byref(out)))
+    return out.value
+
+
+def cr_scene_destroy(handle):
+    _check(lib().cr_scene_destroy(handle))
+
+
+def cr_scene_get_info(handle) -> dict:
+    info = cr_scene_info()
+    _check(lib().cr_scene_get_info(handle, C.byref(info)))
+    d = {k: getattr(info, k) for k, _ in info._fields_}
+    d["bounds_lo"] = list(info.bounds_lo)
+    d["bounds_hi"] = list(info.bounds_hi)
+    return d
+
+
+def make_camera(cam) -> cr_camera:
+    return cr_camera((C.c_float * 3)(*cam.pos), (C.c_float * 3)(*cam.look_at), (C.c_float * 3)(*cam.up),
+                     float(cam.vfov_deg), int(cam.width), int(cam.height))
+
+
+def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_BVH2, block=0, flags=0,
+              stream=None, stats=None, debug=None) -> cr_render_opts:
+    o = cr_render_opts()
+    _check(lib().cr_render_opts_default(C.byref(o)))
+    o.k, o.interleave, o.seed, o.frame_base = k, int(interleave), seed, frame_base
+    o.reuse_depth, o.bvh, o.block, o.flags = reuse_depth, bvh, block, flags
+    o.stream = stream
+    if stats is not None:
+        o.stats = C.pointer(stats)
+    if debug is not None:
+        o.debug = C.pointer(debug)
+    return o
+
+
+def cr_render(handle, cam, spp, max_bounces, mode, group_w, group_h, out_rgb):
+    c = make_camera(cam)
+    _check(lib().cr_render(handle, C.byref(c), spp, max_bounces, MODES.get(mode, mode), group_w, group_h,
+                           _ptr(out_rgb)))
+    return out_rgb
+
+
+def cr_render_ex(handle, cam, spp, max_bounces, mode, group_w, group_h, out_rgb, opts: cr_render_opts | None):
+    c = make_camera(cam)
+    if opts is not None and opts.stream is None:
+        opts.stream = _current_stream([out_rgb])
+    _check(lib().cr_render_ex(handle, C.byref(c), spp, max_bounces, MODES.get(mode, mode), group_w, group_h,
+                              _ptr(out_rgb), C.byref(opts) if opts is not None else None))
+    return out_rgb
+
+
+def cr_trace_rays(handle, rays, skip, prim, t, opts: cr_render_opts | None = None):
+    n = rays.shape[0]
+    if opts is not None and opts.stream is None:
+        opts.stream = _current_stream([rays, prim, t])
+    _check(lib().cr_trace_rays(handle, _ptr(rays), _ptr(skip), n, _ptr(prim), _ptr(t),
+                               C.byref(opts) if opts is not None else None))
+
+
+def cr_debug_groups(width, height, group_w, group_h, interleave, seed, frame, out):
+    _check(lib().cr_debug_groups(width, height, group_w, group_h, int(interleave), seed, frame, _ptr(out)))
+    return out
+
+
+def cr_debug_philox(seed, ctr, out):
+    _check(lib().cr_debug_philox(seed, _ptr(ctr), ctr.shape[0], _ptr(out)))
+    return out
+
+
+def cr_debug_sample(kind, n, wo, u, param, wi, weight, valid):
+    _check(lib().cr_debug_sample(kind, n, _ptr(wo), _ptr(u), _ptr(param), _ptr(wi), _ptr(weight), _ptr(valid)))
+
+
+# ---------------------------------------------------------------------------------------
+# Convenience layer.
+class Scene:
+    """Device-resident scene built from a ``scenes.Scene`` (or raw arrays)."""
+
+    def __init__(self, sc, bvh_flags=CR_BVH2):
+        self.src = sc
+        self.handle = cr_scene_create(sc.tri_xyz, sc.tri_mat, sc.mat_type, sc.mat_params, sc.env, bvh_flags)
+        self.info = cr_scene_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            cr_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
+               seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
+               debug=None, stream=None):
+        """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
+        CUDA tensor by default).  Returns (out, stats dict or None)."""
+        import torch
+        cam = cam or self.src.camera
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+        st = cr_stats() if stats else None
+        o = make_opts(k=k, interleave=interleave, seed=seed, frame_base=frame_base, reuse_depth=reuse_depth, bvh=bvh,
+                      block=block, flags=flags | (CR_OPT_STATS if stats else 0), stream=stream, stats=st,
+                      debug=debug)
+        cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
+        return out, (st.as_dict() if st is not None else None)
+
+    def trace(self, rays, skip=None, *, bvh=CR_BVH2, flags=0, block=0, stats=False):
+        """Closest hits of (n, 8) rays (torch CUDA tensor or numpy) -> (prim, t[, stats])."""
+        import torch
+        n = rays.shape[0]
+        dev = rays.device if isinstance(rays, torch.Tensor) and rays.is_cuda else None
+        if dev is not None:
+            prim = torch.empty(n, dtype=torch.int32, device=dev)
+            t = torch.empty(n, dtype=torch.float32, device=dev)
+        else:
+            prim = np.empty(n, dtype=np.int32)
+            t = np.empty(n, dtype=np.float32)
+        st = cr_stats() if stats else None
+        o = make_opts(bvh=bvh, flags=flags, block=block, stats=st)
+        cr_trace_rays(self.handle, rays, skip, prim, t, o)
+        return (prim, t, st.as_dict()) if stats else (prim, t)
+
+
+def debug_buffers(width, height, max_bounces, device="cuda"):
+    """Allocate (and pre-fill) the per-bounce capture buffers; returns (cr_debug, dict of tensors)."""
+    import torch
+    npx = width * height
+    B = max_bounces
+    bufs = dict(prim=torch.full((B + 1, npx), -2, dtype=torch.int32, device=device),
+                cat=torch.full((B, npx), 255, dtype=torch.uint8, device=device),
+                cls=torch.zeros((B, npx), dtype=torch.uint8, device=device),
+                flags=torch.zeros((B, npx), dtype=torch.uint8, device=device),
+                local=torch.zeros((B, npx, 3), dtype=torch.float32, device=device),
+                world=torch.zeros((B, npx, 3), dtype=torch.float32, device=device))
+    d = cr_debug(*[bufs[k].data_ptr() for k in ("prim", "cat", "cls", "flags", "local", "world")])
+    return d, bufs

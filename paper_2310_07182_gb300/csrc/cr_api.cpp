@@ -1,0 +1,731 @@
+// cr_api.cpp -- the C ABI of libcr.so (include/cr.h): argument checking, scene upload,
+// render orchestration of the wavefront stages on one stream, and the parity entry points.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "cr_internal.h"
+
+namespace cr {
+namespace {
+
+thread_local std::string g_err;
+
+cr_status fail(cr_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CR_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            cr_status s_ = e_ == cudaErrorMemoryAllocation ? CR_ERR_OOM : CR_ERR_CUDA;    \
+            return fail(s_, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                 \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device allocation released on scope exit unless kept.
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t n) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = n;
+        return cudaMalloc(&p, n ? n : 16);
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+} // namespace
+
+CamBasis make_camera(const cr_camera& c) {
+    double p[3] = {c.pos[0], c.pos[1], c.pos[2]};
+    double la[3] = {c.look_at[0], c.look_at[1], c.look_at[2]};
+    double up[3] = {c.up[0], c.up[1], c.up[2]};
+    double f[3] = {la[0] - p[0], la[1] - p[1], la[2] - p[2]};
+    auto norm = [](double* a) {
+        double l = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        a[0] /= l;
+        a[1] /= l;
+        a[2] /= l;
+    };
+    auto cross = [](const double* a, const double* b, double* r) {
+        r[0] = a[1] * b[2] - a[2] * b[1];
+        r[1] = a[2] * b[0] - a[0] * b[2];
+        r[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    norm(f);
+    double r[3], u[3];
+    cross(f, up, r);
+    norm(r);
+    cross(r, f, u);
+    const double th = std::tan(c.vfov_deg * (3.14159265358979323846 / 180.0) * 0.5);
+    CamBasis b;
+    for (int k = 0; k < 3; ++k) {
+        b.pos[k] = c.pos[k];
+        b.fwd[k] = (float)f[k];
+        b.right[k] = (float)r[k];
+        b.up[k] = (float)u[k];
+    }
+    b.ty = (float)th;
+    b.tx = (float)(th * ((double)c.width / (double)c.height));
+    b.width = c.width;
+    b.height = c.height;
+    return b;
+}
+
+} // namespace cr
+
+// ------------------------------------------------------------------------------------
+struct cr_scene {
+    cr::DevScene dev;
+    cr_scene_info info;
+    void* d_nodes2 = nullptr;
+    void* d_nodes8 = nullptr;
+    void* d_tris = nullptr;
+    void* d_mats = nullptr;
+    // render workspace, grown on demand
+    cr::PathBuffers pb;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    float* d_out = nullptr;
+    size_t out_cap = 0;
+};
+
+using namespace cr;
+
+extern "C" const char* cr_last_error(void) { return g_err.c_str(); }
+extern "C" const char* cr_version(void) { return "cr 0.1 sm_103a"; }
+
+extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const uint32_t* tri_mat,
+                                     const cr_material* mats, uint32_t n_mat, const cr_env* env, uint32_t bvh_flags,
+                                     cr_scene** out) {
+    g_err.clear();
+    if (!out) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: out is NULL");
+    *out = nullptr;
+    if (!tri_xyz || !tri_mat || !mats) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: NULL array");
+    if (n_tri == 0 || n_tri > (1u << 28)) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: n_tri=%u out of range", n_tri);
+    if (n_mat == 0) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: n_mat is 0");
+    if (bvh_flags & ~(uint32_t)(CR_BVH2 | CR_BVH8Q)) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: bad bvh_flags");
+    if (bvh_flags & CR_BVH8Q) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: CR_BVH8Q is not available in this build");
+    for (size_t i = 0; i < 9 * (size_t)n_tri; ++i)
+        if (!std::isfinite(tri_xyz[i]))
+            return fail(CR_ERR_INVALID_ARG, "cr_scene_create: vertex coordinate %zu of triangle %zu is not finite", i % 9,
+                        i / 9);
+    for (uint32_t t = 0; t < n_tri; ++t)
+        if (tri_mat[t] >= n_mat)
+            return fail(CR_ERR_INVALID_ARG, "cr_scene_create: triangle %u uses material %u >= n_mat %u", t, tri_mat[t], n_mat);
+    for (uint32_t m = 0; m < n_mat; ++m) {
+        if (mats[m].type > CR_MAT_EMITTER) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: material %u type %u", m, mats[m].type);
+        if (mats[m].type == CR_MAT_GGX && !(mats[m].roughness > 0.0f && mats[m].roughness <= 1.0f))
+            return fail(CR_ERR_INVALID_ARG, "cr_scene_create: material %u roughness %g not in (0, 1]", m, mats[m].roughness);
+    }
+    std::unique_ptr<cr_scene> s(new (std::nothrow) cr_scene());
+    if (!s) return fail(CR_ERR_OOM, "cr_scene_create: host allocation");
+    const auto t0 = std::chrono::steady_clock::now();
+    const unsigned hc = std::thread::hardware_concurrency();
+    HostBVH2 b2;
+    try {
+        b2 = build_bvh2(tri_xyz, n_tri, hc ? (int)hc : 4);
+    } catch (const std::bad_alloc&) {
+        return fail(CR_ERR_OOM, "cr_scene_create: host allocation during BVH build");
+    }
+    // triangles in leaf order: v0 | original index, v1 | material, v2 | 0
+    std::vector<float> tris(12 * (size_t)n_tri);
+    for (uint32_t i = 0; i < n_tri; ++i) {
+        const uint32_t t = b2.leaf_order[i];
+        float* o = &tris[12 * (size_t)i];
+        for (int v = 0; v < 3; ++v)
+            for (int k = 0; k < 3; ++k) o[4 * v + k] = tri_xyz[9 * (size_t)t + 3 * v + k];
+        int32_t orig = (int32_t)t, mat = (int32_t)tri_mat[t];
+        std::memcpy(&o[3], &orig, 4);
+        std::memcpy(&o[7], &mat, 4);
+        o[11] = 0.0f;
+    }
+    std::vector<float> mt(8 * (size_t)n_mat);
+    for (uint32_t m = 0; m < n_mat; ++m) {
+        int32_t ty = (int32_t)mats[m].type;
+        std::memcpy(&mt[8 * m], &ty, 4);
+        mt[8 * m + 1] = mats[m].albedo[0];
+        mt[8 * m + 2] = mats[m].albedo[1];
+        mt[8 * m + 3] = mats[m].albedo[2];
+        mt[8 * m + 4] = mats[m].roughness;
+        mt[8 * m + 5] = mats[m].emission[0];
+        mt[8 * m + 6] = mats[m].emission[1];
+        mt[8 * m + 7] = mats[m].emission[2];
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    DevMem dn, dt, dm;
+    CR_CUDA(dn.alloc(b2.nodes.size() * sizeof(float)));
+    CR_CUDA(dt.alloc(tris.size() * sizeof(float)));
+    CR_CUDA(dm.alloc(mt.size() * sizeof(float)));
+    CR_CUDA(cudaMemcpy(dn.p, b2.nodes.data(), dn.bytes, cudaMemcpyHostToDevice));
+    CR_CUDA(cudaMemcpy(dt.p, tris.data(), dt.bytes, cudaMemcpyHostToDevice));
+    CR_CUDA(cudaMemcpy(dm.p, mt.data(), dm.bytes, cudaMemcpyHostToDevice));
+    s->d_nodes2 = dn.p;
+    s->d_tris = dt.p;
+    s->d_mats = dm.p;
+    dn.p = dt.p = dm.p = nullptr;
+    s->dev.nodes2 = static_cast<const float4*>(s->d_nodes2);
+    s->dev.tris = static_cast<const float4*>(s->d_tris);
+    s->dev.mats = static_cast<const float4*>(s->d_mats);
+    for (int k = 0; k < 3; ++k) {
+        s->dev.env[k] = env ? env->radiance[k] : 0.0f;
+        s->dev.lo[k] = b2.lo[k];
+        s->dev.hi[k] = b2.hi[k];
+    }
+    s->dev.n_tri = n_tri;
+    s->dev.n_mat = n_mat;
+    std::memset(&s->info, 0, sizeof(s->info));
+    s->info.n_tri = n_tri;
+    s->info.n_mat = n_mat;
+    s->info.n_nodes2 = b2.n_nodes;
+    s->info.depth2 = b2.depth;
+    s->info.device_bytes = b2.nodes.size() * 4 + tris.size() * 4 + mt.size() * 4;
+    s->info.build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    for (int k = 0; k < 3; ++k) {
+        s->info.bounds_lo[k] = b2.lo[k];
+        s->info.bounds_hi[k] = b2.hi[k];
+    }
+    *out = s.release();
+    return CR_OK;
+}
+
+static void free_workspace(cr_scene* s) {
+    if (s->ws) cudaFree(s->ws);
+    s->ws = nullptr;
+    s->ws_bytes = 0;
+    s->pb = PathBuffers();
+    if (s->d_out) cudaFree(s->d_out);
+    s->d_out = nullptr;
+    s->out_cap = 0;
+}
+
+extern "C" cr_status cr_scene_destroy(cr_scene* s) {
+    g_err.clear();
+    if (!s) return CR_OK;
+    cudaDeviceSynchronize();
+    free_workspace(s);
+    if (s->d_nodes2) cudaFree(s->d_nodes2);
+    if (s->d_nodes8) cudaFree(s->d_nodes8);
+    if (s->d_tris) cudaFree(s->d_tris);
+    if (s->d_mats) cudaFree(s->d_mats);
+    delete s;
+    return CR_OK;
+}
+
+extern "C" cr_status cr_scene_get_info(const cr_scene* s, cr_scene_info* info) {
+    g_err.clear();
+    if (!s || !info) return fail(CR_ERR_INVALID_ARG, "cr_scene_get_info: NULL argument");
+    *info = s->info;
+    return CR_OK;
+}
+
+extern "C" cr_status cr_render_opts_default(cr_render_opts* o) {
+    g_err.clear();
+    if (!o) return fail(CR_ERR_INVALID_ARG, "cr_render_opts_default: NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->interleave = 1;
+    o->bvh = CR_BVH2;
+    return CR_OK;
+}
+
+// Carve the render workspace for n_slots slots and npx pixels out of one allocation.
+static cr_status ensure_workspace(cr_scene* s, uint32_t n_slots, uint32_t npx) {
+    PathBuffers& b = s->pb;
+    if (b.n_slots >= n_slots && b.n_px_cap >= npx && s->ws) {
+        return CR_OK;
+    }
+    cudaDeviceSynchronize();
+    free_workspace(s);
+    const size_t ns = n_slots, np = npx;
+    const size_t n_cblocks = compact_blocks(n_slots) + 1;
+    const size_t n_hist = sort_hist_len(n_slots);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_pixel = take(4 * ns), o_ro = take(16 * ns), o_rd = take(16 * ns), o_hit = take(8 * ns),
+                 o_beta = take(16 * ns), o_rad = take(16 * ns), o_alive = take(ns), o_rq = take(4 * ns),
+                 o_gq = take(2 * 4 * ns), o_counts = take(4 * kCountsWords), o_bc = take(2 * 4 * n_cblocks),
+                 o_keys = take(2 * 4 * ns), o_vals = take(2 * 4 * ns), o_hist = take(4 * n_hist),
+                 o_acc = take(16 * np);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CR_ERR_OOM, "render workspace of %zu bytes: %s", off, cudaGetErrorString(e));
+    }
+    char* c = static_cast<char*>(base);
+    s->ws = base;
+    s->ws_bytes = off;
+    b.n_slots = n_slots;
+    b.n_px_cap = npx;
+    b.pixel = reinterpret_cast<int32_t*>(c + o_pixel);
+    b.ray_o = reinterpret_cast<float4*>(c + o_ro);
+    b.ray_d = reinterpret_cast<float4*>(c + o_rd);
+    b.hit = reinterpret_cast<int2*>(c + o_hit);
+    b.beta = reinterpret_cast<float4*>(c + o_beta);
+    b.radiance = reinterpret_cast<float4*>(c + o_rad);
+    b.alive = reinterpret_cast<uint8_t*>(c + o_alive);
+    b.ray_queue = reinterpret_cast<int32_t*>(c + o_rq);
+    b.group_queue = reinterpret_cast<int32_t*>(c + o_gq);
+    b.counts = reinterpret_cast<uint32_t*>(c + o_counts);
+    b.block_counts = reinterpret_cast<uint32_t*>(c + o_bc);
+    b.n_blocks_cap = (uint32_t)n_cblocks;
+    b.keys = reinterpret_cast<uint32_t*>(c + o_keys);
+    b.vals = reinterpret_cast<int32_t*>(c + o_vals);
+    b.sort_hist = reinterpret_cast<uint32_t*>(c + o_hist);
+    b.sort_hist_cap = (uint32_t)n_hist;
+    b.accum = reinterpret_cast<float4*>(c + o_acc);
+    b.counters = reinterpret_cast<unsigned long long*>(b.counts + kCounterWord);
+    return CR_OK;
+}
+
+static bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+static cr_status check_camera(const cr_camera* cam) {
+    if (!cam) return fail(CR_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width == 0 || cam->height == 0 || (uint64_t)cam->width * cam->height > (1ull << 26))
+        return fail(CR_ERR_INVALID_ARG, "camera size %ux%u out of range", cam->width, cam->height);
+    if (!(cam->vfov_deg > 0.0f && cam->vfov_deg < 180.0f))
+        return fail(CR_ERR_INVALID_ARG, "camera vfov %g not in (0, 180)", cam->vfov_deg);
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(cam->pos[k]) || !std::isfinite(cam->look_at[k]) || !std::isfinite(cam->up[k]))
+            return fail(CR_ERR_INVALID_ARG, "camera has a non-finite coordinate");
+    const float f[3] = {cam->look_at[0] - cam->pos[0], cam->look_at[1] - cam->pos[1], cam->look_at[2] - cam->pos[2]};
+    const float c[3] = {f[1] * cam->up[2] - f[2] * cam->up[1], f[2] * cam->up[0] - f[0] * cam->up[2],
+                        f[0] * cam->up[1] - f[1] * cam->up[0]};
+    if (c[0] == 0.0f && c[1] == 0.0f && c[2] == 0.0f)
+        return fail(CR_ERR_INVALID_ARG, "camera up is parallel to the view direction (or look_at == pos)");
+    return CR_OK;
+}
+
+// Per-stage CUDA events recorded on the render stream without host synchronisation; the
+// elapsed times are read once, after the stream has finished.
+struct StageEvents {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<size_t, double*>> marks; // (index of start event, accumulator)
+    cudaEvent_t get() {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pool.push_back(e);
+        return e;
+    }
+    void begin(cudaStream_t s, double* acc) {
+        if (!on) return;
+        st = s;
+        cudaEvent_t e = get();
+        if (!e) return;
+        cudaEventRecord(e, st);
+        marks.emplace_back(pool.size() - 1, acc);
+    }
+    void end() {
+        if (!on || marks.empty() || marks.back().first != pool.size() - 1) return;
+        cudaEvent_t e = get();
+        if (e) cudaEventRecord(e, st);
+    }
+    void resolve() {
+        for (auto& m : marks) {
+            if (m.first + 1 >= pool.size()) continue;
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, pool[m.first], pool[m.first + 1]) == cudaSuccess) *m.second += ms;
+        }
+    }
+    ~StageEvents() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t spp, uint32_t max_bounces,
+                                  cr_reuse_mode mode, uint32_t group_w, uint32_t group_h, float* out_rgb,
+                                  const cr_render_opts* opts_in) {
+    g_err.clear();
+    if (!s) return fail(CR_ERR_INVALID_ARG, "cr_render: scene is NULL");
+    if (!out_rgb) return fail(CR_ERR_INVALID_ARG, "cr_render: out_rgb is NULL");
+    cr_status st = check_camera(cam);
+    if (st != CR_OK) return st;
+    if (spp == 0) return fail(CR_ERR_INVALID_ARG, "cr_render: spp must be >= 1");
+    if (max_bounces == 0 || max_bounces > 16) return fail(CR_ERR_INVALID_ARG, "cr_render: max_bounces %u not in [1, 16]", max_bounces);
+    if (mode != CR_INDEPENDENT && mode != CR_MORTON_SORT && mode != CR_DIRECTION_REUSE)
+        return fail(CR_ERR_INVALID_ARG, "cr_render: unknown mode %d", (int)mode);
+    const uint32_t m = group_w * group_h;
+    if (group_w == 0 || group_h == 0 || !pow2(m) || m > 1024)
+        return fail(CR_ERR_INVALID_ARG, "cr_render: group_w*group_h = %ux%u must be a power of two <= 1024", group_w, group_h);
+    cr_render_opts o;
+    cr_render_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    const uint32_t K = o.k ? o.k : m;
+    if (!pow2(K) || m % K != 0 || K > 256)
+        return fail(CR_ERR_INVALID_ARG, "cr_render: K=%u must be a power of two dividing W*H=%u and <= 256", K, m);
+    if (o.bvh != CR_BVH2 && o.bvh != 0)
+        return fail(CR_ERR_INVALID_ARG, "cr_render: bvh %u not available for this scene", o.bvh);
+    const int block = o.block ? (int)o.block : 128;
+    if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "cr_render: block %d", block);
+    if (o.debug && spp != 1) return fail(CR_ERR_INVALID_ARG, "cr_render: debug capture needs spp == 1");
+    if (o.debug && (!o.debug->prim || !o.debug->cat || !o.debug->cls || !o.debug->flags || !o.debug->local || !o.debug->world))
+        return fail(CR_ERR_INVALID_ARG, "cr_render: debug capture needs all six buffers");
+    cudaStream_t stream = static_cast<cudaStream_t>(o.stream);
+
+    RenderParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.cam = make_camera(*cam);
+    p.tile_w = group_w;
+    p.tile_h = group_h;
+    p.m = m;
+    p.k = K;
+    p.tiles_x = (cam->width + group_w - 1) / group_w;
+    p.tiles_y = (cam->height + group_h - 1) / group_h;
+    p.interleave = o.interleave ? 1u : 0u;
+    p.seed = o.seed;
+    p.max_bounces = max_bounces;
+    const uint64_t n_slots64 = (uint64_t)p.tiles_x * p.tiles_y * m;
+    if (n_slots64 > (1ull << 27)) return fail(CR_ERR_INVALID_ARG, "cr_render: %llu slots is too many", (unsigned long long)n_slots64);
+    const uint32_t n_slots = (uint32_t)n_slots64;
+    const uint32_t npx = cam->width * cam->height;
+    st = ensure_workspace(s, n_slots, npx);
+    if (st != CR_OK) return st;
+    PathBuffers& b = s->pb;
+    b.n_groups = n_slots / K;
+    const bool out_dev = is_device_ptr(out_rgb);
+    if (!out_dev && (o.flags & CR_OPT_NO_SYNC))
+        return fail(CR_ERR_INVALID_ARG, "cr_render: CR_OPT_NO_SYNC needs a device out_rgb");
+    if (!out_dev && s->out_cap < (size_t)npx * 3) {
+        if (s->d_out) cudaFree(s->d_out);
+        s->d_out = nullptr;
+        s->out_cap = 0;
+        CR_CUDA(cudaMalloc(&s->d_out, sizeof(float) * 3 * (size_t)npx));
+        s->out_cap = (size_t)npx * 3;
+    }
+
+    LaunchCount lc;
+    StageEvents ev;
+    cr_stats stats;
+    std::memset(&stats, 0, sizeof(stats));
+    ev.on = (o.flags & CR_OPT_STATS) && o.stats;
+    ev.pool.reserve(64 + 16 * (size_t)spp * (max_bounces + 2));
+    cudaEvent_t e_all[2];
+    if (o.stats) {
+        CR_CUDA(cudaEventCreate(&e_all[0]));
+        CR_CUDA(cudaEventCreate(&e_all[1]));
+        CR_CUDA(cudaEventRecord(e_all[0], stream));
+    }
+    CR_CUDA(cudaMemsetAsync(b.counts, 0, 4 * kCountsWords, stream));
+    CR_CUDA(cudaMemsetAsync(b.accum, 0, 16 * (size_t)npx, stream));
+
+    TraceArgs ta;
+    ta.ray_o = b.ray_o;
+    ta.ray_d = b.ray_d;
+    ta.hit = b.hit;
+    ta.block = block;
+    ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
+    ta.work_counter = b.counts + 2;
+    const DevScene& ds = s->dev;
+
+    for (uint32_t si = 0; si < spp; ++si) {
+        p.frame = o.frame_base + si;
+        ev.begin(stream, &stats.ms_raygen);
+        launch_raygen(p, b, stream, lc);
+        ev.end();
+        // primary rays: every slot, in slot (tile, group) order
+        ta.queue = nullptr;
+        ta.queue_count = nullptr;
+        ta.n_max = n_slots;
+        ta.counters = nullptr;
+        if (ta.persistent) CR_CUDA(cudaMemsetAsync(ta.work_counter, 0, 4, stream));
+        ev.begin(stream, &stats.ms_trace_primary);
+        launch_trace(ds, ta, stream, lc);
+        ev.end();
+        for (uint32_t bnc = 1; bnc <= max_bounces; ++bnc) {
+            p.bounce = bnc;
+            p.final_pass = 0;
+            p.reuse = (mode == CR_DIRECTION_REUSE && (o.reuse_depth == 0 || bnc <= o.reuse_depth)) ? 1u : 0u;
+            ev.begin(stream, &stats.ms_shade);
+            launch_shade(ds, p, b, bnc == 1, o.debug, stream, lc);
+            ev.end();
+            ev.begin(stream, &stats.ms_compact);
+            launch_compact(p, b, bnc == 1, stream, lc);
+            ev.end();
+            ta.queue = b.ray_queue;
+            ta.queue_count = b.counts + 8 + 2 * bnc;
+            ta.n_max = n_slots;
+            if (mode == CR_MORTON_SORT) {
+                ev.begin(stream, &stats.ms_sort);
+                ta.queue = launch_morton_sort(ds, b, bnc, stream, lc);
+                ev.end();
+            }
+            ta.counters = (o.flags & CR_OPT_COUNT) ? b.counters : nullptr;
+            if (ta.persistent) CR_CUDA(cudaMemsetAsync(ta.work_counter, 0, 4, stream));
+            ev.begin(stream, &stats.ms_trace_secondary);
+            launch_trace(ds, ta, stream, lc);
+            ev.end();
+        }
+        p.bounce = max_bounces + 1;
+        p.final_pass = 1;
+        p.reuse = 0;
+        ev.begin(stream, &stats.ms_shade);
+        launch_shade(ds, p, b, false, o.debug, stream, lc);
+        ev.end();
+        ev.begin(stream, &stats.ms_accum);
+        launch_accumulate(p, b, stream, lc);
+        ev.end();
+    }
+    float* dst = out_dev ? out_rgb : s->d_out;
+    launch_output(b, npx, 1.0f / (float)spp, dst, stream, lc);
+    CR_CUDA(cudaGetLastError());
+    if (!out_dev) CR_CUDA(cudaMemcpyAsync(out_rgb, s->d_out, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, stream));
+    if (o.stats) {
+        CR_CUDA(cudaEventRecord(e_all[1], stream));
+        uint64_t host_counts[kCountsWords / 2];
+        CR_CUDA(cudaMemcpyAsync(host_counts, b.counts, 4 * kCountsWords, cudaMemcpyDeviceToHost, stream));
+        CR_CUDA(cudaStreamSynchronize(stream));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e_all[0], e_all[1]);
+        ev.resolve();
+        stats.ms_total = ms;
+        const uint64_t* stat = host_counts + kStatWord / 2;
+        for (uint32_t bb = 1; bb <= max_bounces; ++bb) stats.secondary_rays += stat[bb];
+        stats.secondary_rays_b1 = stat[1];
+        const uint64_t* ctr = host_counts + kCounterWord / 2;
+        stats.node_visits = ctr[0];
+        stats.tri_tests = ctr[1];
+        uint64_t valid_px = (uint64_t)npx;
+        stats.primary_rays = valid_px * spp;
+        stats.kernel_launches = lc.n;
+        *o.stats = stats;
+        cudaEventDestroy(e_all[0]);
+        cudaEventDestroy(e_all[1]);
+    }
+    if (!(o.flags & CR_OPT_NO_SYNC)) CR_CUDA(cudaStreamSynchronize(stream));
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+extern "C" cr_status cr_render(cr_scene* s, const cr_camera* cam, uint32_t spp, uint32_t max_bounces, cr_reuse_mode mode,
+                               uint32_t group_w, uint32_t group_h, float* out_rgb) {
+    return cr_render_ex(s, cam, spp, max_bounces, mode, group_w, group_h, out_rgb, nullptr);
+}
+
+// ------------------------------------------------------------------------------------
+// Parity entry points.  Host arguments are staged through temporary device buffers.
+namespace {
+struct Staged {
+    DevMem mem;
+    void* dev = nullptr;
+    bool host = false;
+    void* user = nullptr;
+    size_t bytes = 0;
+};
+
+cudaError_t stage_in(Staged& sb, const void* user, size_t bytes, cudaStream_t st) {
+    sb.user = const_cast<void*>(user);
+    sb.bytes = bytes;
+    if (!user) return cudaSuccess;
+    if (is_device_ptr(user)) {
+        sb.dev = const_cast<void*>(user);
+        return cudaSuccess;
+    }
+    sb.host = true;
+    cudaError_t e = sb.mem.alloc(bytes);
+    if (e != cudaSuccess) return e;
+    sb.dev = sb.mem.p;
+    return cudaMemcpyAsync(sb.dev, user, bytes, cudaMemcpyHostToDevice, st);
+}
+cudaError_t stage_out(Staged& sb, void* user, size_t bytes) {
+    sb.user = user;
+    sb.bytes = bytes;
+    if (is_device_ptr(user)) {
+        sb.dev = user;
+        return cudaSuccess;
+    }
+    sb.host = true;
+    cudaError_t e = sb.mem.alloc(bytes);
+    sb.dev = sb.mem.p;
+    return e;
+}
+cudaError_t finish_out(Staged& sb, cudaStream_t st) {
+    if (!sb.host || !sb.user) return cudaSuccess;
+    return cudaMemcpyAsync(sb.user, sb.dev, sb.bytes, cudaMemcpyDeviceToHost, st);
+}
+} // namespace
+
+extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n, int32_t* prim,
+                                   float* t, const cr_render_opts* opts_in) {
+    g_err.clear();
+    if (!s || (!rays && n) || (!prim && n) || (!t && n)) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: NULL argument");
+    if (n == 0) return CR_OK;
+    if (n > (1u << 28)) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: n=%u too large", n);
+    cr_render_opts o;
+    cr_render_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (o.bvh != CR_BVH2 && o.bvh != 0) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: bvh %u not available", o.bvh);
+    const int block = o.block ? (int)o.block : 128;
+    if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: block %d", block);
+    cudaStream_t stream = static_cast<cudaStream_t>(o.stream);
+    Staged r_in, s_in, p_out, t_out;
+    CR_CUDA(stage_in(r_in, rays, sizeof(float) * 8 * (size_t)n, stream));
+    CR_CUDA(stage_in(s_in, skip_prim, sizeof(int32_t) * (size_t)n, stream));
+    CR_CUDA(stage_out(p_out, prim, sizeof(int32_t) * (size_t)n));
+    CR_CUDA(stage_out(t_out, t, sizeof(float) * (size_t)n));
+    DevMem ro, rd, hit, wc;
+    CR_CUDA(ro.alloc(16 * (size_t)n));
+    CR_CUDA(rd.alloc(16 * (size_t)n));
+    CR_CUDA(hit.alloc(8 * (size_t)n));
+    CR_CUDA(wc.alloc(16 * 4));
+    CR_CUDA(cudaMemsetAsync(wc.p, 0, 64, stream));
+    LaunchCount lc;
+    launch_rays_from_user(r_in.dev ? static_cast<const float*>(r_in.dev) : nullptr,
+                          static_cast<const int32_t*>(s_in.dev), n, ro.as<float4>(), rd.as<float4>(), stream, lc);
+    TraceArgs ta;
+    ta.ray_o = ro.as<float4>();
+    ta.ray_d = rd.as<float4>();
+    ta.hit = hit.as<int2>();
+    ta.n_max = n;
+    ta.block = block;
+    ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
+    ta.work_counter = wc.as<uint32_t>();
+    ta.counters = (o.flags & CR_OPT_COUNT) ? reinterpret_cast<unsigned long long*>(wc.as<uint32_t>() + 4) : nullptr;
+    cudaEvent_t e0, e1;
+    if (o.stats) {
+        CR_CUDA(cudaEventCreate(&e0));
+        CR_CUDA(cudaEventCreate(&e1));
+        CR_CUDA(cudaEventRecord(e0, stream));
+    }
+    launch_trace(s->dev, ta, stream, lc);
+    if (o.stats) CR_CUDA(cudaEventRecord(e1, stream));
+    launch_hits_to_user(s->dev, hit.as<int2>(), n, static_cast<int32_t*>(p_out.dev), static_cast<float*>(t_out.dev), stream, lc);
+    CR_CUDA(cudaGetLastError());
+    CR_CUDA(finish_out(p_out, stream));
+    CR_CUDA(finish_out(t_out, stream));
+    CR_CUDA(cudaStreamSynchronize(stream));
+    if (o.stats) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        std::memset(o.stats, 0, sizeof(cr_stats));
+        o.stats->ms_trace_secondary = ms;
+        o.stats->ms_total = ms;
+        o.stats->secondary_rays = n;
+        o.stats->kernel_launches = lc.n;
+        if (ta.counters) {
+            unsigned long long c[2];
+            CR_CUDA(cudaMemcpy(c, ta.counters, sizeof(c), cudaMemcpyDeviceToHost));
+            o.stats->node_visits = c[0];
+            o.stats->tri_tests = c[1];
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    return CR_OK;
+}
+
+extern "C" cr_status cr_debug_groups(uint32_t width, uint32_t height, uint32_t group_w, uint32_t group_h,
+                                     uint32_t interleave, uint64_t seed, uint32_t frame, uint32_t* slot_of_pixel) {
+    g_err.clear();
+    const uint32_t m = group_w * group_h;
+    if (!slot_of_pixel || !width || !height || (uint64_t)width * height > (1ull << 26))
+        return fail(CR_ERR_INVALID_ARG, "cr_debug_groups: bad size or NULL output");
+    if (!group_w || !group_h || !pow2(m) || m > 1024)
+        return fail(CR_ERR_INVALID_ARG, "cr_debug_groups: W*H must be a power of two <= 1024");
+    RenderParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.cam.width = width;
+    p.cam.height = height;
+    p.tile_w = group_w;
+    p.tile_h = group_h;
+    p.m = m;
+    p.k = m;
+    p.tiles_x = (width + group_w - 1) / group_w;
+    p.tiles_y = (height + group_h - 1) / group_h;
+    p.interleave = interleave ? 1u : 0u;
+    p.seed = seed;
+    p.frame = frame;
+    Staged out;
+    const size_t bytes = sizeof(uint32_t) * (size_t)width * height;
+    CR_CUDA(stage_out(out, slot_of_pixel, bytes));
+    LaunchCount lc;
+    launch_groups(p, static_cast<uint32_t*>(out.dev), 0, lc);
+    CR_CUDA(cudaGetLastError());
+    CR_CUDA(finish_out(out, 0));
+    CR_CUDA(cudaStreamSynchronize(0));
+    return CR_OK;
+}
+
+extern "C" cr_status cr_debug_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out) {
+    g_err.clear();
+    if (n == 0) return CR_OK;
+    if (!ctr || !out) return fail(CR_ERR_INVALID_ARG, "cr_debug_philox: NULL argument");
+    Staged ci, co;
+    CR_CUDA(stage_in(ci, ctr, 16 * (size_t)n, 0));
+    CR_CUDA(stage_out(co, out, 16 * (size_t)n));
+    LaunchCount lc;
+    launch_philox(seed, static_cast<const uint32_t*>(ci.dev), n, static_cast<uint32_t*>(co.dev), 0, lc);
+    CR_CUDA(cudaGetLastError());
+    CR_CUDA(finish_out(co, 0));
+    CR_CUDA(cudaStreamSynchronize(0));
+    return CR_OK;
+}
+
+extern "C" cr_status cr_debug_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param,
+                                     float* wi, float* weight, uint8_t* valid) {
+    g_err.clear();
+    if (n == 0) return CR_OK;
+    if (kind > 3) return fail(CR_ERR_INVALID_ARG, "cr_debug_sample: kind %u", kind);
+    if (!u || !wi || !weight || !valid || ((kind == 1 || kind == 2) && !wo) || (kind == 1 && !param))
+        return fail(CR_ERR_INVALID_ARG, "cr_debug_sample: NULL argument");
+    Staged a, b, c, o1, o2, o3;
+    CR_CUDA(stage_in(a, wo, 12 * (size_t)n, 0));
+    CR_CUDA(stage_in(b, u, 8 * (size_t)n, 0));
+    CR_CUDA(stage_in(c, param, 16 * (size_t)n, 0));
+    CR_CUDA(stage_out(o1, wi, 12 * (size_t)n));
+    CR_CUDA(stage_out(o2, weight, 12 * (size_t)n));
+    CR_CUDA(stage_out(o3, valid, (size_t)n));
+    LaunchCount lc;
+    launch_sample(kind, n, static_cast<const float*>(a.dev), static_cast<const float*>(b.dev),
+                  static_cast<const float*>(c.dev), static_cast<float*>(o1.dev), static_cast<float*>(o2.dev),
+                  static_cast<uint8_t*>(o3.dev), 0, lc);
+    CR_CUDA(cudaGetLastError());
+    CR_CUDA(finish_out(o1, 0));
+    CR_CUDA(finish_out(o2, 0));
+    CR_CUDA(finish_out(o3, 0));
+    CR_CUDA(cudaStreamSynchronize(0));
+    return CR_OK;
+}

@@ -1,0 +1,156 @@
+// cr_internal.h -- host-side declarations shared by the library's translation units
+// (scene build, kernel launchers, C ABI).  Not installed; the public ABI is include/cr.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cr.h"
+
+namespace cr {
+
+// ------------------------------------------------------------------------------------
+// BVH2 in the device layout: 4 x 16 B per inner node, holding both children:
+//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   n3 = (link0, link1, 0, 0) as int bits
+// link >= 0: inner node index; link < 0: leaf ~((first << 2) | (count - 1)), count 1..4,
+// first = index of the leaf's first triangle in leaf order.
+struct HostBVH2 {
+    std::vector<float> nodes;         // 16 floats per inner node
+    std::vector<uint32_t> leaf_order; // leaf-order position -> original triangle index
+    uint32_t n_nodes = 0;
+    uint32_t depth = 0;
+    float lo[3], hi[3];
+};
+
+// Binned-SAH build (32 bins per axis, leaves of <= 4 triangles, median splits below
+// depth 40 so the depth stays <= 64).
+HostBVH2 build_bvh2(const float* tri_xyz, uint32_t n_tri, int n_threads);
+
+// BVH8-Q: 80 B per node (5 x 16 B), after Ylitie et al. 2017:
+//   word0: origin.xyz (float), (ex, ey, ez, imask) bytes
+//   word1: child_base (inner), tri_base, meta[0..3]
+//   word2: meta[4..7], qlo_x[0..7] (8 bytes) , ... packed as in bvh_build.cpp
+// Child boxes are quantised to 8 bits per coordinate on a per-node power-of-two grid,
+// lower bounds rounded down and upper bounds rounded up, so every child box contains the
+// exact one.
+struct HostBVH8 {
+    std::vector<uint32_t> nodes; // 20 words per node
+    uint32_t n_nodes = 0;
+};
+HostBVH8 build_bvh8q(const HostBVH2& b2);
+
+// ------------------------------------------------------------------------------------
+// Device-side scene description passed to kernels.
+struct DevScene {
+    const float4* nodes2 = nullptr; // 4 per node
+    const uint4* nodes8 = nullptr;  // 5 per node
+    const float4* tris = nullptr;   // 3 per triangle in leaf order: v0|orig, v1|mat, v2|0
+    const float4* mats = nullptr;   // 2 per material: (type bits, albedo), (roughness, emission)
+    float env[3] = {0, 0, 0};
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    uint32_t n_tri = 0, n_mat = 0;
+};
+
+// Camera basis rounded to float once (computed in double on the host).
+struct CamBasis {
+    float pos[3], fwd[3], right[3], up[3];
+    float tx, ty; // tan(vfov/2) * aspect, tan(vfov/2)
+    uint32_t width, height;
+};
+CamBasis make_camera(const cr_camera& c);
+
+// Per-call launch statistics.
+struct LaunchCount {
+    uint64_t n = 0;
+};
+
+// Arguments of one trace launch over a queue of slots.
+struct TraceArgs {
+    const float4* ray_o = nullptr; // slot-indexed (o.xyz, skip original index as int bits)
+    const float4* ray_d = nullptr; // slot-indexed (d.xyz, tmax); tmax < 0: no ray
+    const int32_t* queue = nullptr;     // slots to trace; NULL = slots [0, n_direct)
+    const uint32_t* queue_count = nullptr; // device count of queue entries (NULL: n_max)
+    uint32_t n_max = 0;            // upper bound on the number of rays
+    int2* hit = nullptr;           // slot-indexed (leaf triangle index or -1, t bits)
+    unsigned long long* counters = nullptr; // [0] node visits, [1] triangle tests (counting pass)
+    uint32_t* work_counter = nullptr;       // persistent mode: atomic ray counter (zeroed)
+    int block = 128;
+    bool persistent = false;
+    bool bvh8 = false;
+};
+void launch_trace(const DevScene& s, const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
+// Map leaf-order triangle indices of hits to original indices and split (prim, t).
+void launch_hits_to_user(const DevScene& s, const int2* hit, uint32_t n, int32_t* prim, float* t,
+                         cudaStream_t st, LaunchCount& lc);
+
+// ------------------------------------------------------------------------------------
+// Wavefront path state, slot-indexed.  Slot = tile * m + sigma(i) (Sec. 3.3), so a reuse
+// group's K members occupy K consecutive slots.
+struct PathBuffers {
+    uint32_t n_slots = 0, n_groups = 0;
+    int32_t* pixel = nullptr;   // slot -> pixel (-1: none)
+    float4* ray_o = nullptr;
+    float4* ray_d = nullptr;
+    int2* hit = nullptr;
+    float4* beta = nullptr;     // throughput rgb, w unused
+    float4* radiance = nullptr; // path radiance rgb
+    uint8_t* alive = nullptr;   // 1 while the path continues
+    int32_t* ray_queue = nullptr;   // alive slots in slot order
+    int32_t* group_queue = nullptr; // groups with an alive member
+    // counts (kCountsWords words): [2] persistent work counter; [8 + 2b], [8 + 2b + 1] ray and
+    // group queue lengths after the compaction of bounce b; from word kStatWord, 64-bit
+    // running totals of rays traced per bounce (index b); from kCounterWord, 64-bit node
+    // visits and triangle tests of the counting pass.
+    uint32_t* counts = nullptr;
+    uint32_t* block_counts = nullptr; // compaction scratch (2 per block) + offsets
+    uint32_t n_blocks_cap = 0;
+    // Morton sort
+    uint32_t* keys = nullptr;   // 2 x n_slots
+    int32_t* vals = nullptr;    // 2 x n_slots
+    uint32_t* sort_hist = nullptr;
+    uint32_t sort_hist_cap = 0;
+    float4* accum = nullptr;    // per pixel
+    uint32_t n_px_cap = 0;
+    unsigned long long* counters = nullptr; // counting pass
+};
+
+constexpr uint32_t kCountsWords = 256, kStatWord = 64, kCounterWord = 128;
+
+struct RenderParams {
+    CamBasis cam;
+    uint32_t tile_w, tile_h, m, k;
+    uint32_t tiles_x, tiles_y;
+    uint32_t interleave;
+    uint64_t seed;
+    uint32_t frame;
+    uint32_t bounce;      // 1..B for shade
+    uint32_t max_bounces;
+    uint32_t reuse;       // 1: direction reuse at this bounce
+    uint32_t final_pass;  // 1: only environment / emission
+};
+
+void launch_raygen(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
+void launch_shade(const DevScene& s, const RenderParams& p, PathBuffers& b, bool first, const cr_debug* dbg,
+                  cudaStream_t st, LaunchCount& lc);
+// Group-granular compaction of the slots processed by the last shade into ray and group queues.
+void launch_compact(const RenderParams& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc);
+const int32_t* launch_morton_sort(const DevScene& s, PathBuffers& b, uint32_t bounce, cudaStream_t st,
+                                  LaunchCount& lc);
+uint32_t sort_hist_len(uint32_t n_slots);
+uint32_t compact_blocks(uint32_t n_pos);
+void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, float4* ray_o, float4* ray_d,
+                           cudaStream_t st, LaunchCount& lc);
+void launch_accumulate(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
+void launch_output(PathBuffers& b, uint32_t npx, float inv_spp, float* out_rgb, cudaStream_t st, LaunchCount& lc);
+void launch_groups(const RenderParams& p, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc);
+void launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out, cudaStream_t st, LaunchCount& lc);
+void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param, float* wi,
+                   float* weight, uint8_t* valid, cudaStream_t st, LaunchCount& lc);
+
+} // namespace cr

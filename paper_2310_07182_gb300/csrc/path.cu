@@ -1,0 +1,852 @@
+// path.cu -- wavefront path-tracing stages around the traversal: primary ray generation
+// in reuse-group slot order, the fused shade / classify / reuse / spawn stage, group-
+// granular path compaction, the Morton-sort comparator and accumulation.
+//
+// Slot layout (Sec. 3.3): the image is cut into W x H tiles; inside tile t the pixel with
+// row-major index i goes to slot t*m + sigma_{t,f}(i), where sigma is the tile's and
+// frame's LCG shuffle.  Group g of the tile is slots [t*m + g*K, t*m + (g+1)*K), so a
+// group's members are K adjacent lanes of one warp (K <= 32) or of one block (K <= 256).
+#include <cuda_runtime.h>
+
+#include "cr_internal.h"
+#include "device_math.cuh"
+
+namespace cr {
+namespace {
+
+using namespace dev;
+
+// ------------------------------------------------------------------------------------
+// Interleaved grouping (Sec. 3.3).  The tile's LCG x_{k+1} = (a x_k + c) mod m is
+// evaluated at index i by composing the affine map with itself (binary powers), so each
+// thread finds sigma(i) in log2(m) steps.
+struct Lcg {
+    uint32_t a, c, x0;
+};
+
+__device__ __forceinline__ Lcg tile_lcg(uint64_t seed, uint32_t tile, uint32_t frame, uint32_t m, uint32_t interleave) {
+    if (!interleave) return Lcg{1u, 1u, 0u};
+    const uint4 h = philox_seed(seed, tile, frame, kTagInterleave, 0u);
+    const uint32_t q4 = m / 4 > 0 ? m / 4 : 1, q2 = m / 2 > 0 ? m / 2 : 1;
+    return Lcg{4u * (h.x % q4) + 1u, 2u * (h.y % q2) + 1u, h.z % m};
+}
+
+__device__ __forceinline__ uint32_t sigma_of(const Lcg& L, uint32_t i, uint32_t m, uint32_t interleave) {
+    if (!interleave) return i;
+    const uint32_t mask = m - 1u;
+    uint32_t A = 1u, C = 0u;           // accumulated map x -> A x + C
+    uint32_t pa = L.a & mask, pc = L.c & mask; // current power of the step map
+    for (uint32_t e = i; e; e >>= 1) {
+        if (e & 1u) {
+            A = (pa * A) & mask;
+            C = (pa * C + pc) & mask;
+        }
+        const uint32_t na = (pa * pa) & mask;
+        pc = (pa * pc + pc) & mask;
+        pa = na;
+    }
+    return (A * L.x0 + C) & mask;
+}
+
+// Primary ray through (px + u, py + v): pinhole camera with a vertical field of view.
+__device__ __forceinline__ V3 camera_dir(const CamBasis& c, uint32_t px, uint32_t py, float u, float v) {
+    const float sx = fm(fs(fd(fm(2.0f, fa((float)px, u)), (float)c.width), 1.0f), c.tx);
+    const float sy = fm(fs(1.0f, fd(fm(2.0f, fa((float)py, v)), (float)c.height)), c.ty);
+    const V3 d = v3(fa(fa(c.fwd[0], fm(sx, c.right[0])), fm(sy, c.up[0])),
+                    fa(fa(c.fwd[1], fm(sx, c.right[1])), fm(sy, c.up[1])),
+                    fa(fa(c.fwd[2], fm(sx, c.right[2])), fm(sy, c.up[2])));
+    return normalize3(d);
+}
+
+// One block covers blockDim / m whole tiles: every thread finds sigma of its pixel, the
+// inverse map is built in shared memory, then thread j writes slot j of its tile so the
+// slot arrays are written contiguously.
+__global__ void k_raygen(RenderParams p, int32_t* __restrict__ pixel, float4* __restrict__ ray_o,
+                         float4* __restrict__ ray_d, float4* __restrict__ beta, float4* __restrict__ radiance,
+                         uint8_t* __restrict__ alive) {
+    extern __shared__ uint16_t inv[];
+    const uint32_t m = p.m;
+    const uint32_t tiles_per_block = blockDim.x / m;
+    const uint32_t tl = threadIdx.x / m, j = threadIdx.x % m;
+    const uint32_t tile = blockIdx.x * tiles_per_block + tl;
+    const uint32_t n_tiles = p.tiles_x * p.tiles_y;
+    if (tl < tiles_per_block && tile < n_tiles) {
+        const Lcg L = tile_lcg(p.seed, tile, p.frame, m, p.interleave);
+        inv[tl * m + sigma_of(L, j, m, p.interleave)] = (uint16_t)j;
+    }
+    __syncthreads();
+    if (tl >= tiles_per_block || tile >= n_tiles) return;
+    const uint32_t i = inv[tl * m + j];
+    const uint32_t tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+    const uint32_t px = tx * p.tile_w + i % p.tile_w, py = ty * p.tile_h + i / p.tile_w;
+    const uint32_t slot = tile * m + j;
+    if (px < p.cam.width && py < p.cam.height) {
+        const uint32_t pix = py * p.cam.width + px;
+        const uint4 h = philox_seed(p.seed, pix, p.frame, 0u, kTagCamera);
+        const V3 d = camera_dir(p.cam, px, py, unit24(h.x), unit24(h.y));
+        pixel[slot] = (int32_t)pix;
+        ray_o[slot] = make_float4(p.cam.pos[0], p.cam.pos[1], p.cam.pos[2], __int_as_float(-1));
+        ray_d[slot] = make_float4(d.x, d.y, d.z, INFINITY);
+        beta[slot] = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
+        radiance[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        alive[slot] = 1;
+    } else {
+        pixel[slot] = -1;
+        ray_d[slot] = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+        alive[slot] = 0;
+    }
+}
+
+__global__ void k_groups(RenderParams p, uint32_t* __restrict__ slot_of_pixel) {
+    const uint32_t pix = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= p.cam.width * p.cam.height) return;
+    const uint32_t px = pix % p.cam.width, py = pix / p.cam.width;
+    const uint32_t tx = px / p.tile_w, ty = py / p.tile_h;
+    const uint32_t tile = ty * p.tiles_x + tx;
+    const uint32_t i = (py % p.tile_h) * p.tile_w + px % p.tile_w;
+    const Lcg L = tile_lcg(p.seed, tile, p.frame, p.m, p.interleave);
+    slot_of_pixel[pix] = tile * p.m + sigma_of(L, i, p.m, p.interleave);
+}
+
+// ------------------------------------------------------------------------------------
+// Shade + classify + reuse + spawn (Sec. 3.2), one thread per slot of the alive groups.
+struct ShadeArgs {
+    const float4* tris;
+    const float4* mats;
+    float env[3];
+    int32_t* pixel;
+    float4* ray_o;
+    float4* ray_d;
+    const int2* hit;
+    float4* beta;
+    float4* radiance;
+    uint8_t* alive;
+    const int32_t* group_queue; // NULL: all groups in order
+    const uint32_t* group_count;
+    uint32_t n_groups_max;
+    cr_debug dbg;
+    uint32_t npx;
+};
+
+struct Member {
+    int pix;
+    bool alive;
+    int cls;
+    V3 n, t, b, wo;
+    float albedo[3];
+    V3 wl;    // chosen tangent-space exit direction
+    float w[3];
+    bool valid;
+    int orig;
+};
+
+// Shading point of a hit: geometric normal facing the incoming ray, tangent frame, wo.
+__device__ __forceinline__ void setup_member(const ShadeArgs& a, const RenderParams& p, int slot, Member& mb,
+                                             float3& L, const float4 bt) {
+    const int2 h = a.hit[slot];
+    const float4 d4 = a.ray_d[slot];
+    if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&a.tris[3 * h.x]).w) : -1;
+    if (h.x < 0) { // miss: environment
+        L.x = fa(L.x, fm(bt.x, a.env[0]));
+        L.y = fa(L.y, fm(bt.y, a.env[1]));
+        L.z = fa(L.z, fm(bt.z, a.env[2]));
+        mb.alive = false;
+        return;
+    }
+    const float4 v0 = __ldg(&a.tris[3 * h.x + 0]);
+    const float4 v1 = __ldg(&a.tris[3 * h.x + 1]);
+    const float4 v2 = __ldg(&a.tris[3 * h.x + 2]);
+    const int mat = __float_as_int(v1.w);
+    const float4 m0 = __ldg(&a.mats[2 * mat + 0]);
+    const float4 m1 = __ldg(&a.mats[2 * mat + 1]);
+    const uint32_t type = (uint32_t)__float_as_int(m0.x);
+    mb.orig = __float_as_int(v0.w);
+    if (type == kMatEmitter) {
+        L.x = fa(L.x, fm(bt.x, m1.y));
+        L.y = fa(L.y, fm(bt.y, m1.z));
+        L.z = fa(L.z, fm(bt.z, m1.w));
+        mb.alive = false;
+        return;
+    }
+    if (p.final_pass) {
+        mb.alive = false;
+        return;
+    }
+    const V3 a0 = v3(v0.x, v0.y, v0.z), a1 = v3(v1.x, v1.y, v1.z), a2 = v3(v2.x, v2.y, v2.z);
+    const V3 ng = normalize3(cross3(sub3(a1, a0), sub3(a2, a0)));
+    const V3 d = v3(d4.x, d4.y, d4.z);
+    mb.n = dot3(ng, d) < 0.0f ? ng : v3(-ng.x, -ng.y, -ng.z);
+    frame_from(mb.n, mb.t, mb.b);
+    const V3 md = v3(-d.x, -d.y, -d.z);
+    mb.wo = v3(dot3(md, mb.t), dot3(md, mb.b), dot3(md, mb.n));
+    mb.cls = type == kMatLambert ? kClsDiffuse : kClsGlossy;
+    mb.albedo[0] = m0.y;
+    mb.albedo[1] = m0.z;
+    mb.albedo[2] = m0.w;
+    // the member's own BSDF sample, drawn from its pixel's stream
+    const uint4 r = philox_seed(p.seed, (uint32_t)mb.pix, p.frame, p.bounce, kTagBsdf);
+    const float u1 = unit24(r.x), u2 = unit24(r.y);
+    if (type == kMatLambert) {
+        mb.wl = sample_cosine(u1, u2);
+        mb.w[0] = m0.y;
+        mb.w[1] = m0.z;
+        mb.w[2] = m0.w;
+        mb.valid = true;
+    } else if (type == kMatGGX) {
+        mb.valid = sample_ggx(mb.wo, m1.x, mb.albedo, u1, u2, mb.wl, mb.w);
+    } else {
+        mb.wl = v3(-mb.wo.x, -mb.wo.y, mb.wo.z);
+        mb.w[0] = m0.y;
+        mb.w[1] = m0.z;
+        mb.w[2] = m0.w;
+        mb.valid = mb.wo.z > 0.0f;
+    }
+}
+
+__device__ __forceinline__ void take_dir(Member& mb, V3 wl) {
+    mb.wl = wl;
+    mb.w[0] = mb.albedo[0]; // Lambert: f cos / p_cos = albedo
+    mb.w[1] = mb.albedo[1];
+    mb.w[2] = mb.albedo[2];
+    mb.valid = true;
+}
+
+__device__ __forceinline__ void finish_member(const ShadeArgs& a, const RenderParams& p, int slot, Member& mb,
+                                              float3 L, float4 bt, bool was_alive, int cat) {
+    if (a.dbg.cat && mb.pix >= 0 && !p.final_pass) {
+        const uint32_t di = (p.bounce - 1) * a.npx + (uint32_t)mb.pix;
+        a.dbg.cat[di] = (uint8_t)cat;
+        a.dbg.cls[di] = (uint8_t)(mb.alive ? mb.cls : kClsNone);
+        a.dbg.flags[di] = (uint8_t)((mb.alive ? 1 : 0) | (mb.alive && mb.valid ? 2 : 0));
+        V3 lw = v3(0.0f, 0.0f, 0.0f), ww = v3(0.0f, 0.0f, 0.0f);
+        if (mb.alive) {
+            lw = mb.wl;
+            ww = local_to_world(mb.t, mb.b, mb.n, mb.wl);
+        }
+        a.dbg.local[3 * di + 0] = lw.x;
+        a.dbg.local[3 * di + 1] = lw.y;
+        a.dbg.local[3 * di + 2] = lw.z;
+        a.dbg.world[3 * di + 0] = ww.x;
+        a.dbg.world[3 * di + 1] = ww.y;
+        a.dbg.world[3 * di + 2] = ww.z;
+    }
+    if (!was_alive) return;
+    a.radiance[slot] = make_float4(L.x, L.y, L.z, 0.0f);
+    if (mb.alive && mb.valid) {
+        const float4 o4 = a.ray_o[slot];
+        const float4 d4 = a.ray_d[slot];
+        const float th = __int_as_float(a.hit[slot].y);
+        const float px = o4.x + th * d4.x, py = o4.y + th * d4.y, pz = o4.z + th * d4.z;
+        const float amax = fmaxf(1.0f, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
+        const float eps = 0x1.0p-18f * amax;
+        const V3 dw = local_to_world(mb.t, mb.b, mb.n, mb.wl);
+        a.ray_o[slot] = make_float4(px + eps * mb.n.x, py + eps * mb.n.y, pz + eps * mb.n.z, __int_as_float(mb.orig));
+        a.ray_d[slot] = make_float4(dw.x, dw.y, dw.z, INFINITY);
+        a.beta[slot] = make_float4(fm(bt.x, mb.w[0]), fm(bt.y, mb.w[1]), fm(bt.z, mb.w[2]), 0.0f);
+        a.alive[slot] = 1;
+    } else {
+        a.alive[slot] = 0;
+    }
+}
+
+// K <= 32: a group is a K-lane segment of a warp; votes by ballot, the donor's direction by
+// shuffle, the hybrid sum by an xor butterfly (which equals the pairwise tree sum in every
+// lane because float addition is commutative).
+__global__ void k_shade_warp(ShadeArgs a, RenderParams p) {
+    const uint32_t K = p.k;
+    const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gq = pos / K, lane_g = pos % K;
+    const bool active = gq < n_groups;
+    int slot = -1;
+    Member mb;
+    mb.pix = -1;
+    mb.alive = false;
+    mb.cls = kClsNone;
+    mb.valid = false;
+    mb.wl = v3(0.0f, 0.0f, 0.0f);
+    bool was_alive = false;
+    float4 bt = make_float4(0, 0, 0, 0);
+    float3 L = make_float3(0, 0, 0);
+    if (active) {
+        const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
+        slot = (int)(g * K + lane_g);
+        mb.pix = a.pixel[slot];
+        was_alive = mb.pix >= 0 && a.alive[slot];
+        if (was_alive) {
+            mb.alive = true;
+            bt = a.beta[slot];
+            const float4 r4 = a.radiance[slot];
+            L = make_float3(r4.x, r4.y, r4.z);
+            setup_member(a, p, slot, mb, L, bt);
+        }
+    }
+    int cat = kCatEmpty;
+    if (!p.final_pass) {
+        const uint32_t lane = threadIdx.x & 31u;
+        const uint32_t seg = lane & ~(K - 1u);
+        const uint32_t segmask = K == 32u ? 0xffffffffu : (((1u << K) - 1u) << seg);
+        const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse) & segmask;
+        const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy) & segmask;
+        cat = bd && bg ? kCatHybrid : (bd ? kCatDiffuse : (bg ? kCatGlossy : kCatEmpty));
+        if (p.reuse) {
+            const int donor = bd ? __ffs(bd) - 1 : (int)lane;
+            const V3 wd = v3(__shfl_sync(0xffffffffu, mb.wl.x, donor), __shfl_sync(0xffffffffu, mb.wl.y, donor),
+                             __shfl_sync(0xffffffffu, mb.wl.z, donor));
+            const bool contrib = mb.alive && mb.cls == kClsGlossy && mb.valid;
+            V3 s = contrib ? mb.wl : v3(0.0f, 0.0f, 0.0f);
+            for (uint32_t off = 1; off < K; off <<= 1) {
+                const float sx = __shfl_xor_sync(0xffffffffu, s.x, off);
+                const float sy = __shfl_xor_sync(0xffffffffu, s.y, off);
+                const float sz = __shfl_xor_sync(0xffffffffu, s.z, off);
+                s = v3(fa(s.x, sx), fa(s.y, sy), fa(s.z, sz));
+            }
+            if (mb.alive && mb.cls == kClsDiffuse) {
+                if (cat == kCatDiffuse) {
+                    take_dir(mb, wd);
+                } else if (cat == kCatHybrid) {
+                    const float l2 = dot3(s, s);
+                    if (l2 > 0.0f) {
+                        const float l = fq(l2);
+                        take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
+                    } else {
+                        take_dir(mb, wd); // no valid glossy sample: first diffuse member's
+                    }
+                }
+            }
+        }
+    }
+    if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
+}
+
+// 32 < K <= 256: a group spans K/32 warps of a 256-thread block; per-warp ballots and the
+// members' samples go through shared memory and the hybrid sum is a pairwise tree over the
+// group's slots.
+__global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, RenderParams p) {
+    __shared__ uint32_t s_bd[8], s_bg[8];
+    __shared__ float s_own[3][256];
+    __shared__ float s_sum[3][256];
+    const uint32_t K = p.k;
+    const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gq = pos / K, lane_g = pos % K;
+    const bool active = gq < n_groups;
+    int slot = -1;
+    Member mb;
+    mb.pix = -1;
+    mb.alive = false;
+    mb.cls = kClsNone;
+    mb.valid = false;
+    mb.wl = v3(0.0f, 0.0f, 0.0f);
+    bool was_alive = false;
+    float4 bt = make_float4(0, 0, 0, 0);
+    float3 L = make_float3(0, 0, 0);
+    if (active) {
+        const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
+        slot = (int)(g * K + lane_g);
+        mb.pix = a.pixel[slot];
+        was_alive = mb.pix >= 0 && a.alive[slot];
+        if (was_alive) {
+            mb.alive = true;
+            bt = a.beta[slot];
+            const float4 r4 = a.radiance[slot];
+            L = make_float3(r4.x, r4.y, r4.z);
+            setup_member(a, p, slot, mb, L, bt);
+        }
+    }
+    int cat = kCatEmpty;
+    if (!p.final_pass) {
+        const uint32_t t = threadIdx.x, w = t >> 5;
+        const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse);
+        const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy);
+        if ((t & 31u) == 0) {
+            s_bd[w] = bd;
+            s_bg[w] = bg;
+        }
+        const bool contrib = mb.alive && mb.cls == kClsGlossy && mb.valid;
+        s_own[0][t] = mb.wl.x;
+        s_own[1][t] = mb.wl.y;
+        s_own[2][t] = mb.wl.z;
+        s_sum[0][t] = contrib ? mb.wl.x : 0.0f;
+        s_sum[1][t] = contrib ? mb.wl.y : 0.0f;
+        s_sum[2][t] = contrib ? mb.wl.z : 0.0f;
+        __syncthreads();
+        const uint32_t gbase = (t / K) * K; // first thread of the group in the block
+        bool any_d = false, any_g = false;
+        int donor = -1;
+        for (uint32_t ww = gbase >> 5; ww < (gbase + K) >> 5; ++ww) {
+            if (s_bd[ww] && donor < 0) donor = (int)(ww * 32u + __ffs(s_bd[ww]) - 1);
+            any_d |= s_bd[ww] != 0;
+            any_g |= s_bg[ww] != 0;
+        }
+        cat = any_d && any_g ? kCatHybrid : (any_d ? kCatDiffuse : (any_g ? kCatGlossy : kCatEmpty));
+        if (p.reuse) {
+            for (uint32_t stride = 1; stride < K; stride <<= 1) {
+                if ((t - gbase) % (2u * stride) == 0) {
+                    s_sum[0][t] = fa(s_sum[0][t], s_sum[0][t + stride]);
+                    s_sum[1][t] = fa(s_sum[1][t], s_sum[1][t + stride]);
+                    s_sum[2][t] = fa(s_sum[2][t], s_sum[2][t + stride]);
+                }
+                __syncthreads();
+            }
+            if (mb.alive && mb.cls == kClsDiffuse) {
+                const V3 wd = v3(s_own[0][donor], s_own[1][donor], s_own[2][donor]);
+                if (cat == kCatDiffuse) {
+                    take_dir(mb, wd);
+                } else if (cat == kCatHybrid) {
+                    const V3 s = v3(s_sum[0][gbase], s_sum[1][gbase], s_sum[2][gbase]);
+                    const float l2 = dot3(s, s);
+                    if (l2 > 0.0f) {
+                        const float l = fq(l2);
+                        take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
+                    } else {
+                        take_dir(mb, wd);
+                    }
+                }
+            }
+        }
+    }
+    if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
+}
+
+// ------------------------------------------------------------------------------------
+// Group-granular compaction.  Positions [0, n_groups*K) of the last shade (group queue
+// order) are scanned in blocks of 256; a group survives if any member is alive and keeps
+// its K slots together in the group queue, while the ray queue lists the alive slots.
+// Three launches (count, scan, scatter) keep the result deterministic and order-preserving.
+constexpr uint32_t kCompactBlock = 256;
+
+__device__ __forceinline__ void position_info(const int32_t* gq_in, uint32_t n_groups, uint32_t K, uint32_t pos,
+                                              const uint8_t* alive, int& slot, bool& a) {
+    slot = -1;
+    a = false;
+    const uint32_t g = pos / K;
+    if (g < n_groups) {
+        const uint32_t grp = gq_in ? (uint32_t)gq_in[g] : g;
+        slot = (int)(grp * K + pos % K);
+        a = alive[slot] != 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? s_warp[lane] : 0u;
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        if (lane < nw) s_warp[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t nw = blockDim.x >> 5;
+    total = s_warp[nw - 1];
+    const uint32_t excl = x - v + (w > 0 ? s_warp[w - 1] : 0u);
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(kCompactBlock) k_compact_count(const int32_t* gq_in, const uint32_t* n_groups_ptr,
+                                                                 uint32_t n_groups_max, uint32_t K,
+                                                                 const uint8_t* __restrict__ alive,
+                                                                 uint32_t* __restrict__ block_counts) {
+    __shared__ uint8_t s_alive[kCompactBlock];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t n_groups = n_groups_ptr ? min(*n_groups_ptr, n_groups_max) : n_groups_max;
+    const uint32_t pos = blockIdx.x * kCompactBlock + threadIdx.x;
+    int slot;
+    bool a;
+    position_info(gq_in, n_groups, K, pos, alive, slot, a);
+    s_alive[threadIdx.x] = a;
+    __syncthreads();
+    uint32_t gl = 0;
+    if (threadIdx.x % K == 0) {
+        for (uint32_t j = 0; j < K; ++j) gl |= s_alive[threadIdx.x + j];
+    }
+    uint32_t tot_r, tot_g;
+    block_excl_scan(a ? 1u : 0u, s_warp, tot_r);
+    block_excl_scan(gl, s_warp, tot_g);
+    if (threadIdx.x == 0) {
+        block_counts[2 * blockIdx.x + 0] = tot_r;
+        block_counts[2 * blockIdx.x + 1] = tot_g;
+    }
+}
+
+// Exclusive scan of the per-block counts in one block; totals go to out_counts[0..1] and are
+// added to the running statistics.
+__global__ void __launch_bounds__(1024) k_compact_scan(uint32_t* __restrict__ block_counts, uint32_t n_blocks,
+                                                       uint32_t* __restrict__ out_counts,
+                                                       unsigned long long* __restrict__ stat) {
+    __shared__ uint32_t s_warp[32];
+    for (int col = 0; col < 2; ++col) {
+        const uint32_t per = (n_blocks + blockDim.x - 1) / blockDim.x;
+        const uint32_t b0 = threadIdx.x * per;
+        uint32_t local = 0;
+        for (uint32_t k = 0; k < per && b0 + k < n_blocks; ++k) local += block_counts[2 * (b0 + k) + col];
+        uint32_t total;
+        uint32_t run = block_excl_scan(local, s_warp, total);
+        for (uint32_t k = 0; k < per && b0 + k < n_blocks; ++k) {
+            const uint32_t v = block_counts[2 * (b0 + k) + col];
+            block_counts[2 * (b0 + k) + col] = run;
+            run += v;
+        }
+        if (threadIdx.x == 0) {
+            out_counts[col] = total;
+            if (stat && col == 0) atomicAdd(stat, (unsigned long long)total);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kCompactBlock) k_compact_scatter(const int32_t* gq_in, const uint32_t* n_groups_ptr,
+                                                                   uint32_t n_groups_max, uint32_t K,
+                                                                   const uint8_t* __restrict__ alive,
+                                                                   const uint32_t* __restrict__ block_offsets,
+                                                                   int32_t* __restrict__ ray_queue,
+                                                                   int32_t* __restrict__ gq_out) {
+    __shared__ uint8_t s_alive[kCompactBlock];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t n_groups = n_groups_ptr ? min(*n_groups_ptr, n_groups_max) : n_groups_max;
+    const uint32_t pos = blockIdx.x * kCompactBlock + threadIdx.x;
+    int slot;
+    bool a;
+    position_info(gq_in, n_groups, K, pos, alive, slot, a);
+    s_alive[threadIdx.x] = a;
+    __syncthreads();
+    uint32_t gl = 0;
+    if (threadIdx.x % K == 0) {
+        for (uint32_t j = 0; j < K; ++j) gl |= s_alive[threadIdx.x + j];
+    }
+    uint32_t tot;
+    const uint32_t rr = block_excl_scan(a ? 1u : 0u, s_warp, tot);
+    const uint32_t rg = block_excl_scan(gl, s_warp, tot);
+    if (a) ray_queue[block_offsets[2 * blockIdx.x] + rr] = slot;
+    if (gl) gq_out[block_offsets[2 * blockIdx.x + 1] + rg] = slot / (int)K;
+}
+
+// ------------------------------------------------------------------------------------
+// Morton-sort comparator ("TwoPoint", Table 1): 30-bit key interleaving 5 bits of each
+// coordinate of the origin and of the point 0.25 x (largest scene extent) along the ray,
+// quantised in the scene box; then a stable LSD radix sort of (key, slot).
+__global__ void k_morton(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
+                         const int32_t* __restrict__ queue, const uint32_t* __restrict__ count, uint32_t n_max,
+                         float3 lo, float3 scale, float len, uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    const uint32_t n = min(*count, n_max);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int slot = queue[i];
+    const float4 o = ray_o[slot], d = ray_d[slot];
+    const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z) * len;
+    const float p[6] = {o.x, o.y, o.z, o.x + d.x * il, o.y + d.y * il, o.z + d.z * il};
+    const float l[3] = {lo.x, lo.y, lo.z}, s[3] = {scale.x, scale.y, scale.z};
+    uint32_t q[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float f = (p[k] - l[k % 3]) * s[k % 3];
+        q[k] = (uint32_t)fminf(fmaxf(f, 0.0f), 31.0f);
+    }
+    uint32_t key = 0;
+#pragma unroll
+    for (int bit = 4; bit >= 0; --bit)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) key = (key << 1) | ((q[k] >> bit) & 1u);
+    keys[i] = key;
+    vals[i] = slot;
+}
+
+constexpr uint32_t kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ count, uint32_t n_max,
+                                                            uint32_t shift, uint32_t n_blocks,
+                                                            uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    const uint32_t n = min(*count, n_max);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kSortTile;
+    for (uint32_t r = 0; r < kSortItems; ++r) {
+        const uint32_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * n_blocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, uint32_t len) {
+    __shared__ uint32_t s_warp[32];
+    const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (uint32_t k = 0; k < per && b0 + k < len; ++k) local += hist[b0 + k];
+    uint32_t total;
+    uint32_t run = block_excl_scan(local, s_warp, total);
+    for (uint32_t k = 0; k < per && b0 + k < len; ++k) {
+        const uint32_t v = hist[b0 + k];
+        hist[b0 + k] = run;
+        run += v;
+    }
+}
+
+// Stable scatter: items are ranked in index order (round, warp, lane) within each digit.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                               const int32_t* __restrict__ vin,
+                                                               const uint32_t* __restrict__ count, uint32_t n_max,
+                                                               uint32_t shift, uint32_t n_blocks,
+                                                               const uint32_t* __restrict__ hist,
+                                                               uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_wc[kSortThreads / 32][256];
+    const uint32_t n = min(*count, n_max);
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    s_run[threadIdx.x] = hist[threadIdx.x * n_blocks + blockIdx.x];
+    const uint32_t base = blockIdx.x * kSortTile;
+    for (uint32_t r = 0; r < kSortItems; ++r) {
+        for (uint32_t ww = 0; ww < kSortThreads / 32; ++ww) s_wc[ww][threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t i = base + r * kSortThreads + threadIdx.x;
+        const bool ok = i < n;
+        uint32_t key = 0, dig = 256;
+        int32_t val = 0;
+        if (ok) {
+            key = kin[i];
+            val = vin[i];
+            dig = (key >> shift) & 255u;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) s_wc[w][dig] = __popc(peers);
+        __syncthreads();
+        // exclusive prefix over warps for digit d = threadIdx.x, then advance the running base
+        {
+            const uint32_t d = threadIdx.x;
+            uint32_t acc = 0;
+            for (uint32_t ww = 0; ww < kSortThreads / 32; ++ww) {
+                const uint32_t c = s_wc[ww][d];
+                s_wc[ww][d] = acc;
+                acc += c;
+            }
+            // s_run[d] still holds the base for this round; the total is added after use
+            __syncthreads();
+            if (ok) {
+                const uint32_t dst = s_run[dig] + s_wc[w][dig] + rank;
+                kout[dst] = key;
+                vout[dst] = val;
+            }
+            __syncthreads();
+            s_run[d] += acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+__global__ void k_accumulate(const int32_t* __restrict__ pixel, const float4* __restrict__ radiance, uint32_t n_slots,
+                             float4* __restrict__ accum) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slots) return;
+    const int pix = pixel[s];
+    if (pix < 0) return;
+    const float4 l = radiance[s];
+    float4 a = accum[pix];
+    a.x += l.x;
+    a.y += l.y;
+    a.z += l.z;
+    accum[pix] = a;
+}
+
+__global__ void k_output(const float4* __restrict__ accum, uint32_t npx, float inv_spp, float* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    const float4 a = accum[i];
+    out[3 * i + 0] = a.x * inv_spp;
+    out[3 * i + 1] = a.y * inv_spp;
+    out[3 * i + 2] = a.z * inv_spp;
+}
+
+__global__ void k_philox(uint64_t seed, const uint32_t* __restrict__ ctr, uint32_t n, uint32_t* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 r = philox_seed(seed, ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    out[4 * i + 0] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+__global__ void k_sample(uint32_t kind, uint32_t n, const float* __restrict__ wo, const float* __restrict__ u,
+                         const float* __restrict__ param, float* __restrict__ wi, float* __restrict__ weight,
+                         uint8_t* __restrict__ valid) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V3 r = v3(0.0f, 0.0f, 0.0f);
+    float w[3] = {0.0f, 0.0f, 0.0f};
+    bool ok = true;
+    if (kind == 0) {
+        r = sample_cosine(u[2 * i], u[2 * i + 1]);
+        w[0] = w[1] = w[2] = 1.0f;
+    } else if (kind == 1) {
+        const float f0[3] = {param[4 * i + 1], param[4 * i + 2], param[4 * i + 3]};
+        ok = sample_ggx(v3(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]), param[4 * i], f0, u[2 * i], u[2 * i + 1], r, w);
+    } else if (kind == 2) {
+        r = v3(-wo[3 * i], -wo[3 * i + 1], wo[3 * i + 2]);
+        w[0] = w[1] = w[2] = 1.0f;
+        ok = wo[3 * i + 2] > 0.0f;
+    } else {
+        float s, c;
+        sincos_poly(u[2 * i], s, c);
+        r = v3(s, c, 0.0f);
+    }
+    wi[3 * i + 0] = r.x;
+    wi[3 * i + 1] = r.y;
+    wi[3 * i + 2] = r.z;
+    weight[3 * i + 0] = w[0];
+    weight[3 * i + 1] = w[1];
+    weight[3 * i + 2] = w[2];
+    valid[i] = ok ? 1 : 0;
+}
+
+} // namespace
+
+// ------------------------------------------------------------------------------------
+// Launchers.
+void launch_raygen(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
+    const uint32_t block = p.m > 256 ? p.m : 256;
+    const uint32_t tiles_per_block = block / p.m;
+    const uint32_t n_tiles = p.tiles_x * p.tiles_y;
+    const uint32_t grid = (n_tiles + tiles_per_block - 1) / tiles_per_block;
+    k_raygen<<<grid, block, block * sizeof(uint16_t), st>>>(p, b.pixel, b.ray_o, b.ray_d, b.beta, b.radiance, b.alive);
+    lc.n++;
+}
+
+void launch_groups(const RenderParams& p, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc) {
+    const uint32_t npx = p.cam.width * p.cam.height;
+    k_groups<<<(npx + 255) / 256, 256, 0, st>>>(p, slot_of_pixel);
+    lc.n++;
+}
+
+static ShadeArgs shade_args(const DevScene& s, PathBuffers& b, bool first, uint32_t bounce, const cr_debug* dbg,
+                            uint32_t npx) {
+    ShadeArgs a;
+    a.tris = s.tris;
+    a.mats = s.mats;
+    a.env[0] = s.env[0];
+    a.env[1] = s.env[1];
+    a.env[2] = s.env[2];
+    a.pixel = b.pixel;
+    a.ray_o = b.ray_o;
+    a.ray_d = b.ray_d;
+    a.hit = b.hit;
+    a.beta = b.beta;
+    a.radiance = b.radiance;
+    a.alive = b.alive;
+    // group queue written by the compaction after the previous shade (double-buffered)
+    a.group_queue = first ? nullptr : b.group_queue + (size_t)((bounce - 1) & 1) * b.n_groups;
+    a.group_count = first ? nullptr : b.counts + 8 + 2 * (bounce - 1) + 1;
+    a.n_groups_max = b.n_groups;
+    if (dbg) a.dbg = *dbg;
+    else a.dbg = cr_debug{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    a.npx = npx;
+    return a;
+}
+
+void launch_shade(const DevScene& s, const RenderParams& p, PathBuffers& b, bool first, const cr_debug* dbg,
+                  cudaStream_t st, LaunchCount& lc) {
+    ShadeArgs a = shade_args(s, b, first, p.bounce, dbg, p.cam.width * p.cam.height);
+    const uint32_t n_pos = b.n_groups * p.k;
+    if (p.k <= 32) {
+        k_shade_warp<<<(n_pos + 127) / 128, 128, 0, st>>>(a, p);
+    } else {
+        k_shade_block<<<(n_pos + 255) / 256, 256, 0, st>>>(a, p);
+    }
+    lc.n++;
+}
+
+void launch_compact(const RenderParams& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc) {
+    const uint32_t K = p.k;
+    const uint32_t n_pos = b.n_groups * K;
+    const uint32_t n_blocks = (n_pos + kCompactBlock - 1) / kCompactBlock;
+    const int32_t* gq_in = first ? nullptr : b.group_queue + (size_t)((p.bounce - 1) & 1) * b.n_groups;
+    const uint32_t* ng_in = first ? nullptr : b.counts + 8 + 2 * (p.bounce - 1) + 1;
+    int32_t* gq_out = b.group_queue + (size_t)(p.bounce & 1) * b.n_groups;
+    uint32_t* out_counts = b.counts + 8 + 2 * p.bounce;
+    k_compact_count<<<n_blocks, kCompactBlock, 0, st>>>(gq_in, ng_in, b.n_groups, K, b.alive, b.block_counts);
+    k_compact_scan<<<1, 1024, 0, st>>>(b.block_counts, n_blocks, out_counts,
+                                      reinterpret_cast<unsigned long long*>(b.counts + kStatWord) + p.bounce);
+    k_compact_scatter<<<n_blocks, kCompactBlock, 0, st>>>(gq_in, ng_in, b.n_groups, K, b.alive, b.block_counts,
+                                                         b.ray_queue, gq_out);
+    lc.n += 3;
+}
+
+void launch_accumulate(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
+    k_accumulate<<<(b.n_slots + 255) / 256, 256, 0, st>>>(b.pixel, b.radiance, b.n_slots, b.accum);
+    lc.n++;
+}
+
+void launch_output(PathBuffers& b, uint32_t npx, float inv_spp, float* out_rgb, cudaStream_t st, LaunchCount& lc) {
+    k_output<<<(npx + 255) / 256, 256, 0, st>>>(b.accum, npx, inv_spp, out_rgb);
+    lc.n++;
+}
+
+void launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out, cudaStream_t st, LaunchCount& lc) {
+    if (!n) return;
+    k_philox<<<(n + 255) / 256, 256, 0, st>>>(seed, ctr, n, out);
+    lc.n++;
+}
+
+void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param, float* wi,
+                   float* weight, uint8_t* valid, cudaStream_t st, LaunchCount& lc) {
+    if (!n) return;
+    k_sample<<<(n + 255) / 256, 256, 0, st>>>(kind, n, wo, u, param, wi, weight, valid);
+    lc.n++;
+}
+
+// Sort the current bounce's ray queue by TwoPoint key; returns the sorted slot queue.
+const int32_t* launch_morton_sort(const DevScene& s, PathBuffers& b, uint32_t bounce, cudaStream_t st,
+                                  LaunchCount& lc) {
+    const uint32_t n_max = b.n_slots;
+    const uint32_t* count = b.counts + 8 + 2 * bounce;
+    float ext[3], scale[3];
+    float emax = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        ext[k] = s.hi[k] - s.lo[k];
+        emax = ext[k] > emax ? ext[k] : emax;
+    }
+    for (int k = 0; k < 3; ++k) scale[k] = ext[k] > 0.0f ? 32.0f / ext[k] : 0.0f;
+    uint32_t* ka = b.keys;
+    uint32_t* kb = b.keys + n_max;
+    int32_t* va = b.vals;
+    int32_t* vb = b.vals + n_max;
+    k_morton<<<(n_max + 255) / 256, 256, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max,
+                                                  make_float3(s.lo[0], s.lo[1], s.lo[2]),
+                                                  make_float3(scale[0], scale[1], scale[2]), 0.25f * emax, ka, va);
+    lc.n++;
+    const uint32_t n_blocks = (n_max + kSortTile - 1) / kSortTile;
+    for (uint32_t pass = 0; pass < 4; ++pass) {
+        const uint32_t shift = 8 * pass;
+        k_sort_hist<<<n_blocks, kSortThreads, 0, st>>>(ka, count, n_max, shift, n_blocks, b.sort_hist);
+        k_sort_scan<<<1, 1024, 0, st>>>(b.sort_hist, 256 * n_blocks);
+        k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ka, va, count, n_max, shift, n_blocks, b.sort_hist, kb, vb);
+        lc.n += 3;
+        uint32_t* tk = ka;
+        ka = kb;
+        kb = tk;
+        int32_t* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    return va; // after four passes the sorted pairs are back in the first buffers
+}
+
+uint32_t sort_hist_len(uint32_t n_slots) { return 256u * ((n_slots + kSortTile - 1) / kSortTile); }
+uint32_t compact_blocks(uint32_t n_pos) { return (n_pos + kCompactBlock - 1) / kCompactBlock; }
+
+} // namespace cr

@@ -280,8 +280,8 @@ def _box_room(lo, hi):
 def interior(seed: int = 11, n_spheres: int = 2000, width: int = 1280, height: int = 720) -> Scene:
     """Closed room [-4,4]x[0,4]x[-4,4] (12 triangles, Lambert 0.7) with n_spheres UV spheres
     (256 triangles each, radius uniform in [0.05,0.3], centres uniform in the room inset by
-    the radius), materials 60/30/10 per sphere, and a 1.5x1.5 ceiling light at y=3.999
-    (emission 20).  2000 spheres give 512,014 triangles; camera at (0,2,-3.8) looking +z."""
+    the radius, redrawn if closer than 0.25 to the camera), materials 60/30/10 per sphere,
+    and a 1.5x1.5 ceiling light at y=3.999 (emission 20).  2000 spheres give 512,014 triangles; camera at (0,2,-3.8) looking +z."""
     rng = np.random.default_rng(seed)
     room = _box_room((-4.0, 0.0, -4.0), (4.0, 4.0, 4.0))
     mtype, params = _palette(rng)
@@ -296,9 +296,13 @@ def interior(seed: int = 11, n_spheres: int = 2000, width: int = 1280, height: i
     cls = np.where(u < 0.6, 0, np.where(u < 0.9, 1, 2))
     base = np.array([0, N_PAL_LAMBERT, N_PAL_LAMBERT + N_PAL_GGX])
     size = np.array([N_PAL_LAMBERT, N_PAL_GGX, N_PAL_MIRROR])
+    cam_pos = np.array([0.0, 2.0, -3.8])
     for s in range(n_spheres):
-        r = rng.uniform(0.05, 0.3)
-        c = (rng.uniform(-4 + r, 4 - r), rng.uniform(0 + r, 4 - r), rng.uniform(-4 + r, 4 - r))
+        while True:  # keep a 0.25 clearance around the camera (redraw otherwise)
+            r = rng.uniform(0.05, 0.3)
+            c = (rng.uniform(-4 + r, 4 - r), rng.uniform(0 + r, 4 - r), rng.uniform(-4 + r, 4 - r))
+            if np.linalg.norm(np.array(c) - cam_pos) > r + 0.25:
+                break
         t = uv_sphere(c, r)
         sph.append(t)
         m = base[cls[s]] + rng.integers(0, size[cls[s]])

@@ -1,0 +1,181 @@
+"""GPU path tracer vs the CPU oracle on the same seeded inputs and random streams.
+
+Per-pixel radiance within 1e-4 relative (1e-6 absolute below 1e-2), excluding pixels whose
+result depends on a decision the oracle flags as fragile; per-bounce primitive ids, group
+categories, material classes and exit directions bit-exact on the non-fragile pixels."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import radiance_close
+from paper_2310_07182_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    from paper_2310_07182_gb300 import binding
+    binding.lib()
+    return binding
+
+
+_cache = {}
+
+
+def _scenes(cr, orc, name, **kw):
+    key = (name, tuple(sorted(kw.items())))
+    if key not in _cache:
+        sc = getattr(scenes, name)(**kw)
+        _cache[key] = (sc, cr.Scene(sc), orc.Scene(sc))
+    return _cache[key]
+
+
+def _render_both(cr, orc, trio, mode, *, spp=1, B=1, tile=(4, 4), k=None, interleave=True, seed=0, frame_base=0,
+                 cam=None, debug=False, **gkw):
+    sc, S, O = trio
+    cam = cam or sc.camera
+    K = k or tile[0] * tile[1]
+    dbg = None
+    bufs = None
+    if debug:
+        dbg, bufs = cr.debug_buffers(cam.width, cam.height, B)
+    img, st = S.render(cam, spp=spp, max_bounces=B, mode=mode, tile=tile, k=K, interleave=interleave, seed=seed,
+                       frame_base=frame_base, stats=True, debug=dbg, **gkw)
+    ref = orc.render(O, cam, spp=spp, max_bounces=B, mode=mode, tile=tile, k=K, interleave=interleave, seed=seed,
+                     frame_base=frame_base, debug=debug)
+    return img.cpu().numpy(), st, ref, bufs
+
+
+def _check(img, ref, max_taint=0.05):
+    ok = ref["taint"] == 0
+    assert ok.mean() >= 1 - max_taint, f"{(~ok).sum()} tainted pixels"
+    good, excess, nbad = radiance_close(img, ref["rgb"], ok)
+    assert good, f"{nbad} pixels off by up to {excess} beyond tolerance"
+
+
+@pytest.mark.parametrize("mode", ["independent", "direction_reuse", "morton_sort"])
+def test_tiny_config(cr, orc, mode):
+    """The tiny configuration: 64x64, 1,024 random triangles over a ground plane, Lambert,
+    white environment, 1 spp, 1 bounce, 4x4 groups."""
+    trio = _scenes(cr, orc, "tiny")
+    img, st, ref, _ = _render_both(cr, orc, trio, mode, B=1, tile=(4, 4), seed=1)
+    # one fragile ray taints its whole group of K = 16 pixels under direction reuse
+    assert ref["counters"][2] <= 1e-3 * (ref["counters"][0] + ref["counters"][1])
+    _check(img, ref, max_taint=0.002 if mode != "direction_reuse" else 0.02)
+    assert st["secondary_rays"] == ref["counters"][1]
+    assert st["primary_rays"] == 64 * 64
+
+
+@pytest.mark.parametrize("k", [1, 4, 16])
+@pytest.mark.parametrize("interleave", [True, False])
+def test_mixed_materials_multibounce(cr, orc, k, interleave):
+    trio = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    img, st, ref, _ = _render_both(cr, orc, trio, "direction_reuse", B=3, tile=(4, 4), k=k, interleave=interleave,
+                                   seed=7, frame_base=3)
+    _check(img, ref)
+
+
+@pytest.mark.parametrize("tile,k", [((8, 8), 64), ((16, 16), 256), ((16, 8), 32), ((32, 8), 128), ((2, 2), 2)])
+def test_group_shapes(cr, orc, tile, k):
+    trio = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    img, st, ref, _ = _render_both(cr, orc, trio, "direction_reuse", B=2, tile=tile, k=k, seed=11)
+    _check(img, ref)
+
+
+def test_ragged_image(cr, orc):
+    """Image sizes that leave partial tiles at the right and bottom borders."""
+    sc, S, O = _scenes(cr, orc, "tiny", material_mix="mixed")
+    cam = scenes.Camera(sc.camera.pos, sc.camera.look_at, sc.camera.up, 55.0, 53, 29)
+    img, st, ref, _ = _render_both(cr, orc, (sc, S, O), "direction_reuse", B=2, tile=(8, 8), k=8, seed=2, cam=cam)
+    _check(img, ref)
+    assert img.shape == (29, 53, 3)
+
+
+def test_debug_capture_bit_exact(cr, orc):
+    """Per-bounce hit ids, group categories, classes and tangent/world exit directions."""
+    trio = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    B = 3
+    img, st, ref, bufs = _render_both(cr, orc, trio, "direction_reuse", B=B, tile=(8, 4), k=8, seed=5, debug=True)
+    ok = (ref["taint"] == 0).reshape(-1)
+    g = {k: v.cpu().numpy() for k, v in bufs.items()}
+    assert np.array_equal(g["prim"][:, ok], ref["dbg_prim"][:, ok])
+    for b in range(B):
+        alive = (ref["dbg_flags"][b] & 1).astype(bool) & ok
+        assert np.array_equal(g["flags"][b][ok] & 3, ref["dbg_flags"][b][ok] & 3)
+        assert np.array_equal(g["cat"][b][alive], ref["dbg_cat"][b][alive])
+        assert np.array_equal(g["cls"][b][alive], ref["dbg_cls"][b][alive])
+        assert np.array_equal(g["local"][b][alive].view(np.uint32), ref["dbg_local"][b][alive].view(np.uint32))
+        assert np.array_equal(g["world"][b][alive].view(np.uint32), ref["dbg_world"][b][alive].view(np.uint32))
+    cats = set(np.unique(ref["dbg_cat"][0][ok]).tolist())
+    assert {1, 2, 3} <= cats
+
+
+def test_morton_and_k1_equal_independent_bit_exact(cr, orc):
+    sc, S, O = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    kw = dict(spp=2, max_bounces=3, tile=(4, 4), seed=13)
+    a, _ = S.render(mode="independent", k=16, **kw)
+    b, _ = S.render(mode="morton_sort", k=16, **kw)
+    c, _ = S.render(mode="direction_reuse", k=1, **kw)
+    assert torch.equal(a, b) and torch.equal(a, c)
+
+
+def test_furnace_exact(cr, orc):
+    sc = scenes.furnace(albedo=(0.5, 0.25, 0.75), width=64, height=48)
+    S = cr.Scene(sc)
+    alb = torch.tensor(np.float32([0.5, 0.25, 0.75]), device="cuda")
+    for mode in ("independent", "direction_reuse", "morton_sort"):
+        for B in (1, 3):
+            img, _ = S.render(mode=mode, max_bounces=B, tile=(8, 8), k=8, seed=4)
+            hit = (img == alb).all(dim=-1)
+            miss = (img == 1.0).all(dim=-1)
+            assert bool((hit | miss).all())
+            assert 0.2 < float(hit.float().mean()) < 0.9
+
+
+def test_spp_resume_and_determinism(cr, orc):
+    trio = _scenes(cr, orc, "tiny", material_mix="mixed")
+    img, st, ref, _ = _render_both(cr, orc, trio, "direction_reuse", spp=4, B=2, tile=(4, 4), k=4, seed=21)
+    _check(img, ref)
+    sc, S, O = trio
+    a, _ = S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21)
+    b, _ = S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21, flags=cr.CR_OPT_PERSISTENT, block=256)
+    assert torch.equal(a, b)
+    # host output buffer
+    h = np.zeros((sc.camera.height, sc.camera.width, 3), np.float32)
+    S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21, out=h)
+    assert np.array_equal(h, a.cpu().numpy())
+
+
+def test_interior_emitters_sample(cr, orc):
+    """The interior scene (closed room, 2,000 spheres, ceiling light) at a reduced
+    resolution: emission, 4 bounces, all three material classes."""
+    sc = scenes.interior(width=128, height=96)
+    S, O = cr.Scene(sc), orc.Scene(sc)
+    img, st, ref, _ = _render_both(cr, orc, (sc, S, O), "direction_reuse", spp=4, B=4, tile=(8, 8), k=8, seed=11)
+    _check(img, ref, max_taint=0.1)
+    assert (img > 0).any(axis=-1).mean() > 0.01  # light reaches the camera
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", ["direction_reuse", "independent"])
+def test_landscape_full_size_sampled_tiles(cr, orc, mode):
+    """The benchmark's workload and launch configuration (1920x1080 landscape, 2.1M
+    triangles, 1 spp, 2 bounces, 8x8 tiles, K = 8): the GPU renders the whole frame, the
+    oracle renders four bands of 96 tiles, compared pixel by pixel."""
+    sc, S, O = _scenes(cr, orc, "landscape")
+    cam = sc.camera
+    img, st = S.render(spp=1, max_bounces=2, mode=mode, tile=(8, 8), k=8, seed=0, stats=True)
+    img = img.cpu().numpy()
+    ntx, nty = cam.width // 8, cam.height // 8
+    nt = ntx * nty
+    for b0 in (0, nt // 3, 2 * nt // 3, nt - 96):
+        ref = orc.render(O, cam, spp=1, max_bounces=2, mode=mode, tile=(8, 8), k=8, seed=0, tiles=(b0, b0 + 96))
+        mask = np.zeros((cam.height, cam.width), bool)
+        for t in range(b0, b0 + 96):
+            tx, ty = t % ntx, t // ntx
+            mask[ty * 8:(ty + 1) * 8, tx * 8:(tx + 1) * 8] = True
+        ok = mask & (ref["taint"] == 0)
+        assert ok.sum() >= 0.85 * mask.sum()
+        good, excess, nbad = radiance_close(img, ref["rgb"], ok)
+        assert good, f"band {b0}: {nbad} pixels off by {excess}"

@@ -1,0 +1,128 @@
+"""GPU closest-hit traversal vs the FP64 oracle on the same fp32 rays: primitive ids bit-exact
+except decisions the oracle flags as fragile, t within 1e-5 relative."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_07182_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    from paper_2310_07182_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _compare(orc, sc, S, rays, skip=None, max_fragile=2e-3, **kw):
+    O = orc.Scene(sc)
+    p_ref, t_ref, fr = orc.trace(O, rays, skip=skip)
+    prim, t = S.trace(rays, skip, **kw)
+    prim, t = np.asarray(prim), np.asarray(t)
+    ok = fr == 0
+    assert fr.mean() <= max_fragile
+    assert np.array_equal(prim[ok], p_ref[ok])
+    hit = ok & (p_ref >= 0)
+    assert np.all(np.abs(t[hit] - t_ref[hit]) <= 1e-5 * t_ref[hit])
+    assert np.all(np.isinf(t[ok & (p_ref < 0)]))
+    return prim, t
+
+
+@pytest.mark.parametrize("n", [1, 31, 1000, 20001])
+def test_tiny_random_rays(cr, orc, n):
+    sc = scenes.tiny()
+    S = cr.Scene(sc)
+    rays = scenes.random_rays(n, n)
+    _compare(orc, sc, S, rays)
+    # device tensors in and out give the same answer
+    p1, t1 = S.trace(rays)
+    p2, t2 = S.trace(torch.from_numpy(rays).cuda())
+    assert np.array_equal(np.asarray(p1), p2.cpu().numpy())
+    assert np.array_equal(np.asarray(t1), t2.cpu().numpy())
+
+
+def test_launch_shapes_agree(cr, orc):
+    sc = scenes.tiny(seed=4, n_soup=5000)
+    S = cr.Scene(sc)
+    rays = scenes.random_rays(9, 30000)
+    ref = _compare(orc, sc, S, rays)
+    for block in (32, 64, 256, 512):
+        for flags in (0, cr.CR_OPT_PERSISTENT):
+            p, t = S.trace(rays, block=block, flags=flags)
+            assert np.array_equal(np.asarray(p), ref[0]) and np.array_equal(np.asarray(t), ref[1])
+
+
+def test_skip_tmax_axis_aligned_and_ties(cr, orc):
+    tri = [-1, -1, 2, 1, -1, 2, 0, 1, 2]
+    far = [-1, -1, 3, 1, -1, 3, 0, 1, 3]
+    sc = scenes._finish("dup", np.array([far, tri, tri, tri, tri] + [far] * 7), np.zeros(12), [0],
+                        np.zeros((1, 7)), (1, 1, 1), None)
+    S = cr.Scene(sc)
+    rays = np.zeros((6, 8), np.float32)
+    rays[:, 0:3] = (0.1, -0.2, 0.0)
+    rays[:, 4:7] = (0.0, 0.0, 1.0)  # zero direction components
+    rays[:, 7] = np.inf
+    rays[4, 7] = 1.5   # tmax before the first triangle
+    rays[5, 4:7] = (0.0, 0.0, -1.0)
+    skip = np.array([-1, 1, 2, 0, -1, -1], np.int32)
+    prim, t = S.trace(rays, skip)
+    assert np.asarray(prim).tolist() == [1, 2, 1, 1, -1, -1]
+    assert np.asarray(t)[:4].tolist() == [2.0, 2.0, 2.0, 2.0]
+
+
+def test_watertight_shared_edges(cr, orc):
+    """Rays aimed exactly at shared edges and vertices of a closed mesh never slip through."""
+    sc = scenes.furnace(subdiv=3)
+    S = cr.Scene(sc)
+    v = sc.tri_xyz.reshape(-1, 3, 3).astype(np.float64)
+    tgt = np.concatenate([(v[:, 0] + v[:, 1]) / 2, v[:, 2]])  # edge midpoints and vertices
+    o = np.zeros_like(tgt)
+    o[:, :] = tgt * 3.0 + np.array([0.013, -0.007, 0.011])
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.zeros((tgt.shape[0], 8), np.float32)
+    rays[:, 0:3] = o
+    rays[:, 4:7] = d
+    rays[:, 7] = np.inf
+    prim, t = S.trace(rays)
+    assert (np.asarray(prim) >= 0).all()
+
+
+@pytest.mark.slow
+def test_landscape_full_size_sample(cr, orc):
+    """The 2.1M-triangle landscape: camera rays of the bench's 1920x1080 view, traced on the
+    GPU in full, a sample of 3000 checked against the oracle."""
+    sc = scenes.landscape()
+    S = cr.Scene(sc)
+    assert S.info["n_tri"] == 2093058 and S.info["depth2"] < 64
+    rng = np.random.default_rng(1)
+    cam = sc.camera
+    n = 1 << 20
+    px = rng.integers(0, cam.width, n)
+    py = rng.integers(0, cam.height, n)
+    th = np.tan(np.radians(cam.vfov_deg) / 2)
+    f = np.array(cam.look_at) - np.array(cam.pos)
+    f /= np.linalg.norm(f)
+    r = np.cross(f, cam.up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    sx = (2 * (px + 0.5) / cam.width - 1) * th * cam.width / cam.height
+    sy = (1 - 2 * (py + 0.5) / cam.height) * th
+    d = f + sx[:, None] * r + sy[:, None] * u
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.zeros((n, 8), np.float32)
+    rays[:, 0:3] = cam.pos
+    rays[:, 4:7] = d
+    rays[:, 7] = np.inf
+    prim, t = S.trace(torch.from_numpy(rays).cuda())
+    prim, t = prim.cpu().numpy(), t.cpu().numpy()
+    sel = rng.choice(n, 3000, replace=False)
+    O = orc.Scene(sc)
+    p_ref, t_ref, fr = orc.trace(O, rays[sel])
+    ok = fr == 0
+    assert fr.mean() < 1e-2
+    assert np.array_equal(prim[sel][ok], p_ref[ok])
+    hit = ok & (p_ref >= 0)
+    assert np.all(np.abs(t[sel][hit] - t_ref[hit]) <= 1e-5 * t_ref[hit])
