@@ -51,8 +51,8 @@ const char* cr_last_error(void);
 const char* cr_version(void);
 
 /* ---------------------------------------------------------------------------------- */
-/* Scenes.  Material classes follow Sec. 3.2: Lambert is "diffuse", GGX and mirror are
- * "glossy or specular"; emitters end a path and take no part in grouping. */
+/* Scenes.  Material classes follow Sec. 3.2: Lambert is diffuse, GGX and mirror are glossy
+ * or specular; emitters end a path and take no part in grouping. */
 typedef enum { CR_MAT_LAMBERT = 0, CR_MAT_GGX = 1, CR_MAT_MIRROR = 2, CR_MAT_EMITTER = 3 } cr_mat_type;
 
 typedef struct {
@@ -166,7 +166,7 @@ cr_status cr_render_opts_default(cr_render_opts* opts);
  * the mean radiance (linear fp32 RGB, row-major, top row first) to out_rgb.
  *   scene        from cr_scene_create.
  *   camera       host struct.
- *   spp          >= 1 (Sec. 3.1: several samples = one sample in "smaller pixels").
+ *   spp          >= 1 (Sec. 3.1: several samples = one sample in each of several finer pixels).
  *   max_bounces  1..16: number of secondary rays per path (no Russian roulette).
  *   mode         CR_INDEPENDENT (each path samples its own BSDF), CR_MORTON_SORT (the same
  *                paths, secondary rays sorted by a 30-bit TwoPoint Morton key before each

@@ -4,14 +4,14 @@
  * smoke check and the benchmark's CPU baseline, never by the product path.
  *
  * It follows the paper's steps in the paper's order:
- *   Sec. 3.1  one path per pixel per sample ("smaller pixels" for spp > 1); shading point
+ *   Sec. 3.1  one path per pixel per sample (several samples = finer pixels); shading point
  *             = first hit; the secondary ray's direction is the exit direction.
  *   Sec. 3.3  interleaved grouping: W x H tiles, in-tile pixel numbers shuffled by a
  *             linear congruential sequence, group = shuffled number / K.
  *   Sec. 3.2  tangent-space direction reuse with three group types (diffuse: reuse one
  *             member's exit direction; glossy: unchanged; hybrid: diffuse members take the
  *             average tangent-space exit direction of the glossy/specular members).
- *   Sec. 3.1  world-space "direct" reuse, kept only as the ablation / negative control.
+ *   Sec. 3.1  world-space direct reuse, kept only as the ablation / negative control.
  * Intersection is a plain Moller-Trumbore test in FP64 over a median-split BVH (or all
  * triangles).  Choices the paper leaves open are stated where they are made.
  *
@@ -84,9 +84,9 @@ static void philox_seed(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, ui
 static float to_unit(uint32_t x) { return (float)(x >> 8) * 0x1.0p-24f; }
 
 /* ------------------------------------------------------------------------------------ */
-/* Sec. 3.3: "pixels are numbered based on their order on the screen. These numbers are then
- * shuffled using a linear congruence method".  Reading: the shuffled number of the tile's
- * i-th pixel is the i-th term of the full-period sequence x_{k+1} = (a x_k + c) mod m. */
+/* Sec. 3.3 numbers a tile's pixels in screen order and shuffles the numbers with a linear
+ * congruential method whose form it does not give.  Reading: the shuffled number of the
+ * tile's i-th pixel is the i-th term of the full-period sequence x_{k+1} = (a x_k + c) mod m. */
 void orc_lcg_sequence(uint32_t m, uint32_t a, uint32_t c, uint32_t x0, uint32_t* out) {
     uint64_t x = x0 % m;
     for (uint32_t i = 0; i < m; ++i) {
@@ -95,8 +95,8 @@ void orc_lcg_sequence(uint32_t m, uint32_t a, uint32_t c, uint32_t x0, uint32_t*
     }
 }
 
-/* Per tile and per frame parameters (Sec. 3.3: the composition "varies in each tile and in
- * each frame").  With m a power of two, a = 1 (mod 4) and odd c give the full period
+/* Per tile and per frame parameters (Sec. 3.3: group composition changes from tile to tile
+ * and from frame to frame).  With m a power of two, a = 1 (mod 4) and odd c give the full period
  * (Hull-Dobell), so the sequence is a permutation of [0, m). */
 void orc_tile_sigma(uint32_t tile_w, uint32_t tile_h, uint32_t tile, uint32_t frame,
                     uint64_t seed, int lcg, uint32_t* sigma, uint32_t* abc_x0) {
@@ -430,7 +430,9 @@ typedef struct {
     int threat_overflow;
     double hits_t[64];
     int32_t hits_id[64];
+    double hits_terr[64]; /* FP32 error scale of t for each hit */
     int n_hits;
+    double terr_best;
 } tstate;
 
 static void dsub(const double* a, const double* b, double* r) {
@@ -528,9 +530,19 @@ static void test_triangle(const orc_scene* s, uint32_t tri, tstate* st) {
             st->threat_overflow = 1;
     }
     if (hit) {
+        /* error scale of an FP32 t: coordinate rounding (eta) amplified by the obliquity
+         * of the ray to the triangle's plane */
+        double nrm[3];
+        dcross(e1, e2, nrm);
+        double cosv = fabs(ddot(nrm, st->dn)) / sqrt(ddot(nrm, nrm));
+        double omag = fabs(st->o[0]);
+        if (fabs(st->o[1]) > omag) omag = fabs(st->o[1]);
+        if (fabs(st->o[2]) > omag) omag = fabs(st->o[2]);
+        double terr = 4.0 * 0x1.0p-24 * (mag + omag) / st->dlen / (cosv > 1e-12 ? cosv : 1e-12);
         if (st->n_hits < 64) {
             st->hits_t[st->n_hits] = t;
             st->hits_id[st->n_hits] = (int32_t)tri;
+            st->hits_terr[st->n_hits] = terr;
             st->n_hits++;
         } else {
             st->fragile = 1;
@@ -539,6 +551,7 @@ static void test_triangle(const orc_scene* s, uint32_t tri, tstate* st) {
             st->found = 1;
             st->tbest = t;
             st->best = (int32_t)tri;
+            st->terr_best = terr;
         }
     }
 }
@@ -631,7 +644,11 @@ static void trace_ray(const orc_scene* s, const double* o, const double* d, int3
     if (st.threat_overflow) st.fragile = 1;
     *prim = st.found ? st.best : -1;
     *tout = st.found ? st.tbest : INFINITY;
-    *fragile = (uint8_t)st.fragile;
+    /* bit 0: the hit/miss or primitive decision is fragile; bit 1: t itself is
+     * ill-conditioned in FP32 (error scale above 1e-5 t: oblique hits, hits close to the
+     * ray origin relative to the coordinates' magnitude) */
+    int tbad = st.found && st.terr_best > 1e-5 * st.tbest;
+    *fragile = (uint8_t)((st.fragile ? 1 : 0) | (tbad ? 2 : 0));
 }
 
 void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n, int use_bvh,
@@ -782,7 +799,7 @@ static void trace_path(const orc_scene* s, pstate* ps, uint64_t* counters) {
     trace_ray(s, ps->o, d, ps->hit, 1, &prim, &t, &fr);
     ps->hit = prim;
     ps->t = t;
-    if (fr) {
+    if (fr & 1) {
         ps->taint = 1;
         counters[2]++;
     }

@@ -59,8 +59,9 @@ void orc_scene_free(orc_scene* s);
 uint32_t orc_scene_nodes(const orc_scene* s);
 
 /* Closest hit of n rays (rays: n x 8 fp32: o.xyz, unused, d.xyz, unused).
- * prim = original triangle index or -1, t in units of |d|, fragile = decision too close
- * to call in FP32 (near-tie, near an edge, near the origin). use_bvh=0: brute force. */
+ * prim = original triangle index or -1, t in units of |d|; fragile bit 0 = decision too
+ * close to call in FP32 (near-tie, near an edge, near the origin), bit 1 = t too
+ * ill-conditioned in FP32 to agree to 1e-5 relative.  use_bvh=0: brute force. */
 void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
                int use_bvh, int32_t* prim, double* t, uint8_t* fragile);
 

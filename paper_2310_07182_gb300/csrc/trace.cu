@@ -1,4 +1,4 @@
-// trace.cu -- closest-hit BVH traversal (the "intersection" step that dominates path
+// trace.cu -- closest-hit BVH traversal (the intersection step, which dominates path
 // tracing time, Sec. 1), one ray per thread.
 //
 // Stackful while-while traversal of the 64-byte two-child nodes: both child boxes are

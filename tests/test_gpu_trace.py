@@ -21,10 +21,11 @@ def _compare(orc, sc, S, rays, skip=None, max_fragile=2e-3, **kw):
     p_ref, t_ref, fr = orc.trace(O, rays, skip=skip)
     prim, t = S.trace(rays, skip, **kw)
     prim, t = np.asarray(prim), np.asarray(t)
-    ok = fr == 0
-    assert fr.mean() <= max_fragile
+    ok = (fr & 1) == 0
+    assert (~ok).mean() <= max_fragile
+    assert ((fr & 2) != 0).mean() <= 0.1  # origins inside the soup: short, ill-conditioned t
     assert np.array_equal(prim[ok], p_ref[ok])
-    hit = ok & (p_ref >= 0)
+    hit = (fr == 0) & (p_ref >= 0)
     assert np.all(np.abs(t[hit] - t_ref[hit]) <= 1e-5 * t_ref[hit])
     assert np.all(np.isinf(t[ok & (p_ref < 0)]))
     return prim, t
@@ -121,8 +122,8 @@ def test_landscape_full_size_sample(cr, orc):
     sel = rng.choice(n, 3000, replace=False)
     O = orc.Scene(sc)
     p_ref, t_ref, fr = orc.trace(O, rays[sel])
-    ok = fr == 0
-    assert fr.mean() < 1e-2
+    ok = (fr & 1) == 0
+    assert (~ok).mean() < 1e-2
     assert np.array_equal(prim[sel][ok], p_ref[ok])
-    hit = ok & (p_ref >= 0)
+    hit = (fr == 0) & (p_ref >= 0)
     assert np.all(np.abs(t[sel][hit] - t_ref[hit]) <= 1e-5 * t_ref[hit])
