@@ -217,6 +217,31 @@ cr_status cr_debug_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32
 cr_status cr_debug_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param,
                           float* wi, float* weight, uint8_t* valid);
 
+/* ---------------------------------------------------------------------------------- */
+/* Tracing without allocation.  The paper has no counterpart: this is a library service.
+ *
+ * cr_trace_rays allocates device staging buffers on every call.  Some callers cannot allow
+ * that: a host framework that owns all device memory through its own pool allocator and
+ * forbids raw cudaMalloc, a latency-critical loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree, or a process that has reserved nearly all device
+ * memory, so an allocation could fail mid-frame.  cr_trace_rays_static computes exactly
+ * what cr_trace_rays computes (same kernels, BVH2, block 128) but keeps its scratch (ray and
+ * hit records, 40 bytes per ray) in one file-scope device array sized for
+ * CR_TRACE_STATIC_MAX_RAYS rays (2.5 MiB), which every GPU that loads the library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   rays, skip_prim (or NULL), prim, t: DEVICE pointers with the layouts of cr_trace_rays;
+ *   host pointers are rejected (staging them would need an allocation).
+ *   n: 0..CR_TRACE_STATIC_MAX_RAYS; larger n returns CR_ERR_INVALID_ARG (trace in chunks).
+ *   stream: cudaStream_t to run on (NULL = legacy default stream); synchronised on return.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents: calls that overlap on the GPU
+ * (other host threads, or other streams) race on it, so serialise them.
+ * Errors: CR_ERR_INVALID_ARG, CR_ERR_CUDA. */
+#define CR_TRACE_STATIC_MAX_RAYS 65536u
+cr_status cr_trace_rays_static(cr_scene* scene, const float* rays, const int32_t* skip_prim, uint32_t n,
+                               int32_t* prim, float* t, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,7 +100,10 @@ _SIGS = [
     ("cr_debug_philox", C.c_int, [C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p]),
     ("cr_debug_sample", C.c_int, [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    ("cr_trace_rays_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
 ]
+CR_TRACE_STATIC_MAX_RAYS = 65536
 
 
 def exported_names():
@@ -229,6 +232,14 @@ def cr_trace_rays(handle, rays, skip, prim, t, opts: cr_render_opts | None = Non
         opts.stream = _current_stream([rays, prim, t])
     _check(lib().cr_trace_rays(handle, _ptr(rays), _ptr(skip), n, _ptr(prim), _ptr(t),
                                C.byref(opts) if opts is not None else None))
+
+
+def cr_trace_rays_static(handle, rays, skip, prim, t, stream=None):
+    """Allocation-free closest hits: every array must be a CUDA tensor (see include/cr.h)."""
+    n = rays.shape[0]
+    if stream is None:
+        stream = _current_stream([rays, prim, t])
+    _check(lib().cr_trace_rays_static(handle, _ptr(rays), _ptr(skip), n, _ptr(prim), _ptr(t), stream))
 
 
 def cr_debug_groups(width, height, group_w, group_h, interleave, seed, frame, out):

@@ -129,6 +129,11 @@ struct cr_scene {
 
 using namespace cr;
 
+namespace cr {
+void set_last_error(const char* msg) { g_err = msg; }
+const DevScene* dev_scene_of(const cr_scene* s) { return &s->dev; }
+} // namespace cr
+
 extern "C" const char* cr_last_error(void) { return g_err.c_str(); }
 extern "C" const char* cr_version(void) { return "cr 0.1 sm_103a"; }
 

@@ -153,4 +153,8 @@ void launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out
 void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param, float* wi,
                    float* weight, uint8_t* valid, cudaStream_t st, LaunchCount& lc);
 
+// Thread-local message returned by cr_last_error(); handle -> device scene.
+void set_last_error(const char* msg);
+const DevScene* dev_scene_of(const cr_scene* s);
+
 } // namespace cr
