@@ -306,6 +306,12 @@ def run_ours(args):
     e2e_s = aggregate(time.perf_counter() - t0, "max")
     e2e_rays = aggregate(results[modes[0]]["secondary_rays_per_step"] * args.steps, "sum")
 
+    extras = {}
+    if not args.core_only:
+        extras["precision_interior"] = precision_leg(cr, scenes, rank, world, args)
+        extras["table3_sweep"] = sweep_leg(cr, S, cam, out, stream, rank, world)
+        extras["quality"] = quality_leg(cr, S, cam, stream, results)
+
     if rank != 0:
         return
     R = results[modes[0]]
@@ -343,11 +349,122 @@ def run_ours(args):
                         for m in modes if m != "direction_reuse"},
         "secondary_rays_per_step": int(R["secondary_rays_per_step"]),
     }
+    line.update(extras)
     if not args.no_cpu_baseline:
         v, thr, sample, dt = cpu_oracle_rate(sc, args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
+
+
+def _timed_renders(cr, S, cam, out, stream, steps, warmup, frame0=0, **kw):
+    """Device time (ms, summed) and secondary rays of ``steps`` renders after ``warmup``."""
+    import torch
+    spp = kw.pop("spp", SPP)
+    bounces = kw.pop("bounces", BOUNCES)
+    mode = kw.pop("mode", "direction_reuse")
+    tile = kw.pop("tile", TILE)
+    ms = tr = 0.0
+    sec = 0
+    for i in range(warmup + steps):
+        st = cr.cr_stats()
+        o = cr.make_opts(frame_base=frame0 + i, flags=cr.CR_OPT_STATS, stream=stream, stats=st, **kw)
+        cr.cr_render_ex(S.handle, cam, spp, bounces, mode, tile[0], tile[1], out, o)
+        if i >= warmup:
+            d = st.as_dict()
+            ms += d["ms_total"]
+            tr += d["ms_trace_secondary"]
+            sec += d["secondary_rays"]
+    torch.cuda.synchronize()
+    return ms, tr, sec
+
+
+def precision_leg(cr, scenes, rank, world, args):
+    """Interior (1280x720, 512,014 triangles, 16 spp, 4 bounces, direction reuse): FP32 BVH2
+    vs the 8-bit quantised BVH8-Q; the images must be identical bit for bit."""
+    import torch
+    sc = scenes.interior()
+    S8 = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
+    cam = sc.camera
+    out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    res = {"workload": "interior 1280x720, 2,000 UV spheres + room + ceiling light (512,014 tris), 16 spp, "
+                       "4 bounces, direction_reuse 8x8 K=8", "scene_bytes": S8.info["device_bytes"]}
+    imgs = {}
+    for name, bvh in (("bvh2", cr.CR_BVH2), ("bvh8q", cr.CR_BVH8Q)):
+        ms, tr, sec = _timed_renders(cr, S8, cam, out, stream, 3, 2, frame0=rank * 100, spp=16, bounces=4, k=K,
+                                     bvh=bvh)
+        ms = aggregate(ms, "max")
+        sec = aggregate(sec, "sum")
+        res[name] = {"mrays": round(sec / ms / 1e3, 2), "trace_only_mrays": round(sec / aggregate(tr, "max") / 1e3, 2),
+                     "ms_per_render": round(ms / 3, 3)}
+        o = cr.make_opts(k=K, frame_base=0, bvh=bvh, stream=stream)
+        cr.cr_render_ex(S8.handle, cam, 16, 4, "direction_reuse", 8, 8, out, o)
+        imgs[name] = out.clone()
+    res["images_bit_identical"] = bool(torch.equal(imgs["bvh2"], imgs["bvh8q"]))
+    res["nodes"] = {"bvh2": S8.info["n_nodes2"], "bvh8q": S8.info["n_nodes8"]}
+    S8.close()
+    return res
+
+
+def sweep_leg(cr, S, cam, out, stream, rank, world):
+    """Tile (W,H) x group size K sweep on the landscape (the analogue of Table 3): secondary
+    trace-only Mrays/s of direction reuse and its ratio to independent sampling."""
+    ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 3, 1, mode="independent", k=K)
+    base = sec / tr / 1e3
+    rows = {}
+    for tile in ((8, 8), (16, 8), (16, 16), (32, 8)):
+        for k in (8, 16, 32, 64):
+            ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 3, 1, tile=tile, k=k)
+            v = sec / tr / 1e3
+            rows[f"{tile[0]}x{tile[1]}_K{k}"] = {"trace_only_mrays": round(v, 1), "ratio": round(v / base, 3),
+                                                 "whole_step_mrays": round(sec / ms / 1e3, 1)}
+    return {"independent_trace_only_mrays": round(base, 1), "direction_reuse": rows}
+
+
+def quality_leg(cr, S, cam, stream, results):
+    """MSE at equal time against a 4096-spp independent reference (Sec. 5.2 uses 4096
+    iterations), for budgets of 0.1/0.5/2 s of device time per mode, and PSNR at 128 spp
+    (the analogue of Table 2)."""
+    import torch
+    ref = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    img = torch.empty_like(ref)
+    n_ref = 4096
+    for ci, c in enumerate(range(0, n_ref, 256)):  # mean of 16 chunks of 256 samples
+        o = cr.make_opts(k=K, frame_base=1_000_000 + c, stream=stream)
+        cr.cr_render_ex(S.handle, cam, 256, BOUNCES, "independent", TILE[0], TILE[1], img, o)
+        if ci == 0:
+            ref.copy_(img)
+        else:
+            ref += img
+    ref /= n_ref // 256
+    torch.cuda.synchronize()
+    out = {"reference_spp": n_ref, "budgets_s": [0.1, 0.5, 2.0], "modes": {}}
+    peak = float(ref.max())
+    variants = (("direction_reuse", "direction_reuse", 0), ("independent", "independent", 0),
+                ("morton_sort", "morton_sort", 0), ("direction_reuse_bounce1_only", "direction_reuse", 1))
+    for name, mode, depth in variants:
+        ms_spp = results.get(name, {}).get("ms_per_step")
+        if ms_spp is None:
+            ms, _, _ = _timed_renders(cr, S, cam, img, stream, 3, 1, mode=mode, k=K, reuse_depth=depth)
+            ms_spp = ms / 3
+        row = {"ms_per_spp": round(ms_spp, 4), "mse": [], "spp": []}
+        for T in out["budgets_s"]:
+            spp = max(1, int(T * 1e3 / ms_spp))
+            o = cr.make_opts(k=K, frame_base=0, stream=stream, reuse_depth=depth)
+            cr.cr_render_ex(S.handle, cam, spp, BOUNCES, mode, TILE[0], TILE[1], img, o)
+            row["mse"].append(float(((img - ref) ** 2).mean()))
+            row["spp"].append(spp)
+        o = cr.make_opts(k=K, frame_base=0, stream=stream, reuse_depth=depth)
+        cr.cr_render_ex(S.handle, cam, 128, BOUNCES, mode, TILE[0], TILE[1], img, o)
+        mse128 = float(((img - ref) ** 2).mean())
+        row["psnr_128spp_db"] = round(10 * math.log10(peak * peak / mse128), 3)
+        # bias estimate: the 4096-spp mean of the mode against the reference
+        o = cr.make_opts(k=K, frame_base=2_000_000, stream=stream, reuse_depth=depth)
+        cr.cr_render_ex(S.handle, cam, 1024, BOUNCES, mode, TILE[0], TILE[1], img, o)
+        row["mse_1024spp"] = float(((img - ref) ** 2).mean())
+        out["modes"][name] = row
+    return out
 
 
 def main():
@@ -358,6 +475,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--core-only", action="store_true", help="skip the precision, sweep and quality legs")
     ap.add_argument("--modes", default="direction_reuse,independent,morton_sort",
                     help="modes to time (the first is the headline); profiling runs use one")
     args = ap.parse_args()

@@ -66,6 +66,13 @@ class cr_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class cr_bvh_report(C.Structure):
+    _fields_ = [("n_nodes2", C.c_uint32), ("depth2", C.c_uint32), ("n_nodes8", C.c_uint32), ("depth8", C.c_uint32),
+                ("stack_bound8", C.c_uint32), ("covered2", C.c_uint32), ("covered8", C.c_uint32),
+                ("violations2", C.c_uint32), ("violations8", C.c_uint32), ("pad", C.c_uint32),
+                ("build_ms2", C.c_double), ("build_ms8", C.c_double)]
+
+
 class cr_debug(C.Structure):
     _fields_ = [("prim", C.c_void_p), ("cat", C.c_void_p), ("cls", C.c_void_p), ("flags", C.c_void_p),
                 ("local", C.c_void_p), ("world", C.c_void_p)]
@@ -100,6 +107,7 @@ _SIGS = [
     ("cr_debug_philox", C.c_int, [C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p]),
     ("cr_debug_sample", C.c_int, [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    ("cr_debug_bvh_check", C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(cr_bvh_report)]),
     ("cr_trace_rays_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
 ]
@@ -232,6 +240,13 @@ def cr_trace_rays(handle, rays, skip, prim, t, opts: cr_render_opts | None = Non
         opts.stream = _current_stream([rays, prim, t])
     _check(lib().cr_trace_rays(handle, _ptr(rays), _ptr(skip), n, _ptr(prim), _ptr(t),
                                C.byref(opts) if opts is not None else None))
+
+
+def cr_debug_bvh_check(tri_xyz, flags=CR_BVH2 | CR_BVH8Q) -> dict:
+    tri_xyz = np.ascontiguousarray(tri_xyz, dtype=np.float32).reshape(-1, 9)
+    r = cr_bvh_report()
+    _check(lib().cr_debug_bvh_check(_ptr(tri_xyz), tri_xyz.shape[0], flags, C.byref(r)))
+    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 def cr_trace_rays_static(handle, rays, skip, prim, t, stream=None):

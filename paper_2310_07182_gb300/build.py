@@ -29,7 +29,7 @@ def _flags(src: str):
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
     if src.endswith(".cu"):
         return common + ARCH + ["-lineinfo", "-Xptxas", "-O3"]
-    return common + ["-Xcompiler", "-O2"]
+    return common + ["-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off"]
 
 
 def _newest_input() -> float:

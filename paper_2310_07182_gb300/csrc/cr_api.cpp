@@ -118,6 +118,7 @@ struct cr_scene {
     void* d_nodes2 = nullptr;
     void* d_nodes8 = nullptr;
     void* d_tris = nullptr;
+    void* d_tris8 = nullptr;
     void* d_mats = nullptr;
     // render workspace, grown on demand
     cr::PathBuffers pb;
@@ -147,7 +148,6 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     if (n_tri == 0 || n_tri > (1u << 28)) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: n_tri=%u out of range", n_tri);
     if (n_mat == 0) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: n_mat is 0");
     if (bvh_flags & ~(uint32_t)(CR_BVH2 | CR_BVH8Q)) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: bad bvh_flags");
-    if (bvh_flags & CR_BVH8Q) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: CR_BVH8Q is not available in this build");
     for (size_t i = 0; i < 9 * (size_t)n_tri; ++i)
         if (!std::isfinite(tri_xyz[i]))
             return fail(CR_ERR_INVALID_ARG, "cr_scene_create: vertex coordinate %zu of triangle %zu is not finite", i % 9,
@@ -182,6 +182,29 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
         std::memcpy(&o[7], &mat, 4);
         o[11] = 0.0f;
     }
+    HostBVH8 b8;
+    std::vector<float> tris8;
+    if (bvh_flags & CR_BVH8Q) {
+        try {
+            b8 = build_bvh8q(b2);
+        } catch (const std::bad_alloc&) {
+            return fail(CR_ERR_OOM, "cr_scene_create: host allocation during BVH8-Q build");
+        }
+        if (b8.stack_bound > kBvh8StackCapacity)
+            return fail(CR_ERR_STACK_OVERFLOW, "cr_scene_create: BVH8-Q needs a %u-entry stack (> %u)", b8.stack_bound,
+                        kBvh8StackCapacity);
+        tris8.resize(12 * b8.leaf_order.size());
+        for (size_t i = 0; i < b8.leaf_order.size(); ++i) {
+            const uint32_t t = b8.leaf_order[i];
+            float* o = &tris8[12 * i];
+            for (int v = 0; v < 3; ++v)
+                for (int k = 0; k < 3; ++k) o[4 * v + k] = tri_xyz[9 * (size_t)t + 3 * v + k];
+            int32_t orig = (int32_t)t, mat = (int32_t)tri_mat[t];
+            std::memcpy(&o[3], &orig, 4);
+            std::memcpy(&o[7], &mat, 4);
+            o[11] = 0.0f;
+        }
+    }
     std::vector<float> mt(8 * (size_t)n_mat);
     for (uint32_t m = 0; m < n_mat; ++m) {
         int32_t ty = (int32_t)mats[m].type;
@@ -202,10 +225,21 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     CR_CUDA(cudaMemcpy(dn.p, b2.nodes.data(), dn.bytes, cudaMemcpyHostToDevice));
     CR_CUDA(cudaMemcpy(dt.p, tris.data(), dt.bytes, cudaMemcpyHostToDevice));
     CR_CUDA(cudaMemcpy(dm.p, mt.data(), dm.bytes, cudaMemcpyHostToDevice));
+    DevMem dn8, dt8;
+    if (bvh_flags & CR_BVH8Q) {
+        CR_CUDA(dn8.alloc(b8.nodes.size() * sizeof(uint32_t)));
+        CR_CUDA(dt8.alloc(tris8.size() * sizeof(float)));
+        CR_CUDA(cudaMemcpy(dn8.p, b8.nodes.data(), dn8.bytes, cudaMemcpyHostToDevice));
+        CR_CUDA(cudaMemcpy(dt8.p, tris8.data(), dt8.bytes, cudaMemcpyHostToDevice));
+    }
     s->d_nodes2 = dn.p;
     s->d_tris = dt.p;
     s->d_mats = dm.p;
-    dn.p = dt.p = dm.p = nullptr;
+    s->d_nodes8 = dn8.p;
+    s->d_tris8 = dt8.p;
+    dn.p = dt.p = dm.p = dn8.p = dt8.p = nullptr;
+    s->dev.nodes8 = static_cast<const uint4*>(s->d_nodes8);
+    s->dev.tris8 = static_cast<const float4*>(s->d_tris8);
     s->dev.nodes2 = static_cast<const float4*>(s->d_nodes2);
     s->dev.tris = static_cast<const float4*>(s->d_tris);
     s->dev.mats = static_cast<const float4*>(s->d_mats);
@@ -221,7 +255,8 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     s->info.n_mat = n_mat;
     s->info.n_nodes2 = b2.n_nodes;
     s->info.depth2 = b2.depth;
-    s->info.device_bytes = b2.nodes.size() * 4 + tris.size() * 4 + mt.size() * 4;
+    s->info.n_nodes8 = b8.n_nodes;
+    s->info.device_bytes = b2.nodes.size() * 4 + tris.size() * 4 + mt.size() * 4 + b8.nodes.size() * 4 + tris8.size() * 4;
     s->info.build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     for (int k = 0; k < 3; ++k) {
         s->info.bounds_lo[k] = b2.lo[k];
@@ -249,6 +284,7 @@ extern "C" cr_status cr_scene_destroy(cr_scene* s) {
     if (s->d_nodes2) cudaFree(s->d_nodes2);
     if (s->d_nodes8) cudaFree(s->d_nodes8);
     if (s->d_tris) cudaFree(s->d_tris);
+    if (s->d_tris8) cudaFree(s->d_tris8);
     if (s->d_mats) cudaFree(s->d_mats);
     delete s;
     return CR_OK;
@@ -402,7 +438,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     const uint32_t K = o.k ? o.k : m;
     if (!pow2(K) || m % K != 0 || K > 256)
         return fail(CR_ERR_INVALID_ARG, "cr_render: K=%u must be a power of two dividing W*H=%u and <= 256", K, m);
-    if (o.bvh != CR_BVH2 && o.bvh != 0)
+    const bool use8 = o.bvh == CR_BVH8Q;
+    if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8) || (use8 && !s->dev.nodes8))
         return fail(CR_ERR_INVALID_ARG, "cr_render: bvh %u not available for this scene", o.bvh);
     const int block = o.block ? (int)o.block : 128;
     if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "cr_render: block %d", block);
@@ -464,7 +501,9 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     ta.block = block;
     ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
     ta.work_counter = b.counts + 2;
-    const DevScene& ds = s->dev;
+    ta.bvh8 = use8;
+    DevScene ds = s->dev;
+    if (use8) ds.tris = s->dev.tris8; // hits index the BVH8-Q triangle copy
 
     for (uint32_t si = 0; si < spp; ++si) {
         p.frame = o.frame_base + si;
@@ -602,7 +641,11 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     cr_render_opts o;
     cr_render_opts_default(&o);
     if (opts_in) o = *opts_in;
-    if (o.bvh != CR_BVH2 && o.bvh != 0) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: bvh %u not available", o.bvh);
+    const bool use8 = o.bvh == CR_BVH8Q;
+    if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8) || (use8 && !s->dev.nodes8))
+        return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: bvh %u not available", o.bvh);
+    DevScene ds = s->dev;
+    if (use8) ds.tris = s->dev.tris8;
     const int block = o.block ? (int)o.block : 128;
     if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: block %d", block);
     cudaStream_t stream = static_cast<cudaStream_t>(o.stream);
@@ -627,6 +670,7 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     ta.n_max = n;
     ta.block = block;
     ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
+    ta.bvh8 = use8;
     ta.work_counter = wc.as<uint32_t>();
     ta.counters = (o.flags & CR_OPT_COUNT) ? reinterpret_cast<unsigned long long*>(wc.as<uint32_t>() + 4) : nullptr;
     cudaEvent_t e0, e1;
@@ -635,9 +679,9 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
         CR_CUDA(cudaEventCreate(&e1));
         CR_CUDA(cudaEventRecord(e0, stream));
     }
-    launch_trace(s->dev, ta, stream, lc);
+    launch_trace(ds, ta, stream, lc);
     if (o.stats) CR_CUDA(cudaEventRecord(e1, stream));
-    launch_hits_to_user(s->dev, hit.as<int2>(), n, static_cast<int32_t*>(p_out.dev), static_cast<float*>(t_out.dev), stream, lc);
+    launch_hits_to_user(ds, hit.as<int2>(), n, static_cast<int32_t*>(p_out.dev), static_cast<float*>(t_out.dev), stream, lc);
     CR_CUDA(cudaGetLastError());
     CR_CUDA(finish_out(p_out, stream));
     CR_CUDA(finish_out(t_out, stream));
@@ -732,5 +776,34 @@ extern "C" cr_status cr_debug_sample(uint32_t kind, uint32_t n, const float* wo,
     CR_CUDA(finish_out(o2, 0));
     CR_CUDA(finish_out(o3, 0));
     CR_CUDA(cudaStreamSynchronize(0));
+    return CR_OK;
+}
+
+extern "C" cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, uint32_t flags, cr_bvh_report* rep) {
+    g_err.clear();
+    if (!tri_xyz || !rep || n_tri == 0 || n_tri > (1u << 28)) return fail(CR_ERR_INVALID_ARG, "cr_debug_bvh_check: bad arguments");
+    std::memset(rep, 0, sizeof(*rep));
+    try {
+        const auto t0 = std::chrono::steady_clock::now();
+        const unsigned hc = std::thread::hardware_concurrency();
+        HostBVH2 b2 = build_bvh2(tri_xyz, n_tri, hc ? (int)hc : 4);
+        const auto t1 = std::chrono::steady_clock::now();
+        rep->n_nodes2 = b2.n_nodes;
+        rep->depth2 = b2.depth;
+        rep->build_ms2 = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        check_bvh2(b2, tri_xyz, n_tri, rep->covered2, rep->violations2);
+        if (flags & CR_BVH8Q) {
+            const auto t2 = std::chrono::steady_clock::now();
+            HostBVH8 b8 = build_bvh8q(b2);
+            const auto t3 = std::chrono::steady_clock::now();
+            rep->n_nodes8 = b8.n_nodes;
+            rep->depth8 = b8.depth;
+            rep->stack_bound8 = b8.stack_bound;
+            rep->build_ms8 = std::chrono::duration<double, std::milli>(t3 - t2).count();
+            check_bvh8(b8, tri_xyz, n_tri, rep->covered8, rep->violations8);
+        }
+    } catch (const std::bad_alloc&) {
+        return fail(CR_ERR_OOM, "cr_debug_bvh_check: host allocation");
+    }
     return CR_OK;
 }

@@ -32,18 +32,30 @@ struct HostBVH2 {
 // depth 40 so the depth stays <= 64).
 HostBVH2 build_bvh2(const float* tri_xyz, uint32_t n_tri, int n_threads);
 
-// BVH8-Q: 80 B per node (5 x 16 B), after Ylitie et al. 2017:
-//   word0: origin.xyz (float), (ex, ey, ez, imask) bytes
-//   word1: child_base (inner), tri_base, meta[0..3]
-//   word2: meta[4..7], qlo_x[0..7] (8 bytes) , ... packed as in bvh_build.cpp
-// Child boxes are quantised to 8 bits per coordinate on a per-node power-of-two grid,
-// lower bounds rounded down and upper bounds rounded up, so every child box contains the
-// exact one.
+// BVH8-Q: 8-wide nodes of 80 B (five 16-byte words) with 8-bit child boxes, after the
+// compressed wide BVH of Ylitie et al. 2017 (the node format; collapse, slot order and
+// traversal here are our own):
+//   words 0-2  origin.xyz (float)                 word 3  ex | ey << 8 | ez << 16 | imask << 24
+//   word 4     first inner child node             word 5  first triangle (BVH8 leaf order)
+//   words 6-7  meta[8]: inner child: its rank among the inner children; leaf child:
+//              (count << 5) | offset from the first triangle; empty: 0 with imask bit clear
+//   words 8-19 qlo_x[8] qlo_y[8] qlo_z[8] qhi_x[8] qhi_y[8] qhi_z[8]
+// ex/ey/ez are biased float exponents: the grid step of axis a is 2^(e_a - 127).  A child box
+// decodes as origin + q * step in float (one exact product, one rounded add); the builder
+// rounds lower bounds down and upper bounds up and checks the float decode, so every
+// decoded box contains the exact child box.  Children sit in slots by the octant of their
+// centroid, and a ray visits slots in the order k ^ octant(ray direction).
 struct HostBVH8 {
-    std::vector<uint32_t> nodes; // 20 words per node
+    std::vector<uint32_t> nodes;      // 20 words per node
+    std::vector<uint32_t> leaf_order; // BVH8 triangle position -> original triangle index
     uint32_t n_nodes = 0;
+    uint32_t depth = 0;
+    uint32_t stack_bound = 0;         // largest traversal stack a ray can need
 };
 HostBVH8 build_bvh8q(const HostBVH2& b2);
+constexpr uint32_t kBvh8StackCapacity = 128; // traversal stack entries of the BVH8-Q kernel
+void check_bvh2(const HostBVH2& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);
+void check_bvh8(const HostBVH8& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);
 
 // ------------------------------------------------------------------------------------
 // Device-side scene description passed to kernels.
@@ -51,6 +63,7 @@ struct DevScene {
     const float4* nodes2 = nullptr; // 4 per node
     const uint4* nodes8 = nullptr;  // 5 per node
     const float4* tris = nullptr;   // 3 per triangle in leaf order: v0|orig, v1|mat, v2|0
+    const float4* tris8 = nullptr;  // the same records in BVH8-Q leaf order (if built)
     const float4* mats = nullptr;   // 2 per material: (type bits, albedo), (roughness, emission)
     float env[3] = {0, 0, 0};
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -81,6 +94,7 @@ struct TraceArgs {
     unsigned long long* counters = nullptr; // [0] node visits, [1] triangle tests (counting pass)
     uint32_t* work_counter = nullptr;       // persistent mode: atomic ray counter (zeroed)
     int block = 128;
+    uint32_t refill = 0; // persistent mode: refill a warp's idle lanes when at least this many (0 = 8)
     bool persistent = false;
     bool bvh8 = false;
 };

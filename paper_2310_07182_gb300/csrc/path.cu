@@ -581,18 +581,47 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
     hist[threadIdx.x * n_blocks + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, uint32_t len) {
+// Exclusive scan of the digit-major histogram in chunks of kScanChunk entries: each block
+// scans its chunk in place (four contiguous entries per thread, loaded as one uint4) and
+// stores the chunk total; the scatter adds the exclusive prefix of the chunk totals.
+constexpr uint32_t kScanChunk = 4096;
+
+__global__ void __launch_bounds__(1024) k_sort_scan_chunks(uint32_t* __restrict__ hist, uint32_t len,
+                                                            uint32_t* __restrict__ chunk_totals) {
     __shared__ uint32_t s_warp[32];
-    const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
-    const uint32_t b0 = threadIdx.x * per;
-    uint32_t local = 0;
-    for (uint32_t k = 0; k < per && b0 + k < len; ++k) local += hist[b0 + k];
+    const uint32_t base = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (base + 3 < len) {
+        v = *reinterpret_cast<const uint4*>(hist + base);
+    } else {
+        if (base < len) v.x = hist[base];
+        if (base + 1 < len) v.y = hist[base + 1];
+        if (base + 2 < len) v.z = hist[base + 2];
+    }
     uint32_t total;
-    uint32_t run = block_excl_scan(local, s_warp, total);
-    for (uint32_t k = 0; k < per && b0 + k < len; ++k) {
-        const uint32_t v = hist[b0 + k];
-        hist[b0 + k] = run;
-        run += v;
+    const uint32_t ex = block_excl_scan(v.x + v.y + v.z + v.w, s_warp, total);
+    const uint4 o = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+    if (base + 3 < len) {
+        *reinterpret_cast<uint4*>(hist + base) = o;
+    } else {
+        if (base < len) hist[base] = o.x;
+        if (base + 1 < len) hist[base + 1] = o.y;
+        if (base + 2 < len) hist[base + 2] = o.z;
+    }
+    if (threadIdx.x == 0) chunk_totals[blockIdx.x] = total;
+}
+
+// Exclusive scan of the chunk totals in one block, 1024 at a time with a running carry.
+__global__ void __launch_bounds__(1024) k_sort_scan_totals(uint32_t* __restrict__ chunk_totals, uint32_t n) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < n ? chunk_totals[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_excl_scan(v, s_warp, total);
+        if (i < n) chunk_totals[i] = carry + ex;
+        carry += total;
     }
 }
 
@@ -602,12 +631,16 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
                                                                const uint32_t* __restrict__ count, uint32_t n_max,
                                                                uint32_t shift, uint32_t n_blocks,
                                                                const uint32_t* __restrict__ hist,
+                                                               const uint32_t* __restrict__ chunk_prefix,
                                                                uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
     __shared__ uint32_t s_run[256];
     __shared__ uint32_t s_wc[kSortThreads / 32][256];
     const uint32_t n = min(*count, n_max);
     const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    s_run[threadIdx.x] = hist[threadIdx.x * n_blocks + blockIdx.x];
+    {
+        const uint32_t h = threadIdx.x * n_blocks + blockIdx.x;
+        s_run[threadIdx.x] = hist[h] + chunk_prefix[h / kScanChunk];
+    }
     const uint32_t base = blockIdx.x * kSortTile;
     for (uint32_t r = 0; r < kSortItems; ++r) {
         for (uint32_t ww = 0; ww < kSortThreads / 32; ++ww) s_wc[ww][threadIdx.x] = 0;
@@ -832,10 +865,15 @@ const int32_t* launch_morton_sort(const DevScene& s, PathBuffers& b, uint32_t bo
     const uint32_t n_blocks = (n_max + kSortTile - 1) / kSortTile;
     for (uint32_t pass = 0; pass < 4; ++pass) {
         const uint32_t shift = 8 * pass;
+        const uint32_t len = 256 * n_blocks;
+        const uint32_t n_chunks = (len + kScanChunk - 1) / kScanChunk;
+        uint32_t* chunk_totals = b.sort_hist + len;
         k_sort_hist<<<n_blocks, kSortThreads, 0, st>>>(ka, count, n_max, shift, n_blocks, b.sort_hist);
-        k_sort_scan<<<1, 1024, 0, st>>>(b.sort_hist, 256 * n_blocks);
-        k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ka, va, count, n_max, shift, n_blocks, b.sort_hist, kb, vb);
-        lc.n += 3;
+        k_sort_scan_chunks<<<n_chunks, 1024, 0, st>>>(b.sort_hist, len, chunk_totals);
+        k_sort_scan_totals<<<1, 1024, 0, st>>>(chunk_totals, n_chunks);
+        k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ka, va, count, n_max, shift, n_blocks, b.sort_hist,
+                                                          chunk_totals, kb, vb);
+        lc.n += 4;
         uint32_t* tk = ka;
         ka = kb;
         kb = tk;
@@ -846,7 +884,11 @@ const int32_t* launch_morton_sort(const DevScene& s, PathBuffers& b, uint32_t bo
     return va; // after four passes the sorted pairs are back in the first buffers
 }
 
-uint32_t sort_hist_len(uint32_t n_slots) { return 256u * ((n_slots + kSortTile - 1) / kSortTile); }
+// histogram entries plus one chunk total per kScanChunk entries
+uint32_t sort_hist_len(uint32_t n_slots) {
+    const uint32_t len = 256u * ((n_slots + kSortTile - 1) / kSortTile);
+    return len + (len + kScanChunk - 1) / kScanChunk + 4;
+}
 uint32_t compact_blocks(uint32_t n_pos) { return (n_pos + kCompactBlock - 1) / kCompactBlock; }
 
 } // namespace cr

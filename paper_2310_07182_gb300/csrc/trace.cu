@@ -8,7 +8,7 @@
 // distinct banks) and continues in a per-thread local array for deeper trees.  Leaves hold
 // up to four triangles tested with the watertight test of Woop, Benthin and Wald (2013).
 //
-// Closest-hit rule, identical for the BVH2 and BVH8-Q kernels: accept t > 0 if
+// Closest-hit rule, identical for the BVH2 and BVH8-Q kernels (the BVH8-Q kernel is below): accept t > 0 if
 // t < t_best, or t == t_best and the original triangle index is smaller.  Boxes are culled
 // only if their entry distance exceeds t_best (1 + 2^-16) and the slab exit is widened by
 // (1 + 2^-21) > 1 + 2 gamma_3 (Ize 2013), so no box that holds a candidate triangle is ever
@@ -206,30 +206,225 @@ __global__ void k_trace_bvh2(const float4* __restrict__ nodes, const float4* __r
     }
 }
 
-// Persistent variant: a fixed grid of resident blocks; each warp takes 32 rays at a time
-// from an atomic counter until the queue is exhausted.  The loop ends when the counter
-// passes the ray count, which it must since every iteration advances it.
-__global__ void k_trace_bvh2_persistent(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                        const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
-                                        const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
-                                        uint32_t n_max, int2* __restrict__ hit, uint32_t* work) {
+// Persistent variant with dynamic ray fetch: a fixed grid of resident blocks whose warps keep
+// every lane busy.  A lane that finishes its ray takes the next one from its warp's chunk
+// of the queue (the warp grabs kChunk rays at a time with one atomic), once at least
+// `refill` lanes of the warp are idle.  Rays of very different traversal lengths then no
+// longer hold a warp until the slowest one ends.  Each lane advances one leaf at a time, so
+// idle lanes are refilled between leaves.  Every loop iteration either advances a live
+// ray or takes rays from the counter, which only grows, so the loop ends.
+constexpr uint32_t kChunk = 256;
+constexpr int kDone = 0x7fffffff;
+
+__global__ void __launch_bounds__(128) k_trace_bvh2_dynamic(
+    const float4* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ ray_o,
+    const float4* __restrict__ ray_d, const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
+    uint32_t n_max, int2* __restrict__ hit, uint32_t* work, uint32_t refill) {
+    extern __shared__ uint32_t smem_stack[];
+    uint32_t* sstack = smem_stack + threadIdx.x;
+    const int stride = blockDim.x;
+    const uint32_t n = queue_count ? min(*queue_count, n_max) : n_max;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t chunk_next = 0, chunk_end = 0; // warp-uniform
+    bool exhausted = false;                 // warp-uniform
+    bool live = false;
+    RayPre r;
+    int skip = -1, node = kDone, sp = 0, slot = -1;
+    Best best{0.0f, -1, 0x7fffffff};
+    int lstack[kStackTotal - kSmemStack];
+    unsigned long long dummy = 0;
+    while (true) {
+        uint32_t idle = ~__ballot_sync(0xffffffffu, live);
+        if (!exhausted && (uint32_t)__popc(idle) >= refill) {
+            if (chunk_next >= chunk_end) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(work, kChunk);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= n) {
+                    exhausted = true;
+                } else {
+                    chunk_next = base;
+                    chunk_end = min(base + kChunk, n);
+                }
+            }
+            if (!exhausted) {
+                const uint32_t avail = chunk_end - chunk_next;
+                const uint32_t k = (uint32_t)__popc(idle);
+                if (!live) {
+                    const uint32_t rank = __popc(idle & lt_mask);
+                    if (rank < avail) {
+                        const uint32_t i = chunk_next + rank;
+                        slot = queue ? queue[i] : (int)i;
+                        const float4 ro = ray_o[slot];
+                        const float4 rd = ray_d[slot];
+                        if (rd.w >= 0.0f) {
+                            r = prep_ray(ro, rd);
+                            skip = __float_as_int(ro.w);
+                            best = Best{rd.w, -1, 0x7fffffff};
+                            node = 0;
+                            sp = 0;
+                            live = true;
+                        } else {
+                            hit[slot] = make_int2(-1, __float_as_int(INFINITY));
+                        }
+                    }
+                }
+                chunk_next += min(avail, k);
+            }
+            idle = ~__ballot_sync(0xffffffffu, live);
+        }
+        if (idle == 0xffffffffu) {
+            if (exhausted) break;
+            continue;
+        }
+        if (live) {
+            // inner nodes until a leaf is reached or the traversal ends
+            while (node >= 0 && node != kDone) {
+                const float4 n0 = __ldg(&nodes[4 * node + 0]);
+                const float4 n1 = __ldg(&nodes[4 * node + 1]);
+                const float4 n2 = __ldg(&nodes[4 * node + 2]);
+                const float4 n3 = __ldg(&nodes[4 * node + 3]);
+                const float tcull = __fmul_rn(best.t, kCullWiden);
+                const float t0 = box_entry(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
+                const float t1 = box_entry(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
+                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    const int near = first0 ? c0 : c1, far = first0 ? c1 : c0;
+                    if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)far;
+                    else if (sp < kStackTotal) lstack[sp - kSmemStack] = far;
+                    sp = sp < kStackTotal ? sp + 1 : sp; // the builder keeps depth < kStackTotal
+                    node = near;
+                } else if (h0 || h1) {
+                    node = h0 ? c0 : c1;
+                } else if (sp == 0) {
+                    node = kDone;
+                } else {
+                    --sp;
+                    node = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
+                }
+            }
+            if (node != kDone) { // a leaf
+                const uint32_t code = (uint32_t)(~node);
+                test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, dummy);
+                if (sp == 0) {
+                    node = kDone;
+                } else {
+                    --sp;
+                    node = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
+                }
+            }
+            if (node == kDone) {
+                hit[slot] = make_int2(best.leaf, __float_as_int(best.t));
+                live = false;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// BVH8-Q traversal.  Per node: the 80-byte node is fetched with five 16-byte loads, the valid
+// children are decoded (origin + q * step, exact product, one rounded add) and tested with the
+// same conservative slab test as the BVH2 kernel, visiting slots in the order k ^ octant(d)
+// so that near children tend to come first.  Hit children are pushed far to near except the
+// nearest, which is visited next.  Stack entries: inner node index (>= 0) or leaf
+// ~((first triangle << 3) | (count - 1)).  Triangles are the BVH8 copy (same records).
+constexpr int kStack8 = (int)kBvh8StackCapacity; // >= the builder's stack bound (checked at scene creation)
+
+__device__ __forceinline__ uint32_t byte_of(uint32_t lo, uint32_t hi, uint32_t slot) {
+    return ((slot < 4 ? lo : hi) >> (8 * (slot & 3))) & 0xffu;
+}
+
+template <bool kCount>
+__device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, const float4* __restrict__ tris,
+                                               float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
+                                               unsigned long long& n_tri) {
+    const RayPre r = prep_ray(ro, rd);
+    const int skip = __float_as_int(ro.w);
+    const uint32_t oct = (rd.x < 0.0f ? 1u : 0u) | (rd.y < 0.0f ? 2u : 0u) | (rd.z < 0.0f ? 4u : 0u);
+    Best best{rd.w, -1, 0x7fffffff};
+    int lstack[kStack8 - kSmemStack];
+    int sp = 0;
+    int entry = 0;
+    const int stride = blockDim.x;
+    while (true) {
+        if (entry >= 0) {
+            if (kCount) ++n_node;
+            const uint4 w0 = __ldg(&nodes[5 * entry + 0]);
+            const uint4 w1 = __ldg(&nodes[5 * entry + 1]);
+            const uint4 w2 = __ldg(&nodes[5 * entry + 2]);
+            const uint4 w3 = __ldg(&nodes[5 * entry + 3]);
+            const uint4 w4 = __ldg(&nodes[5 * entry + 4]);
+            const float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
+            const float sx = __uint_as_float((w0.w & 0xffu) << 23);
+            const float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
+            const float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
+            const uint32_t imask = w0.w >> 24;
+            const float tcull = __fmul_rn(best.t, kCullWiden);
+            int next = kDone;
+#pragma unroll 1
+            for (int k = 7; k >= 0; --k) {
+                const uint32_t sl = (uint32_t)k ^ oct;
+                const uint32_t m = byte_of(w1.z, w1.w, sl);
+                const bool inner = (imask >> sl) & 1u;
+                if (!inner && m < 32u) continue; // empty slot
+                const float lox = __fadd_rn(ox, __fmul_rn((float)byte_of(w2.x, w2.y, sl), sx));
+                const float loy = __fadd_rn(oy, __fmul_rn((float)byte_of(w2.z, w2.w, sl), sy));
+                const float loz = __fadd_rn(oz, __fmul_rn((float)byte_of(w3.x, w3.y, sl), sz));
+                const float hix = __fadd_rn(ox, __fmul_rn((float)byte_of(w3.z, w3.w, sl), sx));
+                const float hiy = __fadd_rn(oy, __fmul_rn((float)byte_of(w4.x, w4.y, sl), sy));
+                const float hiz = __fadd_rn(oz, __fmul_rn((float)byte_of(w4.z, w4.w, sl), sz));
+                if (box_entry(r, lox, hix, loy, hiy, loz, hiz, tcull) == INFINITY) continue;
+                const int e = inner ? (int)(w1.x + m) : ~(int)(((w1.y + (m & 31u)) << 3) | ((m >> 5) - 1u));
+                if (next != kDone) {
+                    if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)next;
+                    else if (sp < kStack8) lstack[sp - kSmemStack] = next;
+                    sp = sp < kStack8 ? sp + 1 : sp; // scene creation checks the bound
+                }
+                next = e;
+            }
+            if (next != kDone) {
+                entry = next;
+                continue;
+            }
+        } else {
+            const uint32_t code = (uint32_t)(~entry);
+            test_leaf(tris, r, skip, code >> 3, (code & 7u) + 1u, best, n_tri);
+        }
+        if (sp == 0) break;
+        --sp;
+        entry = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
+    }
+    return make_int2(best.leaf, __float_as_int(best.t));
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(128, 8) k_trace_bvh8(const uint4* __restrict__ nodes, const float4* __restrict__ tris,
+                             const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
+                             const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
+                             uint32_t n_max, int2* __restrict__ hit, unsigned long long* counters) {
     extern __shared__ uint32_t smem_stack[];
     const uint32_t n = queue_count ? min(*queue_count, n_max) : n_max;
-    const int lane = threadIdx.x & 31;
-    unsigned long long dn = 0, dt = 0;
-    while (true) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(work, 32u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
-        const uint32_t i = base + lane;
-        if (i < n) {
-            const int slot = queue ? queue[i] : (int)i;
-            const float4 ro = ray_o[slot];
-            const float4 rd = ray_d[slot];
-            int2 h = make_int2(-1, __float_as_int(INFINITY));
-            if (rd.w >= 0.0f) h = trace_bvh2_one<false>(nodes, tris, ro, rd, smem_stack + threadIdx.x, dn, dt);
-            hit[slot] = h;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long n_node = 0, n_tri = 0;
+    if (i < n) {
+        const int slot = queue ? queue[i] : (int)i;
+        const float4 ro = ray_o[slot];
+        const float4 rd = ray_d[slot];
+        int2 h = make_int2(-1, __float_as_int(INFINITY));
+        if (rd.w >= 0.0f) h = trace_bvh8_one<kCount>(nodes, tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+        hit[slot] = h;
+    }
+    if (kCount) {
+        for (int off = 16; off > 0; off >>= 1) {
+            n_node += __shfl_down_sync(0xffffffffu, n_node, off);
+            n_tri += __shfl_down_sync(0xffffffffu, n_tri, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&counters[0], n_node);
+            atomicAdd(&counters[1], n_tri);
         }
     }
 }
@@ -265,15 +460,28 @@ void launch_trace(const DevScene& s, const TraceArgs& a, cudaStream_t st, Launch
     if (a.n_max == 0) return;
     const int block = a.block;
     const size_t smem = (size_t)kSmemStack * block * sizeof(uint32_t);
+    const size_t smem128 = (size_t)kSmemStack * 128 * sizeof(uint32_t);
+    if (a.bvh8) {
+        const uint32_t grid = (a.n_max + block - 1) / block;
+        if (a.counters)
+            k_trace_bvh8<true><<<grid, block, smem, st>>>(s.nodes8, s.tris, a.ray_o, a.ray_d, a.queue, a.queue_count,
+                                                          a.n_max, a.hit, a.counters);
+        else
+            k_trace_bvh8<false><<<grid, block, smem, st>>>(s.nodes8, s.tris, a.ray_o, a.ray_d, a.queue,
+                                                           a.queue_count, a.n_max, a.hit, nullptr);
+        lc.n++;
+        return;
+    }
     if (a.persistent && !a.counters) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bvh2_persistent, block, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bvh2_dynamic, 128, smem128);
         const uint32_t grid_max = (uint32_t)sms * (uint32_t)(per_sm > 0 ? per_sm : 1);
-        const uint32_t need = (a.n_max + block - 1) / block;
-        k_trace_bvh2_persistent<<<need < grid_max ? need : grid_max, block, smem, st>>>(
-            s.nodes2, s.tris, a.ray_o, a.ray_d, a.queue, a.queue_count, a.n_max, a.hit, a.work_counter);
+        const uint32_t need = (a.n_max + 127) / 128;
+        k_trace_bvh2_dynamic<<<need < grid_max ? need : grid_max, 128, smem128, st>>>(
+            s.nodes2, s.tris, a.ray_o, a.ray_d, a.queue, a.queue_count, a.n_max, a.hit, a.work_counter,
+            a.refill == 0 ? 8u : (a.refill > 32u ? 32u : a.refill));
     } else {
         const uint32_t grid = (a.n_max + block - 1) / block;
         if (a.counters)

@@ -179,3 +179,17 @@ def test_landscape_full_size_sampled_tiles(cr, orc, mode):
         assert ok.sum() >= 0.85 * mask.sum()
         good, excess, nbad = radiance_close(img, ref["rgb"], ok)
         assert good, f"band {b0}: {nbad} pixels off by {excess}"
+
+
+def test_bvh8q_render_identical(cr, orc):
+    """The precision variant: the interior scene rendered through the BVH8-Q gives the same
+    image bit for bit as through the FP32 BVH2, and matches the oracle."""
+    sc = scenes.interior(width=160, height=96)
+    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
+    kw = dict(spp=4, max_bounces=4, mode="direction_reuse", tile=(8, 8), k=8, seed=11)
+    a, sa = S.render(bvh=cr.CR_BVH2, stats=True, **kw)
+    b, sb = S.render(bvh=cr.CR_BVH8Q, stats=True, **kw)
+    assert torch.equal(a, b)
+    assert sa["secondary_rays"] == sb["secondary_rays"]
+    ref = orc.render(orc.Scene(sc), sc.camera, **kw)
+    _check(b.cpu().numpy(), ref, max_taint=0.1)
