@@ -311,6 +311,10 @@ def run_ours(args):
         extras["precision_interior"] = precision_leg(cr, scenes, rank, world, args)
         extras["table3_sweep"] = sweep_leg(cr, S, cam, out, stream, rank, world)
         extras["quality"] = quality_leg(cr, S, cam, stream, results)
+        if not args.no_batched:
+            extras["batched"] = batched_leg(cr, scenes, rank, args)
+        if not args.no_serving and rank == 0:
+            extras["serving"] = serving_leg(cr, scenes, args)
 
     if rank != 0:
         return
@@ -467,6 +471,137 @@ def quality_leg(cr, S, cam, stream, results):
     return out
 
 
+def batched_leg(cr, scenes, rank, args):
+    """64 jobs (sides uniform over 256..1024 in steps of 256, over the terrain, the interior and
+    random soups of 1M and 4M triangles), 4 spp, 3 bounces, direction reuse: one wavefront per
+    sample pass, CUDA-graph replay, tile shape / K / interleave / block from the autotuner.
+    Compared with rendering the same jobs one at a time and with the untuned default."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(21)
+    world = {"terrain": scenes.landscape(), "interior": scenes.interior(), "soup1m": scenes.soup(31, 1_000_000),
+             "soup4m": scenes.soup(32, 4_000_000)}
+    S = {k: cr.Scene(v) for k, v in world.items()}
+    names = list(world)
+    specs = []
+    for i in range(64):
+        side = int(rng.choice([256, 512, 768, 1024]))
+        specs.append((names[int(rng.integers(0, 4))], side, int(rng.integers(0, 1 << 30))))
+    outs = [torch.empty((sd, sd, 3), dtype=torch.float32, device="cuda") for _, sd, _ in specs]
+
+    def jobs_for(spp):
+        js = []
+        for (name, sd, seed), o in zip(specs, outs):
+            c = world[name].camera
+            cam = scenes.Camera(c.pos, c.look_at, c.up, c.vfov_deg, sd, sd)
+            js.append(cr.make_job(S[name].handle, cam, o, spp=spp, max_bounces=3, mode="direction_reuse", seed=seed,
+                                  frame_base=rank * 1000))
+        return js
+
+    jobs = jobs_for(4)
+    opts = cr.make_batch_opts(tile=(8, 8), k=8)
+    t0 = time.perf_counter()
+    rep = cr.cr_batch_autotune(jobs_for(1), opts, allow_contiguous=True)
+    tune_s = time.perf_counter() - t0
+    res = {"workload": "64 jobs, sides {256,512,768,1024}^2, scenes {terrain 2.1M, interior 0.5M, soup 1M, soup 4M}, "
+                       "4 spp, 3 bounces, direction_reuse",
+           "pixels": int(sum(sd * sd for _, sd, _ in specs)),
+           "autotune": {"seconds": round(tune_s, 1), "candidates": rep["n_candidates"],
+                        "best": f"{opts.group_w}x{opts.group_h} K={opts.k} interleave={'lcg' if opts.interleave else 'contiguous'} block={opts.block}",
+                        "best_ms_spp1": round(rep["best_ms"], 3), "default_ms_spp1": round(rep["default_ms"], 3)}}
+    variants = {"graph_autotuned": (opts, cr.CR_BATCH_GRAPH),
+                "graph_default": (cr.make_batch_opts(tile=(8, 8), k=8), cr.CR_BATCH_GRAPH),
+                "direct_autotuned": (opts, 0)}
+    for name, (o, flags) in variants.items():
+        oo = cr.make_batch_opts(tile=(o.group_w, o.group_h), k=o.k, interleave=bool(o.interleave), block=o.block,
+                                flags=flags)
+        b = cr.cr_batch_create(jobs, oo)
+        cr.cr_batch_run(b)
+        ms, sec, launches = [], 0, 0
+        for _ in range(3):
+            st = cr.cr_batch_run(b)
+            ms.append(st["ms_total"])
+            sec += st["secondary_rays"]
+            launches = st["kernel_launches"]
+        cr.cr_batch_destroy(b)
+        res[name] = {"ms_per_batch": round(sum(ms) / 3, 2), "mrays": round(sec / sum(ms) / 1e3, 1),
+                     "launches_per_batch": launches}
+    # the same jobs rendered one at a time (one job per wavefront, no graph)
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sec = 0
+    ev0.record()
+    for (name, sd, seed), o in zip(specs, outs):
+        c = world[name].camera
+        cam = scenes.Camera(c.pos, c.look_at, c.up, c.vfov_deg, sd, sd)
+        st = cr.cr_stats()
+        cr.cr_render_ex(S[name].handle, cam, 4, 3, "direction_reuse", opts.group_w, opts.group_h, o,
+                        cr.make_opts(k=opts.k, interleave=bool(opts.interleave), block=opts.block, seed=seed,
+                                     frame_base=rank * 1000, stream=stream, stats=st))
+        sec += st.secondary_rays
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    res["one_at_a_time"] = {"ms_per_batch": round(ms, 2), "mrays": round(sec / ms / 1e3, 1)}
+    for v in S.values():
+        v.close()
+    return res
+
+
+def serving_leg(cr, scenes, args):
+    """Poisson arrivals against six resident scenes (tiny, soups 1M/4M, interior, landscape,
+    terrain 2236^2 = 9,990,450 triangles), sides log-uniform in [128, 2048] (multiples of
+    16), spp in {1,4,16,64}, 1-4 bounces, host outputs; p50/p99 latency from submission to
+    the result on the host, and throughput, for direction reuse + BVH8-Q and for
+    independent sampling + BVH2."""
+    import numpy as np
+    world = {"tiny": scenes.tiny(), "soup1m": scenes.soup(31, 1_000_000), "soup4m": scenes.soup(32, 4_000_000),
+             "interior": scenes.interior(), "landscape": scenes.landscape(), "terrain": scenes.terrain()}
+    S = {k: cr.Scene(v, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q) for k, v in world.items()}
+    names = list(world)
+    out = {"window_s": args.serve_window, "rates": list(args.serve_rates), "configs": {}}
+    for cfg, mode, bvh in (("reuse_bvh8q", "direction_reuse", cr.CR_BVH8Q), ("independent_bvh2", "independent", cr.CR_BVH2)):
+        rows = {}
+        for lam in args.serve_rates:
+            rng = np.random.default_rng(41 + int(lam))
+            srv = cr.cr_server_create(48 << 30, tile=(8, 8), k=8, bvh=bvh)
+            t_next = 0.0
+            arrivals = []
+            while True:
+                t_next += rng.exponential(1.0 / lam)
+                if t_next > args.serve_window:
+                    break
+                arrivals.append(t_next)
+            reqs = []
+            t0 = time.perf_counter()
+            for ta in arrivals:
+                side = int(round(math.exp(rng.uniform(math.log(128), math.log(2048))) / 16) * 16)
+                name = names[int(rng.integers(0, 6))]
+                spp = int(rng.choice([1, 4, 16, 64]))
+                B = int(rng.integers(1, 5))
+                c = world[name].camera
+                cam = scenes.Camera(c.pos, c.look_at, c.up, c.vfov_deg, side, side)
+                host = np.empty((side, side, 3), np.float32)
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                jid = cr.cr_server_submit(srv, cr.make_job(S[name].handle, cam, host, spp=spp, max_bounces=B,
+                                                           mode=mode, seed=int(rng.integers(0, 1 << 30))))
+                reqs.append((jid, host))
+            lat = [cr.cr_server_wait(srv, jid, 600000)["latency_ms"] for jid, _ in reqs]
+            wall = time.perf_counter() - t0
+            st = cr.cr_server_get_stats(srv)
+            cr.cr_server_destroy(srv)
+            rows[str(lam)] = {"requests": len(reqs), "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                              "p99_ms": round(float(np.percentile(lat, 99)), 1), "wall_s": round(wall, 2),
+                              "mrays": round(st["secondary_rays"] / wall / 1e6, 1), "passes": st["passes"]}
+        out["configs"][cfg] = rows
+    for v in S.values():
+        v.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,7 +610,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--core-only", action="store_true", help="skip the precision, sweep and quality legs")
+    ap.add_argument("--core-only", action="store_true", help="skip the precision, sweep, quality, batched and serving legs")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-window", type=float, default=1.5, help="seconds of Poisson arrivals per rate")
+    ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[20.0, 50.0, 100.0, 200.0])
     ap.add_argument("--modes", default="direction_reuse,independent,morton_sort",
                     help="modes to time (the first is the headline); profiling runs use one")
     args = ap.parse_args()

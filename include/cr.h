@@ -187,6 +187,105 @@ cr_status cr_render_ex(cr_scene* scene, const cr_camera* camera, uint32_t spp, u
                        const cr_render_opts* opts);
 
 /* ---------------------------------------------------------------------------------- */
+/* Batched rendering: many jobs (scenes, cameras, spp, bounces, modes) merged into one
+ * wavefront, one launch per stage per bounce over the slots of all jobs, optionally replayed
+ * from a CUDA graph.  Jobs of one batch share the tile shape, K, interleave and BVH layout. */
+typedef struct {
+    cr_scene* scene;     /* must outlive the batch */
+    cr_camera camera;
+    uint32_t spp;        /* >= 1 */
+    uint32_t max_bounces;/* 1..16 */
+    uint32_t mode;       /* cr_reuse_mode */
+    uint32_t reuse_depth;/* 0 = every bounce */
+    uint64_t seed;
+    uint32_t frame_base;
+    uint32_t pad;
+    float* out_rgb;      /* DEVICE buffer of width*height*3 floats */
+} cr_job;                /* 96 bytes */
+
+enum { CR_BATCH_GRAPH = 1u /* capture the launch sequence once, replay it on every run */ };
+
+typedef struct {
+    uint32_t group_w, group_h; /* tile W x H */
+    uint32_t k;                /* 0 = W*H */
+    uint32_t interleave;       /* 1 LCG (Sec. 3.3), 0 contiguous */
+    uint32_t bvh;              /* CR_BVH2 or CR_BVH8Q (every scene must have it) */
+    uint32_t block;            /* trace block size; 0 = 128 */
+    uint32_t flags;            /* CR_BATCH_GRAPH | CR_OPT_PERSISTENT */
+    uint32_t pad;
+    void* stream;              /* cudaStream_t used by cr_batch_run (NULL = a stream the batch owns) */
+} cr_batch_opts;
+
+typedef struct cr_batch cr_batch;
+
+/* Plan a batch: checks every job, builds the per-sample-pass job tables, allocates the path
+ * state for the largest pass (see cr_batch_device_bytes) and, with CR_BATCH_GRAPH, captures
+ * the whole launch sequence into a CUDA graph.  jobs is copied; scenes and outputs are not.
+ * Errors: CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA. */
+cr_status cr_batch_create(const cr_job* jobs, uint32_t n_jobs, const cr_batch_opts* opts, cr_batch** out);
+/* Render every job of the batch once (each job's spp samples) into its out_rgb and wait.
+ * stats (may be NULL): ms_total (CUDA events around the run), secondary rays, launches. */
+cr_status cr_batch_run(cr_batch* batch, cr_stats* stats);
+cr_status cr_batch_destroy(cr_batch* batch);
+/* Path-state bytes a batch of these jobs would allocate (admission by device footprint). */
+cr_status cr_batch_device_bytes(const cr_job* jobs, uint32_t n_jobs, const cr_batch_opts* opts, uint64_t* bytes);
+
+/* Autotuner: times candidate (W,H) in {4x4, 8x8, 16x16}, K <= W*H/4 (larger K loses image
+ * quality, Sec. 5.3), interleave {LCG, contiguous} if allowed, and trace block {64, 128,
+ * 256} on the given jobs (renders them), and writes the fastest into *opts (its bvh and flags
+ * are kept).  allow_contiguous = 0 keeps the LCG interleave of Sec. 3.3. */
+typedef struct {
+    uint32_t n_candidates;
+    uint32_t best_group_w, best_group_h, best_k, best_interleave, best_block;
+    double best_ms;   /* device ms of one run of the best candidate */
+    double worst_ms;  /* slowest candidate */
+    double default_ms;/* 8x8, K=8, LCG, block 128 */
+} cr_tune_report;
+
+cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint32_t allow_contiguous, cr_batch_opts* opts,
+                            cr_tune_report* report);
+
+/* ---------------------------------------------------------------------------------- */
+/* Serving: a request loop with continuous batching.  A server thread renders one sample
+ * pass of every admitted job at a time, all jobs merged into one wavefront; between passes
+ * finished jobs are written out and queued jobs are admitted while their device footprint
+ * (accumulation 16 B/px + output staging 12 B/px for host outputs + path state ~130 B per
+ * slot) fits hbm_budget, so requests that arrive while others run join the next pass.
+ * Results equal stand-alone renders with the same tile shape, K and interleave. */
+typedef struct {
+    uint64_t hbm_budget;       /* bytes of device memory the server may use (>= 64 MiB) */
+    uint32_t group_w, group_h, k, interleave, bvh, block; /* as cr_batch_opts */
+} cr_server_opts;
+
+typedef struct {
+    double t_submit_ms, t_admit_ms, t_done_ms; /* server clock (ms since cr_server_create) */
+    double latency_ms;                         /* t_done - t_submit: result available on the host */
+    uint32_t samples, pad;
+    uint64_t footprint_bytes;
+} cr_job_stats;
+
+typedef struct {
+    uint64_t jobs_submitted, jobs_done, passes, secondary_rays, kernel_launches, used_bytes;
+    double busy_ms;            /* wall time of the passes (device work + output copies) */
+    uint32_t queued, active;
+} cr_server_stats;
+
+typedef struct cr_server cr_server;
+
+cr_status cr_server_create(const cr_server_opts* opts, cr_server** out);
+/* Queue a job (copied).  out_rgb may be host or device memory and must stay valid until the
+ * job completes.  Errors: CR_ERR_INVALID_ARG, CR_ERR_OOM (larger than the whole budget). */
+cr_status cr_server_submit(cr_server* server, const cr_job* job, uint64_t* job_id);
+/* CR_OK once the job's output is written (then the id is forgotten), CR_ERR_BUSY while it is
+ * queued or rendering, CR_ERR_NOT_FOUND for unknown ids, or the job's error. */
+cr_status cr_server_poll(cr_server* server, uint64_t job_id, cr_job_stats* stats);
+/* As poll, but waits up to timeout_ms; CR_ERR_TIMEOUT if the job is still running. */
+cr_status cr_server_wait(cr_server* server, uint64_t job_id, uint32_t timeout_ms, cr_job_stats* stats);
+cr_status cr_server_get_stats(cr_server* server, cr_server_stats* stats);
+/* Stop the loop (jobs still queued are dropped) and free the server's memory. */
+cr_status cr_server_destroy(cr_server* server);
+
+/* ---------------------------------------------------------------------------------- */
 /* Parity / debug entry points (the same kernels as the render path). */
 
 /* Closest hit of n rays (Sec. 1: the intersection step).

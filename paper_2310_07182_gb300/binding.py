@@ -78,6 +78,41 @@ class cr_debug(C.Structure):
                 ("local", C.c_void_p), ("world", C.c_void_p)]
 
 
+class cr_job(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("camera", cr_camera), ("spp", C.c_uint32), ("max_bounces", C.c_uint32),
+                ("mode", C.c_uint32), ("reuse_depth", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
+                ("pad", C.c_uint32), ("out_rgb", C.c_void_p)]
+
+
+class cr_batch_opts(C.Structure):
+    _fields_ = [("group_w", C.c_uint32), ("group_h", C.c_uint32), ("k", C.c_uint32), ("interleave", C.c_uint32),
+                ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32), ("pad", C.c_uint32),
+                ("stream", C.c_void_p)]
+
+
+class cr_tune_report(C.Structure):
+    _fields_ = [("n_candidates", C.c_uint32), ("best_group_w", C.c_uint32), ("best_group_h", C.c_uint32),
+                ("best_k", C.c_uint32), ("best_interleave", C.c_uint32), ("best_block", C.c_uint32),
+                ("best_ms", C.c_double), ("worst_ms", C.c_double), ("default_ms", C.c_double)]
+
+
+class cr_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_uint64), ("group_w", C.c_uint32), ("group_h", C.c_uint32), ("k", C.c_uint32),
+                ("interleave", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32)]
+
+
+class cr_job_stats(C.Structure):
+    _fields_ = [("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double),
+                ("latency_ms", C.c_double), ("samples", C.c_uint32), ("pad", C.c_uint32),
+                ("footprint_bytes", C.c_uint64)]
+
+
+class cr_server_stats(C.Structure):
+    _fields_ = [("jobs_submitted", C.c_uint64), ("jobs_done", C.c_uint64), ("passes", C.c_uint64),
+                ("secondary_rays", C.c_uint64), ("kernel_launches", C.c_uint64), ("used_bytes", C.c_uint64),
+                ("busy_ms", C.c_double), ("queued", C.c_uint32), ("active", C.c_uint32)]
+
+
 class cr_render_opts(C.Structure):
     _fields_ = [("k", C.c_uint32), ("interleave", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
                 ("reuse_depth", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32),
@@ -107,6 +142,18 @@ _SIGS = [
     ("cr_debug_philox", C.c_int, [C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p]),
     ("cr_debug_sample", C.c_int, [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    ("cr_batch_create", C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(cr_batch_opts), C.POINTER(C.c_void_p)]),
+    ("cr_batch_run", C.c_int, [C.c_void_p, C.POINTER(cr_stats)]),
+    ("cr_batch_destroy", C.c_int, [C.c_void_p]),
+    ("cr_batch_device_bytes", C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(cr_batch_opts), C.POINTER(C.c_uint64)]),
+    ("cr_batch_autotune", C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(cr_batch_opts),
+                                    C.POINTER(cr_tune_report)]),
+    ("cr_server_create", C.c_int, [C.POINTER(cr_server_opts), C.POINTER(C.c_void_p)]),
+    ("cr_server_submit", C.c_int, [C.c_void_p, C.POINTER(cr_job), C.POINTER(C.c_uint64)]),
+    ("cr_server_poll", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(cr_job_stats)]),
+    ("cr_server_wait", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(cr_job_stats)]),
+    ("cr_server_get_stats", C.c_int, [C.c_void_p, C.POINTER(cr_server_stats)]),
+    ("cr_server_destroy", C.c_int, [C.c_void_p]),
     ("cr_debug_bvh_check", C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(cr_bvh_report)]),
     ("cr_trace_rays_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
@@ -240,6 +287,103 @@ def cr_trace_rays(handle, rays, skip, prim, t, opts: cr_render_opts | None = Non
         opts.stream = _current_stream([rays, prim, t])
     _check(lib().cr_trace_rays(handle, _ptr(rays), _ptr(skip), n, _ptr(prim), _ptr(t),
                                C.byref(opts) if opts is not None else None))
+
+
+CR_BATCH_GRAPH = 1
+
+
+def make_job(scene_handle, cam, out, spp=1, max_bounces=1, mode="direction_reuse", reuse_depth=0, seed=0,
+             frame_base=0) -> cr_job:
+    j = cr_job()
+    j.scene = scene_handle
+    j.camera = make_camera(cam)
+    j.spp, j.max_bounces, j.mode, j.reuse_depth = spp, max_bounces, MODES.get(mode, mode), reuse_depth
+    j.seed, j.frame_base = seed, frame_base
+    j.out_rgb = _ptr(out)
+    return j
+
+
+def make_batch_opts(tile=(8, 8), k=0, interleave=True, bvh=CR_BVH2, block=0, flags=0, stream=None) -> cr_batch_opts:
+    o = cr_batch_opts()
+    o.group_w, o.group_h, o.k, o.interleave = tile[0], tile[1], k, int(interleave)
+    o.bvh, o.block, o.flags = bvh, block, flags
+    o.stream = stream
+    return o
+
+
+def _job_array(jobs):
+    arr = (cr_job * len(jobs))(*jobs)
+    return arr
+
+
+def cr_batch_create(jobs, opts: cr_batch_opts):
+    arr = _job_array(jobs)
+    out = C.c_void_p()
+    _check(lib().cr_batch_create(C.addressof(arr), len(jobs), C.byref(opts), C.byref(out)))
+    return out.value
+
+
+def cr_batch_run(handle, stats=True):
+    st = cr_stats() if stats else None
+    _check(lib().cr_batch_run(handle, C.byref(st) if st is not None else None))
+    return st.as_dict() if st is not None else None
+
+
+def cr_batch_destroy(handle):
+    _check(lib().cr_batch_destroy(handle))
+
+
+def cr_batch_device_bytes(jobs, opts: cr_batch_opts) -> int:
+    arr = _job_array(jobs)
+    v = C.c_uint64()
+    _check(lib().cr_batch_device_bytes(C.addressof(arr), len(jobs), C.byref(opts), C.byref(v)))
+    return v.value
+
+
+def cr_batch_autotune(jobs, opts: cr_batch_opts, allow_contiguous=False) -> dict:
+    arr = _job_array(jobs)
+    rep = cr_tune_report()
+    _check(lib().cr_batch_autotune(C.addressof(arr), len(jobs), int(allow_contiguous), C.byref(opts), C.byref(rep)))
+    return {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+def cr_server_create(hbm_budget, tile=(8, 8), k=0, interleave=True, bvh=CR_BVH2, block=0):
+    o = cr_server_opts(int(hbm_budget), tile[0], tile[1], k, int(interleave), bvh, block)
+    out = C.c_void_p()
+    _check(lib().cr_server_create(C.byref(o), C.byref(out)))
+    return out.value
+
+
+def cr_server_submit(handle, job: cr_job) -> int:
+    jid = C.c_uint64()
+    _check(lib().cr_server_submit(handle, C.byref(job), C.byref(jid)))
+    return jid.value
+
+
+def cr_server_poll(handle, job_id):
+    """Returns the job's stats dict once done, None while it is queued or rendering."""
+    js = cr_job_stats()
+    st = lib().cr_server_poll(handle, job_id, C.byref(js))
+    if st == CR_ERR_BUSY:
+        return None
+    _check(st)
+    return {k: getattr(js, k) for k, _ in js._fields_}
+
+
+def cr_server_wait(handle, job_id, timeout_ms=60000):
+    js = cr_job_stats()
+    _check(lib().cr_server_wait(handle, job_id, timeout_ms, C.byref(js)))
+    return {k: getattr(js, k) for k, _ in js._fields_}
+
+
+def cr_server_get_stats(handle) -> dict:
+    st = cr_server_stats()
+    _check(lib().cr_server_get_stats(handle, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def cr_server_destroy(handle):
+    _check(lib().cr_server_destroy(handle))
 
 
 def cr_debug_bvh_check(tri_xyz, flags=CR_BVH2 | CR_BVH8Q) -> dict:

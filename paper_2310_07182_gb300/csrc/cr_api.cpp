@@ -120,10 +120,10 @@ struct cr_scene {
     void* d_tris = nullptr;
     void* d_tris8 = nullptr;
     void* d_mats = nullptr;
-    // render workspace, grown on demand
-    cr::PathBuffers pb;
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
+    cr::SceneDev* d_entries = nullptr; // [0] BVH2 layout, [1] BVH8-Q layout (scene-table entries)
+    // render workspace and job tables, grown on demand
+    cr::Workspace ws;
+    cr::Plan plan_dev;
     float* d_out = nullptr;
     size_t out_cap = 0;
 };
@@ -133,6 +133,8 @@ using namespace cr;
 namespace cr {
 void set_last_error(const char* msg) { g_err = msg; }
 const DevScene* dev_scene_of(const cr_scene* s) { return &s->dev; }
+const SceneDev* dev_scene_entry(const cr_scene* s, bool bvh8) { return s->d_entries + (bvh8 ? 1 : 0); }
+bool scene_has_bvh8(const cr_scene* s) { return s->dev.nodes8 != nullptr; }
 } // namespace cr
 
 extern "C" const char* cr_last_error(void) { return g_err.c_str(); }
@@ -250,6 +252,14 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     }
     s->dev.n_tri = n_tri;
     s->dev.n_mat = n_mat;
+    {
+        SceneDev ent[2] = {scene_entry(s->dev, false), scene_entry(s->dev, s->dev.nodes8 != nullptr)};
+        DevMem de;
+        CR_CUDA(de.alloc(sizeof(ent)));
+        CR_CUDA(cudaMemcpy(de.p, ent, sizeof(ent), cudaMemcpyHostToDevice));
+        s->d_entries = static_cast<SceneDev*>(de.p);
+        de.p = nullptr;
+    }
     std::memset(&s->info, 0, sizeof(s->info));
     s->info.n_tri = n_tri;
     s->info.n_mat = n_mat;
@@ -267,10 +277,8 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
 }
 
 static void free_workspace(cr_scene* s) {
-    if (s->ws) cudaFree(s->ws);
-    s->ws = nullptr;
-    s->ws_bytes = 0;
-    s->pb = PathBuffers();
+    s->ws.release();
+    s->plan_dev.release();
     if (s->d_out) cudaFree(s->d_out);
     s->d_out = nullptr;
     s->out_cap = 0;
@@ -286,6 +294,7 @@ extern "C" cr_status cr_scene_destroy(cr_scene* s) {
     if (s->d_tris) cudaFree(s->d_tris);
     if (s->d_tris8) cudaFree(s->d_tris8);
     if (s->d_mats) cudaFree(s->d_mats);
+    if (s->d_entries) cudaFree(s->d_entries);
     delete s;
     return CR_OK;
 }
@@ -303,60 +312,6 @@ extern "C" cr_status cr_render_opts_default(cr_render_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->interleave = 1;
     o->bvh = CR_BVH2;
-    return CR_OK;
-}
-
-// Carve the render workspace for n_slots slots and npx pixels out of one allocation.
-static cr_status ensure_workspace(cr_scene* s, uint32_t n_slots, uint32_t npx) {
-    PathBuffers& b = s->pb;
-    if (b.n_slots >= n_slots && b.n_px_cap >= npx && s->ws) {
-        return CR_OK;
-    }
-    cudaDeviceSynchronize();
-    free_workspace(s);
-    const size_t ns = n_slots, np = npx;
-    const size_t n_cblocks = compact_blocks(n_slots) + 1;
-    const size_t n_hist = sort_hist_len(n_slots);
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        size_t o = off;
-        off += (bytes + 255) & ~(size_t)255;
-        return o;
-    };
-    const size_t o_pixel = take(4 * ns), o_ro = take(16 * ns), o_rd = take(16 * ns), o_hit = take(8 * ns),
-                 o_beta = take(16 * ns), o_rad = take(16 * ns), o_alive = take(ns), o_rq = take(4 * ns),
-                 o_gq = take(2 * 4 * ns), o_counts = take(4 * kCountsWords), o_bc = take(2 * 4 * n_cblocks),
-                 o_keys = take(2 * 4 * ns), o_vals = take(2 * 4 * ns), o_hist = take(4 * n_hist),
-                 o_acc = take(16 * np);
-    void* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, off);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CR_ERR_OOM, "render workspace of %zu bytes: %s", off, cudaGetErrorString(e));
-    }
-    char* c = static_cast<char*>(base);
-    s->ws = base;
-    s->ws_bytes = off;
-    b.n_slots = n_slots;
-    b.n_px_cap = npx;
-    b.pixel = reinterpret_cast<int32_t*>(c + o_pixel);
-    b.ray_o = reinterpret_cast<float4*>(c + o_ro);
-    b.ray_d = reinterpret_cast<float4*>(c + o_rd);
-    b.hit = reinterpret_cast<int2*>(c + o_hit);
-    b.beta = reinterpret_cast<float4*>(c + o_beta);
-    b.radiance = reinterpret_cast<float4*>(c + o_rad);
-    b.alive = reinterpret_cast<uint8_t*>(c + o_alive);
-    b.ray_queue = reinterpret_cast<int32_t*>(c + o_rq);
-    b.group_queue = reinterpret_cast<int32_t*>(c + o_gq);
-    b.counts = reinterpret_cast<uint32_t*>(c + o_counts);
-    b.block_counts = reinterpret_cast<uint32_t*>(c + o_bc);
-    b.n_blocks_cap = (uint32_t)n_cblocks;
-    b.keys = reinterpret_cast<uint32_t*>(c + o_keys);
-    b.vals = reinterpret_cast<int32_t*>(c + o_vals);
-    b.sort_hist = reinterpret_cast<uint32_t*>(c + o_hist);
-    b.sort_hist_cap = (uint32_t)n_hist;
-    b.accum = reinterpret_cast<float4*>(c + o_acc);
-    b.counters = reinterpret_cast<unsigned long long*>(b.counts + kCounterWord);
     return CR_OK;
 }
 
@@ -417,27 +372,300 @@ struct StageEvents {
     }
 };
 
+namespace cr {
+
+void Workspace::release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    bytes = 0;
+    pb = PathBuffers();
+}
+
+// Carve the path state for n_slots slots and npx accumulation pixels out of one allocation.
+cr_status Workspace::ensure(uint32_t n_slots, uint32_t npx) {
+    if (base && pb.n_slots >= n_slots && pb.n_px_cap >= npx) return CR_OK;
+    cudaDeviceSynchronize();
+    release();
+    const size_t ns = n_slots, np = npx;
+    const size_t n_cblocks = compact_blocks(n_slots) + 1;
+    const size_t n_hist = sort_hist_len(n_slots);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += (b + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_pixel = take(4 * ns), o_job = take(2 * ns), o_scene = take(2 * ns), o_ro = take(16 * ns),
+                 o_rd = take(16 * ns), o_hit = take(8 * ns), o_beta = take(16 * ns), o_rad = take(16 * ns),
+                 o_alive = take(ns), o_rq = take(4 * ns), o_gq = take(2 * 4 * ns), o_counts = take(4 * kCountsWords),
+                 o_bc = take(2 * 4 * n_cblocks), o_keys = take(2 * 4 * ns), o_vals = take(2 * 4 * ns),
+                 o_hist = take(4 * n_hist), o_acc = take(16 * np);
+    cudaError_t e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        base = nullptr;
+        return fail(CR_ERR_OOM, "render workspace of %zu bytes: %s", off, cudaGetErrorString(e));
+    }
+    char* c = static_cast<char*>(base);
+    bytes = off;
+    pb.n_slots = n_slots;
+    pb.n_px_cap = npx;
+    pb.pixel = reinterpret_cast<int32_t*>(c + o_pixel);
+    pb.slot_job = reinterpret_cast<uint16_t*>(c + o_job);
+    pb.slot_scene = reinterpret_cast<uint16_t*>(c + o_scene);
+    pb.ray_o = reinterpret_cast<float4*>(c + o_ro);
+    pb.ray_d = reinterpret_cast<float4*>(c + o_rd);
+    pb.hit = reinterpret_cast<int2*>(c + o_hit);
+    pb.beta = reinterpret_cast<float4*>(c + o_beta);
+    pb.radiance = reinterpret_cast<float4*>(c + o_rad);
+    pb.alive = reinterpret_cast<uint8_t*>(c + o_alive);
+    pb.ray_queue = reinterpret_cast<int32_t*>(c + o_rq);
+    pb.group_queue = reinterpret_cast<int32_t*>(c + o_gq);
+    pb.counts = reinterpret_cast<uint32_t*>(c + o_counts);
+    pb.block_counts = reinterpret_cast<uint32_t*>(c + o_bc);
+    pb.n_blocks_cap = (uint32_t)n_cblocks;
+    pb.keys = reinterpret_cast<uint32_t*>(c + o_keys);
+    pb.vals = reinterpret_cast<int32_t*>(c + o_vals);
+    pb.sort_hist = reinterpret_cast<uint32_t*>(c + o_hist);
+    pb.sort_hist_cap = (uint32_t)n_hist;
+    pb.accum = reinterpret_cast<float4*>(c + o_acc);
+    pb.counters = reinterpret_cast<unsigned long long*>(pb.counts + kCounterWord);
+    return CR_OK;
+}
+
+// Device bytes of path state for n_slots slots and npx pixels (what Workspace::ensure takes).
+size_t workspace_bytes(uint32_t n_slots, uint32_t npx) {
+    const size_t ns = n_slots;
+    return ns * (4 + 2 + 2 + 16 + 16 + 8 + 16 + 16 + 1 + 4 + 8 + 8 + 8) + 16ull * npx +
+           4ull * sort_hist_len(n_slots) + 8ull * (compact_blocks(n_slots) + 1) + 4 * kCountsWords + 17 * 256;
+}
+
+// Check one job and fill the part of its device entry that does not depend on the pass.
+cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h) {
+    if (!j.scene) return fail(CR_ERR_INVALID_ARG, "job scene is NULL");
+    cr_status st = check_camera(&j.camera);
+    if (st != CR_OK) return st;
+    if (j.spp == 0) return fail(CR_ERR_INVALID_ARG, "spp must be >= 1");
+    if (j.max_bounces == 0 || j.max_bounces > 16)
+        return fail(CR_ERR_INVALID_ARG, "max_bounces %u not in [1, 16]", j.max_bounces);
+    if (j.mode != CR_INDEPENDENT && j.mode != CR_MORTON_SORT && j.mode != CR_DIRECTION_REUSE)
+        return fail(CR_ERR_INVALID_ARG, "unknown mode %u", j.mode);
+    (void)tile_w;
+    (void)tile_h;
+    return CR_OK;
+}
+
+// Build the per-pass job tables of a set of jobs that share the tile shape and K.
+cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, RenderPlan& plan) {
+    if (n_jobs == 0 || n_jobs > 65535) return fail(CR_ERR_INVALID_ARG, "n_jobs %u not in [1, 65535]", n_jobs);
+    const uint32_t m = po.tile_w * po.tile_h;
+    if (po.tile_w == 0 || po.tile_h == 0 || !pow2(m) || m > 1024)
+        return fail(CR_ERR_INVALID_ARG, "group_w*group_h = %ux%u must be a power of two <= 1024", po.tile_w, po.tile_h);
+    const uint32_t K = po.k ? po.k : m;
+    if (!pow2(K) || m % K != 0 || K > 256)
+        return fail(CR_ERR_INVALID_ARG, "K=%u must be a power of two dividing W*H=%u and <= 256", K, m);
+    plan = RenderPlan();
+    plan.tile_w = po.tile_w;
+    plan.tile_h = po.tile_h;
+    plan.m = m;
+    plan.k = K;
+    plan.bvh8 = po.bvh8;
+    // scene table
+    std::vector<const cr_scene*> uniq;
+    std::vector<uint32_t> scene_idx(n_jobs);
+    uint32_t max_spp = 0, px = 0;
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        cr_status st = check_job(jobs[i], po.tile_w, po.tile_h);
+        if (st != CR_OK) return st;
+        if (po.bvh8 && !jobs[i].scene->dev.nodes8)
+            return fail(CR_ERR_INVALID_ARG, "job %u: the scene has no BVH8-Q (create it with CR_BVH8Q)", i);
+        uint32_t k = 0;
+        while (k < uniq.size() && uniq[k] != jobs[i].scene) ++k;
+        if (k == uniq.size()) uniq.push_back(jobs[i].scene);
+        scene_idx[i] = k;
+        max_spp = std::max(max_spp, jobs[i].spp);
+        plan.max_bounces = std::max(plan.max_bounces, jobs[i].max_bounces);
+        if (jobs[i].mode == CR_MORTON_SORT) plan.sort = true;
+        px += jobs[i].camera.width * jobs[i].camera.height;
+        if ((uint64_t)px > (1ull << 28)) return fail(CR_ERR_INVALID_ARG, "too many pixels in the batch");
+    }
+    for (auto* sc : uniq) plan.scenes.push_back(scene_entry(sc->dev, po.bvh8));
+    plan.npx_total = px;
+    // passes: pass p renders sample p of every job with spp > p
+    uint32_t px_base = 0;
+    std::vector<uint32_t> pxb(n_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        pxb[i] = px_base;
+        px_base += jobs[i].camera.width * jobs[i].camera.height;
+    }
+    for (uint32_t p = 0; p < max_spp; ++p) {
+        Pass ps;
+        ps.job_offset = (uint32_t)plan.jobs.size();
+        uint32_t tiles = 0;
+        for (uint32_t i = 0; i < n_jobs; ++i) {
+            const cr_job& j = jobs[i];
+            if (j.spp <= p) continue;
+            JobDev d;
+            std::memset(&d, 0, sizeof(d));
+            d.cam = make_camera(j.camera);
+            d.tiles_x = (j.camera.width + po.tile_w - 1) / po.tile_w;
+            const uint32_t tiles_y = (j.camera.height + po.tile_h - 1) / po.tile_h;
+            d.tile_base = tiles;
+            d.px_base = pxb[i];
+            d.scene = scene_idx[i];
+            d.frame = j.frame_base + p;
+            d.max_bounces = j.max_bounces;
+            d.reuse_mask = 0;
+            if (j.mode == CR_DIRECTION_REUSE)
+                for (uint32_t b = 1; b <= j.max_bounces; ++b)
+                    if (j.reuse_depth == 0 || b <= j.reuse_depth) d.reuse_mask |= 1u << b;
+            d.interleave = po.interleave ? 1u : 0u;
+            d.seed = j.seed;
+            d.out = j.out_rgb;
+            d.inv_spp = 1.0f / (float)j.spp;
+            const uint64_t t64 = (uint64_t)tiles + (uint64_t)d.tiles_x * tiles_y;
+            if (t64 * m > (1ull << 27)) return fail(CR_ERR_INVALID_ARG, "pass %u: too many slots", p);
+            tiles = (uint32_t)t64;
+            plan.jobs.push_back(d);
+        }
+        ps.n_jobs = (uint32_t)plan.jobs.size() - ps.job_offset;
+        ps.n_tiles = tiles;
+        plan.max_slots = std::max(plan.max_slots, tiles * m);
+        plan.passes.push_back(ps);
+    }
+    return CR_OK;
+}
+
+cr_status Plan::upload(const RenderPlan& p, cudaStream_t st) {
+    size_t bj = sizeof(JobDev) * p.jobs.size(), bs = sizeof(SceneDev) * p.scenes.size();
+    cudaError_t e = cudaSuccess;
+    if (bj > cap_jobs || bs > cap_scenes) { // grow (the tables are reused across calls)
+        cudaDeviceSynchronize();
+        release();
+        e = cudaMalloc(&d_jobs, bj);
+        if (e == cudaSuccess) e = cudaMalloc(&d_scenes, bs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            release();
+            return fail(CR_ERR_OOM, "job tables: %s", cudaGetErrorString(e));
+        }
+        cap_jobs = bj;
+        cap_scenes = bs;
+    }
+    e = cudaMemcpyAsync(d_jobs, p.jobs.data(), bj, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_scenes, p.scenes.data(), bs, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(CR_ERR_CUDA, "job tables: %s", cudaGetErrorString(e));
+    return CR_OK;
+}
+
+void Plan::release() {
+    if (d_jobs) cudaFree(d_jobs);
+    if (d_scenes) cudaFree(d_scenes);
+    d_jobs = nullptr;
+    d_scenes = nullptr;
+    cap_jobs = cap_scenes = 0;
+}
+
+// Enqueue every stage of a plan on one stream (all passes, all bounces, then the output).
+// Nothing here synchronises the host, so the sequence can also be captured into a graph.
+cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, const ExecOpts& eo, cudaStream_t stream,
+                       LaunchCount& lc, StageTimes* times) {
+    PathBuffers& b = ws.pb;
+    StageEvents ev;
+    ev.on = times != nullptr;
+    cr_status failst = CR_OK;
+    auto check = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && failst == CR_OK) failst = fail(CR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    check(cudaMemsetAsync(b.counts, 0, 4 * kCountsWords, stream), "memset counts");
+    if (eo.clear_accum) check(cudaMemsetAsync(b.accum, 0, 16 * (size_t)p.npx_total, stream), "memset accum");
+    TraceArgs ta;
+    ta.ray_o = b.ray_o;
+    ta.ray_d = b.ray_d;
+    ta.hit = b.hit;
+    ta.block = eo.block;
+    ta.persistent = eo.persistent;
+    ta.work_counter = b.counts + 2;
+    ta.bvh8 = p.bvh8;
+    ta.scenes = dev.d_scenes;
+    ta.slot_scene = b.slot_scene;
+    double dummy = 0.0;
+    for (const Pass& ps : p.passes) {
+        PassArgs P;
+        P.jobs = dev.d_jobs + ps.job_offset;
+        P.n_jobs = ps.n_jobs;
+        P.scenes = dev.d_scenes;
+        P.tile_w = p.tile_w;
+        P.tile_h = p.tile_h;
+        P.m = p.m;
+        P.k = p.k;
+        P.n_tiles = ps.n_tiles;
+        P.npx = eo.debug_npx;
+        const uint32_t n_slots = ps.n_tiles * p.m;
+        b.n_groups = n_slots / p.k;
+        ev.begin(stream, times ? &times->raygen : &dummy);
+        launch_raygen(P, b, stream, lc);
+        ev.end();
+        ta.queue = nullptr;
+        ta.queue_count = nullptr;
+        ta.n_max = n_slots;
+        ta.counters = nullptr;
+        if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
+        ev.begin(stream, times ? &times->trace_primary : &dummy);
+        launch_trace(ta, stream, lc);
+        ev.end();
+        for (uint32_t bnc = 1; bnc <= p.max_bounces; ++bnc) {
+            P.bounce = bnc;
+            ev.begin(stream, times ? &times->shade : &dummy);
+            launch_shade(P, b, bnc == 1, eo.debug, stream, lc);
+            ev.end();
+            ev.begin(stream, times ? &times->compact : &dummy);
+            launch_compact(P, b, bnc == 1, stream, lc);
+            ev.end();
+            ta.queue = b.ray_queue;
+            ta.queue_count = b.counts + 8 + 2 * bnc;
+            ta.n_max = n_slots;
+            if (p.sort) {
+                ev.begin(stream, times ? &times->sort : &dummy);
+                ta.queue = launch_morton_sort(P, b, bnc, stream, lc);
+                ev.end();
+            }
+            ta.counters = eo.count ? b.counters : nullptr;
+            if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
+            ev.begin(stream, times ? &times->trace_secondary : &dummy);
+            launch_trace(ta, stream, lc);
+            ev.end();
+        }
+        P.bounce = p.max_bounces + 1;
+        ev.begin(stream, times ? &times->shade : &dummy);
+        launch_shade(P, b, false, eo.debug, stream, lc);
+        ev.end();
+        ev.begin(stream, times ? &times->accum : &dummy);
+        launch_accumulate(P, b, stream, lc);
+        ev.end();
+    }
+    // pass 0 holds every job (spp >= 1), with the px_base and output of each
+    if (eo.write_output) launch_output(dev.d_jobs, p.passes[0].n_jobs, b.accum, p.npx_total, stream, lc);
+    check(cudaGetLastError(), "launch");
+    if (times) {
+        // the caller synchronises the stream before reading; resolve needs completed events
+        check(cudaStreamSynchronize(stream), "sync");
+        ev.resolve();
+    }
+    return failst;
+}
+
+} // namespace cr
+
 extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t spp, uint32_t max_bounces,
                                   cr_reuse_mode mode, uint32_t group_w, uint32_t group_h, float* out_rgb,
                                   const cr_render_opts* opts_in) {
     g_err.clear();
     if (!s) return fail(CR_ERR_INVALID_ARG, "cr_render: scene is NULL");
     if (!out_rgb) return fail(CR_ERR_INVALID_ARG, "cr_render: out_rgb is NULL");
-    cr_status st = check_camera(cam);
-    if (st != CR_OK) return st;
-    if (spp == 0) return fail(CR_ERR_INVALID_ARG, "cr_render: spp must be >= 1");
-    if (max_bounces == 0 || max_bounces > 16) return fail(CR_ERR_INVALID_ARG, "cr_render: max_bounces %u not in [1, 16]", max_bounces);
-    if (mode != CR_INDEPENDENT && mode != CR_MORTON_SORT && mode != CR_DIRECTION_REUSE)
-        return fail(CR_ERR_INVALID_ARG, "cr_render: unknown mode %d", (int)mode);
-    const uint32_t m = group_w * group_h;
-    if (group_w == 0 || group_h == 0 || !pow2(m) || m > 1024)
-        return fail(CR_ERR_INVALID_ARG, "cr_render: group_w*group_h = %ux%u must be a power of two <= 1024", group_w, group_h);
     cr_render_opts o;
     cr_render_opts_default(&o);
     if (opts_in) o = *opts_in;
-    const uint32_t K = o.k ? o.k : m;
-    if (!pow2(K) || m % K != 0 || K > 256)
-        return fail(CR_ERR_INVALID_ARG, "cr_render: K=%u must be a power of two dividing W*H=%u and <= 256", K, m);
     const bool use8 = o.bvh == CR_BVH8Q;
     if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8) || (use8 && !s->dev.nodes8))
         return fail(CR_ERR_INVALID_ARG, "cr_render: bvh %u not available for this scene", o.bvh);
@@ -447,30 +675,12 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     if (o.debug && (!o.debug->prim || !o.debug->cat || !o.debug->cls || !o.debug->flags || !o.debug->local || !o.debug->world))
         return fail(CR_ERR_INVALID_ARG, "cr_render: debug capture needs all six buffers");
     cudaStream_t stream = static_cast<cudaStream_t>(o.stream);
-
-    RenderParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.cam = make_camera(*cam);
-    p.tile_w = group_w;
-    p.tile_h = group_h;
-    p.m = m;
-    p.k = K;
-    p.tiles_x = (cam->width + group_w - 1) / group_w;
-    p.tiles_y = (cam->height + group_h - 1) / group_h;
-    p.interleave = o.interleave ? 1u : 0u;
-    p.seed = o.seed;
-    p.max_bounces = max_bounces;
-    const uint64_t n_slots64 = (uint64_t)p.tiles_x * p.tiles_y * m;
-    if (n_slots64 > (1ull << 27)) return fail(CR_ERR_INVALID_ARG, "cr_render: %llu slots is too many", (unsigned long long)n_slots64);
-    const uint32_t n_slots = (uint32_t)n_slots64;
-    const uint32_t npx = cam->width * cam->height;
-    st = ensure_workspace(s, n_slots, npx);
+    cr_status st = check_camera(cam);
     if (st != CR_OK) return st;
-    PathBuffers& b = s->pb;
-    b.n_groups = n_slots / K;
     const bool out_dev = is_device_ptr(out_rgb);
     if (!out_dev && (o.flags & CR_OPT_NO_SYNC))
         return fail(CR_ERR_INVALID_ARG, "cr_render: CR_OPT_NO_SYNC needs a device out_rgb");
+    const uint32_t npx = cam->width * cam->height;
     if (!out_dev && s->out_cap < (size_t)npx * 3) {
         if (s->d_out) cudaFree(s->d_out);
         s->d_out = nullptr;
@@ -478,102 +688,72 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         CR_CUDA(cudaMalloc(&s->d_out, sizeof(float) * 3 * (size_t)npx));
         s->out_cap = (size_t)npx * 3;
     }
-
+    cr_job job;
+    std::memset(&job, 0, sizeof(job));
+    job.scene = s;
+    job.camera = *cam;
+    job.spp = spp;
+    job.max_bounces = max_bounces;
+    job.mode = (uint32_t)mode;
+    job.reuse_depth = o.reuse_depth;
+    job.seed = o.seed;
+    job.frame_base = o.frame_base;
+    job.out_rgb = out_dev ? out_rgb : s->d_out;
+    PlanOpts po;
+    po.tile_w = group_w;
+    po.tile_h = group_h;
+    po.k = o.k;
+    po.interleave = o.interleave;
+    po.bvh8 = use8;
+    RenderPlan plan;
+    st = build_plan(&job, 1, po, plan);
+    if (st != CR_OK) return st;
+    st = s->ws.ensure(plan.max_slots, plan.npx_total);
+    if (st != CR_OK) return st;
+    Plan& dev = s->plan_dev;
+    st = dev.upload(plan, stream);
+    if (st != CR_OK) return st;
+    ExecOpts eo;
+    eo.block = block;
+    eo.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
+    eo.count = (o.flags & CR_OPT_COUNT) != 0;
+    eo.debug = o.debug;
+    eo.debug_npx = npx;
     LaunchCount lc;
-    StageEvents ev;
-    cr_stats stats;
-    std::memset(&stats, 0, sizeof(stats));
-    ev.on = (o.flags & CR_OPT_STATS) && o.stats;
-    ev.pool.reserve(64 + 16 * (size_t)spp * (max_bounces + 2));
+    StageTimes times;
     cudaEvent_t e_all[2];
     if (o.stats) {
         CR_CUDA(cudaEventCreate(&e_all[0]));
         CR_CUDA(cudaEventCreate(&e_all[1]));
         CR_CUDA(cudaEventRecord(e_all[0], stream));
     }
-    CR_CUDA(cudaMemsetAsync(b.counts, 0, 4 * kCountsWords, stream));
-    CR_CUDA(cudaMemsetAsync(b.accum, 0, 16 * (size_t)npx, stream));
-
-    TraceArgs ta;
-    ta.ray_o = b.ray_o;
-    ta.ray_d = b.ray_d;
-    ta.hit = b.hit;
-    ta.block = block;
-    ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
-    ta.work_counter = b.counts + 2;
-    ta.bvh8 = use8;
-    DevScene ds = s->dev;
-    if (use8) ds.tris = s->dev.tris8; // hits index the BVH8-Q triangle copy
-
-    for (uint32_t si = 0; si < spp; ++si) {
-        p.frame = o.frame_base + si;
-        ev.begin(stream, &stats.ms_raygen);
-        launch_raygen(p, b, stream, lc);
-        ev.end();
-        // primary rays: every slot, in slot (tile, group) order
-        ta.queue = nullptr;
-        ta.queue_count = nullptr;
-        ta.n_max = n_slots;
-        ta.counters = nullptr;
-        if (ta.persistent) CR_CUDA(cudaMemsetAsync(ta.work_counter, 0, 4, stream));
-        ev.begin(stream, &stats.ms_trace_primary);
-        launch_trace(ds, ta, stream, lc);
-        ev.end();
-        for (uint32_t bnc = 1; bnc <= max_bounces; ++bnc) {
-            p.bounce = bnc;
-            p.final_pass = 0;
-            p.reuse = (mode == CR_DIRECTION_REUSE && (o.reuse_depth == 0 || bnc <= o.reuse_depth)) ? 1u : 0u;
-            ev.begin(stream, &stats.ms_shade);
-            launch_shade(ds, p, b, bnc == 1, o.debug, stream, lc);
-            ev.end();
-            ev.begin(stream, &stats.ms_compact);
-            launch_compact(p, b, bnc == 1, stream, lc);
-            ev.end();
-            ta.queue = b.ray_queue;
-            ta.queue_count = b.counts + 8 + 2 * bnc;
-            ta.n_max = n_slots;
-            if (mode == CR_MORTON_SORT) {
-                ev.begin(stream, &stats.ms_sort);
-                ta.queue = launch_morton_sort(ds, b, bnc, stream, lc);
-                ev.end();
-            }
-            ta.counters = (o.flags & CR_OPT_COUNT) ? b.counters : nullptr;
-            if (ta.persistent) CR_CUDA(cudaMemsetAsync(ta.work_counter, 0, 4, stream));
-            ev.begin(stream, &stats.ms_trace_secondary);
-            launch_trace(ds, ta, stream, lc);
-            ev.end();
-        }
-        p.bounce = max_bounces + 1;
-        p.final_pass = 1;
-        p.reuse = 0;
-        ev.begin(stream, &stats.ms_shade);
-        launch_shade(ds, p, b, false, o.debug, stream, lc);
-        ev.end();
-        ev.begin(stream, &stats.ms_accum);
-        launch_accumulate(p, b, stream, lc);
-        ev.end();
-    }
-    float* dst = out_dev ? out_rgb : s->d_out;
-    launch_output(b, npx, 1.0f / (float)spp, dst, stream, lc);
-    CR_CUDA(cudaGetLastError());
+    st = enqueue_plan(plan, dev, s->ws, eo, stream, lc, (o.stats && (o.flags & CR_OPT_STATS)) ? &times : nullptr);
+    if (st != CR_OK) return st;
     if (!out_dev) CR_CUDA(cudaMemcpyAsync(out_rgb, s->d_out, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, stream));
     if (o.stats) {
+        cr_stats stats;
+        std::memset(&stats, 0, sizeof(stats));
         CR_CUDA(cudaEventRecord(e_all[1], stream));
         uint64_t host_counts[kCountsWords / 2];
-        CR_CUDA(cudaMemcpyAsync(host_counts, b.counts, 4 * kCountsWords, cudaMemcpyDeviceToHost, stream));
+        CR_CUDA(cudaMemcpyAsync(host_counts, s->ws.pb.counts, 4 * kCountsWords, cudaMemcpyDeviceToHost, stream));
         CR_CUDA(cudaStreamSynchronize(stream));
         float ms = 0;
         cudaEventElapsedTime(&ms, e_all[0], e_all[1]);
-        ev.resolve();
         stats.ms_total = ms;
+        stats.ms_raygen = times.raygen;
+        stats.ms_trace_primary = times.trace_primary;
+        stats.ms_trace_secondary = times.trace_secondary;
+        stats.ms_shade = times.shade;
+        stats.ms_compact = times.compact;
+        stats.ms_sort = times.sort;
+        stats.ms_accum = times.accum;
         const uint64_t* stat = host_counts + kStatWord / 2;
         for (uint32_t bb = 1; bb <= max_bounces; ++bb) stats.secondary_rays += stat[bb];
         stats.secondary_rays_b1 = stat[1];
         const uint64_t* ctr = host_counts + kCounterWord / 2;
         stats.node_visits = ctr[0];
         stats.tri_tests = ctr[1];
-        uint64_t valid_px = (uint64_t)npx;
-        stats.primary_rays = valid_px * spp;
+        stats.primary_rays = (uint64_t)npx * spp;
         stats.kernel_launches = lc.n;
         *o.stats = stats;
         cudaEventDestroy(e_all[0]);
@@ -644,8 +824,7 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     const bool use8 = o.bvh == CR_BVH8Q;
     if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8) || (use8 && !s->dev.nodes8))
         return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: bvh %u not available", o.bvh);
-    DevScene ds = s->dev;
-    if (use8) ds.tris = s->dev.tris8;
+    const float4* tris = use8 ? s->dev.tris8 : s->dev.tris;
     const int block = o.block ? (int)o.block : 128;
     if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: block %d", block);
     cudaStream_t stream = static_cast<cudaStream_t>(o.stream);
@@ -671,6 +850,8 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     ta.block = block;
     ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
     ta.bvh8 = use8;
+    ta.scenes = dev_scene_entry(s, use8);
+    ta.slot_scene = nullptr;
     ta.work_counter = wc.as<uint32_t>();
     ta.counters = (o.flags & CR_OPT_COUNT) ? reinterpret_cast<unsigned long long*>(wc.as<uint32_t>() + 4) : nullptr;
     cudaEvent_t e0, e1;
@@ -679,9 +860,9 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
         CR_CUDA(cudaEventCreate(&e1));
         CR_CUDA(cudaEventRecord(e0, stream));
     }
-    launch_trace(ds, ta, stream, lc);
+    launch_trace(ta, stream, lc);
     if (o.stats) CR_CUDA(cudaEventRecord(e1, stream));
-    launch_hits_to_user(ds, hit.as<int2>(), n, static_cast<int32_t*>(p_out.dev), static_cast<float*>(t_out.dev), stream, lc);
+    launch_hits_to_user(tris, hit.as<int2>(), n, static_cast<int32_t*>(p_out.dev), static_cast<float*>(t_out.dev), stream, lc);
     CR_CUDA(cudaGetLastError());
     CR_CUDA(finish_out(p_out, stream));
     CR_CUDA(finish_out(t_out, stream));
@@ -714,24 +895,15 @@ extern "C" cr_status cr_debug_groups(uint32_t width, uint32_t height, uint32_t g
         return fail(CR_ERR_INVALID_ARG, "cr_debug_groups: bad size or NULL output");
     if (!group_w || !group_h || !pow2(m) || m > 1024)
         return fail(CR_ERR_INVALID_ARG, "cr_debug_groups: W*H must be a power of two <= 1024");
-    RenderParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.cam.width = width;
-    p.cam.height = height;
-    p.tile_w = group_w;
-    p.tile_h = group_h;
-    p.m = m;
-    p.k = m;
-    p.tiles_x = (width + group_w - 1) / group_w;
-    p.tiles_y = (height + group_h - 1) / group_h;
-    p.interleave = interleave ? 1u : 0u;
-    p.seed = seed;
-    p.frame = frame;
+    CamBasis cam;
+    std::memset(&cam, 0, sizeof(cam));
+    cam.width = width;
+    cam.height = height;
     Staged out;
     const size_t bytes = sizeof(uint32_t) * (size_t)width * height;
     CR_CUDA(stage_out(out, slot_of_pixel, bytes));
     LaunchCount lc;
-    launch_groups(p, static_cast<uint32_t*>(out.dev), 0, lc);
+    launch_groups(cam, group_w, group_h, interleave ? 1u : 0u, seed, frame, static_cast<uint32_t*>(out.dev), 0, lc);
     CR_CUDA(cudaGetLastError());
     CR_CUDA(finish_out(out, 0));
     CR_CUDA(cudaStreamSynchronize(0));
@@ -805,5 +977,226 @@ extern "C" cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, ui
     } catch (const std::bad_alloc&) {
         return fail(CR_ERR_OOM, "cr_debug_bvh_check: host allocation");
     }
+    return CR_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Batches: many jobs in one wavefront, optionally replayed from a CUDA graph.
+struct cr_batch {
+    std::vector<cr_job> jobs;
+    cr_batch_opts opts;
+    cr::RenderPlan plan;
+    cr::Plan dev;
+    cr::Workspace ws;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;
+};
+
+static cr_status batch_opts_check(const cr_batch_opts* o, PlanOpts& po, ExecOpts& eo) {
+    if (!o) return fail(CR_ERR_INVALID_ARG, "batch options are NULL");
+    if (o->bvh != CR_BVH2 && o->bvh != CR_BVH8Q && o->bvh != 0) return fail(CR_ERR_INVALID_ARG, "bvh %u", o->bvh);
+    const int block = o->block ? (int)o->block : 128;
+    if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "block %d", block);
+    po.tile_w = o->group_w;
+    po.tile_h = o->group_h;
+    po.k = o->k;
+    po.interleave = o->interleave;
+    po.bvh8 = o->bvh == CR_BVH8Q;
+    eo.block = block;
+    eo.persistent = (o->flags & CR_OPT_PERSISTENT) != 0;
+    return CR_OK;
+}
+
+static cr_status check_job_outputs(const cr_job* jobs, uint32_t n) {
+    for (uint32_t i = 0; i < n; ++i)
+        if (!jobs[i].out_rgb || !is_device_ptr(jobs[i].out_rgb))
+            return fail(CR_ERR_INVALID_ARG, "job %u: out_rgb must be a device buffer", i);
+    return CR_OK;
+}
+
+extern "C" cr_status cr_batch_device_bytes(const cr_job* jobs, uint32_t n_jobs, const cr_batch_opts* opts,
+                                           uint64_t* bytes) {
+    g_err.clear();
+    if (!jobs || !bytes) return fail(CR_ERR_INVALID_ARG, "cr_batch_device_bytes: NULL argument");
+    PlanOpts po;
+    ExecOpts eo;
+    cr_status st = batch_opts_check(opts, po, eo);
+    if (st != CR_OK) return st;
+    RenderPlan plan;
+    st = build_plan(jobs, n_jobs, po, plan);
+    if (st != CR_OK) return st;
+    *bytes = workspace_bytes(plan.max_slots, plan.npx_total) + sizeof(JobDev) * plan.jobs.size() +
+             sizeof(SceneDev) * plan.scenes.size();
+    return CR_OK;
+}
+
+extern "C" cr_status cr_batch_create(const cr_job* jobs, uint32_t n_jobs, const cr_batch_opts* opts, cr_batch** out) {
+    g_err.clear();
+    if (!out || !jobs) return fail(CR_ERR_INVALID_ARG, "cr_batch_create: NULL argument");
+    *out = nullptr;
+    PlanOpts po;
+    ExecOpts eo;
+    cr_status st = batch_opts_check(opts, po, eo);
+    if (st != CR_OK) return st;
+    st = check_job_outputs(jobs, n_jobs);
+    if (st != CR_OK) return st;
+    std::unique_ptr<cr_batch> b(new (std::nothrow) cr_batch());
+    if (!b) return fail(CR_ERR_OOM, "cr_batch_create: host allocation");
+    b->jobs.assign(jobs, jobs + n_jobs);
+    b->opts = *opts;
+    st = build_plan(b->jobs.data(), n_jobs, po, b->plan);
+    if (st != CR_OK) return st;
+    if (opts->stream) {
+        b->stream = static_cast<cudaStream_t>(opts->stream);
+    } else {
+        CR_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    st = b->ws.ensure(b->plan.max_slots, b->plan.npx_total);
+    if (st != CR_OK) return st;
+    st = b->dev.upload(b->plan, b->stream);
+    if (st != CR_OK) return st;
+    CR_CUDA(cudaStreamSynchronize(b->stream));
+    if (opts->flags & CR_BATCH_GRAPH) {
+        LaunchCount lc;
+        CR_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_plan(b->plan, b->dev, b->ws, eo, b->stream, lc, nullptr);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st != CR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(CR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        b->graph = g;
+        CR_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+        b->launches = lc.n;
+    }
+    *out = b.release();
+    return CR_OK;
+}
+
+extern "C" cr_status cr_batch_run(cr_batch* b, cr_stats* stats) {
+    g_err.clear();
+    if (!b) return fail(CR_ERR_INVALID_ARG, "cr_batch_run: NULL batch");
+    PlanOpts po;
+    ExecOpts eo;
+    cr_status st = batch_opts_check(&b->opts, po, eo);
+    if (st != CR_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        CR_CUDA(cudaEventCreate(&e0));
+        CR_CUDA(cudaEventCreate(&e1));
+        CR_CUDA(cudaEventRecord(e0, b->stream));
+    }
+    uint64_t launches = b->launches;
+    if (b->exec) {
+        CR_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    } else {
+        LaunchCount lc;
+        st = enqueue_plan(b->plan, b->dev, b->ws, eo, b->stream, lc, nullptr);
+        if (st != CR_OK) return st;
+        launches = lc.n;
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        CR_CUDA(cudaEventRecord(e1, b->stream));
+        uint64_t host_counts[kCountsWords / 2];
+        CR_CUDA(cudaMemcpyAsync(host_counts, b->ws.pb.counts, 4 * kCountsWords, cudaMemcpyDeviceToHost, b->stream));
+        CR_CUDA(cudaStreamSynchronize(b->stream));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        stats->ms_total = ms;
+        const uint64_t* stat = host_counts + kStatWord / 2;
+        for (uint32_t bb = 1; bb <= b->plan.max_bounces; ++bb) stats->secondary_rays += stat[bb];
+        stats->secondary_rays_b1 = stat[1];
+        uint64_t prim = 0;
+        for (const cr_job& j : b->jobs) prim += (uint64_t)j.camera.width * j.camera.height * j.spp;
+        stats->primary_rays = prim;
+        stats->kernel_launches = launches;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    CR_CUDA(cudaStreamSynchronize(b->stream));
+    CR_CUDA(cudaGetLastError());
+    return CR_OK;
+}
+
+extern "C" cr_status cr_batch_destroy(cr_batch* b) {
+    g_err.clear();
+    if (!b) return CR_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->ws.release();
+    b->dev.release();
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return CR_OK;
+}
+
+extern "C" cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint32_t allow_contiguous,
+                                       cr_batch_opts* opts, cr_tune_report* report) {
+    g_err.clear();
+    if (!jobs || !opts) return fail(CR_ERR_INVALID_ARG, "cr_batch_autotune: NULL argument");
+    cr_tune_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    rep.best_ms = 1e30;
+    const uint32_t tiles[3][2] = {{4, 4}, {8, 8}, {16, 16}};
+    auto time_one = [&](const cr_batch_opts& o, double& ms_out) -> cr_status {
+        cr_batch* b = nullptr;
+        cr_status st = cr_batch_create(jobs, n_jobs, &o, &b);
+        if (st != CR_OK) return st;
+        cr_stats s1;
+        double best = 1e30;
+        for (int r = 0; r < 3; ++r) { // one warm-up, best of two
+            st = cr_batch_run(b, &s1);
+            if (st != CR_OK) break;
+            if (r > 0) best = std::min(best, s1.ms_total);
+        }
+        cr_batch_destroy(b);
+        ms_out = best;
+        return st;
+    };
+    for (const auto& t : tiles) {
+        const uint32_t m = t[0] * t[1];
+        for (uint32_t k = 4; k <= m / 4 && k <= 64; k *= 2) {
+            for (uint32_t il_i = 0; il_i < (allow_contiguous ? 2u : 1u); ++il_i) {
+                const uint32_t il = 1u - il_i;
+                for (uint32_t block : {64u, 128u, 256u}) {
+                    cr_batch_opts o = *opts;
+                    o.group_w = t[0];
+                    o.group_h = t[1];
+                    o.k = k;
+                    o.interleave = il;
+                    o.block = block;
+                    o.flags &= ~(uint32_t)CR_BATCH_GRAPH;
+                    double ms = 0;
+                    cr_status st = time_one(o, ms);
+                    if (st != CR_OK) return st;
+                    rep.n_candidates++;
+                    rep.worst_ms = std::max(rep.worst_ms, ms);
+                    if (t[0] == 8 && k == 8 && il == 1 && block == 128) rep.default_ms = ms;
+                    if (ms < rep.best_ms) {
+                        rep.best_ms = ms;
+                        rep.best_group_w = t[0];
+                        rep.best_group_h = t[1];
+                        rep.best_k = k;
+                        rep.best_interleave = il;
+                        rep.best_block = block;
+                    }
+                }
+            }
+        }
+    }
+    opts->group_w = rep.best_group_w;
+    opts->group_h = rep.best_group_h;
+    opts->k = rep.best_k;
+    opts->interleave = rep.best_interleave;
+    opts->block = rep.best_block;
+    if (report) *report = rep;
     return CR_OK;
 }

@@ -58,7 +58,7 @@ void check_bvh2(const HostBVH2& b, const float* v, uint32_t n_tri, uint32_t& cov
 void check_bvh8(const HostBVH8& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);
 
 // ------------------------------------------------------------------------------------
-// Device-side scene description passed to kernels.
+// Device-side scene description (host copy kept in the scene handle).
 struct DevScene {
     const float4* nodes2 = nullptr; // 4 per node
     const uint4* nodes8 = nullptr;  // 5 per node
@@ -70,6 +70,17 @@ struct DevScene {
     uint32_t n_tri = 0, n_mat = 0;
 };
 
+// One entry of the device scene table a pass reads (tris in the order of the BVH traversed).
+struct SceneDev {
+    const float4* nodes2;
+    const uint4* nodes8;
+    const float4* tris;
+    const float4* mats;
+    float env[4];
+    float lo[4], hi[4];
+};
+SceneDev scene_entry(const DevScene& s, bool bvh8);
+
 // Camera basis rounded to float once (computed in double on the host).
 struct CamBasis {
     float pos[3], fwd[3], right[3], up[3];
@@ -77,6 +88,35 @@ struct CamBasis {
     uint32_t width, height;
 };
 CamBasis make_camera(const cr_camera& c);
+
+// One render job of one sample pass: a device table entry.  Jobs of a pass occupy
+// consecutive tile ranges; every reuse group lies inside one tile, hence inside one job.
+struct JobDev {
+    CamBasis cam;
+    uint32_t tiles_x;
+    uint32_t tile_base;   // first tile of the job in the pass
+    uint32_t px_base;     // first pixel of the job in the accumulation buffer
+    uint32_t scene;       // index into the scene table
+    uint32_t frame;       // frame index of this pass (frame_base + sample)
+    uint32_t max_bounces; // B of the job
+    uint32_t reuse_mask;  // bit b: direction reuse at bounce b
+    uint32_t interleave;
+    uint64_t seed;
+    float* out;           // device output (w*h*3 floats) of the job
+    float inv_spp;
+    uint32_t pad;
+};
+
+// Launch-uniform description of a pass.
+struct PassArgs {
+    const JobDev* jobs = nullptr;
+    uint32_t n_jobs = 0;
+    const SceneDev* scenes = nullptr;
+    uint32_t tile_w = 0, tile_h = 0, m = 0, k = 0;
+    uint32_t n_tiles = 0;  // tiles of all jobs of the pass
+    uint32_t bounce = 0;   // shade: 1..B (B + 1 = final)
+    uint32_t npx = 0;      // pixels of the debug capture (single-job renders)
+};
 
 // Per-call launch statistics.
 struct LaunchCount {
@@ -87,10 +127,12 @@ struct LaunchCount {
 struct TraceArgs {
     const float4* ray_o = nullptr; // slot-indexed (o.xyz, skip original index as int bits)
     const float4* ray_d = nullptr; // slot-indexed (d.xyz, tmax); tmax < 0: no ray
-    const int32_t* queue = nullptr;     // slots to trace; NULL = slots [0, n_direct)
+    const int32_t* queue = nullptr;     // slots to trace; NULL = slots [0, n_max)
     const uint32_t* queue_count = nullptr; // device count of queue entries (NULL: n_max)
     uint32_t n_max = 0;            // upper bound on the number of rays
     int2* hit = nullptr;           // slot-indexed (leaf triangle index or -1, t bits)
+    const SceneDev* scenes = nullptr;  // scene table
+    const uint16_t* slot_scene = nullptr; // per-slot scene index (NULL: scene 0)
     unsigned long long* counters = nullptr; // [0] node visits, [1] triangle tests (counting pass)
     uint32_t* work_counter = nullptr;       // persistent mode: atomic ray counter (zeroed)
     int block = 128;
@@ -98,17 +140,19 @@ struct TraceArgs {
     bool persistent = false;
     bool bvh8 = false;
 };
-void launch_trace(const DevScene& s, const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
+void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
 // Map leaf-order triangle indices of hits to original indices and split (prim, t).
-void launch_hits_to_user(const DevScene& s, const int2* hit, uint32_t n, int32_t* prim, float* t,
+void launch_hits_to_user(const float4* tris, const int2* hit, uint32_t n, int32_t* prim, float* t,
                          cudaStream_t st, LaunchCount& lc);
 
 // ------------------------------------------------------------------------------------
-// Wavefront path state, slot-indexed.  Slot = tile * m + sigma(i) (Sec. 3.3), so a reuse
-// group's K members occupy K consecutive slots.
+// Wavefront path state, slot-indexed.  Slot = (tile of the pass) * m + sigma(i) (Sec. 3.3),
+// so a reuse group's K members occupy K consecutive slots.
 struct PathBuffers {
     uint32_t n_slots = 0, n_groups = 0;
-    int32_t* pixel = nullptr;   // slot -> pixel (-1: none)
+    int32_t* pixel = nullptr;   // slot -> pixel of its job (-1: none)
+    uint16_t* slot_job = nullptr;   // slot -> job of the pass
+    uint16_t* slot_scene = nullptr; // slot -> scene table index
     float4* ray_o = nullptr;
     float4* ray_d = nullptr;
     int2* hit = nullptr;
@@ -116,7 +160,7 @@ struct PathBuffers {
     float4* radiance = nullptr; // path radiance rgb
     uint8_t* alive = nullptr;   // 1 while the path continues
     int32_t* ray_queue = nullptr;   // alive slots in slot order
-    int32_t* group_queue = nullptr; // groups with an alive member
+    int32_t* group_queue = nullptr; // groups with an alive member (2 x n_groups, double-buffered)
     // counts (kCountsWords words): [2] persistent work counter; [8 + 2b], [8 + 2b + 1] ray and
     // group queue lengths after the compaction of bounce b; from word kStatWord, 64-bit
     // running totals of rays traced per bounce (index b); from kCounterWord, 64-bit node
@@ -129,46 +173,93 @@ struct PathBuffers {
     int32_t* vals = nullptr;    // 2 x n_slots
     uint32_t* sort_hist = nullptr;
     uint32_t sort_hist_cap = 0;
-    float4* accum = nullptr;    // per pixel
+    float4* accum = nullptr;    // per pixel of all jobs
     uint32_t n_px_cap = 0;
     unsigned long long* counters = nullptr; // counting pass
 };
 
 constexpr uint32_t kCountsWords = 256, kStatWord = 64, kCounterWord = 128;
 
-struct RenderParams {
-    CamBasis cam;
-    uint32_t tile_w, tile_h, m, k;
-    uint32_t tiles_x, tiles_y;
-    uint32_t interleave;
-    uint64_t seed;
-    uint32_t frame;
-    uint32_t bounce;      // 1..B for shade
-    uint32_t max_bounces;
-    uint32_t reuse;       // 1: direction reuse at this bounce
-    uint32_t final_pass;  // 1: only environment / emission
-};
-
-void launch_raygen(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
-void launch_shade(const DevScene& s, const RenderParams& p, PathBuffers& b, bool first, const cr_debug* dbg,
-                  cudaStream_t st, LaunchCount& lc);
+void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
+void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,
+                  LaunchCount& lc);
 // Group-granular compaction of the slots processed by the last shade into ray and group queues.
-void launch_compact(const RenderParams& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc);
-const int32_t* launch_morton_sort(const DevScene& s, PathBuffers& b, uint32_t bounce, cudaStream_t st,
+void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc);
+const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, cudaStream_t st,
                                   LaunchCount& lc);
 uint32_t sort_hist_len(uint32_t n_slots);
 uint32_t compact_blocks(uint32_t n_pos);
 void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, float4* ray_o, float4* ray_d,
                            cudaStream_t st, LaunchCount& lc);
-void launch_accumulate(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
-void launch_output(PathBuffers& b, uint32_t npx, float inv_spp, float* out_rgb, cudaStream_t st, LaunchCount& lc);
-void launch_groups(const RenderParams& p, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc);
+void launch_accumulate(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
+// out[job] = accum / spp for every job of the table (all pixels of all jobs, one launch).
+void launch_output(const JobDev* jobs, uint32_t n_jobs, const float4* accum, uint32_t npx_total, cudaStream_t st,
+                   LaunchCount& lc);
+// out = accum[0, npx) * inv_spp for one job (accum already offset to the job's pixels).
+void launch_output_one(const float4* accum, uint32_t npx, float inv_spp, float* out, cudaStream_t st, LaunchCount& lc);
+void launch_groups(const CamBasis& cam, uint32_t tile_w, uint32_t tile_h, uint32_t interleave, uint64_t seed,
+                   uint32_t frame, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc);
 void launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out, cudaStream_t st, LaunchCount& lc);
 void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, const float* param, float* wi,
                    float* weight, uint8_t* valid, cudaStream_t st, LaunchCount& lc);
 
+// Path-state allocation of a scene (single renders) or a batch.
+struct Workspace {
+    PathBuffers pb;
+    void* base = nullptr;
+    size_t bytes = 0;
+    cr_status ensure(uint32_t n_slots, uint32_t npx);
+    void release();
+    ~Workspace() { release(); }
+};
+size_t workspace_bytes(uint32_t n_slots, uint32_t npx);
+
+// A set of jobs sharing the tile shape, K, interleave and BVH layout, cut into sample
+// passes: pass p renders sample p of every job with spp > p, all jobs in one wavefront.
+struct PlanOpts {
+    uint32_t tile_w = 8, tile_h = 8, k = 0, interleave = 1;
+    bool bvh8 = false;
+};
+struct Pass {
+    uint32_t job_offset = 0, n_jobs = 0, n_tiles = 0;
+};
+struct RenderPlan {
+    uint32_t tile_w = 0, tile_h = 0, m = 0, k = 0;
+    bool bvh8 = false, sort = false;
+    uint32_t max_bounces = 0, max_slots = 0, npx_total = 0;
+    std::vector<JobDev> jobs;     // all passes' tables, pass by pass
+    std::vector<SceneDev> scenes; // scene table
+    std::vector<Pass> passes;
+};
+// Device copies of a plan's tables.
+struct Plan {
+    JobDev* d_jobs = nullptr;
+    SceneDev* d_scenes = nullptr;
+    size_t cap_jobs = 0, cap_scenes = 0;
+    cr_status upload(const RenderPlan& p, cudaStream_t st);
+    void release();
+    ~Plan() { release(); }
+};
+struct ExecOpts {
+    int block = 128;
+    bool persistent = false, count = false;
+    bool clear_accum = true; // zero the accumulation buffer first
+    bool write_output = true; // write every job's output after the last pass
+    const cr_debug* debug = nullptr;
+    uint32_t debug_npx = 0;
+};
+struct StageTimes {
+    double raygen = 0, trace_primary = 0, trace_secondary = 0, shade = 0, compact = 0, sort = 0, accum = 0;
+};
+cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, RenderPlan& plan);
+cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h);
+bool scene_has_bvh8(const cr_scene* s);
+cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, const ExecOpts& eo, cudaStream_t stream,
+                       LaunchCount& lc, StageTimes* times);
+
 // Thread-local message returned by cr_last_error(); handle -> device scene.
 void set_last_error(const char* msg);
 const DevScene* dev_scene_of(const cr_scene* s);
+const SceneDev* dev_scene_entry(const cr_scene* s, bool bvh8); // device pointer
 
 } // namespace cr

@@ -58,34 +58,52 @@ __device__ __forceinline__ V3 camera_dir(const CamBasis& c, uint32_t px, uint32_
     return normalize3(d);
 }
 
+// Job of a pass tile: the last job whose first tile is <= tile (jobs are in tile order).
+__device__ __forceinline__ uint32_t job_of_tile(const JobDev* jobs, uint32_t n_jobs, uint32_t tile) {
+    uint32_t lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].tile_base <= tile) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // One block covers blockDim / m whole tiles: every thread finds sigma of its pixel, the
 // inverse map is built in shared memory, then thread j writes slot j of its tile so the
 // slot arrays are written contiguously.
-__global__ void k_raygen(RenderParams p, int32_t* __restrict__ pixel, float4* __restrict__ ray_o,
-                         float4* __restrict__ ray_d, float4* __restrict__ beta, float4* __restrict__ radiance,
-                         uint8_t* __restrict__ alive) {
+__global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __restrict__ slot_job,
+                         uint16_t* __restrict__ slot_scene, float4* __restrict__ ray_o, float4* __restrict__ ray_d,
+                         float4* __restrict__ beta, float4* __restrict__ radiance, uint8_t* __restrict__ alive) {
     extern __shared__ uint16_t inv[];
     const uint32_t m = p.m;
     const uint32_t tiles_per_block = blockDim.x / m;
     const uint32_t tl = threadIdx.x / m, j = threadIdx.x % m;
     const uint32_t tile = blockIdx.x * tiles_per_block + tl;
-    const uint32_t n_tiles = p.tiles_x * p.tiles_y;
-    if (tl < tiles_per_block && tile < n_tiles) {
-        const Lcg L = tile_lcg(p.seed, tile, p.frame, m, p.interleave);
-        inv[tl * m + sigma_of(L, j, m, p.interleave)] = (uint16_t)j;
+    const bool in = tl < tiles_per_block && tile < p.n_tiles;
+    uint32_t jid = 0;
+    if (in) {
+        jid = job_of_tile(p.jobs, p.n_jobs, tile);
+        const JobDev& J = p.jobs[jid];
+        const Lcg L = tile_lcg(J.seed, tile - J.tile_base, J.frame, m, J.interleave);
+        inv[tl * m + sigma_of(L, j, m, J.interleave)] = (uint16_t)j;
     }
     __syncthreads();
-    if (tl >= tiles_per_block || tile >= n_tiles) return;
+    if (!in) return;
+    const JobDev& J = p.jobs[jid];
+    const uint32_t t = tile - J.tile_base;
     const uint32_t i = inv[tl * m + j];
-    const uint32_t tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+    const uint32_t tx = t % J.tiles_x, ty = t / J.tiles_x;
     const uint32_t px = tx * p.tile_w + i % p.tile_w, py = ty * p.tile_h + i / p.tile_w;
     const uint32_t slot = tile * m + j;
-    if (px < p.cam.width && py < p.cam.height) {
-        const uint32_t pix = py * p.cam.width + px;
-        const uint4 h = philox_seed(p.seed, pix, p.frame, 0u, kTagCamera);
-        const V3 d = camera_dir(p.cam, px, py, unit24(h.x), unit24(h.y));
+    slot_job[slot] = (uint16_t)jid;
+    slot_scene[slot] = (uint16_t)J.scene;
+    if (px < J.cam.width && py < J.cam.height) {
+        const uint32_t pix = py * J.cam.width + px;
+        const uint4 h = philox_seed(J.seed, pix, J.frame, 0u, kTagCamera);
+        const V3 d = camera_dir(J.cam, px, py, unit24(h.x), unit24(h.y));
         pixel[slot] = (int32_t)pix;
-        ray_o[slot] = make_float4(p.cam.pos[0], p.cam.pos[1], p.cam.pos[2], __int_as_float(-1));
+        ray_o[slot] = make_float4(J.cam.pos[0], J.cam.pos[1], J.cam.pos[2], __int_as_float(-1));
         ray_d[slot] = make_float4(d.x, d.y, d.z, INFINITY);
         beta[slot] = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
         radiance[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -97,23 +115,25 @@ __global__ void k_raygen(RenderParams p, int32_t* __restrict__ pixel, float4* __
     }
 }
 
-__global__ void k_groups(RenderParams p, uint32_t* __restrict__ slot_of_pixel) {
+__global__ void k_groups(CamBasis cam, uint32_t tile_w, uint32_t tile_h, uint32_t interleave, uint64_t seed,
+                         uint32_t frame, uint32_t* __restrict__ slot_of_pixel) {
     const uint32_t pix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= p.cam.width * p.cam.height) return;
-    const uint32_t px = pix % p.cam.width, py = pix / p.cam.width;
-    const uint32_t tx = px / p.tile_w, ty = py / p.tile_h;
-    const uint32_t tile = ty * p.tiles_x + tx;
-    const uint32_t i = (py % p.tile_h) * p.tile_w + px % p.tile_w;
-    const Lcg L = tile_lcg(p.seed, tile, p.frame, p.m, p.interleave);
-    slot_of_pixel[pix] = tile * p.m + sigma_of(L, i, p.m, p.interleave);
+    if (pix >= cam.width * cam.height) return;
+    const uint32_t m = tile_w * tile_h;
+    const uint32_t tiles_x = (cam.width + tile_w - 1) / tile_w;
+    const uint32_t px = pix % cam.width, py = pix / cam.width;
+    const uint32_t tile = (py / tile_h) * tiles_x + px / tile_w;
+    const uint32_t i = (py % tile_h) * tile_w + px % tile_w;
+    const Lcg L = tile_lcg(seed, tile, frame, m, interleave);
+    slot_of_pixel[pix] = tile * m + sigma_of(L, i, m, interleave);
 }
 
 // ------------------------------------------------------------------------------------
 // Shade + classify + reuse + spawn (Sec. 3.2), one thread per slot of the alive groups.
 struct ShadeArgs {
-    const float4* tris;
-    const float4* mats;
-    float env[3];
+    const JobDev* jobs;
+    const SceneDev* scenes;
+    const uint16_t* slot_job;
     int32_t* pixel;
     float4* ray_o;
     float4* ray_d;
@@ -131,6 +151,10 @@ struct ShadeArgs {
 struct Member {
     int pix;
     bool alive;
+    bool final_pass; // the job's last secondary ray has been traced
+    bool reuse;      // the job reuses directions at this bounce
+    uint64_t seed;
+    uint32_t frame;
     int cls;
     V3 n, t, b, wo;
     float albedo[3];
@@ -141,24 +165,24 @@ struct Member {
 };
 
 // Shading point of a hit: geometric normal facing the incoming ray, tangent frame, wo.
-__device__ __forceinline__ void setup_member(const ShadeArgs& a, const RenderParams& p, int slot, Member& mb,
-                                             float3& L, const float4 bt) {
+__device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs& p, const SceneDev& sc, int slot,
+                                             Member& mb, float3& L, const float4 bt) {
     const int2 h = a.hit[slot];
     const float4 d4 = a.ray_d[slot];
-    if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&a.tris[3 * h.x]).w) : -1;
+    if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
     if (h.x < 0) { // miss: environment
-        L.x = fa(L.x, fm(bt.x, a.env[0]));
-        L.y = fa(L.y, fm(bt.y, a.env[1]));
-        L.z = fa(L.z, fm(bt.z, a.env[2]));
+        L.x = fa(L.x, fm(bt.x, sc.env[0]));
+        L.y = fa(L.y, fm(bt.y, sc.env[1]));
+        L.z = fa(L.z, fm(bt.z, sc.env[2]));
         mb.alive = false;
         return;
     }
-    const float4 v0 = __ldg(&a.tris[3 * h.x + 0]);
-    const float4 v1 = __ldg(&a.tris[3 * h.x + 1]);
-    const float4 v2 = __ldg(&a.tris[3 * h.x + 2]);
+    const float4 v0 = __ldg(&sc.tris[3 * h.x + 0]);
+    const float4 v1 = __ldg(&sc.tris[3 * h.x + 1]);
+    const float4 v2 = __ldg(&sc.tris[3 * h.x + 2]);
     const int mat = __float_as_int(v1.w);
-    const float4 m0 = __ldg(&a.mats[2 * mat + 0]);
-    const float4 m1 = __ldg(&a.mats[2 * mat + 1]);
+    const float4 m0 = __ldg(&sc.mats[2 * mat + 0]);
+    const float4 m1 = __ldg(&sc.mats[2 * mat + 1]);
     const uint32_t type = (uint32_t)__float_as_int(m0.x);
     mb.orig = __float_as_int(v0.w);
     if (type == kMatEmitter) {
@@ -168,7 +192,7 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const RenderPar
         mb.alive = false;
         return;
     }
-    if (p.final_pass) {
+    if (mb.final_pass) {
         mb.alive = false;
         return;
     }
@@ -184,7 +208,7 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const RenderPar
     mb.albedo[1] = m0.z;
     mb.albedo[2] = m0.w;
     // the member's own BSDF sample, drawn from its pixel's stream
-    const uint4 r = philox_seed(p.seed, (uint32_t)mb.pix, p.frame, p.bounce, kTagBsdf);
+    const uint4 r = philox_seed(mb.seed, (uint32_t)mb.pix, mb.frame, p.bounce, kTagBsdf);
     const float u1 = unit24(r.x), u2 = unit24(r.y);
     if (type == kMatLambert) {
         mb.wl = sample_cosine(u1, u2);
@@ -211,9 +235,9 @@ __device__ __forceinline__ void take_dir(Member& mb, V3 wl) {
     mb.valid = true;
 }
 
-__device__ __forceinline__ void finish_member(const ShadeArgs& a, const RenderParams& p, int slot, Member& mb,
+__device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs& p, int slot, Member& mb,
                                               float3 L, float4 bt, bool was_alive, int cat) {
-    if (a.dbg.cat && mb.pix >= 0 && !p.final_pass) {
+    if (a.dbg.cat && mb.pix >= 0 && !mb.final_pass) {
         const uint32_t di = (p.bounce - 1) * a.npx + (uint32_t)mb.pix;
         a.dbg.cat[di] = (uint8_t)cat;
         a.dbg.cls[di] = (uint8_t)(mb.alive ? mb.cls : kClsNone);
@@ -252,7 +276,7 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const RenderPa
 // K <= 32: a group is a K-lane segment of a warp; votes by ballot, the donor's direction by
 // shuffle, the hybrid sum by an xor butterfly (which equals the pairwise tree sum in every
 // lane because float addition is commutative).
-__global__ void k_shade_warp(ShadeArgs a, RenderParams p) {
+__global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     const uint32_t K = p.k;
     const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,28 +292,41 @@ __global__ void k_shade_warp(ShadeArgs a, RenderParams p) {
     bool was_alive = false;
     float4 bt = make_float4(0, 0, 0, 0);
     float3 L = make_float3(0, 0, 0);
+    mb.final_pass = true;
+    mb.reuse = false;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
         mb.pix = a.pixel[slot];
+        const JobDev* Jp = nullptr;
+        if (mb.pix >= 0) { // every valid slot knows whether its job is past its last bounce
+            Jp = &a.jobs[a.slot_job[slot]];
+            mb.final_pass = p.bounce > Jp->max_bounces;
+            mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
+            mb.seed = Jp->seed;
+            mb.frame = Jp->frame;
+        }
         was_alive = mb.pix >= 0 && a.alive[slot];
         if (was_alive) {
+            const JobDev& J = *Jp;
             mb.alive = true;
             bt = a.beta[slot];
             const float4 r4 = a.radiance[slot];
             L = make_float3(r4.x, r4.y, r4.z);
-            setup_member(a, p, slot, mb, L, bt);
+            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
         }
     }
     int cat = kCatEmpty;
-    if (!p.final_pass) {
+    {
         const uint32_t lane = threadIdx.x & 31u;
         const uint32_t seg = lane & ~(K - 1u);
         const uint32_t segmask = K == 32u ? 0xffffffffu : (((1u << K) - 1u) << seg);
         const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse) & segmask;
         const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy) & segmask;
         cat = bd && bg ? kCatHybrid : (bd ? kCatDiffuse : (bg ? kCatGlossy : kCatEmpty));
-        if (p.reuse) {
+        // reuse is uniform within a group (one job); the shuffles run in every lane of a
+        // warp that has any reusing lane
+        if (__any_sync(0xffffffffu, mb.reuse)) {
             const int donor = bd ? __ffs(bd) - 1 : (int)lane;
             const V3 wd = v3(__shfl_sync(0xffffffffu, mb.wl.x, donor), __shfl_sync(0xffffffffu, mb.wl.y, donor),
                              __shfl_sync(0xffffffffu, mb.wl.z, donor));
@@ -301,7 +338,7 @@ __global__ void k_shade_warp(ShadeArgs a, RenderParams p) {
                 const float sz = __shfl_xor_sync(0xffffffffu, s.z, off);
                 s = v3(fa(s.x, sx), fa(s.y, sy), fa(s.z, sz));
             }
-            if (mb.alive && mb.cls == kClsDiffuse) {
+            if (mb.reuse && mb.alive && mb.cls == kClsDiffuse) {
                 if (cat == kCatDiffuse) {
                     take_dir(mb, wd);
                 } else if (cat == kCatHybrid) {
@@ -322,7 +359,7 @@ __global__ void k_shade_warp(ShadeArgs a, RenderParams p) {
 // 32 < K <= 256: a group spans K/32 warps of a 256-thread block; per-warp ballots and the
 // members' samples go through shared memory and the hybrid sum is a pairwise tree over the
 // group's slots.
-__global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, RenderParams p) {
+__global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     __shared__ uint32_t s_bd[8], s_bg[8];
     __shared__ float s_own[3][256];
     __shared__ float s_sum[3][256];
@@ -341,21 +378,32 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, RenderParams p
     bool was_alive = false;
     float4 bt = make_float4(0, 0, 0, 0);
     float3 L = make_float3(0, 0, 0);
+    mb.final_pass = true;
+    mb.reuse = false;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
         mb.pix = a.pixel[slot];
+        const JobDev* Jp = nullptr;
+        if (mb.pix >= 0) { // every valid slot knows whether its job is past its last bounce
+            Jp = &a.jobs[a.slot_job[slot]];
+            mb.final_pass = p.bounce > Jp->max_bounces;
+            mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
+            mb.seed = Jp->seed;
+            mb.frame = Jp->frame;
+        }
         was_alive = mb.pix >= 0 && a.alive[slot];
         if (was_alive) {
+            const JobDev& J = *Jp;
             mb.alive = true;
             bt = a.beta[slot];
             const float4 r4 = a.radiance[slot];
             L = make_float3(r4.x, r4.y, r4.z);
-            setup_member(a, p, slot, mb, L, bt);
+            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
         }
     }
     int cat = kCatEmpty;
-    if (!p.final_pass) {
+    {
         const uint32_t t = threadIdx.x, w = t >> 5;
         const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse);
         const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy);
@@ -380,7 +428,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, RenderParams p
             any_g |= s_bg[ww] != 0;
         }
         cat = any_d && any_g ? kCatHybrid : (any_d ? kCatDiffuse : (any_g ? kCatGlossy : kCatEmpty));
-        if (p.reuse) {
+        if (__syncthreads_or(mb.reuse)) {
             for (uint32_t stride = 1; stride < K; stride <<= 1) {
                 if ((t - gbase) % (2u * stride) == 0) {
                     s_sum[0][t] = fa(s_sum[0][t], s_sum[0][t + stride]);
@@ -389,7 +437,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, RenderParams p
                 }
                 __syncthreads();
             }
-            if (mb.alive && mb.cls == kClsDiffuse) {
+            if (mb.reuse && mb.alive && mb.cls == kClsDiffuse) {
                 const V3 wd = v3(s_own[0][donor], s_own[1][donor], s_own[2][donor]);
                 if (cat == kCatDiffuse) {
                     take_dir(mb, wd);
@@ -538,15 +586,25 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_scatter(const int32_t
 // quantised in the scene box; then a stable LSD radix sort of (key, slot).
 __global__ void k_morton(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                          const int32_t* __restrict__ queue, const uint32_t* __restrict__ count, uint32_t n_max,
-                         float3 lo, float3 scale, float len, uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+                         const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
+                         uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
     const uint32_t n = min(*count, n_max);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int slot = queue[i];
+    const SceneDev& sc = scenes[slot_scene[slot]];
+    float l[3], s[3], emax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float ext = sc.hi[k] - sc.lo[k];
+        l[k] = sc.lo[k];
+        s[k] = ext > 0.0f ? 32.0f / ext : 0.0f;
+        emax = fmaxf(emax, ext);
+    }
+    const float len = 0.25f * emax;
     const float4 o = ray_o[slot], d = ray_d[slot];
     const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z) * len;
     const float p[6] = {o.x, o.y, o.z, o.x + d.x * il, o.y + d.y * il, o.z + d.z * il};
-    const float l[3] = {lo.x, lo.y, lo.z}, s[3] = {scale.x, scale.y, scale.z};
     uint32_t q[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -682,21 +740,46 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 }
 
 // ------------------------------------------------------------------------------------
-__global__ void k_accumulate(const int32_t* __restrict__ pixel, const float4* __restrict__ radiance, uint32_t n_slots,
+__global__ void k_accumulate(const int32_t* __restrict__ pixel, const uint16_t* __restrict__ slot_job,
+                             const JobDev* __restrict__ jobs, const float4* __restrict__ radiance, uint32_t n_slots,
                              float4* __restrict__ accum) {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
     const int pix = pixel[s];
     if (pix < 0) return;
     const float4 l = radiance[s];
-    float4 a = accum[pix];
+    const uint32_t at = jobs[slot_job[s]].px_base + (uint32_t)pix;
+    float4 a = accum[at];
     a.x += l.x;
     a.y += l.y;
     a.z += l.z;
-    accum[pix] = a;
+    accum[at] = a;
 }
 
-__global__ void k_output(const float4* __restrict__ accum, uint32_t npx, float inv_spp, float* __restrict__ out) {
+// Job of an accumulation pixel: the last job whose first pixel is <= i.
+__device__ __forceinline__ uint32_t job_of_pixel(const JobDev* jobs, uint32_t n_jobs, uint32_t i) {
+    uint32_t lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].px_base <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_output(const JobDev* __restrict__ jobs, uint32_t n_jobs, const float4* __restrict__ accum,
+                         uint32_t npx_total) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx_total) return;
+    const JobDev& J = jobs[job_of_pixel(jobs, n_jobs, i)];
+    const uint32_t p = i - J.px_base;
+    const float4 a = accum[i];
+    J.out[3 * p + 0] = a.x * J.inv_spp;
+    J.out[3 * p + 1] = a.y * J.inv_spp;
+    J.out[3 * p + 2] = a.z * J.inv_spp;
+}
+
+__global__ void k_output_one(const float4* __restrict__ accum, uint32_t npx, float inv_spp, float* __restrict__ out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npx) return;
     const float4 a = accum[i];
@@ -751,29 +834,27 @@ __global__ void k_sample(uint32_t kind, uint32_t n, const float* __restrict__ wo
 
 // ------------------------------------------------------------------------------------
 // Launchers.
-void launch_raygen(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
+void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
     const uint32_t block = p.m > 256 ? p.m : 256;
     const uint32_t tiles_per_block = block / p.m;
-    const uint32_t n_tiles = p.tiles_x * p.tiles_y;
-    const uint32_t grid = (n_tiles + tiles_per_block - 1) / tiles_per_block;
-    k_raygen<<<grid, block, block * sizeof(uint16_t), st>>>(p, b.pixel, b.ray_o, b.ray_d, b.beta, b.radiance, b.alive);
+    const uint32_t grid = (p.n_tiles + tiles_per_block - 1) / tiles_per_block;
+    k_raygen<<<grid, block, block * sizeof(uint16_t), st>>>(p, b.pixel, b.slot_job, b.slot_scene, b.ray_o, b.ray_d,
+                                                             b.beta, b.radiance, b.alive);
     lc.n++;
 }
 
-void launch_groups(const RenderParams& p, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc) {
-    const uint32_t npx = p.cam.width * p.cam.height;
-    k_groups<<<(npx + 255) / 256, 256, 0, st>>>(p, slot_of_pixel);
+void launch_groups(const CamBasis& cam, uint32_t tile_w, uint32_t tile_h, uint32_t interleave, uint64_t seed,
+                   uint32_t frame, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc) {
+    const uint32_t npx = cam.width * cam.height;
+    k_groups<<<(npx + 255) / 256, 256, 0, st>>>(cam, tile_w, tile_h, interleave, seed, frame, slot_of_pixel);
     lc.n++;
 }
 
-static ShadeArgs shade_args(const DevScene& s, PathBuffers& b, bool first, uint32_t bounce, const cr_debug* dbg,
-                            uint32_t npx) {
+static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg) {
     ShadeArgs a;
-    a.tris = s.tris;
-    a.mats = s.mats;
-    a.env[0] = s.env[0];
-    a.env[1] = s.env[1];
-    a.env[2] = s.env[2];
+    a.jobs = p.jobs;
+    a.scenes = p.scenes;
+    a.slot_job = b.slot_job;
     a.pixel = b.pixel;
     a.ray_o = b.ray_o;
     a.ray_d = b.ray_d;
@@ -782,18 +863,18 @@ static ShadeArgs shade_args(const DevScene& s, PathBuffers& b, bool first, uint3
     a.radiance = b.radiance;
     a.alive = b.alive;
     // group queue written by the compaction after the previous shade (double-buffered)
-    a.group_queue = first ? nullptr : b.group_queue + (size_t)((bounce - 1) & 1) * b.n_groups;
-    a.group_count = first ? nullptr : b.counts + 8 + 2 * (bounce - 1) + 1;
+    a.group_queue = first ? nullptr : b.group_queue + (size_t)((p.bounce - 1) & 1) * b.n_groups;
+    a.group_count = first ? nullptr : b.counts + 8 + 2 * (p.bounce - 1) + 1;
     a.n_groups_max = b.n_groups;
     if (dbg) a.dbg = *dbg;
     else a.dbg = cr_debug{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    a.npx = npx;
+    a.npx = p.npx;
     return a;
 }
 
-void launch_shade(const DevScene& s, const RenderParams& p, PathBuffers& b, bool first, const cr_debug* dbg,
-                  cudaStream_t st, LaunchCount& lc) {
-    ShadeArgs a = shade_args(s, b, first, p.bounce, dbg, p.cam.width * p.cam.height);
+void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,
+                  LaunchCount& lc) {
+    ShadeArgs a = shade_args(p, b, first, dbg);
     const uint32_t n_pos = b.n_groups * p.k;
     if (p.k <= 32) {
         k_shade_warp<<<(n_pos + 127) / 128, 128, 0, st>>>(a, p);
@@ -803,7 +884,7 @@ void launch_shade(const DevScene& s, const RenderParams& p, PathBuffers& b, bool
     lc.n++;
 }
 
-void launch_compact(const RenderParams& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc) {
+void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc) {
     const uint32_t K = p.k;
     const uint32_t n_pos = b.n_groups * K;
     const uint32_t n_blocks = (n_pos + kCompactBlock - 1) / kCompactBlock;
@@ -819,13 +900,21 @@ void launch_compact(const RenderParams& p, PathBuffers& b, bool first, cudaStrea
     lc.n += 3;
 }
 
-void launch_accumulate(const RenderParams& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
-    k_accumulate<<<(b.n_slots + 255) / 256, 256, 0, st>>>(b.pixel, b.radiance, b.n_slots, b.accum);
+void launch_accumulate(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
+    const uint32_t n_slots = p.n_tiles * p.m;
+    k_accumulate<<<(n_slots + 255) / 256, 256, 0, st>>>(b.pixel, b.slot_job, p.jobs, b.radiance, n_slots, b.accum);
     lc.n++;
 }
 
-void launch_output(PathBuffers& b, uint32_t npx, float inv_spp, float* out_rgb, cudaStream_t st, LaunchCount& lc) {
-    k_output<<<(npx + 255) / 256, 256, 0, st>>>(b.accum, npx, inv_spp, out_rgb);
+void launch_output(const JobDev* jobs, uint32_t n_jobs, const float4* accum, uint32_t npx_total, cudaStream_t st,
+                   LaunchCount& lc) {
+    k_output<<<(npx_total + 255) / 256, 256, 0, st>>>(jobs, n_jobs, accum, npx_total);
+    lc.n++;
+}
+
+void launch_output_one(const float4* accum, uint32_t npx, float inv_spp, float* out, cudaStream_t st, LaunchCount& lc) {
+    if (!npx) return;
+    k_output_one<<<(npx + 255) / 256, 256, 0, st>>>(accum, npx, inv_spp, out);
     lc.n++;
 }
 
@@ -843,24 +932,16 @@ void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, c
 }
 
 // Sort the current bounce's ray queue by TwoPoint key; returns the sorted slot queue.
-const int32_t* launch_morton_sort(const DevScene& s, PathBuffers& b, uint32_t bounce, cudaStream_t st,
+const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, cudaStream_t st,
                                   LaunchCount& lc) {
     const uint32_t n_max = b.n_slots;
     const uint32_t* count = b.counts + 8 + 2 * bounce;
-    float ext[3], scale[3];
-    float emax = 0.0f;
-    for (int k = 0; k < 3; ++k) {
-        ext[k] = s.hi[k] - s.lo[k];
-        emax = ext[k] > emax ? ext[k] : emax;
-    }
-    for (int k = 0; k < 3; ++k) scale[k] = ext[k] > 0.0f ? 32.0f / ext[k] : 0.0f;
     uint32_t* ka = b.keys;
     uint32_t* kb = b.keys + n_max;
     int32_t* va = b.vals;
     int32_t* vb = b.vals + n_max;
-    k_morton<<<(n_max + 255) / 256, 256, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max,
-                                                  make_float3(s.lo[0], s.lo[1], s.lo[2]),
-                                                  make_float3(scale[0], scale[1], scale[2]), 0.25f * emax, ka, va);
+    k_morton<<<(n_max + 255) / 256, 256, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max, p.scenes,
+                                                  b.slot_scene, ka, va);
     lc.n++;
     const uint32_t n_blocks = (n_max + kSortTile - 1) / kSortTile;
     for (uint32_t pass = 0; pass < 4; ++pass) {

@@ -178,7 +178,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
 }
 
 template <bool kCount>
-__global__ void k_trace_bvh2(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+__global__ void k_trace_bvh2(const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
                              const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                              const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
                              uint32_t n_max, int2* __restrict__ hit, unsigned long long* counters) {
@@ -188,10 +188,12 @@ __global__ void k_trace_bvh2(const float4* __restrict__ nodes, const float4* __r
     unsigned long long n_node = 0, n_tri = 0;
     if (i < n) {
         const int slot = queue ? queue[i] : (int)i;
+        const SceneDev& sc = scenes[slot_scene ? slot_scene[slot] : 0];
         const float4 ro = ray_o[slot];
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
-        if (rd.w >= 0.0f) h = trace_bvh2_one<kCount>(nodes, tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+        if (rd.w >= 0.0f)
+            h = trace_bvh2_one<kCount>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
         hit[slot] = h;
     }
     if (kCount) {
@@ -217,7 +219,7 @@ constexpr uint32_t kChunk = 256;
 constexpr int kDone = 0x7fffffff;
 
 __global__ void __launch_bounds__(128) k_trace_bvh2_dynamic(
-    const float4* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ ray_o,
+    const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, const float4* __restrict__ ray_o,
     const float4* __restrict__ ray_d, const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
     uint32_t n_max, int2* __restrict__ hit, uint32_t* work, uint32_t refill) {
     extern __shared__ uint32_t smem_stack[];
@@ -231,6 +233,8 @@ __global__ void __launch_bounds__(128) k_trace_bvh2_dynamic(
     bool live = false;
     RayPre r;
     int skip = -1, node = kDone, sp = 0, slot = -1;
+    const float4* nodes = nullptr;
+    const float4* tris = nullptr;
     Best best{0.0f, -1, 0x7fffffff};
     int lstack[kStackTotal - kSmemStack];
     unsigned long long dummy = 0;
@@ -259,6 +263,9 @@ __global__ void __launch_bounds__(128) k_trace_bvh2_dynamic(
                         const float4 ro = ray_o[slot];
                         const float4 rd = ray_d[slot];
                         if (rd.w >= 0.0f) {
+                            const SceneDev& sc = scenes[slot_scene ? slot_scene[slot] : 0];
+                            nodes = sc.nodes2;
+                            tris = sc.tris;
                             r = prep_ray(ro, rd);
                             skip = __float_as_int(ro.w);
                             best = Best{rd.w, -1, 0x7fffffff};
@@ -401,7 +408,8 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(128, 8) k_trace_bvh8(const uint4* __restrict__ nodes, const float4* __restrict__ tris,
+__global__ void __launch_bounds__(128, 8) k_trace_bvh8(const SceneDev* __restrict__ scenes,
+                             const uint16_t* __restrict__ slot_scene,
                              const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                              const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
                              uint32_t n_max, int2* __restrict__ hit, unsigned long long* counters) {
@@ -411,10 +419,12 @@ __global__ void __launch_bounds__(128, 8) k_trace_bvh8(const uint4* __restrict__
     unsigned long long n_node = 0, n_tri = 0;
     if (i < n) {
         const int slot = queue ? queue[i] : (int)i;
+        const SceneDev& sc = scenes[slot_scene ? slot_scene[slot] : 0];
         const float4 ro = ray_o[slot];
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
-        if (rd.w >= 0.0f) h = trace_bvh8_one<kCount>(nodes, tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+        if (rd.w >= 0.0f)
+            h = trace_bvh8_one<kCount>(sc.nodes8, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
         hit[slot] = h;
     }
     if (kCount) {
@@ -456,7 +466,22 @@ void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, f
     lc.n++;
 }
 
-void launch_trace(const DevScene& s, const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
+SceneDev scene_entry(const DevScene& s, bool bvh8) {
+    SceneDev e;
+    e.nodes2 = s.nodes2;
+    e.nodes8 = s.nodes8;
+    e.tris = bvh8 ? s.tris8 : s.tris;
+    e.mats = s.mats;
+    for (int k = 0; k < 3; ++k) {
+        e.env[k] = s.env[k];
+        e.lo[k] = s.lo[k];
+        e.hi[k] = s.hi[k];
+    }
+    e.env[3] = e.lo[3] = e.hi[3] = 0.0f;
+    return e;
+}
+
+void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
     if (a.n_max == 0) return;
     const int block = a.block;
     const size_t smem = (size_t)kSmemStack * block * sizeof(uint32_t);
@@ -464,10 +489,10 @@ void launch_trace(const DevScene& s, const TraceArgs& a, cudaStream_t st, Launch
     if (a.bvh8) {
         const uint32_t grid = (a.n_max + block - 1) / block;
         if (a.counters)
-            k_trace_bvh8<true><<<grid, block, smem, st>>>(s.nodes8, s.tris, a.ray_o, a.ray_d, a.queue, a.queue_count,
-                                                          a.n_max, a.hit, a.counters);
+            k_trace_bvh8<true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
+                                                          a.queue_count, a.n_max, a.hit, a.counters);
         else
-            k_trace_bvh8<false><<<grid, block, smem, st>>>(s.nodes8, s.tris, a.ray_o, a.ray_d, a.queue,
+            k_trace_bvh8<false><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
                                                            a.queue_count, a.n_max, a.hit, nullptr);
         lc.n++;
         return;
@@ -480,24 +505,24 @@ void launch_trace(const DevScene& s, const TraceArgs& a, cudaStream_t st, Launch
         const uint32_t grid_max = (uint32_t)sms * (uint32_t)(per_sm > 0 ? per_sm : 1);
         const uint32_t need = (a.n_max + 127) / 128;
         k_trace_bvh2_dynamic<<<need < grid_max ? need : grid_max, 128, smem128, st>>>(
-            s.nodes2, s.tris, a.ray_o, a.ray_d, a.queue, a.queue_count, a.n_max, a.hit, a.work_counter,
+            a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue, a.queue_count, a.n_max, a.hit, a.work_counter,
             a.refill == 0 ? 8u : (a.refill > 32u ? 32u : a.refill));
     } else {
         const uint32_t grid = (a.n_max + block - 1) / block;
         if (a.counters)
-            k_trace_bvh2<true><<<grid, block, smem, st>>>(s.nodes2, s.tris, a.ray_o, a.ray_d, a.queue, a.queue_count,
-                                                          a.n_max, a.hit, a.counters);
+            k_trace_bvh2<true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
+                                                          a.queue_count, a.n_max, a.hit, a.counters);
         else
-            k_trace_bvh2<false><<<grid, block, smem, st>>>(s.nodes2, s.tris, a.ray_o, a.ray_d, a.queue,
+            k_trace_bvh2<false><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
                                                            a.queue_count, a.n_max, a.hit, nullptr);
     }
     lc.n++;
 }
 
-void launch_hits_to_user(const DevScene& s, const int2* hit, uint32_t n, int32_t* prim, float* t, cudaStream_t st,
+void launch_hits_to_user(const float4* tris, const int2* hit, uint32_t n, int32_t* prim, float* t, cudaStream_t st,
                          LaunchCount& lc) {
     if (n == 0) return;
-    k_hits_to_user<<<(n + 255) / 256, 256, 0, st>>>(s.tris, hit, n, prim, t);
+    k_hits_to_user<<<(n + 255) / 256, 256, 0, st>>>(tris, hit, n, prim, t);
     lc.n++;
 }
 

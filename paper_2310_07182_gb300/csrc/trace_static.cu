@@ -96,6 +96,7 @@ extern "C" cr_status cr_trace_rays_static(cr_scene* scene, const float* rays, co
     int2* hit = reinterpret_cast<int2*>(b + kOffHit);
     const DevScene& ds = *dev_scene_of(scene);
     LaunchCount lc;
+    // the scene's device table entry was made by cr_scene_create, so nothing is allocated here
     // every scratch record read below is written first by this call, so nothing needs clearing
     launch_rays_from_user(rays, skip_prim, n, ro, rd, st, lc);
     TraceArgs ta;
@@ -104,8 +105,9 @@ extern "C" cr_status cr_trace_rays_static(cr_scene* scene, const float* rays, co
     ta.hit = hit;
     ta.n_max = n;
     ta.block = 128;
-    launch_trace(ds, ta, st, lc);
-    launch_hits_to_user(ds, hit, n, prim, t, st, lc);
+    ta.scenes = dev_scene_entry(scene, false);
+    launch_trace(ta, st, lc);
+    launch_hits_to_user(ds.tris, hit, n, prim, t, st, lc);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {

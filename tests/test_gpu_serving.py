@@ -1,0 +1,101 @@
+"""Serving with continuous batching: requests of several scenes, sizes, spp and bounce counts
+submitted while others render; each result must equal its stand-alone render (same tile
+shape, K and interleave) bit for bit, alone or in the mix, with host or device outputs."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_07182_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    from paper_2310_07182_gb300 import binding
+    binding.lib()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def world(cr):
+    sc = {"tiny": scenes.tiny(material_mix="mixed", n_soup=3000), "furnace": scenes.furnace(),
+          "interior": scenes.interior(n_spheres=300, width=96, height=64)}
+    S = {k: cr.Scene(v, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q) for k, v in sc.items()}
+    return sc, S
+
+
+def _cam(c, w, h):
+    return scenes.Camera(c.pos, c.look_at, c.up, c.vfov_deg, w, h)
+
+
+def _requests(rng, n):
+    names = ["tiny", "furnace", "interior"]
+    modes = ["direction_reuse", "independent", "morton_sort"]
+    out = []
+    for i in range(n):
+        out.append(dict(name=names[i % 3], w=int(rng.integers(8, 120)), h=int(rng.integers(8, 90)),
+                        spp=int(rng.choice([1, 2, 4, 7])), B=int(rng.integers(1, 5)), mode=modes[(i // 3) % 3],
+                        seed=int(rng.integers(0, 1000)), fb=int(rng.integers(0, 50))))
+    return out
+
+
+@pytest.mark.parametrize("bvh", [1, 2])
+def test_results_equal_standalone_in_the_mix(cr, world, bvh):
+    sc, S = world
+    rng = np.random.default_rng(bvh)
+    reqs = _requests(rng, 24)
+    srv = cr.cr_server_create(512 << 20, tile=(8, 8), k=8, bvh=bvh)
+    try:
+        ids, outs = [], []
+        for i, r in enumerate(reqs):
+            cam = _cam(sc[r["name"]].camera, r["w"], r["h"])
+            out = (np.full((r["h"], r["w"], 3), -1, np.float32) if i % 2 else
+                   torch.full((r["h"], r["w"], 3), -1.0, device="cuda"))
+            outs.append(out)
+            j = cr.make_job(S[r["name"]].handle, cam, out, spp=r["spp"], max_bounces=r["B"], mode=r["mode"],
+                            seed=r["seed"], frame_base=r["fb"])
+            ids.append(cr.cr_server_submit(srv, j))
+            if i % 5 == 0:
+                time.sleep(0.002)  # requests keep arriving while earlier ones render
+        lat = [cr.cr_server_wait(srv, jid, 60000) for jid in ids]
+        st = cr.cr_server_get_stats(srv)
+        assert st["jobs_done"] == len(reqs) and st["passes"] >= max(r["spp"] for r in reqs)
+        assert st["passes"] < sum(r["spp"] for r in reqs)  # jobs shared passes
+        for r, out, l in zip(reqs, outs, lat):
+            cam = _cam(sc[r["name"]].camera, r["w"], r["h"])
+            ref, _ = S[r["name"]].render(cam, spp=r["spp"], max_bounces=r["B"], mode=r["mode"], tile=(8, 8), k=8,
+                                         seed=r["seed"], frame_base=r["fb"], bvh=bvh)
+            got = out if isinstance(out, np.ndarray) else out.cpu().numpy()
+            assert np.array_equal(got, ref.cpu().numpy())
+            assert l["latency_ms"] >= 0 and l["samples"] == r["spp"]
+        with pytest.raises(cr.CrError) as ei:
+            cr.cr_server_wait(srv, ids[0], 10)  # already collected
+        assert ei.value.status == cr.CR_ERR_NOT_FOUND
+    finally:
+        cr.cr_server_destroy(srv)
+
+
+def test_admission_by_footprint(cr, world):
+    """A budget that holds only a few jobs at a time still completes all of them, and a job
+    larger than the whole budget is refused at submission."""
+    sc, S = world
+    srv = cr.cr_server_create(64 << 20, tile=(8, 8), k=8)
+    try:
+        cam = _cam(sc["tiny"].camera, 256, 256)
+        outs = [torch.empty((256, 256, 3), device="cuda") for _ in range(6)]
+        ids = [cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, cam, o, spp=3, max_bounces=2, seed=i))
+               for i, o in enumerate(outs)]
+        stats = [cr.cr_server_wait(srv, i, 60000) for i in ids]
+        admits = sorted(s["t_admit_ms"] for s in stats)
+        dones = sorted(s["t_done_ms"] for s in stats)
+        assert admits[-1] >= dones[0]  # the last admission waited for a completion
+        big = cr.make_job(S["tiny"].handle, _cam(sc["tiny"].camera, 4096, 4096), torch.empty(1, device="cuda"))
+        with pytest.raises(cr.CrError) as ei:
+            cr.cr_server_submit(srv, big)
+        assert ei.value.status == cr.CR_ERR_OOM
+    finally:
+        cr.cr_server_destroy(srv)
