@@ -140,7 +140,10 @@ enum {
     CR_OPT_STATS = 1u,      /* record per-stage CUDA events (adds event records between launches) */
     CR_OPT_COUNT = 2u,      /* counting pass: count node visits / triangle tests (slower) */
     CR_OPT_NO_SYNC = 4u,    /* return without synchronising the stream (device out_rgb only) */
-    CR_OPT_PERSISTENT = 8u  /* persistent trace kernel with an atomic ray counter */
+    CR_OPT_PERSISTENT = 8u, /* persistent trace kernel with dynamic ray fetch (BVH2) */
+    CR_OPT_SPECULATIVE = 16u, /* speculative traversal with a parked leaf per lane (BVH2) */
+    CR_OPT_PACKET_PRIMARY = 32u,  /* warp-packet traversal of primary rays (BVH2) */
+    CR_OPT_PACKET_SECONDARY = 64u /* warp-packet traversal of secondary rays (BVH2) */
 };
 
 typedef struct {

@@ -585,6 +585,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
     ta.hit = b.hit;
     ta.block = eo.block;
     ta.persistent = eo.persistent;
+    ta.speculative = eo.speculative;
     ta.work_counter = b.counts + 2;
     ta.bvh8 = p.bvh8;
     ta.scenes = dev.d_scenes;
@@ -611,9 +612,11 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         ta.n_max = n_slots;
         ta.counters = nullptr;
         if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
+        ta.packet = eo.packet_primary;
         ev.begin(stream, times ? &times->trace_primary : &dummy);
         launch_trace(ta, stream, lc);
         ev.end();
+        ta.packet = eo.packet_secondary;
         for (uint32_t bnc = 1; bnc <= p.max_bounces; ++bnc) {
             P.bounce = bnc;
             ev.begin(stream, times ? &times->shade : &dummy);
@@ -716,6 +719,9 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     ExecOpts eo;
     eo.block = block;
     eo.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
+    eo.speculative = (o.flags & CR_OPT_SPECULATIVE) != 0;
+    eo.packet_primary = (o.flags & CR_OPT_PACKET_PRIMARY) != 0;
+    eo.packet_secondary = (o.flags & CR_OPT_PACKET_SECONDARY) != 0;
     eo.count = (o.flags & CR_OPT_COUNT) != 0;
     eo.debug = o.debug;
     eo.debug_npx = npx;
@@ -849,6 +855,8 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     ta.n_max = n;
     ta.block = block;
     ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
+    ta.speculative = (o.flags & CR_OPT_SPECULATIVE) != 0;
+    ta.packet = (o.flags & (CR_OPT_PACKET_PRIMARY | CR_OPT_PACKET_SECONDARY)) != 0;
     ta.bvh8 = use8;
     ta.scenes = dev_scene_entry(s, use8);
     ta.slot_scene = nullptr;

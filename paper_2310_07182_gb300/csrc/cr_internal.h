@@ -138,6 +138,8 @@ struct TraceArgs {
     int block = 128;
     uint32_t refill = 0; // persistent mode: refill a warp's idle lanes when at least this many (0 = 8)
     bool persistent = false;
+    bool speculative = false; // parked-leaf speculative traversal (BVH2)
+    bool packet = false;      // warp-packet traversal (BVH2)
     bool bvh8 = false;
 };
 void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
@@ -242,7 +244,8 @@ struct Plan {
 };
 struct ExecOpts {
     int block = 128;
-    bool persistent = false, count = false;
+    bool persistent = false, count = false, speculative = false;
+    bool packet_primary = false, packet_secondary = false; // warp-packet traversal per ray kind
     bool clear_accum = true; // zero the accumulation buffer first
     bool write_output = true; // write every job's output after the last pass
     const cr_debug* debug = nullptr;

@@ -31,6 +31,10 @@ struct RayPre {
     int kx, ky, kz;
     float sx, sy, sz; // shear constants of the watertight test
     float dx, dy, dz;
+    // slab offsets for t = fma(plane, 1/d, offset): -o/d biased outward by 2^-22 |o/d|, which
+    // bounds the rounding of o/d and of the offset, so the FMA interval contains the one the
+    // exact (plane - o) / d form gives (see box_entry_fma)
+    float lox, loy, loz, hix, hiy, hiz;
 };
 
 __device__ __forceinline__ float sel3(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
@@ -63,6 +67,17 @@ __device__ __forceinline__ RayPre prep_ray(float4 o, float4 d) {
     r.sx = sel3(d.x, d.y, d.z, kx) / dkz;
     r.sy = sel3(d.x, d.y, d.z, ky) / dkz;
     r.sz = 1.0f / dkz;
+    // plane of the lower bound enters first when 1/d >= 0; bias each offset so that the
+    // entry distance can only decrease and the exit distance only increase
+    const float oix = __fmul_rn(r.ox, r.ix), oiy = __fmul_rn(r.oy, r.iy), oiz = __fmul_rn(r.oz, r.iz);
+    const float ex = __fmul_rn(fabsf(oix), 0x1.0p-22f), ey = __fmul_rn(fabsf(oiy), 0x1.0p-22f),
+                ez = __fmul_rn(fabsf(oiz), 0x1.0p-22f);
+    r.lox = r.ix >= 0.0f ? -oix - ex : -oix + ex;
+    r.hix = r.ix >= 0.0f ? -oix + ex : -oix - ex;
+    r.loy = r.iy >= 0.0f ? -oiy - ey : -oiy + ey;
+    r.hiy = r.iy >= 0.0f ? -oiy + ey : -oiy - ey;
+    r.loz = r.iz >= 0.0f ? -oiz - ez : -oiz + ez;
+    r.hiz = r.iz >= 0.0f ? -oiz + ez : -oiz - ez;
     return r;
 }
 
@@ -74,6 +89,43 @@ __device__ __forceinline__ float box_entry(const RayPre& r, float lox, float hix
     const float tz0 = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), tz1 = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
     const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
     const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    return (tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull) ? tn : INFINITY;
+}
+
+// The same test with one FMA per plane.  Each plane distance fma(x, 1/d, offset) differs
+// from (x - o) * (1/d) by at most the rounding of o/d and of the offset (<= 2^-23 |o/d|) plus a
+// relative 2^-24; the offsets are pre-biased by 2^-22 |o/d| toward a larger interval and the
+// exit is widened by (1 + 2^-21), so no box that the exact form would enter is rejected.
+#ifndef CR_TRACE_MINMAX3
+#define CR_TRACE_MINMAX3 1
+#endif
+// three-input min / max (one instruction each on sm_100 and later)
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+#if CR_TRACE_MINMAX3
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+#else
+    return fminf(fminf(a, b), c);
+#endif
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+#if CR_TRACE_MINMAX3
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+#else
+    return fmaxf(fmaxf(a, b), c);
+#endif
+}
+
+__device__ __forceinline__ float box_entry_fma(const RayPre& r, float lox, float hix, float loy, float hiy, float loz,
+                                               float hiz, float tcull) {
+    const float tx0 = fmaf(lox, r.ix, r.lox), tx1 = fmaf(hix, r.ix, r.hix);
+    const float ty0 = fmaf(loy, r.iy, r.loy), ty1 = fmaf(hiy, r.iy, r.hiy);
+    const float tz0 = fmaf(loz, r.iz, r.loz), tz1 = fmaf(hiz, r.iz, r.hiz);
+    const float tn = max3f(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = min3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fmaxf(tz0, tz1));
     return (tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull) ? tn : INFINITY;
 }
 
@@ -128,6 +180,28 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
     }
 }
 
+#ifndef CR_TRACE_LOCAL_STACK
+#define CR_TRACE_LOCAL_STACK 0
+#endif
+#if CR_TRACE_LOCAL_STACK
+// whole stack in a per-thread local array (L1-resident); depth < kStackTotal by construction
+#define STACK_PUSH(v) (lstack_all[sp++] = (v))
+#define STACK_POP(v) ((v) = lstack_all[--sp])
+#else
+// first kSmemStack entries in shared memory, the rest in a local array
+#define STACK_PUSH(v)                                                                \
+    do {                                                                             \
+        if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)(v);                    \
+        else if (sp < kStackTotal) lstack[sp - kSmemStack] = (v);                   \
+        sp = sp < kStackTotal ? sp + 1 : sp; /* the builder keeps depth < kStackTotal */ \
+    } while (0)
+#define STACK_POP(v)                                                                 \
+    do {                                                                             \
+        --sp;                                                                        \
+        (v) = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack]; \
+    } while (0)
+#endif
+
 template <bool kCount>
 __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
@@ -135,10 +209,15 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
     const RayPre r = prep_ray(ro, rd);
     const int skip = __float_as_int(ro.w);
     Best best{rd.w, -1, 0x7fffffff};
+#if CR_TRACE_LOCAL_STACK
+    int lstack_all[kStackTotal];
+    (void)sstack;
+#else
     int lstack[kStackTotal - kSmemStack];
+    const int stride = blockDim.x;
+#endif
     int sp = 0;
     int node = 0;
-    const int stride = blockDim.x;
     while (true) {
         while (node >= 0) {
             if (kCount) ++n_node;
@@ -147,23 +226,20 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
             const float4 n2 = __ldg(&nodes[4 * node + 2]);
             const float4 n3 = __ldg(&nodes[4 * node + 3]);
             const float tcull = __fmul_rn(best.t, kCullWiden);
-            const float t0 = box_entry(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
-            const float t1 = box_entry(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
+            const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
+            const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
             const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
             const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
             if (h0 && h1) {
                 const bool first0 = t0 <= t1;
                 const int near = first0 ? c0 : c1, far = first0 ? c1 : c0;
-                if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)far;
-                else if (sp < kStackTotal) lstack[sp - kSmemStack] = far;
-                sp = sp < kStackTotal ? sp + 1 : sp; // the builder keeps depth < kStackTotal
+                STACK_PUSH(far);
                 node = near;
             } else if (h0 || h1) {
                 node = h0 ? c0 : c1;
             } else {
                 if (sp == 0) { node = 0x7fffffff; break; }
-                --sp;
-                node = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
+                STACK_POP(node);
             }
         }
         if (node == 0x7fffffff) break;
@@ -171,14 +247,17 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
         const uint32_t code = (uint32_t)(~node);
         test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, n_tri);
         if (sp == 0) break;
-        --sp;
-        node = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
+        STACK_POP(node);
     }
     return make_int2(best.leaf, __float_as_int(best.t));
 }
 
+#ifndef CR_TRACE_MAXNREG
+#define CR_TRACE_MAXNREG 48 // caps registers so 10 blocks of 128 threads stay resident per SM
+#endif
+
 template <bool kCount>
-__global__ void k_trace_bvh2(const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
+__global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
                              const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                              const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
                              uint32_t n_max, int2* __restrict__ hit, unsigned long long* counters) {
@@ -205,6 +284,199 @@ __global__ void k_trace_bvh2(const SceneDev* __restrict__ scenes, const uint16_t
             atomicAdd(&counters[0], n_node);
             atomicAdd(&counters[1], n_tri);
         }
+    }
+}
+
+// Warp-packet variant: the 32 lanes of a warp traverse ONE node sequence.  At each inner
+// node every lane tests both child boxes against its own ray (with its own culling
+// distance); a child is entered if any lane's ray reaches it, nearer-first by majority.
+// Leaves are tested by every lane against its own ray.  Each lane therefore visits a
+// superset of the boxes its own ray enters, with the same triangle test and tie rule, so
+// the hits are the single-ray kernel's bit for bit.  Control flow is warp-uniform, which
+// pays off when the rays of a warp are coherent (primary rays, reused directions) and
+// costs extra box and triangle tests when they are not.
+__global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2_packet(
+    const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, const float4* __restrict__ ray_o,
+    const float4* __restrict__ ray_d, const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
+    uint32_t n_max, int2* __restrict__ hit) {
+    extern __shared__ uint32_t smem_stack[];
+    uint32_t* sstack = smem_stack + threadIdx.x;
+    const int stride = blockDim.x;
+    const uint32_t n = queue_count ? min(*queue_count, n_max) : n_max;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (__all_sync(0xffffffffu, i >= n)) return;
+    int slot = -1;
+    bool valid = false;
+    RayPre r;
+    int skip = -1;
+    Best best{-1.0f, -1, 0x7fffffff}; // t < 0: a lane without a ray never enters a box
+    uint32_t sid = 0;
+    if (i < n) {
+        slot = queue ? queue[i] : (int)i;
+        const float4 ro = ray_o[slot];
+        const float4 rd = ray_d[slot];
+        sid = slot_scene ? slot_scene[slot] : 0;
+        if (rd.w >= 0.0f) {
+            r = prep_ray(ro, rd);
+            skip = __float_as_int(ro.w);
+            best = Best{rd.w, -1, 0x7fffffff};
+            valid = true;
+        } else {
+            hit[slot] = make_int2(-1, __float_as_int(INFINITY));
+        }
+    }
+    // a warp shares one scene (slots of one tile are one job); mixed warps take the slow path
+    const uint32_t sid0 = __shfl_sync(0xffffffffu, sid, 0);
+    const bool uniform_scene = __all_sync(0xffffffffu, !valid || sid == sid0);
+    const SceneDev& sc = scenes[uniform_scene ? sid0 : sid];
+    const float4* nodes = sc.nodes2;
+    const float4* tris = sc.tris;
+    unsigned long long dummy = 0;
+    if (!uniform_scene) { // rare: a warp straddling two jobs of different scenes
+        if (valid) {
+            int2 h = trace_bvh2_one<false>(nodes, tris, ray_o[slot], ray_d[slot], sstack, dummy, dummy);
+            hit[slot] = h;
+        }
+        return;
+    }
+#if CR_TRACE_LOCAL_STACK
+    int lstack_all[kStackTotal];
+#else
+    int lstack[kStackTotal - kSmemStack];
+#endif
+    int sp = 0;
+    int node = 0;
+    if (!valid) r = prep_ray(make_float4(0, 0, 0, 0), make_float4(0, 0, 1, -1)); // inert ray
+    while (true) {
+        if (node >= 0) {
+            const float4 n0 = __ldg(&nodes[4 * node + 0]);
+            const float4 n1 = __ldg(&nodes[4 * node + 1]);
+            const float4 n2 = __ldg(&nodes[4 * node + 2]);
+            const float4 n3 = __ldg(&nodes[4 * node + 3]);
+            const float tcull = __fmul_rn(best.t, kCullWiden); // negative for lanes without a ray
+            const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
+            const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
+            const uint32_t v0 = __ballot_sync(0xffffffffu, h0 && (!h1 || t0 <= t1));
+            const uint32_t v1 = __ballot_sync(0xffffffffu, h1 && (!h0 || t1 < t0));
+            const bool any0 = __any_sync(0xffffffffu, h0), any1 = __any_sync(0xffffffffu, h1);
+            if (any0 && any1) {
+                const bool first0 = __popc(v0) >= __popc(v1);
+                STACK_PUSH(first0 ? c1 : c0);
+                node = first0 ? c0 : c1;
+                continue;
+            } else if (any0 || any1) {
+                node = any0 ? c0 : c1;
+                continue;
+            }
+        } else {
+            const uint32_t code = (uint32_t)(~node);
+            if (valid) test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, dummy);
+        }
+        if (sp == 0) break;
+        STACK_POP(node);
+    }
+    if (valid) hit[slot] = make_int2(best.leaf, __float_as_int(best.t));
+}
+
+// Speculative variant: lanes keep one reached leaf pending and go on descending inner
+// nodes until every lane of the warp holds a leaf or has finished; then all lanes test
+// their pending leaves together.  Inner-node and leaf phases thus run with more active
+// lanes.  The loops are warp-synchronous: every lane (finished or not) executes each
+// iteration, and every iteration either visits a node, parks a leaf or tests one.
+constexpr int kEmpty = 0x7fffffff; // stack exhausted
+
+__global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2_spec(
+    const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, const float4* __restrict__ ray_o,
+    const float4* __restrict__ ray_d, const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
+    uint32_t n_max, int2* __restrict__ hit) {
+    extern __shared__ uint32_t smem_stack[];
+    uint32_t* sstack = smem_stack + threadIdx.x;
+    const int stride = blockDim.x;
+    const uint32_t n = queue_count ? min(*queue_count, n_max) : n_max;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    // whole warps past the end leave together; the others run every iteration
+    if (__all_sync(0xffffffffu, i >= n)) return;
+    int slot = -1;
+    bool done = true;
+    RayPre r;
+    int skip = -1;
+    Best best{0.0f, -1, 0x7fffffff};
+    const float4* nodes = nullptr;
+    const float4* tris = nullptr;
+    if (i < n) {
+        slot = queue ? queue[i] : (int)i;
+        const float4 ro = ray_o[slot];
+        const float4 rd = ray_d[slot];
+        if (rd.w >= 0.0f) {
+            const SceneDev& sc = scenes[slot_scene ? slot_scene[slot] : 0];
+            nodes = sc.nodes2;
+            tris = sc.tris;
+            r = prep_ray(ro, rd);
+            skip = __float_as_int(ro.w);
+            best = Best{rd.w, -1, 0x7fffffff};
+            done = false;
+        } else {
+            hit[slot] = make_int2(-1, __float_as_int(INFINITY));
+        }
+    }
+    int lstack[kStackTotal - kSmemStack];
+    int sp = 0, node = done ? kEmpty : 0, leaf = 0;
+    unsigned long long dummy = 0;
+    auto pop = [&]() -> int {
+        if (sp == 0) return kEmpty;
+        --sp;
+        return sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
+    };
+    while (true) {
+        // inner phase
+        while (true) {
+            if (node >= 0 && node != kEmpty) {
+                const float4 n0 = __ldg(&nodes[4 * node + 0]);
+                const float4 n1 = __ldg(&nodes[4 * node + 1]);
+                const float4 n2 = __ldg(&nodes[4 * node + 2]);
+                const float4 n3 = __ldg(&nodes[4 * node + 3]);
+                const float tcull = __fmul_rn(best.t, kCullWiden);
+                const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
+                const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
+                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    const int far = first0 ? c1 : c0;
+                    node = first0 ? c0 : c1;
+                    if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)far;
+                    else if (sp < kStackTotal) lstack[sp - kSmemStack] = far;
+                    sp = sp < kStackTotal ? sp + 1 : sp; // the builder keeps depth < kStackTotal
+                } else if (h0 || h1) {
+                    node = h0 ? c0 : c1;
+                } else {
+                    node = pop();
+                }
+            }
+            if (node < 0 && leaf == 0) { // park the reached leaf and keep descending
+                leaf = node;
+                node = pop();
+            }
+            const bool searching = leaf == 0 && node != kEmpty;
+            if (!__any_sync(0xffffffffu, searching)) break;
+        }
+        // leaf phase: the parked leaf, then any leaf the descent stopped on
+        while (leaf < 0) {
+            const uint32_t code = (uint32_t)(~leaf);
+            test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, dummy);
+            leaf = 0;
+            if (node < 0) {
+                leaf = node;
+                node = pop();
+            }
+        }
+        if (!done && node == kEmpty) {
+            hit[slot] = make_int2(best.leaf, __float_as_int(best.t));
+            done = true;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
     }
 }
 
@@ -293,8 +565,8 @@ __global__ void __launch_bounds__(128) k_trace_bvh2_dynamic(
                 const float4 n2 = __ldg(&nodes[4 * node + 2]);
                 const float4 n3 = __ldg(&nodes[4 * node + 3]);
                 const float tcull = __fmul_rn(best.t, kCullWiden);
-                const float t0 = box_entry(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
-                const float t1 = box_entry(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
+                const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
+                const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
                 const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
                 const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
                 if (h0 && h1) {
@@ -494,6 +766,20 @@ void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
         else
             k_trace_bvh8<false><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
                                                            a.queue_count, a.n_max, a.hit, nullptr);
+        lc.n++;
+        return;
+    }
+    if (a.packet && !a.counters) {
+        const uint32_t grid = (a.n_max + block - 1) / block;
+        k_trace_bvh2_packet<<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
+                                                       a.queue_count, a.n_max, a.hit);
+        lc.n++;
+        return;
+    }
+    if (a.speculative && !a.counters) {
+        const uint32_t grid = (a.n_max + block - 1) / block;
+        k_trace_bvh2_spec<<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue, a.queue_count,
+                                                     a.n_max, a.hit);
         lc.n++;
         return;
     }

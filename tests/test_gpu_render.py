@@ -141,6 +141,11 @@ def test_spp_resume_and_determinism(cr, orc):
     a, _ = S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21)
     b, _ = S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21, flags=cr.CR_OPT_PERSISTENT, block=256)
     assert torch.equal(a, b)
+    c, _ = S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21, flags=cr.CR_OPT_SPECULATIVE, block=64)
+    assert torch.equal(a, c)
+    d, _ = S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21,
+                    flags=cr.CR_OPT_PACKET_PRIMARY | cr.CR_OPT_PACKET_SECONDARY)
+    assert torch.equal(a, d)
     # host output buffer
     h = np.zeros((sc.camera.height, sc.camera.width, 3), np.float32)
     S.render(spp=4, max_bounces=2, tile=(4, 4), k=4, seed=21, out=h)

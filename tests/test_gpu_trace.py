@@ -50,7 +50,7 @@ def test_launch_shapes_agree(cr, orc):
     rays = scenes.random_rays(9, 30000)
     ref = _compare(orc, sc, S, rays)
     for block in (32, 64, 256, 512):
-        for flags in (0, cr.CR_OPT_PERSISTENT):
+        for flags in (0, cr.CR_OPT_PERSISTENT, cr.CR_OPT_SPECULATIVE, cr.CR_OPT_PACKET_SECONDARY):
             p, t = S.trace(rays, block=block, flags=flags)
             assert np.array_equal(np.asarray(p), ref[0]) and np.array_equal(np.asarray(t), ref[1])
 
