@@ -191,7 +191,7 @@ def run_reference(args):
     cam = sc.camera
     ntiles = math.ceil(cam.width / TILE[0]) * math.ceil(cam.height / TILE[1])
     threads = os.cpu_count() or 1
-    n = min(ntiles, 16 * threads)
+    n = min(ntiles, 600 * threads)  # about 1-3 s of oracle work per step on the host cores
     for s in range(args.warmup + args.steps):
         start = (s * 7919 * n) % (ntiles - n)
         t0 = time.perf_counter()
@@ -236,14 +236,18 @@ def run_ours(args):
     setup_s = time.perf_counter() - t_setup
 
     def step(mode, frame, flags=0):
+        # "morton_sort:<key>" selects a reordering key (Table 1 comparators)
+        m, _, key = mode.partition(":")
         st = cr.cr_stats()
         o = cr.make_opts(k=K, interleave=True, seed=0, frame_base=frame,
-                         flags=cr.CR_OPT_STATS | flags, stream=stream, stats=st)
-        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, mode, TILE[0], TILE[1], out, o)
+                         flags=cr.CR_OPT_STATS | flags, stream=stream, stats=st, sort_key=key or "two_point")
+        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m, TILE[0], TILE[1], out, o)
         return st.as_dict()
 
     # counting pass (untimed): node visits and triangle tests of the secondary traces
     modes = args.modes.split(",")
+    if not args.core_only and "morton_sort" in modes:  # the other reordering keys of Table 1
+        modes += ["morton_sort:origin", "morton_sort:reis", "morton_sort:costa", "morton_sort:aila_compact"]
     counts = {}
     for mode in modes:
         counts[mode] = step(mode, frame_of(rank, 0, world), flags=cr.CR_OPT_COUNT)
@@ -628,7 +632,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-window", type=float, default=1.5, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[20.0, 50.0, 100.0, 200.0])
-    ap.add_argument("--modes", default="direction_reuse,independent,morton_sort",
+    ap.add_argument("--modes", default="direction_reuse,independent,morton_sort,world_reuse",
                     help="modes to time (the first is the headline); profiling runs use one")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps

@@ -110,7 +110,10 @@ typedef struct {
     uint32_t width, height;  /* >= 1, width * height <= 2^26 */
 } cr_camera;
 
-typedef enum { CR_INDEPENDENT = 0, CR_MORTON_SORT = 1, CR_DIRECTION_REUSE = 2 } cr_reuse_mode;
+/* CR_WORLD_REUSE is the paper's Sec. 3.1 direct direction reusing, kept as an ablation: the
+ * first alive member of a group shares its world-space exit direction and each diffuse
+ * member weighs it with its own material (directions below its surface end the path). */
+typedef enum { CR_INDEPENDENT = 0, CR_MORTON_SORT = 1, CR_DIRECTION_REUSE = 2, CR_WORLD_REUSE = 3 } cr_reuse_mode;
 
 /* Per-call statistics (filled when cr_render_opts.stats != NULL).  Stage times are CUDA
  * event times on the call's stream summed over samples and bounces. */
@@ -146,6 +149,14 @@ enum {
     CR_OPT_PACKET_SECONDARY = 64u /* warp-packet traversal of secondary rays (BVH2) */
 };
 
+/* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):
+ * TwoPoint interleaves origin and an estimated end point 0.25 x the largest scene extent
+ * away; Origin is the origin's Morton code; Reis puts origin bits above direction bits,
+ * Costa the reverse; AilaCompact interleaves origin and direction. */
+typedef enum {
+    CR_SORT_TWO_POINT = 0, CR_SORT_ORIGIN = 1, CR_SORT_REIS = 2, CR_SORT_COSTA = 3, CR_SORT_AILA_COMPACT = 4
+} cr_sort_key;
+
 typedef struct {
     uint32_t k;            /* pixels per reuse group K; 0 = W*H.  Power of two dividing W*H, <= 256 */
     uint32_t interleave;   /* 1: LCG-shuffled groups (Sec. 3.3, default); 0: contiguous groups */
@@ -155,7 +166,7 @@ typedef struct {
     uint32_t bvh;          /* CR_BVH2 (default) or CR_BVH8Q (scene must have it) */
     uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 */
     uint32_t flags;        /* CR_OPT_* */
-    uint32_t pad;
+    uint32_t sort_key;     /* cr_sort_key of CR_MORTON_SORT (default TwoPoint) */
     void* stream;          /* cudaStream_t to run on; NULL = legacy default stream */
     cr_stats* stats;       /* optional, host */
     cr_debug* debug;       /* optional, host struct of device pointers */
@@ -215,7 +226,7 @@ typedef struct {
     uint32_t bvh;              /* CR_BVH2 or CR_BVH8Q (every scene must have it) */
     uint32_t block;            /* trace block size; 0 = 128 */
     uint32_t flags;            /* CR_BATCH_GRAPH | CR_OPT_PERSISTENT */
-    uint32_t pad;
+    uint32_t sort_key;         /* cr_sort_key of CR_MORTON_SORT jobs */
     void* stream;              /* cudaStream_t used by cr_batch_run (NULL = a stream the batch owns) */
 } cr_batch_opts;
 

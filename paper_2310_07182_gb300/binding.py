@@ -24,10 +24,11 @@ CR_OK, CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT, CR_ERR_STACK
     CR_ERR_NOT_FOUND = range(8)
 CR_MAT_LAMBERT, CR_MAT_GGX, CR_MAT_MIRROR, CR_MAT_EMITTER = range(4)
 CR_BVH2, CR_BVH8Q = 1, 2
-CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE = 0, 1, 2
+CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE, CR_WORLD_REUSE = 0, 1, 2, 3
 CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIVE = 1, 2, 4, 8, 16
 CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY = 32, 64
-MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE}
+MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE,
+         "world_reuse": CR_WORLD_REUSE}
 
 
 class CrError(RuntimeError):
@@ -87,7 +88,7 @@ class cr_job(C.Structure):
 
 class cr_batch_opts(C.Structure):
     _fields_ = [("group_w", C.c_uint32), ("group_h", C.c_uint32), ("k", C.c_uint32), ("interleave", C.c_uint32),
-                ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32), ("pad", C.c_uint32),
+                ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32), ("sort_key", C.c_uint32),
                 ("stream", C.c_void_p)]
 
 
@@ -117,7 +118,7 @@ class cr_server_stats(C.Structure):
 class cr_render_opts(C.Structure):
     _fields_ = [("k", C.c_uint32), ("interleave", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
                 ("reuse_depth", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32),
-                ("pad", C.c_uint32), ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
+                ("sort_key", C.c_uint32), ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
                 ("debug", C.POINTER(cr_debug))]
 
 
@@ -252,12 +253,16 @@ def make_camera(cam) -> cr_camera:
                      float(cam.vfov_deg), int(cam.width), int(cam.height))
 
 
+SORT_KEYS = {"two_point": 0, "origin": 1, "reis": 2, "costa": 3, "aila_compact": 4}
+
+
 def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_BVH2, block=0, flags=0,
-              stream=None, stats=None, debug=None) -> cr_render_opts:
+              stream=None, stats=None, debug=None, sort_key=0) -> cr_render_opts:
     o = cr_render_opts()
     _check(lib().cr_render_opts_default(C.byref(o)))
     o.k, o.interleave, o.seed, o.frame_base = k, int(interleave), seed, frame_base
     o.reuse_depth, o.bvh, o.block, o.flags = reuse_depth, bvh, block, flags
+    o.sort_key = SORT_KEYS.get(sort_key, sort_key)
     o.stream = stream
     if stats is not None:
         o.stats = C.pointer(stats)
@@ -439,7 +444,7 @@ class Scene:
 
     def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
                seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
-               debug=None, stream=None):
+               debug=None, stream=None, sort_key=0):
         """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
         CUDA tensor by default).  Returns (out, stats dict or None)."""
         import torch
@@ -449,7 +454,7 @@ class Scene:
         st = cr_stats() if stats else None
         o = make_opts(k=k, interleave=interleave, seed=seed, frame_base=frame_base, reuse_depth=reuse_depth, bvh=bvh,
                       block=block, flags=flags | (CR_OPT_STATS if stats else 0), stream=stream, stats=st,
-                      debug=debug)
+                      debug=debug, sort_key=sort_key)
         cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
         return out, (st.as_dict() if st is not None else None)
 

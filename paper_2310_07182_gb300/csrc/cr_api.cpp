@@ -448,8 +448,7 @@ cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h) {
     if (j.spp == 0) return fail(CR_ERR_INVALID_ARG, "spp must be >= 1");
     if (j.max_bounces == 0 || j.max_bounces > 16)
         return fail(CR_ERR_INVALID_ARG, "max_bounces %u not in [1, 16]", j.max_bounces);
-    if (j.mode != CR_INDEPENDENT && j.mode != CR_MORTON_SORT && j.mode != CR_DIRECTION_REUSE)
-        return fail(CR_ERR_INVALID_ARG, "unknown mode %u", j.mode);
+    if (j.mode > CR_WORLD_REUSE) return fail(CR_ERR_INVALID_ARG, "unknown mode %u", j.mode);
     (void)tile_w;
     (void)tile_h;
     return CR_OK;
@@ -516,9 +515,12 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
             d.frame = j.frame_base + p;
             d.max_bounces = j.max_bounces;
             d.reuse_mask = 0;
-            if (j.mode == CR_DIRECTION_REUSE)
-                for (uint32_t b = 1; b <= j.max_bounces; ++b)
-                    if (j.reuse_depth == 0 || b <= j.reuse_depth) d.reuse_mask |= 1u << b;
+            d.world_mask = 0;
+            for (uint32_t b = 1; b <= j.max_bounces; ++b)
+                if (j.reuse_depth == 0 || b <= j.reuse_depth) {
+                    if (j.mode == CR_DIRECTION_REUSE) d.reuse_mask |= 1u << b;
+                    if (j.mode == CR_WORLD_REUSE) d.world_mask |= 1u << b;
+                }
             d.interleave = po.interleave ? 1u : 0u;
             d.seed = j.seed;
             d.out = j.out_rgb;
@@ -630,7 +632,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             ta.n_max = n_slots;
             if (p.sort) {
                 ev.begin(stream, times ? &times->sort : &dummy);
-                ta.queue = launch_morton_sort(P, b, bnc, stream, lc);
+                ta.queue = launch_morton_sort(P, b, bnc, eo.sort_key, stream, lc);
                 ev.end();
             }
             ta.counters = eo.count ? b.counters : nullptr;
@@ -723,6 +725,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     eo.packet_primary = (o.flags & CR_OPT_PACKET_PRIMARY) != 0;
     eo.packet_secondary = (o.flags & CR_OPT_PACKET_SECONDARY) != 0;
     eo.count = (o.flags & CR_OPT_COUNT) != 0;
+    if (o.sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "cr_render: sort_key %u", o.sort_key);
+    eo.sort_key = o.sort_key;
     eo.debug = o.debug;
     eo.debug_npx = npx;
     LaunchCount lc;
@@ -1015,6 +1019,8 @@ static cr_status batch_opts_check(const cr_batch_opts* o, PlanOpts& po, ExecOpts
     po.bvh8 = o->bvh == CR_BVH8Q;
     eo.block = block;
     eo.persistent = (o->flags & CR_OPT_PERSISTENT) != 0;
+    if (o->sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "sort_key %u", o->sort_key);
+    eo.sort_key = o->sort_key;
     return CR_OK;
 }
 

@@ -104,7 +104,7 @@ struct JobDev {
     uint64_t seed;
     float* out;           // device output (w*h*3 floats) of the job
     float inv_spp;
-    uint32_t pad;
+    uint32_t world_mask;  // bit b: world-space direct reuse (Sec. 3.1 ablation) at bounce b
 };
 
 // Launch-uniform description of a pass.
@@ -187,8 +187,8 @@ void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug*
                   LaunchCount& lc);
 // Group-granular compaction of the slots processed by the last shade into ray and group queues.
 void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc);
-const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, cudaStream_t st,
-                                  LaunchCount& lc);
+const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, uint32_t key_kind,
+                                  cudaStream_t st, LaunchCount& lc);
 uint32_t sort_hist_len(uint32_t n_slots);
 uint32_t compact_blocks(uint32_t n_pos);
 void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, float4* ray_o, float4* ray_d,
@@ -246,6 +246,7 @@ struct ExecOpts {
     int block = 128;
     bool persistent = false, count = false, speculative = false;
     bool packet_primary = false, packet_secondary = false; // warp-packet traversal per ray kind
+    uint32_t sort_key = 0; // reordering key of CR_MORTON_SORT (cr_sort_key)
     bool clear_accum = true; // zero the accumulation buffer first
     bool write_output = true; // write every job's output after the last pass
     const cr_debug* debug = nullptr;

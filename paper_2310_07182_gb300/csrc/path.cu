@@ -153,6 +153,7 @@ struct Member {
     bool alive;
     bool final_pass; // the job's last secondary ray has been traced
     bool reuse;      // the job reuses directions at this bounce
+    bool world;      // the job reuses world-space directions at this bounce (Sec. 3.1 ablation)
     uint64_t seed;
     uint32_t frame;
     int cls;
@@ -294,6 +295,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     float3 L = make_float3(0, 0, 0);
     mb.final_pass = true;
     mb.reuse = false;
+    mb.world = false;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
@@ -303,6 +305,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             Jp = &a.jobs[a.slot_job[slot]];
             mb.final_pass = p.bounce > Jp->max_bounces;
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
+            mb.world = (Jp->world_mask >> p.bounce) & 1u;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
         }
@@ -352,6 +355,21 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
                 }
             }
         }
+        // Sec. 3.1 direct reuse (ablation): the first alive member's world-space direction,
+        // re-expressed in each diffuse member's frame; below the surface the path ends
+        if (__any_sync(0xffffffffu, mb.world)) {
+            const uint32_t ba = __ballot_sync(0xffffffffu, mb.alive) & segmask;
+            const int wdonor = ba ? __ffs(ba) - 1 : (int)lane;
+            const V3 ww = mb.alive ? local_to_world(mb.t, mb.b, mb.n, mb.wl) : v3(0.0f, 0.0f, 0.0f);
+            const V3 wdw = v3(__shfl_sync(0xffffffffu, ww.x, wdonor), __shfl_sync(0xffffffffu, ww.y, wdonor),
+                              __shfl_sync(0xffffffffu, ww.z, wdonor));
+            const bool dvalid = __shfl_sync(0xffffffffu, mb.valid ? 1 : 0, wdonor) != 0;
+            if (mb.world && mb.alive && mb.cls == kClsDiffuse && ba && dvalid) {
+                const V3 l = v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n));
+                take_dir(mb, l);
+                if (!(l.z > 0.0f)) mb.valid = false;
+            }
+        }
     }
     if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
 }
@@ -360,9 +378,10 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
 // members' samples go through shared memory and the hybrid sum is a pairwise tree over the
 // group's slots.
 __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
-    __shared__ uint32_t s_bd[8], s_bg[8];
+    __shared__ uint32_t s_bd[8], s_bg[8], s_ba[8];
     __shared__ float s_own[3][256];
     __shared__ float s_sum[3][256];
+    __shared__ float s_world[4][256]; // world-space direction and validity (Sec. 3.1 ablation)
     const uint32_t K = p.k;
     const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,6 +399,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     float3 L = make_float3(0, 0, 0);
     mb.final_pass = true;
     mb.reuse = false;
+    mb.world = false;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
@@ -389,6 +409,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             Jp = &a.jobs[a.slot_job[slot]];
             mb.final_pass = p.bounce > Jp->max_bounces;
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
+            mb.world = (Jp->world_mask >> p.bounce) & 1u;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
         }
@@ -407,9 +428,18 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
         const uint32_t t = threadIdx.x, w = t >> 5;
         const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse);
         const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy);
+        const uint32_t ba = __ballot_sync(0xffffffffu, mb.alive);
         if ((t & 31u) == 0) {
             s_bd[w] = bd;
             s_bg[w] = bg;
+            s_ba[w] = ba;
+        }
+        {
+            const V3 ww = mb.alive ? local_to_world(mb.t, mb.b, mb.n, mb.wl) : v3(0.0f, 0.0f, 0.0f);
+            s_world[0][t] = ww.x;
+            s_world[1][t] = ww.y;
+            s_world[2][t] = ww.z;
+            s_world[3][t] = mb.valid ? 1.0f : 0.0f;
         }
         const bool contrib = mb.alive && mb.cls == kClsGlossy && mb.valid;
         s_own[0][t] = mb.wl.x;
@@ -451,6 +481,17 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
                         take_dir(mb, wd);
                     }
                 }
+            }
+        }
+        if (mb.world && mb.alive && mb.cls == kClsDiffuse) {
+            int wdonor = -1;
+            for (uint32_t ww = gbase >> 5; ww < (gbase + K) >> 5 && wdonor < 0; ++ww)
+                if (s_ba[ww]) wdonor = (int)(ww * 32u + __ffs(s_ba[ww]) - 1);
+            if (wdonor >= 0 && s_world[3][wdonor] != 0.0f) {
+                const V3 wdw = v3(s_world[0][wdonor], s_world[1][wdonor], s_world[2][wdonor]);
+                const V3 l = v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n));
+                take_dir(mb, l);
+                if (!(l.z > 0.0f)) mb.valid = false;
             }
         }
     }
@@ -581,12 +622,33 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_scatter(const int32_t
 }
 
 // ------------------------------------------------------------------------------------
-// Morton-sort comparator ("TwoPoint", Table 1): 30-bit key interleaving 5 bits of each
-// coordinate of the origin and of the point 0.25 x (largest scene extent) along the ray,
-// quantised in the scene box; then a stable LSD radix sort of (key, slot).
+// Reordering comparators (Table 1): a 30-bit key per ray, then a stable LSD radix sort of
+// (key, slot).  Positions are quantised in the scene box; directions through the octahedral
+// map of the unit sphere onto [-1,1]^2.  Keys (the paper cites their sources without giving
+// bit layouts; these layouts are our readings):
+//   0 TwoPoint     5 bits of each coordinate of the origin and of the point 0.25 x (largest
+//                  scene extent) along the ray, interleaved (6-D Morton)
+//   1 Origin       10 bits per origin coordinate (3-D Morton)
+//   2 Reis         origin (6 bits per coordinate, 3-D Morton) above direction (6 bits per
+//                  octahedral coordinate, 2-D Morton)
+//   3 Costa        the same fields with the direction above the origin
+//   4 AilaCompact  origin and direction interleaved (5-D Morton, 6 bits per coordinate)
+__device__ __forceinline__ uint32_t quant(float v, float lo, float scale, uint32_t bits) {
+    const float m = (float)((1u << bits) - 1u);
+    return (uint32_t)fminf(fmaxf((v - lo) * scale * m, 0.0f), m);
+}
+
+// interleave n coordinates of `bits` bits each, coordinate 0 most significant at each level
+__device__ __forceinline__ uint32_t interleave(const uint32_t* q, int n, int bits) {
+    uint32_t key = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int k = 0; k < n; ++k) key = (key << 1) | ((q[k] >> b) & 1u);
+    return key;
+}
+
 __global__ void k_morton(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                          const int32_t* __restrict__ queue, const uint32_t* __restrict__ count, uint32_t n_max,
-                         const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
+                         const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, uint32_t kind,
                          uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
     const uint32_t n = min(*count, n_max);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -598,24 +660,50 @@ __global__ void k_morton(const float4* __restrict__ ray_o, const float4* __restr
     for (int k = 0; k < 3; ++k) {
         const float ext = sc.hi[k] - sc.lo[k];
         l[k] = sc.lo[k];
-        s[k] = ext > 0.0f ? 32.0f / ext : 0.0f;
+        s[k] = ext > 0.0f ? 1.0f / ext : 0.0f;
         emax = fmaxf(emax, ext);
     }
-    const float len = 0.25f * emax;
     const float4 o = ray_o[slot], d = ray_d[slot];
-    const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z) * len;
-    const float p[6] = {o.x, o.y, o.z, o.x + d.x * il, o.y + d.y * il, o.z + d.z * il};
-    uint32_t q[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const float f = (p[k] - l[k % 3]) * s[k % 3];
-        q[k] = (uint32_t)fminf(fmaxf(f, 0.0f), 31.0f);
-    }
+    const float po[3] = {o.x, o.y, o.z};
     uint32_t key = 0;
+    if (kind == 0) {
+        const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z) * (0.25f * emax);
+        const float pe[3] = {o.x + d.x * il, o.y + d.y * il, o.z + d.z * il};
+        uint32_t q[6];
 #pragma unroll
-    for (int bit = 4; bit >= 0; --bit)
+        for (int k = 0; k < 3; ++k) {
+            q[k] = quant(po[k], l[k], s[k], 5);
+            q[3 + k] = quant(pe[k], l[k], s[k], 5);
+        }
+        key = interleave(q, 6, 5);
+    } else if (kind == 1) {
+        uint32_t q[3];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) key = (key << 1) | ((q[k] >> bit) & 1u);
+        for (int k = 0; k < 3; ++k) q[k] = quant(po[k], l[k], s[k], 10);
+        key = interleave(q, 3, 10);
+    } else {
+        // octahedral direction coordinates in [-1, 1]
+        const float inv = 1.0f / (fabsf(d.x) + fabsf(d.y) + fabsf(d.z));
+        float u = d.x * inv, v = d.y * inv;
+        if (d.z < 0.0f) {
+            const float uu = (1.0f - fabsf(v)) * copysignf(1.0f, u);
+            const float vv = (1.0f - fabsf(u)) * copysignf(1.0f, v);
+            u = uu;
+            v = vv;
+        }
+        uint32_t qd[2] = {quant(u, -1.0f, 0.5f, 6), quant(v, -1.0f, 0.5f, 6)};
+        uint32_t qo[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) qo[k] = quant(po[k], l[k], s[k], 6);
+        if (kind == 2) {
+            key = (interleave(qo, 3, 6) << 12) | interleave(qd, 2, 6);
+        } else if (kind == 3) {
+            key = (interleave(qd, 2, 6) << 18) | interleave(qo, 3, 6);
+        } else {
+            const uint32_t q5[5] = {qo[0], qo[1], qo[2], qd[0], qd[1]};
+            key = interleave(q5, 5, 6);
+        }
+    }
     keys[i] = key;
     vals[i] = slot;
 }
@@ -932,8 +1020,8 @@ void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, c
 }
 
 // Sort the current bounce's ray queue by TwoPoint key; returns the sorted slot queue.
-const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, cudaStream_t st,
-                                  LaunchCount& lc) {
+const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, uint32_t key_kind,
+                                  cudaStream_t st, LaunchCount& lc) {
     const uint32_t n_max = b.n_slots;
     const uint32_t* count = b.counts + 8 + 2 * bounce;
     uint32_t* ka = b.keys;
@@ -941,7 +1029,7 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
     int32_t* va = b.vals;
     int32_t* vb = b.vals + n_max;
     k_morton<<<(n_max + 255) / 256, 256, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max, p.scenes,
-                                                  b.slot_scene, ka, va);
+                                                  b.slot_scene, key_kind, ka, va);
     lc.n++;
     const uint32_t n_blocks = (n_max + kSortTile - 1) / kSortTile;
     for (uint32_t pass = 0; pass < 4; ++pass) {

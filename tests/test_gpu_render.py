@@ -198,3 +198,28 @@ def test_bvh8q_render_identical(cr, orc):
     assert sa["secondary_rays"] == sb["secondary_rays"]
     ref = orc.render(orc.Scene(sc), sc.camera, **kw)
     _check(b.cpu().numpy(), ref, max_taint=0.1)
+
+
+@pytest.mark.parametrize("key", ["two_point", "origin", "reis", "costa", "aila_compact"])
+def test_every_sort_key_gives_the_independent_image(cr, orc, key):
+    """Reordering only changes the order rays are traced in (Table 1 comparators)."""
+    sc, S, O = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    kw = dict(spp=2, max_bounces=3, tile=(8, 8), k=8, seed=17)
+    a, _ = S.render(mode="independent", **kw)
+    b, st = S.render(mode="morton_sort", sort_key=key, stats=True, **kw)
+    assert torch.equal(a, b) and st["ms_sort"] > 0
+
+
+def test_world_space_reuse_matches_oracle_and_fails_furnace(cr, orc):
+    """Sec. 3.1 direct reuse (ablation): parity with the oracle's world-space rule, and the
+    white furnace detects its lower-hemisphere directions."""
+    trio = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    for tile, k in (((8, 4), 8), ((8, 8), 64)):
+        img, st, ref, _ = _render_both(cr, orc, trio, "world_reuse", B=2, tile=tile, k=k, seed=9)
+        _check(img, ref, max_taint=0.05 if k == 8 else 0.2)  # one fragile ray taints its K pixels
+    sc = scenes.furnace(albedo=(0.5, 0.25, 0.75), width=64, height=48)
+    S = cr.Scene(sc)
+    alb = torch.tensor(np.float32([0.5, 0.25, 0.75]), device="cuda")
+    img, _ = S.render(mode="world_reuse", max_bounces=1, tile=(8, 8), k=64, seed=4)
+    ok = (img == alb).all(dim=-1) | (img == 1.0).all(dim=-1)
+    assert int((~ok).sum()) > 20
