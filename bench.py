@@ -235,12 +235,25 @@ def run_ours(args):
     stream = torch.cuda.current_stream().cuda_stream
     setup_s = time.perf_counter() - t_setup
 
-    def step(mode, frame, flags=0):
-        # "morton_sort:<key>" selects a reordering key (Table 1 comparators)
+    variant_flags = {"two_phase": cr.CR_OPT_TWO_PHASE, "packet": cr.CR_OPT_PACKET_SECONDARY,
+                     "speculative": cr.CR_OPT_SPECULATIVE, "persistent": cr.CR_OPT_PERSISTENT}
+
+    def parse(mode):
+        # "morton_sort:<key>" selects a reordering key (Table 1 comparators); a "+<variant>"
+        # suffix selects a traversal variant of the secondary trace
+        mode, *variants = mode.split("+")
         m, _, key = mode.partition(":")
+        flags = 0
+        for v in variants:
+            flags |= variant_flags[v]
+        return m, key or "two_point", flags
+
+    def step(mode, frame, flags=0):
+        m, key, vflags = parse(mode)
+        flags |= vflags
         st = cr.cr_stats()
         o = cr.make_opts(k=K, interleave=True, seed=0, frame_base=frame,
-                         flags=cr.CR_OPT_STATS | flags, stream=stream, stats=st, sort_key=key or "two_point")
+                         flags=cr.CR_OPT_STATS | flags, stream=stream, stats=st, sort_key=key)
         cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m, TILE[0], TILE[1], out, o)
         return st.as_dict()
 
@@ -298,15 +311,17 @@ def run_ours(args):
 
     # end to end through the C ABI into pinned host memory
     host = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, pin_memory=True)
+    m0, key0, flags0 = parse(modes[0])
     for w in range(args.warmup):
-        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, modes[0], TILE[0], TILE[1], host,
-                        cr.make_opts(k=K, frame_base=frame_of(rank, w, world)))
+        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m0, TILE[0], TILE[1], host,
+                        cr.make_opts(k=K, frame_base=frame_of(rank, w, world), flags=flags0, sort_key=key0))
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for s in range(args.steps):
-        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, modes[0], TILE[0], TILE[1], host,
-                        cr.make_opts(k=K, frame_base=frame_of(rank, args.warmup + s, world)))
+        cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m0, TILE[0], TILE[1], host,
+                        cr.make_opts(k=K, frame_base=frame_of(rank, args.warmup + s, world), flags=flags0,
+                                     sort_key=key0))
     e2e_s = aggregate(time.perf_counter() - t0, "max")
     e2e_rays = aggregate(results[modes[0]]["secondary_rays_per_step"] * args.steps, "sum")
 

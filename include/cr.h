@@ -146,7 +146,8 @@ enum {
     CR_OPT_PERSISTENT = 8u, /* persistent trace kernel with dynamic ray fetch (BVH2) */
     CR_OPT_SPECULATIVE = 16u, /* speculative traversal with a parked leaf per lane (BVH2) */
     CR_OPT_PACKET_PRIMARY = 32u,  /* warp-packet traversal of primary rays (BVH2) */
-    CR_OPT_PACKET_SECONDARY = 64u /* warp-packet traversal of secondary rays (BVH2) */
+    CR_OPT_PACKET_SECONDARY = 64u, /* warp-packet traversal of secondary rays (BVH2) */
+    CR_OPT_TWO_PHASE = 128u /* secondary rays: 32-visit budget, compact the unfinished, resume (BVH2) */
 };
 
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):

@@ -26,7 +26,7 @@ CR_MAT_LAMBERT, CR_MAT_GGX, CR_MAT_MIRROR, CR_MAT_EMITTER = range(4)
 CR_BVH2, CR_BVH8Q = 1, 2
 CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE, CR_WORLD_REUSE = 0, 1, 2, 3
 CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIVE = 1, 2, 4, 8, 16
-CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY = 32, 64
+CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY, CR_OPT_TWO_PHASE = 32, 64, 128
 MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE,
          "world_reuse": CR_WORLD_REUSE}
 

@@ -379,6 +379,37 @@ void Workspace::release() {
     base = nullptr;
     bytes = 0;
     pb = PathBuffers();
+    if (phase_base) cudaFree(phase_base);
+    phase_base = nullptr;
+    phase_slots = 0;
+    phase = PhaseBuffers();
+}
+
+#ifndef CR_PHASE_BUDGET
+#define CR_PHASE_BUDGET 32 // node and leaf visits of the two-phase trace's first phase
+#endif
+
+cr_status Workspace::ensure_phase(uint32_t n_slots) {
+    if (phase_base && phase_slots >= n_slots) return CR_OK;
+    if (phase_base) cudaFree(phase_base);
+    phase_base = nullptr;
+    const size_t ns = n_slots, nb = (ns + 255) / 256 + 1;
+    const size_t o_state = 0, o_susp = o_state + sizeof(TraceState) * ns, o_q2 = (o_susp + ns + 255) & ~(size_t)255,
+                 o_cnt = o_q2 + 4 * ns, o_bc = o_cnt + 256, total = o_bc + 8 * nb;
+    cudaError_t e = cudaMalloc(&phase_base, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        phase_base = nullptr;
+        return fail(CR_ERR_OOM, "two-phase trace buffers: %s", cudaGetErrorString(e));
+    }
+    char* c = static_cast<char*>(phase_base);
+    phase.state = reinterpret_cast<TraceState*>(c + o_state);
+    phase.susp = reinterpret_cast<uint8_t*>(c + o_susp);
+    phase.queue2 = reinterpret_cast<int32_t*>(c + o_q2);
+    phase.count2 = reinterpret_cast<uint32_t*>(c + o_cnt);
+    phase.block_counts = reinterpret_cast<uint32_t*>(c + o_bc);
+    phase_slots = n_slots;
+    return CR_OK;
 }
 
 // Carve the path state for n_slots slots and npx accumulation pixels out of one allocation.
@@ -637,6 +668,9 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             }
             ta.counters = eo.count ? b.counters : nullptr;
             if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
+            ta.two_phase = eo.phase_budget > 0 && ws.phase.state;
+            ta.phase = ws.phase;
+            ta.phase.budget = eo.phase_budget;
             ev.begin(stream, times ? &times->trace_secondary : &dummy);
             launch_trace(ta, stream, lc);
             ev.end();
@@ -727,6 +761,11 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     eo.count = (o.flags & CR_OPT_COUNT) != 0;
     if (o.sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "cr_render: sort_key %u", o.sort_key);
     eo.sort_key = o.sort_key;
+    if (o.flags & CR_OPT_TWO_PHASE) {
+        eo.phase_budget = CR_PHASE_BUDGET;
+        st = s->ws.ensure_phase(plan.max_slots);
+        if (st != CR_OK) return st;
+    }
     eo.debug = o.debug;
     eo.debug_npx = npx;
     LaunchCount lc;

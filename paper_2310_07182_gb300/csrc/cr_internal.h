@@ -123,6 +123,25 @@ struct LaunchCount {
     uint64_t n = 0;
 };
 
+// Saved traversal of a ray suspended by the two-phase trace (128 bytes).
+struct TraceState {
+    int node, sp, leaf, orig;
+    float t;
+    int pad[3];
+    int stack[24];
+};
+// Buffers of the two-phase trace (per slot: state, flag; per queue entry: second queue).
+struct PhaseBuffers {
+    TraceState* state = nullptr;
+    uint8_t* susp = nullptr;
+    int32_t* queue2 = nullptr;
+    uint32_t* count2 = nullptr;       // device count of queue2 (+ scratch words)
+    uint32_t* block_counts = nullptr; // compaction scratch
+    uint32_t budget = 32;
+};
+// Exclusive scan of per-block counts (column 0 of 2) into offsets; total -> *total.
+void launch_scan_counts(uint32_t* block_counts, uint32_t n_blocks, uint32_t* total, cudaStream_t st);
+
 // Arguments of one trace launch over a queue of slots.
 struct TraceArgs {
     const float4* ray_o = nullptr; // slot-indexed (o.xyz, skip original index as int bits)
@@ -140,6 +159,8 @@ struct TraceArgs {
     bool persistent = false;
     bool speculative = false; // parked-leaf speculative traversal (BVH2)
     bool packet = false;      // warp-packet traversal (BVH2)
+    bool two_phase = false;   // budgeted traversal, compaction of unfinished rays, resume (BVH2)
+    PhaseBuffers phase;
     bool bvh8 = false;
 };
 void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
@@ -210,7 +231,12 @@ struct Workspace {
     PathBuffers pb;
     void* base = nullptr;
     size_t bytes = 0;
+    // two-phase trace buffers, allocated on first use
+    void* phase_base = nullptr;
+    uint32_t phase_slots = 0;
+    PhaseBuffers phase;
     cr_status ensure(uint32_t n_slots, uint32_t npx);
+    cr_status ensure_phase(uint32_t n_slots);
     void release();
     ~Workspace() { release(); }
 };
@@ -247,6 +273,7 @@ struct ExecOpts {
     bool persistent = false, count = false, speculative = false;
     bool packet_primary = false, packet_secondary = false; // warp-packet traversal per ray kind
     uint32_t sort_key = 0; // reordering key of CR_MORTON_SORT (cr_sort_key)
+    uint32_t phase_budget = 0; // two-phase secondary trace: node visits before suspension (0 = off)
     bool clear_accum = true; // zero the accumulation buffer first
     bool write_output = true; // write every job's output after the last pass
     const cr_debug* debug = nullptr;

@@ -1054,6 +1054,11 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
 }
 
 // histogram entries plus one chunk total per kScanChunk entries
+void launch_scan_counts(uint32_t* block_counts, uint32_t n_blocks, uint32_t* total, cudaStream_t st) {
+    // k_compact_scan scans both columns; column 1 is zero here and its total lands in total[1]
+    k_compact_scan<<<1, 1024, 0, st>>>(block_counts, n_blocks, total, nullptr);
+}
+
 uint32_t sort_hist_len(uint32_t n_slots) {
     const uint32_t len = 256u * ((n_slots + kSortTile - 1) / kSortTile);
     return len + (len + kScanChunk - 1) / kScanChunk + 4;

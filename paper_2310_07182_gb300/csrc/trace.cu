@@ -287,6 +287,140 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __res
     }
 }
 
+// Two-phase variant: phase 1 traverses every ray for at most `budget` node and leaf visits;
+// a ray that runs out saves its traversal state (next node, stack, best hit) and is flagged.
+// The flagged rays are compacted in queue order (so neighbours stay neighbours) and phase 2
+// resumes them in full warps, so short rays no longer leave most lanes of a warp idle while
+// its long rays finish.  Suspension only happens with at most kSaveStack entries on the
+// stack (deeper rays run to completion in phase 1).  The visit order is the single-ray
+// kernel's, so the hits are identical.
+constexpr int kSaveStack = 24;
+
+__device__ __forceinline__ int2 trace_bvh2_resumable(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                     float4 ro, float4 rd, uint32_t* sstack, uint32_t budget,
+                                                     TraceState* st, bool resume, bool& suspended) {
+    const RayPre r = prep_ray(ro, rd);
+    const int skip = __float_as_int(ro.w);
+    Best best{rd.w, -1, 0x7fffffff};
+    int lstack[kStackTotal - kSmemStack];
+    const int stride = blockDim.x;
+    int sp = 0, node = 0;
+    if (resume) {
+        node = st->node;
+        sp = st->sp;
+        best = Best{st->t, st->leaf, st->orig};
+        for (int k = 0; k < sp; ++k) {
+            const int v = st->stack[k];
+            if (k < kSmemStack) sstack[k * stride] = (uint32_t)v;
+            else lstack[k - kSmemStack] = v;
+        }
+    }
+    uint32_t visits = 0;
+    suspended = false;
+    while (true) {
+        while (node >= 0) {
+            if (++visits > budget && sp <= kSaveStack) {
+                suspended = true;
+                break;
+            }
+            const float4 n0 = __ldg(&nodes[4 * node + 0]);
+            const float4 n1 = __ldg(&nodes[4 * node + 1]);
+            const float4 n2 = __ldg(&nodes[4 * node + 2]);
+            const float4 n3 = __ldg(&nodes[4 * node + 3]);
+            const float tcull = __fmul_rn(best.t, kCullWiden);
+            const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
+            const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+            const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                const int near = first0 ? c0 : c1, far = first0 ? c1 : c0;
+                STACK_PUSH(far);
+                node = near;
+            } else if (h0 || h1) {
+                node = h0 ? c0 : c1;
+            } else {
+                if (sp == 0) { node = 0x7fffffff; break; }
+                STACK_POP(node);
+            }
+        }
+        if (suspended || node == 0x7fffffff) break;
+        const uint32_t code = (uint32_t)(~node);
+        unsigned long long dummy = 0;
+        test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, dummy);
+        ++visits;
+        if (sp == 0) break;
+        STACK_POP(node);
+    }
+    if (suspended) {
+        st->node = node;
+        st->sp = sp;
+        st->t = best.t;
+        st->leaf = best.leaf;
+        st->orig = best.orig;
+        for (int k = 0; k < sp; ++k) st->stack[k] = k < kSmemStack ? (int)sstack[k * stride] : lstack[k - kSmemStack];
+    }
+    return make_int2(best.leaf, __float_as_int(best.t));
+}
+
+__global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2_phase(
+    const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, const float4* __restrict__ ray_o,
+    const float4* __restrict__ ray_d, const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
+    uint32_t n_max, int2* __restrict__ hit, TraceState* __restrict__ state, uint8_t* __restrict__ susp,
+    uint32_t budget, int resume) {
+    extern __shared__ uint32_t smem_stack[];
+    const uint32_t n = queue_count ? min(*queue_count, n_max) : n_max;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int slot = queue ? queue[i] : (int)i;
+    const float4 ro = ray_o[slot];
+    const float4 rd = ray_d[slot];
+    bool suspended = false;
+    int2 h = make_int2(-1, __float_as_int(INFINITY));
+    if (rd.w >= 0.0f) {
+        const SceneDev& sc = scenes[slot_scene ? slot_scene[slot] : 0];
+        h = trace_bvh2_resumable(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, budget, &state[slot],
+                                 resume != 0, suspended);
+    }
+    if (!suspended) hit[slot] = h;
+    if (susp) susp[i] = suspended ? 1 : 0;
+}
+
+// Order-preserving compaction of the suspended rays' queue entries (count, scan, scatter).
+__global__ void __launch_bounds__(256) k_susp_count(const uint8_t* __restrict__ susp, const uint32_t* __restrict__ count,
+                                                    uint32_t n_max, uint32_t* __restrict__ block_counts) {
+    __shared__ uint32_t s_w[8];
+    const uint32_t n = min(*count, n_max);
+    const uint32_t i = blockIdx.x * 256 + threadIdx.x;
+    const uint32_t f = (i < n && susp[i]) ? 1u : 0u;
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += s_w[w];
+        block_counts[2 * blockIdx.x] = t;
+        block_counts[2 * blockIdx.x + 1] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_susp_scatter(const uint8_t* __restrict__ susp, const int32_t* __restrict__ queue,
+                                                      const uint32_t* __restrict__ count, uint32_t n_max,
+                                                      const uint32_t* __restrict__ block_offsets,
+                                                      int32_t* __restrict__ out_queue) {
+    __shared__ uint32_t s_w[8];
+    const uint32_t n = min(*count, n_max);
+    const uint32_t i = blockIdx.x * 256 + threadIdx.x;
+    const uint32_t f = (i < n && susp[i]) ? 1u : 0u;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_w[w] = __popc(b);
+    __syncthreads();
+    uint32_t before = 0;
+    for (uint32_t k = 0; k < w; ++k) before += s_w[k];
+    if (f) out_queue[block_offsets[2 * blockIdx.x] + before + __popc(b & ((1u << lane) - 1u))] = queue[i];
+}
+
 // Warp-packet variant: the 32 lanes of a warp traverse ONE node sequence.  At each inner
 // node every lane tests both child boxes against its own ray (with its own culling
 // distance); a child is entered if any lane's ray reaches it, nearer-first by majority.
@@ -767,6 +901,21 @@ void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
             k_trace_bvh8<false><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
                                                            a.queue_count, a.n_max, a.hit, nullptr);
         lc.n++;
+        return;
+    }
+    if (a.two_phase && !a.counters && a.phase.state && a.queue && a.queue_count) {
+        const uint32_t grid = (a.n_max + block - 1) / block;
+        const uint32_t nb = (a.n_max + 255) / 256;
+        k_trace_bvh2_phase<<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue, a.queue_count,
+                                                      a.n_max, a.hit, a.phase.state, a.phase.susp, a.phase.budget, 0);
+        k_susp_count<<<nb, 256, 0, st>>>(a.phase.susp, a.queue_count, a.n_max, a.phase.block_counts);
+        launch_scan_counts(a.phase.block_counts, nb, a.phase.count2, st);
+        k_susp_scatter<<<nb, 256, 0, st>>>(a.phase.susp, a.queue, a.queue_count, a.n_max, a.phase.block_counts,
+                                          a.phase.queue2);
+        k_trace_bvh2_phase<<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.phase.queue2,
+                                                      a.phase.count2, a.n_max, a.hit, a.phase.state, nullptr,
+                                                      0xffffffffu, 1);
+        lc.n += 5;
         return;
     }
     if (a.packet && !a.counters) {
