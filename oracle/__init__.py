@@ -53,7 +53,7 @@ class _Params(C.Structure):
     _fields_ = [("spp", C.c_uint32), ("max_bounces", C.c_uint32), ("mode", C.c_uint32),
                 ("tile_w", C.c_uint32), ("tile_h", C.c_uint32), ("k", C.c_uint32),
                 ("interleave", C.c_uint32), ("frame_base", C.c_uint32), ("reuse_depth", C.c_uint32),
-                ("pad", C.c_uint32), ("seed", C.c_uint64)]
+                ("nee", C.c_uint32), ("seed", C.c_uint64)]
 
 
 class _Outputs(C.Structure):
@@ -82,6 +82,14 @@ def lib():
         L.orc_scene_nodes.argtypes = [vp]
         L.orc_scene_nodes.restype = u32
         L.orc_trace.argtypes = [vp, vp, vp, u32, i32, vp, vp, vp]
+        L.orc_shadow.argtypes = [vp, vp, vp, u32, i32, vp, vp]
+        L.orc_triangle_area.argtypes = [vp]
+        L.orc_triangle_area.restype = C.c_double
+        L.orc_scene_lights.argtypes = [vp, vp]
+        L.orc_scene_lights.restype = u32
+        L.orc_light_sample.argtypes = [vp, C.c_float, C.c_float, C.c_float, vp]
+        L.orc_light_sample.restype = C.c_int32
+        L.orc_eval_ggx.argtypes = [vp, vp, C.c_float, vp, vp]
         L.orc_render_tiles.argtypes = [vp, C.POINTER(_Camera), C.POINTER(_Params), u32, u32,
                                        C.POINTER(_Outputs)]
         _lib = L
@@ -166,6 +174,46 @@ class Scene:
             self.h = None
 
 
+def eval_ggx(wo, wi, alpha, f0):
+    """GGX BSDF value f(wo, wi) (tangent frame) -> float64[3]."""
+    wo = np.ascontiguousarray(wo, dtype=np.float32)
+    wi = np.ascontiguousarray(wi, dtype=np.float32)
+    f0 = np.ascontiguousarray(f0, dtype=np.float32)
+    f = np.zeros(3, dtype=np.float64)
+    lib().orc_eval_ggx(_p(wo), _p(wi), float(np.float32(alpha)), _p(f0), _p(f))
+    return f
+
+
+def triangle_area(v9) -> float:
+    v = np.ascontiguousarray(v9, dtype=np.float32).reshape(9)
+    return lib().orc_triangle_area(_p(v))
+
+
+def lights(scene) -> tuple:
+    """(number of emitter triangles, total emitter area as float32)."""
+    tot = np.zeros(1, dtype=np.float32)
+    n = lib().orc_scene_lights(scene.h, _p(tot))
+    return n, tot[0]
+
+
+def light_sample(scene, u0, u1, u2):
+    """-> (emitter's original triangle index, point float32[3])."""
+    p = np.zeros(3, dtype=np.float32)
+    t = lib().orc_light_sample(scene.h, float(np.float32(u0)), float(np.float32(u1)), float(np.float32(u2)), _p(p))
+    return t, p
+
+
+def shadow(scene, rays, skip=None, use_bvh=True):
+    """Visibility of (n, 8) fp32 shadow rays (tmax in column 7) -> (occluded, fragile) uint8."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32)
+    n = rays.shape[0]
+    sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.int32)
+    occ = np.zeros(n, dtype=np.uint8)
+    fr = np.zeros(n, dtype=np.uint8)
+    lib().orc_shadow(scene.h, _p(rays), _p(sk), n, int(use_bvh), _p(occ), _p(fr))
+    return occ, fr
+
+
 def trace(scene: Scene, rays, skip=None, use_bvh=True):
     """Closest hit of (n, 8) fp32 rays -> (prim int32, t float64, fragile uint8)."""
     rays = np.ascontiguousarray(rays, dtype=np.float32)
@@ -180,12 +228,13 @@ def trace(scene: Scene, rays, skip=None, use_bvh=True):
 
 def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=None,
            interleave=True, seed=0, frame_base=0, reuse_depth=0, debug=False, threads=None,
-           tiles=None, accum=None):
+           tiles=None, accum=None, nee=False):
     """Run the oracle path tracer.  Returns a dict with ``rgb`` (mean radiance, float64 h x w x 3),
     ``taint`` (h x w uint8), ``counters`` and, with debug=True (spp 1), per-bounce arrays.
     ``tiles`` = (begin, end) restricts the work to a tile range (other pixels stay 0).
     ``accum`` (npx x 3 float64) continues an earlier accumulation in place (progressive
-    rendering resumed at ``frame_base``)."""
+    rendering resumed at ``frame_base``).  ``nee`` adds next-event estimation (one light
+    sample and shadow ray per non-specular shading point)."""
     W, H = tile
     K = W * H if k is None else k
     w, h = cam.width, cam.height
@@ -205,10 +254,10 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
     camc = _Camera((C.c_float * 3)(*cam.pos), (C.c_float * 3)(*cam.look_at), (C.c_float * 3)(*cam.up),
                    cam.vfov_deg, w, h)
     par = _Params(spp, B, MODES[mode] if isinstance(mode, str) else mode, W, H, K, int(interleave),
-                  frame_base, reuse_depth, 0, seed)
+                  frame_base, reuse_depth, int(bool(nee)), seed)
     nthreads = threads or max(1, min(os.cpu_count() or 1, t1 - t0))
     bounds = np.linspace(t0, t1, nthreads + 1).astype(int)
-    counters = np.zeros((nthreads, 3), dtype=np.uint64)
+    counters = np.zeros((nthreads, 5), dtype=np.uint64)
 
     def work(i):
         o = _Outputs(_p(accum), _p(taint), _p(dbg.get("prim")), _p(dbg.get("cat")), _p(dbg.get("cls")),

@@ -12,6 +12,9 @@
  *             member's exit direction; glossy: unchanged; hybrid: diffuse members take the
  *             average tangent-space exit direction of the glossy/specular members).
  *   Sec. 3.1  world-space direct reuse, kept only as the ablation / negative control.
+ * Next-event estimation (one light sample per non-specular shading point, shadow ray for
+ * visibility) is an optional standard path-tracing estimator the paper does not discuss;
+ * its readings are stated where it is implemented.
  * Intersection is a plain Moller-Trumbore test in FP64 over a median-split BVH (or all
  * triangles).  Choices the paper leaves open are stated where they are made.
  *
@@ -32,6 +35,7 @@
 #define TAG_CAMERA 0x43414D45u /* "CAME" */
 #define TAG_BSDF 0x42534446u   /* "BSDF" */
 #define TAG_INTL 0x494E544Cu   /* "INTL" */
+#define TAG_LITE 0x4C495445u   /* "LITE" */
 
 #define MAT_LAMBERT 0u
 #define MAT_GGX 1u
@@ -166,6 +170,7 @@ void orc_sincos(float x, float* s, float* c) {
     *c = 1.0f + x2 * pc;
 }
 
+#define PI_D 3.14159265358979323846
 #define PI4F 0x1.921fb6p-1f
 #define PI2F 0x1.921fb6p+0f
 #define INV_SQRT2F 0x1.6a09e6p-1f
@@ -260,6 +265,38 @@ int orc_sample_ggx(const float* wo, float alpha, const float* f0, float u1, floa
     return 1;
 }
 
+/* GGX reflection BSDF value f(wo, wi) (both in the tangent frame, z up), the density that
+ * orc_sample_ggx draws from: f = D(h) G1(wo) G1(wi) F(wo.h) / (4 wo.z wi.z) with the
+ * half vector h = normalize(wo + wi), D(h) = alpha^2 / (pi (1 + (alpha^2 - 1) h.z^2)^2)
+ * (Walter et al. 2007, Eq. 33), the same Smith G1 and Schlick F.  Zero below either side.
+ * Evaluated in double. */
+void orc_eval_ggx(const float* wo, const float* wi, float alpha, const float* f0, double* f) {
+    f[0] = f[1] = f[2] = 0.0;
+    double o[3] = {wo[0], wo[1], wo[2]}, i[3] = {wi[0], wi[1], wi[2]};
+    if (!(o[2] > 0.0) || !(i[2] > 0.0)) return;
+    double h[3] = {o[0] + i[0], o[1] + i[1], o[2] + i[2]};
+    double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    if (!(hl > 0.0)) return;
+    for (int k = 0; k < 3; ++k) h[k] /= hl;
+    double a2 = (double)alpha * (double)alpha;
+    double q = 1.0 + (a2 - 1.0) * h[2] * h[2];
+    double D = a2 / (PI_D * q * q);
+    double g = 1.0;
+    for (int side = 0; side < 2; ++side) {
+        double z = side ? i[2] : o[2];
+        double tan2 = (1.0 - z * z) / (z * z);
+        if (tan2 < 0.0) tan2 = 0.0;
+        g *= 2.0 / (1.0 + sqrt(1.0 + a2 * tan2));
+    }
+    double oh = o[0] * h[0] + o[1] * h[1] + o[2] * h[2];
+    if (!(oh > 0.0)) return;
+    double p5 = pow(1.0 - oh, 5.0);
+    for (int k = 0; k < 3; ++k) {
+        double F = f0[k] + (1.0 - f0[k]) * p5;
+        f[k] = D * g * F / (4.0 * o[2] * i[2]);
+    }
+}
+
 /* Orthonormal basis from a unit normal: Duff et al., "Building an Orthonormal Basis,
  * Revisited" (JCGT 2017).  Depends on n only, so coplanar points share a frame. */
 static void onb(f3 n, f3* t, f3* b) {
@@ -300,6 +337,11 @@ struct orc_scene {
     uint32_t n_nodes, cap_nodes;
     uint32_t* order;
     double max_abs;
+    /* emitter triangles (original ids, ascending) and their cumulative areas */
+    uint32_t n_light;
+    uint32_t* light_tri;
+    float* light_cdf;
+    float light_total;
 };
 
 static double* g_sort_key; /* qsort has no context argument in C11 */
@@ -357,6 +399,20 @@ static uint32_t build_node(orc_scene* s, double* cen, uint32_t lo, uint32_t hi) 
     return id;
 }
 
+/* Area of a triangle given by 9 floats: half the length of the cross product of two edges,
+ * in double. */
+double orc_triangle_area(const float* v) {
+    double e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = (double)v[3 + k] - (double)v[k];
+        e2[k] = (double)v[6 + k] - (double)v[k];
+    }
+    double cx = e1[1] * e2[2] - e1[2] * e2[1];
+    double cy = e1[2] * e2[0] - e1[0] * e2[2];
+    double cz = e1[0] * e2[1] - e1[1] * e2[0];
+    return 0.5 * sqrt((cx * cx + cy * cy) + cz * cz);
+}
+
 orc_scene* orc_scene_new(const float* tri_xyz, uint32_t n_tri, const uint32_t* tri_mat,
                          const uint32_t* mat_type, const float* mat_params, uint32_t n_mat,
                          const float* env) {
@@ -387,6 +443,26 @@ orc_scene* orc_scene_new(const float* tri_xyz, uint32_t n_tri, const uint32_t* t
     s->n_nodes = 0;
     if (n_tri > 0) build_node(s, cen, 0, n_tri);
     free(cen);
+    /* Light table for next-event estimation: every emitter triangle in index order, with
+     * the running sum of the areas (computed in double from the FP32 vertices) rounded to
+     * float.  An emitter is chosen with probability proportional to its area. */
+    s->n_light = 0;
+    for (uint32_t t = 0; t < n_tri; ++t)
+        if (tri_mat[t] < n_mat && mat_type[tri_mat[t]] == MAT_EMITTER) s->n_light++;
+    s->light_tri = (uint32_t*)malloc(sizeof(uint32_t) * (s->n_light ? s->n_light : 1));
+    s->light_cdf = (float*)malloc(sizeof(float) * (s->n_light ? s->n_light : 1));
+    {
+        double run = 0.0;
+        uint32_t i = 0;
+        for (uint32_t t = 0; t < n_tri; ++t) {
+            if (!(tri_mat[t] < n_mat && mat_type[tri_mat[t]] == MAT_EMITTER)) continue;
+            run += orc_triangle_area(&s->v[9 * t]);
+            s->light_tri[i] = t;
+            s->light_cdf[i] = (float)run;
+            ++i;
+        }
+        s->light_total = s->n_light ? s->light_cdf[s->n_light - 1] : 0.0f;
+    }
     return s;
 }
 
@@ -398,6 +474,8 @@ void orc_scene_free(orc_scene* s) {
     free(s->mat_params);
     free(s->nodes);
     free(s->order);
+    free(s->light_tri);
+    free(s->light_cdf);
     free(s);
 }
 
@@ -431,6 +509,7 @@ typedef struct {
     double hits_t[64];
     int32_t hits_id[64];
     double hits_terr[64]; /* FP32 error scale of t for each hit */
+    int hits_edge[64];    /* the ray passes within eta of the hit triangle's boundary */
     int n_hits;
     double terr_best;
 } tstate;
@@ -543,6 +622,7 @@ static void test_triangle(const orc_scene* s, uint32_t tri, tstate* st) {
             st->hits_t[st->n_hits] = t;
             st->hits_id[st->n_hits] = (int32_t)tri;
             st->hits_terr[st->n_hits] = terr;
+            st->hits_edge[st->n_hits] = near_edge;
             st->n_hits++;
         } else {
             st->fragile = 1;
@@ -585,8 +665,9 @@ static int box_hit(const onode* nd, const tstate* st, double pad, double tcull) 
     return tn <= tf && tn <= tcull;
 }
 
-static void trace_ray(const orc_scene* s, const double* o, const double* d, int32_t skip, int use_bvh,
-                      int32_t* prim, double* tout, uint8_t* fragile) {
+/* Closest-hit search; leaves the hits, the near-edge candidates and the winner in st. */
+static void traverse(const orc_scene* s, const double* o, const double* d, int32_t skip, int use_bvh, tstate* stp,
+                     double* omax_out) {
     tstate st;
     memset(&st, 0, sizeof(st));
     for (int k = 0; k < 3; ++k) {
@@ -631,6 +712,15 @@ static void trace_ray(const orc_scene* s, const double* o, const double* d, int3
             }
         }
     }
+    *stp = st;
+    *omax_out = omax;
+}
+
+static void trace_ray(const orc_scene* s, const double* o, const double* d, int32_t skip, int use_bvh,
+                      int32_t* prim, double* tout, uint8_t* fragile) {
+    tstate st;
+    double omax;
+    traverse(s, o, d, skip, use_bvh, &st, &omax);
     if (st.found) {
         double eta_t = 16.0 * 0x1.0p-24 * (2.0 * (omax + s->max_abs)) / st.dlen;
         double band = st.tbest * 1e-6 + eta_t;
@@ -649,6 +739,70 @@ static void trace_ray(const orc_scene* s, const double* o, const double* d, int3
      * ray origin relative to the coordinates' magnitude) */
     int tbad = st.found && st.terr_best > 1e-5 * st.tbest;
     *fragile = (uint8_t)((st.fragile ? 1 : 0) | (tbad ? 2 : 0));
+}
+
+/* Visibility of a shadow ray: occluded when some triangle other than `skip` is hit at
+ * 0 < t < tmax (t in units of d).  Fragile when an FP32 traversal could decide differently:
+ * unless a hit well before tmax (by the band below) on a triangle whose boundary the ray
+ * does not graze settles it, any grazed triangle in front of tmax, any hit within the band
+ * of tmax, or a candidate at the ray origin makes the answer fragile. */
+static void shadow_ray(const orc_scene* s, const double* o, const double* d, double tmax, int32_t skip,
+                       int use_bvh, int* occluded, int* fragile) {
+    tstate st;
+    double omax;
+    traverse(s, o, d, skip, use_bvh, &st, &omax);
+    double eta_t = 16.0 * 0x1.0p-24 * (2.0 * (omax + s->max_abs)) / st.dlen;
+    double band = tmax * 1e-6 + eta_t;
+    *occluded = st.found && st.tbest < tmax;
+    int robust = 0;
+    for (int i = 0; i < st.n_hits; ++i)
+        if (st.hits_t[i] < tmax - band && !st.hits_edge[i]) robust = 1;
+    int fr = 0;
+    if (!robust) {
+        for (int i = 0; i < st.n_hits; ++i)
+            if (st.hits_t[i] <= tmax + band) fr = 1;
+        for (int i = 0; i < st.n_threat; ++i)
+            if (st.threat_tlo[i] < tmax + band) fr = 1;
+        if (st.fragile || st.threat_overflow || st.n_hits >= 64) fr = 1;
+    }
+    *fragile = fr;
+}
+
+void orc_shadow(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n, int use_bvh,
+                uint8_t* occluded, uint8_t* fragile) {
+    for (uint32_t i = 0; i < n; ++i) {
+        double o[3] = {rays[8 * i + 0], rays[8 * i + 1], rays[8 * i + 2]};
+        double d[3] = {rays[8 * i + 4], rays[8 * i + 5], rays[8 * i + 6]};
+        int oc, fr;
+        shadow_ray(s, o, d, (double)rays[8 * i + 7], skip_prim ? skip_prim[i] : -1, use_bvh, &oc, &fr);
+        occluded[i] = (uint8_t)oc;
+        fragile[i] = (uint8_t)fr;
+    }
+}
+
+/* Light sample for next-event estimation from three uniforms in [0, 1).
+ * Emitter choice: x = u0 * total (float); the first emitter whose running area exceeds x
+ * (the last one if rounding leaves none), i.e. probability area / total.
+ * Point: uniform on the triangle by the square-root map (Shirley & Chiu / Turk 1990):
+ * with s = sqrt(u1), p = (1 - s) v0 + s (1 - u2) v1 + s u2 v2, in float.
+ * Returns the emitter's original triangle index, -1 if the scene has no emitter. */
+int32_t orc_light_sample(const orc_scene* s, float u0, float u1, float u2, float* p) {
+    if (s->n_light == 0) return -1;
+    float x = u0 * s->light_total;
+    uint32_t i = 0;
+    while (i < s->n_light && !(x < s->light_cdf[i])) ++i;
+    if (i == s->n_light) i = s->n_light - 1;
+    const uint32_t t = s->light_tri[i];
+    const float* v = &s->v[9 * t];
+    float sq = sqrtf(u1);
+    float b0 = 1.0f - sq, b1 = sq * (1.0f - u2), b2 = sq * u2;
+    for (int k = 0; k < 3; ++k) p[k] = (v[k] * b0 + v[3 + k] * b1) + v[6 + k] * b2;
+    return (int32_t)t;
+}
+
+uint32_t orc_scene_lights(const orc_scene* s, float* total) {
+    if (total) *total = s->light_total;
+    return s->n_light;
 }
 
 void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n, int use_bvh,
@@ -711,6 +865,8 @@ typedef struct {
     int32_t pixel; /* -1: slot of a pixel outside the image */
     int alive;
     int taint;
+    int staint;    /* a fragile shadow-ray decision of this pixel (does not spread to its group) */
+    int see_emit;  /* emission met by the next trace counts: camera rays, after a mirror, no NEE */
     float beta[3];
     double L[3];
     double o[3];
@@ -791,6 +947,78 @@ static f3 tree_sum(f3* v, uint32_t k) {
     return v[0];
 }
 
+/* Spawn point of the next ray: p = o + t d in FP64, offset along the shading normal by
+ * 2^-18 max(1, |p|_inf), so that the new ray clears the surface it leaves. */
+static void spawn_point(const pstate* ps, double* out) {
+    double pt[3], amax = 1.0;
+    double dd[3] = {ps->d.x, ps->d.y, ps->d.z};
+    for (int k = 0; k < 3; ++k) {
+        pt[k] = ps->o[k] + ps->t * dd[k];
+        if (fabs(pt[k]) > amax) amax = fabs(pt[k]);
+    }
+    double eps = 0x1.0p-18 * amax;
+    double nn[3] = {ps->n.x, ps->n.y, ps->n.z};
+    for (int k = 0; k < 3; ++k) out[k] = pt[k] + eps * nn[k];
+}
+
+#define SHADOW_TMAX (1.0 - 0x1.0p-10) /* shadow rays run to 1 - 2^-10 of the way to the light point */
+#define NEE_COS_FRAGILE 1e-4
+
+/* Next-event estimation at a non-specular shading point (a standard estimator; the paper
+ * is silent): one emitter point drawn by area, p_A = 1 / total emitter area, and
+ *   L += beta f(wo, wi) Le cos_i cos_l / r^2 / p_A   if the shadow ray reaches it,
+ * with wi toward the point, cos_i at the shading point, cos_l at the (two-sided) emitter.
+ * Emission that a BSDF-sampled ray then meets is not counted again (see see_emit), so
+ * the estimate has the same mean as plain path tracing. */
+static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32_t bounce, pstate* ps,
+                       uint64_t* counters) {
+    uint32_t h[4];
+    philox_seed(seed, (uint32_t)ps->pixel, frame, bounce, TAG_LITE, h);
+    float pl[3];
+    int32_t lt = orc_light_sample(s, to_unit(h[0]), to_unit(h[1]), to_unit(h[2]), pl);
+    if (lt < 0) return;
+    double o[3], dl[3];
+    spawn_point(ps, o);
+    for (int k = 0; k < 3; ++k) dl[k] = (double)pl[k] - o[k];
+    double r2 = ddot(dl, dl);
+    if (!(r2 > 0.0)) return;
+    double r = sqrt(r2);
+    double nn[3] = {ps->n.x, ps->n.y, ps->n.z};
+    double cos_i = ddot(nn, dl) / r;
+    const float* lv = &s->v[9 * lt];
+    double e1[3], e2[3], nl[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = (double)lv[3 + k] - (double)lv[k];
+        e2[k] = (double)lv[6 + k] - (double)lv[k];
+    }
+    dcross(e1, e2, nl);
+    double cos_l = fabs(ddot(nl, dl)) / (sqrt(ddot(nl, nl)) * r);
+    if (fabs(cos_i) < NEE_COS_FRAGILE || cos_l < NEE_COS_FRAGILE) ps->staint = 1;
+    if (!(cos_i > 0.0) || !(cos_l > 0.0)) return;
+    int occluded, fragile;
+    shadow_ray(s, o, dl, SHADOW_TMAX, ps->hit, 1, &occluded, &fragile);
+    counters[3]++;
+    if (fragile) {
+        ps->staint = 1;
+        counters[4]++;
+    }
+    if (occluded) return;
+    const float* mp = &s->mat_params[7 * ps->mat];
+    const float* le = &s->mat_params[7 * s->tri_mat[lt] + 4];
+    double f[3];
+    if (s->mat_type[ps->mat] == MAT_LAMBERT) {
+        for (int k = 0; k < 3; ++k) f[k] = (double)mp[k] / PI_D;
+    } else {
+        double wi[3] = {dl[0] / r, dl[1] / r, dl[2] / r};
+        double T[3] = {ps->T.x, ps->T.y, ps->T.z}, B[3] = {ps->B.x, ps->B.y, ps->B.z};
+        float wil[3] = {(float)ddot(T, wi), (float)ddot(B, wi), (float)ddot(nn, wi)};
+        float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z};
+        orc_eval_ggx(wo, wil, mp[3], mp, f);
+    }
+    double g = cos_i * cos_l / r2 * (double)s->light_total;
+    for (int k = 0; k < 3; ++k) ps->L[k] += (double)ps->beta[k] * f[k] * (double)le[k] * g;
+}
+
 static void trace_path(const orc_scene* s, pstate* ps, uint64_t* counters) {
     int32_t prim;
     double t;
@@ -815,7 +1043,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
     uint32_t* sigma = (uint32_t*)malloc(sizeof(uint32_t) * m);
     pstate* slot = (pstate*)malloc(sizeof(pstate) * m);
     f3* sumbuf = (f3*)malloc(sizeof(f3) * K);
-    uint64_t cnt_local[3] = {0, 0, 0};
+    uint64_t cnt_local[5] = {0, 0, 0, 0, 0};
 
     for (uint32_t si = 0; si < p->spp; ++si) {
         const uint32_t f = p->frame_base + si;
@@ -831,6 +1059,8 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                 ps->pixel = (int32_t)(py * w + px);
                 ps->alive = 1;
                 ps->taint = 0;
+                ps->staint = 0;
+                ps->see_emit = 1;
                 ps->beta[0] = ps->beta[1] = ps->beta[2] = 1.0f;
                 ps->L[0] = ps->L[1] = ps->L[2] = 0.0;
                 uint32_t hc[4];
@@ -857,11 +1087,13 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                     uint32_t mt = s->mat_type[s->tri_mat[ps->hit]];
                     if (mt == MAT_EMITTER) {
                         const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]);
+                        if (!p->nee || ps->see_emit)
+                            for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]);
                         ps->alive = 0;
                         continue;
                     }
                     shade_setup(s, ps);
+                    if (p->nee && s->mat_type[ps->mat] != MAT_MIRROR) next_event(s, p->seed, f, b, ps, cnt_local);
                 }
                 const int reuse_now = (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
                                       (p->reuse_depth == 0 || b <= p->reuse_depth);
@@ -954,17 +1186,11 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                             ps->alive = 0;
                             continue;
                         }
-                        /* spawn: p = o + t d in FP64, offset along the shading normal */
-                        double pt[3], amax = 1.0;
-                        double dd[3] = {ps->d.x, ps->d.y, ps->d.z};
-                        for (int k = 0; k < 3; ++k) {
-                            pt[k] = ps->o[k] + ps->t * dd[k];
-                            if (fabs(pt[k]) > amax) amax = fabs(pt[k]);
-                        }
-                        double eps = 0x1.0p-18 * amax;
-                        double nn[3] = {ps->n.x, ps->n.y, ps->n.z};
-                        for (int k = 0; k < 3; ++k) ps->o[k] = pt[k] + eps * nn[k];
+                        double o2[3];
+                        spawn_point(ps, o2);
+                        for (int k = 0; k < 3; ++k) ps->o[k] = o2[k];
                         ps->d = to_world(ps, ps->wl);
+                        ps->see_emit = !p->nee || s->mat_type[ps->mat] == MAT_MIRROR;
                         for (int k = 0; k < 3; ++k) ps->beta[k] = ps->beta[k] * ps->w[k];
                     }
                 }
@@ -984,21 +1210,18 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                 if (ps->alive) {
                     if (ps->hit < 0) {
                         for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
-                    } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER) {
+                    } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER && (!p->nee || ps->see_emit)) {
                         const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
                         for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]);
                     }
                 }
                 for (int k = 0; k < 3; ++k) out->accum[3 * ps->pixel + k] += ps->L[k];
-                if (out->taint && ps->taint) out->taint[ps->pixel] = 1;
+                if (out->taint && (ps->taint || ps->staint)) out->taint[ps->pixel] = 1;
             }
         }
     }
-    if (out->counters) {
-        out->counters[0] += cnt_local[0];
-        out->counters[1] += cnt_local[1];
-        out->counters[2] += cnt_local[2];
-    }
+    if (out->counters)
+        for (int k = 0; k < 5; ++k) out->counters[k] += cnt_local[k];
     free(sigma);
     free(slot);
     free(sumbuf);

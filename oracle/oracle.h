@@ -65,6 +65,24 @@ uint32_t orc_scene_nodes(const orc_scene* s);
 void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
                int use_bvh, int32_t* prim, double* t, uint8_t* fragile);
 
+/* Shadow rays (n x 8 floats: origin, unused, direction, tmax): occluded if a triangle other
+ * than skip_prim[i] is hit at 0 < t < tmax; fragile if FP32 could decide otherwise. */
+void orc_shadow(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
+                int use_bvh, uint8_t* occluded, uint8_t* fragile);
+
+/* Area of the triangle given by 9 floats (double arithmetic). */
+double orc_triangle_area(const float* v);
+
+/* Emitter triangles of the scene and their total area (float running sum). */
+uint32_t orc_scene_lights(const orc_scene* s, float* total);
+
+/* Light sample from uniforms (u0: emitter by area, u1 u2: point); returns the emitter's
+ * original triangle index (-1: no emitter) and the point in p[3]. */
+int32_t orc_light_sample(const orc_scene* s, float u0, float u1, float u2, float* p);
+
+/* GGX BSDF value f(wo, wi) in the tangent frame (double). */
+void orc_eval_ggx(const float* wo, const float* wi, float alpha, const float* f0, double* f);
+
 typedef struct {
     float pos[3], look_at[3], up[3];
     float vfov_deg;
@@ -77,7 +95,7 @@ typedef struct {
     uint32_t spp, max_bounces, mode;
     uint32_t tile_w, tile_h, k, interleave;
     uint32_t frame_base, reuse_depth; /* reuse at bounces b <= reuse_depth; 0 = all */
-    uint32_t pad;
+    uint32_t nee;                     /* 1: next-event estimation at non-specular points */
     uint64_t seed;
 } orc_params;
 
@@ -91,7 +109,8 @@ typedef struct {
     uint8_t* dbg_flags; /* B*npx: bit0 alive at step b, bit1 spawned a ray, bit2 tainted */
     float* dbg_local;   /* B*npx*3: tangent-space exit direction */
     float* dbg_world;   /* B*npx*3: world-space exit direction */
-    uint64_t* counters; /* [0] primary rays, [1] secondary rays, [2] fragile decisions */
+    uint64_t* counters; /* [0] primary rays, [1] secondary rays, [2] fragile decisions,
+                           [3] shadow rays, [4] fragile shadow decisions */
 } orc_outputs;
 
 /* Render tiles [tile_begin, tile_end) of the image (Sec. 3, whole method). */

@@ -317,6 +317,39 @@ def interior(seed: int = 11, n_spheres: int = 2000, width: int = 1280, height: i
                    seed=seed)
 
 
+def emitter_box(floor=MAT_LAMBERT, floor_params=(0.6, 0.5, 0.4, 0.3), le=(1.0, 1.0, 1.0), n_spheres=0,
+                seed: int = 3, width: int = 32, height: int = 32) -> Scene:
+    """Closed box [-1,1]^3 lit by its own walls: the floor (y = -1, triangles 8 and 9) has the
+    material ``floor`` (params: albedo rgb, roughness) and the five other faces emit ``le``;
+    the environment is black.  Without occluders every floor point sees emitters over its
+    whole upper hemisphere (irradiance pi * le), so a Lambert floor's outgoing radiance is
+    exactly albedo * le.  ``n_spheres`` UV spheres (radius 0.1-0.25; Lambert, GGX and mirror
+    in turn) add occlusion and all three material classes."""
+    rng = np.random.default_rng(seed)
+    box = _box_room((-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))
+    mtype = [floor, MAT_EMITTER, MAT_LAMBERT, MAT_GGX, MAT_MIRROR]
+    params = np.zeros((5, 7))
+    params[0, 0:4] = floor_params
+    params[1, 4:7] = le
+    params[2, 0:3] = (0.5, 0.6, 0.7)
+    params[3, 0:4] = (0.8, 0.7, 0.5, 0.25)
+    params[4, 0:3] = (0.9, 0.9, 0.9)
+    tri_mat = np.full(12, 1)
+    tri_mat[8:10] = 0
+    sph, sph_mat = [], []
+    for s in range(n_spheres):
+        r = rng.uniform(0.1, 0.25)
+        c = (rng.uniform(-1 + r, 1 - r), rng.uniform(-1 + r, 0.2), rng.uniform(-0.3, 1 - r))
+        t = uv_sphere(c, r)
+        sph.append(t)
+        sph_mat.append(np.full(t.shape[0], 2 + s % 3))
+    tris = np.concatenate([box] + sph, axis=0)
+    tri_mat = np.concatenate([tri_mat] + sph_mat)
+    cam = Camera((0.0, 0.5, -0.95), (0.0, -1.0, 0.4), (0.0, 1.0, 0.0), 60.0, width, height)
+    return _finish(f"emitter_box{n_spheres}", tris, tri_mat, np.array(mtype), params, (0.0, 0.0, 0.0), cam,
+                   seed=seed)
+
+
 def terrain(seed: int = 51, n_grid: int = 2236, width: int = 1024, height: int = 1024) -> Scene:
     """Large terrain: the landscape generator on a 2236^2 grid (9,990,450 triangles)."""
     return landscape(seed=seed, n_grid=n_grid, width=width, height=height, mat_seed=seed + 1)
