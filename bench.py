@@ -329,6 +329,7 @@ def run_ours(args):
     if not args.core_only:
         extras["precision_interior"] = precision_leg(cr, scenes, rank, world, args)
         extras["table3_sweep"] = sweep_leg(cr, S, cam, out, stream, rank, world)
+        extras["next_event_estimation"] = nee_leg(cr, scenes, rank, args)
         extras["quality"] = quality_leg(cr, S, cam, stream, results)
         if not args.no_batched:
             extras["batched"] = batched_leg(cr, scenes, rank, args)
@@ -441,6 +442,59 @@ def precision_leg(cr, scenes, rank, world, args):
     res["nodes"] = {"bvh2": S8.info["n_nodes2"], "bvh8q": S8.info["n_nodes8"]}
     S8.close()
     return res
+
+
+def nee_leg(cr, scenes, rank, args):
+    """Next-event estimation on the interior (640x360, 512,014 triangles, small ceiling light,
+    4 bounces): ray throughput with shadow rays, and MSE at equal device time against a
+    2048-spp independent + NEE reference (both estimators have the same mean)."""
+    import torch
+    sc = scenes.interior(width=640, height=360)
+    S = cr.Scene(sc)
+    cam = sc.camera
+    stream = torch.cuda.current_stream().cuda_stream
+    img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    ref = torch.zeros_like(img)
+    B = 4
+
+    def render(spp, mode, nee, frame, stats=None):
+        o = cr.make_opts(k=K, frame_base=frame, stream=stream, stats=stats,
+                         flags=(cr.CR_OPT_NEE if nee else 0) | (cr.CR_OPT_STATS if stats is not None else 0))
+        cr.cr_render_ex(S.handle, cam, spp, B, mode, TILE[0], TILE[1], img, o)
+
+    n_ref = 2048
+    for c in range(0, n_ref, 256):
+        render(256, "independent", True, 5_000_000 + c)
+        ref += img
+    ref /= n_ref // 256
+    torch.cuda.synchronize()
+    out = {"workload": "interior 640x360, 512,014 tris, 4 bounces, 8x8 K=8", "reference_spp": n_ref,
+           "budgets_s": [0.05, 0.25], "modes": {}}
+    for mode in ("direction_reuse", "independent"):
+        for nee in (False, True):
+            ms = sec = shadow = tsh = 0.0
+            for i in range(5):
+                st = cr.cr_stats()
+                render(1, mode, nee, rank * 100 + i, st)
+                if i >= 2:
+                    d = st.as_dict()
+                    ms += d["ms_total"]
+                    sec += d["secondary_rays"]
+                    shadow += d["shadow_rays"]
+                    tsh += d["ms_trace_shadow"]
+            ms_spp = ms / 3
+            row = {"ms_per_spp": round(ms_spp, 4), "mrays_incl_shadow": round((sec + shadow) / ms / 1e3, 1),
+                   "secondary_rays_per_spp": int(sec / 3), "shadow_rays_per_spp": int(shadow / 3), "mse": [], "spp": []}
+            if nee:
+                row["shadow_trace_mrays"] = round(shadow / tsh / 1e3, 1) if tsh > 0 else None
+            for T in out["budgets_s"]:
+                spp = max(1, int(T * 1e3 / ms_spp))
+                render(spp, mode, nee, 0)
+                row["mse"].append(float(((img - ref) ** 2).mean()))
+                row["spp"].append(spp)
+            out["modes"][mode + ("+nee" if nee else "")] = row
+    S.close()
+    return out
 
 
 def sweep_leg(cr, S, cam, out, stream, rank, world):

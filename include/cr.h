@@ -94,10 +94,11 @@ typedef struct {
     uint32_t n_tri, n_mat;
     uint32_t n_nodes2, depth2; /* BVH2 inner nodes, maximum leaf depth */
     uint32_t n_nodes8;         /* BVH8-Q nodes (0 if not built) */
-    uint32_t pad;
+    uint32_t n_lights;         /* emitter triangles (light samples of next-event estimation) */
     uint64_t device_bytes;     /* scene bytes resident on the device */
     double build_ms;           /* host build time */
     float bounds_lo[3], bounds_hi[3];
+    float light_area;          /* total emitter area: float running sum of the areas (below) */
 } cr_scene_info;
 
 cr_status cr_scene_get_info(const cr_scene* scene, cr_scene_info* info);
@@ -125,6 +126,8 @@ typedef struct {
     uint64_t secondary_rays_b1;/* rays traced at bounce 1 */
     uint64_t kernel_launches;  /* library kernels launched by the call */
     uint64_t node_visits, tri_tests; /* counting pass only (CR_OPT_COUNT) */
+    uint64_t shadow_rays;      /* shadow rays of next-event estimation (CR_OPT_NEE) */
+    double ms_trace_shadow;    /* their any-hit trace */
 } cr_stats;
 
 /* Optional per-bounce capture (device pointers, spp must be 1).  npx = width * height.
@@ -147,7 +150,9 @@ enum {
     CR_OPT_SPECULATIVE = 16u, /* speculative traversal with a parked leaf per lane (BVH2) */
     CR_OPT_PACKET_PRIMARY = 32u,  /* warp-packet traversal of primary rays (BVH2) */
     CR_OPT_PACKET_SECONDARY = 64u, /* warp-packet traversal of secondary rays (BVH2) */
-    CR_OPT_TWO_PHASE = 128u /* secondary rays: 32-visit budget, compact the unfinished, resume (BVH2) */
+    CR_OPT_TWO_PHASE = 128u, /* secondary rays: 32-visit budget, compact the unfinished, resume (BVH2) */
+    CR_OPT_NEE = 256u,     /* cr_render: next-event estimation (the job flag CR_JOB_NEE) */
+    CR_OPT_ANY_HIT = 512u  /* cr_trace_rays: visibility only (any hit before tmax, see there) */
 };
 
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):
@@ -214,9 +219,28 @@ typedef struct {
     uint32_t reuse_depth;/* 0 = every bounce */
     uint64_t seed;
     uint32_t frame_base;
-    uint32_t pad;
+    uint32_t flags;      /* CR_JOB_* */
     float* out_rgb;      /* DEVICE buffer of width*height*3 floats */
 } cr_job;                /* 96 bytes */
+
+/* Next-event estimation (a standard path-tracing estimator the paper does not discuss; it
+ * leaves the reuse of exit directions unchanged).  At every shading point that is not a
+ * mirror, one emitter point is drawn and joined by a shadow ray:
+ *   emitter  x = u0 * A (float), A = the float running sum of the emitter triangles' areas
+ *            in triangle-index order, each area 0.5 |(v1 - v0) x (v2 - v0)| in double; the
+ *            first emitter whose running sum exceeds x (the last if none), i.e. by area;
+ *   point    s = sqrt(u1), p = (1 - s) v0 + s (1 - u2) v1 + s u2 v2 (float);
+ *   (u0, u1, u2) from Philox(seed; pixel, frame, bounce, "LITE").
+ * The shadow ray leaves from the spawn point of the path's next ray toward p and ends at
+ * 1 - 2^-10 of the way; if nothing blocks it, L += w_l beta f Le cos_i cos_l A / r^2 (cos_l
+ * at the two-sided emitter).  Emission that the path's next BSDF-sampled ray meets is
+ * weighed by 1 - w_l of that direction: multiple importance sampling with the power
+ * heuristic, w_l = p_l^2 / (p_l^2 + p_b^2), p_l = r^2 / (cos_l A) the light sample's
+ * solid-angle density and p_b the shading point's own BSDF density (cos / pi, or the GGX
+ * reflection density; mirrors and camera rays keep full emission).  Where the continuation
+ * direction has density p_b (independent sampling, diffuse and glossy groups) the mean
+ * equals plain path tracing's. */
+enum { CR_JOB_NEE = 1u };
 
 enum { CR_BATCH_GRAPH = 1u /* capture the launch sequence once, replay it on every run */ };
 
@@ -309,7 +333,10 @@ cr_status cr_server_destroy(cr_server* server);
  *   prim      host or device, n int32: original index of the closest hit, -1 if none.
  *   t         host or device, n floats: hit distance in units of |d| (inf if none).
  * Hit rule: watertight test (Woop et al. 2013), t > 0, edges inclusive; equal t goes to the
- * smaller original index.  opts may be NULL (bvh, block, stream, flags are read). */
+ * smaller original index.  opts may be NULL (bvh, block, stream, flags are read).
+ * With CR_OPT_ANY_HIT in opts->flags the traversal stops at the first triangle hit before
+ * tmax (the shadow-ray kernel's traversal): prim is then some occluder (not necessarily the
+ * closest) and t its distance, or -1 and inf if the ray reaches tmax unblocked. */
 cr_status cr_trace_rays(cr_scene* scene, const float* rays, const int32_t* skip_prim, uint32_t n,
                         int32_t* prim, float* t, const cr_render_opts* opts);
 

@@ -90,6 +90,8 @@ def lib():
         L.orc_light_sample.argtypes = [vp, C.c_float, C.c_float, C.c_float, vp]
         L.orc_light_sample.restype = C.c_int32
         L.orc_eval_ggx.argtypes = [vp, vp, C.c_float, vp, vp]
+        L.orc_pdf_ggx.argtypes = [vp, vp, C.c_float]
+        L.orc_pdf_ggx.restype = C.c_double
         L.orc_render_tiles.argtypes = [vp, C.POINTER(_Camera), C.POINTER(_Params), u32, u32,
                                        C.POINTER(_Outputs)]
         _lib = L
@@ -182,6 +184,13 @@ def eval_ggx(wo, wi, alpha, f0):
     f = np.zeros(3, dtype=np.float64)
     lib().orc_eval_ggx(_p(wo), _p(wi), float(np.float32(alpha)), _p(f0), _p(f))
     return f
+
+
+def pdf_ggx(wo, wi, alpha) -> float:
+    """Solid-angle density of sample_ggx's direction wi."""
+    wo = np.ascontiguousarray(wo, dtype=np.float32)
+    wi = np.ascontiguousarray(wi, dtype=np.float32)
+    return lib().orc_pdf_ggx(_p(wo), _p(wi), float(np.float32(alpha)))
 
 
 def triangle_area(v9) -> float:

@@ -297,6 +297,24 @@ void orc_eval_ggx(const float* wo, const float* wi, float alpha, const float* f0
     }
 }
 
+/* Density in solid angle with which orc_sample_ggx draws wi: the microfacet normal h has
+ * density D(h) h.z and the reflection maps it with Jacobian 1 / (4 wo.h), so
+ * pdf(wi) = D(h) h.z / (4 wo.h), h = normalize(wo + wi); 0 below either side. */
+double orc_pdf_ggx(const float* wo, const float* wi, float alpha) {
+    double o[3] = {wo[0], wo[1], wo[2]}, i[3] = {wi[0], wi[1], wi[2]};
+    if (!(o[2] > 0.0) || !(i[2] > 0.0)) return 0.0;
+    double h[3] = {o[0] + i[0], o[1] + i[1], o[2] + i[2]};
+    double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    if (!(hl > 0.0)) return 0.0;
+    for (int k = 0; k < 3; ++k) h[k] /= hl;
+    double oh = o[0] * h[0] + o[1] * h[1] + o[2] * h[2];
+    if (!(oh > 0.0)) return 0.0;
+    double a2 = (double)alpha * (double)alpha;
+    double q = 1.0 + (a2 - 1.0) * h[2] * h[2];
+    double D = a2 / (PI_D * q * q);
+    return D * h[2] / (4.0 * oh);
+}
+
 /* Orthonormal basis from a unit normal: Duff et al., "Building an Orthonormal Basis,
  * Revisited" (JCGT 2017).  Depends on n only, so coplanar points share a frame. */
 static void onb(f3 n, f3* t, f3* b) {
@@ -866,7 +884,7 @@ typedef struct {
     int alive;
     int taint;
     int staint;    /* a fragile shadow-ray decision of this pixel (does not spread to its group) */
-    int see_emit;  /* emission met by the next trace counts: camera rays, after a mirror, no NEE */
+    double pdf;    /* solid-angle density of the direction just traced (0: camera ray or mirror) */
     float beta[3];
     double L[3];
     double o[3];
@@ -947,6 +965,39 @@ static f3 tree_sum(f3* v, uint32_t k) {
     return v[0];
 }
 
+/* Solid-angle density with which the shading point's own BSDF sampling draws the
+ * tangent-space direction wl: cos / pi (Lambert), the GGX reflection density (GGX), 0 for
+ * the mirror's delta distribution (its emission is never weighed). */
+static double bsdf_pdf(const orc_scene* s, const pstate* ps, f3 wl) {
+    uint32_t ty = s->mat_type[ps->mat];
+    if (ty == MAT_LAMBERT) return wl.z > 0.0f ? (double)wl.z / PI_D : 0.0;
+    if (ty == MAT_GGX) {
+        float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z}, wi[3] = {wl.x, wl.y, wl.z};
+        return orc_pdf_ggx(wo, wi, s->mat_params[7 * ps->mat + 3]);
+    }
+    return 0.0;
+}
+
+/* MIS weight of emission met by the path's last trace (power heuristic): the ray's
+ * direction had density ps->pdf (0: camera ray or mirror, weight 1); a light sample would
+ * have reached the same point with density r^2 / (cos_l A). */
+static double emit_weight(const orc_scene* s, const pstate* ps) {
+    if (ps->pdf == 0.0) return 1.0;
+    const float* lv = &s->v[9 * ps->hit];
+    double e1[3], e2[3], nl[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = (double)lv[3 + k] - (double)lv[k];
+        e2[k] = (double)lv[6 + k] - (double)lv[k];
+    }
+    dcross(e1, e2, nl);
+    double d[3] = {ps->d.x, ps->d.y, ps->d.z};
+    double dd = ddot(d, d);
+    double cos_l = fabs(ddot(nl, d)) / sqrt(ddot(nl, nl) * dd);
+    if (!(cos_l > 0.0)) return 1.0;
+    double p_l = ps->t * ps->t * dd / (cos_l * (double)s->light_total);
+    return ps->pdf * ps->pdf / (ps->pdf * ps->pdf + p_l * p_l);
+}
+
 /* Spawn point of the next ray: p = o + t d in FP64, offset along the shading normal by
  * 2^-18 max(1, |p|_inf), so that the new ray clears the surface it leaves. */
 static void spawn_point(const pstate* ps, double* out) {
@@ -965,11 +1016,16 @@ static void spawn_point(const pstate* ps, double* out) {
 #define NEE_COS_FRAGILE 1e-4
 
 /* Next-event estimation at a non-specular shading point (a standard estimator; the paper
- * is silent): one emitter point drawn by area, p_A = 1 / total emitter area, and
- *   L += beta f(wo, wi) Le cos_i cos_l / r^2 / p_A   if the shadow ray reaches it,
+ * is silent): one emitter point drawn by area, p_A = 1 / total emitter area A, and
+ *   L += w_l beta f(wo, wi) Le cos_i cos_l / r^2 / p_A   if the shadow ray reaches it,
  * with wi toward the point, cos_i at the shading point, cos_l at the (two-sided) emitter.
- * Emission that a BSDF-sampled ray then meets is not counted again (see see_emit), so
- * the estimate has the same mean as plain path tracing. */
+ * The same emission can also be met by the path's next BSDF-sampled ray; the two
+ * estimates are combined by multiple importance sampling with the power heuristic (Veach
+ * & Guibas 1995): in solid angle the light sample has density p_l = r^2 / (cos_l A) and the
+ * BSDF density p_b is the shading point's own (bsdf_pdf); w_l = p_l^2 / (p_l^2 + p_b^2),
+ * and an emitter hit by the BSDF-sampled ray weighs its emission by the complement
+ * (emit_weight).  Both weights use the same two densities, so the estimate keeps the
+ * mean of plain path tracing whenever the continuation direction has density p_b. */
 static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32_t bounce, pstate* ps,
                        uint64_t* counters) {
     uint32_t h[4];
@@ -1005,17 +1061,21 @@ static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
     if (occluded) return;
     const float* mp = &s->mat_params[7 * ps->mat];
     const float* le = &s->mat_params[7 * s->tri_mat[lt] + 4];
+    /* the light direction in the shading frame */
+    double wi[3] = {dl[0] / r, dl[1] / r, dl[2] / r};
+    double T[3] = {ps->T.x, ps->T.y, ps->T.z}, B[3] = {ps->B.x, ps->B.y, ps->B.z};
+    f3 wil = f3m((float)ddot(T, wi), (float)ddot(B, wi), (float)ddot(nn, wi));
     double f[3];
     if (s->mat_type[ps->mat] == MAT_LAMBERT) {
         for (int k = 0; k < 3; ++k) f[k] = (double)mp[k] / PI_D;
     } else {
-        double wi[3] = {dl[0] / r, dl[1] / r, dl[2] / r};
-        double T[3] = {ps->T.x, ps->T.y, ps->T.z}, B[3] = {ps->B.x, ps->B.y, ps->B.z};
-        float wil[3] = {(float)ddot(T, wi), (float)ddot(B, wi), (float)ddot(nn, wi)};
-        float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z};
-        orc_eval_ggx(wo, wil, mp[3], mp, f);
+        float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z}, wv[3] = {wil.x, wil.y, wil.z};
+        orc_eval_ggx(wo, wv, mp[3], mp, f);
     }
-    double g = cos_i * cos_l / r2 * (double)s->light_total;
+    double p_l = r2 / (cos_l * (double)s->light_total);
+    double p_b = bsdf_pdf(s, ps, wil);
+    double wl = p_l * p_l / (p_l * p_l + p_b * p_b);
+    double g = cos_i * cos_l / r2 * (double)s->light_total * wl;
     for (int k = 0; k < 3; ++k) ps->L[k] += (double)ps->beta[k] * f[k] * (double)le[k] * g;
 }
 
@@ -1060,7 +1120,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                 ps->alive = 1;
                 ps->taint = 0;
                 ps->staint = 0;
-                ps->see_emit = 1;
+                ps->pdf = 0.0;
                 ps->beta[0] = ps->beta[1] = ps->beta[2] = 1.0f;
                 ps->L[0] = ps->L[1] = ps->L[2] = 0.0;
                 uint32_t hc[4];
@@ -1087,8 +1147,8 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                     uint32_t mt = s->mat_type[s->tri_mat[ps->hit]];
                     if (mt == MAT_EMITTER) {
                         const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        if (!p->nee || ps->see_emit)
-                            for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]);
+                        double wb = p->nee ? emit_weight(s, ps) : 1.0;
+                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
                         ps->alive = 0;
                         continue;
                     }
@@ -1190,7 +1250,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         spawn_point(ps, o2);
                         for (int k = 0; k < 3; ++k) ps->o[k] = o2[k];
                         ps->d = to_world(ps, ps->wl);
-                        ps->see_emit = !p->nee || s->mat_type[ps->mat] == MAT_MIRROR;
+                        ps->pdf = bsdf_pdf(s, ps, ps->wl);
                         for (int k = 0; k < 3; ++k) ps->beta[k] = ps->beta[k] * ps->w[k];
                     }
                 }
@@ -1210,9 +1270,10 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                 if (ps->alive) {
                     if (ps->hit < 0) {
                         for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
-                    } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER && (!p->nee || ps->see_emit)) {
+                    } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER) {
                         const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]);
+                        double wb = p->nee ? emit_weight(s, ps) : 1.0;
+                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
                     }
                 }
                 for (int k = 0; k < 3; ++k) out->accum[3 * ps->pixel + k] += ps->L[k];

@@ -80,6 +80,9 @@ uint32_t orc_scene_lights(const orc_scene* s, float* total);
  * original triangle index (-1: no emitter) and the point in p[3]. */
 int32_t orc_light_sample(const orc_scene* s, float u0, float u1, float u2, float* p);
 
+/* Solid-angle density of orc_sample_ggx's direction wi (double). */
+double orc_pdf_ggx(const float* wo, const float* wi, float alpha);
+
 /* GGX BSDF value f(wo, wi) in the tangent frame (double). */
 void orc_eval_ggx(const float* wo, const float* wi, float alpha, const float* f0, double* f);
 

@@ -27,6 +27,8 @@ CR_BVH2, CR_BVH8Q = 1, 2
 CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE, CR_WORLD_REUSE = 0, 1, 2, 3
 CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIVE = 1, 2, 4, 8, 16
 CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY, CR_OPT_TWO_PHASE = 32, 64, 128
+CR_OPT_NEE, CR_OPT_ANY_HIT = 256, 512
+CR_JOB_NEE = 1
 MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE,
          "world_reuse": CR_WORLD_REUSE}
 
@@ -48,8 +50,9 @@ class cr_env(C.Structure):
 
 class cr_scene_info(C.Structure):
     _fields_ = [("n_tri", C.c_uint32), ("n_mat", C.c_uint32), ("n_nodes2", C.c_uint32), ("depth2", C.c_uint32),
-                ("n_nodes8", C.c_uint32), ("pad", C.c_uint32), ("device_bytes", C.c_uint64),
-                ("build_ms", C.c_double), ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3)]
+                ("n_nodes8", C.c_uint32), ("n_lights", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("build_ms", C.c_double), ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3),
+                ("light_area", C.c_float)]
 
 
 class cr_camera(C.Structure):
@@ -62,7 +65,8 @@ class cr_stats(C.Structure):
                 ("ms_trace_secondary", C.c_double), ("ms_shade", C.c_double), ("ms_compact", C.c_double),
                 ("ms_sort", C.c_double), ("ms_accum", C.c_double), ("primary_rays", C.c_uint64),
                 ("secondary_rays", C.c_uint64), ("secondary_rays_b1", C.c_uint64),
-                ("kernel_launches", C.c_uint64), ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64),
+                ("shadow_rays", C.c_uint64), ("ms_trace_shadow", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,7 +87,7 @@ class cr_debug(C.Structure):
 class cr_job(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("camera", cr_camera), ("spp", C.c_uint32), ("max_bounces", C.c_uint32),
                 ("mode", C.c_uint32), ("reuse_depth", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
-                ("pad", C.c_uint32), ("out_rgb", C.c_void_p)]
+                ("flags", C.c_uint32), ("out_rgb", C.c_void_p)]
 
 
 class cr_batch_opts(C.Structure):
@@ -299,8 +303,9 @@ CR_BATCH_GRAPH = 1
 
 
 def make_job(scene_handle, cam, out, spp=1, max_bounces=1, mode="direction_reuse", reuse_depth=0, seed=0,
-             frame_base=0) -> cr_job:
+             frame_base=0, nee=False) -> cr_job:
     j = cr_job()
+    j.flags = CR_JOB_NEE if nee else 0
     j.scene = scene_handle
     j.camera = make_camera(cam)
     j.spp, j.max_bounces, j.mode, j.reuse_depth = spp, max_bounces, MODES.get(mode, mode), reuse_depth
@@ -444,7 +449,7 @@ class Scene:
 
     def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
                seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
-               debug=None, stream=None, sort_key=0):
+               debug=None, stream=None, sort_key=0, nee=False):
         """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
         CUDA tensor by default).  Returns (out, stats dict or None)."""
         import torch
@@ -453,13 +458,16 @@ class Scene:
             out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
         st = cr_stats() if stats else None
         o = make_opts(k=k, interleave=interleave, seed=seed, frame_base=frame_base, reuse_depth=reuse_depth, bvh=bvh,
-                      block=block, flags=flags | (CR_OPT_STATS if stats else 0), stream=stream, stats=st,
+                      block=block, flags=flags | (CR_OPT_STATS if stats else 0) | (CR_OPT_NEE if nee else 0),
+                      stream=stream, stats=st,
                       debug=debug, sort_key=sort_key)
         cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
         return out, (st.as_dict() if st is not None else None)
 
-    def trace(self, rays, skip=None, *, bvh=CR_BVH2, flags=0, block=0, stats=False):
-        """Closest hits of (n, 8) rays (torch CUDA tensor or numpy) -> (prim, t[, stats])."""
+    def trace(self, rays, skip=None, *, bvh=CR_BVH2, flags=0, block=0, stats=False, any_hit=False):
+        """Closest hits of (n, 8) rays (torch CUDA tensor or numpy) -> (prim, t[, stats]).
+        any_hit: visibility only (some occluder before tmax, or -1)."""
+        flags |= CR_OPT_ANY_HIT if any_hit else 0
         import torch
         n = rays.shape[0]
         dev = rays.device if isinstance(rays, torch.Tensor) and rays.is_cuda else None

@@ -120,6 +120,7 @@ struct cr_scene {
     void* d_tris = nullptr;
     void* d_tris8 = nullptr;
     void* d_mats = nullptr;
+    void* d_lights = nullptr; // emitter records and their running areas (one allocation)
     cr::SceneDev* d_entries = nullptr; // [0] BVH2 layout, [1] BVH8-Q layout (scene-table entries)
     // render workspace and job tables, grown on demand
     cr::Workspace ws;
@@ -219,6 +220,34 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
         mt[8 * m + 6] = mats[m].emission[1];
         mt[8 * m + 7] = mats[m].emission[2];
     }
+    // Emitter table for next-event estimation: triangle-index order, 4 float4 per emitter
+    // (v0|orig, v1, v2, emission) and the float running sum of the areas, each area
+    // 0.5 |(v1 - v0) x (v2 - v0)| evaluated in double.
+    std::vector<float> lrec, lcdf;
+    {
+        double run = 0.0;
+        for (uint32_t t = 0; t < n_tri; ++t) {
+            const cr_material& mm = mats[tri_mat[t]];
+            if (mm.type != CR_MAT_EMITTER) continue;
+            const float* v = &tri_xyz[9 * (size_t)t];
+            double e1[3], e2[3];
+            for (int k = 0; k < 3; ++k) {
+                e1[k] = (double)v[3 + k] - (double)v[k];
+                e2[k] = (double)v[6 + k] - (double)v[k];
+            }
+            const double cx = e1[1] * e2[2] - e1[2] * e2[1];
+            const double cy = e1[2] * e2[0] - e1[0] * e2[2];
+            const double cz = e1[0] * e2[1] - e1[1] * e2[0];
+            run += 0.5 * std::sqrt((cx * cx + cy * cy) + cz * cz);
+            lcdf.push_back((float)run);
+            int32_t orig = (int32_t)t;
+            float ob;
+            std::memcpy(&ob, &orig, 4);
+            const float rec[16] = {v[0], v[1], v[2], ob, v[3], v[4], v[5], 0.0f, v[6], v[7], v[8], 0.0f,
+                                   mm.emission[0], mm.emission[1], mm.emission[2], 0.0f};
+            lrec.insert(lrec.end(), rec, rec + 16);
+        }
+    }
     const auto t1 = std::chrono::steady_clock::now();
     DevMem dn, dt, dm;
     CR_CUDA(dn.alloc(b2.nodes.size() * sizeof(float)));
@@ -234,6 +263,21 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
         CR_CUDA(cudaMemcpy(dn8.p, b8.nodes.data(), dn8.bytes, cudaMemcpyHostToDevice));
         CR_CUDA(cudaMemcpy(dt8.p, tris8.data(), dt8.bytes, cudaMemcpyHostToDevice));
     }
+    DevMem dl;
+    const uint32_t n_lights = (uint32_t)lcdf.size();
+    if (n_lights) {
+        CR_CUDA(dl.alloc(lrec.size() * 4 + lcdf.size() * 4));
+        CR_CUDA(cudaMemcpy(dl.p, lrec.data(), lrec.size() * 4, cudaMemcpyHostToDevice));
+        CR_CUDA(cudaMemcpy(static_cast<char*>(dl.p) + lrec.size() * 4, lcdf.data(), lcdf.size() * 4,
+                           cudaMemcpyHostToDevice));
+    }
+    s->d_lights = dl.p;
+    dl.p = nullptr;
+    s->dev.lights = static_cast<const float4*>(s->d_lights);
+    s->dev.light_cdf = n_lights ? reinterpret_cast<const float*>(static_cast<const char*>(s->d_lights) + lrec.size() * 4)
+                                : nullptr;
+    s->dev.n_lights = n_lights;
+    s->dev.light_total = n_lights ? lcdf.back() : 0.0f;
     s->d_nodes2 = dn.p;
     s->d_tris = dt.p;
     s->d_mats = dm.p;
@@ -266,7 +310,10 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     s->info.n_nodes2 = b2.n_nodes;
     s->info.depth2 = b2.depth;
     s->info.n_nodes8 = b8.n_nodes;
-    s->info.device_bytes = b2.nodes.size() * 4 + tris.size() * 4 + mt.size() * 4 + b8.nodes.size() * 4 + tris8.size() * 4;
+    s->info.device_bytes = b2.nodes.size() * 4 + tris.size() * 4 + mt.size() * 4 + b8.nodes.size() * 4 + tris8.size() * 4 +
+                           lrec.size() * 4 + lcdf.size() * 4;
+    s->info.n_lights = n_lights;
+    s->info.light_area = s->dev.light_total;
     s->info.build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     for (int k = 0; k < 3; ++k) {
         s->info.bounds_lo[k] = b2.lo[k];
@@ -294,6 +341,7 @@ extern "C" cr_status cr_scene_destroy(cr_scene* s) {
     if (s->d_tris) cudaFree(s->d_tris);
     if (s->d_tris8) cudaFree(s->d_tris8);
     if (s->d_mats) cudaFree(s->d_mats);
+    if (s->d_lights) cudaFree(s->d_lights);
     if (s->d_entries) cudaFree(s->d_entries);
     delete s;
     return CR_OK;
@@ -383,6 +431,30 @@ void Workspace::release() {
     phase_base = nullptr;
     phase_slots = 0;
     phase = PhaseBuffers();
+    if (nee_base) cudaFree(nee_base);
+    nee_base = nullptr;
+    nee_slots = 0;
+}
+
+// Shadow-ray records of next-event estimation (48 bytes per slot), allocated after ensure().
+cr_status Workspace::ensure_nee(uint32_t n_slots) {
+    if (nee_base && nee_slots >= n_slots && pb.shadow_d) return CR_OK;
+    if (nee_base) cudaFree(nee_base);
+    nee_base = nullptr;
+    nee_slots = 0;
+    cudaError_t e = cudaMalloc(&nee_base, 48 * (size_t)n_slots);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        nee_base = nullptr;
+        pb.shadow_o = pb.shadow_d = pb.shadow_c = nullptr;
+        return fail(CR_ERR_OOM, "shadow-ray buffers: %s", cudaGetErrorString(e));
+    }
+    float4* f = static_cast<float4*>(nee_base);
+    pb.shadow_o = f;
+    pb.shadow_d = f + n_slots;
+    pb.shadow_c = f + 2 * (size_t)n_slots;
+    nee_slots = n_slots;
+    return CR_OK;
 }
 
 #ifndef CR_PHASE_BUDGET
@@ -480,6 +552,7 @@ cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h) {
     if (j.max_bounces == 0 || j.max_bounces > 16)
         return fail(CR_ERR_INVALID_ARG, "max_bounces %u not in [1, 16]", j.max_bounces);
     if (j.mode > CR_WORLD_REUSE) return fail(CR_ERR_INVALID_ARG, "unknown mode %u", j.mode);
+    if (j.flags & ~(uint32_t)CR_JOB_NEE) return fail(CR_ERR_INVALID_ARG, "unknown job flags 0x%x", j.flags);
     (void)tile_w;
     (void)tile_h;
     return CR_OK;
@@ -553,6 +626,8 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
                     if (j.mode == CR_WORLD_REUSE) d.world_mask |= 1u << b;
                 }
             d.interleave = po.interleave ? 1u : 0u;
+            d.nee = (j.flags & CR_JOB_NEE) ? 1u : 0u;
+            if (d.nee) plan.nee = true;
             d.seed = j.seed;
             d.out = j.out_rgb;
             d.inv_spp = 1.0f / (float)j.spp;
@@ -635,6 +710,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         P.k = p.k;
         P.n_tiles = ps.n_tiles;
         P.npx = eo.debug_npx;
+        P.nee = p.nee;
         const uint32_t n_slots = ps.n_tiles * p.m;
         b.n_groups = n_slots / p.k;
         ev.begin(stream, times ? &times->raygen : &dummy);
@@ -655,6 +731,11 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             ev.begin(stream, times ? &times->shade : &dummy);
             launch_shade(P, b, bnc == 1, eo.debug, stream, lc);
             ev.end();
+            if (P.nee && b.shadow_d) {
+                ev.begin(stream, times ? &times->trace_shadow : &dummy);
+                launch_shadow(P, b, bnc == 1, p.bvh8, stream, lc);
+                ev.end();
+            }
             ev.begin(stream, times ? &times->compact : &dummy);
             launch_compact(P, b, bnc == 1, stream, lc);
             ev.end();
@@ -737,6 +818,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     job.reuse_depth = o.reuse_depth;
     job.seed = o.seed;
     job.frame_base = o.frame_base;
+    job.flags = (o.flags & CR_OPT_NEE) ? CR_JOB_NEE : 0u;
     job.out_rgb = out_dev ? out_rgb : s->d_out;
     PlanOpts po;
     po.tile_w = group_w;
@@ -749,6 +831,10 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     if (st != CR_OK) return st;
     st = s->ws.ensure(plan.max_slots, plan.npx_total);
     if (st != CR_OK) return st;
+    if (plan.nee) {
+        st = s->ws.ensure_nee(plan.max_slots);
+        if (st != CR_OK) return st;
+    }
     Plan& dev = s->plan_dev;
     st = dev.upload(plan, stream);
     if (st != CR_OK) return st;
@@ -802,6 +888,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         const uint64_t* ctr = host_counts + kCounterWord / 2;
         stats.node_visits = ctr[0];
         stats.tri_tests = ctr[1];
+        stats.shadow_rays = host_counts[kShadowWord / 2];
+        stats.ms_trace_shadow = times.trace_shadow;
         stats.primary_rays = (uint64_t)npx * spp;
         stats.kernel_launches = lc.n;
         *o.stats = stats;
@@ -900,6 +988,7 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     ta.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
     ta.speculative = (o.flags & CR_OPT_SPECULATIVE) != 0;
     ta.packet = (o.flags & (CR_OPT_PACKET_PRIMARY | CR_OPT_PACKET_SECONDARY)) != 0;
+    ta.any_hit = (o.flags & CR_OPT_ANY_HIT) != 0;
     ta.bvh8 = use8;
     ta.scenes = dev_scene_entry(s, use8);
     ta.slot_scene = nullptr;
@@ -1082,7 +1171,7 @@ extern "C" cr_status cr_batch_device_bytes(const cr_job* jobs, uint32_t n_jobs, 
     st = build_plan(jobs, n_jobs, po, plan);
     if (st != CR_OK) return st;
     *bytes = workspace_bytes(plan.max_slots, plan.npx_total) + sizeof(JobDev) * plan.jobs.size() +
-             sizeof(SceneDev) * plan.scenes.size();
+             sizeof(SceneDev) * plan.scenes.size() + (plan.nee ? 48 * (uint64_t)plan.max_slots : 0);
     return CR_OK;
 }
 
@@ -1110,6 +1199,10 @@ extern "C" cr_status cr_batch_create(const cr_job* jobs, uint32_t n_jobs, const 
     }
     st = b->ws.ensure(b->plan.max_slots, b->plan.npx_total);
     if (st != CR_OK) return st;
+    if (b->plan.nee) {
+        st = b->ws.ensure_nee(b->plan.max_slots);
+        if (st != CR_OK) return st;
+    }
     st = b->dev.upload(b->plan, b->stream);
     if (st != CR_OK) return st;
     CR_CUDA(cudaStreamSynchronize(b->stream));
@@ -1166,6 +1259,7 @@ extern "C" cr_status cr_batch_run(cr_batch* b, cr_stats* stats) {
         const uint64_t* stat = host_counts + kStatWord / 2;
         for (uint32_t bb = 1; bb <= b->plan.max_bounces; ++bb) stats->secondary_rays += stat[bb];
         stats->secondary_rays_b1 = stat[1];
+        stats->shadow_rays = host_counts[kShadowWord / 2];
         uint64_t prim = 0;
         for (const cr_job& j : b->jobs) prim += (uint64_t)j.camera.width * j.camera.height * j.spp;
         stats->primary_rays = prim;

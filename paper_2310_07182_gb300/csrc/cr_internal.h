@@ -68,6 +68,11 @@ struct DevScene {
     float env[3] = {0, 0, 0};
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     uint32_t n_tri = 0, n_mat = 0;
+    // emitter triangles for next-event estimation
+    const float* light_cdf = nullptr; // float running sum of the areas, triangle-index order
+    const float4* lights = nullptr;   // 4 per emitter: v0|orig, v1|0, v2|0, emission|0
+    uint32_t n_lights = 0;
+    float light_total = 0.0f;
 };
 
 // One entry of the device scene table a pass reads (tris in the order of the BVH traversed).
@@ -78,6 +83,10 @@ struct SceneDev {
     const float4* mats;
     float env[4];
     float lo[4], hi[4];
+    const float* light_cdf;
+    const float4* lights;
+    uint32_t n_lights;
+    float light_total;
 };
 SceneDev scene_entry(const DevScene& s, bool bvh8);
 
@@ -105,6 +114,7 @@ struct JobDev {
     float* out;           // device output (w*h*3 floats) of the job
     float inv_spp;
     uint32_t world_mask;  // bit b: world-space direct reuse (Sec. 3.1 ablation) at bounce b
+    uint32_t nee;         // 1: next-event estimation
 };
 
 // Launch-uniform description of a pass.
@@ -116,6 +126,7 @@ struct PassArgs {
     uint32_t n_tiles = 0;  // tiles of all jobs of the pass
     uint32_t bounce = 0;   // shade: 1..B (B + 1 = final)
     uint32_t npx = 0;      // pixels of the debug capture (single-job renders)
+    bool nee = false;      // some job of the plan uses next-event estimation
 };
 
 // Per-call launch statistics.
@@ -159,6 +170,7 @@ struct TraceArgs {
     bool persistent = false;
     bool speculative = false; // parked-leaf speculative traversal (BVH2)
     bool packet = false;      // warp-packet traversal (BVH2)
+    bool any_hit = false;     // stop at the first hit before tmax (visibility)
     bool two_phase = false;   // budgeted traversal, compaction of unfinished rays, resume (BVH2)
     PhaseBuffers phase;
     bool bvh8 = false;
@@ -190,6 +202,11 @@ struct PathBuffers {
     // visits and triangle tests of the counting pass.
     uint32_t* counts = nullptr;
     uint32_t* block_counts = nullptr; // compaction scratch (2 per block) + offsets
+    // next-event estimation (allocated on first use): shadow ray origin|skip, direction|tmax
+    // (w < 0: no shadow ray), unoccluded contribution rgb
+    float4* shadow_o = nullptr;
+    float4* shadow_d = nullptr;
+    float4* shadow_c = nullptr;
     uint32_t n_blocks_cap = 0;
     // Morton sort
     uint32_t* keys = nullptr;   // 2 x n_slots
@@ -201,7 +218,14 @@ struct PathBuffers {
     unsigned long long* counters = nullptr; // counting pass
 };
 
-constexpr uint32_t kCountsWords = 256, kStatWord = 64, kCounterWord = 128;
+constexpr uint32_t kCountsWords = 256, kStatWord = 64, kCounterWord = 128, kShadowWord = 200;
+// Shadow rays of the last shade (positions of its group queue): any-hit traversal, and the
+// contribution of each unblocked one added to the path radiance.
+void launch_shadow(const PassArgs& p, PathBuffers& b, bool first, bool bvh8, cudaStream_t st, LaunchCount& lc);
+void launch_shadow_rays(const SceneDev* scenes, const uint16_t* slot_scene, const float4* sh_o, const float4* sh_d,
+                        const float4* sh_c, const int32_t* group_queue, const uint32_t* group_count,
+                        uint32_t n_groups_max, uint32_t K, float4* radiance, unsigned long long* n_traced, bool bvh8,
+                        cudaStream_t st, LaunchCount& lc);
 
 void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
 void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,
@@ -231,6 +255,10 @@ struct Workspace {
     PathBuffers pb;
     void* base = nullptr;
     size_t bytes = 0;
+    // shadow-ray buffers of next-event estimation, allocated on first use
+    void* nee_base = nullptr;
+    uint32_t nee_slots = 0;
+    cr_status ensure_nee(uint32_t n_slots);
     // two-phase trace buffers, allocated on first use
     void* phase_base = nullptr;
     uint32_t phase_slots = 0;
@@ -254,6 +282,7 @@ struct Pass {
 struct RenderPlan {
     uint32_t tile_w = 0, tile_h = 0, m = 0, k = 0;
     bool bvh8 = false, sort = false;
+    bool nee = false; // some job uses next-event estimation
     uint32_t max_bounces = 0, max_slots = 0, npx_total = 0;
     std::vector<JobDev> jobs;     // all passes' tables, pass by pass
     std::vector<SceneDev> scenes; // scene table
@@ -281,6 +310,7 @@ struct ExecOpts {
 };
 struct StageTimes {
     double raygen = 0, trace_primary = 0, trace_secondary = 0, shade = 0, compact = 0, sort = 0, accum = 0;
+    double trace_shadow = 0;
 };
 cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, RenderPlan& plan);
 cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h);

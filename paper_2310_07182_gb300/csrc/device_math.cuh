@@ -15,6 +15,7 @@ namespace dev {
 constexpr uint32_t kTagCamera = 0x43414D45u;     // "CAME"
 constexpr uint32_t kTagBsdf = 0x42534446u;       // "BSDF"
 constexpr uint32_t kTagInterleave = 0x494E544Cu; // "INTL"
+constexpr uint32_t kTagLight = 0x4C495445u;      // "LITE"
 
 constexpr uint32_t kMatLambert = 0, kMatGGX = 1, kMatMirror = 2, kMatEmitter = 3;
 constexpr int kClsNone = 0, kClsDiffuse = 1, kClsGlossy = 2;
@@ -165,6 +166,51 @@ __device__ __forceinline__ bool sample_ggx(V3 wo, float alpha, const float* f0, 
         w[k] = fd(fm(fm(F, g), d), den);
     }
     return true;
+}
+
+// GGX reflection value f(wo, wi) in the tangent frame: the density sample_ggx draws from,
+// D(h) G1(wo) G1(wi) F(wo.h) / (4 wo.z wi.z) with h = normalize(wo + wi) and
+// D(h) = alpha^2 / (pi (1 + (alpha^2 - 1) h.z^2)^2) (Walter et al. 2007); 0 below either side.
+__device__ __forceinline__ void eval_ggx(V3 wo, V3 wi, float alpha, const float* f0, float* f) {
+    f[0] = f[1] = f[2] = 0.0f;
+    if (!(wo.z > 0.0f) || !(wi.z > 0.0f)) return;
+    const V3 hs = v3(fa(wo.x, wi.x), fa(wo.y, wi.y), fa(wo.z, wi.z));
+    const float hl2 = dot3(hs, hs);
+    if (!(hl2 > 0.0f)) return;
+    const float hl = fq(hl2);
+    const V3 h = v3(fd(hs.x, hl), fd(hs.y, hl), fd(hs.z, hl));
+    const float oh = dot3(wo, h);
+    if (!(oh > 0.0f)) return;
+    const float a2 = fm(alpha, alpha);
+    const float q = fa(1.0f, fm(fs(a2, 1.0f), fm(h.z, h.z)));
+    const float D = fd(a2, fm(3.14159265358979f, fm(q, q)));
+    const float g = fm(smith_g1(wo.z, a2), smith_g1(wi.z, a2));
+    const float om = fs(1.0f, oh);
+    const float om2 = fm(om, om);
+    const float p5 = fm(fm(om2, om2), om);
+    const float den = fm(4.0f, fm(wo.z, wi.z));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float F = fa(f0[k], fm(fs(1.0f, f0[k]), p5));
+        f[k] = fd(fm(fm(D, g), F), den);
+    }
+}
+
+// Solid-angle density with which sample_ggx draws wi: D(h) h.z / (4 wo.h), h = normalize(wo + wi)
+// (the microfacet normal has density D(h) h.z; reflection has Jacobian 1 / (4 wo.h)).
+__device__ __forceinline__ float pdf_ggx(V3 wo, V3 wi, float alpha) {
+    if (!(wo.z > 0.0f) || !(wi.z > 0.0f)) return 0.0f;
+    const V3 hs = v3(fa(wo.x, wi.x), fa(wo.y, wi.y), fa(wo.z, wi.z));
+    const float hl2 = dot3(hs, hs);
+    if (!(hl2 > 0.0f)) return 0.0f;
+    const float hl = fq(hl2);
+    const V3 h = v3(fd(hs.x, hl), fd(hs.y, hl), fd(hs.z, hl));
+    const float oh = dot3(wo, h);
+    if (!(oh > 0.0f)) return 0.0f;
+    const float a2 = fm(alpha, alpha);
+    const float q = fa(1.0f, fm(fs(a2, 1.0f), fm(h.z, h.z)));
+    const float D = fd(a2, fm(3.14159265358979f, fm(q, q)));
+    return fd(fm(D, h.z), fm(4.0f, oh));
 }
 
 // Orthonormal basis (t, b, n) from a unit normal after Duff et al., "Building an

@@ -105,7 +105,7 @@ __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __re
         pixel[slot] = (int32_t)pix;
         ray_o[slot] = make_float4(J.cam.pos[0], J.cam.pos[1], J.cam.pos[2], __int_as_float(-1));
         ray_d[slot] = make_float4(d.x, d.y, d.z, INFINITY);
-        beta[slot] = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
+        beta[slot] = make_float4(1.0f, 1.0f, 1.0f, 0.0f); // w: direction density, 0 for camera rays
         radiance[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         alive[slot] = 1;
     } else {
@@ -146,6 +146,10 @@ struct ShadeArgs {
     uint32_t n_groups_max;
     cr_debug dbg;
     uint32_t npx;
+    // next-event estimation: shadow ray records per slot (NULL when no job uses it)
+    float4* shadow_o;
+    float4* shadow_d;
+    float4* shadow_c;
 };
 
 struct Member {
@@ -154,6 +158,10 @@ struct Member {
     bool final_pass; // the job's last secondary ray has been traced
     bool reuse;      // the job reuses directions at this bounce
     bool world;      // the job reuses world-space directions at this bounce (Sec. 3.1 ablation)
+    bool nee;        // the job uses next-event estimation
+    uint32_t scene;  // scene table index
+    uint32_t type;   // material type of the shading point
+    float rough;     // its roughness
     uint64_t seed;
     uint32_t frame;
     int cls;
@@ -187,9 +195,26 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     const uint32_t type = (uint32_t)__float_as_int(m0.x);
     mb.orig = __float_as_int(v0.w);
     if (type == kMatEmitter) {
-        L.x = fa(L.x, fm(bt.x, m1.y));
-        L.y = fa(L.y, fm(bt.y, m1.z));
-        L.z = fa(L.z, fm(bt.z, m1.w));
+        // under next-event estimation the emission met by a BSDF-sampled ray is weighed
+        // against the light sample that could have found it (power heuristic): the ray's
+        // direction had density beta.w (0: camera ray or mirror, full weight), a light sample
+        // density r^2 / (cos_l A)
+        float w = 1.0f;
+        if (mb.nee && bt.w > 0.0f) {
+            const V3 e0 = v3(v0.x, v0.y, v0.z);
+            const V3 nl = cross3(sub3(v3(v1.x, v1.y, v1.z), e0), sub3(v3(v2.x, v2.y, v2.z), e0));
+            const V3 d = v3(d4.x, d4.y, d4.z);
+            const float dd = dot3(d, d);
+            const float cl = fd(fabsf(dot3(nl, d)), fq(fm(dot3(nl, nl), dd)));
+            if (cl > 0.0f) {
+                const float th = __int_as_float(h.y);
+                const float pl = fd(fm(fm(th, th), dd), fm(cl, sc.light_total));
+                w = fd(fm(bt.w, bt.w), fa(fm(bt.w, bt.w), fm(pl, pl)));
+            }
+        }
+        L.x = fa(L.x, fm(fm(bt.x, m1.y), w));
+        L.y = fa(L.y, fm(fm(bt.y, m1.z), w));
+        L.z = fa(L.z, fm(fm(bt.z, m1.w), w));
         mb.alive = false;
         return;
     }
@@ -205,6 +230,8 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     const V3 md = v3(-d.x, -d.y, -d.z);
     mb.wo = v3(dot3(md, mb.t), dot3(md, mb.b), dot3(md, mb.n));
     mb.cls = type == kMatLambert ? kClsDiffuse : kClsGlossy;
+    mb.type = type;
+    mb.rough = m1.x;
     mb.albedo[0] = m0.y;
     mb.albedo[1] = m0.z;
     mb.albedo[2] = m0.w;
@@ -236,6 +263,92 @@ __device__ __forceinline__ void take_dir(Member& mb, V3 wl) {
     mb.valid = true;
 }
 
+// Spawn point of the slot's next ray: p = o + t d, offset along the shading normal by
+// 2^-18 max(1, |p|_inf) so that the new ray clears the surface it leaves.
+__device__ __forceinline__ V3 spawn_point(const ShadeArgs& a, int slot, V3 n) {
+    const float4 o4 = a.ray_o[slot];
+    const float4 d4 = a.ray_d[slot];
+    const float th = __int_as_float(a.hit[slot].y);
+    const float px = o4.x + th * d4.x, py = o4.y + th * d4.y, pz = o4.z + th * d4.z;
+    const float amax = fmaxf(1.0f, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
+    const float eps = 0x1.0p-18f * amax;
+    return v3(px + eps * n.x, py + eps * n.y, pz + eps * n.z);
+}
+
+// Solid-angle density with which the member's own BSDF draws the tangent-space direction
+// wl: cos / pi (Lambert), the GGX reflection density, 0 for the mirror's delta.
+__device__ __forceinline__ float own_pdf(const Member& mb, V3 wl) {
+    if (mb.type == kMatLambert) return wl.z > 0.0f ? fm(wl.z, 0.318309886f) : 0.0f;
+    if (mb.type == kMatGGX) return pdf_ggx(mb.wo, wl, mb.rough);
+    return 0.0f;
+}
+
+// Next-event estimation at a shading point that is not a mirror (a standard estimator the
+// paper does not discuss): one emitter point chosen by area, p_A = 1 / A, and the shadow ray
+// from the spawn point toward it (direction p - o, ending at 1 - 2^-10 of the way).  The
+// contribution w_l beta f Le cos_i cos_l A / r^2 is added by the shadow kernel if the ray is
+// unblocked; w_l = p_l^2 / (p_l^2 + p_b^2) is the power-heuristic weight of the light sample
+// (p_l = r^2 / (cos_l A), p_b = own_pdf).  Every active position writes its slot's record
+// (w < 0: no shadow ray).
+__device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p, int slot, const Member& mb,
+                                           const float4 bt) {
+    float4 dr = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    if (mb.alive && mb.nee && mb.type != kMatMirror) {
+        const SceneDev& sc = a.scenes[mb.scene];
+        if (sc.n_lights > 0) {
+            const uint4 r = philox_seed(mb.seed, (uint32_t)mb.pix, mb.frame, p.bounce, kTagLight);
+            const float u0 = unit24(r.x), u1 = unit24(r.y), u2 = unit24(r.z);
+            // the first emitter whose running area exceeds u0 * A (the last if none)
+            const float x = fm(u0, sc.light_total);
+            uint32_t lo = 0, hi = sc.n_lights;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (x < __ldg(&sc.light_cdf[mid])) hi = mid;
+                else lo = mid + 1;
+            }
+            const uint32_t li = lo < sc.n_lights ? lo : sc.n_lights - 1;
+            const float4 l0 = __ldg(&sc.lights[4 * li + 0]);
+            const float4 l1 = __ldg(&sc.lights[4 * li + 1]);
+            const float4 l2 = __ldg(&sc.lights[4 * li + 2]);
+            const float4 le = __ldg(&sc.lights[4 * li + 3]);
+            const float sq = fq(u1);
+            const float b0 = fs(1.0f, sq), b1 = fm(sq, fs(1.0f, u2)), b2 = fm(sq, u2);
+            const V3 pl = v3(fa(fa(fm(l0.x, b0), fm(l1.x, b1)), fm(l2.x, b2)),
+                             fa(fa(fm(l0.y, b0), fm(l1.y, b1)), fm(l2.y, b2)),
+                             fa(fa(fm(l0.z, b0), fm(l1.z, b1)), fm(l2.z, b2)));
+            const V3 o = spawn_point(a, slot, mb.n);
+            const V3 dl = sub3(pl, o);
+            const float r2 = dot3(dl, dl);
+            const float rl = fq(r2);
+            const float ci = fd(dot3(mb.n, dl), rl);
+            const V3 a0 = v3(l0.x, l0.y, l0.z);
+            const V3 nl = cross3(sub3(v3(l1.x, l1.y, l1.z), a0), sub3(v3(l2.x, l2.y, l2.z), a0));
+            const float cl = fd(fabsf(dot3(nl, dl)), fm(fq(dot3(nl, nl)), rl));
+            if (r2 > 0.0f && ci > 0.0f && cl > 0.0f) {
+                const V3 wi = v3(fd(dl.x, rl), fd(dl.y, rl), fd(dl.z, rl));
+                const V3 wil = v3(dot3(wi, mb.t), dot3(wi, mb.b), dot3(wi, mb.n));
+                float f[3];
+                if (mb.type == kMatLambert) {
+                    f[0] = fm(mb.albedo[0], 0.318309886f);
+                    f[1] = fm(mb.albedo[1], 0.318309886f);
+                    f[2] = fm(mb.albedo[2], 0.318309886f);
+                } else {
+                    eval_ggx(mb.wo, wil, mb.rough, mb.albedo, f);
+                }
+                const float pl = fd(r2, fm(cl, sc.light_total));
+                const float pb = own_pdf(mb, wil);
+                const float wlt = fd(fm(pl, pl), fa(fm(pl, pl), fm(pb, pb)));
+                const float g = fm(fm(fd(fm(ci, cl), r2), sc.light_total), wlt);
+                a.shadow_o[slot] = make_float4(o.x, o.y, o.z, __int_as_float(mb.orig));
+                a.shadow_c[slot] = make_float4(fm(fm(fm(bt.x, f[0]), le.x), g), fm(fm(fm(bt.y, f[1]), le.y), g),
+                                               fm(fm(fm(bt.z, f[2]), le.z), g), 0.0f);
+                dr = make_float4(dl.x, dl.y, dl.z, 1.0f - 0x1.0p-10f);
+            }
+        }
+    }
+    a.shadow_d[slot] = dr;
+}
+
 __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs& p, int slot, Member& mb,
                                               float3 L, float4 bt, bool was_alive, int cat) {
     if (a.dbg.cat && mb.pix >= 0 && !mb.final_pass) {
@@ -258,16 +371,14 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs
     if (!was_alive) return;
     a.radiance[slot] = make_float4(L.x, L.y, L.z, 0.0f);
     if (mb.alive && mb.valid) {
-        const float4 o4 = a.ray_o[slot];
-        const float4 d4 = a.ray_d[slot];
-        const float th = __int_as_float(a.hit[slot].y);
-        const float px = o4.x + th * d4.x, py = o4.y + th * d4.y, pz = o4.z + th * d4.z;
-        const float amax = fmaxf(1.0f, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
-        const float eps = 0x1.0p-18f * amax;
+        const V3 o = spawn_point(a, slot, mb.n);
         const V3 dw = local_to_world(mb.t, mb.b, mb.n, mb.wl);
-        a.ray_o[slot] = make_float4(px + eps * mb.n.x, py + eps * mb.n.y, pz + eps * mb.n.z, __int_as_float(mb.orig));
+        a.ray_o[slot] = make_float4(o.x, o.y, o.z, __int_as_float(mb.orig));
         a.ray_d[slot] = make_float4(dw.x, dw.y, dw.z, INFINITY);
-        a.beta[slot] = make_float4(fm(bt.x, mb.w[0]), fm(bt.y, mb.w[1]), fm(bt.z, mb.w[2]), 0.0f);
+        // beta.w: density of the new direction for the MIS weight of the emission it may
+        // meet (next-event estimation only; 0 = mirror)
+        a.beta[slot] = make_float4(fm(bt.x, mb.w[0]), fm(bt.y, mb.w[1]), fm(bt.z, mb.w[2]),
+                                   mb.nee ? own_pdf(mb, mb.wl) : 0.0f);
         a.alive[slot] = 1;
     } else {
         a.alive[slot] = 0;
@@ -296,6 +407,8 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     mb.final_pass = true;
     mb.reuse = false;
     mb.world = false;
+    mb.nee = false;
+    mb.type = kMatLambert;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
@@ -306,6 +419,8 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.final_pass = p.bounce > Jp->max_bounces;
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
+            mb.nee = Jp->nee != 0;
+            mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
         }
@@ -318,6 +433,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             L = make_float3(r4.x, r4.y, r4.z);
             setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
         }
+        if (a.shadow_d) next_event(a, p, slot, mb, bt);
     }
     int cat = kCatEmpty;
     {
@@ -400,6 +516,8 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     mb.final_pass = true;
     mb.reuse = false;
     mb.world = false;
+    mb.nee = false;
+    mb.type = kMatLambert;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
@@ -410,6 +528,8 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             mb.final_pass = p.bounce > Jp->max_bounces;
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
+            mb.nee = Jp->nee != 0;
+            mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
         }
@@ -422,6 +542,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             L = make_float3(r4.x, r4.y, r4.z);
             setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
         }
+        if (a.shadow_d) next_event(a, p, slot, mb, bt);
     }
     int cat = kCatEmpty;
     {
@@ -957,7 +1078,19 @@ static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, const
     if (dbg) a.dbg = *dbg;
     else a.dbg = cr_debug{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     a.npx = p.npx;
+    const bool nee = p.nee && b.shadow_d;
+    a.shadow_o = nee ? b.shadow_o : nullptr;
+    a.shadow_d = nee ? b.shadow_d : nullptr;
+    a.shadow_c = nee ? b.shadow_c : nullptr;
     return a;
+}
+
+void launch_shadow(const PassArgs& p, PathBuffers& b, bool first, bool bvh8, cudaStream_t st, LaunchCount& lc) {
+    if (!p.nee || !b.shadow_d) return;
+    const ShadeArgs a = shade_args(p, b, first, nullptr);
+    launch_shadow_rays(p.scenes, b.slot_scene, b.shadow_o, b.shadow_d, b.shadow_c, a.group_queue, a.group_count,
+                       a.n_groups_max, p.k, b.radiance, reinterpret_cast<unsigned long long*>(b.counts + kShadowWord),
+                       bvh8, st, lc);
 }
 
 void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,

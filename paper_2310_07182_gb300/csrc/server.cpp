@@ -24,7 +24,8 @@
 namespace cr {
 namespace {
 
-constexpr uint64_t kSlotBytes = 4 + 2 + 2 + 16 + 16 + 8 + 16 + 16 + 1 + 4 + 8 + 8 + 8; // path state per slot
+// path state per slot, with the 48 bytes of shadow-ray records (jobs may use CR_JOB_NEE)
+constexpr uint64_t kSlotBytes = 4 + 2 + 2 + 16 + 16 + 8 + 16 + 16 + 1 + 4 + 8 + 8 + 8 + 48;
 
 struct SJob {
     uint64_t id = 0;
@@ -285,6 +286,7 @@ extern "C" cr_status cr_server_create(const cr_server_opts* o, cr_server** out) 
         return e == cudaErrorMemoryAllocation ? CR_ERR_OOM : CR_ERR_CUDA;
     }
     cr_status st = s->ws.ensure(s->slots_cap, 1);
+    if (st == CR_OK) st = s->ws.ensure_nee(s->slots_cap);
     if (st != CR_OK) {
         cudaFree(s->arena);
         cudaStreamDestroy(s->stream);

@@ -202,7 +202,8 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
     } while (0)
 #endif
 
-template <bool kCount>
+// kAny: visibility only; the traversal ends at the first triangle hit before the ray's tmax.
+template <bool kCount, bool kAny = false>
 __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
                                                unsigned long long& n_tri) {
@@ -246,6 +247,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
         // leaf
         const uint32_t code = (uint32_t)(~node);
         test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, n_tri);
+        if (kAny && best.leaf >= 0) break;
         if (sp == 0) break;
         STACK_POP(node);
     }
@@ -256,7 +258,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
 #define CR_TRACE_MAXNREG 48 // caps registers so 10 blocks of 128 threads stay resident per SM
 #endif
 
-template <bool kCount>
+template <bool kCount, bool kAny = false>
 __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
                              const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                              const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
@@ -272,7 +274,7 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __res
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
         if (rd.w >= 0.0f)
-            h = trace_bvh2_one<kCount>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+            h = trace_bvh2_one<kCount, kAny>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
         hit[slot] = h;
     }
     if (kCount) {
@@ -750,7 +752,7 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t lo, uint32_t hi, uint32_t s
     return ((slot < 4 ? lo : hi) >> (8 * (slot & 3))) & 0xffu;
 }
 
-template <bool kCount>
+template <bool kCount, bool kAny = false>
 __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
                                                unsigned long long& n_tri) {
@@ -805,6 +807,7 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
         } else {
             const uint32_t code = (uint32_t)(~entry);
             test_leaf(tris, r, skip, code >> 3, (code & 7u) + 1u, best, n_tri);
+            if (kAny && best.leaf >= 0) break;
         }
         if (sp == 0) break;
         --sp;
@@ -813,7 +816,7 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
     return make_int2(best.leaf, __float_as_int(best.t));
 }
 
-template <bool kCount>
+template <bool kCount, bool kAny = false>
 __global__ void __launch_bounds__(128, 8) k_trace_bvh8(const SceneDev* __restrict__ scenes,
                              const uint16_t* __restrict__ slot_scene,
                              const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
@@ -830,7 +833,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_bvh8(const SceneDev* __restric
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
         if (rd.w >= 0.0f)
-            h = trace_bvh8_one<kCount>(sc.nodes8, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+            h = trace_bvh8_one<kCount, kAny>(sc.nodes8, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
         hit[slot] = h;
     }
     if (kCount) {
@@ -845,13 +848,50 @@ __global__ void __launch_bounds__(128, 8) k_trace_bvh8(const SceneDev* __restric
     }
 }
 
+// Shadow rays of next-event estimation, one thread per position of the last shade's group
+// queue (so a reuse group's rays run in adjacent lanes, as they were shaded).  A ray whose
+// direction record has w = tmax > 0 is traced for visibility only; if nothing blocks it, its
+// contribution is added to the path radiance of its slot.  Rays traced are counted.
+template <bool kBvh8>
+__global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_shadow(
+    const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, const float4* __restrict__ sh_o,
+    const float4* __restrict__ sh_d, const float4* __restrict__ sh_c, const int32_t* __restrict__ group_queue,
+    const uint32_t* __restrict__ group_count, uint32_t n_groups_max, uint32_t K, float4* __restrict__ radiance,
+    unsigned long long* __restrict__ n_traced) {
+    extern __shared__ uint32_t smem_stack[];
+    const uint32_t n_groups = group_queue ? min(*group_count, n_groups_max) : n_groups_max;
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    bool traced = false;
+    if (pos < n_groups * K) {
+        const uint32_t g = group_queue ? (uint32_t)group_queue[pos / K] : pos / K;
+        const int slot = (int)(g * K + pos % K);
+        const float4 rd = sh_d[slot];
+        if (rd.w > 0.0f) {
+            traced = true;
+            const float4 ro = sh_o[slot];
+            const SceneDev& sc = scenes[slot_scene[slot]];
+            unsigned long long dn = 0, dt = 0;
+            const int2 h = kBvh8 ? trace_bvh8_one<false, true>(sc.nodes8, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt)
+                                 : trace_bvh2_one<false, true>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt);
+            if (h.x < 0) {
+                const float4 c = sh_c[slot];
+                const float4 L = radiance[slot];
+                radiance[slot] = make_float4(__fadd_rn(L.x, c.x), __fadd_rn(L.y, c.y), __fadd_rn(L.z, c.z), L.w);
+            }
+        }
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, traced);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_traced, (unsigned long long)__popc(b));
+}
+
+
 __global__ void k_hits_to_user(const float4* __restrict__ tris, const int2* __restrict__ hit, uint32_t n,
                                int32_t* __restrict__ prim, float* __restrict__ t) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int2 h = hit[i];
     prim[i] = h.x >= 0 ? __float_as_int(__ldg(&tris[3 * h.x]).w) : -1;
-    t[i] = __int_as_float(h.y);
+    t[i] = h.x >= 0 ? __int_as_float(h.y) : INFINITY; // a miss of a bounded ray reports inf, not tmax
 }
 
 __global__ void k_rays_from_user(const float* __restrict__ rays, const int32_t* __restrict__ skip, uint32_t n,
@@ -864,6 +904,24 @@ __global__ void k_rays_from_user(const float* __restrict__ rays, const int32_t* 
 }
 
 } // namespace
+
+void launch_shadow_rays(const SceneDev* scenes, const uint16_t* slot_scene, const float4* sh_o, const float4* sh_d,
+                        const float4* sh_c, const int32_t* group_queue, const uint32_t* group_count,
+                        uint32_t n_groups_max, uint32_t K, float4* radiance, unsigned long long* n_traced, bool bvh8,
+                        cudaStream_t st, LaunchCount& lc) {
+    const uint32_t n_pos = n_groups_max * K;
+    if (n_pos == 0) return;
+    const int block = 128;
+    const size_t smem = (size_t)kSmemStack * block * sizeof(uint32_t);
+    const uint32_t grid = (n_pos + block - 1) / block;
+    if (bvh8)
+        k_trace_shadow<true><<<grid, block, smem, st>>>(scenes, slot_scene, sh_o, sh_d, sh_c, group_queue, group_count,
+                                                        n_groups_max, K, radiance, n_traced);
+    else
+        k_trace_shadow<false><<<grid, block, smem, st>>>(scenes, slot_scene, sh_o, sh_d, sh_c, group_queue, group_count,
+                                                         n_groups_max, K, radiance, n_traced);
+    lc.n++;
+}
 
 void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, float4* ray_o, float4* ray_d,
                            cudaStream_t st, LaunchCount& lc) {
@@ -884,6 +942,10 @@ SceneDev scene_entry(const DevScene& s, bool bvh8) {
         e.hi[k] = s.hi[k];
     }
     e.env[3] = e.lo[3] = e.hi[3] = 0.0f;
+    e.light_cdf = s.light_cdf;
+    e.lights = s.lights;
+    e.n_lights = s.n_lights;
+    e.light_total = s.light_total;
     return e;
 }
 
@@ -892,6 +954,17 @@ void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
     const int block = a.block;
     const size_t smem = (size_t)kSmemStack * block * sizeof(uint32_t);
     const size_t smem128 = (size_t)kSmemStack * 128 * sizeof(uint32_t);
+    if (a.any_hit) { // visibility queries (cr_trace_rays with CR_OPT_ANY_HIT)
+        const uint32_t grid = (a.n_max + block - 1) / block;
+        if (a.bvh8)
+            k_trace_bvh8<false, true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
+                                                                 a.queue_count, a.n_max, a.hit, nullptr);
+        else
+            k_trace_bvh2<false, true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
+                                                                 a.queue_count, a.n_max, a.hit, nullptr);
+        lc.n++;
+        return;
+    }
     if (a.bvh8) {
         const uint32_t grid = (a.n_max + block - 1) / block;
         if (a.counters)

@@ -203,3 +203,54 @@ def test_nee_changes_nothing_without_emitters_or_at_mirrors(orc):
     assert floor.mean() > 0.3
     assert np.array_equal(c["rgb"][floor], d["rgb"][floor])
     assert np.allclose(c["rgb"][floor], np.float32([0.9, 0.8, 0.7]))
+
+
+@pytest.mark.parametrize("alpha", [0.15, 0.4])
+def test_ggx_pdf_is_the_sampler_density(orc, alpha):
+    """pdf_ggx integrates over the upper hemisphere to the fraction of valid samples of
+    sample_ggx, and f cos / pdf reproduces the sampler's weight for every sampled direction."""
+    f0 = [0.9, 0.6, 0.3]
+    wo = np.float32([np.sin(0.7), 0.0, np.cos(0.7)])
+    G = 120
+    valid = 0
+    for a in range(G):
+        for b in range(G):
+            ok, wi, wt = orc.sample_ggx(wo, alpha, f0, (a + 0.5) / G, (b + 0.5) / G)
+            if not ok:
+                continue
+            valid += 1
+            pdf = orc.pdf_ggx(wo, wi, alpha)
+            f = orc.eval_ggx(wo, wi, alpha, f0)
+            assert np.allclose(f * wi[2] / pdf, wt, rtol=2e-4), (f * wi[2] / pdf, wt)
+    nt, nphi = 500, 400
+    mu = (np.arange(nt) + 0.5) / nt
+    phi = (np.arange(nphi) + 0.5) / nphi * 2 * np.pi
+    mass = 0.0
+    for m in mu:
+        st = np.sqrt(1 - m * m)
+        for ph in phi:
+            mass += orc.pdf_ggx(wo, [st * np.cos(ph), st * np.sin(ph), m], alpha)
+    mass *= (1.0 / nt) * (2 * np.pi / nphi)
+    assert abs(mass - valid / G ** 2) < 0.01, (mass, valid / G ** 2)
+
+
+def test_nee_lowers_variance_under_a_small_light(orc):
+    """A closed box lit by a small ceiling patch: light sampling with MIS has the mean of
+    plain path tracing and a clearly lower per-pixel variance."""
+    sc = scenes.emitter_box(n_spheres=6, seed=2, width=24, height=24)
+    # keep only a 0.4 x 0.4 emitter patch under the ceiling; the walls become Lambert
+    tris = np.concatenate([sc.tri_xyz, np.array([[-0.2, 0.999, -0.2, 0.2, 0.999, -0.2, 0.2, 0.999, 0.2],
+                                                  [-0.2, 0.999, -0.2, 0.2, 0.999, 0.2, -0.2, 0.999, 0.2]],
+                                                 np.float32)])
+    mat = np.concatenate([np.where(sc.tri_mat == 1, 2, sc.tri_mat), [1, 1]])
+    params = sc.mat_params.copy()
+    params[1, 4:7] = 30.0
+    small = scenes._finish("small_light", tris, mat, sc.mat_type, params, (0, 0, 0), sc.camera)
+    S = orc.Scene(small)
+    kw = dict(mode="independent", max_bounces=2, tile=(8, 8), spp=16)
+    res = {}
+    for nee in (False, True):
+        imgs = np.array([orc.render(S, small.camera, seed=s, nee=nee, **kw)["rgb"] for s in (1, 2, 3, 4)])
+        res[nee] = (imgs.mean(), imgs.var(axis=0, ddof=1).mean())
+    assert abs(res[True][0] - res[False][0]) < 0.05 * res[False][0], res
+    assert res[True][1] < 0.5 * res[False][1], res
