@@ -76,6 +76,8 @@ def lib():
         L.orc_sample_ggx.argtypes = [vp, C.c_float, vp, C.c_float, C.c_float, vp, vp]
         L.orc_sample_ggx.restype = i32
         L.orc_frame.argtypes = [vp, vp, vp]
+        L.orc_sample_dielectric.argtypes = [vp, C.c_float, i32, C.c_float, vp]
+        L.orc_sample_dielectric.restype = i32
         L.orc_scene_new.argtypes = [vp, u32, vp, vp, vp, u32, vp]
         L.orc_scene_new.restype = vp
         L.orc_scene_free.argtypes = [vp]
@@ -143,6 +145,14 @@ def sample_ggx(wo, alpha, f0, u1, u2):
     ok = lib().orc_sample_ggx(_p(wo), float(np.float32(alpha)), _p(f0), float(np.float32(u1)),
                               float(np.float32(u2)), _p(wi), _p(wt))
     return bool(ok), wi, wt
+
+
+def sample_dielectric(wo, eta, front, u):
+    """-> (refracted?, wi float32[3]) of a smooth dielectric (IOR eta, entering if front)."""
+    wo = np.ascontiguousarray(wo, dtype=np.float32)
+    wi = np.zeros(3, dtype=np.float32)
+    r = lib().orc_sample_dielectric(_p(wo), float(np.float32(eta)), int(bool(front)), float(np.float32(u)), _p(wi))
+    return bool(r), wi
 
 
 def frame(n):

@@ -40,11 +40,14 @@
 #define MAT_LAMBERT 0u
 #define MAT_GGX 1u
 #define MAT_MIRROR 2u
+#define MAT_DIELECTRIC 4u  /* smooth dielectric: Fresnel reflection or refraction; IOR in the roughness slot */
+#define MAT_TRANSLUCENT 5u /* Lambertian transmission into the lower hemisphere */
 #define MAT_EMITTER 3u
 
 #define CLS_NONE 0
 #define CLS_DIFFUSE 1
 #define CLS_GLOSSY 2 /* glossy or specular */
+#define DBG_CLS_TRANSLUCENT 3 /* debug output only: a diffuse-class point that transmits */
 
 #define CAT_EMPTY 0
 #define CAT_DIFFUSE 1
@@ -899,6 +902,8 @@ typedef struct {
     f3 wl;
     float w[3];
     int valid;
+    float hemi;  /* +1: the diffuse lobe is the upper hemisphere, -1: the lower (translucent) */
+    int front;   /* the incoming ray met the triangle's front face (cross(v1-v0, v2-v0) side) */
 } pstate;
 
 static void shade_setup(const orc_scene* s, pstate* ps) {
@@ -906,14 +911,47 @@ static void shade_setup(const orc_scene* s, pstate* ps) {
     f3 v0 = f3m(v[0], v[1], v[2]), v1 = f3m(v[3], v[4], v[5]), v2 = f3m(v[6], v[7], v[8]);
     f3 ng = f3normalize(f3cross(f3sub(v1, v0), f3sub(v2, v0)));
     /* two-sided: the shading normal faces the incoming ray */
-    f3 n = f3dot(ng, ps->d) < 0.0f ? ng : f3m(-ng.x, -ng.y, -ng.z);
+    ps->front = f3dot(ng, ps->d) < 0.0f;
+    f3 n = ps->front ? ng : f3m(-ng.x, -ng.y, -ng.z);
     ps->n = n;
     onb(n, &ps->T, &ps->B);
     f3 md = f3m(-ps->d.x, -ps->d.y, -ps->d.z);
     ps->wo = f3m(f3dot(md, ps->T), f3dot(md, ps->B), f3dot(md, n));
     ps->mat = s->tri_mat[ps->hit];
     uint32_t ty = s->mat_type[ps->mat];
-    ps->cls = ty == MAT_LAMBERT ? CLS_DIFFUSE : CLS_GLOSSY;
+    /* Transmission (the paper's future work, Sec. 6): a Lambertian transmitter joins the
+     * diffuse class with its lobe in the lower hemisphere; a smooth dielectric is specular. */
+    ps->cls = (ty == MAT_LAMBERT || ty == MAT_TRANSLUCENT) ? CLS_DIFFUSE : CLS_GLOSSY;
+    ps->hemi = ty == MAT_TRANSLUCENT ? -1.0f : 1.0f;
+}
+
+/* Smooth dielectric (IOR eta inside, 1 outside; the inside lies behind the front face):
+ * unpolarised Fresnel reflectance F from the relative index e = eta_i / eta_t, reflection
+ * when u < F (total internal reflection when sin^2 t >= 1), else refraction by Snell's law,
+ * wi = (-e wo.x, -e wo.y, -cos t).  Both branches carry the tint (F and 1 - F cancel
+ * against their selection probabilities).  FP32, one fixed operation order. */
+int orc_sample_dielectric(const float* wo, float eta, int front, float u, float* wi) {
+    float eta_i = front ? 1.0f : eta, eta_t = front ? eta : 1.0f;
+    float e = eta_i / eta_t;
+    float ci = wo[2];
+    float s2 = (e * e) * (1.0f - ci * ci);
+    float F = 1.0f, ct = 0.0f;
+    if (s2 < 1.0f) {
+        ct = sqrtf(1.0f - s2);
+        float rs = (eta_i * ci - eta_t * ct) / (eta_i * ci + eta_t * ct);
+        float rp = (eta_t * ci - eta_i * ct) / (eta_t * ci + eta_i * ct);
+        F = 0.5f * (rs * rs + rp * rp);
+    }
+    if (u < F) {
+        wi[0] = -wo[0];
+        wi[1] = -wo[1];
+        wi[2] = wo[2];
+        return 0;
+    }
+    wi[0] = -(e * wo[0]);
+    wi[1] = -(e * wo[1]);
+    wi[2] = -ct;
+    return 1;
 }
 
 static void bsdf_rand(uint64_t seed, const pstate* ps, uint32_t frame, uint32_t bounce, float* u1, float* u2) {
@@ -938,6 +976,17 @@ static void own_sample(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
         float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z};
         ps->valid = orc_sample_ggx(wo, mp[3], mp, u1, u2, wl, ps->w);
         ps->wl = f3m(wl[0], wl[1], wl[2]);
+    } else if (ty == MAT_TRANSLUCENT) {
+        orc_sample_cosine(u1, u2, wl);
+        ps->wl = f3m(wl[0], wl[1], -wl[2]);
+        for (int k = 0; k < 3; ++k) ps->w[k] = mp[k];
+        ps->valid = 1;
+    } else if (ty == MAT_DIELECTRIC) {
+        float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z};
+        orc_sample_dielectric(wo, mp[3], ps->front, u1, wl);
+        ps->wl = f3m(wl[0], wl[1], wl[2]);
+        for (int k = 0; k < 3; ++k) ps->w[k] = mp[k];
+        ps->valid = ps->wo.z > 0.0f;
     } else { /* mirror */
         ps->wl = f3m(-ps->wo.x, -ps->wo.y, ps->wo.z);
         for (int k = 0; k < 3; ++k) ps->w[k] = mp[k];
@@ -951,6 +1000,11 @@ static void take_direction(const orc_scene* s, pstate* ps, f3 wl) {
     for (int k = 0; k < 3; ++k) ps->w[k] = mp[k]; /* Lambert: f cos / p_cos = albedo */
     ps->valid = 1;
 }
+
+/* A shared tangent-space direction taken into the member's own diffuse lobe: its normal
+ * component becomes hemi * |z| (a translucent member mirrors it through the tangent plane),
+ * so a cosine-distributed direction stays cosine-distributed in either lobe. */
+static f3 into_lobe(const pstate* ps, f3 wl) { return f3m(wl.x, wl.y, ps->hemi * fabsf(wl.z)); }
 
 static f3 to_world(const pstate* ps, f3 l) {
     return f3m((ps->T.x * l.x + ps->B.x * l.y) + ps->n.x * l.z, (ps->T.y * l.x + ps->B.y * l.y) + ps->n.y * l.z,
@@ -971,6 +1025,7 @@ static f3 tree_sum(f3* v, uint32_t k) {
 static double bsdf_pdf(const orc_scene* s, const pstate* ps, f3 wl) {
     uint32_t ty = s->mat_type[ps->mat];
     if (ty == MAT_LAMBERT) return wl.z > 0.0f ? (double)wl.z / PI_D : 0.0;
+    if (ty == MAT_TRANSLUCENT) return wl.z < 0.0f ? -(double)wl.z / PI_D : 0.0;
     if (ty == MAT_GGX) {
         float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z}, wi[3] = {wl.x, wl.y, wl.z};
         return orc_pdf_ggx(wo, wi, s->mat_params[7 * ps->mat + 3]);
@@ -998,9 +1053,10 @@ static double emit_weight(const orc_scene* s, const pstate* ps) {
     return ps->pdf * ps->pdf / (ps->pdf * ps->pdf + p_l * p_l);
 }
 
-/* Spawn point of the next ray: p = o + t d in FP64, offset along the shading normal by
- * 2^-18 max(1, |p|_inf), so that the new ray clears the surface it leaves. */
-static void spawn_point(const pstate* ps, double* out) {
+/* Spawn point of the next ray: p = o + t d in FP64, offset by 2^-18 max(1, |p|_inf) along
+ * the shading normal times side (+1 for a ray leaving on the incoming side, -1 for a
+ * transmitted one), so that the new ray clears the surface it leaves. */
+static void spawn_point(const pstate* ps, double side, double* out) {
     double pt[3], amax = 1.0;
     double dd[3] = {ps->d.x, ps->d.y, ps->d.z};
     for (int k = 0; k < 3; ++k) {
@@ -1009,7 +1065,7 @@ static void spawn_point(const pstate* ps, double* out) {
     }
     double eps = 0x1.0p-18 * amax;
     double nn[3] = {ps->n.x, ps->n.y, ps->n.z};
-    for (int k = 0; k < 3; ++k) out[k] = pt[k] + eps * nn[k];
+    for (int k = 0; k < 3; ++k) out[k] = pt[k] + (side * eps) * nn[k];
 }
 
 #define SHADOW_TMAX (1.0 - 0x1.0p-10) /* shadow rays run to 1 - 2^-10 of the way to the light point */
@@ -1034,13 +1090,13 @@ static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
     int32_t lt = orc_light_sample(s, to_unit(h[0]), to_unit(h[1]), to_unit(h[2]), pl);
     if (lt < 0) return;
     double o[3], dl[3];
-    spawn_point(ps, o);
+    spawn_point(ps, (double)ps->hemi, o);
     for (int k = 0; k < 3; ++k) dl[k] = (double)pl[k] - o[k];
     double r2 = ddot(dl, dl);
     if (!(r2 > 0.0)) return;
     double r = sqrt(r2);
     double nn[3] = {ps->n.x, ps->n.y, ps->n.z};
-    double cos_i = ddot(nn, dl) / r;
+    double cos_i = (double)ps->hemi * ddot(nn, dl) / r; /* on the lobe's side of the surface */
     const float* lv = &s->v[9 * lt];
     double e1[3], e2[3], nl[3];
     for (int k = 0; k < 3; ++k) {
@@ -1066,7 +1122,7 @@ static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
     double T[3] = {ps->T.x, ps->T.y, ps->T.z}, B[3] = {ps->B.x, ps->B.y, ps->B.z};
     f3 wil = f3m((float)ddot(T, wi), (float)ddot(B, wi), (float)ddot(nn, wi));
     double f[3];
-    if (s->mat_type[ps->mat] == MAT_LAMBERT) {
+    if (s->mat_type[ps->mat] == MAT_LAMBERT || s->mat_type[ps->mat] == MAT_TRANSLUCENT) {
         for (int k = 0; k < 3; ++k) f[k] = (double)mp[k] / PI_D;
     } else {
         float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z}, wv[3] = {wil.x, wil.y, wil.z};
@@ -1153,7 +1209,8 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         continue;
                     }
                     shade_setup(s, ps);
-                    if (p->nee && s->mat_type[ps->mat] != MAT_MIRROR) next_event(s, p->seed, f, b, ps, cnt_local);
+                    if (p->nee && s->mat_type[ps->mat] != MAT_MIRROR && s->mat_type[ps->mat] != MAT_DIELECTRIC)
+                        next_event(s, p->seed, f, b, ps, cnt_local);
                 }
                 const int reuse_now = (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
                                       (p->reuse_depth == 0 || b <= p->reuse_depth);
@@ -1187,7 +1244,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                                 if (ps->pixel < 0 || !ps->alive || ps->cls != CLS_DIFFUSE) continue;
                                 f3 l = f3m(f3dot(wd, ps->T), f3dot(wd, ps->B), f3dot(wd, ps->n));
                                 take_direction(s, ps, l);
-                                if (!(l.z > 0.0f)) ps->valid = 0; /* below the surface: f = 0 */
+                                if (!(ps->hemi * l.z > 0.0f)) ps->valid = 0; /* outside the lobe: f = 0 */
                             }
                         }
                     } else if (reuse_now && cat == CAT_DIFFUSE) {
@@ -1197,7 +1254,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                             if (G[j].pixel >= 0 && G[j].alive) donor = (int)j;
                         f3 wl = G[donor].wl;
                         for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive) take_direction(s, &G[j], wl);
+                            if (G[j].pixel >= 0 && G[j].alive) take_direction(s, &G[j], into_lobe(&G[j], wl));
                     } else if (reuse_now && cat == CAT_HYBRID) {
                         /* hybrid group: diffuse members take the normalised tangent-space sum of
                          * the valid glossy/specular exit directions */
@@ -1220,7 +1277,8 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                             wl = G[donor].wl;
                         }
                         for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE) take_direction(s, &G[j], wl);
+                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE)
+                                take_direction(s, &G[j], into_lobe(&G[j], wl));
                     }
                     /* glossy groups and the independent mode keep every member's own sample */
                     for (uint32_t j = 0; j < K; ++j) {
@@ -1229,7 +1287,8 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         uint32_t di = (b - 1) * npx + (uint32_t)ps->pixel;
                         if (out->dbg_cat) {
                             out->dbg_cat[di] = (uint8_t)cat;
-                            out->dbg_cls[di] = (uint8_t)(ps->alive ? ps->cls : CLS_NONE);
+                            out->dbg_cls[di] = (uint8_t)(!ps->alive ? CLS_NONE
+                                                         : (ps->hemi < 0.0f ? DBG_CLS_TRANSLUCENT : ps->cls));
                             out->dbg_flags[di] = (uint8_t)((ps->alive ? 1 : 0) | (ps->alive && ps->valid ? 2 : 0) |
                                                            (ps->taint ? 4 : 0));
                             f3 wv = ps->alive ? to_world(ps, ps->wl) : f3m(0.0f, 0.0f, 0.0f);
@@ -1247,7 +1306,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                             continue;
                         }
                         double o2[3];
-                        spawn_point(ps, o2);
+                        spawn_point(ps, ps->wl.z < 0.0f ? -1.0 : 1.0, o2);
                         for (int k = 0; k < 3; ++k) ps->o[k] = o2[k];
                         ps->d = to_world(ps, ps->wl);
                         ps->pdf = bsdf_pdf(s, ps, ps->wl);

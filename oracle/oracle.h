@@ -50,6 +50,10 @@ int orc_sample_ggx(const float* wo, float alpha, const float* f0, float u1, floa
 /* Tangent frame (t, b) of a unit normal n (Duff et al., JCGT 2017). */
 void orc_frame(const float* n, float* t, float* b);
 
+/* Smooth dielectric scattering (IOR eta, front = entering through the front face): writes
+ * the reflected (returns 0) or refracted (returns 1) tangent-space direction. */
+int orc_sample_dielectric(const float* wo, float eta, int front, float u, float* wi);
+
 typedef struct orc_scene orc_scene;
 
 orc_scene* orc_scene_new(const float* tri_xyz, uint32_t n_tri, const uint32_t* tri_mat,

@@ -30,6 +30,8 @@ MAT_LAMBERT = 0
 MAT_GGX = 1
 MAT_MIRROR = 2
 MAT_EMITTER = 3
+MAT_DIELECTRIC = 4   # smooth dielectric; the roughness slot holds the index of refraction
+MAT_TRANSLUCENT = 5  # Lambertian transmission
 
 
 @dataclass
@@ -125,9 +127,15 @@ def tiny(seed: int = 1, n_soup: int = 1024, width: int = 64, height: int = 64,
     elif material_mix == "glossy":  # GGX and mirror only
         u = rng.random(n)
         mtype = np.where(u < 0.75, MAT_GGX, MAT_MIRROR).astype(np.uint32)
+    elif material_mix == "transmissive":  # 35/25/15/10/15 Lambert/translucent/GGX/mirror/dielectric
+        u = rng.random(n)
+        mtype = np.select([u < 0.35, u < 0.6, u < 0.75, u < 0.85], [MAT_LAMBERT, MAT_TRANSLUCENT, MAT_GGX, MAT_MIRROR],
+                          MAT_DIELECTRIC).astype(np.uint32)
     else:
         raise ValueError(material_mix)
     rough = rng.uniform(0.05, 0.5, size=n)
+    if material_mix == "transmissive":
+        rough = np.where(mtype == MAT_DIELECTRIC, rng.uniform(1.3, 1.7, size=n), rough)
     params = np.zeros((n, 7))
     params[:, 0:3] = albedo
     params[:, 3] = rough
