@@ -52,13 +52,27 @@ const char* cr_version(void);
 
 /* ---------------------------------------------------------------------------------- */
 /* Scenes.  Material classes follow Sec. 3.2: Lambert is diffuse, GGX and mirror are glossy
- * or specular; emitters end a path and take no part in grouping. */
-typedef enum { CR_MAT_LAMBERT = 0, CR_MAT_GGX = 1, CR_MAT_MIRROR = 2, CR_MAT_EMITTER = 3 } cr_mat_type;
+ * or specular; emitters end a path and take no part in grouping.
+ * Transmission (the paper's future work, Sec. 6): a translucent material (Lambertian
+ * transmission) is diffuse with its lobe in the lower hemisphere; direction reuse gives it
+ * the shared tangent-space direction mirrored through the tangent plane (z -> -|z|), so
+ * the direction stays cosine-distributed in its own lobe.  A dielectric (smooth glass:
+ * Fresnel reflection or Snell refraction, chosen by the reflectance) is specular.  Its
+ * inside lies behind the triangles' front faces, the side cross(v1 - v0, v2 - v0) points
+ * away from. */
+typedef enum {
+    CR_MAT_LAMBERT = 0,
+    CR_MAT_GGX = 1,
+    CR_MAT_MIRROR = 2,
+    CR_MAT_EMITTER = 3,
+    CR_MAT_DIELECTRIC = 4,
+    CR_MAT_TRANSLUCENT = 5
+} cr_mat_type;
 
 typedef struct {
     uint32_t type;     /* cr_mat_type */
-    float albedo[3];   /* Lambert albedo, GGX/mirror F0 (Schlick), each in [0, 1] */
-    float roughness;   /* GGX alpha, in (0, 1]; ignored by other types */
+    float albedo[3];   /* Lambert/translucent albedo, GGX/mirror F0 (Schlick), dielectric tint; in [0, 1] */
+    float roughness;   /* GGX alpha in (0, 1]; dielectric index of refraction in (0, 10]; else ignored */
     float emission[3]; /* emitter radiance; ignored by other types */
 } cr_material;         /* 32 bytes */
 
@@ -136,7 +150,8 @@ typedef struct {
 typedef struct {
     int32_t* prim;   /* (B+1) * npx: original triangle index hit by trace b (0 = primary), -1 miss */
     uint8_t* cat;    /* B * npx: category of the pixel's group at step b: 0 empty, 1 diffuse, 2 glossy, 3 hybrid */
-    uint8_t* cls;    /* B * npx: class of the pixel's shading point: 0 none, 1 diffuse, 2 glossy/specular */
+    uint8_t* cls;    /* B * npx: class of the pixel's shading point: 0 none, 1 diffuse, 2 glossy/specular,
+                        3 diffuse transmission (translucent, grouped with the diffuse class) */
     uint8_t* flags;  /* B * npx: bit0 alive at step b, bit1 spawned a secondary ray */
     float* local;    /* B * npx * 3: tangent-space exit direction */
     float* world;    /* B * npx * 3: world-space exit direction */

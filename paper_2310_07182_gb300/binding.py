@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_PKG, "libcr.so")
 
 CR_OK, CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT, CR_ERR_STACK_OVERFLOW, CR_ERR_BUSY, \
     CR_ERR_NOT_FOUND = range(8)
-CR_MAT_LAMBERT, CR_MAT_GGX, CR_MAT_MIRROR, CR_MAT_EMITTER = range(4)
+CR_MAT_LAMBERT, CR_MAT_GGX, CR_MAT_MIRROR, CR_MAT_EMITTER, CR_MAT_DIELECTRIC, CR_MAT_TRANSLUCENT = range(6)
 CR_BVH2, CR_BVH8Q = 1, 2
 CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE, CR_WORLD_REUSE = 0, 1, 2, 3
 CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIVE = 1, 2, 4, 8, 16

@@ -159,7 +159,11 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
         if (tri_mat[t] >= n_mat)
             return fail(CR_ERR_INVALID_ARG, "cr_scene_create: triangle %u uses material %u >= n_mat %u", t, tri_mat[t], n_mat);
     for (uint32_t m = 0; m < n_mat; ++m) {
-        if (mats[m].type > CR_MAT_EMITTER) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: material %u type %u", m, mats[m].type);
+        if (mats[m].type > CR_MAT_TRANSLUCENT)
+            return fail(CR_ERR_INVALID_ARG, "cr_scene_create: material %u type %u", m, mats[m].type);
+        if (mats[m].type == CR_MAT_DIELECTRIC && !(mats[m].roughness > 0.0f && mats[m].roughness <= 10.0f))
+            return fail(CR_ERR_INVALID_ARG, "cr_scene_create: material %u index of refraction %g not in (0, 10]", m,
+                        mats[m].roughness);
         if (mats[m].type == CR_MAT_GGX && !(mats[m].roughness > 0.0f && mats[m].roughness <= 1.0f))
             return fail(CR_ERR_INVALID_ARG, "cr_scene_create: material %u roughness %g not in (0, 1]", m, mats[m].roughness);
     }

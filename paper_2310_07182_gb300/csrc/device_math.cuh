@@ -17,7 +17,8 @@ constexpr uint32_t kTagBsdf = 0x42534446u;       // "BSDF"
 constexpr uint32_t kTagInterleave = 0x494E544Cu; // "INTL"
 constexpr uint32_t kTagLight = 0x4C495445u;      // "LITE"
 
-constexpr uint32_t kMatLambert = 0, kMatGGX = 1, kMatMirror = 2, kMatEmitter = 3;
+constexpr uint32_t kMatLambert = 0, kMatGGX = 1, kMatMirror = 2, kMatEmitter = 3, kMatDielectric = 4,
+                   kMatTranslucent = 5;
 constexpr int kClsNone = 0, kClsDiffuse = 1, kClsGlossy = 2;
 constexpr int kCatEmpty = 0, kCatDiffuse = 1, kCatGlossy = 2, kCatHybrid = 3;
 
@@ -166,6 +167,26 @@ __device__ __forceinline__ bool sample_ggx(V3 wo, float alpha, const float* f0, 
         w[k] = fd(fm(fm(F, g), d), den);
     }
     return true;
+}
+
+// Smooth dielectric (IOR eta inside, 1 outside; the inside lies behind the triangle's front
+// face): unpolarised Fresnel reflectance F from e = eta_i / eta_t, reflection when u < F
+// (always under total internal reflection, sin^2 t >= 1), else Snell refraction
+// wi = (-e wo.x, -e wo.y, -cos t).  The weight is the tint for both branches.
+__device__ __forceinline__ V3 sample_dielectric(V3 wo, float eta, bool front, float u) {
+    const float eta_i = front ? 1.0f : eta, eta_t = front ? eta : 1.0f;
+    const float e = fd(eta_i, eta_t);
+    const float ci = wo.z;
+    const float s2 = fm(fm(e, e), fs(1.0f, fm(ci, ci)));
+    float F = 1.0f, ct = 0.0f;
+    if (s2 < 1.0f) {
+        ct = fq(fs(1.0f, s2));
+        const float rs = fd(fs(fm(eta_i, ci), fm(eta_t, ct)), fa(fm(eta_i, ci), fm(eta_t, ct)));
+        const float rp = fd(fs(fm(eta_t, ci), fm(eta_i, ct)), fa(fm(eta_t, ci), fm(eta_i, ct)));
+        F = fm(0.5f, fa(fm(rs, rs), fm(rp, rp)));
+    }
+    if (u < F) return v3(-wo.x, -wo.y, wo.z);
+    return v3(-fm(e, wo.x), -fm(e, wo.y), -ct);
 }
 
 // GGX reflection value f(wo, wi) in the tangent frame: the density sample_ggx draws from,

@@ -161,7 +161,9 @@ struct Member {
     bool nee;        // the job uses next-event estimation
     uint32_t scene;  // scene table index
     uint32_t type;   // material type of the shading point
-    float rough;     // its roughness
+    float rough;     // its roughness (the IOR of a dielectric)
+    float hemi;      // +1: diffuse lobe in the upper hemisphere, -1: lower (translucent)
+    bool front;      // the incoming ray met the triangle's front face
     uint64_t seed;
     uint32_t frame;
     int cls;
@@ -225,11 +227,15 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     const V3 a0 = v3(v0.x, v0.y, v0.z), a1 = v3(v1.x, v1.y, v1.z), a2 = v3(v2.x, v2.y, v2.z);
     const V3 ng = normalize3(cross3(sub3(a1, a0), sub3(a2, a0)));
     const V3 d = v3(d4.x, d4.y, d4.z);
-    mb.n = dot3(ng, d) < 0.0f ? ng : v3(-ng.x, -ng.y, -ng.z);
+    mb.front = dot3(ng, d) < 0.0f;
+    mb.n = mb.front ? ng : v3(-ng.x, -ng.y, -ng.z);
     frame_from(mb.n, mb.t, mb.b);
     const V3 md = v3(-d.x, -d.y, -d.z);
     mb.wo = v3(dot3(md, mb.t), dot3(md, mb.b), dot3(md, mb.n));
-    mb.cls = type == kMatLambert ? kClsDiffuse : kClsGlossy;
+    // transmission (the paper's future work, Sec. 6): a Lambertian transmitter joins the
+    // diffuse class with its lobe in the lower hemisphere; a smooth dielectric is specular
+    mb.cls = (type == kMatLambert || type == kMatTranslucent) ? kClsDiffuse : kClsGlossy;
+    mb.hemi = type == kMatTranslucent ? -1.0f : 1.0f;
     mb.type = type;
     mb.rough = m1.x;
     mb.albedo[0] = m0.y;
@@ -246,6 +252,19 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
         mb.valid = true;
     } else if (type == kMatGGX) {
         mb.valid = sample_ggx(mb.wo, m1.x, mb.albedo, u1, u2, mb.wl, mb.w);
+    } else if (type == kMatTranslucent) {
+        const V3 c = sample_cosine(u1, u2);
+        mb.wl = v3(c.x, c.y, -c.z);
+        mb.w[0] = m0.y;
+        mb.w[1] = m0.z;
+        mb.w[2] = m0.w;
+        mb.valid = true;
+    } else if (type == kMatDielectric) {
+        mb.wl = sample_dielectric(mb.wo, m1.x, mb.front, u1);
+        mb.w[0] = m0.y;
+        mb.w[1] = m0.z;
+        mb.w[2] = m0.w;
+        mb.valid = mb.wo.z > 0.0f;
     } else {
         mb.wl = v3(-mb.wo.x, -mb.wo.y, mb.wo.z);
         mb.w[0] = m0.y;
@@ -255,16 +274,29 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     }
 }
 
+// A shared tangent-space direction taken into the member's own diffuse lobe: the normal
+// component becomes hemi * |z| (a translucent member mirrors it through the tangent plane),
+// so a cosine-distributed direction stays cosine-distributed in either lobe.
 __device__ __forceinline__ void take_dir(Member& mb, V3 wl) {
-    mb.wl = wl;
+    mb.wl = v3(wl.x, wl.y, fm(mb.hemi, fabsf(wl.z)));
     mb.w[0] = mb.albedo[0]; // Lambert: f cos / p_cos = albedo
     mb.w[1] = mb.albedo[1];
     mb.w[2] = mb.albedo[2];
     mb.valid = true;
 }
 
-// Spawn point of the slot's next ray: p = o + t d, offset along the shading normal by
-// 2^-18 max(1, |p|_inf) so that the new ray clears the surface it leaves.
+// Sec. 3.1 ablation: a world-space direction re-expressed in the member's frame is taken as
+// is; outside the member's lobe f = 0 and the path ends.
+__device__ __forceinline__ void take_dir_world(Member& mb, V3 l) {
+    mb.wl = l;
+    mb.w[0] = mb.albedo[0];
+    mb.w[1] = mb.albedo[1];
+    mb.w[2] = mb.albedo[2];
+    mb.valid = fm(mb.hemi, l.z) > 0.0f;
+}
+
+// Spawn point of the slot's next ray: p = o + t d, offset by 2^-18 max(1, |p|_inf) along the
+// shading normal n (pass -n for a transmitted ray) so that the new ray clears the surface.
 __device__ __forceinline__ V3 spawn_point(const ShadeArgs& a, int slot, V3 n) {
     const float4 o4 = a.ray_o[slot];
     const float4 d4 = a.ray_d[slot];
@@ -279,6 +311,7 @@ __device__ __forceinline__ V3 spawn_point(const ShadeArgs& a, int slot, V3 n) {
 // wl: cos / pi (Lambert), the GGX reflection density, 0 for the mirror's delta.
 __device__ __forceinline__ float own_pdf(const Member& mb, V3 wl) {
     if (mb.type == kMatLambert) return wl.z > 0.0f ? fm(wl.z, 0.318309886f) : 0.0f;
+    if (mb.type == kMatTranslucent) return wl.z < 0.0f ? fm(-wl.z, 0.318309886f) : 0.0f;
     if (mb.type == kMatGGX) return pdf_ggx(mb.wo, wl, mb.rough);
     return 0.0f;
 }
@@ -293,7 +326,7 @@ __device__ __forceinline__ float own_pdf(const Member& mb, V3 wl) {
 __device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p, int slot, const Member& mb,
                                            const float4 bt) {
     float4 dr = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-    if (mb.alive && mb.nee && mb.type != kMatMirror) {
+    if (mb.alive && mb.nee && mb.type != kMatMirror && mb.type != kMatDielectric) {
         const SceneDev& sc = a.scenes[mb.scene];
         if (sc.n_lights > 0) {
             const uint4 r = philox_seed(mb.seed, (uint32_t)mb.pix, mb.frame, p.bounce, kTagLight);
@@ -316,11 +349,12 @@ __device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p
             const V3 pl = v3(fa(fa(fm(l0.x, b0), fm(l1.x, b1)), fm(l2.x, b2)),
                              fa(fa(fm(l0.y, b0), fm(l1.y, b1)), fm(l2.y, b2)),
                              fa(fa(fm(l0.z, b0), fm(l1.z, b1)), fm(l2.z, b2)));
-            const V3 o = spawn_point(a, slot, mb.n);
+            // leave on the side of the lobe (below the surface for a translucent point)
+            const V3 o = spawn_point(a, slot, v3(fm(mb.hemi, mb.n.x), fm(mb.hemi, mb.n.y), fm(mb.hemi, mb.n.z)));
             const V3 dl = sub3(pl, o);
             const float r2 = dot3(dl, dl);
             const float rl = fq(r2);
-            const float ci = fd(dot3(mb.n, dl), rl);
+            const float ci = fm(mb.hemi, fd(dot3(mb.n, dl), rl));
             const V3 a0 = v3(l0.x, l0.y, l0.z);
             const V3 nl = cross3(sub3(v3(l1.x, l1.y, l1.z), a0), sub3(v3(l2.x, l2.y, l2.z), a0));
             const float cl = fd(fabsf(dot3(nl, dl)), fm(fq(dot3(nl, nl)), rl));
@@ -328,7 +362,7 @@ __device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p
                 const V3 wi = v3(fd(dl.x, rl), fd(dl.y, rl), fd(dl.z, rl));
                 const V3 wil = v3(dot3(wi, mb.t), dot3(wi, mb.b), dot3(wi, mb.n));
                 float f[3];
-                if (mb.type == kMatLambert) {
+                if (mb.type == kMatLambert || mb.type == kMatTranslucent) {
                     f[0] = fm(mb.albedo[0], 0.318309886f);
                     f[1] = fm(mb.albedo[1], 0.318309886f);
                     f[2] = fm(mb.albedo[2], 0.318309886f);
@@ -354,7 +388,7 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs
     if (a.dbg.cat && mb.pix >= 0 && !mb.final_pass) {
         const uint32_t di = (p.bounce - 1) * a.npx + (uint32_t)mb.pix;
         a.dbg.cat[di] = (uint8_t)cat;
-        a.dbg.cls[di] = (uint8_t)(mb.alive ? mb.cls : kClsNone);
+        a.dbg.cls[di] = (uint8_t)(!mb.alive ? kClsNone : (mb.hemi < 0.0f ? 3 : mb.cls)); // 3: translucent
         a.dbg.flags[di] = (uint8_t)((mb.alive ? 1 : 0) | (mb.alive && mb.valid ? 2 : 0));
         V3 lw = v3(0.0f, 0.0f, 0.0f), ww = v3(0.0f, 0.0f, 0.0f);
         if (mb.alive) {
@@ -371,7 +405,7 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs
     if (!was_alive) return;
     a.radiance[slot] = make_float4(L.x, L.y, L.z, 0.0f);
     if (mb.alive && mb.valid) {
-        const V3 o = spawn_point(a, slot, mb.n);
+        const V3 o = spawn_point(a, slot, mb.wl.z < 0.0f ? v3(-mb.n.x, -mb.n.y, -mb.n.z) : mb.n);
         const V3 dw = local_to_world(mb.t, mb.b, mb.n, mb.wl);
         a.ray_o[slot] = make_float4(o.x, o.y, o.z, __int_as_float(mb.orig));
         a.ray_d[slot] = make_float4(dw.x, dw.y, dw.z, INFINITY);
@@ -409,6 +443,8 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     mb.world = false;
     mb.nee = false;
     mb.type = kMatLambert;
+    mb.hemi = 1.0f;
+    mb.front = true;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
@@ -481,9 +517,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
                               __shfl_sync(0xffffffffu, ww.z, wdonor));
             const bool dvalid = __shfl_sync(0xffffffffu, mb.valid ? 1 : 0, wdonor) != 0;
             if (mb.world && mb.alive && mb.cls == kClsDiffuse && ba && dvalid) {
-                const V3 l = v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n));
-                take_dir(mb, l);
-                if (!(l.z > 0.0f)) mb.valid = false;
+                take_dir_world(mb, v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n)));
             }
         }
     }
@@ -518,6 +552,8 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     mb.world = false;
     mb.nee = false;
     mb.type = kMatLambert;
+    mb.hemi = 1.0f;
+    mb.front = true;
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
@@ -610,9 +646,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
                 if (s_ba[ww]) wdonor = (int)(ww * 32u + __ffs(s_ba[ww]) - 1);
             if (wdonor >= 0 && s_world[3][wdonor] != 0.0f) {
                 const V3 wdw = v3(s_world[0][wdonor], s_world[1][wdonor], s_world[2][wdonor]);
-                const V3 l = v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n));
-                take_dir(mb, l);
-                if (!(l.z > 0.0f)) mb.valid = false;
+                take_dir_world(mb, v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n)));
             }
         }
     }
