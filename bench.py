@@ -330,6 +330,7 @@ def run_ours(args):
         extras["precision_interior"] = precision_leg(cr, scenes, rank, world, args)
         extras["table3_sweep"] = sweep_leg(cr, S, cam, out, stream, rank, world)
         extras["next_event_estimation"] = nee_leg(cr, scenes, rank, args)
+        extras["transmission"] = transmission_leg(cr, scenes, rank, args)
         extras["quality"] = quality_leg(cr, S, cam, stream, results)
         if not args.no_batched:
             extras["batched"] = batched_leg(cr, scenes, rank, args)
@@ -495,6 +496,39 @@ def nee_leg(cr, scenes, rank, args):
             out["modes"][mode + ("+nee" if nee else "")] = row
     S.close()
     return out
+
+
+def transmission_leg(cr, scenes, rank, args):
+    """Transmission materials (Sec. 6 future work): 1M-triangle soup with 35/25/15/10/15
+    Lambert/translucent/GGX/mirror/dielectric triangles, 1024x1024, 1 spp, 3 bounces, 8x8
+    K=8.  Translucent points join the diffuse class (lower-hemisphere lobe), so groups mixing
+    them with Lambert points still share one direction."""
+    import numpy as np
+    import torch
+    sc = scenes.tiny(seed=9, n_soup=1_000_000, width=1024, height=1024, material_mix="transmissive")
+    S = cr.Scene(sc)
+    cam = sc.camera
+    out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    res = {"workload": "soup 1M tris, transmissive mix, 1024x1024, 1 spp, B=3, 8x8 K=8"}
+    for mode in ("direction_reuse", "independent"):
+        ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 5, 2, frame0=rank * 100, bounces=3, mode=mode, k=K)
+        res[mode] = {"mrays": round(sec / ms / 1e3, 1), "trace_only_mrays": round(sec / tr / 1e3, 1)}
+    res["trace_ratio_reuse_over_independent"] = round(res["direction_reuse"]["trace_only_mrays"] /
+                                                      res["independent"]["trace_only_mrays"], 3)
+    dbg, bufs = cr.debug_buffers(cam.width, cam.height, 1)
+    o = cr.make_opts(k=K, frame_base=0, stream=stream, debug=dbg)
+    cr.cr_render_ex(S.handle, cam, 1, 1, "direction_reuse", TILE[0], TILE[1], out, o)
+    cls = bufs["cls"][0].cpu().numpy()
+    cat = bufs["cat"][0].cpu().numpy()
+    alive = cls > 0
+    res["bounce1_classes"] = {"lambert": round(float((cls == 1).sum() / alive.sum()), 3),
+                              "translucent": round(float((cls == 3).sum() / alive.sum()), 3),
+                              "glossy_specular": round(float((cls == 2).sum() / alive.sum()), 3)}
+    res["bounce1_categories"] = {name: round(float((cat[alive] == c).mean()), 3)
+                                 for c, name in ((1, "diffuse"), (2, "glossy"), (3, "hybrid"))}
+    S.close()
+    return res
 
 
 def sweep_leg(cr, S, cam, out, stream, rank, world):
