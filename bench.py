@@ -128,11 +128,18 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_file: str):
+def kernel_source_sha(files=("trace.cu", "trace_common.cuh")) -> str:
+    """sha256 (16 hex digits) of the sources that define the BVH2 trace kernel."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2310_07182_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
     """DRAM bytes per launch of the trace kernel from the committed ncu summary, or None if
     the kernel source changed since that capture."""
     summ = os.path.join(ROOT, "profiles", "k_trace_bvh2.landscape.txt")
-    src = os.path.join(ROOT, "paper_2310_07182_gb300", "csrc", kernel_file)
     if not os.path.exists(summ):
         return None
     kv = {}
@@ -141,8 +148,7 @@ def profile_traffic(kernel_file: str):
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("source_sha") != sha or "dram_bytes_per_launch_full" not in kv:
+    if kv.get("source_sha") != kernel_source_sha() or "dram_bytes_per_launch_full" not in kv:
         return None
     return float(kv["dram_bytes_per_launch_full"])
 
@@ -227,7 +233,10 @@ def run_ours(args):
     from paper_2310_07182_gb300 import scenes
     crbuild.build()
     t_setup = time.perf_counter()
-    sc = scenes.landscape()
+    # --scene interior: the indoor workload with its ceiling light (profiling shadow rays);
+    # the headline metric is the landscape's
+    sc = scenes.landscape() if args.scene == "landscape" else scenes.interior()
+    workload = WORKLOAD if args.scene == "landscape" else "interior 1280x720 (512,014 tris), 1 spp, B=2, 8x8 K=8"
     S = cr.Scene(sc)
     cam = sc.camera
     out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
@@ -236,7 +245,8 @@ def run_ours(args):
     setup_s = time.perf_counter() - t_setup
 
     variant_flags = {"two_phase": cr.CR_OPT_TWO_PHASE, "packet": cr.CR_OPT_PACKET_SECONDARY,
-                     "speculative": cr.CR_OPT_SPECULATIVE, "persistent": cr.CR_OPT_PERSISTENT}
+                     "speculative": cr.CR_OPT_SPECULATIVE, "persistent": cr.CR_OPT_PERSISTENT,
+                     "nee": cr.CR_OPT_NEE}
 
     def parse(mode):
         # "morton_sort:<key>" selects a reordering key (Table 1 comparators); a "+<variant>"
@@ -356,12 +366,13 @@ def run_ours(args):
     bytes_per_ray = 32 + 4 + 8 + 64 * R["nodes_per_ray"] + 48 * R["tris_per_ray"]
     achieved = bytes_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e9
     peak, peak_kind = load_peaks()
-    traffic = profile_traffic("trace.cu")
+    traffic = profile_traffic()
+    l2_gbs = l2_copy_bandwidth()
     line = {
         "metric": METRIC, "value": round(R["mrays"], 2), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(R["ms_per_step"], 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mode": modes[0], "l2": "flushed between steps (256 MB write)",
+        "config": {"workload": workload, "mode": modes[0], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (frames per rank)", "timing": "CUDA events on the render stream"},
         "clocks": clocks,
         "e2e": {"value": round(e2e_rays / e2e_s / 1e6, 2), "unit": "Mrays/s",
@@ -376,6 +387,10 @@ def run_ours(args):
                          "frac": round(achieved / peak, 4), "bytes_per_ray": round(bytes_per_ray, 1),
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                          "note": "algorithmic node+triangle bytes; mostly served by L1/L2 (DRAM traffic is the 'traffic' key)"},
+        "roofline_l2": {"achieved": round(achieved, 1), "peak": round(l2_gbs, 1), "unit": "GB/s",
+                        "frac": round(achieved / l2_gbs, 4),
+                        "peak_source": "copy of an L2-resident 32 MB buffer (64 MB read+write), CUDA events",
+                        "note": "algorithmic node+triangle bytes against the L2 roof; < 1 means L1 hits carry the rest"},
         "trace_only_mrays": round(R["trace_mrays"], 2),
         "stages_ms": {k: round(R[k], 4) for k in ("ms_trace_primary", "ms_trace_secondary", "ms_shade", "ms_compact",
                                                    "ms_sort")},
@@ -393,6 +408,25 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
+
+
+def l2_copy_bandwidth(mb=32, reps=50):
+    """Bytes read + written per second by a device copy of an L2-resident buffer (the L2
+    roof of the roofline; measured, not a datasheet figure)."""
+    import torch
+    n = mb * (1 << 20) // 4
+    a = torch.empty(n, dtype=torch.float32, device="cuda").fill_(1.0)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
 def _timed_renders(cr, S, cam, out, stream, steps, warmup, frame0=0, **kw):
@@ -735,6 +769,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-window", type=float, default=1.5, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[20.0, 50.0, 100.0, 200.0])
+    ap.add_argument("--scene", default="landscape", choices=["landscape", "interior"],
+                    help="workload scene; the headline metric is the landscape's")
     ap.add_argument("--modes", default="direction_reuse,independent,morton_sort,world_reuse",
                     help="modes to time (the first is the headline); profiling runs use one")
     args = ap.parse_args()

@@ -346,7 +346,7 @@ struct B8 {
     }
 
     // Emit the node at index `self` (already reserved) for BVH2 node n.
-    void emit(uint32_t self, uint32_t n, uint32_t depth, uint32_t stack_so_far) {
+    void emit(uint32_t self, uint32_t n, uint32_t depth) {
         max_depth = std::max(max_depth, depth);
         std::vector<Child> ch = gather(n);
         // node box and octant slot assignment by the child centroids
@@ -440,9 +440,9 @@ struct B8 {
         const uint32_t child_base = (uint32_t)(nodes.size() / 20);
         w[4] = child_base;
         nodes.resize(nodes.size() + 20 * inner.size());
-        const uint32_t here = stack_so_far + (uint32_t)ch.size() - 1;
-        stack_bound = std::max(stack_bound, here + 1);
-        for (size_t i = 0; i < inner.size(); ++i) emit(child_base + (uint32_t)i, inner[i].second, depth + 1, here);
+        // the traversal keeps at most one (first child, hit mask) entry per tree level
+        stack_bound = std::max(stack_bound, depth);
+        for (size_t i = 0; i < inner.size(); ++i) emit(child_base + (uint32_t)i, inner[i].second, depth + 1);
     }
 };
 
@@ -451,7 +451,7 @@ struct B8 {
 HostBVH8 build_bvh8q(const HostBVH2& b2) {
     B8 b(b2);
     b.nodes.resize(20);
-    b.emit(0, 0, 1, 0);
+    b.emit(0, 0, 1);
     HostBVH8 out;
     out.n_nodes = (uint32_t)(b.nodes.size() / 20);
     out.nodes.swap(b.nodes);

@@ -50,10 +50,10 @@ struct HostBVH8 {
     std::vector<uint32_t> leaf_order; // BVH8 triangle position -> original triangle index
     uint32_t n_nodes = 0;
     uint32_t depth = 0;
-    uint32_t stack_bound = 0;         // largest traversal stack a ray can need
+    uint32_t stack_bound = 0;         // largest traversal stack a ray can need (the depth)
 };
 HostBVH8 build_bvh8q(const HostBVH2& b2);
-constexpr uint32_t kBvh8StackCapacity = 128; // traversal stack entries of the BVH8-Q kernel
+constexpr uint32_t kBvh8StackCapacity = 48; // traversal stack entries of the BVH8-Q kernel (one per level)
 void check_bvh2(const HostBVH2& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);
 void check_bvh8(const HostBVH8& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);
 
@@ -222,6 +222,11 @@ constexpr uint32_t kCountsWords = 256, kStatWord = 64, kCounterWord = 128, kShad
 // Shadow rays of the last shade (positions of its group queue): any-hit traversal, and the
 // contribution of each unblocked one added to the path radiance.
 void launch_shadow(const PassArgs& p, PathBuffers& b, bool first, bool bvh8, cudaStream_t st, LaunchCount& lc);
+void launch_trace_bvh8(const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
+void launch_shadow_rays_bvh8(const SceneDev* scenes, const uint16_t* slot_scene, const float4* sh_o,
+                             const float4* sh_d, const float4* sh_c, const int32_t* group_queue,
+                             const uint32_t* group_count, uint32_t n_groups_max, uint32_t K, float4* radiance,
+                             unsigned long long* n_traced, cudaStream_t st, LaunchCount& lc);
 void launch_shadow_rays(const SceneDev* scenes, const uint16_t* slot_scene, const float4* sh_o, const float4* sh_d,
                         const float4* sh_c, const int32_t* group_queue, const uint32_t* group_count,
                         uint32_t n_groups_max, uint32_t K, float4* radiance, unsigned long long* n_traced, bool bvh8,

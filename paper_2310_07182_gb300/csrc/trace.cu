@@ -1,4 +1,4 @@
-// trace.cu -- closest-hit BVH traversal (the intersection step, which dominates path
+// trace.cu -- closest-hit BVH2 traversal (the intersection step, which dominates path
 // tracing time, Sec. 1), one ray per thread.
 //
 // Stackful while-while traversal of the 64-byte two-child nodes: both child boxes are
@@ -7,200 +7,15 @@
 // in shared memory (kSmemStack entries per thread, interleaved so that a warp's pushes hit
 // distinct banks) and continues in a per-thread local array for deeper trees.  Leaves hold
 // up to four triangles tested with the watertight test of Woop, Benthin and Wald (2013).
-//
-// Closest-hit rule, identical for the BVH2 and BVH8-Q kernels (the BVH8-Q kernel is below): accept t > 0 if
-// t < t_best, or t == t_best and the original triangle index is smaller.  Boxes are culled
-// only if their entry distance exceeds t_best (1 + 2^-16) and the slab exit is widened by
-// (1 + 2^-21) > 1 + 2 gamma_3 (Ize 2013), so no box that holds a candidate triangle is ever
-// skipped and both BVH layouts return the same hit bit for bit.
+// The primitives and the closest-hit rule shared with the BVH8-Q kernels (trace_bvh8.cu)
+// are in trace_common.cuh.
 #include <cuda_runtime.h>
 
 #include "cr_internal.h"
+#include "trace_common.cuh"
 
 namespace cr {
 namespace {
-
-constexpr int kSmemStack = 16;  // entries per thread in shared memory
-constexpr int kStackTotal = 64; // >= BVH depth (the builder keeps depth <= 64)
-constexpr float kFarWiden = 1.0f + 0x1.0p-21f;
-constexpr float kCullWiden = 1.0f + 0x1.0p-16f;
-
-struct RayPre {
-    float ox, oy, oz;
-    float ix, iy, iz; // 1 / d (zero components replaced by +-1e-20 first)
-    int kx, ky, kz;
-    float sx, sy, sz; // shear constants of the watertight test
-    float dx, dy, dz;
-    // slab offsets for t = fma(plane, 1/d, offset): -o/d biased outward by 2^-22 |o/d|, which
-    // bounds the rounding of o/d and of the offset, so the FMA interval contains the one the
-    // exact (plane - o) / d form gives (see box_entry_fma)
-    float lox, loy, loz, hix, hiy, hiz;
-};
-
-__device__ __forceinline__ float sel3(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
-
-__device__ __forceinline__ RayPre prep_ray(float4 o, float4 d) {
-    RayPre r;
-    r.ox = o.x;
-    r.oy = o.y;
-    r.oz = o.z;
-    r.dx = d.x;
-    r.dy = d.y;
-    r.dz = d.z;
-    const float tiny = 1e-20f;
-    r.ix = 1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x));
-    r.iy = 1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y));
-    r.iz = 1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z));
-    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    int kz = ax > ay ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    int kx = kz + 1 == 3 ? 0 : kz + 1;
-    int ky = kx + 1 == 3 ? 0 : kx + 1;
-    const float dkz = sel3(d.x, d.y, d.z, kz);
-    if (dkz < 0.0f) {
-        int t = kx;
-        kx = ky;
-        ky = t;
-    }
-    r.kx = kx;
-    r.ky = ky;
-    r.kz = kz;
-    r.sx = sel3(d.x, d.y, d.z, kx) / dkz;
-    r.sy = sel3(d.x, d.y, d.z, ky) / dkz;
-    r.sz = 1.0f / dkz;
-    // plane of the lower bound enters first when 1/d >= 0; bias each offset so that the
-    // entry distance can only decrease and the exit distance only increase
-    const float oix = __fmul_rn(r.ox, r.ix), oiy = __fmul_rn(r.oy, r.iy), oiz = __fmul_rn(r.oz, r.iz);
-    const float ex = __fmul_rn(fabsf(oix), 0x1.0p-22f), ey = __fmul_rn(fabsf(oiy), 0x1.0p-22f),
-                ez = __fmul_rn(fabsf(oiz), 0x1.0p-22f);
-    r.lox = r.ix >= 0.0f ? -oix - ex : -oix + ex;
-    r.hix = r.ix >= 0.0f ? -oix + ex : -oix - ex;
-    r.loy = r.iy >= 0.0f ? -oiy - ey : -oiy + ey;
-    r.hiy = r.iy >= 0.0f ? -oiy + ey : -oiy - ey;
-    r.loz = r.iz >= 0.0f ? -oiz - ez : -oiz + ez;
-    r.hiz = r.iz >= 0.0f ? -oiz + ez : -oiz - ez;
-    return r;
-}
-
-// Slab test of one box; returns the entry distance, or +inf if the box is missed or culled.
-__device__ __forceinline__ float box_entry(const RayPre& r, float lox, float hix, float loy, float hiy, float loz,
-                                           float hiz, float tcull) {
-    const float tx0 = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), tx1 = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
-    const float ty0 = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), ty1 = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
-    const float tz0 = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), tz1 = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
-    return (tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull) ? tn : INFINITY;
-}
-
-// The same test with one FMA per plane.  Each plane distance fma(x, 1/d, offset) differs
-// from (x - o) * (1/d) by at most the rounding of o/d and of the offset (<= 2^-23 |o/d|) plus a
-// relative 2^-24; the offsets are pre-biased by 2^-22 |o/d| toward a larger interval and the
-// exit is widened by (1 + 2^-21), so no box that the exact form would enter is rejected.
-#ifndef CR_TRACE_MINMAX3
-#define CR_TRACE_MINMAX3 1
-#endif
-// three-input min / max (one instruction each on sm_100 and later)
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-#if CR_TRACE_MINMAX3
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-#else
-    return fminf(fminf(a, b), c);
-#endif
-}
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-#if CR_TRACE_MINMAX3
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-#else
-    return fmaxf(fmaxf(a, b), c);
-#endif
-}
-
-__device__ __forceinline__ float box_entry_fma(const RayPre& r, float lox, float hix, float loy, float hiy, float loz,
-                                               float hiz, float tcull) {
-    const float tx0 = fmaf(lox, r.ix, r.lox), tx1 = fmaf(hix, r.ix, r.hix);
-    const float ty0 = fmaf(loy, r.iy, r.loy), ty1 = fmaf(hiy, r.iy, r.hiy);
-    const float tz0 = fmaf(loz, r.iz, r.loz), tz1 = fmaf(hiz, r.iz, r.hiz);
-    const float tn = max3f(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float tf = min3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fmaxf(tz0, tz1));
-    return (tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull) ? tn : INFINITY;
-}
-
-// Watertight ray/triangle test (Woop, Benthin, Wald 2013) without the double-precision
-// fallback: edge functions of exactly zero count as inside, so shared edges are covered.
-__device__ __forceinline__ bool tri_test(const RayPre& r, float4 a4, float4 b4, float4 c4, float& t_out) {
-    const float Ax3 = a4.x - r.ox, Ay3 = a4.y - r.oy, Az3 = a4.z - r.oz;
-    const float Bx3 = b4.x - r.ox, By3 = b4.y - r.oy, Bz3 = b4.z - r.oz;
-    const float Cx3 = c4.x - r.ox, Cy3 = c4.y - r.oy, Cz3 = c4.z - r.oz;
-    const float Akx = sel3(Ax3, Ay3, Az3, r.kx), Aky = sel3(Ax3, Ay3, Az3, r.ky), Akz = sel3(Ax3, Ay3, Az3, r.kz);
-    const float Bkx = sel3(Bx3, By3, Bz3, r.kx), Bky = sel3(Bx3, By3, Bz3, r.ky), Bkz = sel3(Bx3, By3, Bz3, r.kz);
-    const float Ckx = sel3(Cx3, Cy3, Cz3, r.kx), Cky = sel3(Cx3, Cy3, Cz3, r.ky), Ckz = sel3(Cx3, Cy3, Cz3, r.kz);
-    const float Ax = __fsub_rn(Akx, __fmul_rn(r.sx, Akz)), Ay = __fsub_rn(Aky, __fmul_rn(r.sy, Akz));
-    const float Bx = __fsub_rn(Bkx, __fmul_rn(r.sx, Bkz)), By = __fsub_rn(Bky, __fmul_rn(r.sy, Bkz));
-    const float Cx = __fsub_rn(Ckx, __fmul_rn(r.sx, Ckz)), Cy = __fsub_rn(Cky, __fmul_rn(r.sy, Ckz));
-    const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
-    const float det = __fadd_rn(__fadd_rn(U, V), W);
-    if (det == 0.0f) return false;
-    const float Az = __fmul_rn(r.sz, Akz), Bz = __fmul_rn(r.sz, Bkz), Cz = __fmul_rn(r.sz, Ckz);
-    const float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Az), __fmul_rn(V, Bz)), __fmul_rn(W, Cz));
-    const float t = __fdiv_rn(T, det);
-    if (!(t > 0.0f)) return false;
-    t_out = t;
-    return true;
-}
-
-struct Best {
-    float t;
-    int leaf;
-    int orig;
-};
-
-__device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const RayPre& r, int skip, uint32_t first,
-                                          uint32_t count, Best& best, unsigned long long& n_tri) {
-    for (uint32_t i = 0; i < count; ++i) {
-        const uint32_t tri = first + i;
-        const float4 a = __ldg(&tris[3 * tri + 0]);
-        const int orig = __float_as_int(a.w);
-        if (orig == skip) continue;
-        const float4 b = __ldg(&tris[3 * tri + 1]);
-        const float4 c = __ldg(&tris[3 * tri + 2]);
-        ++n_tri;
-        float t;
-        if (tri_test(r, a, b, c, t) && (t < best.t || (t == best.t && orig < best.orig))) {
-            best.t = t;
-            best.leaf = (int)tri;
-            best.orig = orig;
-        }
-    }
-}
-
-#ifndef CR_TRACE_LOCAL_STACK
-#define CR_TRACE_LOCAL_STACK 0
-#endif
-#if CR_TRACE_LOCAL_STACK
-// whole stack in a per-thread local array (L1-resident); depth < kStackTotal by construction
-#define STACK_PUSH(v) (lstack_all[sp++] = (v))
-#define STACK_POP(v) ((v) = lstack_all[--sp])
-#else
-// first kSmemStack entries in shared memory, the rest in a local array
-#define STACK_PUSH(v)                                                                \
-    do {                                                                             \
-        if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)(v);                    \
-        else if (sp < kStackTotal) lstack[sp - kSmemStack] = (v);                   \
-        sp = sp < kStackTotal ? sp + 1 : sp; /* the builder keeps depth < kStackTotal */ \
-    } while (0)
-#define STACK_POP(v)                                                                 \
-    do {                                                                             \
-        --sp;                                                                        \
-        (v) = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack]; \
-    } while (0)
-#endif
 
 // kAny: visibility only; the traversal ends at the first triangle hit before the ray's tmax.
 template <bool kCount, bool kAny = false>
@@ -739,120 +554,10 @@ __global__ void __launch_bounds__(128) k_trace_bvh2_dynamic(
     }
 }
 
-// ------------------------------------------------------------------------------------
-// BVH8-Q traversal.  Per node: the 80-byte node is fetched with five 16-byte loads, the valid
-// children are decoded (origin + q * step, exact product, one rounded add) and tested with the
-// same conservative slab test as the BVH2 kernel, visiting slots in the order k ^ octant(d)
-// so that near children tend to come first.  Hit children are pushed far to near except the
-// nearest, which is visited next.  Stack entries: inner node index (>= 0) or leaf
-// ~((first triangle << 3) | (count - 1)).  Triangles are the BVH8 copy (same records).
-constexpr int kStack8 = (int)kBvh8StackCapacity; // >= the builder's stack bound (checked at scene creation)
-
-__device__ __forceinline__ uint32_t byte_of(uint32_t lo, uint32_t hi, uint32_t slot) {
-    return ((slot < 4 ? lo : hi) >> (8 * (slot & 3))) & 0xffu;
-}
-
-template <bool kCount, bool kAny = false>
-__device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, const float4* __restrict__ tris,
-                                               float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
-                                               unsigned long long& n_tri) {
-    const RayPre r = prep_ray(ro, rd);
-    const int skip = __float_as_int(ro.w);
-    const uint32_t oct = (rd.x < 0.0f ? 1u : 0u) | (rd.y < 0.0f ? 2u : 0u) | (rd.z < 0.0f ? 4u : 0u);
-    Best best{rd.w, -1, 0x7fffffff};
-    int lstack[kStack8 - kSmemStack];
-    int sp = 0;
-    int entry = 0;
-    const int stride = blockDim.x;
-    while (true) {
-        if (entry >= 0) {
-            if (kCount) ++n_node;
-            const uint4 w0 = __ldg(&nodes[5 * entry + 0]);
-            const uint4 w1 = __ldg(&nodes[5 * entry + 1]);
-            const uint4 w2 = __ldg(&nodes[5 * entry + 2]);
-            const uint4 w3 = __ldg(&nodes[5 * entry + 3]);
-            const uint4 w4 = __ldg(&nodes[5 * entry + 4]);
-            const float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
-            const float sx = __uint_as_float((w0.w & 0xffu) << 23);
-            const float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
-            const float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
-            const uint32_t imask = w0.w >> 24;
-            const float tcull = __fmul_rn(best.t, kCullWiden);
-            int next = kDone;
-#pragma unroll 1
-            for (int k = 7; k >= 0; --k) {
-                const uint32_t sl = (uint32_t)k ^ oct;
-                const uint32_t m = byte_of(w1.z, w1.w, sl);
-                const bool inner = (imask >> sl) & 1u;
-                if (!inner && m < 32u) continue; // empty slot
-                const float lox = __fadd_rn(ox, __fmul_rn((float)byte_of(w2.x, w2.y, sl), sx));
-                const float loy = __fadd_rn(oy, __fmul_rn((float)byte_of(w2.z, w2.w, sl), sy));
-                const float loz = __fadd_rn(oz, __fmul_rn((float)byte_of(w3.x, w3.y, sl), sz));
-                const float hix = __fadd_rn(ox, __fmul_rn((float)byte_of(w3.z, w3.w, sl), sx));
-                const float hiy = __fadd_rn(oy, __fmul_rn((float)byte_of(w4.x, w4.y, sl), sy));
-                const float hiz = __fadd_rn(oz, __fmul_rn((float)byte_of(w4.z, w4.w, sl), sz));
-                if (box_entry(r, lox, hix, loy, hiy, loz, hiz, tcull) == INFINITY) continue;
-                const int e = inner ? (int)(w1.x + m) : ~(int)(((w1.y + (m & 31u)) << 3) | ((m >> 5) - 1u));
-                if (next != kDone) {
-                    if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)next;
-                    else if (sp < kStack8) lstack[sp - kSmemStack] = next;
-                    sp = sp < kStack8 ? sp + 1 : sp; // scene creation checks the bound
-                }
-                next = e;
-            }
-            if (next != kDone) {
-                entry = next;
-                continue;
-            }
-        } else {
-            const uint32_t code = (uint32_t)(~entry);
-            test_leaf(tris, r, skip, code >> 3, (code & 7u) + 1u, best, n_tri);
-            if (kAny && best.leaf >= 0) break;
-        }
-        if (sp == 0) break;
-        --sp;
-        entry = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack];
-    }
-    return make_int2(best.leaf, __float_as_int(best.t));
-}
-
-template <bool kCount, bool kAny = false>
-__global__ void __launch_bounds__(128, 8) k_trace_bvh8(const SceneDev* __restrict__ scenes,
-                             const uint16_t* __restrict__ slot_scene,
-                             const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
-                             const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
-                             uint32_t n_max, int2* __restrict__ hit, unsigned long long* counters) {
-    extern __shared__ uint32_t smem_stack[];
-    const uint32_t n = queue_count ? min(*queue_count, n_max) : n_max;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long n_node = 0, n_tri = 0;
-    if (i < n) {
-        const int slot = queue ? queue[i] : (int)i;
-        const SceneDev& sc = scenes[slot_scene ? slot_scene[slot] : 0];
-        const float4 ro = ray_o[slot];
-        const float4 rd = ray_d[slot];
-        int2 h = make_int2(-1, __float_as_int(INFINITY));
-        if (rd.w >= 0.0f)
-            h = trace_bvh8_one<kCount, kAny>(sc.nodes8, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
-        hit[slot] = h;
-    }
-    if (kCount) {
-        for (int off = 16; off > 0; off >>= 1) {
-            n_node += __shfl_down_sync(0xffffffffu, n_node, off);
-            n_tri += __shfl_down_sync(0xffffffffu, n_tri, off);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&counters[0], n_node);
-            atomicAdd(&counters[1], n_tri);
-        }
-    }
-}
-
 // Shadow rays of next-event estimation, one thread per position of the last shade's group
 // queue (so a reuse group's rays run in adjacent lanes, as they were shaded).  A ray whose
 // direction record has w = tmax > 0 is traced for visibility only; if nothing blocks it, its
 // contribution is added to the path radiance of its slot.  Rays traced are counted.
-template <bool kBvh8>
 __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_shadow(
     const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, const float4* __restrict__ sh_o,
     const float4* __restrict__ sh_d, const float4* __restrict__ sh_c, const int32_t* __restrict__ group_queue,
@@ -871,8 +576,7 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_shadow(
             const float4 ro = sh_o[slot];
             const SceneDev& sc = scenes[slot_scene[slot]];
             unsigned long long dn = 0, dt = 0;
-            const int2 h = kBvh8 ? trace_bvh8_one<false, true>(sc.nodes8, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt)
-                                 : trace_bvh2_one<false, true>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt);
+            const int2 h = trace_bvh2_one<false, true>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt);
             if (h.x < 0) {
                 const float4 c = sh_c[slot];
                 const float4 L = radiance[slot];
@@ -914,12 +618,13 @@ void launch_shadow_rays(const SceneDev* scenes, const uint16_t* slot_scene, cons
     const int block = 128;
     const size_t smem = (size_t)kSmemStack * block * sizeof(uint32_t);
     const uint32_t grid = (n_pos + block - 1) / block;
-    if (bvh8)
-        k_trace_shadow<true><<<grid, block, smem, st>>>(scenes, slot_scene, sh_o, sh_d, sh_c, group_queue, group_count,
-                                                        n_groups_max, K, radiance, n_traced);
-    else
-        k_trace_shadow<false><<<grid, block, smem, st>>>(scenes, slot_scene, sh_o, sh_d, sh_c, group_queue, group_count,
-                                                         n_groups_max, K, radiance, n_traced);
+    if (bvh8) {
+        launch_shadow_rays_bvh8(scenes, slot_scene, sh_o, sh_d, sh_c, group_queue, group_count, n_groups_max, K,
+                                radiance, n_traced, st, lc);
+        return;
+    }
+    k_trace_shadow<<<grid, block, smem, st>>>(scenes, slot_scene, sh_o, sh_d, sh_c, group_queue, group_count,
+                                              n_groups_max, K, radiance, n_traced);
     lc.n++;
 }
 
@@ -954,25 +659,14 @@ void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
     const int block = a.block;
     const size_t smem = (size_t)kSmemStack * block * sizeof(uint32_t);
     const size_t smem128 = (size_t)kSmemStack * 128 * sizeof(uint32_t);
-    if (a.any_hit) { // visibility queries (cr_trace_rays with CR_OPT_ANY_HIT)
-        const uint32_t grid = (a.n_max + block - 1) / block;
-        if (a.bvh8)
-            k_trace_bvh8<false, true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
-                                                                 a.queue_count, a.n_max, a.hit, nullptr);
-        else
-            k_trace_bvh2<false, true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
-                                                                 a.queue_count, a.n_max, a.hit, nullptr);
-        lc.n++;
+    if (a.bvh8) { // BVH8-Q kernels (trace_bvh8.cu)
+        launch_trace_bvh8(a, st, lc);
         return;
     }
-    if (a.bvh8) {
+    if (a.any_hit) { // visibility queries (cr_trace_rays with CR_OPT_ANY_HIT)
         const uint32_t grid = (a.n_max + block - 1) / block;
-        if (a.counters)
-            k_trace_bvh8<true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
-                                                          a.queue_count, a.n_max, a.hit, a.counters);
-        else
-            k_trace_bvh8<false><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
-                                                           a.queue_count, a.n_max, a.hit, nullptr);
+        k_trace_bvh2<false, true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
+                                                             a.queue_count, a.n_max, a.hit, nullptr);
         lc.n++;
         return;
     }
