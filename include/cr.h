@@ -412,6 +412,16 @@ cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, uint32_t flag
 cr_status cr_trace_rays_static(cr_scene* scene, const float* rays, const int32_t* skip_prim, uint32_t n,
                                int32_t* prim, float* t, void* stream);
 
+/* ---------------------------------------------------------------------------------- */
+/* Measurement utility (no counterpart in the paper): the L2 read roof of the roofline.
+ * Allocates a device buffer of `bytes` (rounded down to 16 B), fills it, reads it once to
+ * warm the L2, then times `reps` passes of a read-only kernel (16-byte read-only loads, a
+ * grid of 8 blocks of 256 threads per SM, a grid-stride loop) with CUDA events and writes the
+ * bytes read per second (GB/s, 1e9) to *gbs.  Choose `bytes` well below the L2 size so the
+ * passes hit in L2.  Frees the buffer before returning.
+ * Errors: CR_ERR_INVALID_ARG (bytes < 1 MiB, reps 0, NULL gbs), CR_ERR_OOM, CR_ERR_CUDA. */
+cr_status cr_measure_l2_read(uint64_t bytes, uint32_t reps, double* gbs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,7 @@ _SIGS = [
     ("cr_debug_bvh_check", C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.POINTER(cr_bvh_report)]),
     ("cr_trace_rays_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
+    ("cr_measure_l2_read", C.c_int, [C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]),
 ]
 CR_TRACE_STATIC_MAX_RAYS = 65536
 
@@ -395,6 +396,13 @@ def cr_server_get_stats(handle) -> dict:
 
 def cr_server_destroy(handle):
     _check(lib().cr_server_destroy(handle))
+
+
+def cr_measure_l2_read(nbytes=48 << 20, reps=100) -> float:
+    """L2 read bandwidth (GB/s) of a read-only kernel over an L2-resident buffer."""
+    v = C.c_double()
+    _check(lib().cr_measure_l2_read(C.c_uint64(nbytes), reps, C.byref(v)))
+    return v.value
 
 
 def cr_debug_bvh_check(tri_xyz, flags=CR_BVH2 | CR_BVH8Q) -> dict:

@@ -157,3 +157,12 @@ def test_bvh8q_hits_identical_to_bvh2(cr, orc, name):
     # and against the oracle on a sample of the unbounded rays (the oracle has no tmax)
     unb = np.isinf(rays[:, 7])
     _compare(orc, sc, S, rays[unb][:4000], skip.cpu().numpy()[unb][:4000], bvh=cr.CR_BVH8Q)
+
+
+def test_l2_read_probe(cr):
+    """The roofline's L2 roof: a positive finite bandwidth for an L2-resident buffer, and
+    argument errors reported as such."""
+    gbs = cr.cr_measure_l2_read(48 << 20, 20)
+    assert 1000.0 < gbs < 1e6
+    with pytest.raises(cr.CrError):
+        cr.cr_measure_l2_read(1024, 1)
