@@ -471,7 +471,7 @@ cr_status Workspace::ensure_phase(uint32_t n_slots) {
     phase_base = nullptr;
     const size_t ns = n_slots, nb = (ns + 255) / 256 + 1;
     const size_t o_state = 0, o_susp = o_state + sizeof(TraceState) * ns, o_q2 = (o_susp + ns + 255) & ~(size_t)255,
-                 o_cnt = o_q2 + 4 * ns, o_bc = o_cnt + 256, total = o_bc + 8 * nb;
+                 o_cnt = (o_q2 + 4 * ns + 255) & ~(size_t)255, o_bc = o_cnt + 256, total = o_bc + 8 * nb;
     cudaError_t e = cudaMalloc(&phase_base, total);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -715,9 +715,9 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_count(const int32_t* 
     if (threadIdx.x % K == 0) {
         for (uint32_t j = 0; j < K; ++j) gl |= s_alive[threadIdx.x + j];
     }
-    uint32_t tot_r, tot_g;
-    block_excl_scan(a ? 1u : 0u, s_warp, tot_r);
-    block_excl_scan(gl, s_warp, tot_g);
+    (void)s_warp;
+    const uint32_t tot_r = (uint32_t)__syncthreads_count(a);
+    const uint32_t tot_g = (uint32_t)__syncthreads_count(gl != 0u);
     if (threadIdx.x == 0) {
         block_counts[2 * blockIdx.x + 0] = tot_r;
         block_counts[2 * blockIdx.x + 1] = tot_g;
@@ -729,24 +729,49 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_count(const int32_t* 
 __global__ void __launch_bounds__(1024) k_compact_scan(uint32_t* __restrict__ block_counts, uint32_t n_blocks,
                                                        uint32_t* __restrict__ out_counts,
                                                        unsigned long long* __restrict__ stat) {
-    __shared__ uint32_t s_warp[32];
-    for (int col = 0; col < 2; ++col) {
-        const uint32_t per = (n_blocks + blockDim.x - 1) / blockDim.x;
-        const uint32_t b0 = threadIdx.x * per;
-        uint32_t local = 0;
-        for (uint32_t k = 0; k < per && b0 + k < n_blocks; ++k) local += block_counts[2 * (b0 + k) + col];
-        uint32_t total;
-        uint32_t run = block_excl_scan(local, s_warp, total);
-        for (uint32_t k = 0; k < per && b0 + k < n_blocks; ++k) {
-            const uint32_t v = block_counts[2 * (b0 + k) + col];
-            block_counts[2 * (b0 + k) + col] = run;
-            run += v;
+    // both columns at once: each thread loads its run of (rays, groups) pairs as 8-byte
+    // words (independent loads), the two counts travel packed in one 64-bit value through
+    // the block scan (each column total < 2^32)
+    __shared__ unsigned long long s_w[32];
+    uint2* bc = reinterpret_cast<uint2*>(block_counts);
+    const uint32_t per = (n_blocks + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = threadIdx.x * per;
+    unsigned long long local = 0;
+    for (uint32_t k = 0; k < per; ++k)
+        if (b0 + k < n_blocks) {
+            const uint2 v = bc[b0 + k];
+            local += (unsigned long long)v.x | ((unsigned long long)v.y << 32);
         }
-        if (threadIdx.x == 0) {
-            out_counts[col] = total;
-            if (stat && col == 0) atomicAdd(stat, (unsigned long long)total);
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    unsigned long long x = local;
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t nw = blockDim.x >> 5;
+        unsigned long long t = lane < nw ? s_w[lane] : 0ull;
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
         }
-        __syncthreads();
+        if (lane < nw) s_w[lane] = t;
+    }
+    __syncthreads();
+    unsigned long long run = x - local + (w > 0 ? s_w[w - 1] : 0ull);
+    for (uint32_t k = 0; k < per; ++k)
+        if (b0 + k < n_blocks) {
+            const uint2 v = bc[b0 + k];
+            bc[b0 + k] = make_uint2((uint32_t)run, (uint32_t)(run >> 32));
+            run += (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+        }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = s_w[(blockDim.x >> 5) - 1];
+        out_counts[0] = (uint32_t)total;
+        out_counts[1] = (uint32_t)(total >> 32);
+        if (stat) atomicAdd(stat, (unsigned long long)(uint32_t)total);
     }
 }
 
