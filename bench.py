@@ -694,15 +694,16 @@ def serving_leg(cr, scenes, args):
     """Poisson arrivals against six resident scenes (tiny, soups 1M/4M, interior, landscape,
     terrain 2236^2 = 9,990,450 triangles), sides log-uniform in [128, 2048] (multiples of
     16), spp in {1,4,16,64}, 1-4 bounces, host outputs; p50/p99 latency from submission to
-    the result on the host, and throughput, for direction reuse + BVH8-Q and for
-    independent sampling + BVH2."""
+    the result on the host, and throughput, for direction reuse + BVH8-Q, independent
+    sampling + BVH2 and direction reuse + BVH2."""
     import numpy as np
     world = {"tiny": scenes.tiny(), "soup1m": scenes.soup(31, 1_000_000), "soup4m": scenes.soup(32, 4_000_000),
              "interior": scenes.interior(), "landscape": scenes.landscape(), "terrain": scenes.terrain()}
     S = {k: cr.Scene(v, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q) for k, v in world.items()}
     names = list(world)
     out = {"window_s": args.serve_window, "rates": list(args.serve_rates), "configs": {}}
-    for cfg, mode, bvh in (("reuse_bvh8q", "direction_reuse", cr.CR_BVH8Q), ("independent_bvh2", "independent", cr.CR_BVH2)):
+    for cfg, mode, bvh in (("reuse_bvh8q", "direction_reuse", cr.CR_BVH8Q), ("independent_bvh2", "independent", cr.CR_BVH2),
+                           ("reuse_bvh2", "direction_reuse", cr.CR_BVH2)):
         rows = {}
         for lam in args.serve_rates:
             rng = np.random.default_rng(41 + int(lam))
