@@ -648,7 +648,7 @@ def batched_leg(cr, scenes, rank, args):
                        "4 spp, 3 bounces, direction_reuse",
            "pixels": int(sum(sd * sd for _, sd, _ in specs)),
            "autotune": {"seconds": round(tune_s, 1), "candidates": rep["n_candidates"],
-                        "best": f"{opts.group_w}x{opts.group_h} K={opts.k} interleave={'lcg' if opts.interleave else 'contiguous'} block={opts.block}",
+                        "best": f"{opts.group_w}x{opts.group_h} K={opts.k} interleave={'lcg' if opts.interleave else 'contiguous'} block={opts.block} stack={opts.stack}",
                         "best_ms_spp1": round(rep["best_ms"], 3), "default_ms_spp1": round(rep["default_ms"], 3)}}
     variants = {"graph_autotuned": (opts, cr.CR_BATCH_GRAPH),
                 "graph_default": (cr.make_batch_opts(tile=(8, 8), k=8), cr.CR_BATCH_GRAPH),

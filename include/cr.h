@@ -188,6 +188,7 @@ typedef struct {
     uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 */
     uint32_t flags;        /* CR_OPT_* */
     uint32_t sort_key;     /* cr_sort_key of CR_MORTON_SORT (default TwoPoint) */
+    uint32_t stack;        /* BVH2 traversal stack entries per thread in shared memory: 8, 16 or 32 (0 = 16) */
     void* stream;          /* cudaStream_t to run on; NULL = legacy default stream */
     cr_stats* stats;       /* optional, host */
     cr_debug* debug;       /* optional, host struct of device pointers */
@@ -267,6 +268,7 @@ typedef struct {
     uint32_t block;            /* trace block size; 0 = 128 */
     uint32_t flags;            /* CR_BATCH_GRAPH | CR_OPT_PERSISTENT */
     uint32_t sort_key;         /* cr_sort_key of CR_MORTON_SORT jobs */
+    uint32_t stack;            /* shared-memory traversal stack entries: 8, 16, 32 (0 = 16) */
     void* stream;              /* cudaStream_t used by cr_batch_run (NULL = a stream the batch owns) */
 } cr_batch_opts;
 
@@ -286,11 +288,12 @@ cr_status cr_batch_device_bytes(const cr_job* jobs, uint32_t n_jobs, const cr_ba
 
 /* Autotuner: times candidate (W,H) in {4x4, 8x8, 16x16}, K <= W*H/4 (larger K loses image
  * quality, Sec. 5.3), interleave {LCG, contiguous} if allowed, and trace block {64, 128,
- * 256} on the given jobs (renders them), and writes the fastest into *opts (its bvh and flags
- * are kept).  allow_contiguous = 0 keeps the LCG interleave of Sec. 3.3. */
+ * 256} on the given jobs (renders them), then the traversal stack depth in shared memory
+ * {8, 16, 32} for the fastest of those, and writes the winner into *opts (its bvh and
+ * flags are kept).  allow_contiguous = 0 keeps the LCG interleave of Sec. 3.3. */
 typedef struct {
     uint32_t n_candidates;
-    uint32_t best_group_w, best_group_h, best_k, best_interleave, best_block;
+    uint32_t best_group_w, best_group_h, best_k, best_interleave, best_block, best_stack;
     double best_ms;   /* device ms of one run of the best candidate */
     double worst_ms;  /* slowest candidate */
     double default_ms;/* 8x8, K=8, LCG, block 128 */

@@ -93,13 +93,13 @@ class cr_job(C.Structure):
 class cr_batch_opts(C.Structure):
     _fields_ = [("group_w", C.c_uint32), ("group_h", C.c_uint32), ("k", C.c_uint32), ("interleave", C.c_uint32),
                 ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32), ("sort_key", C.c_uint32),
-                ("stream", C.c_void_p)]
+                ("stack", C.c_uint32), ("stream", C.c_void_p)]
 
 
 class cr_tune_report(C.Structure):
     _fields_ = [("n_candidates", C.c_uint32), ("best_group_w", C.c_uint32), ("best_group_h", C.c_uint32),
                 ("best_k", C.c_uint32), ("best_interleave", C.c_uint32), ("best_block", C.c_uint32),
-                ("best_ms", C.c_double), ("worst_ms", C.c_double), ("default_ms", C.c_double)]
+                ("best_stack", C.c_uint32), ("best_ms", C.c_double), ("worst_ms", C.c_double), ("default_ms", C.c_double)]
 
 
 class cr_server_opts(C.Structure):
@@ -122,7 +122,7 @@ class cr_server_stats(C.Structure):
 class cr_render_opts(C.Structure):
     _fields_ = [("k", C.c_uint32), ("interleave", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
                 ("reuse_depth", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32),
-                ("sort_key", C.c_uint32), ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
+                ("sort_key", C.c_uint32), ("stack", C.c_uint32), ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
                 ("debug", C.POINTER(cr_debug))]
 
 
@@ -262,12 +262,13 @@ SORT_KEYS = {"two_point": 0, "origin": 1, "reis": 2, "costa": 3, "aila_compact":
 
 
 def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_BVH2, block=0, flags=0,
-              stream=None, stats=None, debug=None, sort_key=0) -> cr_render_opts:
+              stream=None, stats=None, debug=None, sort_key=0, stack=0) -> cr_render_opts:
     o = cr_render_opts()
     _check(lib().cr_render_opts_default(C.byref(o)))
     o.k, o.interleave, o.seed, o.frame_base = k, int(interleave), seed, frame_base
     o.reuse_depth, o.bvh, o.block, o.flags = reuse_depth, bvh, block, flags
     o.sort_key = SORT_KEYS.get(sort_key, sort_key)
+    o.stack = stack
     o.stream = stream
     if stats is not None:
         o.stats = C.pointer(stats)
@@ -315,10 +316,11 @@ def make_job(scene_handle, cam, out, spp=1, max_bounces=1, mode="direction_reuse
     return j
 
 
-def make_batch_opts(tile=(8, 8), k=0, interleave=True, bvh=CR_BVH2, block=0, flags=0, stream=None) -> cr_batch_opts:
+def make_batch_opts(tile=(8, 8), k=0, interleave=True, bvh=CR_BVH2, block=0, flags=0, stream=None,
+                    stack=0) -> cr_batch_opts:
     o = cr_batch_opts()
     o.group_w, o.group_h, o.k, o.interleave = tile[0], tile[1], k, int(interleave)
-    o.bvh, o.block, o.flags = bvh, block, flags
+    o.bvh, o.block, o.flags, o.stack = bvh, block, flags, stack
     o.stream = stream
     return o
 
@@ -457,7 +459,7 @@ class Scene:
 
     def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
                seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
-               debug=None, stream=None, sort_key=0, nee=False):
+               debug=None, stream=None, sort_key=0, nee=False, stack=0):
         """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
         CUDA tensor by default).  Returns (out, stats dict or None)."""
         import torch
@@ -467,8 +469,7 @@ class Scene:
         st = cr_stats() if stats else None
         o = make_opts(k=k, interleave=interleave, seed=seed, frame_base=frame_base, reuse_depth=reuse_depth, bvh=bvh,
                       block=block, flags=flags | (CR_OPT_STATS if stats else 0) | (CR_OPT_NEE if nee else 0),
-                      stream=stream, stats=st,
-                      debug=debug, sort_key=sort_key)
+                      stream=stream, stats=st, debug=debug, sort_key=sort_key, stack=stack)
         cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
         return out, (st.as_dict() if st is not None else None)
 

@@ -696,6 +696,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
     ta.ray_d = b.ray_d;
     ta.hit = b.hit;
     ta.block = eo.block;
+    ta.stack = eo.stack;
     ta.persistent = eo.persistent;
     ta.speculative = eo.speculative;
     ta.work_counter = b.counts + 2;
@@ -844,6 +845,9 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     if (st != CR_OK) return st;
     ExecOpts eo;
     eo.block = block;
+    if (o.stack != 0 && o.stack != 8 && o.stack != 16 && o.stack != 32)
+        return fail(CR_ERR_INVALID_ARG, "cr_render: stack %u not in {8, 16, 32}", o.stack);
+    eo.stack = o.stack ? o.stack : 16;
     eo.persistent = (o.flags & CR_OPT_PERSISTENT) != 0;
     eo.speculative = (o.flags & CR_OPT_SPECULATIVE) != 0;
     eo.packet_primary = (o.flags & CR_OPT_PACKET_PRIMARY) != 0;
@@ -1150,6 +1154,9 @@ static cr_status batch_opts_check(const cr_batch_opts* o, PlanOpts& po, ExecOpts
     po.interleave = o->interleave;
     po.bvh8 = o->bvh == CR_BVH8Q;
     eo.block = block;
+    if (o->stack != 0 && o->stack != 8 && o->stack != 16 && o->stack != 32)
+        return fail(CR_ERR_INVALID_ARG, "stack %u not in {8, 16, 32}", o->stack);
+    eo.stack = o->stack ? o->stack : 16;
     eo.persistent = (o->flags & CR_OPT_PERSISTENT) != 0;
     if (o->sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "sort_key %u", o->sort_key);
     eo.sort_key = o->sort_key;
@@ -1343,11 +1350,33 @@ extern "C" cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint
             }
         }
     }
+    // second stage: the stack depth in shared memory for the winner of the first
+    rep.best_stack = opts->stack ? opts->stack : 16;
+    for (uint32_t stack : {8u, 16u, 32u}) {
+        cr_batch_opts o = *opts;
+        o.group_w = rep.best_group_w;
+        o.group_h = rep.best_group_h;
+        o.k = rep.best_k;
+        o.interleave = rep.best_interleave;
+        o.block = rep.best_block;
+        o.stack = stack;
+        o.flags &= ~(uint32_t)CR_BATCH_GRAPH;
+        double ms = 0;
+        cr_status st = time_one(o, ms);
+        if (st != CR_OK) return st;
+        rep.n_candidates++;
+        rep.worst_ms = std::max(rep.worst_ms, ms);
+        if (ms < rep.best_ms) {
+            rep.best_ms = ms;
+            rep.best_stack = stack;
+        }
+    }
     opts->group_w = rep.best_group_w;
     opts->group_h = rep.best_group_h;
     opts->k = rep.best_k;
     opts->interleave = rep.best_interleave;
     opts->block = rep.best_block;
+    opts->stack = rep.best_stack;
     if (report) *report = rep;
     return CR_OK;
 }

@@ -171,6 +171,7 @@ struct TraceArgs {
     bool speculative = false; // parked-leaf speculative traversal (BVH2)
     bool packet = false;      // warp-packet traversal (BVH2)
     bool any_hit = false;     // stop at the first hit before tmax (visibility)
+    uint32_t stack = 16;      // BVH2 stack entries per thread in shared memory (8, 16, 32)
     bool two_phase = false;   // budgeted traversal, compaction of unfinished rays, resume (BVH2)
     PhaseBuffers phase;
     bool bvh8 = false;
@@ -304,6 +305,7 @@ struct Plan {
 };
 struct ExecOpts {
     int block = 128;
+    uint32_t stack = 16; // BVH2 traversal stack entries per thread in shared memory
     bool persistent = false, count = false, speculative = false;
     bool packet_primary = false, packet_secondary = false; // warp-packet traversal per ray kind
     uint32_t sort_key = 0; // reordering key of CR_MORTON_SORT (cr_sort_key)

@@ -18,7 +18,9 @@ namespace cr {
 namespace {
 
 // kAny: visibility only; the traversal ends at the first triangle hit before the ray's tmax.
-template <bool kCount, bool kAny = false>
+// kSmemS: stack entries per thread kept in shared memory (8, 16 or 32; deeper ones go to a
+// local array), a launch-shape knob of the autotuner.
+template <bool kCount, bool kAny = false, int kSmemS = kSmemStack>
 __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
                                                unsigned long long& n_tri) {
@@ -29,7 +31,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
     int lstack_all[kStackTotal];
     (void)sstack;
 #else
-    int lstack[kStackTotal - kSmemStack];
+    int lstack[kStackTotal - kSmemS];
     const int stride = blockDim.x;
 #endif
     int sp = 0;
@@ -73,7 +75,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
 #define CR_TRACE_MAXNREG 48 // caps registers so 10 blocks of 128 threads stay resident per SM
 #endif
 
-template <bool kCount, bool kAny = false>
+template <bool kCount, bool kAny = false, int kSmemS = kSmemStack>
 __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene,
                              const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                              const int32_t* __restrict__ queue, const uint32_t* __restrict__ queue_count,
@@ -89,7 +91,8 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __res
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
         if (rd.w >= 0.0f)
-            h = trace_bvh2_one<kCount, kAny>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+            h = trace_bvh2_one<kCount, kAny, kSmemS>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node,
+                                                     n_tri);
         hit[slot] = h;
     }
     if (kCount) {
@@ -116,6 +119,7 @@ constexpr int kSaveStack = 24;
 __device__ __forceinline__ int2 trace_bvh2_resumable(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                      float4 ro, float4 rd, uint32_t* sstack, uint32_t budget,
                                                      TraceState* st, bool resume, bool& suspended) {
+    constexpr int kSmemS = kSmemStack;
     const RayPre r = prep_ray(ro, rd);
     const int skip = __float_as_int(ro.w);
     Best best{rd.w, -1, 0x7fffffff};
@@ -290,6 +294,7 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2_packet(
         }
         return;
     }
+    constexpr int kSmemS = kSmemStack;
 #if CR_TRACE_LOCAL_STACK
     int lstack_all[kStackTotal];
 #else
@@ -711,12 +716,24 @@ void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
             a.refill == 0 ? 8u : (a.refill > 32u ? 32u : a.refill));
     } else {
         const uint32_t grid = (a.n_max + block - 1) / block;
-        if (a.counters)
+        if (a.counters) {
             k_trace_bvh2<true><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
                                                           a.queue_count, a.n_max, a.hit, a.counters);
-        else
+        } else if (a.stack == 8) {
+            k_trace_bvh2<false, false, 8><<<grid, block, (size_t)8 * block * 4, st>>>(
+                a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue, a.queue_count, a.n_max, a.hit, nullptr);
+        } else if (a.stack == 32) {
+            const size_t smem32 = (size_t)32 * block * 4;
+            if (smem32 > 48 * 1024) // 512-thread blocks need the opt-in beyond 48 KB
+                cudaFuncSetAttribute(k_trace_bvh2<false, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem32);
+            k_trace_bvh2<false, false, 32><<<grid, block, smem32, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d,
+                                                                        a.queue, a.queue_count, a.n_max, a.hit,
+                                                                        nullptr);
+        } else {
             k_trace_bvh2<false><<<grid, block, smem, st>>>(a.scenes, a.slot_scene, a.ray_o, a.ray_d, a.queue,
                                                            a.queue_count, a.n_max, a.hit, nullptr);
+        }
     }
     lc.n++;
 }

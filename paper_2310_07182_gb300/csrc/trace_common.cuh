@@ -183,17 +183,18 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
 #define STACK_PUSH(v) (lstack_all[sp++] = (v))
 #define STACK_POP(v) ((v) = lstack_all[--sp])
 #else
-// first kSmemStack entries in shared memory, the rest in a local array
+// first kSmemS entries (the user's constant: kSmemStack, or a template parameter) in shared
+// memory, the rest in a local array
 #define STACK_PUSH(v)                                                                \
     do {                                                                             \
-        if (sp < kSmemStack) sstack[sp * stride] = (uint32_t)(v);                    \
-        else if (sp < kStackTotal) lstack[sp - kSmemStack] = (v);                   \
+        if (sp < kSmemS) sstack[sp * stride] = (uint32_t)(v);                        \
+        else if (sp < kStackTotal) lstack[sp - kSmemS] = (v);                        \
         sp = sp < kStackTotal ? sp + 1 : sp; /* the builder keeps depth < kStackTotal */ \
     } while (0)
 #define STACK_POP(v)                                                                 \
     do {                                                                             \
         --sp;                                                                        \
-        (v) = sp < kSmemStack ? (int)sstack[sp * stride] : lstack[sp - kSmemStack]; \
+        (v) = sp < kSmemS ? (int)sstack[sp * stride] : lstack[sp - kSmemS];          \
     } while (0)
 #endif
 

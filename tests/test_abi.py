@@ -35,8 +35,33 @@ def test_exports_every_declared_symbol(cr):
 def test_struct_layouts(cr):
     assert C.sizeof(cr.cr_material) == 32
     assert C.sizeof(cr.cr_camera) == 48
-    assert C.sizeof(cr.cr_render_opts) == 64
+    assert C.sizeof(cr.cr_render_opts) == 72
     assert C.sizeof(cr.cr_debug) == 48
+
+
+def test_struct_layouts_match_the_header(cr, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that a C compiler
+    gives the declaration in include/cr.h."""
+    import subprocess
+    names = ["cr_material", "cr_env", "cr_scene_info", "cr_camera", "cr_stats", "cr_debug", "cr_job",
+             "cr_batch_opts", "cr_tune_report", "cr_server_opts", "cr_job_stats", "cr_server_stats",
+             "cr_render_opts", "cr_bvh_report"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cr.h"', "int main(void) {"]
+    expect = []
+    for n in names:
+        cls = getattr(cr, n)
+        lines.append(f'printf("%zu\\n", sizeof({n}));')
+        expect.append(C.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({n}, {f}));')
+            expect.append(getattr(cls, f).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
 
 
 def test_version(cr):

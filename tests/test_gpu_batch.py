@@ -79,11 +79,12 @@ def test_device_bytes_and_autotune(cr, world):
     three = cr.cr_batch_device_bytes(jobs, opts)
     assert 64 * 64 * 100 < one < three
     rep = cr.cr_batch_autotune(jobs, opts, allow_contiguous=True)
-    assert rep["n_candidates"] == 54
+    assert rep["n_candidates"] == 54 + 3  # then the stack depth of the winner
     assert rep["best_ms"] <= rep["default_ms"] <= rep["worst_ms"]
     assert opts.group_w in (4, 8, 16) and opts.k <= opts.group_w * opts.group_h // 4
-    assert (opts.group_w, opts.k, opts.interleave, opts.block) == (rep["best_group_w"], rep["best_k"],
-                                                                    rep["best_interleave"], rep["best_block"])
+    assert (opts.group_w, opts.k, opts.interleave, opts.block, opts.stack) == (
+        rep["best_group_w"], rep["best_k"], rep["best_interleave"], rep["best_block"], rep["best_stack"])
+    assert opts.stack in (8, 16, 32)
 
 
 def test_batch_rejects_bad_jobs(cr, world):

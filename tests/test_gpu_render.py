@@ -239,3 +239,18 @@ def test_two_phase_trace_identical_on_deep_scene(cr):
         a, _ = S.render(spp=2, max_bounces=3, tile=(8, 8), k=8, seed=5, mode=mode)
         b, _ = S.render(spp=2, max_bounces=3, tile=(8, 8), k=8, seed=5, mode=mode, flags=cr.CR_OPT_TWO_PHASE)
         assert torch.equal(a, b), mode
+
+
+def test_stack_depth_option_changes_nothing_but_speed(cr):
+    """The shared-memory share of the traversal stack (8, 16, 32 entries per thread; the
+    rest in local memory) is a launch-shape knob: images are bit-identical, bad values are
+    rejected."""
+    sc = scenes.interior(width=96, height=64)
+    S = cr.Scene(sc)
+    kw = dict(spp=2, max_bounces=3, tile=(8, 8), k=8, seed=3)
+    a, _ = S.render(**kw)
+    for stack, block in ((8, 128), (32, 128), (32, 512), (8, 64)):
+        b, _ = S.render(stack=stack, block=block, **kw)
+        assert torch.equal(a, b), (stack, block)
+    with pytest.raises(cr.CrError):
+        S.render(stack=12, **kw)
