@@ -154,9 +154,10 @@ def profile_traffic():
 
 
 # ---------------------------------------------------------------------------------------
-def cpu_oracle_rate(sc, target_s: float, max_tiles=None, mode="direction_reuse", frame_base=0):
+def cpu_oracle_rate(sc, target_s: float, max_tiles=None, mode="direction_reuse", frame_base=0, bounces=None):
     """Time the CPU oracle (all host cores) on a bounded sample of the workload's tiles.
     Returns (secondary Mrays/s, threads, sample description, seconds)."""
+    B = BOUNCES if bounces is None else bounces
     import oracle
     O = oracle.Scene(sc)
     cam = sc.camera
@@ -167,7 +168,7 @@ def cpu_oracle_rate(sc, target_s: float, max_tiles=None, mode="direction_reuse",
     # probe, then size the sample for ~target_s
     n = min(ntiles, 8 * threads)
     t0 = time.perf_counter()
-    r = oracle.render(O, cam, spp=SPP, max_bounces=BOUNCES, mode=mode, tile=TILE, k=K, seed=0,
+    r = oracle.render(O, cam, spp=SPP, max_bounces=B, mode=mode, tile=TILE, k=K, seed=0,
                       frame_base=frame_base, tiles=(0, n), threads=threads)
     dt = time.perf_counter() - t0
     n2 = int(min(ntiles, max(n, n * target_s / max(dt, 1e-3))))
@@ -175,11 +176,11 @@ def cpu_oracle_rate(sc, target_s: float, max_tiles=None, mode="direction_reuse",
         n2 = min(n2, max_tiles)
     start = (ntiles - n2) // 2  # a band through the middle of the image
     t0 = time.perf_counter()
-    r = oracle.render(O, cam, spp=SPP, max_bounces=BOUNCES, mode=mode, tile=TILE, k=K, seed=0,
+    r = oracle.render(O, cam, spp=SPP, max_bounces=B, mode=mode, tile=TILE, k=K, seed=0,
                       frame_base=frame_base, tiles=(start, start + n2), threads=threads)
     dt = time.perf_counter() - t0
     sec = int(r["counters"][1])
-    sample = f"{n2} of {ntiles} 8x8 tiles ({100.0 * n2 / ntiles:.1f}% of the image), {mode}, 1 spp, 2 bounces"
+    sample = f"{n2} of {ntiles} 8x8 tiles ({100.0 * n2 / ntiles:.1f}% of the image), {mode}, 1 spp, {B} bounces"
     return sec / dt / 1e6, r["threads"], sample, dt
 
 
@@ -407,6 +408,14 @@ def run_ours(args):
         v, thr, sample, dt = cpu_oracle_rate(sc, args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                                 "sample": sample}
+        if not args.core_only:
+            # the oracle on the other workloads (context): tiny in full, the interior at 1 spp
+            # on a sample of tiles (a 16-spp render takes 16 times as long)
+            extra = {}
+            for name, scn, b in (("tiny", scenes.tiny(), 1), ("interior", scenes.interior(), 4)):
+                v2, thr2, sample2, dt2 = cpu_oracle_rate(scn, 4.0, bounces=b)
+                extra[name] = {"mrays": round(v2, 4), "cores": thr2, "sample": sample2, "seconds": round(dt2, 2)}
+            line["cpu_baseline"]["other_workloads"] = extra
     print(json.dumps(line), flush=True)
 
 
