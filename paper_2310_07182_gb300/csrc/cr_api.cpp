@@ -721,7 +721,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         ev.begin(stream, times ? &times->raygen : &dummy);
         launch_raygen(P, b, stream, lc);
         ev.end();
-        ta.queue = nullptr;
+        ta.queue = primary_pixel_order() ? b.ray_queue : nullptr; // written by raygen: pixel order per tile
         ta.queue_count = nullptr;
         ta.n_max = n_slots;
         ta.counters = nullptr;

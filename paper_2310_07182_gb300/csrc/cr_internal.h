@@ -234,6 +234,8 @@ void launch_shadow_rays(const SceneDev* scenes, const uint16_t* slot_scene, cons
                         cudaStream_t st, LaunchCount& lc);
 
 void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
+// raygen leaves the primary trace's visiting order (row-major pixels per tile) in the ray queue
+bool primary_pixel_order();
 void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,
                   LaunchCount& lc);
 // Group-granular compaction of the slots processed by the last shade into ray and group queues.

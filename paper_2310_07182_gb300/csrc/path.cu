@@ -72,9 +72,12 @@ __device__ __forceinline__ uint32_t job_of_tile(const JobDev* jobs, uint32_t n_j
 // One block covers blockDim / m whole tiles: every thread finds sigma of its pixel, the
 // inverse map is built in shared memory, then thread j writes slot j of its tile so the
 // slot arrays are written contiguously.
+// primary_queue (optional): entry tile * m + i = the slot of the tile's i-th pixel, so that the
+// primary trace can visit a tile's pixels in row-major order (compact pixel blocks per warp).
 __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __restrict__ slot_job,
                          uint16_t* __restrict__ slot_scene, float4* __restrict__ ray_o, float4* __restrict__ ray_d,
-                         float4* __restrict__ beta, float4* __restrict__ radiance, uint8_t* __restrict__ alive) {
+                         float4* __restrict__ beta, float4* __restrict__ radiance, uint8_t* __restrict__ alive,
+                         int32_t* __restrict__ primary_queue) {
     extern __shared__ uint16_t inv[];
     const uint32_t m = p.m;
     const uint32_t tiles_per_block = blockDim.x / m;
@@ -86,7 +89,9 @@ __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __re
         jid = job_of_tile(p.jobs, p.n_jobs, tile);
         const JobDev& J = p.jobs[jid];
         const Lcg L = tile_lcg(J.seed, tile - J.tile_base, J.frame, m, J.interleave);
-        inv[tl * m + sigma_of(L, j, m, J.interleave)] = (uint16_t)j;
+        const uint32_t s = sigma_of(L, j, m, J.interleave);
+        inv[tl * m + s] = (uint16_t)j;
+        if (primary_queue) primary_queue[tile * m + j] = (int32_t)(tile * m + s);
     }
     __syncthreads();
     if (!in) return;
@@ -1106,10 +1111,17 @@ void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCou
     const uint32_t block = p.m > 256 ? p.m : 256;
     const uint32_t tiles_per_block = block / p.m;
     const uint32_t grid = (p.n_tiles + tiles_per_block - 1) / tiles_per_block;
+#ifndef CR_PRIMARY_PIXEL_ORDER
+#define CR_PRIMARY_PIXEL_ORDER 1
+#endif
+    // the ray queue is free until the first compaction: it carries the primary trace's order
     k_raygen<<<grid, block, block * sizeof(uint16_t), st>>>(p, b.pixel, b.slot_job, b.slot_scene, b.ray_o, b.ray_d,
-                                                             b.beta, b.radiance, b.alive);
+                                                             b.beta, b.radiance, b.alive,
+                                                             CR_PRIMARY_PIXEL_ORDER ? b.ray_queue : nullptr);
     lc.n++;
 }
+
+bool primary_pixel_order() { return CR_PRIMARY_PIXEL_ORDER != 0; }
 
 void launch_groups(const CamBasis& cam, uint32_t tile_w, uint32_t tile_h, uint32_t interleave, uint64_t seed,
                    uint32_t frame, uint32_t* slot_of_pixel, cudaStream_t st, LaunchCount& lc) {
