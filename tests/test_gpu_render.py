@@ -254,3 +254,31 @@ def test_stack_depth_option_changes_nothing_but_speed(cr):
         assert torch.equal(a, b), (stack, block)
     with pytest.raises(cr.CrError):
         S.render(stack=12, **kw)
+
+
+@pytest.mark.parametrize("bvh", ["bvh2", "bvh8q"])
+def test_interior_full_size_sampled_tiles(cr, orc, bvh):
+    """The dense-interior precision workload at full size (1280x720, 512,014 triangles,
+    16 spp, 4 bounces, direction reuse, 8x8 tiles, K = 8): the GPU renders the whole frame
+    with either BVH layout, the oracle renders three bands of 48 tiles."""
+    sc = scenes.interior()
+    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
+    O = orc.Scene(sc)
+    cam = sc.camera
+    img, st = S.render(spp=16, max_bounces=4, mode="direction_reuse", tile=(8, 8), k=8, seed=0, stats=True,
+                       bvh=cr.CR_BVH2 if bvh == "bvh2" else cr.CR_BVH8Q)
+    img = img.cpu().numpy()
+    ntx, nty = cam.width // 8, cam.height // 8
+    nt = ntx * nty
+    for b0 in (0, nt // 2, nt - 48):
+        ref = orc.render(O, cam, spp=16, max_bounces=4, mode="direction_reuse", tile=(8, 8), k=8, seed=0,
+                         tiles=(b0, b0 + 48))
+        mask = np.zeros((cam.height, cam.width), bool)
+        for t in range(b0, b0 + 48):
+            tx, ty = t % ntx, t // ntx
+            mask[ty * 8:(ty + 1) * 8, tx * 8:(tx + 1) * 8] = True
+        ok = mask & (ref["taint"] == 0)
+        # over 16 samples and 4 bounces a fragile ray anywhere in a group taints its pixels
+        assert ok.sum() >= 0.6 * mask.sum()
+        good, excess, nbad = radiance_close(img, ref["rgb"], ok)
+        assert good, f"band {b0}: {nbad} pixels off by {excess}"
