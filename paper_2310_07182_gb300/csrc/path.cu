@@ -427,7 +427,14 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs
 // K <= 32: a group is a K-lane segment of a warp; votes by ballot, the donor's direction by
 // shuffle, the hybrid sum by an xor butterfly (which equals the pairwise tree sum in every
 // lane because float addition is commutative).
+#ifndef CR_SHADE_MIN_BLOCKS
+#define CR_SHADE_MIN_BLOCKS 8 // registers sized for 8 resident 128-thread blocks per SM (0: no cap)
+#endif
+#if CR_SHADE_MIN_BLOCKS
+__global__ void __launch_bounds__(128, CR_SHADE_MIN_BLOCKS) k_shade_warp(ShadeArgs a, PassArgs p) {
+#else
 __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
+#endif
     const uint32_t K = p.k;
     const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
