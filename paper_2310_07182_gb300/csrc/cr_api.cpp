@@ -177,6 +177,9 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     } catch (const std::bad_alloc&) {
         return fail(CR_ERR_OOM, "cr_scene_create: host allocation during BVH build");
     }
+    if (b2.depth >= kBvh2StackCapacity)
+        return fail(CR_ERR_STACK_OVERFLOW, "cr_scene_create: BVH2 depth %u needs a deeper traversal stack (%u)", b2.depth,
+                    kBvh2StackCapacity);
     // triangles in leaf order: v0 | original index, v1 | material, v2 | 0
     std::vector<float> tris(12 * (size_t)n_tri);
     for (uint32_t i = 0; i < n_tri; ++i) {

@@ -17,6 +17,10 @@
 namespace cr {
 namespace {
 
+#ifndef CR_TRACE_BOOL_HIT
+#define CR_TRACE_BOOL_HIT 1 // box tests return a hit flag; the cull distance is updated per leaf
+#endif
+
 // kAny: visibility only; the traversal ends at the first triangle hit before the ray's tmax.
 // kSmemS: stack entries per thread kept in shared memory (8, 16 or 32; deeper ones go to a
 // local array), a launch-shape knob of the autotuner.
@@ -36,6 +40,9 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
 #endif
     int sp = 0;
     int node = 0;
+#if CR_TRACE_BOOL_HIT
+    float tcull = __fmul_rn(best.t, kCullWiden); // changes only after a leaf
+#endif
     while (true) {
         while (node >= 0) {
             if (kCount) ++n_node;
@@ -43,11 +50,18 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
             const float4 n1 = __ldg(&nodes[4 * node + 1]);
             const float4 n2 = __ldg(&nodes[4 * node + 2]);
             const float4 n3 = __ldg(&nodes[4 * node + 3]);
+#if CR_TRACE_BOOL_HIT
+            float t0, t1;
+            const bool h0 = box_hit_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull, t0);
+            const bool h1 = box_hit_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull, t1);
+            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+#else
             const float tcull = __fmul_rn(best.t, kCullWiden);
             const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
             const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
             const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
             const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
+#endif
             if (h0 && h1) {
                 const bool first0 = t0 <= t1;
                 const int near = first0 ? c0 : c1, far = first0 ? c1 : c0;
@@ -65,6 +79,9 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
         const uint32_t code = (uint32_t)(~node);
         test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, n_tri);
         if (kAny && best.leaf >= 0) break;
+#if CR_TRACE_BOOL_HIT
+        tcull = __fmul_rn(best.t, kCullWiden);
+#endif
         if (sp == 0) break;
         STACK_POP(node);
     }

@@ -16,7 +16,7 @@ namespace cr {
 namespace {
 
 constexpr int kSmemStack = 16;  // entries per thread in shared memory
-constexpr int kStackTotal = 64; // >= BVH depth (the builder keeps depth <= 64)
+constexpr int kStackTotal = (int)kBvh2StackCapacity; // > BVH2 depth (checked at scene creation)
 constexpr float kFarWiden = 1.0f + 0x1.0p-21f;
 constexpr float kCullWiden = 1.0f + 0x1.0p-16f;
 
@@ -124,6 +124,17 @@ __device__ __forceinline__ float box_entry_fma(const RayPre& r, float lox, float
     return (tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull) ? tn : INFINITY;
 }
 
+// box_entry_fma as a hit flag plus the entry distance (no +inf sentinel to test again).
+__device__ __forceinline__ bool box_hit_fma(const RayPre& r, float lox, float hix, float loy, float hiy, float loz,
+                                            float hiz, float tcull, float& tn) {
+    const float tx0 = fmaf(lox, r.ix, r.lox), tx1 = fmaf(hix, r.ix, r.hix);
+    const float ty0 = fmaf(loy, r.iy, r.loy), ty1 = fmaf(hiy, r.iy, r.hiy);
+    const float tz0 = fmaf(loz, r.iz, r.loz), tz1 = fmaf(hiz, r.iz, r.hiz);
+    tn = max3f(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = min3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fmaxf(tz0, tz1));
+    return tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull;
+}
+
 // Watertight ray/triangle test (Woop, Benthin, Wald 2013) without the double-precision
 // fallback: edge functions of exactly zero count as inside, so shared edges are covered.
 __device__ __forceinline__ bool tri_test(const RayPre& r, float4 a4, float4 b4, float4 c4, float& t_out) {
@@ -185,11 +196,12 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
 #else
 // first kSmemS entries (the user's constant: kSmemStack, or a template parameter) in shared
 // memory, the rest in a local array
+// (a push never exceeds the tree depth, which scene creation checks is below kStackTotal)
 #define STACK_PUSH(v)                                                                \
     do {                                                                             \
         if (sp < kSmemS) sstack[sp * stride] = (uint32_t)(v);                        \
-        else if (sp < kStackTotal) lstack[sp - kSmemS] = (v);                        \
-        sp = sp < kStackTotal ? sp + 1 : sp; /* the builder keeps depth < kStackTotal */ \
+        else lstack[sp - kSmemS] = (v);                                              \
+        ++sp;                                                                        \
     } while (0)
 #define STACK_POP(v)                                                                 \
     do {                                                                             \
