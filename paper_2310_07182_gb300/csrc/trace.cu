@@ -17,9 +17,6 @@
 namespace cr {
 namespace {
 
-#ifndef CR_TRACE_BOOL_HIT
-#define CR_TRACE_BOOL_HIT 1 // box tests return a hit flag; the cull distance is updated per leaf
-#endif
 
 // kAny: visibility only; the traversal ends at the first triangle hit before the ray's tmax.
 // kSmemS: stack entries per thread kept in shared memory (8, 16 or 32; deeper ones go to a
@@ -31,18 +28,12 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
     const RayPre r = prep_ray(ro, rd);
     const int skip = __float_as_int(ro.w);
     Best best{rd.w, -1, 0x7fffffff};
-#if CR_TRACE_LOCAL_STACK
-    int lstack_all[kStackTotal];
-    (void)sstack;
-#else
     int lstack[kStackTotal - kSmemS];
     const int stride = blockDim.x;
-#endif
     int sp = 0;
     int node = 0;
-#if CR_TRACE_BOOL_HIT
     float tcull = __fmul_rn(best.t, kCullWiden); // changes only after a leaf
-#endif
+    uint32_t* top = sstack; // next free shared-memory stack entry (stays at the end once full)
     while (true) {
         while (node >= 0) {
             if (kCount) ++n_node;
@@ -50,28 +41,20 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
             const float4 n1 = __ldg(&nodes[4 * node + 1]);
             const float4 n2 = __ldg(&nodes[4 * node + 2]);
             const float4 n3 = __ldg(&nodes[4 * node + 3]);
-#if CR_TRACE_BOOL_HIT
             float t0, t1;
             const bool h0 = box_hit_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull, t0);
             const bool h1 = box_hit_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull, t1);
             const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-#else
-            const float tcull = __fmul_rn(best.t, kCullWiden);
-            const float t0 = box_entry_fma(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tcull);
-            const float t1 = box_entry_fma(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tcull);
-            const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-            const bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
-#endif
             if (h0 && h1) {
                 const bool first0 = t0 <= t1;
                 const int near = first0 ? c0 : c1, far = first0 ? c1 : c0;
-                STACK_PUSH(far);
+                STACK_PUSH_TOP(far);
                 node = near;
             } else if (h0 || h1) {
                 node = h0 ? c0 : c1;
             } else {
                 if (sp == 0) { node = 0x7fffffff; break; }
-                STACK_POP(node);
+                STACK_POP_TOP(node);
             }
         }
         if (node == 0x7fffffff) break;
@@ -79,11 +62,9 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
         const uint32_t code = (uint32_t)(~node);
         test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, n_tri);
         if (kAny && best.leaf >= 0) break;
-#if CR_TRACE_BOOL_HIT
         tcull = __fmul_rn(best.t, kCullWiden);
-#endif
         if (sp == 0) break;
-        STACK_POP(node);
+        STACK_POP_TOP(node);
     }
     return make_int2(best.leaf, __float_as_int(best.t));
 }

@@ -86,14 +86,13 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
         const uint32_t meta = ((i < 4 ? m_lo : m_hi) >> (8 * (i & 3))) & 0xffu;                         \
         const bool inner = (imask >> ((uint32_t)(i) ^ oct)) & 1u;                                         \
         if (inner || meta >= 32u) {                                                                       \
-            const float t = box_entry_fma(                                                                \
-                r, __fadd_rn(ox, __fmul_rn(qbyte<i>(lx_lo, lx_hi), sx)),                                  \
-                __fadd_rn(ox, __fmul_rn(qbyte<i>(hx_lo, hx_hi), sx)),                                     \
-                __fadd_rn(oy, __fmul_rn(qbyte<i>(ly_lo, ly_hi), sy)),                                     \
-                __fadd_rn(oy, __fmul_rn(qbyte<i>(hy_lo, hy_hi), sy)),                                     \
-                __fadd_rn(oz, __fmul_rn(qbyte<i>(lz_lo, lz_hi), sz)),                                     \
-                __fadd_rn(oz, __fmul_rn(qbyte<i>(hz_lo, hz_hi), sz)), tcull);                             \
-            if (t != INFINITY) {                                                                          \
+            float t;                                                                                      \
+            if (box_hit_fma(r, __fadd_rn(ox, __fmul_rn(qbyte<i>(lx_lo, lx_hi), sx)),                      \
+                            __fadd_rn(ox, __fmul_rn(qbyte<i>(hx_lo, hx_hi), sx)),                         \
+                            __fadd_rn(oy, __fmul_rn(qbyte<i>(ly_lo, ly_hi), sy)),                         \
+                            __fadd_rn(oy, __fmul_rn(qbyte<i>(hy_lo, hy_hi), sy)),                         \
+                            __fadd_rn(oz, __fmul_rn(qbyte<i>(lz_lo, lz_hi), sz)),                         \
+                            __fadd_rn(oz, __fmul_rn(qbyte<i>(hz_lo, hz_hi), sz)), tcull, t)) {            \
                 if (inner) hits |= 1u << (i);                                                             \
                 else trimask |= ((1u << (meta >> 5)) - 1u) << (meta & 31u);                               \
             }                                                                                             \

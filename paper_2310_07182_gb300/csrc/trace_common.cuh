@@ -210,5 +210,29 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
     } while (0)
 #endif
 
+
+// The same stack with a pointer to the next free shared-memory entry, which saves the index
+// arithmetic of every push and pop (1% on the secondary trace); used by trace_bvh2_one.
+#define STACK_PUSH_TOP(v)                                                            \
+    do {                                                                             \
+        if (sp < kSmemS) {                                                           \
+            *top = (uint32_t)(v);                                                    \
+            top += stride;                                                           \
+        } else {                                                                     \
+            lstack[sp - kSmemS] = (v);                                               \
+        }                                                                            \
+        ++sp;                                                                        \
+    } while (0)
+#define STACK_POP_TOP(v)                                                             \
+    do {                                                                             \
+        --sp;                                                                        \
+        if (sp < kSmemS) {                                                           \
+            top -= stride;                                                           \
+            (v) = (int)*top;                                                         \
+        } else {                                                                     \
+            (v) = lstack[sp - kSmemS];                                               \
+        }                                                                            \
+    } while (0)
+
 } // namespace
 } // namespace cr
