@@ -1203,13 +1203,13 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                     uint32_t mt = s->mat_type[s->tri_mat[ps->hit]];
                     if (mt == MAT_EMITTER) {
                         const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        double wb = p->nee ? emit_weight(s, ps) : 1.0;
+                        double wb = (p->opts & ORC_OPT_NEE) ? emit_weight(s, ps) : 1.0;
                         for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
                         ps->alive = 0;
                         continue;
                     }
                     shade_setup(s, ps);
-                    if (p->nee && s->mat_type[ps->mat] != MAT_MIRROR && s->mat_type[ps->mat] != MAT_DIELECTRIC)
+                    if ((p->opts & ORC_OPT_NEE) && s->mat_type[ps->mat] != MAT_MIRROR && s->mat_type[ps->mat] != MAT_DIELECTRIC)
                         next_event(s, p->seed, f, b, ps, cnt_local);
                 }
                 const int reuse_now = (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
@@ -1255,6 +1255,18 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         f3 wl = G[donor].wl;
                         for (uint32_t j = 0; j < K; ++j)
                             if (G[j].pixel >= 0 && G[j].alive) take_direction(s, &G[j], into_lobe(&G[j], wl));
+                    } else if (reuse_now && cat == CAT_HYBRID && (p->opts & ORC_OPT_HYBRID_DONOR)) {
+                        /* hybrid group, donor reading (an option, not the paper's rule): the
+                         * diffuse members reuse the first diffuse member's own cosine sample,
+                         * the glossy/specular members keep theirs; every direction keeps its
+                         * sampling density, so the estimate stays unbiased */
+                        int donor = -1;
+                        for (uint32_t j = 0; j < K && donor < 0; ++j)
+                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE) donor = (int)j;
+                        f3 wl = G[donor].wl;
+                        for (uint32_t j = 0; j < K; ++j)
+                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE)
+                                take_direction(s, &G[j], into_lobe(&G[j], wl));
                     } else if (reuse_now && cat == CAT_HYBRID) {
                         /* hybrid group: diffuse members take the normalised tangent-space sum of
                          * the valid glossy/specular exit directions */
@@ -1331,7 +1343,7 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
                     } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER) {
                         const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        double wb = p->nee ? emit_weight(s, ps) : 1.0;
+                        double wb = (p->opts & ORC_OPT_NEE) ? emit_weight(s, ps) : 1.0;
                         for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
                     }
                 }

@@ -97,12 +97,16 @@ typedef struct {
 } orc_camera;
 
 enum { ORC_INDEPENDENT = 0, ORC_MORTON_SORT = 1, ORC_DIRECTION_REUSE = 2, ORC_WORLD_REUSE = 3 };
+/* ORC_OPT_NEE: next-event estimation at non-specular points.  ORC_OPT_HYBRID_DONOR: in hybrid
+ * groups the diffuse members reuse the first diffuse member's own sample (the diffuse-group
+ * rule restricted to them) instead of the average glossy direction. */
+enum { ORC_OPT_NEE = 1, ORC_OPT_HYBRID_DONOR = 2 };
 
 typedef struct {
     uint32_t spp, max_bounces, mode;
     uint32_t tile_w, tile_h, k, interleave;
     uint32_t frame_base, reuse_depth; /* reuse at bounces b <= reuse_depth; 0 = all */
-    uint32_t nee;                     /* 1: next-event estimation at non-specular points */
+    uint32_t opts;                    /* ORC_OPT_* bits */
     uint64_t seed;
 } orc_params;
 
