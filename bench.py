@@ -432,11 +432,12 @@ def _timed_renders(cr, S, cam, out, stream, steps, warmup, frame0=0, **kw):
     bounces = kw.pop("bounces", BOUNCES)
     mode = kw.pop("mode", "direction_reuse")
     tile = kw.pop("tile", TILE)
+    extra_flags = kw.pop("extra_flags", 0)
     ms = tr = 0.0
     sec = 0
     for i in range(warmup + steps):
         st = cr.cr_stats()
-        o = cr.make_opts(frame_base=frame0 + i, flags=cr.CR_OPT_STATS, stream=stream, stats=st, **kw)
+        o = cr.make_opts(frame_base=frame0 + i, flags=cr.CR_OPT_STATS | extra_flags, stream=stream, stats=st, **kw)
         cr.cr_render_ex(S.handle, cam, spp, bounces, mode, tile[0], tile[1], out, o)
         if i >= warmup:
             d = st.as_dict()
@@ -595,26 +596,28 @@ def quality_leg(cr, S, cam, stream, results):
     torch.cuda.synchronize()
     out = {"reference_spp": n_ref, "budgets_s": [0.1, 0.5, 2.0], "modes": {}}
     peak = float(ref.max())
-    variants = (("direction_reuse", "direction_reuse", 0), ("independent", "independent", 0),
-                ("morton_sort", "morton_sort", 0), ("direction_reuse_bounce1_only", "direction_reuse", 1))
-    for name, mode, depth in variants:
+    variants = (("direction_reuse", "direction_reuse", 0, 0), ("independent", "independent", 0, 0),
+                ("morton_sort", "morton_sort", 0, 0), ("direction_reuse_bounce1_only", "direction_reuse", 1, 0),
+                ("direction_reuse_hybrid_donor", "direction_reuse", 0, cr.CR_OPT_HYBRID_DONOR))
+    for name, mode, depth, vflags in variants:
         ms_spp = results.get(name, {}).get("ms_per_step")
         if ms_spp is None:
-            ms, _, _ = _timed_renders(cr, S, cam, img, stream, 3, 1, mode=mode, k=K, reuse_depth=depth)
+            ms, _, _ = _timed_renders(cr, S, cam, img, stream, 3, 1, mode=mode, k=K, reuse_depth=depth,
+                                      extra_flags=vflags)
             ms_spp = ms / 3
         row = {"ms_per_spp": round(ms_spp, 4), "mse": [], "spp": []}
         for T in out["budgets_s"]:
             spp = max(1, int(T * 1e3 / ms_spp))
-            o = cr.make_opts(k=K, frame_base=0, stream=stream, reuse_depth=depth)
+            o = cr.make_opts(k=K, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags)
             cr.cr_render_ex(S.handle, cam, spp, BOUNCES, mode, TILE[0], TILE[1], img, o)
             row["mse"].append(float(((img - ref) ** 2).mean()))
             row["spp"].append(spp)
-        o = cr.make_opts(k=K, frame_base=0, stream=stream, reuse_depth=depth)
+        o = cr.make_opts(k=K, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags)
         cr.cr_render_ex(S.handle, cam, 128, BOUNCES, mode, TILE[0], TILE[1], img, o)
         mse128 = float(((img - ref) ** 2).mean())
         row["psnr_128spp_db"] = round(10 * math.log10(peak * peak / mse128), 3)
-        # bias estimate: the 4096-spp mean of the mode against the reference
-        o = cr.make_opts(k=K, frame_base=2_000_000, stream=stream, reuse_depth=depth)
+        # bias estimate: the 1024-spp mean of the mode against the reference
+        o = cr.make_opts(k=K, frame_base=2_000_000, stream=stream, reuse_depth=depth, flags=vflags)
         cr.cr_render_ex(S.handle, cam, 1024, BOUNCES, mode, TILE[0], TILE[1], img, o)
         row["mse_1024spp"] = float(((img - ref) ** 2).mean())
         out["modes"][name] = row

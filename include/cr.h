@@ -167,7 +167,8 @@ enum {
     CR_OPT_PACKET_SECONDARY = 64u, /* warp-packet traversal of secondary rays (BVH2) */
     CR_OPT_TWO_PHASE = 128u, /* secondary rays: 32-visit budget, compact the unfinished, resume (BVH2) */
     CR_OPT_NEE = 256u,     /* cr_render: next-event estimation (the job flag CR_JOB_NEE) */
-    CR_OPT_ANY_HIT = 512u  /* cr_trace_rays: visibility only (any hit before tmax, see there) */
+    CR_OPT_ANY_HIT = 512u, /* cr_trace_rays: visibility only (any hit before tmax, see there) */
+    CR_OPT_HYBRID_DONOR = 1024u /* cr_render: the job flag CR_JOB_HYBRID_DONOR */
 };
 
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):
@@ -256,7 +257,12 @@ typedef struct {
  * reflection density; mirrors and camera rays keep full emission).  Where the continuation
  * direction has density p_b (independent sampling, diffuse and glossy groups) the mean
  * equals plain path tracing's. */
-enum { CR_JOB_NEE = 1u };
+/* CR_JOB_HYBRID_DONOR: an unbiased alternative to the paper's hybrid-group rule (Sec. 3.2
+ * gives diffuse members the average glossy direction, which is not cosine-distributed, so
+ * the image is biased).  With the flag, the diffuse members of a hybrid group reuse the
+ * first diffuse member's own cosine sample (the diffuse-group rule among them) and the
+ * glossy / specular members keep their own samples: every direction keeps its density. */
+enum { CR_JOB_NEE = 1u, CR_JOB_HYBRID_DONOR = 2u };
 
 enum { CR_BATCH_GRAPH = 1u /* capture the launch sequence once, replay it on every run */ };
 

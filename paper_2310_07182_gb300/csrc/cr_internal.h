@@ -116,6 +116,7 @@ struct JobDev {
     float inv_spp;
     uint32_t world_mask;  // bit b: world-space direct reuse (Sec. 3.1 ablation) at bounce b
     uint32_t nee;         // 1: next-event estimation
+    uint32_t hybrid_donor; // 1: hybrid groups reuse the first diffuse member's sample
 };
 
 // Launch-uniform description of a pass.

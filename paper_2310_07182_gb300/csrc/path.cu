@@ -164,6 +164,7 @@ struct Member {
     bool reuse;      // the job reuses directions at this bounce
     bool world;      // the job reuses world-space directions at this bounce (Sec. 3.1 ablation)
     bool nee;        // the job uses next-event estimation
+    bool hdonor;     // hybrid groups: diffuse members reuse the first diffuse member's sample
     uint32_t scene;  // scene table index
     uint32_t type;   // material type of the shading point
     float rough;     // its roughness (the IOR of a dielectric)
@@ -454,6 +455,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     mb.reuse = false;
     mb.world = false;
     mb.nee = false;
+    mb.hdonor = false;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
     mb.front = true;
@@ -468,6 +470,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
             mb.nee = Jp->nee != 0;
+            mb.hdonor = Jp->hybrid_donor != 0;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
@@ -510,7 +513,9 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
                     take_dir(mb, wd);
                 } else if (cat == kCatHybrid) {
                     const float l2 = dot3(s, s);
-                    if (l2 > 0.0f) {
+                    if (mb.hdonor) {
+                        take_dir(mb, wd); // donor option: the first diffuse member's own sample
+                    } else if (l2 > 0.0f) {
                         const float l = fq(l2);
                         take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
                     } else {
@@ -563,6 +568,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     mb.reuse = false;
     mb.world = false;
     mb.nee = false;
+    mb.hdonor = false;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
     mb.front = true;
@@ -577,6 +583,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
             mb.nee = Jp->nee != 0;
+            mb.hdonor = Jp->hybrid_donor != 0;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
@@ -643,7 +650,9 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
                 } else if (cat == kCatHybrid) {
                     const V3 s = v3(s_sum[0][gbase], s_sum[1][gbase], s_sum[2][gbase]);
                     const float l2 = dot3(s, s);
-                    if (l2 > 0.0f) {
+                    if (mb.hdonor) {
+                        take_dir(mb, wd); // donor option: the first diffuse member's own sample
+                    } else if (l2 > 0.0f) {
                         const float l = fq(l2);
                         take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
                     } else {

@@ -282,3 +282,24 @@ def test_interior_full_size_sampled_tiles(cr, orc, bvh):
         assert ok.sum() >= 0.6 * mask.sum()
         good, excess, nbad = radiance_close(img, ref["rgb"], ok)
         assert good, f"band {b0}: {nbad} pixels off by {excess}"
+
+
+@pytest.mark.parametrize("tile,k", [((8, 4), 8), ((8, 8), 64)])
+def test_hybrid_donor_option_bit_exact(cr, orc, tile, k):
+    """The unbiased hybrid-group option: per-bounce directions bit-exact against the oracle,
+    in the warp (K <= 32) and block (K > 32) shade kernels."""
+    sc, S, O = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
+    B = 3
+    dbg, bufs = cr.debug_buffers(sc.camera.width, sc.camera.height, B)
+    img, _ = S.render(spp=1, max_bounces=B, mode="direction_reuse", tile=tile, k=k, seed=5, debug=dbg,
+                      hybrid_donor=True)
+    ref = orc.render(O, sc.camera, spp=1, max_bounces=B, mode="direction_reuse", tile=tile, k=k, seed=5,
+                     debug=True, hybrid_donor=True)
+    ok = (ref["taint"] == 0).reshape(-1)
+    g = {key: v.cpu().numpy() for key, v in bufs.items()}
+    for b in range(B):
+        alive = (ref["dbg_flags"][b] & 1).astype(bool) & ok
+        assert np.array_equal(g["cat"][b][alive], ref["dbg_cat"][b][alive])
+        assert np.array_equal(g["local"][b][alive].view(np.uint32), ref["dbg_local"][b][alive].view(np.uint32))
+    assert (ref["dbg_cat"][0][ok] == 3).sum() > 50
+    _check(img.cpu().numpy(), ref, max_taint=0.1 if k == 64 else 0.05)
