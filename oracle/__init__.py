@@ -247,7 +247,7 @@ def trace(scene: Scene, rays, skip=None, use_bvh=True):
 
 def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=None,
            interleave=True, seed=0, frame_base=0, reuse_depth=0, debug=False, threads=None,
-           tiles=None, accum=None, nee=False, hybrid_donor=False):
+           tiles=None, accum=None, nee=False, hybrid_donor=False, nee_shared=False):
     """Run the oracle path tracer.  Returns a dict with ``rgb`` (mean radiance, float64 h x w x 3),
     ``taint`` (h x w uint8), ``counters`` and, with debug=True (spp 1), per-bounce arrays.
     ``tiles`` = (begin, end) restricts the work to a tile range (other pixels stay 0).
@@ -255,7 +255,8 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
     rendering resumed at ``frame_base``).  ``nee`` adds next-event estimation (one light
     sample and shadow ray per non-specular shading point).  ``hybrid_donor`` makes the diffuse
     members of hybrid groups reuse the first diffuse member's own sample instead of the
-    average glossy direction (an unbiased option)."""
+    average glossy direction (an unbiased option).  ``nee_shared`` (with ``nee``) makes the
+    members of a group join one light point."""
     W, H = tile
     K = W * H if k is None else k
     w, h = cam.width, cam.height
@@ -275,7 +276,8 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
     camc = _Camera((C.c_float * 3)(*cam.pos), (C.c_float * 3)(*cam.look_at), (C.c_float * 3)(*cam.up),
                    cam.vfov_deg, w, h)
     par = _Params(spp, B, MODES[mode] if isinstance(mode, str) else mode, W, H, K, int(interleave),
-                  frame_base, reuse_depth, (1 if nee else 0) | (2 if hybrid_donor else 0), seed)
+                  frame_base, reuse_depth, (1 if nee else 0) | (2 if hybrid_donor else 0) | (4 if nee_shared else 0),
+                  seed)
     nthreads = threads or max(1, min(os.cpu_count() or 1, t1 - t0))
     bounds = np.linspace(t0, t1, nthreads + 1).astype(int)
     counters = np.zeros((nthreads, 5), dtype=np.uint64)

@@ -1083,9 +1083,9 @@ static void spawn_point(const pstate* ps, double side, double* out) {
  * (emit_weight).  Both weights use the same two densities, so the estimate keeps the
  * mean of plain path tracing whenever the continuation direction has density p_b. */
 static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32_t bounce, pstate* ps,
-                       uint64_t* counters) {
+                       int32_t light_pixel, uint64_t* counters) {
     uint32_t h[4];
-    philox_seed(seed, (uint32_t)ps->pixel, frame, bounce, TAG_LITE, h);
+    philox_seed(seed, (uint32_t)light_pixel, frame, bounce, TAG_LITE, h);
     float pl[3];
     int32_t lt = orc_light_sample(s, to_unit(h[0]), to_unit(h[1]), to_unit(h[2]), pl);
     if (lt < 0) return;
@@ -1209,8 +1209,26 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         continue;
                     }
                     shade_setup(s, ps);
-                    if ((p->opts & ORC_OPT_NEE) && s->mat_type[ps->mat] != MAT_MIRROR && s->mat_type[ps->mat] != MAT_DIELECTRIC)
-                        next_event(s, p->seed, f, b, ps, cnt_local);
+                }
+                /* next-event estimation at the shading points; with shared light samples
+                 * every member of a group joins the point drawn from the stream of the
+                 * group's first alive member (each member's point is still distributed by
+                 * area, so every pixel's estimate keeps its mean) */
+                if (p->opts & ORC_OPT_NEE) {
+                    for (uint32_t g = 0; g < m / K; ++g) {
+                        pstate* G = &slot[g * K];
+                        int32_t owner = -1;
+                        for (uint32_t j = 0; j < K && owner < 0; ++j)
+                            if (G[j].pixel >= 0 && G[j].alive) owner = G[j].pixel;
+                        for (uint32_t j = 0; j < K; ++j) {
+                            pstate* ps = &G[j];
+                            if (ps->pixel < 0 || !ps->alive) continue;
+                            uint32_t ty = s->mat_type[ps->mat];
+                            if (ty == MAT_MIRROR || ty == MAT_DIELECTRIC) continue;
+                            next_event(s, p->seed, f, b, ps, (p->opts & ORC_OPT_NEE_SHARED) ? owner : ps->pixel,
+                                       cnt_local);
+                        }
+                    }
                 }
                 const int reuse_now = (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
                                       (p->reuse_depth == 0 || b <= p->reuse_depth);

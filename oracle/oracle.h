@@ -100,7 +100,9 @@ enum { ORC_INDEPENDENT = 0, ORC_MORTON_SORT = 1, ORC_DIRECTION_REUSE = 2, ORC_WO
 /* ORC_OPT_NEE: next-event estimation at non-specular points.  ORC_OPT_HYBRID_DONOR: in hybrid
  * groups the diffuse members reuse the first diffuse member's own sample (the diffuse-group
  * rule restricted to them) instead of the average glossy direction. */
-enum { ORC_OPT_NEE = 1, ORC_OPT_HYBRID_DONOR = 2 };
+enum { ORC_OPT_NEE = 1, ORC_OPT_HYBRID_DONOR = 2, ORC_OPT_NEE_SHARED = 4 };
+/* ORC_OPT_NEE_SHARED (with ORC_OPT_NEE): the members of a group join one light point, drawn
+ * from the stream of the group's first alive member. */
 
 typedef struct {
     uint32_t spp, max_bounces, mode;

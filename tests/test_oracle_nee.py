@@ -254,3 +254,25 @@ def test_nee_lowers_variance_under_a_small_light(orc):
         res[nee] = (imgs.mean(), imgs.var(axis=0, ddof=1).mean())
     assert abs(res[True][0] - res[False][0]) < 0.05 * res[False][0], res
     assert res[True][1] < 0.5 * res[False][1], res
+
+
+def test_shared_light_samples(orc):
+    """Shared light samples (every member of a group joins the light point of the group's
+    first alive member): with one pixel per group they are each pixel's own samples, bit
+    for bit; with groups of 16 the image keeps the mean of plain path tracing."""
+    sc = scenes.emitter_box(floor=scenes.MAT_GGX, floor_params=(0.9, 0.7, 0.4, 0.3), n_spheres=12, seed=4,
+                            width=24, height=24)
+    S = orc.Scene(sc)
+    kw = dict(mode="independent", max_bounces=3, tile=(4, 4), spp=4, seed=3)
+    own = orc.render(S, sc.camera, k=1, nee=True, **kw)
+    shared = orc.render(S, sc.camera, k=1, nee=True, nee_shared=True, **kw)
+    assert np.array_equal(own["rgb"], shared["rgb"])
+    a, b = [], []
+    for f in range(24):
+        kw = dict(mode="independent", max_bounces=3, tile=(4, 4), k=16, spp=4, seed=5, frame_base=100 * f)
+        a.append(orc.render(S, sc.camera, **kw)["rgb"].mean())
+        b.append(orc.render(S, sc.camera, nee=True, nee_shared=True, **kw)["rgb"].mean())
+    a, b = np.array(a), np.array(b)
+    se = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
+    assert abs(a.mean() - b.mean()) < 4 * se, (a.mean(), b.mean(), se)
+    assert abs(a.mean() - b.mean()) < 0.02 * a.mean()
