@@ -490,20 +490,23 @@ def nee_leg(cr, scenes, rank, args):
     B = 4
 
     def render(spp, mode, nee, frame, stats=None):
+        # nee: 0 off, 1 one light sample per pixel, 2 one light point per reuse group
         o = cr.make_opts(k=K, frame_base=frame, stream=stream, stats=stats,
-                         flags=(cr.CR_OPT_NEE if nee else 0) | (cr.CR_OPT_STATS if stats is not None else 0))
+                         flags=(cr.CR_OPT_NEE if nee else 0) | (cr.CR_OPT_NEE_SHARED if nee == 2 else 0) |
+                         (cr.CR_OPT_STATS if stats is not None else 0))
         cr.cr_render_ex(S.handle, cam, spp, B, mode, TILE[0], TILE[1], img, o)
 
     n_ref = 2048
     for c in range(0, n_ref, 256):
-        render(256, "independent", True, 5_000_000 + c)
+        render(256, "independent", 1, 5_000_000 + c)
         ref += img
     ref /= n_ref // 256
     torch.cuda.synchronize()
     out = {"workload": "interior 640x360, 512,014 tris, 4 bounces, 8x8 K=8", "reference_spp": n_ref,
            "budgets_s": [0.05, 0.25], "modes": {}}
-    for mode in ("direction_reuse", "independent"):
-        for nee in (False, True):
+    for mode, nee in (("direction_reuse", 0), ("direction_reuse", 1), ("direction_reuse", 2), ("independent", 0),
+                      ("independent", 1)):
+        if True:
             ms = sec = shadow = tsh = 0.0
             for i in range(5):
                 st = cr.cr_stats()
@@ -524,7 +527,7 @@ def nee_leg(cr, scenes, rank, args):
                 render(spp, mode, nee, 0)
                 row["mse"].append(float(((img - ref) ** 2).mean()))
                 row["spp"].append(spp)
-            out["modes"][mode + ("+nee" if nee else "")] = row
+            out["modes"][mode + ("", "+nee", "+nee_shared")[nee]] = row
     S.close()
     return out
 

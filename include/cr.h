@@ -168,7 +168,8 @@ enum {
     CR_OPT_TWO_PHASE = 128u, /* secondary rays: 32-visit budget, compact the unfinished, resume (BVH2) */
     CR_OPT_NEE = 256u,     /* cr_render: next-event estimation (the job flag CR_JOB_NEE) */
     CR_OPT_ANY_HIT = 512u, /* cr_trace_rays: visibility only (any hit before tmax, see there) */
-    CR_OPT_HYBRID_DONOR = 1024u /* cr_render: the job flag CR_JOB_HYBRID_DONOR */
+    CR_OPT_HYBRID_DONOR = 1024u, /* cr_render: the job flag CR_JOB_HYBRID_DONOR */
+    CR_OPT_NEE_SHARED = 2048u    /* cr_render: the job flag CR_JOB_NEE_SHARED */
 };
 
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):
@@ -262,7 +263,11 @@ typedef struct {
  * the image is biased).  With the flag, the diffuse members of a hybrid group reuse the
  * first diffuse member's own cosine sample (the diffuse-group rule among them) and the
  * glossy / specular members keep their own samples: every direction keeps its density. */
-enum { CR_JOB_NEE = 1u, CR_JOB_HYBRID_DONOR = 2u };
+/* CR_JOB_NEE_SHARED (with CR_JOB_NEE): the members of a reuse group join one light point,
+ * drawn from the "LITE" stream of the group's first alive member, so the group's shadow rays
+ * converge (coherent traversal); each pixel's light point is still distributed by area, so
+ * the estimate keeps its mean (an extension in the spirit of Sec. 3.2, not in the paper). */
+enum { CR_JOB_NEE = 1u, CR_JOB_HYBRID_DONOR = 2u, CR_JOB_NEE_SHARED = 4u };
 
 enum { CR_BATCH_GRAPH = 1u /* capture the launch sequence once, replay it on every run */ };
 

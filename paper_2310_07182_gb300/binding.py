@@ -27,8 +27,8 @@ CR_BVH2, CR_BVH8Q = 1, 2
 CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE, CR_WORLD_REUSE = 0, 1, 2, 3
 CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIVE = 1, 2, 4, 8, 16
 CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY, CR_OPT_TWO_PHASE = 32, 64, 128
-CR_OPT_NEE, CR_OPT_ANY_HIT, CR_OPT_HYBRID_DONOR = 256, 512, 1024
-CR_JOB_NEE, CR_JOB_HYBRID_DONOR = 1, 2
+CR_OPT_NEE, CR_OPT_ANY_HIT, CR_OPT_HYBRID_DONOR, CR_OPT_NEE_SHARED = 256, 512, 1024, 2048
+CR_JOB_NEE, CR_JOB_HYBRID_DONOR, CR_JOB_NEE_SHARED = 1, 2, 4
 MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE,
          "world_reuse": CR_WORLD_REUSE}
 
@@ -305,9 +305,10 @@ CR_BATCH_GRAPH = 1
 
 
 def make_job(scene_handle, cam, out, spp=1, max_bounces=1, mode="direction_reuse", reuse_depth=0, seed=0,
-             frame_base=0, nee=False, hybrid_donor=False) -> cr_job:
+             frame_base=0, nee=False, hybrid_donor=False, nee_shared=False) -> cr_job:
     j = cr_job()
-    j.flags = (CR_JOB_NEE if nee else 0) | (CR_JOB_HYBRID_DONOR if hybrid_donor else 0)
+    j.flags = ((CR_JOB_NEE if nee else 0) | (CR_JOB_HYBRID_DONOR if hybrid_donor else 0)
+               | (CR_JOB_NEE_SHARED if nee_shared else 0))
     j.scene = scene_handle
     j.camera = make_camera(cam)
     j.spp, j.max_bounces, j.mode, j.reuse_depth = spp, max_bounces, MODES.get(mode, mode), reuse_depth
@@ -459,7 +460,7 @@ class Scene:
 
     def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
                seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
-               debug=None, stream=None, sort_key=0, nee=False, stack=0, hybrid_donor=False):
+               debug=None, stream=None, sort_key=0, nee=False, stack=0, hybrid_donor=False, nee_shared=False):
         """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
         CUDA tensor by default).  Returns (out, stats dict or None)."""
         import torch
@@ -469,7 +470,7 @@ class Scene:
         st = cr_stats() if stats else None
         o = make_opts(k=k, interleave=interleave, seed=seed, frame_base=frame_base, reuse_depth=reuse_depth, bvh=bvh,
                       block=block, flags=flags | (CR_OPT_STATS if stats else 0) | (CR_OPT_NEE if nee else 0)
-                      | (CR_OPT_HYBRID_DONOR if hybrid_donor else 0),
+                      | (CR_OPT_HYBRID_DONOR if hybrid_donor else 0) | (CR_OPT_NEE_SHARED if nee_shared else 0),
                       stream=stream, stats=st, debug=debug, sort_key=sort_key, stack=stack)
         cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
         return out, (st.as_dict() if st is not None else None)

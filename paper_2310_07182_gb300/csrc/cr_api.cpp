@@ -559,7 +559,7 @@ cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h) {
     if (j.max_bounces == 0 || j.max_bounces > 16)
         return fail(CR_ERR_INVALID_ARG, "max_bounces %u not in [1, 16]", j.max_bounces);
     if (j.mode > CR_WORLD_REUSE) return fail(CR_ERR_INVALID_ARG, "unknown mode %u", j.mode);
-    if (j.flags & ~(uint32_t)(CR_JOB_NEE | CR_JOB_HYBRID_DONOR))
+    if (j.flags & ~(uint32_t)(CR_JOB_NEE | CR_JOB_HYBRID_DONOR | CR_JOB_NEE_SHARED))
         return fail(CR_ERR_INVALID_ARG, "unknown job flags 0x%x", j.flags);
     (void)tile_w;
     (void)tile_h;
@@ -634,7 +634,7 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
                     if (j.mode == CR_WORLD_REUSE) d.world_mask |= 1u << b;
                 }
             d.interleave = po.interleave ? 1u : 0u;
-            d.nee = (j.flags & CR_JOB_NEE) ? 1u : 0u;
+            d.nee = (j.flags & CR_JOB_NEE) ? ((j.flags & CR_JOB_NEE_SHARED) ? 2u : 1u) : 0u;
             d.hybrid_donor = (j.flags & CR_JOB_HYBRID_DONOR) ? 1u : 0u;
             if (d.nee) plan.nee = true;
             d.seed = j.seed;
@@ -828,7 +828,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     job.reuse_depth = o.reuse_depth;
     job.seed = o.seed;
     job.frame_base = o.frame_base;
-    job.flags = ((o.flags & CR_OPT_NEE) ? CR_JOB_NEE : 0u) | ((o.flags & CR_OPT_HYBRID_DONOR) ? CR_JOB_HYBRID_DONOR : 0u);
+    job.flags = ((o.flags & CR_OPT_NEE) ? CR_JOB_NEE : 0u) | ((o.flags & CR_OPT_HYBRID_DONOR) ? CR_JOB_HYBRID_DONOR : 0u) |
+                ((o.flags & CR_OPT_NEE_SHARED) ? CR_JOB_NEE_SHARED : 0u);
     job.out_rgb = out_dev ? out_rgb : s->d_out;
     PlanOpts po;
     po.tile_w = group_w;

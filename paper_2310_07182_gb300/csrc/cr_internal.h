@@ -115,7 +115,7 @@ struct JobDev {
     float* out;           // device output (w*h*3 floats) of the job
     float inv_spp;
     uint32_t world_mask;  // bit b: world-space direct reuse (Sec. 3.1 ablation) at bounce b
-    uint32_t nee;         // 1: next-event estimation
+    uint32_t nee;         // 1: next-event estimation, 2: with light points shared per group
     uint32_t hybrid_donor; // 1: hybrid groups reuse the first diffuse member's sample
 };
 

@@ -164,6 +164,7 @@ struct Member {
     bool reuse;      // the job reuses directions at this bounce
     bool world;      // the job reuses world-space directions at this bounce (Sec. 3.1 ablation)
     bool nee;        // the job uses next-event estimation
+    bool nee_shared; // ... with one light point per group
     bool hdonor;     // hybrid groups: diffuse members reuse the first diffuse member's sample
     uint32_t scene;  // scene table index
     uint32_t type;   // material type of the shading point
@@ -330,12 +331,12 @@ __device__ __forceinline__ float own_pdf(const Member& mb, V3 wl) {
 // (p_l = r^2 / (cos_l A), p_b = own_pdf).  Every active position writes its slot's record
 // (w < 0: no shadow ray).
 __device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p, int slot, const Member& mb,
-                                           const float4 bt) {
+                                           const float4 bt, int light_pix) {
     float4 dr = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     if (mb.alive && mb.nee && mb.type != kMatMirror && mb.type != kMatDielectric) {
         const SceneDev& sc = a.scenes[mb.scene];
         if (sc.n_lights > 0) {
-            const uint4 r = philox_seed(mb.seed, (uint32_t)mb.pix, mb.frame, p.bounce, kTagLight);
+            const uint4 r = philox_seed(mb.seed, (uint32_t)light_pix, mb.frame, p.bounce, kTagLight);
             const float u0 = unit24(r.x), u1 = unit24(r.y), u2 = unit24(r.z);
             // the first emitter whose running area exceeds u0 * A (the last if none)
             const float x = fm(u0, sc.light_total);
@@ -455,6 +456,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     mb.reuse = false;
     mb.world = false;
     mb.nee = false;
+    mb.nee_shared = false;
     mb.hdonor = false;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
@@ -470,6 +472,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
             mb.nee = Jp->nee != 0;
+            mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
@@ -484,13 +487,20 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             L = make_float3(r4.x, r4.y, r4.z);
             setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
         }
-        if (a.shadow_d) next_event(a, p, slot, mb, bt);
     }
     int cat = kCatEmpty;
+    int light_pix = mb.pix;
     {
         const uint32_t lane = threadIdx.x & 31u;
         const uint32_t seg = lane & ~(K - 1u);
         const uint32_t segmask = K == 32u ? 0xffffffffu : (((1u << K) - 1u) << seg);
+        // shared light samples: the group's first alive member owns the light stream
+        if (__any_sync(0xffffffffu, mb.nee_shared)) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, mb.alive) & segmask;
+            const int owner = bal ? __ffs(bal) - 1 : (int)lane;
+            const int opix = __shfl_sync(0xffffffffu, mb.pix, owner);
+            if (mb.nee_shared) light_pix = opix;
+        }
         const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse) & segmask;
         const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy) & segmask;
         cat = bd && bg ? kCatHybrid : (bd ? kCatDiffuse : (bg ? kCatGlossy : kCatEmpty));
@@ -538,6 +548,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             }
         }
     }
+    if (active && a.shadow_d) next_event(a, p, slot, mb, bt, light_pix);
     if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
 }
 
@@ -549,6 +560,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     __shared__ float s_own[3][256];
     __shared__ float s_sum[3][256];
     __shared__ float s_world[4][256]; // world-space direction and validity (Sec. 3.1 ablation)
+    __shared__ int s_pix[256];        // members' pixels (owner of a shared light sample)
     const uint32_t K = p.k;
     const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,6 +580,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     mb.reuse = false;
     mb.world = false;
     mb.nee = false;
+    mb.nee_shared = false;
     mb.hdonor = false;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
@@ -583,6 +596,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
             mb.nee = Jp->nee != 0;
+            mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
@@ -597,11 +611,12 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             L = make_float3(r4.x, r4.y, r4.z);
             setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
         }
-        if (a.shadow_d) next_event(a, p, slot, mb, bt);
     }
     int cat = kCatEmpty;
+    int light_pix = mb.pix;
     {
         const uint32_t t = threadIdx.x, w = t >> 5;
+        s_pix[t] = mb.pix;
         const uint32_t bd = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsDiffuse);
         const uint32_t bg = __ballot_sync(0xffffffffu, mb.alive && mb.cls == kClsGlossy);
         const uint32_t ba = __ballot_sync(0xffffffffu, mb.alive);
@@ -670,7 +685,14 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
                 take_dir_world(mb, v3(dot3(wdw, mb.t), dot3(wdw, mb.b), dot3(wdw, mb.n)));
             }
         }
+        if (mb.nee_shared) { // the group's first alive member owns the light stream
+            int owner = -1;
+            for (uint32_t ww = gbase >> 5; ww < (gbase + K) >> 5 && owner < 0; ++ww)
+                if (s_ba[ww]) owner = (int)(ww * 32u + __ffs(s_ba[ww]) - 1);
+            if (owner >= 0) light_pix = s_pix[owner];
+        }
     }
+    if (active && a.shadow_d) next_event(a, p, slot, mb, bt, light_pix);
     if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
 }
 

@@ -135,3 +135,17 @@ def test_nee_bvh8_batch_and_server_identical(cr, orc):
     finally:
         cr.cr_server_destroy(srv)
     assert torch.equal(out, a)
+
+
+@pytest.mark.parametrize("tile,k", [((8, 8), 8), ((8, 8), 64)])
+def test_shared_light_samples_match_oracle(cr, orc, tile, k):
+    """One light point per group (drawn from the first alive member's stream): warp and
+    block shade kernels against the oracle."""
+    sc, S, O = _trio(cr, orc, "emitter_box", floor=scenes.MAT_GGX, floor_params=(0.9, 0.7, 0.4, 0.3),
+                     n_spheres=12, seed=4, width=48, height=40)
+    kw = dict(spp=2, max_bounces=3, mode="direction_reuse", tile=tile, k=k, seed=7)
+    img, st = S.render(stats=True, nee=True, nee_shared=True, **kw)
+    ref = orc.render(O, sc.camera, nee=True, nee_shared=True, **kw)
+    _check(img.cpu().numpy(), ref, max_taint=0.06 if k == 64 else 0.03)
+    own, _ = S.render(nee=True, **kw)
+    assert not torch.equal(img, own)
