@@ -340,6 +340,12 @@ def run_ours(args):
     if not args.core_only:
         extras["precision_interior"] = precision_leg(cr, scenes, rank, world, args)
         extras["table3_sweep"] = sweep_leg(cr, S, cam, out, stream, rank, world)
+        # the paper sweeps an indoor scene (Sibenik): the same sweep on the interior, 4 bounces
+        si = scenes.interior()
+        Si = cr.Scene(si)
+        outi = torch.empty((si.camera.height, si.camera.width, 3), dtype=torch.float32, device="cuda")
+        extras["table3_sweep_interior"] = sweep_leg(cr, Si, si.camera, outi, stream, rank, world, bounces=4)
+        Si.close()
         extras["next_event_estimation"] = nee_leg(cr, scenes, rank, args)
         extras["transmission"] = transmission_leg(cr, scenes, rank, args)
         extras["quality"] = quality_leg(cr, S, cam, stream, results)
@@ -565,15 +571,16 @@ def transmission_leg(cr, scenes, rank, args):
     return res
 
 
-def sweep_leg(cr, S, cam, out, stream, rank, world):
-    """Tile (W,H) x group size K sweep on the landscape (the analogue of Table 3): secondary
-    trace-only Mrays/s of direction reuse and its ratio to independent sampling."""
-    ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 3, 1, mode="independent", k=K)
+def sweep_leg(cr, S, cam, out, stream, rank, world, bounces=None):
+    """Tile (W,H) x group size K sweep (the analogue of Table 3): secondary trace-only
+    Mrays/s of direction reuse and its ratio to independent sampling."""
+    kb = {} if bounces is None else {"bounces": bounces}
+    ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 3, 1, mode="independent", k=K, **kb)
     base = sec / tr / 1e3
     rows = {}
     for tile in ((8, 8), (16, 8), (16, 16), (32, 8)):
         for k in (8, 16, 32, 64):
-            ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 3, 1, tile=tile, k=k)
+            ms, tr, sec = _timed_renders(cr, S, cam, out, stream, 3, 1, tile=tile, k=k, **kb)
             v = sec / tr / 1e3
             rows[f"{tile[0]}x{tile[1]}_K{k}"] = {"trace_only_mrays": round(v, 1), "ratio": round(v / base, 3),
                                                  "whole_step_mrays": round(sec / ms / 1e3, 1)}
