@@ -136,9 +136,9 @@ def kernel_source_sha(files=("trace.cu", "trace_common.cuh")) -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per launch of the trace kernel from the committed ncu summary, or None if
-    the kernel source changed since that capture."""
+def profile_traffic(key="dram_bytes_per_launch_full"):
+    """A figure of the trace kernel's committed ncu summary (DRAM bytes per launch by
+    default), or None if the kernel source changed since that capture."""
     summ = os.path.join(ROOT, "profiles", "k_trace_bvh2.landscape.txt")
     if not os.path.exists(summ):
         return None
@@ -148,9 +148,9 @@ def profile_traffic():
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 kv[k.strip()] = v.strip()
-    if kv.get("source_sha") != kernel_source_sha() or "dram_bytes_per_launch_full" not in kv:
+    if kv.get("source_sha") != kernel_source_sha() or key not in kv:
         return None
-    return float(kv["dram_bytes_per_launch_full"])
+    return float(kv[key])
 
 
 # ---------------------------------------------------------------------------------------
@@ -394,6 +394,7 @@ def run_ours(args):
                          "frac": round(achieved / peak, 4), "bytes_per_ray": round(bytes_per_ray, 1),
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                          "note": "algorithmic node+triangle bytes; mostly served by L1/L2 (DRAM traffic is the 'traffic' key)"},
+        "roofline_issue": issue_roof(R, clk),
         "roofline_l2": {"achieved": round(achieved, 1), "peak": round(l2_gbs, 1), "unit": "GB/s",
                         "frac": round(achieved / l2_gbs, 4),
                         "peak_source": "cr_measure_l2_read: read-only kernel over an L2-resident 48 MB buffer, CUDA events",
@@ -423,6 +424,20 @@ def run_ours(args):
                 extra[name] = {"mrays": round(v2, 4), "cores": thr2, "sample": sample2, "seconds": round(dt2, 2)}
             line["cpu_baseline"]["other_workloads"] = extra
     print(json.dumps(line), flush=True)
+
+
+def issue_roof(R, clk):
+    """The trace kernel's binding roof (ncu: issue-bound): warp instructions per second
+    against one instruction per scheduler per clock (152 SMs x 4 schedulers).  Instructions
+    per ray come from the committed ncu capture; the ray rate is this run's."""
+    ipr = profile_traffic("warp_instructions_per_ray")
+    peak = 152 * 4 * clk * 1e6 / 1e12
+    if ipr is None:
+        return {"achieved": None, "peak": round(peak, 3), "unit": "T warp instructions/s", "frac": None}
+    ach = ipr * R["trace_mrays"] * 1e6 / 1e12
+    return {"achieved": round(ach, 3), "peak": round(peak, 3), "unit": "T warp instructions/s",
+            "frac": round(ach / peak, 4), "instructions_per_ray": ipr,
+            "source": "warp instructions per ray from profiles/k_trace_bvh2.landscape.txt x this run's trace-only rate"}
 
 
 def l2_read_bandwidth(cr, mb=48, reps=100):
