@@ -259,12 +259,16 @@ def run_ours(args):
             flags |= variant_flags[v]
         return m, key or "two_point", flags
 
-    def step(mode, frame, flags=0):
+    def step(mode, frame, flags=0, stats_flag=None):
+        # timed steps record events only around the trace launches (the whole-step time, the
+        # trace-only rate and the roofline's launch time); the full per-stage breakdown comes
+        # from separate untimed steps, because ~30 event records per step cost ~3% of it
         m, key, vflags = parse(mode)
         flags |= vflags
         st = cr.cr_stats()
         o = cr.make_opts(k=K, interleave=True, seed=0, frame_base=frame,
-                         flags=cr.CR_OPT_STATS | flags, stream=stream, stats=st, sort_key=key)
+                         flags=(cr.CR_OPT_STATS_TRACES if stats_flag is None else stats_flag) | flags, stream=stream,
+                         stats=st, sort_key=key)
         cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m, TILE[0], TILE[1], out, o)
         return st.as_dict()
 
@@ -308,9 +312,6 @@ def run_ours(args):
             ms_per_step=ms_max / args.steps,
             trace_mrays=sec / (sum(x["ms_trace_secondary"] for x in stats) / 1e3) / 1e6,
             ms_trace_secondary=sum(x["ms_trace_secondary"] for x in stats) / args.steps,
-            ms_shade=sum(x["ms_shade"] for x in stats) / args.steps,
-            ms_compact=sum(x["ms_compact"] for x in stats) / args.steps,
-            ms_sort=sum(x["ms_sort"] for x in stats) / args.steps,
             ms_trace_primary=sum(x["ms_trace_primary"] for x in stats) / args.steps,
             secondary_rays_per_step=sec / args.steps,
             launches_per_step=stats[0]["kernel_launches"],
@@ -319,6 +320,11 @@ def run_ours(args):
         c = counts[mode]
         results[mode]["nodes_per_ray"] = c["node_visits"] / max(c["secondary_rays"], 1)
         results[mode]["tris_per_ray"] = c["tri_tests"] / max(c["secondary_rays"], 1)
+        # stage breakdown (untimed steps with events between all stages)
+        br = [step(mode, frame_of(rank, args.warmup + args.steps + i, world), stats_flag=cr.CR_OPT_STATS)
+              for i in range(3)]
+        for key in ("ms_shade", "ms_compact", "ms_sort", "ms_raygen", "ms_accum"):
+            results[mode][key] = sum(x[key] for x in br) / len(br)
 
     # end to end through the C ABI into pinned host memory
     host = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, pin_memory=True)
@@ -401,7 +407,8 @@ def run_ours(args):
                         "note": "algorithmic node+triangle bytes against the L2 roof; < 1 means L1 hits carry the rest"},
         "trace_only_mrays": round(R["trace_mrays"], 2),
         "stages_ms": {k: round(R[k], 4) for k in ("ms_trace_primary", "ms_trace_secondary", "ms_shade", "ms_compact",
-                                                   "ms_sort")},
+                                                   "ms_sort", "ms_raygen", "ms_accum")},
+        "stages_note": "trace stages from the timed steps; the others from 3 untimed steps with events between all stages",
         "comparators": {m: {"mrays": round(results[m]["mrays"], 2), "trace_only_mrays": round(results[m]["trace_mrays"], 2),
                             "ms_per_step": round(results[m]["ms_per_step"], 4),
                             "nodes_per_ray": round(results[m]["nodes_per_ray"], 2),
@@ -458,7 +465,8 @@ def _timed_renders(cr, S, cam, out, stream, steps, warmup, frame0=0, **kw):
     sec = 0
     for i in range(warmup + steps):
         st = cr.cr_stats()
-        o = cr.make_opts(frame_base=frame0 + i, flags=cr.CR_OPT_STATS | extra_flags, stream=stream, stats=st, **kw)
+        o = cr.make_opts(frame_base=frame0 + i, flags=cr.CR_OPT_STATS_TRACES | extra_flags, stream=stream, stats=st,
+                         **kw)
         cr.cr_render_ex(S.handle, cam, spp, bounces, mode, tile[0], tile[1], out, o)
         if i >= warmup:
             d = st.as_dict()
@@ -514,7 +522,7 @@ def nee_leg(cr, scenes, rank, args):
         # nee: 0 off, 1 one light sample per pixel, 2 one light point per reuse group
         o = cr.make_opts(k=K, frame_base=frame, stream=stream, stats=stats,
                          flags=(cr.CR_OPT_NEE if nee else 0) | (cr.CR_OPT_NEE_SHARED if nee == 2 else 0) |
-                         (cr.CR_OPT_STATS if stats is not None else 0))
+                         (cr.CR_OPT_STATS_TRACES if stats is not None else 0))
         cr.cr_render_ex(S.handle, cam, spp, B, mode, TILE[0], TILE[1], img, o)
 
     n_ref = 2048

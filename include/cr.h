@@ -169,7 +169,9 @@ enum {
     CR_OPT_NEE = 256u,     /* cr_render: next-event estimation (the job flag CR_JOB_NEE) */
     CR_OPT_ANY_HIT = 512u, /* cr_trace_rays: visibility only (any hit before tmax, see there) */
     CR_OPT_HYBRID_DONOR = 1024u, /* cr_render: the job flag CR_JOB_HYBRID_DONOR */
-    CR_OPT_NEE_SHARED = 2048u    /* cr_render: the job flag CR_JOB_NEE_SHARED */
+    CR_OPT_NEE_SHARED = 2048u,   /* cr_render: the job flag CR_JOB_NEE_SHARED */
+    CR_OPT_STATS_TRACES = 4096u  /* like CR_OPT_STATS but events only around the trace launches
+                                    (less event traffic in the step; other stage times read 0) */
 };
 
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):

@@ -402,8 +402,9 @@ struct StageEvents {
         pool.push_back(e);
         return e;
     }
-    void begin(cudaStream_t s, double* acc) {
-        if (!on) return;
+    bool traces_only = false; // record only the trace stages (fewer event records in the step)
+    void begin(cudaStream_t s, double* acc, bool is_trace = false) {
+        if (!on || (traces_only && !is_trace)) return;
         st = s;
         cudaEvent_t e = get();
         if (!e) return;
@@ -690,6 +691,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
     PathBuffers& b = ws.pb;
     StageEvents ev;
     ev.on = times != nullptr;
+    ev.traces_only = eo.stats_traces_only;
     cr_status failst = CR_OK;
     auto check = [&](cudaError_t e, const char* what) {
         if (e != cudaSuccess && failst == CR_OK) failst = fail(CR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -732,7 +734,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         ta.counters = nullptr;
         if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
         ta.packet = eo.packet_primary;
-        ev.begin(stream, times ? &times->trace_primary : &dummy);
+        ev.begin(stream, times ? &times->trace_primary : &dummy, true);
         launch_trace(ta, stream, lc);
         ev.end();
         ta.packet = eo.packet_secondary;
@@ -742,7 +744,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             launch_shade(P, b, bnc == 1, eo.debug, stream, lc);
             ev.end();
             if (P.nee && b.shadow_d) {
-                ev.begin(stream, times ? &times->trace_shadow : &dummy);
+                ev.begin(stream, times ? &times->trace_shadow : &dummy, true);
                 launch_shadow(P, b, bnc == 1, p.bvh8, stream, lc);
                 ev.end();
             }
@@ -762,7 +764,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             ta.two_phase = eo.phase_budget > 0 && ws.phase.state;
             ta.phase = ws.phase;
             ta.phase.budget = eo.phase_budget;
-            ev.begin(stream, times ? &times->trace_secondary : &dummy);
+            ev.begin(stream, times ? &times->trace_secondary : &dummy, true);
             launch_trace(ta, stream, lc);
             ev.end();
         }
@@ -868,6 +870,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     }
     eo.debug = o.debug;
     eo.debug_npx = npx;
+    eo.stats_traces_only = (o.flags & CR_OPT_STATS_TRACES) && !(o.flags & CR_OPT_STATS);
     LaunchCount lc;
     StageTimes times;
     cudaEvent_t e_all[2];
@@ -876,7 +879,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         CR_CUDA(cudaEventCreate(&e_all[1]));
         CR_CUDA(cudaEventRecord(e_all[0], stream));
     }
-    st = enqueue_plan(plan, dev, s->ws, eo, stream, lc, (o.stats && (o.flags & CR_OPT_STATS)) ? &times : nullptr);
+    st = enqueue_plan(plan, dev, s->ws, eo, stream, lc,
+                      (o.stats && (o.flags & (CR_OPT_STATS | CR_OPT_STATS_TRACES))) ? &times : nullptr);
     if (st != CR_OK) return st;
     if (!out_dev) CR_CUDA(cudaMemcpyAsync(out_rgb, s->d_out, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, stream));
     if (o.stats) {

@@ -315,6 +315,7 @@ struct ExecOpts {
     uint32_t sort_key = 0; // reordering key of CR_MORTON_SORT (cr_sort_key)
     uint32_t phase_budget = 0; // two-phase secondary trace: node visits before suspension (0 = off)
     bool clear_accum = true; // zero the accumulation buffer first
+    bool stats_traces_only = false; // stage events only around the trace launches
     bool write_output = true; // write every job's output after the last pass
     const cr_debug* debug = nullptr;
     uint32_t debug_npx = 0;

@@ -303,3 +303,22 @@ def test_hybrid_donor_option_bit_exact(cr, orc, tile, k):
         assert np.array_equal(g["local"][b][alive].view(np.uint32), ref["dbg_local"][b][alive].view(np.uint32))
     assert (ref["dbg_cat"][0][ok] == 3).sum() > 50
     _check(img.cpu().numpy(), ref, max_taint=0.1 if k == 64 else 0.05)
+
+
+def test_trace_only_stage_events(cr):
+    """CR_OPT_STATS_TRACES times the trace launches only (the other stage times read 0) and
+    leaves the image unchanged."""
+    sc = scenes.interior(width=96, height=64)
+    S = cr.Scene(sc)
+    kw = dict(spp=2, max_bounces=3, tile=(8, 8), k=8, seed=3)
+    a, full = S.render(stats=True, **kw)
+    b, st = S.render(flags=cr.CR_OPT_STATS_TRACES, **kw)  # stats object via flags only: none
+    assert torch.equal(a, b)
+    st = cr.cr_stats()
+    o = cr.make_opts(k=8, seed=3, flags=cr.CR_OPT_STATS_TRACES, stats=st)
+    out = torch.empty_like(a)
+    cr.cr_render_ex(S.handle, sc.camera, 2, 3, "direction_reuse", 8, 8, out, o)
+    d = st.as_dict()
+    assert torch.equal(out, a)
+    assert d["ms_trace_secondary"] > 0 and d["ms_trace_primary"] > 0 and d["ms_shade"] == 0
+    assert d["ms_total"] > 0 and full["ms_shade"] > 0
