@@ -322,3 +322,17 @@ def test_trace_only_stage_events(cr):
     assert torch.equal(out, a)
     assert d["ms_trace_secondary"] > 0 and d["ms_trace_primary"] > 0 and d["ms_shade"] == 0
     assert d["ms_total"] > 0 and full["ms_shade"] > 0
+
+
+def test_pinned_host_output_written_directly(cr):
+    """A page-locked host output is written by the output kernel itself; pageable host and
+    device outputs give the same bits."""
+    sc = scenes.interior(width=96, height=64)
+    S = cr.Scene(sc)
+    kw = dict(spp=2, max_bounces=2, tile=(8, 8), k=8, seed=2)
+    dev, _ = S.render(**kw)
+    pinned = torch.zeros((64, 96, 3), dtype=torch.float32).pin_memory()
+    S.render(out=pinned, **kw)
+    pageable = np.zeros((64, 96, 3), np.float32)
+    S.render(out=pageable, **kw)
+    assert torch.equal(pinned, dev.cpu()) and np.array_equal(pageable, dev.cpu().numpy())
