@@ -84,8 +84,8 @@ enum { CR_BVH2 = 1u, CR_BVH8Q = 2u };
 
 typedef struct cr_scene cr_scene;
 
-/* Build a device-resident scene: a binned-SAH BVH2 (32 bins, <= 4 triangles per leaf,
- * depth <= 64) on the host, optionally collapsed into 8-wide nodes with 8-bit
+/* Build a device-resident scene: an SAH BVH2 (exact sweep up to 1024 triangles, 32 bins
+ * above, SAH-chosen leaves of <= 4 triangles, depth <= 64) on the host, optionally collapsed into 8-wide nodes with 8-bit
  * conservatively quantised child boxes (bvh_flags & CR_BVH8Q; Ylitie et al. 2017, cited
  * in Sec. 2.3), then uploaded once.
  *   tri_xyz  host, n_tri * 9 floats: v0.xyz v1.xyz v2.xyz per triangle; all finite.

