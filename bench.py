@@ -247,7 +247,7 @@ def run_ours(args):
 
     variant_flags = {"two_phase": cr.CR_OPT_TWO_PHASE, "packet": cr.CR_OPT_PACKET_SECONDARY,
                      "speculative": cr.CR_OPT_SPECULATIVE, "persistent": cr.CR_OPT_PERSISTENT,
-                     "nee": cr.CR_OPT_NEE}
+                     "nee": cr.CR_OPT_NEE, "ordered": cr.CR_OPT_ORDERED_QUEUES}
 
     def parse(mode):
         # "morton_sort:<key>" selects a reordering key (Table 1 comparators); a "+<variant>"

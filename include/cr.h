@@ -131,7 +131,8 @@ typedef struct {
 typedef enum { CR_INDEPENDENT = 0, CR_MORTON_SORT = 1, CR_DIRECTION_REUSE = 2, CR_WORLD_REUSE = 3 } cr_reuse_mode;
 
 /* Per-call statistics (filled when cr_render_opts.stats != NULL).  Stage times are CUDA
- * event times on the call's stream summed over samples and bounces. */
+ * event times on the call's stream summed over samples and bounces.  The queue compaction
+ * runs inside the shade kernels (ms_compact reads 0) unless CR_OPT_ORDERED_QUEUES. */
 typedef struct {
     double ms_total;           /* first launch to last (events) */
     double ms_raygen, ms_trace_primary, ms_trace_secondary, ms_shade, ms_compact, ms_sort, ms_accum;
@@ -170,8 +171,11 @@ enum {
     CR_OPT_ANY_HIT = 512u, /* cr_trace_rays: visibility only (any hit before tmax, see there) */
     CR_OPT_HYBRID_DONOR = 1024u, /* cr_render: the job flag CR_JOB_HYBRID_DONOR */
     CR_OPT_NEE_SHARED = 2048u,   /* cr_render: the job flag CR_JOB_NEE_SHARED */
-    CR_OPT_STATS_TRACES = 4096u  /* like CR_OPT_STATS but events only around the trace launches
+    CR_OPT_STATS_TRACES = 4096u, /* like CR_OPT_STATS but events only around the trace launches
                                     (less event traffic in the step; other stage times read 0) */
+    CR_OPT_ORDERED_QUEUES = 8192u /* build the ray and group queues in position order with a
+                                     separate three-launch compaction (count, scan, scatter)
+                                     instead of appending them in the shade; same images */
 };
 
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):

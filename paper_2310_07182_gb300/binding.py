@@ -29,6 +29,7 @@ CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIV
 CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY, CR_OPT_TWO_PHASE = 32, 64, 128
 CR_OPT_NEE, CR_OPT_ANY_HIT, CR_OPT_HYBRID_DONOR, CR_OPT_NEE_SHARED = 256, 512, 1024, 2048
 CR_OPT_STATS_TRACES = 4096
+CR_OPT_ORDERED_QUEUES = 8192
 CR_JOB_NEE, CR_JOB_HYBRID_DONOR, CR_JOB_NEE_SHARED = 1, 2, 4
 MODES = {"independent": CR_INDEPENDENT, "morton_sort": CR_MORTON_SORT, "direction_reuse": CR_DIRECTION_REUSE,
          "world_reuse": CR_WORLD_REUSE}

@@ -556,6 +556,12 @@ cr_status Workspace::ensure(uint32_t n_slots, uint32_t npx) {
     return CR_OK;
 }
 
+cr_status queue_status(const uint64_t* host_counts) {
+    if (reinterpret_cast<const uint32_t*>(host_counts)[kQueueErrWord])
+        return fail(CR_ERR_CUDA, "queue compaction: an append would overflow a queue");
+    return CR_OK;
+}
+
 // Device bytes of path state for n_slots slots and npx pixels (what Workspace::ensure takes).
 size_t workspace_bytes(uint32_t n_slots, uint32_t npx) {
     const size_t ns = n_slots;
@@ -753,16 +759,18 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         for (uint32_t bnc = 1; bnc <= p.max_bounces; ++bnc) {
             P.bounce = bnc;
             ev.begin(stream, times ? &times->shade : &dummy);
-            launch_shade(P, b, bnc == 1, eo.debug, stream, lc);
+            launch_shade(P, b, bnc == 1, !eo.ordered_queues, eo.debug, stream, lc);
             ev.end();
             if (P.nee && b.shadow_d) {
                 ev.begin(stream, times ? &times->trace_shadow : &dummy, true);
                 launch_shadow(P, b, bnc == 1, p.bvh8, stream, lc);
                 ev.end();
             }
-            ev.begin(stream, times ? &times->compact : &dummy);
-            launch_compact(P, b, bnc == 1, stream, lc);
-            ev.end();
+            if (eo.ordered_queues) {
+                ev.begin(stream, times ? &times->compact : &dummy);
+                launch_compact(P, b, bnc == 1, stream, lc);
+                ev.end();
+            }
             ta.queue = b.ray_queue;
             ta.queue_count = b.counts + 8 + 2 * bnc;
             ta.n_max = n_slots;
@@ -782,7 +790,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         }
         P.bounce = p.max_bounces + 1;
         ev.begin(stream, times ? &times->shade : &dummy);
-        launch_shade(P, b, false, eo.debug, stream, lc);
+        launch_shade(P, b, false, false, eo.debug, stream, lc);
         ev.end();
         ev.begin(stream, times ? &times->accum : &dummy);
         launch_accumulate(P, b, stream, lc);
@@ -885,6 +893,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     eo.debug = o.debug;
     eo.debug_npx = npx;
     eo.stats_traces_only = (o.flags & CR_OPT_STATS_TRACES) && !(o.flags & CR_OPT_STATS);
+    eo.ordered_queues = (o.flags & CR_OPT_ORDERED_QUEUES) != 0;
     LaunchCount lc;
     StageTimes times;
     cudaEvent_t e_all[2];
@@ -928,6 +937,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         *o.stats = stats;
         cudaEventDestroy(e_all[0]);
         cudaEventDestroy(e_all[1]);
+        st = queue_status(host_counts);
+        if (st != CR_OK) return st;
     }
     if (!(o.flags & CR_OPT_NO_SYNC)) CR_CUDA(cudaStreamSynchronize(stream));
     CR_CUDA(cudaGetLastError());
@@ -1183,6 +1194,7 @@ static cr_status batch_opts_check(const cr_batch_opts* o, PlanOpts& po, ExecOpts
         return fail(CR_ERR_INVALID_ARG, "stack %u not in {8, 16, 32}", o->stack);
     eo.stack = o->stack ? o->stack : 16;
     eo.persistent = (o->flags & CR_OPT_PERSISTENT) != 0;
+    eo.ordered_queues = (o->flags & CR_OPT_ORDERED_QUEUES) != 0;
     if (o->sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "sort_key %u", o->sort_key);
     eo.sort_key = o->sort_key;
     return CR_OK;
@@ -1302,6 +1314,8 @@ extern "C" cr_status cr_batch_run(cr_batch* b, cr_stats* stats) {
         stats->kernel_launches = launches;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        const cr_status qst = queue_status(host_counts);
+        if (qst != CR_OK) return qst;
     }
     CR_CUDA(cudaStreamSynchronize(b->stream));
     CR_CUDA(cudaGetLastError());

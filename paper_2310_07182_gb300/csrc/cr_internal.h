@@ -199,8 +199,9 @@ struct PathBuffers {
     uint8_t* alive = nullptr;   // 1 while the path continues
     int32_t* ray_queue = nullptr;   // alive slots in slot order
     int32_t* group_queue = nullptr; // groups with an alive member (2 x n_groups, double-buffered)
-    // counts (kCountsWords words): [2] persistent work counter; [8 + 2b], [8 + 2b + 1] ray and
-    // group queue lengths after the compaction of bounce b; from word kStatWord, 64-bit
+    // counts (kCountsWords words): [2] persistent work counter; [kQueueErrWord] queue
+    // overflow flag; [8 + 2b], [8 + 2b + 1] ray and group queue lengths after the compaction
+    // of bounce b (kQueueCountWords words, zeroed by raygen each pass); from word kStatWord, 64-bit
     // running totals of rays traced per bounce (index b); from kCounterWord, 64-bit node
     // visits and triangle tests of the counting pass.
     uint32_t* counts = nullptr;
@@ -222,6 +223,7 @@ struct PathBuffers {
 };
 
 constexpr uint32_t kCountsWords = 256, kStatWord = 64, kCounterWord = 128, kShadowWord = 200;
+constexpr uint32_t kQueueErrWord = 5, kQueueCountWords = kStatWord - 8;
 // Shadow rays of the last shade (positions of its group queue): any-hit traversal, and the
 // contribution of each unblocked one added to the path radiance.
 void launch_shadow(const PassArgs& p, PathBuffers& b, bool first, bool bvh8, cudaStream_t st, LaunchCount& lc);
@@ -238,9 +240,13 @@ void launch_shadow_rays(const SceneDev* scenes, const uint16_t* slot_scene, cons
 void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
 // raygen leaves the primary trace's visiting order (row-major pixels per tile) in the ray queue
 bool primary_pixel_order();
-void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,
-                  LaunchCount& lc);
-// Group-granular compaction of the slots processed by the last shade into ray and group queues.
+// Shade the slots of the current group queue.  With `compact` the same launch appends the
+// continuing slots and groups to the next ray and group queues (block ranges in completion
+// order); without it launch_compact builds them in position order.
+void launch_shade(const PassArgs& p, PathBuffers& b, bool first, bool compact, const cr_debug* dbg,
+                  cudaStream_t st, LaunchCount& lc);
+// Group-granular, order-preserving compaction (three launches) of the slots processed by the
+// last shade into ray and group queues.
 void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t st, LaunchCount& lc);
 const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, uint32_t key_kind,
                                   cudaStream_t st, LaunchCount& lc);
@@ -317,6 +323,7 @@ struct ExecOpts {
     bool clear_accum = true; // zero the accumulation buffer first
     bool stats_traces_only = false; // stage events only around the trace launches
     bool write_output = true; // write every job's output after the last pass
+    bool ordered_queues = false; // three-launch order-preserving compaction instead of appends
     const cr_debug* debug = nullptr;
     uint32_t debug_npx = 0;
 };
@@ -325,6 +332,8 @@ struct StageTimes {
     double trace_shadow = 0;
 };
 cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, RenderPlan& plan);
+// CR_OK unless the queues of the run whose counts words these are overflowed (never expected)
+cr_status queue_status(const uint64_t* host_counts);
 cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h);
 bool scene_has_bvh8(const cr_scene* s);
 cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, const ExecOpts& eo, cudaStream_t stream,

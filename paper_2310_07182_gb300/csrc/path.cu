@@ -77,8 +77,10 @@ __device__ __forceinline__ uint32_t job_of_tile(const JobDev* jobs, uint32_t n_j
 __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __restrict__ slot_job,
                          uint16_t* __restrict__ slot_scene, float4* __restrict__ ray_o, float4* __restrict__ ray_d,
                          float4* __restrict__ beta, float4* __restrict__ radiance, uint8_t* __restrict__ alive,
-                         int32_t* __restrict__ primary_queue) {
+                         int32_t* __restrict__ primary_queue, uint32_t* __restrict__ queue_counts) {
     extern __shared__ uint16_t inv[];
+    // the shade kernels append to the per-bounce queue counters: zero them for this pass
+    if (blockIdx.x == 0 && threadIdx.x < kQueueCountWords) queue_counts[threadIdx.x] = 0u;
     const uint32_t m = p.m;
     const uint32_t tiles_per_block = blockDim.x / m;
     const uint32_t tl = threadIdx.x / m, j = threadIdx.x % m;
@@ -155,6 +157,13 @@ struct ShadeArgs {
     float4* shadow_o;
     float4* shadow_d;
     float4* shadow_c;
+    // queue compaction in the shade (ray_queue NULL: this launch does not compact)
+    int32_t* ray_queue;              // continuing slots
+    int32_t* group_queue_out;        // groups with a continuing member
+    uint32_t* queue_counts;          // [0] rays, [1] groups appended (zeroed by raygen)
+    unsigned long long* rays_queued; // running total of rays queued at this bounce
+    uint32_t* queue_err;             // set if an append would overflow a queue (never expected)
+    uint32_t ray_cap, group_cap;
 };
 
 struct Member {
@@ -390,7 +399,8 @@ __device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p
     a.shadow_d[slot] = dr;
 }
 
-__device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs& p, int slot, Member& mb,
+// Returns whether the path continues (its slot is alive for the next trace).
+__device__ __forceinline__ bool finish_member(const ShadeArgs& a, const PassArgs& p, int slot, Member& mb,
                                               float3 L, float4 bt, bool was_alive, int cat) {
     if (a.dbg.cat && mb.pix >= 0 && !mb.final_pass) {
         const uint32_t di = (p.bounce - 1) * a.npx + (uint32_t)mb.pix;
@@ -409,7 +419,7 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs
         a.dbg.world[3 * di + 1] = ww.y;
         a.dbg.world[3 * di + 2] = ww.z;
     }
-    if (!was_alive) return;
+    if (!was_alive) return false;
     a.radiance[slot] = make_float4(L.x, L.y, L.z, 0.0f);
     if (mb.alive && mb.valid) {
         const V3 o = spawn_point(a, slot, mb.wl.z < 0.0f ? v3(-mb.n.x, -mb.n.y, -mb.n.z) : mb.n);
@@ -421,8 +431,63 @@ __device__ __forceinline__ void finish_member(const ShadeArgs& a, const PassArgs
         a.beta[slot] = make_float4(fm(bt.x, mb.w[0]), fm(bt.y, mb.w[1]), fm(bt.z, mb.w[2]),
                                    mb.nee ? own_pdf(mb, mb.wl) : 0.0f);
         a.alive[slot] = 1;
-    } else {
-        a.alive[slot] = 0;
+        return true;
+    }
+    a.alive[slot] = 0;
+    return false;
+}
+
+// Queue compaction inside the shade (the default): after shading, each block appends its
+// continuing slots to the ray queue and its groups with a continuing member to the group
+// queue, in position order, at ranges it reserves with one atomic add per queue.  Groups
+// keep their K slots together and a block's slots stay adjacent; the blocks' ranges follow
+// their completion order, so the queue order (not the result of any slot) can differ from
+// run to run.  CR_OPT_ORDERED_QUEUES uses the three-launch order-preserving compaction.
+template <uint32_t kThreads>
+__device__ __forceinline__ void append_queues(const ShadeArgs& a, uint32_t K, int slot, bool alive, bool group_head) {
+    __shared__ unsigned long long s_w[kThreads / 32];
+    __shared__ unsigned long long s_base;
+    constexpr uint32_t nw = kThreads / 32;
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    // block-exclusive ranks of (ray, group), packed as rays | groups << 32
+    const unsigned long long v = (alive ? 1ull : 0ull) | (group_head ? 1ull << 32 : 0ull);
+    unsigned long long x = v;
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long t = lane < nw ? s_w[lane] : 0ull;
+        for (uint32_t off = 1; off < nw; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
+        }
+        if (lane < nw) s_w[lane] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long agg = s_w[nw - 1];
+        const uint32_t nr = (uint32_t)agg, ng = (uint32_t)(agg >> 32);
+        uint32_t br = 0, bg = 0;
+        if (nr) {
+            br = atomicAdd(&a.queue_counts[0], nr);
+            atomicAdd(a.rays_queued, (unsigned long long)nr);
+        }
+        if (ng) bg = atomicAdd(&a.queue_counts[1], ng);
+        s_base = (unsigned long long)br | ((unsigned long long)bg << 32);
+    }
+    __syncthreads();
+    const unsigned long long rank = x - v + (w > 0 ? s_w[w - 1] : 0ull);
+    const uint32_t qr = (uint32_t)s_base + (uint32_t)rank, qg = (uint32_t)(s_base >> 32) + (uint32_t)(rank >> 32);
+    if (alive) {
+        if (qr < a.ray_cap) a.ray_queue[qr] = slot;
+        else atomicOr(a.queue_err, 1u);
+    }
+    if (group_head) {
+        if (qg < a.group_cap) a.group_queue_out[qg] = slot / (int)K;
+        else atomicOr(a.queue_err, 1u);
     }
 }
 
@@ -490,10 +555,10 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     }
     int cat = kCatEmpty;
     int light_pix = mb.pix;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t seg = lane & ~(K - 1u);
+    const uint32_t segmask = K == 32u ? 0xffffffffu : (((1u << K) - 1u) << seg);
     {
-        const uint32_t lane = threadIdx.x & 31u;
-        const uint32_t seg = lane & ~(K - 1u);
-        const uint32_t segmask = K == 32u ? 0xffffffffu : (((1u << K) - 1u) << seg);
         // shared light samples: the group's first alive member owns the light stream
         if (__any_sync(0xffffffffu, mb.nee_shared)) {
             const uint32_t bal = __ballot_sync(0xffffffffu, mb.alive) & segmask;
@@ -549,7 +614,12 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
         }
     }
     if (active && a.shadow_d) next_event(a, p, slot, mb, bt, light_pix);
-    if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
+    const bool next_alive = active && finish_member(a, p, slot, mb, L, bt, was_alive, cat);
+    if (a.ray_queue) {
+        // groups are K-lane segments of a warp: a group continues if any member does
+        const uint32_t nb = __ballot_sync(0xffffffffu, next_alive) & segmask;
+        append_queues<128>(a, K, slot, next_alive, lane == seg && nb != 0u);
+    }
 }
 
 // 32 < K <= 256: a group spans K/32 warps of a 256-thread block; per-warp ballots and the
@@ -561,6 +631,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     __shared__ float s_sum[3][256];
     __shared__ float s_world[4][256]; // world-space direction and validity (Sec. 3.1 ablation)
     __shared__ int s_pix[256];        // members' pixels (owner of a shared light sample)
+    __shared__ uint32_t s_next[8];    // per-warp ballots of the slots that continue
     const uint32_t K = p.k;
     const uint32_t n_groups = a.group_queue ? min(*a.group_count, a.n_groups_max) : a.n_groups_max;
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -693,7 +764,18 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
         }
     }
     if (active && a.shadow_d) next_event(a, p, slot, mb, bt, light_pix);
-    if (active) finish_member(a, p, slot, mb, L, bt, was_alive, cat);
+    const bool next_alive = active && finish_member(a, p, slot, mb, L, bt, was_alive, cat);
+    if (a.ray_queue) {
+        // a group spans K/32 warps of the block: OR of their ballots
+        const uint32_t t = threadIdx.x;
+        const uint32_t nb = __ballot_sync(0xffffffffu, next_alive);
+        if ((t & 31u) == 0) s_next[t >> 5] = nb;
+        __syncthreads();
+        bool head = false;
+        if (t % K == 0)
+            for (uint32_t ww = t >> 5; ww < (t + K) >> 5; ++ww) head |= s_next[ww] != 0u;
+        append_queues<256>(a, K, slot, next_alive, head);
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -1155,7 +1237,8 @@ void launch_raygen(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCou
     // the ray queue is free until the first compaction: it carries the primary trace's order
     k_raygen<<<grid, block, block * sizeof(uint16_t), st>>>(p, b.pixel, b.slot_job, b.slot_scene, b.ray_o, b.ray_d,
                                                              b.beta, b.radiance, b.alive,
-                                                             CR_PRIMARY_PIXEL_ORDER ? b.ray_queue : nullptr);
+                                                             CR_PRIMARY_PIXEL_ORDER ? b.ray_queue : nullptr,
+                                                             b.counts + 8);
     lc.n++;
 }
 
@@ -1168,7 +1251,7 @@ void launch_groups(const CamBasis& cam, uint32_t tile_w, uint32_t tile_h, uint32
     lc.n++;
 }
 
-static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg) {
+static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, bool compact, const cr_debug* dbg) {
     ShadeArgs a;
     a.jobs = p.jobs;
     a.scenes = p.scenes;
@@ -1191,20 +1274,27 @@ static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, const
     a.shadow_o = nee ? b.shadow_o : nullptr;
     a.shadow_d = nee ? b.shadow_d : nullptr;
     a.shadow_c = nee ? b.shadow_c : nullptr;
+    a.ray_queue = compact ? b.ray_queue : nullptr;
+    a.group_queue_out = b.group_queue + (size_t)(p.bounce & 1) * b.n_groups;
+    a.queue_counts = b.counts + 8 + 2 * p.bounce;
+    a.rays_queued = reinterpret_cast<unsigned long long*>(b.counts + kStatWord) + p.bounce;
+    a.queue_err = b.counts + kQueueErrWord;
+    a.ray_cap = b.n_groups * p.k;
+    a.group_cap = b.n_groups;
     return a;
 }
 
 void launch_shadow(const PassArgs& p, PathBuffers& b, bool first, bool bvh8, cudaStream_t st, LaunchCount& lc) {
     if (!p.nee || !b.shadow_d) return;
-    const ShadeArgs a = shade_args(p, b, first, nullptr);
+    const ShadeArgs a = shade_args(p, b, first, false, nullptr);
     launch_shadow_rays(p.scenes, b.slot_scene, b.shadow_o, b.shadow_d, b.shadow_c, a.group_queue, a.group_count,
                        a.n_groups_max, p.k, b.radiance, reinterpret_cast<unsigned long long*>(b.counts + kShadowWord),
                        bvh8, st, lc);
 }
 
-void launch_shade(const PassArgs& p, PathBuffers& b, bool first, const cr_debug* dbg, cudaStream_t st,
-                  LaunchCount& lc) {
-    ShadeArgs a = shade_args(p, b, first, dbg);
+void launch_shade(const PassArgs& p, PathBuffers& b, bool first, bool compact, const cr_debug* dbg,
+                  cudaStream_t st, LaunchCount& lc) {
+    ShadeArgs a = shade_args(p, b, first, compact, dbg);
     const uint32_t n_pos = b.n_groups * p.k;
     if (p.k <= 32) {
         k_shade_warp<<<(n_pos + 127) / 128, 128, 0, st>>>(a, p);

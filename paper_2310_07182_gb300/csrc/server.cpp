@@ -204,6 +204,11 @@ void cr_server::loop() {
                 std::lock_guard<std::mutex> lk(mu);
                 fatal_msg = cudaGetErrorString(e);
             }
+            if (e == cudaSuccess && st == CR_OK && queue_status(counts) != CR_OK) {
+                st = CR_ERR_CUDA;
+                std::lock_guard<std::mutex> lk(mu);
+                fatal_msg = "queue compaction overflowed";
+            }
             if (st == CR_OK) {
                 std::lock_guard<std::mutex> lk(mu);
                 stats.passes++;

@@ -336,3 +336,20 @@ def test_pinned_host_output_written_directly(cr):
     pageable = np.zeros((64, 96, 3), np.float32)
     S.render(out=pageable, **kw)
     assert torch.equal(pinned, dev.cpu()) and np.array_equal(pageable, dev.cpu().numpy())
+
+
+@pytest.mark.parametrize("k,tile,nee", [(8, (8, 8), False), (32, (8, 8), True), (64, (8, 8), False),
+                                        (256, (16, 16), True)])
+def test_appended_and_ordered_queues_render_the_same(cr, k, tile, nee):
+    """The shade's in-kernel queue appends (block ranges in completion order) and the
+    order-preserving three-launch compaction give the same image, ray counts and queue
+    lengths: no slot's result depends on the queue order."""
+    sc = scenes.tiny(material_mix="mixed", n_soup=3000)
+    S = cr.Scene(sc)
+    kw = dict(spp=2, max_bounces=4, mode="direction_reuse", tile=tile, k=k, seed=3, stats=True, nee=nee)
+    a, sa = S.render(**kw)
+    b, sb = S.render(flags=cr.CR_OPT_ORDERED_QUEUES, **kw)
+    assert torch.equal(a, b)
+    for key in ("secondary_rays", "secondary_rays_b1", "shadow_rays"):
+        assert sa[key] == sb[key], key
+    assert sa["secondary_rays"] > 0 and sa["ms_compact"] == 0.0 and sb["ms_compact"] > 0.0
