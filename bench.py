@@ -128,8 +128,9 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha(files=("trace.cu", "trace_common.cuh")) -> str:
-    """sha256 (16 hex digits) of the sources that define the BVH2 trace kernel."""
+def kernel_source_sha(files=("trace.cu", "trace_common.cuh", "bvh_build.cpp")) -> str:
+    """sha256 (16 hex digits) of the sources that define the BVH2 trace kernel and the tree
+    it traverses (a new tree changes its traffic and instruction counts)."""
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_2310_07182_gb300", "csrc", f), "rb").read())
