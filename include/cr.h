@@ -217,9 +217,11 @@ cr_status cr_render_opts_default(cr_render_opts* opts);
  *                trace), CR_DIRECTION_REUSE (Sec. 3.2-3.3).
  *   group_w, group_h  tile W x H of the reuse-domain partition (Sec. 3.3); W*H a power of
  *                two <= 1024.  Rays of every mode are laid out tile by tile.
- *   out_rgb      host or device, width*height*3 floats, written once at the end.  The output
- *                kernel writes device memory and page-locked host memory directly; other host
- *                memory gets a staging buffer and one copy.
+ *   out_rgb      host or device, width*height*3 floats, written once at the end.  Host
+ *                memory gets a staging buffer and one device-to-host copy (a DMA copy from
+ *                page-locked memory; on GB300 it beats the output kernel writing
+ *                page-locked memory over the chip-to-chip link: 0.13 ms against 0.15-0.48
+ *                ms for a 1920x1080 image).
  * With opts == NULL (cr_render) K = W*H.  The result depends only on (scene, camera, spp,
  * bounces, mode, W, H, K, interleave, seed, frame_base, reuse_depth): random numbers are
  * keyed by (pixel, frame, bounce), never by ray order, so CR_MORTON_SORT gives the same

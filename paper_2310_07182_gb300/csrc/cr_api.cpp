@@ -39,18 +39,6 @@ cr_status fail(cr_status st, const char* fmt, ...) {
         }                                                                                 \
     } while (0)
 
-// Device-side address of page-locked host memory (cudaHostAlloc / cudaHostRegister), or NULL
-// for anything else: the output kernel can then write a host output directly.
-void* pinned_host_device_ptr(void* p) {
-    if (!p) return nullptr;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
-}
-
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -830,12 +818,10 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     cr_status st = check_camera(cam);
     if (st != CR_OK) return st;
     const bool out_dev = is_device_ptr(out_rgb);
-    // page-locked host output: the output kernel writes it directly (no staging copy)
-    float* out_pinned = out_dev ? nullptr : static_cast<float*>(pinned_host_device_ptr(out_rgb));
     if (!out_dev && (o.flags & CR_OPT_NO_SYNC))
         return fail(CR_ERR_INVALID_ARG, "cr_render: CR_OPT_NO_SYNC needs a device out_rgb");
     const uint32_t npx = cam->width * cam->height;
-    if (!out_dev && !out_pinned && s->out_cap < (size_t)npx * 3) {
+    if (!out_dev && s->out_cap < (size_t)npx * 3) {
         if (s->d_out) cudaFree(s->d_out);
         s->d_out = nullptr;
         s->out_cap = 0;
@@ -854,7 +840,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     job.frame_base = o.frame_base;
     job.flags = ((o.flags & CR_OPT_NEE) ? CR_JOB_NEE : 0u) | ((o.flags & CR_OPT_HYBRID_DONOR) ? CR_JOB_HYBRID_DONOR : 0u) |
                 ((o.flags & CR_OPT_NEE_SHARED) ? CR_JOB_NEE_SHARED : 0u);
-    job.out_rgb = out_dev ? out_rgb : (out_pinned ? out_pinned : s->d_out);
+    job.out_rgb = out_dev ? out_rgb : s->d_out;
     PlanOpts po;
     po.tile_w = group_w;
     po.tile_h = group_h;
@@ -905,8 +891,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     st = enqueue_plan(plan, dev, s->ws, eo, stream, lc,
                       (o.stats && (o.flags & (CR_OPT_STATS | CR_OPT_STATS_TRACES))) ? &times : nullptr);
     if (st != CR_OK) return st;
-    if (!out_dev && !out_pinned)
-        CR_CUDA(cudaMemcpyAsync(out_rgb, s->d_out, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, stream));
+    if (!out_dev) CR_CUDA(cudaMemcpyAsync(out_rgb, s->d_out, sizeof(float) * 3 * (size_t)npx, cudaMemcpyDeviceToHost, stream));
     if (o.stats) {
         cr_stats stats;
         std::memset(&stats, 0, sizeof(stats));

@@ -324,9 +324,9 @@ def test_trace_only_stage_events(cr):
     assert d["ms_total"] > 0 and full["ms_shade"] > 0
 
 
-def test_pinned_host_output_written_directly(cr):
-    """A page-locked host output is written by the output kernel itself; pageable host and
-    device outputs give the same bits."""
+def test_host_outputs_match_the_device_output(cr):
+    """Page-locked and pageable host outputs (staging buffer plus one copy) give the device
+    output's bits."""
     sc = scenes.interior(width=96, height=64)
     S = cr.Scene(sc)
     kw = dict(spp=2, max_bounces=2, tile=(8, 8), k=8, seed=2)
