@@ -193,9 +193,7 @@ struct Member {
 
 // Shading point of a hit: geometric normal facing the incoming ray, tangent frame, wo.
 __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs& p, const SceneDev& sc, int slot,
-                                             Member& mb, float3& L, const float4 bt) {
-    const int2 h = a.hit[slot];
-    const float4 d4 = a.ray_d[slot];
+                                             Member& mb, float3& L, const float4 bt, const int2 h, const float4 d4) {
     if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
     if (h.x < 0) { // miss: environment
         L.x = fa(L.x, fm(bt.x, sc.env[0]));
@@ -529,10 +527,18 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
+        // the slot's state in one round of independent loads (read even for slots that turn
+        // out dead, which takes them off the dependency chain of the live ones)
         mb.pix = a.pixel[slot];
+        const uint32_t jid = a.slot_job[slot];
+        const bool alive_in = a.alive[slot] != 0;
+        const int2 h = a.hit[slot];
+        const float4 d4 = a.ray_d[slot];
+        const float4 b4 = a.beta[slot];
+        const float4 r4 = a.radiance[slot];
         const JobDev* Jp = nullptr;
         if (mb.pix >= 0) { // every valid slot knows whether its job is past its last bounce
-            Jp = &a.jobs[a.slot_job[slot]];
+            Jp = &a.jobs[jid];
             mb.final_pass = p.bounce > Jp->max_bounces;
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
@@ -543,14 +549,13 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
         }
-        was_alive = mb.pix >= 0 && a.alive[slot];
+        was_alive = mb.pix >= 0 && alive_in;
         if (was_alive) {
             const JobDev& J = *Jp;
             mb.alive = true;
-            bt = a.beta[slot];
-            const float4 r4 = a.radiance[slot];
+            bt = b4;
             L = make_float3(r4.x, r4.y, r4.z);
-            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
+            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt, h, d4);
         }
     }
     int cat = kCatEmpty;
@@ -659,10 +664,18 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     if (active) {
         const uint32_t g = a.group_queue ? (uint32_t)a.group_queue[gq] : gq;
         slot = (int)(g * K + lane_g);
+        // the slot's state in one round of independent loads (read even for slots that turn
+        // out dead, which takes them off the dependency chain of the live ones)
         mb.pix = a.pixel[slot];
+        const uint32_t jid = a.slot_job[slot];
+        const bool alive_in = a.alive[slot] != 0;
+        const int2 h = a.hit[slot];
+        const float4 d4 = a.ray_d[slot];
+        const float4 b4 = a.beta[slot];
+        const float4 r4 = a.radiance[slot];
         const JobDev* Jp = nullptr;
         if (mb.pix >= 0) { // every valid slot knows whether its job is past its last bounce
-            Jp = &a.jobs[a.slot_job[slot]];
+            Jp = &a.jobs[jid];
             mb.final_pass = p.bounce > Jp->max_bounces;
             mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
             mb.world = (Jp->world_mask >> p.bounce) & 1u;
@@ -673,14 +686,13 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
         }
-        was_alive = mb.pix >= 0 && a.alive[slot];
+        was_alive = mb.pix >= 0 && alive_in;
         if (was_alive) {
             const JobDev& J = *Jp;
             mb.alive = true;
-            bt = a.beta[slot];
-            const float4 r4 = a.radiance[slot];
+            bt = b4;
             L = make_float3(r4.x, r4.y, r4.z);
-            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt);
+            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt, h, d4);
         }
     }
     int cat = kCatEmpty;
