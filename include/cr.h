@@ -143,6 +143,8 @@ typedef struct {
     uint64_t node_visits, tri_tests; /* counting pass only (CR_OPT_COUNT) */
     uint64_t shadow_rays;      /* shadow rays of next-event estimation (CR_OPT_NEE) */
     double ms_trace_shadow;    /* their any-hit trace */
+    uint64_t h2d_bytes;        /* bytes the call copied host to device (job and scene tables) */
+    uint64_t d2h_bytes;        /* bytes it copied device to host (a host out_rgb) */
 } cr_stats;
 
 /* Optional per-bounce capture (device pointers, spp must be 1).  npx = width * height.

@@ -68,7 +68,8 @@ class cr_stats(C.Structure):
                 ("ms_sort", C.c_double), ("ms_accum", C.c_double), ("primary_rays", C.c_uint64),
                 ("secondary_rays", C.c_uint64), ("secondary_rays_b1", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64),
-                ("shadow_rays", C.c_uint64), ("ms_trace_shadow", C.c_double)]
+                ("shadow_rays", C.c_uint64), ("ms_trace_shadow", C.c_double), ("h2d_bytes", C.c_uint64),
+                ("d2h_bytes", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

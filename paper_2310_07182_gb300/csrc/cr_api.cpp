@@ -917,6 +917,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         stats.tri_tests = ctr[1];
         stats.shadow_rays = host_counts[kShadowWord / 2];
         stats.ms_trace_shadow = times.trace_shadow;
+        stats.h2d_bytes = sizeof(JobDev) * plan.jobs.size() + sizeof(SceneDev) * plan.scenes.size();
+        stats.d2h_bytes = out_dev ? 0 : sizeof(float) * 3 * (uint64_t)npx;
         stats.primary_rays = (uint64_t)npx * spp;
         stats.kernel_launches = lc.n;
         *o.stats = stats;
