@@ -777,11 +777,8 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             ev.end();
         }
         P.bounce = p.max_bounces + 1;
-        ev.begin(stream, times ? &times->shade : &dummy);
-        launch_shade(P, b, false, false, eo.debug, stream, lc);
-        ev.end();
         ev.begin(stream, times ? &times->accum : &dummy);
-        launch_accumulate(P, b, stream, lc);
+        launch_finish_accumulate(P, b, eo.debug, stream, lc);
         ev.end();
     }
     // pass 0 holds every job (spp >= 1), with the px_base and output of each

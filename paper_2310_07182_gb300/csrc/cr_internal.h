@@ -254,7 +254,10 @@ uint32_t sort_hist_len(uint32_t n_slots);
 uint32_t compact_blocks(uint32_t n_pos);
 void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, float4* ray_o, float4* ray_d,
                            cudaStream_t st, LaunchCount& lc);
-void launch_accumulate(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc);
+// End of a pass (bounce B + 1): the environment or emission where each live path's last ray
+// ended, then every slot's radiance added to its pixel.
+void launch_finish_accumulate(const PassArgs& p, PathBuffers& b, const cr_debug* dbg, cudaStream_t st,
+                              LaunchCount& lc);
 // out[job] = accum / spp for every job of the table (all pixels of all jobs, one launch).
 void launch_output(const JobDev* jobs, uint32_t n_jobs, const float4* accum, uint32_t npx_total, cudaStream_t st,
                    LaunchCount& lc);

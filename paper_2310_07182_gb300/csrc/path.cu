@@ -192,13 +192,44 @@ struct Member {
 };
 
 // Shading point of a hit: geometric normal facing the incoming ray, tangent frame, wo.
+// Radiance picked up where a ray ends without scattering.  Miss: beta times the constant
+// environment.
+__device__ __forceinline__ void add_environment(const SceneDev& sc, const float4 bt, float3& L) {
+    L.x = fa(L.x, fm(bt.x, sc.env[0]));
+    L.y = fa(L.y, fm(bt.y, sc.env[1]));
+    L.z = fa(L.z, fm(bt.z, sc.env[2]));
+}
+
+// Emitter (triangle v0 v1 v2, emission m1.yzw): beta times the emission.  Under next-event
+// estimation the emission met by a BSDF-sampled ray is weighed against the light sample that
+// could have found it (power heuristic): the ray's direction had density beta.w (0: camera
+// ray or mirror, full weight), a light sample density r^2 / (cos_l A).
+__device__ __forceinline__ void add_emission(const SceneDev& sc, const float4 v0, const float4 v1, const float4 v2,
+                                             const float4 m1, const float4 bt, const int2 h, const float4 d4,
+                                             bool nee, float3& L) {
+    float w = 1.0f;
+    if (nee && bt.w > 0.0f) {
+        const V3 e0 = v3(v0.x, v0.y, v0.z);
+        const V3 nl = cross3(sub3(v3(v1.x, v1.y, v1.z), e0), sub3(v3(v2.x, v2.y, v2.z), e0));
+        const V3 d = v3(d4.x, d4.y, d4.z);
+        const float dd = dot3(d, d);
+        const float cl = fd(fabsf(dot3(nl, d)), fq(fm(dot3(nl, nl), dd)));
+        if (cl > 0.0f) {
+            const float th = __int_as_float(h.y);
+            const float pl = fd(fm(fm(th, th), dd), fm(cl, sc.light_total));
+            w = fd(fm(bt.w, bt.w), fa(fm(bt.w, bt.w), fm(pl, pl)));
+        }
+    }
+    L.x = fa(L.x, fm(fm(bt.x, m1.y), w));
+    L.y = fa(L.y, fm(fm(bt.y, m1.z), w));
+    L.z = fa(L.z, fm(fm(bt.z, m1.w), w));
+}
+
 __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs& p, const SceneDev& sc, int slot,
                                              Member& mb, float3& L, const float4 bt, const int2 h, const float4 d4) {
     if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
     if (h.x < 0) { // miss: environment
-        L.x = fa(L.x, fm(bt.x, sc.env[0]));
-        L.y = fa(L.y, fm(bt.y, sc.env[1]));
-        L.z = fa(L.z, fm(bt.z, sc.env[2]));
+        add_environment(sc, bt, L);
         mb.alive = false;
         return;
     }
@@ -211,26 +242,7 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     const uint32_t type = (uint32_t)__float_as_int(m0.x);
     mb.orig = __float_as_int(v0.w);
     if (type == kMatEmitter) {
-        // under next-event estimation the emission met by a BSDF-sampled ray is weighed
-        // against the light sample that could have found it (power heuristic): the ray's
-        // direction had density beta.w (0: camera ray or mirror, full weight), a light sample
-        // density r^2 / (cos_l A)
-        float w = 1.0f;
-        if (mb.nee && bt.w > 0.0f) {
-            const V3 e0 = v3(v0.x, v0.y, v0.z);
-            const V3 nl = cross3(sub3(v3(v1.x, v1.y, v1.z), e0), sub3(v3(v2.x, v2.y, v2.z), e0));
-            const V3 d = v3(d4.x, d4.y, d4.z);
-            const float dd = dot3(d, d);
-            const float cl = fd(fabsf(dot3(nl, d)), fq(fm(dot3(nl, nl), dd)));
-            if (cl > 0.0f) {
-                const float th = __int_as_float(h.y);
-                const float pl = fd(fm(fm(th, th), dd), fm(cl, sc.light_total));
-                w = fd(fm(bt.w, bt.w), fa(fm(bt.w, bt.w), fm(pl, pl)));
-            }
-        }
-        L.x = fa(L.x, fm(fm(bt.x, m1.y), w));
-        L.y = fa(L.y, fm(fm(bt.y, m1.z), w));
-        L.z = fa(L.z, fm(fm(bt.z, m1.w), w));
+        add_emission(sc, v0, v1, v2, m1, bt, h, d4, mb.nee, L);
         mb.alive = false;
         return;
     }
@@ -1145,19 +1157,50 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 }
 
 // ------------------------------------------------------------------------------------
-__global__ void k_accumulate(const int32_t* __restrict__ pixel, const uint16_t* __restrict__ slot_job,
-                             const JobDev* __restrict__ jobs, const float4* __restrict__ radiance, uint32_t n_slots,
-                             float4* __restrict__ accum) {
+// End of a pass, one thread per slot: a path still alive after its last secondary ray
+// only adds the environment or the emission where that ray ended (no group logic is left
+// to do), then the sample's radiance goes to its pixel.  Each pixel has one slot per pass
+// and passes run in sample order, so the sum keeps that order.
+__global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixel,
+                                    const uint16_t* __restrict__ slot_job, const uint8_t* __restrict__ alive,
+                                    const int2* __restrict__ hit, const float4* __restrict__ ray_d,
+                                    const float4* __restrict__ beta, const float4* __restrict__ radiance,
+                                    uint32_t n_slots, float4* __restrict__ accum, int32_t* __restrict__ dbg_prim,
+                                    uint32_t dbg_npx) {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
     const int pix = pixel[s];
     if (pix < 0) return;
-    const float4 l = radiance[s];
-    const uint32_t at = jobs[slot_job[s]].px_base + (uint32_t)pix;
+    const JobDev& J = p.jobs[slot_job[s]];
+    const bool on = alive[s] != 0;
+    const float4 r4 = radiance[s];
+    float3 L = make_float3(r4.x, r4.y, r4.z);
+    if (on) {
+        const SceneDev& sc = p.scenes[J.scene];
+        const int2 h = hit[s];
+        const float4 bt = beta[s];
+        if (dbg_prim)
+            dbg_prim[(p.bounce - 1) * dbg_npx + (uint32_t)pix] =
+                h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
+        if (h.x < 0) {
+            add_environment(sc, bt, L);
+        } else {
+            const float4 v1 = __ldg(&sc.tris[3 * h.x + 1]);
+            const int mat = __float_as_int(v1.w);
+            const float4 m0 = __ldg(&sc.mats[2 * mat + 0]);
+            if ((uint32_t)__float_as_int(m0.x) == kMatEmitter) {
+                const float4 v0 = __ldg(&sc.tris[3 * h.x + 0]);
+                const float4 v2 = __ldg(&sc.tris[3 * h.x + 2]);
+                const float4 m1 = __ldg(&sc.mats[2 * mat + 1]);
+                add_emission(sc, v0, v1, v2, m1, bt, h, ray_d[s], J.nee != 0, L);
+            }
+        }
+    }
+    const uint32_t at = J.px_base + (uint32_t)pix;
     float4 a = accum[at];
-    a.x += l.x;
-    a.y += l.y;
-    a.z += l.z;
+    a.x += L.x;
+    a.y += L.y;
+    a.z += L.z;
     accum[at] = a;
 }
 
@@ -1332,9 +1375,12 @@ void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t 
     lc.n += 3;
 }
 
-void launch_accumulate(const PassArgs& p, PathBuffers& b, cudaStream_t st, LaunchCount& lc) {
+void launch_finish_accumulate(const PassArgs& p, PathBuffers& b, const cr_debug* dbg, cudaStream_t st,
+                              LaunchCount& lc) {
     const uint32_t n_slots = p.n_tiles * p.m;
-    k_accumulate<<<(n_slots + 255) / 256, 256, 0, st>>>(b.pixel, b.slot_job, p.jobs, b.radiance, n_slots, b.accum);
+    k_finish_accumulate<<<(n_slots + 255) / 256, 256, 0, st>>>(p, b.pixel, b.slot_job, b.alive, b.hit, b.ray_d,
+                                                               b.beta, b.radiance, n_slots, b.accum,
+                                                               dbg ? dbg->prim : nullptr, p.npx);
     lc.n++;
 }
 
