@@ -647,6 +647,7 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
             d.seed = j.seed;
             d.out = j.out_rgb;
             d.inv_spp = 1.0f / (float)j.spp;
+            d.sample_flags = (p == 0 ? 1u : 0u) | (p + 1 == j.spp ? 2u : 0u);
             const uint64_t t64 = (uint64_t)tiles + (uint64_t)d.tiles_x * tiles_y;
             if (t64 * m > (1ull << 27)) return fail(CR_ERR_INVALID_ARG, "pass %u: too many slots", p);
             tiles = (uint32_t)t64;
@@ -703,7 +704,11 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         if (e != cudaSuccess && failst == CR_OK) failst = fail(CR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     };
     check(cudaMemsetAsync(b.counts, 0, 4 * kCountsWords, stream), "memset counts");
-    if (eo.clear_accum) check(cudaMemsetAsync(b.accum, 0, 16 * (size_t)p.npx_total, stream), "memset accum");
+    // a fresh render writes its first samples' sums and its outputs from the accumulation
+    // kernel; otherwise (the server's resident sums) the buffer is cleared / output as asked
+    const bool fused_out = eo.clear_accum && eo.write_output;
+    if (eo.clear_accum && !fused_out)
+        check(cudaMemsetAsync(b.accum, 0, 16 * (size_t)p.npx_total, stream), "memset accum");
     TraceArgs ta;
     ta.ray_o = b.ray_o;
     ta.ray_d = b.ray_d;
@@ -729,6 +734,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         P.n_tiles = ps.n_tiles;
         P.npx = eo.debug_npx;
         P.nee = p.nee;
+        P.accum_mode = fused_out ? 3u : 0u;
         const uint32_t n_slots = ps.n_tiles * p.m;
         b.n_groups = n_slots / p.k;
         ev.begin(stream, times ? &times->raygen : &dummy);
@@ -782,7 +788,8 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         ev.end();
     }
     // pass 0 holds every job (spp >= 1), with the px_base and output of each
-    if (eo.write_output) launch_output(dev.d_jobs, p.passes[0].n_jobs, b.accum, p.npx_total, stream, lc);
+    if (eo.write_output && !fused_out)
+        launch_output(dev.d_jobs, p.passes[0].n_jobs, b.accum, p.npx_total, stream, lc);
     check(cudaGetLastError(), "launch");
     if (times) {
         // the caller synchronises the stream before reading; resolve needs completed events

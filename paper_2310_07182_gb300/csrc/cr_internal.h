@@ -117,6 +117,7 @@ struct JobDev {
     uint32_t world_mask;  // bit b: world-space direct reuse (Sec. 3.1 ablation) at bounce b
     uint32_t nee;         // 1: next-event estimation, 2: with light points shared per group
     uint32_t hybrid_donor; // 1: hybrid groups reuse the first diffuse member's sample
+    uint32_t sample_flags; // bit 0: this pass is the job's first sample, bit 1: its last
 };
 
 // Launch-uniform description of a pass.
@@ -129,6 +130,9 @@ struct PassArgs {
     uint32_t bounce = 0;   // shade: 1..B (B + 1 = final)
     uint32_t npx = 0;      // pixels of the debug capture (single-job renders)
     bool nee = false;      // some job of the plan uses next-event estimation
+    // bit 0: a job's first sample writes its pixel sums without reading them (the buffer is
+    // not cleared first); bit 1: its last sample writes the output instead of the sums
+    uint32_t accum_mode = 0;
 };
 
 // Per-call launch statistics.

@@ -1160,7 +1160,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // End of a pass, one thread per slot: a path still alive after its last secondary ray
 // only adds the environment or the emission where that ray ended (no group logic is left
 // to do), then the sample's radiance goes to its pixel.  Each pixel has one slot per pass
-// and passes run in sample order, so the sum keeps that order.
+// and passes run in sample order, so the sum keeps that order.  With p.accum_mode, a job's
+// first sample starts the sum (no cleared buffer is read) and its last sample writes the
+// output, sum / spp, instead of the sum.
 __global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixel,
                                     const uint16_t* __restrict__ slot_job, const uint8_t* __restrict__ alive,
                                     const int2* __restrict__ hit, const float4* __restrict__ ray_d,
@@ -1197,11 +1199,19 @@ __global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixe
         }
     }
     const uint32_t at = J.px_base + (uint32_t)pix;
-    float4 a = accum[at];
+    const bool first = (p.accum_mode & 1u) && (J.sample_flags & 1u);
+    const bool last = (p.accum_mode & 2u) && (J.sample_flags & 2u);
+    float4 a = first ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : accum[at];
     a.x += L.x;
     a.y += L.y;
     a.z += L.z;
-    accum[at] = a;
+    if (last) {
+        J.out[3 * pix + 0] = a.x * J.inv_spp;
+        J.out[3 * pix + 1] = a.y * J.inv_spp;
+        J.out[3 * pix + 2] = a.z * J.inv_spp;
+    } else {
+        accum[at] = a;
+    }
 }
 
 // Job of an accumulation pixel: the last job whose first pixel is <= i.
