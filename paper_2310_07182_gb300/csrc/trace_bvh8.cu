@@ -17,8 +17,8 @@ namespace {
 // low / high planes per axis.  Children sit in slots by the octant of their centroid, so
 // visiting slot i ^ octant(d) for i = 0..7 goes roughly near to far without sorting.
 //
-// One iteration intersects one node: the 8 children are decoded (origin + q * step, exact
-// product, one rounded add, conservative by construction) and slab-tested; hit inner
+// One iteration intersects one node: the 8 children are slab-tested straight from their
+// bytes (one FMA per plane, with error bounds that keep the test conservative); hit inner
 // children form a bit mask in visiting order, hit leaves a mask of their triangles, which
 // are tested at once.  The nearest inner child is visited next and the rest of the mask is
 // pushed as one (first child, mask) entry, so the stack holds at most one entry per tree
@@ -38,6 +38,7 @@ __device__ __forceinline__ void octant_order(uint32_t& lo, uint32_t& hi, uint32_
     hi = __byte_perm(hi, 0u, sel);
 }
 
+// byte i of the 8-byte field (lo, hi) as a float (exact)
 template <int i>
 __device__ __forceinline__ float qbyte(uint32_t lo, uint32_t hi) {
     return __uint2float_rn(((i < 4 ? lo : hi) >> (8 * (i & 3))) & 0xffu);
@@ -80,19 +81,50 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
         octant_order(hy_lo, hy_hi, oct, sel);
         octant_order(hz_lo, hz_hi, oct, sel);
         const float tcull = __fmul_rn(best.t, kCullWiden);
+        // Plane distances straight from the bytes: a plane at origin + q * step meets the ray
+        // at fma(q, a, b) with a = step / d (exact, step is a power of two) and
+        // b = (origin - o) / d.  Against the decoded plane fl(origin + q * step), whose box
+        // the builder makes contain the child, this is off by at most a relative 2^-23 plus
+        // 2^-23 |1/d| (|origin| + 255 step + |origin - o|); b is biased by twice that, down
+        // for the entry plane and up for the exit plane, and the exit widened as in the
+        // BVH2 test, so no child box the decoded form would enter is rejected (2^-100 more
+        // covers a step / d that falls into the subnormal range).
+        float ax, ay, az, blx, bhx, bly, bhy, blz, bhz;
+        {
+            const float dx = __fsub_rn(ox, r.ox), dy = __fsub_rn(oy, r.oy), dz = __fsub_rn(oz, r.oz);
+            ax = __fmul_rn(sx, r.ix);
+            ay = __fmul_rn(sy, r.iy);
+            az = __fmul_rn(sz, r.iz);
+            const float bx = __fmul_rn(dx, r.ix), by = __fmul_rn(dy, r.iy), bz = __fmul_rn(dz, r.iz);
+            const float ex = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn(fabsf(ox), __fmul_rn(255.0f, sx)), fabsf(dx)),
+                                                 fabsf(r.ix)), 0x1.0p-22f) + 0x1.0p-100f;
+            const float ey = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn(fabsf(oy), __fmul_rn(255.0f, sy)), fabsf(dy)),
+                                                 fabsf(r.iy)), 0x1.0p-22f) + 0x1.0p-100f;
+            const float ez = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn(fabsf(oz), __fmul_rn(255.0f, sz)), fabsf(dz)),
+                                                 fabsf(r.iz)), 0x1.0p-22f) + 0x1.0p-100f;
+            // the low plane is the entry one where 1/d >= 0
+            blx = r.ix >= 0.0f ? __fsub_rn(bx, ex) : __fadd_rn(bx, ex);
+            bhx = r.ix >= 0.0f ? __fadd_rn(bx, ex) : __fsub_rn(bx, ex);
+            bly = r.iy >= 0.0f ? __fsub_rn(by, ey) : __fadd_rn(by, ey);
+            bhy = r.iy >= 0.0f ? __fadd_rn(by, ey) : __fsub_rn(by, ey);
+            blz = r.iz >= 0.0f ? __fsub_rn(bz, ez) : __fadd_rn(bz, ez);
+            bhz = r.iz >= 0.0f ? __fadd_rn(bz, ez) : __fsub_rn(bz, ez);
+        }
         uint32_t hits = 0, trimask = 0;
 #define CR_BVH8_CHILD(i)                                                                                  \
     {                                                                                                     \
         const uint32_t meta = ((i < 4 ? m_lo : m_hi) >> (8 * (i & 3))) & 0xffu;                         \
         const bool inner = (imask >> ((uint32_t)(i) ^ oct)) & 1u;                                         \
         if (inner || meta >= 32u) {                                                                       \
-            float t;                                                                                      \
-            if (box_hit_fma(r, __fadd_rn(ox, __fmul_rn(qbyte<i>(lx_lo, lx_hi), sx)),                      \
-                            __fadd_rn(ox, __fmul_rn(qbyte<i>(hx_lo, hx_hi), sx)),                         \
-                            __fadd_rn(oy, __fmul_rn(qbyte<i>(ly_lo, ly_hi), sy)),                         \
-                            __fadd_rn(oy, __fmul_rn(qbyte<i>(hy_lo, hy_hi), sy)),                         \
-                            __fadd_rn(oz, __fmul_rn(qbyte<i>(lz_lo, lz_hi), sz)),                         \
-                            __fadd_rn(oz, __fmul_rn(qbyte<i>(hz_lo, hz_hi), sz)), tcull, t)) {            \
+            const float tlx = fmaf(qbyte<i>(lx_lo, lx_hi), ax, blx);                                      \
+            const float thx = fmaf(qbyte<i>(hx_lo, hx_hi), ax, bhx);                                      \
+            const float tly = fmaf(qbyte<i>(ly_lo, ly_hi), ay, bly);                                      \
+            const float thy = fmaf(qbyte<i>(hy_lo, hy_hi), ay, bhy);                                      \
+            const float tlz = fmaf(qbyte<i>(lz_lo, lz_hi), az, blz);                                      \
+            const float thz = fmaf(qbyte<i>(hz_lo, hz_hi), az, bhz);                                      \
+            const float tn = max3f(fminf(tlx, thx), fminf(tly, thy), fmaxf(fminf(tlz, thz), 0.0f));       \
+            const float tf = min3f(fmaxf(tlx, thx), fmaxf(tly, thy), fmaxf(tlz, thz));                    \
+            if (tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull) {                                          \
                 if (inner) hits |= 1u << (i);                                                             \
                 else trimask |= ((1u << (meta >> 5)) - 1u) << (meta & 31u);                               \
             }                                                                                             \
