@@ -330,12 +330,15 @@ def test_host_outputs_match_the_device_output(cr):
     sc = scenes.interior(width=96, height=64)
     S = cr.Scene(sc)
     kw = dict(spp=2, max_bounces=2, tile=(8, 8), k=8, seed=2)
-    dev, _ = S.render(**kw)
+    dev, sd = S.render(stats=True, **kw)
     pinned = torch.zeros((64, 96, 3), dtype=torch.float32).pin_memory()
-    S.render(out=pinned, **kw)
+    _, sp = S.render(out=pinned, stats=True, **kw)
     pageable = np.zeros((64, 96, 3), np.float32)
     S.render(out=pageable, **kw)
     assert torch.equal(pinned, dev.cpu()) and np.array_equal(pageable, dev.cpu().numpy())
+    # the call's host-device bytes: the job and scene tables up, the image down for a host output
+    assert sd["h2d_bytes"] == sp["h2d_bytes"] > 0
+    assert sd["d2h_bytes"] == 0 and sp["d2h_bytes"] == 64 * 96 * 12
 
 
 @pytest.mark.parametrize("k,tile,nee", [(8, (8, 8), False), (32, (8, 8), True), (64, (8, 8), False),
