@@ -1,6 +1,7 @@
 // cr_api.cpp -- the C ABI of libcr.so (include/cr.h): argument checking, scene upload,
 // render orchestration of the wavefront stages on one stream, and the parity entry points.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <cmath>
@@ -403,7 +404,10 @@ struct StageEvents {
         return e;
     }
     bool traces_only = false; // record only the trace stages (fewer event records in the step)
-    void begin(cudaStream_t s, double* acc, bool is_trace = false) {
+    // Every stage is also an NVTX range named after it (host enqueue time; a no-op unless a
+    // tool is attached), so profilers can filter by stage.
+    void begin(cudaStream_t s, double* acc, const char* name, bool is_trace = false) {
+        nvtxRangePushA(name);
         if (!on || (traces_only && !is_trace)) return;
         st = s;
         cudaEvent_t e = get();
@@ -412,6 +416,7 @@ struct StageEvents {
         marks.emplace_back(pool.size() - 1, acc);
     }
     void end() {
+        nvtxRangePop();
         if (!on || marks.empty() || marks.back().first != pool.size() - 1) return;
         cudaEvent_t e = get();
         if (e) cudaEventRecord(e, st);
@@ -737,7 +742,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         P.accum_mode = fused_out ? 3u : 0u;
         const uint32_t n_slots = ps.n_tiles * p.m;
         b.n_groups = n_slots / p.k;
-        ev.begin(stream, times ? &times->raygen : &dummy);
+        ev.begin(stream, times ? &times->raygen : &dummy, "cr raygen");
         launch_raygen(P, b, stream, lc);
         ev.end();
         ta.queue = primary_pixel_order() ? b.ray_queue : nullptr; // written by raygen: pixel order per tile
@@ -746,22 +751,22 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         ta.counters = nullptr;
         if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
         ta.packet = eo.packet_primary;
-        ev.begin(stream, times ? &times->trace_primary : &dummy, true);
+        ev.begin(stream, times ? &times->trace_primary : &dummy, "cr trace primary", true);
         launch_trace(ta, stream, lc);
         ev.end();
         ta.packet = eo.packet_secondary;
         for (uint32_t bnc = 1; bnc <= p.max_bounces; ++bnc) {
             P.bounce = bnc;
-            ev.begin(stream, times ? &times->shade : &dummy);
+            ev.begin(stream, times ? &times->shade : &dummy, "cr shade");
             launch_shade(P, b, bnc == 1, !eo.ordered_queues, eo.debug, stream, lc);
             ev.end();
             if (P.nee && b.shadow_d) {
-                ev.begin(stream, times ? &times->trace_shadow : &dummy, true);
+                ev.begin(stream, times ? &times->trace_shadow : &dummy, "cr trace shadow", true);
                 launch_shadow(P, b, bnc == 1, p.bvh8, stream, lc);
                 ev.end();
             }
             if (eo.ordered_queues) {
-                ev.begin(stream, times ? &times->compact : &dummy);
+                ev.begin(stream, times ? &times->compact : &dummy, "cr compact");
                 launch_compact(P, b, bnc == 1, stream, lc);
                 ev.end();
             }
@@ -769,7 +774,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             ta.queue_count = b.counts + 8 + 2 * bnc;
             ta.n_max = n_slots;
             if (p.sort) {
-                ev.begin(stream, times ? &times->sort : &dummy);
+                ev.begin(stream, times ? &times->sort : &dummy, "cr sort");
                 ta.queue = launch_morton_sort(P, b, bnc, eo.sort_key, stream, lc);
                 ev.end();
             }
@@ -778,12 +783,12 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
             ta.two_phase = eo.phase_budget > 0 && ws.phase.state;
             ta.phase = ws.phase;
             ta.phase.budget = eo.phase_budget;
-            ev.begin(stream, times ? &times->trace_secondary : &dummy, true);
+            ev.begin(stream, times ? &times->trace_secondary : &dummy, "cr trace secondary", true);
             launch_trace(ta, stream, lc);
             ev.end();
         }
         P.bounce = p.max_bounces + 1;
-        ev.begin(stream, times ? &times->accum : &dummy);
+        ev.begin(stream, times ? &times->accum : &dummy, "cr accumulate");
         launch_finish_accumulate(P, b, eo.debug, stream, lc);
         ev.end();
     }
