@@ -404,6 +404,22 @@ def furnace(albedo=(0.5, 0.5, 0.5), env=(1.0, 1.0, 1.0), subdiv=2, width=32, hei
     return _finish("furnace", tris, np.zeros(n), [MAT_LAMBERT], params, env, cam)
 
 
+def mixed_furnace(width=32, height=32) -> Scene:
+    """A convex icosphere whose triangles alternate Lambert (albedo 0.5, 0.25, 0.75) with GGX
+    (roughness 0.3) and mirror, in a uniform unit environment: every exit direction above a
+    point escapes, so a Lambert point is exactly albedo * env whichever direction it takes,
+    while most reuse groups are hybrid."""
+    tris = icosphere(2)
+    n = tris.shape[0]
+    params = np.zeros((3, 7))
+    params[0, 0:3] = (0.5, 0.25, 0.75)
+    params[1, 0:4] = (0.8, 0.7, 0.6, 0.3)
+    params[2, 0:3] = (0.9, 0.9, 0.9)
+    cam = Camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, width, height)
+    mat = np.array([0 if i % 2 == 0 else (1 if i % 4 == 1 else 2) for i in range(n)])
+    return _finish("mixed_furnace", tris, mat, [MAT_LAMBERT, MAT_GGX, MAT_MIRROR], params, (1.0, 1.0, 1.0), cam)
+
+
 def split_plane(width=32, height=32, left=MAT_LAMBERT, right=MAT_GGX, n_strips=1) -> Scene:
     """A plane z=0 seen head-on (orthogonal to the view axis) whose left half (x>0 seen from
     the camera at z=-2) is material ``left`` and right half ``right``; used to predict group

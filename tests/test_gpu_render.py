@@ -356,3 +356,26 @@ def test_appended_and_ordered_queues_render_the_same(cr, k, tile, nee):
     for key in ("secondary_rays", "secondary_rays_b1", "shadow_rays"):
         assert sa[key] == sb[key], key
     assert sa["secondary_rays"] > 0 and sa["ms_compact"] == 0.0 and sb["ms_compact"] > 0.0
+
+
+@pytest.mark.parametrize("hybrid_donor", [False, True])
+def test_hybrid_weight_reading_in_a_mixed_furnace_on_gpu(cr, hybrid_donor):
+    """The hybrid rule's weight reading on the GPU: in the mixed furnace every Lambert pixel
+    is exactly its albedo (diffuse members weigh any taken direction by f cos / p_cos),
+    and glossy pixels equal independent sampling's bit for bit."""
+    sc = scenes.mixed_furnace()
+    S = cr.Scene(sc)
+    B = 1
+    kw = dict(spp=1, max_bounces=B, tile=(4, 4), k=16, seed=5)
+    dbg, bufs = cr.debug_buffers(sc.camera.width, sc.camera.height, B)
+    img, _ = S.render(mode="direction_reuse", hybrid_donor=hybrid_donor, debug=dbg, **kw)
+    ind, _ = S.render(mode="independent", **kw)
+    cls = bufs["cls"][0].cpu().numpy()
+    cat = bufs["cat"][0].cpu().numpy()
+    rgb = img.cpu().numpy().reshape(-1, 3)
+    lam = cls == 1
+    assert (lam & (cat == 3)).sum() > 100
+    assert (rgb[lam] == np.float32([0.5, 0.25, 0.75])).all()
+    glossy = cls == 2
+    assert glossy.sum() > 20
+    assert np.array_equal(rgb[glossy], ind.cpu().numpy().reshape(-1, 3)[glossy])

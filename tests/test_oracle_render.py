@@ -42,6 +42,31 @@ def test_white_furnace_exact(orc, furnace, mode, k, interleave, bounces):
         assert r["taint"].sum() == 0
 
 
+@pytest.mark.parametrize("hybrid_donor", [False, True])
+def test_hybrid_weight_reading_in_a_mixed_furnace(orc, hybrid_donor):
+    """Reading of the hybrid rule's weight (Sec. 3.2 gives none): a diffuse member that takes
+    the group's average glossy direction weighs it by its own material, f cos / p_cos =
+    albedo.  In a mixed furnace that makes every Lambert pixel exactly albedo, in diffuse
+    and in hybrid groups alike; glossy members keep their own samples (their pixels equal
+    independent sampling's, bit for bit)."""
+    sc = scenes.mixed_furnace()
+    S = orc.Scene(sc)
+    alb = np.float32([0.5, 0.25, 0.75]).astype(np.float64)
+    kw = dict(spp=1, max_bounces=1, tile=(4, 4), k=16, seed=5)
+    r = orc.render(S, sc.camera, mode="direction_reuse", debug=True, hybrid_donor=hybrid_donor, **kw)
+    ind = orc.render(S, sc.camera, mode="independent", debug=True, **kw)
+    cls, cat = r["dbg_cls"][0], r["dbg_cat"][0]
+    rgb = r["rgb"].reshape(-1, 3)
+    lam = cls == 1
+    hybrid_lam = lam & (cat == 3)
+    assert hybrid_lam.sum() > 100
+    assert (rgb[lam] == alb).all()
+    glossy = cls == 2
+    assert glossy.sum() > 20
+    assert np.array_equal(rgb[glossy], ind["rgb"].reshape(-1, 3)[glossy])
+    assert r["taint"].sum() == 0
+
+
 def test_world_space_reuse_fails_furnace(orc, furnace):
     """Sec. 3.1: reusing a world-space direction sends some rays below the surface; the
     furnace detects it (the test that the tangent-space method passes)."""
