@@ -53,7 +53,7 @@ class _Params(C.Structure):
     _fields_ = [("spp", C.c_uint32), ("max_bounces", C.c_uint32), ("mode", C.c_uint32),
                 ("tile_w", C.c_uint32), ("tile_h", C.c_uint32), ("k", C.c_uint32),
                 ("interleave", C.c_uint32), ("frame_base", C.c_uint32), ("reuse_depth", C.c_uint32),
-                ("opts", C.c_uint32), ("seed", C.c_uint64)]
+                ("opts", C.c_uint32), ("seed", C.c_uint64), ("diffuse_roughness", C.c_float)]
 
 
 class _Outputs(C.Structure):
@@ -247,7 +247,7 @@ def trace(scene: Scene, rays, skip=None, use_bvh=True):
 
 def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=None,
            interleave=True, seed=0, frame_base=0, reuse_depth=0, debug=False, threads=None,
-           tiles=None, accum=None, nee=False, hybrid_donor=False, nee_shared=False):
+           tiles=None, accum=None, nee=False, hybrid_donor=False, nee_shared=False, diffuse_roughness=0.0):
     """Run the oracle path tracer.  Returns a dict with ``rgb`` (mean radiance, float64 h x w x 3),
     ``taint`` (h x w uint8), ``counters`` and, with debug=True (spp 1), per-bounce arrays.
     ``tiles`` = (begin, end) restricts the work to a tile range (other pixels stay 0).
@@ -256,7 +256,9 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
     sample and shadow ray per non-specular shading point).  ``hybrid_donor`` makes the diffuse
     members of hybrid groups reuse the first diffuse member's own sample instead of the
     average glossy direction (an unbiased option).  ``nee_shared`` (with ``nee``) makes the
-    members of a group join one light point."""
+    members of a group join one light point.  ``diffuse_roughness`` > 0 puts GGX points of at
+    least that roughness in the diffuse class where directions are reused (cosine samples,
+    weight pi f)."""
     W, H = tile
     K = W * H if k is None else k
     w, h = cam.width, cam.height
@@ -277,7 +279,7 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
                    cam.vfov_deg, w, h)
     par = _Params(spp, B, MODES[mode] if isinstance(mode, str) else mode, W, H, K, int(interleave),
                   frame_base, reuse_depth, (1 if nee else 0) | (2 if hybrid_donor else 0) | (4 if nee_shared else 0),
-                  seed)
+                  seed, float(diffuse_roughness))
     nthreads = threads or max(1, min(os.cpu_count() or 1, t1 - t0))
     bounds = np.linspace(t0, t1, nthreads + 1).astype(int)
     counters = np.zeros((nthreads, 5), dtype=np.uint64)

@@ -897,6 +897,7 @@ typedef struct {
     /* shading point */
     f3 n, T, B, wo;
     int cls;
+    int cosgl;   /* a GGX point in the diffuse class while reusing: cosine sampling, pi f weights */
     uint32_t mat;
     /* direction chosen at this step */
     f3 wl;
@@ -906,7 +907,7 @@ typedef struct {
     int front;   /* the incoming ray met the triangle's front face (cross(v1-v0, v2-v0) side) */
 } pstate;
 
-static void shade_setup(const orc_scene* s, pstate* ps) {
+static void shade_setup(const orc_scene* s, pstate* ps, float diffuse_roughness, int reuse_now) {
     const float* v = &s->v[9 * ps->hit];
     f3 v0 = f3m(v[0], v[1], v[2]), v1 = f3m(v[3], v[4], v[5]), v2 = f3m(v[6], v[7], v[8]);
     f3 ng = f3normalize(f3cross(f3sub(v1, v0), f3sub(v2, v0)));
@@ -922,7 +923,23 @@ static void shade_setup(const orc_scene* s, pstate* ps) {
     /* Transmission (the paper's future work, Sec. 6): a Lambertian transmitter joins the
      * diffuse class with its lobe in the lower hemisphere; a smooth dielectric is specular. */
     ps->cls = (ty == MAT_LAMBERT || ty == MAT_TRANSLUCENT) ? CLS_DIFFUSE : CLS_GLOSSY;
+    /* roughness threshold of the classes: a rough GGX point joins the diffuse class */
+    const int rough = ty == MAT_GGX && diffuse_roughness > 0.0f &&
+                      s->mat_params[7 * ps->mat + 3] >= diffuse_roughness;
+    if (rough) ps->cls = CLS_DIFFUSE;
+    ps->cosgl = rough && reuse_now;
     ps->hemi = ty == MAT_TRANSLUCENT ? -1.0f : 1.0f;
+}
+
+/* Weight pi f(wo, wi) (= f cos / p_cos) of a cosine-class GGX point for the tangent-space
+ * direction wl; the direction is usable when both it and wo lie above the surface. */
+static void rough_weight(const orc_scene* s, pstate* ps, f3 wl) {
+    const float* mp = &s->mat_params[7 * ps->mat];
+    float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z}, wi[3] = {wl.x, wl.y, wl.z};
+    double f[3];
+    orc_eval_ggx(wo, wi, mp[3], mp, f);
+    for (int k = 0; k < 3; ++k) ps->w[k] = (float)(PI_D * f[k]);
+    ps->valid = wl.z > 0.0f && ps->wo.z > 0.0f;
 }
 
 /* Smooth dielectric (IOR eta inside, 1 outside; the inside lies behind the front face):
@@ -972,6 +989,10 @@ static void own_sample(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
         ps->wl = f3m(wl[0], wl[1], wl[2]);
         for (int k = 0; k < 3; ++k) ps->w[k] = mp[k];
         ps->valid = 1;
+    } else if (ps->cosgl) { /* a GGX point of the diffuse class: cosine sample, pi f weight */
+        orc_sample_cosine(u1, u2, wl);
+        ps->wl = f3m(wl[0], wl[1], wl[2]);
+        rough_weight(s, ps, ps->wl);
     } else if (ty == MAT_GGX) {
         float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z};
         ps->valid = orc_sample_ggx(wo, mp[3], mp, u1, u2, wl, ps->w);
@@ -997,6 +1018,10 @@ static void own_sample(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
 static void take_direction(const orc_scene* s, pstate* ps, f3 wl) {
     const float* mp = &s->mat_params[7 * ps->mat];
     ps->wl = wl;
+    if (ps->cosgl) {
+        rough_weight(s, ps, wl);
+        return;
+    }
     for (int k = 0; k < 3; ++k) ps->w[k] = mp[k]; /* Lambert: f cos / p_cos = albedo */
     ps->valid = 1;
 }
@@ -1026,6 +1051,7 @@ static double bsdf_pdf(const orc_scene* s, const pstate* ps, f3 wl) {
     uint32_t ty = s->mat_type[ps->mat];
     if (ty == MAT_LAMBERT) return wl.z > 0.0f ? (double)wl.z / PI_D : 0.0;
     if (ty == MAT_TRANSLUCENT) return wl.z < 0.0f ? -(double)wl.z / PI_D : 0.0;
+    if (ps->cosgl) return wl.z > 0.0f ? (double)wl.z / PI_D : 0.0;
     if (ty == MAT_GGX) {
         float wo[3] = {ps->wo.x, ps->wo.y, ps->wo.z}, wi[3] = {wl.x, wl.y, wl.z};
         return orc_pdf_ggx(wo, wi, s->mat_params[7 * ps->mat + 3]);
@@ -1208,7 +1234,9 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         ps->alive = 0;
                         continue;
                     }
-                    shade_setup(s, ps);
+                    shade_setup(s, ps, p->diffuse_roughness,
+                                (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
+                                    (p->reuse_depth == 0 || b <= p->reuse_depth));
                 }
                 /* next-event estimation at the shading points; with shared light samples
                  * every member of a group joins the point drawn from the stream of the

@@ -110,6 +110,11 @@ typedef struct {
     uint32_t frame_base, reuse_depth; /* reuse at bounces b <= reuse_depth; 0 = all */
     uint32_t opts;                    /* ORC_OPT_* bits */
     uint64_t seed;
+    /* Roughness threshold of the reuse classes (a knob the paper leaves open, Sec. 3.2): with
+     * diffuse_roughness > 0 a GGX point of roughness >= it joins the diffuse class where
+     * directions are reused; it then draws a cosine sample and weighs any direction it takes
+     * by f cos / p_cos = pi f.  0: classes by material type only. */
+    float diffuse_roughness;
 } orc_params;
 
 typedef struct {
