@@ -199,6 +199,10 @@ typedef struct {
     uint32_t flags;        /* CR_OPT_* */
     uint32_t sort_key;     /* cr_sort_key of CR_MORTON_SORT (default TwoPoint) */
     uint32_t stack;        /* BVH2 traversal stack entries per thread in shared memory: 8, 16 or 32 (0 = 16) */
+    float diffuse_roughness; /* > 0: GGX of at least this roughness joins the diffuse class
+                              * of the reuse groups (cosine samples weighted pi f while
+                              * directions are reused; independent sampling is unchanged);
+                              * 0: classes by material type (Sec. 3.2).  Finite, >= 0. */
     void* stream;          /* cudaStream_t to run on; NULL = legacy default stream */
     cr_stats* stats;       /* optional, host */
     cr_debug* debug;       /* optional, host struct of device pointers */
@@ -251,7 +255,8 @@ typedef struct {
     uint32_t frame_base;
     uint32_t flags;      /* CR_JOB_* */
     float* out_rgb;      /* DEVICE buffer of width*height*3 floats */
-} cr_job;                /* 96 bytes */
+    float diffuse_roughness; /* as in cr_render_opts (0: classes by material type) */
+} cr_job;                /* 104 bytes */
 
 /* Next-event estimation (a standard path-tracing estimator the paper does not discuss; it
  * leaves the reuse of exit directions unchanged).  At every shading point that is not a

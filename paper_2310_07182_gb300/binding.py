@@ -90,7 +90,7 @@ class cr_debug(C.Structure):
 class cr_job(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("camera", cr_camera), ("spp", C.c_uint32), ("max_bounces", C.c_uint32),
                 ("mode", C.c_uint32), ("reuse_depth", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
-                ("flags", C.c_uint32), ("out_rgb", C.c_void_p)]
+                ("flags", C.c_uint32), ("out_rgb", C.c_void_p), ("diffuse_roughness", C.c_float)]
 
 
 class cr_batch_opts(C.Structure):
@@ -125,7 +125,8 @@ class cr_server_stats(C.Structure):
 class cr_render_opts(C.Structure):
     _fields_ = [("k", C.c_uint32), ("interleave", C.c_uint32), ("seed", C.c_uint64), ("frame_base", C.c_uint32),
                 ("reuse_depth", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32),
-                ("sort_key", C.c_uint32), ("stack", C.c_uint32), ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
+                ("sort_key", C.c_uint32), ("stack", C.c_uint32), ("diffuse_roughness", C.c_float),
+                ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
                 ("debug", C.POINTER(cr_debug))]
 
 
@@ -265,13 +266,14 @@ SORT_KEYS = {"two_point": 0, "origin": 1, "reis": 2, "costa": 3, "aila_compact":
 
 
 def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_BVH2, block=0, flags=0,
-              stream=None, stats=None, debug=None, sort_key=0, stack=0) -> cr_render_opts:
+              stream=None, stats=None, debug=None, sort_key=0, stack=0, diffuse_roughness=0.0) -> cr_render_opts:
     o = cr_render_opts()
     _check(lib().cr_render_opts_default(C.byref(o)))
     o.k, o.interleave, o.seed, o.frame_base = k, int(interleave), seed, frame_base
     o.reuse_depth, o.bvh, o.block, o.flags = reuse_depth, bvh, block, flags
     o.sort_key = SORT_KEYS.get(sort_key, sort_key)
     o.stack = stack
+    o.diffuse_roughness = float(diffuse_roughness)
     o.stream = stream
     if stats is not None:
         o.stats = C.pointer(stats)
@@ -308,7 +310,7 @@ CR_BATCH_GRAPH = 1
 
 
 def make_job(scene_handle, cam, out, spp=1, max_bounces=1, mode="direction_reuse", reuse_depth=0, seed=0,
-             frame_base=0, nee=False, hybrid_donor=False, nee_shared=False) -> cr_job:
+             frame_base=0, nee=False, hybrid_donor=False, nee_shared=False, diffuse_roughness=0.0) -> cr_job:
     j = cr_job()
     j.flags = ((CR_JOB_NEE if nee else 0) | (CR_JOB_HYBRID_DONOR if hybrid_donor else 0)
                | (CR_JOB_NEE_SHARED if nee_shared else 0))
@@ -317,6 +319,7 @@ def make_job(scene_handle, cam, out, spp=1, max_bounces=1, mode="direction_reuse
     j.spp, j.max_bounces, j.mode, j.reuse_depth = spp, max_bounces, MODES.get(mode, mode), reuse_depth
     j.seed, j.frame_base = seed, frame_base
     j.out_rgb = _ptr(out)
+    j.diffuse_roughness = float(diffuse_roughness)
     return j
 
 
@@ -463,7 +466,8 @@ class Scene:
 
     def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
                seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
-               debug=None, stream=None, sort_key=0, nee=False, stack=0, hybrid_donor=False, nee_shared=False):
+               debug=None, stream=None, sort_key=0, nee=False, stack=0, hybrid_donor=False, nee_shared=False,
+               diffuse_roughness=0.0):
         """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
         CUDA tensor by default).  Returns (out, stats dict or None)."""
         import torch
@@ -474,7 +478,8 @@ class Scene:
         o = make_opts(k=k, interleave=interleave, seed=seed, frame_base=frame_base, reuse_depth=reuse_depth, bvh=bvh,
                       block=block, flags=flags | (CR_OPT_STATS if stats else 0) | (CR_OPT_NEE if nee else 0)
                       | (CR_OPT_HYBRID_DONOR if hybrid_donor else 0) | (CR_OPT_NEE_SHARED if nee_shared else 0),
-                      stream=stream, stats=st, debug=debug, sort_key=sort_key, stack=stack)
+                      stream=stream, stats=st, debug=debug, sort_key=sort_key, stack=stack,
+                      diffuse_roughness=diffuse_roughness)
         cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
         return out, (st.as_dict() if st is not None else None)
 

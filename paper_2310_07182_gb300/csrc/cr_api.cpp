@@ -573,6 +573,8 @@ cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h) {
     if (j.mode > CR_WORLD_REUSE) return fail(CR_ERR_INVALID_ARG, "unknown mode %u", j.mode);
     if (j.flags & ~(uint32_t)(CR_JOB_NEE | CR_JOB_HYBRID_DONOR | CR_JOB_NEE_SHARED))
         return fail(CR_ERR_INVALID_ARG, "unknown job flags 0x%x", j.flags);
+    if (!(j.diffuse_roughness >= 0.0f) || !std::isfinite(j.diffuse_roughness))
+        return fail(CR_ERR_INVALID_ARG, "diffuse_roughness %g not finite and >= 0", (double)j.diffuse_roughness);
     (void)tile_w;
     (void)tile_h;
     return CR_OK;
@@ -653,6 +655,7 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
             d.out = j.out_rgb;
             d.inv_spp = 1.0f / (float)j.spp;
             d.sample_flags = (p == 0 ? 1u : 0u) | (p + 1 == j.spp ? 2u : 0u);
+            d.diffuse_rough = j.diffuse_roughness;
             const uint64_t t64 = (uint64_t)tiles + (uint64_t)d.tiles_x * tiles_y;
             if (t64 * m > (1ull << 27)) return fail(CR_ERR_INVALID_ARG, "pass %u: too many slots", p);
             tiles = (uint32_t)t64;
@@ -847,6 +850,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     job.reuse_depth = o.reuse_depth;
     job.seed = o.seed;
     job.frame_base = o.frame_base;
+    job.diffuse_roughness = o.diffuse_roughness;
     job.flags = ((o.flags & CR_OPT_NEE) ? CR_JOB_NEE : 0u) | ((o.flags & CR_OPT_HYBRID_DONOR) ? CR_JOB_HYBRID_DONOR : 0u) |
                 ((o.flags & CR_OPT_NEE_SHARED) ? CR_JOB_NEE_SHARED : 0u);
     job.out_rgb = out_dev ? out_rgb : s->d_out;

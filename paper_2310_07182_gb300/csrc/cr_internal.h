@@ -118,6 +118,7 @@ struct JobDev {
     uint32_t nee;         // 1: next-event estimation, 2: with light points shared per group
     uint32_t hybrid_donor; // 1: hybrid groups reuse the first diffuse member's sample
     uint32_t sample_flags; // bit 0: this pass is the job's first sample, bit 1: its last
+    float diffuse_rough;   // GGX of at least this roughness is in the diffuse class (0: off)
 };
 
 // Launch-uniform description of a pass.

@@ -175,6 +175,8 @@ struct Member {
     bool nee;        // the job uses next-event estimation
     bool nee_shared; // ... with one light point per group
     bool hdonor;     // hybrid groups: diffuse members reuse the first diffuse member's sample
+    bool cosgl;      // a GGX point in the diffuse class while reusing: cosine samples, pi f weights
+    float tau;       // roughness threshold of the diffuse class (0: classes by material type)
     uint32_t scene;  // scene table index
     uint32_t type;   // material type of the shading point
     float rough;     // its roughness (the IOR of a dielectric)
@@ -192,6 +194,17 @@ struct Member {
 };
 
 // Shading point of a hit: geometric normal facing the incoming ray, tangent frame, wo.
+// Weight pi f(wo, wi) (= f cos / p_cos) of a cosine-class GGX point for the tangent-space
+// direction wl; usable when both it and wo lie above the surface.
+__device__ __forceinline__ void rough_weight(Member& mb, V3 wl) {
+    float f[3];
+    eval_ggx(mb.wo, wl, mb.rough, mb.albedo, f);
+    mb.w[0] = fm(3.14159265358979f, f[0]);
+    mb.w[1] = fm(3.14159265358979f, f[1]);
+    mb.w[2] = fm(3.14159265358979f, f[2]);
+    mb.valid = wl.z > 0.0f && mb.wo.z > 0.0f;
+}
+
 // Radiance picked up where a ray ends without scattering.  Miss: beta times the constant
 // environment.
 __device__ __forceinline__ void add_environment(const SceneDev& sc, const float4 bt, float3& L) {
@@ -261,6 +274,11 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     // transmission (the paper's future work, Sec. 6): a Lambertian transmitter joins the
     // diffuse class with its lobe in the lower hemisphere; a smooth dielectric is specular
     mb.cls = (type == kMatLambert || type == kMatTranslucent) ? kClsDiffuse : kClsGlossy;
+    // roughness threshold of the classes (a reading: Sec. 3.2 classifies by material): a
+    // rough GGX point joins the diffuse class, and while reusing it samples a cosine lobe
+    const bool rough_cls = type == kMatGGX && mb.tau > 0.0f && m1.x >= mb.tau;
+    if (rough_cls) mb.cls = kClsDiffuse;
+    mb.cosgl = rough_cls && (mb.reuse || mb.world);
     mb.hemi = type == kMatTranslucent ? -1.0f : 1.0f;
     mb.type = type;
     mb.rough = m1.x;
@@ -276,6 +294,9 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
         mb.w[1] = m0.z;
         mb.w[2] = m0.w;
         mb.valid = true;
+    } else if (mb.cosgl) { // a GGX point of the diffuse class: cosine sample, weight pi f
+        mb.wl = sample_cosine(u1, u2);
+        rough_weight(mb, mb.wl);
     } else if (type == kMatGGX) {
         mb.valid = sample_ggx(mb.wo, m1.x, mb.albedo, u1, u2, mb.wl, mb.w);
     } else if (type == kMatTranslucent) {
@@ -305,6 +326,10 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
 // so a cosine-distributed direction stays cosine-distributed in either lobe.
 __device__ __forceinline__ void take_dir(Member& mb, V3 wl) {
     mb.wl = v3(wl.x, wl.y, fm(mb.hemi, fabsf(wl.z)));
+    if (mb.cosgl) {
+        rough_weight(mb, mb.wl);
+        return;
+    }
     mb.w[0] = mb.albedo[0]; // Lambert: f cos / p_cos = albedo
     mb.w[1] = mb.albedo[1];
     mb.w[2] = mb.albedo[2];
@@ -315,6 +340,10 @@ __device__ __forceinline__ void take_dir(Member& mb, V3 wl) {
 // is; outside the member's lobe f = 0 and the path ends.
 __device__ __forceinline__ void take_dir_world(Member& mb, V3 l) {
     mb.wl = l;
+    if (mb.cosgl) {
+        rough_weight(mb, l);
+        return;
+    }
     mb.w[0] = mb.albedo[0];
     mb.w[1] = mb.albedo[1];
     mb.w[2] = mb.albedo[2];
@@ -338,6 +367,7 @@ __device__ __forceinline__ V3 spawn_point(const ShadeArgs& a, int slot, V3 n) {
 __device__ __forceinline__ float own_pdf(const Member& mb, V3 wl) {
     if (mb.type == kMatLambert) return wl.z > 0.0f ? fm(wl.z, 0.318309886f) : 0.0f;
     if (mb.type == kMatTranslucent) return wl.z < 0.0f ? fm(-wl.z, 0.318309886f) : 0.0f;
+    if (mb.cosgl) return wl.z > 0.0f ? fm(wl.z, 0.318309886f) : 0.0f;
     if (mb.type == kMatGGX) return pdf_ggx(mb.wo, wl, mb.rough);
     return 0.0f;
 }
@@ -533,6 +563,8 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     mb.nee = false;
     mb.nee_shared = false;
     mb.hdonor = false;
+    mb.cosgl = false;
+    mb.tau = 0.0f;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
     mb.front = true;
@@ -557,6 +589,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.nee = Jp->nee != 0;
             mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
+            mb.tau = Jp->diffuse_rough;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
@@ -670,6 +703,8 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
     mb.nee = false;
     mb.nee_shared = false;
     mb.hdonor = false;
+    mb.cosgl = false;
+    mb.tau = 0.0f;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
     mb.front = true;
@@ -694,6 +729,7 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
             mb.nee = Jp->nee != 0;
             mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
+            mb.tau = Jp->diffuse_rough;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
