@@ -671,29 +671,37 @@ def quality_leg(cr, S, cam, stream, results):
     out = {"reference_spp": n_ref, "budgets_s": [0.1, 0.5, 2.0], "modes": {}}
     peak = float(ref.max())
     donor = cr.CR_OPT_HYBRID_DONOR
-    variants = (("direction_reuse", "direction_reuse", 0, 0, K), ("independent", "independent", 0, 0, K),
-                ("morton_sort", "morton_sort", 0, 0, K), ("direction_reuse_bounce1_only", "direction_reuse", 1, 0, K),
-                ("direction_reuse_hybrid_donor", "direction_reuse", 0, donor, K),
-                ("direction_reuse_hybrid_donor_k64", "direction_reuse", 0, donor, 64))
-    for name, mode, depth, vflags, k in variants:
+    # (name, mode, reuse depth, flags, K, roughness threshold of the diffuse class)
+    variants = (("direction_reuse", "direction_reuse", 0, 0, K, 0.0), ("independent", "independent", 0, 0, K, 0.0),
+                ("morton_sort", "morton_sort", 0, 0, K, 0.0),
+                ("direction_reuse_bounce1_only", "direction_reuse", 1, 0, K, 0.0),
+                ("direction_reuse_hybrid_donor", "direction_reuse", 0, donor, K, 0.0),
+                ("direction_reuse_hybrid_donor_k64", "direction_reuse", 0, donor, 64, 0.0),
+                ("direction_reuse_rough030", "direction_reuse", 0, 0, K, 0.3),
+                ("direction_reuse_rough030_hybrid_donor", "direction_reuse", 0, donor, K, 0.3))
+    for name, mode, depth, vflags, k, tau in variants:
         ms_spp = results.get(name, {}).get("ms_per_step")
         if ms_spp is None:
-            ms, _, _ = _timed_renders(cr, S, cam, img, stream, 3, 1, mode=mode, k=k, reuse_depth=depth,
-                                      extra_flags=vflags)
+            ms, tr, sec = _timed_renders(cr, S, cam, img, stream, 3, 1, mode=mode, k=k, reuse_depth=depth,
+                                         extra_flags=vflags, diffuse_roughness=tau)
             ms_spp = ms / 3
         row = {"ms_per_spp": round(ms_spp, 4), "mse": [], "spp": []}
+        if tau > 0:
+            row["diffuse_roughness"] = tau
+            row["trace_only_mrays"] = round(sec / (tr / 1e3) / 1e6, 1)
         for T in out["budgets_s"]:
             spp = max(1, int(T * 1e3 / ms_spp))
-            o = cr.make_opts(k=k, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags)
+            o = cr.make_opts(k=k, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags, diffuse_roughness=tau)
             cr.cr_render_ex(S.handle, cam, spp, BOUNCES, mode, TILE[0], TILE[1], img, o)
             row["mse"].append(float(((img - ref) ** 2).mean()))
             row["spp"].append(spp)
-        o = cr.make_opts(k=k, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags)
+        o = cr.make_opts(k=k, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags, diffuse_roughness=tau)
         cr.cr_render_ex(S.handle, cam, 128, BOUNCES, mode, TILE[0], TILE[1], img, o)
         mse128 = float(((img - ref) ** 2).mean())
         row["psnr_128spp_db"] = round(10 * math.log10(peak * peak / mse128), 3)
         # bias estimate: the 1024-spp mean of the mode against the reference
-        o = cr.make_opts(k=k, frame_base=2_000_000, stream=stream, reuse_depth=depth, flags=vflags)
+        o = cr.make_opts(k=k, frame_base=2_000_000, stream=stream, reuse_depth=depth, flags=vflags,
+                         diffuse_roughness=tau)
         cr.cr_render_ex(S.handle, cam, 1024, BOUNCES, mode, TILE[0], TILE[1], img, o)
         row["mse_1024spp"] = float(((img - ref) ** 2).mean())
         out["modes"][name] = row

@@ -1323,9 +1323,14 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                         f3 v = tree_sum(sumbuf, K);
                         float l2 = f3dot(v, v);
                         f3 wl;
+                        int keep_rough = 0;
                         if (l2 > 0.0f) {
                             float l = sqrtf(l2);
                             wl = f3m(v.x / l, v.y / l, v.z / l);
+                            /* a rough GGX member (roughness threshold) keeps its own cosine
+                             * sample: its weight pi f at the glossy average, near its own
+                             * specular peak, would be far above 1 */
+                            keep_rough = 1;
                         } else {
                             /* no valid glossy sample: fall back to the diffuse-group rule
                              * among the diffuse members */
@@ -1335,7 +1340,8 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                             wl = G[donor].wl;
                         }
                         for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE)
+                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE &&
+                                !(keep_rough && G[j].cosgl))
                                 take_direction(s, &G[j], into_lobe(&G[j], wl));
                     }
                     /* glossy groups and the independent mode keep every member's own sample */

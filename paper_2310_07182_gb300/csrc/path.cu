@@ -641,8 +641,10 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
                     if (mb.hdonor) {
                         take_dir(mb, wd); // donor option: the first diffuse member's own sample
                     } else if (l2 > 0.0f) {
+                        // a rough GGX member keeps its own cosine sample: its weight pi f at
+                        // the glossy average (near its specular peak) would be far above 1
                         const float l = fq(l2);
-                        take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
+                        if (!mb.cosgl) take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
                     } else {
                         take_dir(mb, wd); // no valid glossy sample: first diffuse member's
                     }
@@ -799,8 +801,8 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
                     if (mb.hdonor) {
                         take_dir(mb, wd); // donor option: the first diffuse member's own sample
                     } else if (l2 > 0.0f) {
-                        const float l = fq(l2);
-                        take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
+                        const float l = fq(l2); // rough GGX members keep their own cosine sample
+                        if (!mb.cosgl) take_dir(mb, v3(fd(s.x, l), fd(s.y, l), fd(s.z, l)));
                     } else {
                         take_dir(mb, wd);
                     }

@@ -342,3 +342,35 @@ def test_cosine_sampled_rough_ggx_has_the_directional_albedo(orc):
     assert abs(x.mean() / y.mean() - 1.0) < 3 * se
     # the two estimators really differ sample by sample (cosine vs GGX directions)
     assert not np.array_equal(x, y)
+
+
+def test_rough_members_of_hybrid_groups_keep_their_own_cosine_sample(orc):
+    """Under the paper's hybrid rule the Lambert members take the glossy average, but a
+    rough GGX member of the diffuse class keeps its own cosine sample (weighing the average
+    by pi f, near its own specular peak, would add energy): its direction equals the one it
+    draws alone (K = 1)."""
+    sc = scenes.tiny(material_mix="mixed", n_soup=3000)
+    S = orc.Scene(sc)
+    kw = dict(spp=1, max_bounces=1, seed=9, debug=True, diffuse_roughness=0.25, mode="direction_reuse")
+    r = orc.render(S, sc.camera, tile=(4, 4), k=16, **kw)
+    alone = orc.render(S, sc.camera, tile=(4, 4), k=1, **kw)
+    prim = r["dbg_prim"][0]
+    hit = prim >= 0
+    mat = np.full(prim.shape, -1)
+    mat[hit] = sc.tri_mat[prim[hit]]
+    rough = hit & (sc.mat_type[np.maximum(mat, 0)] == scenes.MAT_GGX) & (sc.mat_params[np.maximum(mat, 0), 3] >= 0.25)
+    fl, cls = r["dbg_flags"][0], r["dbg_cls"][0]
+    w = sc.camera.width
+    ntx = w // 4
+    n = 0
+    for tile in range(ntx * (sc.camera.height // 4)):
+        sigma, _ = orc.tile_sigma(4, 4, tile, 0, 9)
+        tx, ty = tile % ntx, tile // ntx
+        mem = np.array([(ty * 4 + i // 4) * w + tx * 4 + i % 4 for i in range(16)])[np.argsort(sigma)]
+        # hybrid groups whose glossy average exists (a valid glossy/specular sample)
+        if r["dbg_cat"][0, mem[0]] != 3 or not ((cls[mem] == 2) & ((fl[mem] & 2) == 2)).any():
+            continue
+        sel = mem[rough[mem] & ((fl[mem] & 1) == 1)]
+        assert np.array_equal(r["dbg_local"][0][sel].view(np.uint32), alone["dbg_local"][0][sel].view(np.uint32))
+        n += len(sel)
+    assert n > 20
