@@ -1,6 +1,7 @@
 // path.cu -- wavefront path-tracing stages around the traversal: primary ray generation
-// in reuse-group slot order, the fused shade / classify / reuse / spawn stage, group-
-// granular path compaction, the Morton-sort comparator and accumulation.
+// in reuse-group slot order, the fused shade / classify / reuse / spawn stage with the
+// group-granular path compaction inside it (or, as an option, a separate order-preserving
+// compaction), the Morton-sort comparator, and the accumulation that finishes a pass.
 //
 // Slot layout (Sec. 3.3): the image is cut into W x H tiles; inside tile t the pixel with
 // row-major index i goes to slot t*m + sigma_{t,f}(i), where sigma is the tile's and
@@ -841,10 +842,11 @@ __global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
 }
 
 // ------------------------------------------------------------------------------------
-// Group-granular compaction.  Positions [0, n_groups*K) of the last shade (group queue
-// order) are scanned in blocks of 256; a group survives if any member is alive and keeps
-// its K slots together in the group queue, while the ray queue lists the alive slots.
-// Three launches (count, scan, scatter) keep the result deterministic and order-preserving.
+// Order-preserving group-granular compaction (CR_OPT_ORDERED_QUEUES; the default appends in
+// the shade instead).  Positions [0, n_groups*K) of the last shade (group queue order) are
+// scanned in blocks of 256; a group survives if any member is alive and keeps its K slots
+// together in the group queue, while the ray queue lists the alive slots.  Three launches
+// (count, scan, scatter) keep the whole queue in position order.
 constexpr uint32_t kCompactBlock = 256;
 
 __device__ __forceinline__ void position_info(const int32_t* gq_in, uint32_t n_groups, uint32_t K, uint32_t pos,
@@ -1366,7 +1368,7 @@ static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, bool 
     a.beta = b.beta;
     a.radiance = b.radiance;
     a.alive = b.alive;
-    // group queue written by the compaction after the previous shade (double-buffered)
+    // group queue written by the previous shade's compaction (double-buffered)
     a.group_queue = first ? nullptr : b.group_queue + (size_t)((p.bounce - 1) & 1) * b.n_groups;
     a.group_count = first ? nullptr : b.counts + 8 + 2 * (p.bounce - 1) + 1;
     a.n_groups_max = b.n_groups;
