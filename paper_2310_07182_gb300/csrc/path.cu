@@ -675,10 +675,16 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     }
 }
 
+#ifndef CR_SHADE_BLOCK_MIN_BLOCKS
+// registers sized for 4 resident 256-thread blocks per SM (64 per thread): 12-18% less shade
+// time at K = 64 and 256 than the uncapped 79 registers (3 blocks); caps for 3 or 5 blocks
+// do worse
+#define CR_SHADE_BLOCK_MIN_BLOCKS 4
+#endif
 // 32 < K <= 256: a group spans K/32 warps of a 256-thread block; per-warp ballots and the
 // members' samples go through shared memory and the hybrid sum is a pairwise tree over the
 // group's slots.
-__global__ void __launch_bounds__(256) k_shade_block(ShadeArgs a, PassArgs p) {
+__global__ void __launch_bounds__(256, CR_SHADE_BLOCK_MIN_BLOCKS) k_shade_block(ShadeArgs a, PassArgs p) {
     __shared__ uint32_t s_bd[8], s_bg[8], s_ba[8];
     __shared__ float s_own[3][256];
     __shared__ float s_sum[3][256];
