@@ -177,7 +177,6 @@ struct Member {
     bool nee_shared; // ... with one light point per group
     bool hdonor;     // hybrid groups: diffuse members reuse the first diffuse member's sample
     bool cosgl;      // a GGX point in the diffuse class while reusing: cosine samples, pi f weights
-    float tau;       // roughness threshold of the diffuse class (0: classes by material type)
     uint32_t scene;  // scene table index
     uint32_t type;   // material type of the shading point
     float rough;     // its roughness (the IOR of a dielectric)
@@ -240,7 +239,8 @@ __device__ __forceinline__ void add_emission(const SceneDev& sc, const float4 v0
 }
 
 __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs& p, const SceneDev& sc, int slot,
-                                             Member& mb, float3& L, const float4 bt, const int2 h, const float4 d4) {
+                                             Member& mb, float3& L, const float4 bt, const int2 h, const float4 d4,
+                                             const float tau) {
     if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
     if (h.x < 0) { // miss: environment
         add_environment(sc, bt, L);
@@ -277,7 +277,7 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     mb.cls = (type == kMatLambert || type == kMatTranslucent) ? kClsDiffuse : kClsGlossy;
     // roughness threshold of the classes (a reading: Sec. 3.2 classifies by material): a
     // rough GGX point joins the diffuse class, and while reusing it samples a cosine lobe
-    const bool rough_cls = type == kMatGGX && mb.tau > 0.0f && m1.x >= mb.tau;
+    const bool rough_cls = type == kMatGGX && tau > 0.0f && m1.x >= tau;
     if (rough_cls) mb.cls = kClsDiffuse;
     mb.cosgl = rough_cls && (mb.reuse || mb.world);
     mb.hemi = type == kMatTranslucent ? -1.0f : 1.0f;
@@ -565,7 +565,6 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     mb.nee_shared = false;
     mb.hdonor = false;
     mb.cosgl = false;
-    mb.tau = 0.0f;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
     mb.front = true;
@@ -590,7 +589,6 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.nee = Jp->nee != 0;
             mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
-            mb.tau = Jp->diffuse_rough;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
@@ -601,7 +599,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
             mb.alive = true;
             bt = b4;
             L = make_float3(r4.x, r4.y, r4.z);
-            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt, h, d4);
+            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt, h, d4, J.diffuse_rough);
         }
     }
     int cat = kCatEmpty;
@@ -713,7 +711,6 @@ __global__ void __launch_bounds__(256, CR_SHADE_BLOCK_MIN_BLOCKS) k_shade_block(
     mb.nee_shared = false;
     mb.hdonor = false;
     mb.cosgl = false;
-    mb.tau = 0.0f;
     mb.type = kMatLambert;
     mb.hemi = 1.0f;
     mb.front = true;
@@ -738,7 +735,6 @@ __global__ void __launch_bounds__(256, CR_SHADE_BLOCK_MIN_BLOCKS) k_shade_block(
             mb.nee = Jp->nee != 0;
             mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
-            mb.tau = Jp->diffuse_rough;
             mb.scene = Jp->scene;
             mb.seed = Jp->seed;
             mb.frame = Jp->frame;
@@ -749,7 +745,7 @@ __global__ void __launch_bounds__(256, CR_SHADE_BLOCK_MIN_BLOCKS) k_shade_block(
             mb.alive = true;
             bt = b4;
             L = make_float3(r4.x, r4.y, r4.z);
-            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt, h, d4);
+            setup_member(a, p, a.scenes[J.scene], slot, mb, L, bt, h, d4, J.diffuse_rough);
         }
     }
     int cat = kCatEmpty;
