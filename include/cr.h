@@ -195,7 +195,8 @@ typedef struct {
     uint32_t frame_base;   /* frame index of the first sample (progressive rendering) */
     uint32_t reuse_depth;  /* reuse at bounces b <= reuse_depth; 0 = every bounce */
     uint32_t bvh;          /* CR_BVH2 (default) or CR_BVH8Q (scene must have it) */
-    uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 */
+    uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 for
+                            * primary rays and 64 for secondary rays */
     uint32_t flags;        /* CR_OPT_* */
     uint32_t sort_key;     /* cr_sort_key of CR_MORTON_SORT (default TwoPoint) */
     uint32_t stack;        /* BVH2 traversal stack entries per thread in shared memory: 8, 16 or 32 (0 = 16) */

@@ -754,10 +754,12 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
         ta.counters = nullptr;
         if (ta.persistent) check(cudaMemsetAsync(ta.work_counter, 0, 4, stream), "memset");
         ta.packet = eo.packet_primary;
+        ta.block = eo.block;
         ev.begin(stream, times ? &times->trace_primary : &dummy, "cr trace primary", true);
         launch_trace(ta, stream, lc);
         ev.end();
         ta.packet = eo.packet_secondary;
+        ta.block = eo.block_secondary ? eo.block_secondary : eo.block;
         for (uint32_t bnc = 1; bnc <= p.max_bounces; ++bnc) {
             P.bounce = bnc;
             ev.begin(stream, times ? &times->shade : &dummy, "cr shade");
@@ -874,6 +876,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     if (st != CR_OK) return st;
     ExecOpts eo;
     eo.block = block;
+    eo.block_secondary = o.block ? block : kSecondaryBlock;
     if (o.stack != 0 && o.stack != 8 && o.stack != 16 && o.stack != 32)
         return fail(CR_ERR_INVALID_ARG, "cr_render: stack %u not in {8, 16, 32}", o.stack);
     eo.stack = o.stack ? o.stack : 16;
@@ -1190,6 +1193,7 @@ static cr_status batch_opts_check(const cr_batch_opts* o, PlanOpts& po, ExecOpts
     po.interleave = o->interleave;
     po.bvh8 = o->bvh == CR_BVH8Q;
     eo.block = block;
+    eo.block_secondary = o->block ? block : kSecondaryBlock;
     if (o->stack != 0 && o->stack != 8 && o->stack != 16 && o->stack != 32)
         return fail(CR_ERR_INVALID_ARG, "stack %u not in {8, 16, 32}", o->stack);
     eo.stack = o->stack ? o->stack : 16;

@@ -321,8 +321,13 @@ struct Plan {
     void release();
     ~Plan() { release(); }
 };
+// Default trace block sizes (cr_render_opts.block = 0): 128 threads for the coherent primary
+// rays, 64 for secondary rays (1.4% less secondary trace time on the landscape, 0.8% on the
+// interior; primary rays are 0.5-1% faster in blocks of 128).
+constexpr int kSecondaryBlock = 64;
 struct ExecOpts {
-    int block = 128;
+    int block = 128;           // trace block size of the primary rays
+    int block_secondary = 0;   // of the secondary rays (0: block)
     uint32_t stack = 16; // BVH2 traversal stack entries per thread in shared memory
     bool persistent = false, count = false, speculative = false;
     bool packet_primary = false, packet_secondary = false; // warp-packet traversal per ray kind

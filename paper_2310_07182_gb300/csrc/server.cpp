@@ -267,6 +267,7 @@ extern "C" cr_status cr_server_create(const cr_server_opts* o, cr_server** out) 
     s->po.interleave = o->interleave;
     s->po.bvh8 = o->bvh == CR_BVH8Q;
     s->eo.block = o->block ? (int)o->block : 128;
+    s->eo.block_secondary = o->block ? (int)o->block : kSecondaryBlock;
     s->eo.clear_accum = false;
     s->eo.write_output = false;
     const uint32_t m = o->group_w * o->group_h;
