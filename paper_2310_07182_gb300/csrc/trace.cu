@@ -70,7 +70,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
 }
 
 #ifndef CR_TRACE_MAXNREG
-#define CR_TRACE_MAXNREG 48 // caps registers so 10 blocks of 128 threads stay resident per SM
+#define CR_TRACE_MAXNREG 48 // 42 warps resident per SM (10 blocks of 128 or 21 of 64 threads); 40 spills
 #endif
 
 template <bool kCount, bool kAny = false, int kSmemS = kSmemStack>
