@@ -538,8 +538,14 @@ __device__ __forceinline__ void append_queues(const ShadeArgs& a, uint32_t K, in
 #ifndef CR_SHADE_MIN_BLOCKS
 #define CR_SHADE_MIN_BLOCKS 8 // registers sized for 8 resident 128-thread blocks per SM (0: no cap)
 #endif
+#ifndef CR_SHADE_WARP_BLOCK
+// threads per block of the K <= 32 shade kernel: 256 and 512 give longer appended queue
+// ranges (secondary trace 0.6-1% faster) but a slower shade; the step is within 0.4% either way
+#define CR_SHADE_WARP_BLOCK 128
+#endif
 #if CR_SHADE_MIN_BLOCKS
-__global__ void __launch_bounds__(128, CR_SHADE_MIN_BLOCKS) k_shade_warp(ShadeArgs a, PassArgs p) {
+__global__ void __launch_bounds__(CR_SHADE_WARP_BLOCK, CR_SHADE_MIN_BLOCKS * 128 / CR_SHADE_WARP_BLOCK)
+    k_shade_warp(ShadeArgs a, PassArgs p) {
 #else
 __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
 #endif
@@ -669,7 +675,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     if (a.ray_queue) {
         // groups are K-lane segments of a warp: a group continues if any member does
         const uint32_t nb = __ballot_sync(0xffffffffu, next_alive) & segmask;
-        append_queues<128>(a, K, slot, next_alive, lane == seg && nb != 0u);
+        append_queues<CR_SHADE_WARP_BLOCK>(a, K, slot, next_alive, lane == seg && nb != 0u);
     }
 }
 
@@ -1404,7 +1410,7 @@ void launch_shade(const PassArgs& p, PathBuffers& b, bool first, bool compact, c
     ShadeArgs a = shade_args(p, b, first, compact, dbg);
     const uint32_t n_pos = b.n_groups * p.k;
     if (p.k <= 32) {
-        k_shade_warp<<<(n_pos + 127) / 128, 128, 0, st>>>(a, p);
+        k_shade_warp<<<(n_pos + CR_SHADE_WARP_BLOCK - 1) / CR_SHADE_WARP_BLOCK, CR_SHADE_WARP_BLOCK, 0, st>>>(a, p);
     } else {
         k_shade_block<<<(n_pos + 255) / 256, 256, 0, st>>>(a, p);
     }
