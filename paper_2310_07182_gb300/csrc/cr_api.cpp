@@ -853,8 +853,9 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     job.seed = o.seed;
     job.frame_base = o.frame_base;
     job.diffuse_roughness = o.diffuse_roughness;
-    job.flags = ((o.flags & CR_OPT_NEE) ? CR_JOB_NEE : 0u) | ((o.flags & CR_OPT_HYBRID_DONOR) ? CR_JOB_HYBRID_DONOR : 0u) |
-                ((o.flags & CR_OPT_NEE_SHARED) ? CR_JOB_NEE_SHARED : 0u);
+    job.flags = ((o.flags & CR_OPT_NEE) ? (uint32_t)CR_JOB_NEE : 0u) |
+                ((o.flags & CR_OPT_HYBRID_DONOR) ? (uint32_t)CR_JOB_HYBRID_DONOR : 0u) |
+                ((o.flags & CR_OPT_NEE_SHARED) ? (uint32_t)CR_JOB_NEE_SHARED : 0u);
     job.out_rgb = out_dev ? out_rgb : s->d_out;
     PlanOpts po;
     po.tile_w = group_w;

@@ -900,7 +900,6 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_count(const int32_t* 
                                                                  const uint8_t* __restrict__ alive,
                                                                  uint32_t* __restrict__ block_counts) {
     __shared__ uint8_t s_alive[kCompactBlock];
-    __shared__ uint32_t s_warp[32];
     const uint32_t n_groups = n_groups_ptr ? min(*n_groups_ptr, n_groups_max) : n_groups_max;
     const uint32_t pos = blockIdx.x * kCompactBlock + threadIdx.x;
     int slot;
@@ -912,7 +911,6 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_count(const int32_t* 
     if (threadIdx.x % K == 0) {
         for (uint32_t j = 0; j < K; ++j) gl |= s_alive[threadIdx.x + j];
     }
-    (void)s_warp;
     const uint32_t tot_r = (uint32_t)__syncthreads_count(a);
     const uint32_t tot_g = (uint32_t)__syncthreads_count(gl != 0u);
     if (threadIdx.x == 0) {
