@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcr.so")
-SOURCES = ["trace.cu", "trace_bvh8.cu", "path.cu", "cr_api.cpp", "bvh_build.cpp", "trace_static.cu", "server.cpp", "probe.cu"]
+SOURCES = ["trace.cu", "trace_bvh8.cu", "path.cu", "cr_api.cpp", "bvh_build.cpp", "bvh8_build.cpp", "trace_static.cu", "server.cpp", "probe.cu"]
 HEADERS = ["cr_internal.h", "device_math.cuh", "trace_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

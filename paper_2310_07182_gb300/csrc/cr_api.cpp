@@ -197,7 +197,7 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     std::vector<float> tris8;
     if (bvh_flags & CR_BVH8Q) {
         try {
-            b8 = build_bvh8q(b2);
+            b8 = build_bvh8q(b2, tri_xyz);
         } catch (const std::bad_alloc&) {
             return fail(CR_ERR_OOM, "cr_scene_create: host allocation during BVH8-Q build");
         }
@@ -1154,7 +1154,7 @@ extern "C" cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, ui
         check_bvh2(b2, tri_xyz, n_tri, rep->covered2, rep->violations2);
         if (flags & CR_BVH8Q) {
             const auto t2 = std::chrono::steady_clock::now();
-            HostBVH8 b8 = build_bvh8q(b2);
+            HostBVH8 b8 = build_bvh8q(b2, tri_xyz);
             const auto t3 = std::chrono::steady_clock::now();
             rep->n_nodes8 = b8.n_nodes;
             rep->depth8 = b8.depth;

@@ -52,7 +52,7 @@ struct HostBVH8 {
     uint32_t depth = 0;
     uint32_t stack_bound = 0;         // largest traversal stack a ray can need (the depth)
 };
-HostBVH8 build_bvh8q(const HostBVH2& b2);
+HostBVH8 build_bvh8q(const HostBVH2& b2, const float* tri_xyz);
 constexpr uint32_t kBvh2StackCapacity = 64; // traversal stack entries of the BVH2 kernels (> tree depth)
 constexpr uint32_t kBvh8StackCapacity = 48; // traversal stack entries of the BVH8-Q kernel (one per level)
 void check_bvh2(const HostBVH2& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);

@@ -30,7 +30,7 @@ static int check(const std::vector<float>& v, const char* what) {
         seen[t] = 1;
     }
     if (b2.depth >= cr::kBvh2StackCapacity) return 1;
-    cr::HostBVH8 b8 = cr::build_bvh8q(b2);
+    cr::HostBVH8 b8 = cr::build_bvh8q(b2, v.data());
     cr::check_bvh8(b8, v.data(), n, cov, bad);
     if (bad || cov != n) {
         std::printf("%s: BVH8-Q covered %u of %u, %u violations\n", what, cov, n, bad);

@@ -50,6 +50,7 @@ def test_bvh_builders_under_sanitizers(tmp_path):
     exe = str(tmp_path / "bvh_san")
     csrc = os.path.join(ROOT, "paper_2310_07182_gb300", "csrc")
     cmd = ["g++", "-std=c++17", *SAN, "-I", os.path.join(ROOT, "include"), "-I", csrc, "-I", inc,
-           os.path.join(csrc, "bvh_build.cpp"), os.path.join(HERE, "helpers", "bvh_sanitize_main.cpp"),
+           os.path.join(csrc, "bvh_build.cpp"), os.path.join(csrc, "bvh8_build.cpp"),
+           os.path.join(HERE, "helpers", "bvh_sanitize_main.cpp"),
            "-o", exe, "-lpthread"]
     assert "bvh sanitize run ok" in _run(cmd, exe, tmp_path)
