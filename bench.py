@@ -239,7 +239,8 @@ def run_ours(args):
     # the headline metric is the landscape's
     sc = scenes.landscape() if args.scene == "landscape" else scenes.interior()
     workload = WORKLOAD if args.scene == "landscape" else "interior 1280x720 (512,014 tris), 1 spp, B=2, 8x8 K=8"
-    S = cr.Scene(sc)
+    # a "+bvh8q" mode traces through the 8-wide quantised BVH (profiling its kernel)
+    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | (cr.CR_BVH8Q if "+bvh8q" in args.modes else 0))
     cam = sc.camera
     out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
@@ -252,22 +253,25 @@ def run_ours(args):
 
     def parse(mode):
         # "morton_sort:<key>" selects a reordering key (Table 1 comparators); a "+<variant>"
-        # suffix selects a traversal variant of the secondary trace
+        # suffix selects a traversal variant of the secondary trace, "+bvh8q" the BVH8-Q
         mode, *variants = mode.split("+")
         m, _, key = mode.partition(":")
-        flags = 0
+        flags, bvh = 0, cr.CR_BVH2
         for v in variants:
-            flags |= variant_flags[v]
-        return m, key or "two_point", flags
+            if v == "bvh8q":
+                bvh = cr.CR_BVH8Q
+            else:
+                flags |= variant_flags[v]
+        return m, key or "two_point", flags, bvh
 
     def step(mode, frame, flags=0, stats_flag=None):
         # timed steps record events only around the trace launches (the whole-step time, the
         # trace-only rate and the roofline's launch time); the full per-stage breakdown comes
         # from separate untimed steps, because ~30 event records per step cost ~3% of it
-        m, key, vflags = parse(mode)
+        m, key, vflags, bvh = parse(mode)
         flags |= vflags
         st = cr.cr_stats()
-        o = cr.make_opts(k=K, interleave=True, seed=0, frame_base=frame,
+        o = cr.make_opts(k=K, interleave=True, seed=0, frame_base=frame, bvh=bvh,
                          flags=(cr.CR_OPT_STATS_TRACES if stats_flag is None else stats_flag) | flags, stream=stream,
                          stats=st, sort_key=key)
         cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m, TILE[0], TILE[1], out, o)
@@ -332,20 +336,20 @@ def run_ours(args):
     # call after the other.  (2) pipelined: double-buffered device images, each copied to its
     # own host buffer on a side stream while the next step renders (how a frame loop
     # overlaps readback with work); all copies finish inside the timed region.
-    m0, key0, flags0 = parse(modes[0])
+    m0, key0, flags0, bvh0 = parse(modes[0])
     hosts = [torch.empty((cam.height, cam.width, 3), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     devs = [torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     st_io = cr.cr_stats()
     cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m0, TILE[0], TILE[1], hosts[0],
                     cr.make_opts(k=K, frame_base=frame_of(rank, 0, world), flags=flags0 | cr.CR_OPT_STATS_TRACES,
-                                 sort_key=key0, stats=st_io))
+                                 sort_key=key0, stats=st_io, bvh=bvh0))
     h2d_step = int(st_io.h2d_bytes)
 
     def e2e_sync(n, s0):
         for s in range(n):
             cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m0, TILE[0], TILE[1], hosts[0],
                             cr.make_opts(k=K, frame_base=frame_of(rank, s0 + s, world), flags=flags0,
-                                         sort_key=key0))
+                                         sort_key=key0, bvh=bvh0))
 
     main_stream = torch.cuda.current_stream()
     copy_stream = torch.cuda.Stream()
@@ -358,7 +362,7 @@ def run_ours(args):
             main_stream.wait_event(copied[b])  # the copy of step s - 2 has left this buffer
             cr.cr_render_ex(S.handle, cam, SPP, BOUNCES, m0, TILE[0], TILE[1], devs[b],
                             cr.make_opts(k=K, frame_base=frame_of(rank, s0 + s, world),
-                                         flags=flags0 | cr.CR_OPT_NO_SYNC, sort_key=key0,
+                                         flags=flags0 | cr.CR_OPT_NO_SYNC, sort_key=key0, bvh=bvh0,
                                          stream=main_stream.cuda_stream))
             rendered[b].record(main_stream)
             copy_stream.wait_event(rendered[b])
@@ -405,17 +409,20 @@ def run_ours(args):
     # watertight ray/triangle test, counted by the counting pass, against 152 SMs x 128 FP32
     # lanes x the SM clock sampled during the timed region.  The node-byte rate against the
     # measured HBM copy bandwidth is reported beside it.
+    # With "+bvh8q" first, the figures describe k_trace_bvh8 instead: 8 box tests and 80 B
+    # per node visit, and no ncu-derived keys (the committed summary is the BVH2 kernel's).
+    bvh8 = parse(modes[0])[3] == cr.CR_BVH8Q
     launches = BOUNCES
     rays_per_launch = R["secondary_rays_per_step"] / launches
     ms_per_launch = R["ms_trace_secondary"] / launches
-    ops_per_ray = 2 * 24 * R["nodes_per_ray"] + 40 * R["tris_per_ray"]
+    ops_per_ray = (8 if bvh8 else 2) * 24 * R["nodes_per_ray"] + 40 * R["tris_per_ray"]
     achieved_ops = ops_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e12
     clk = (clocks or {}).get("sm_mhz") or 2070.0
     peak_ops = 152 * 128 * clk * 1e6 / 1e12
-    bytes_per_ray = 32 + 4 + 8 + 64 * R["nodes_per_ray"] + 48 * R["tris_per_ray"]
+    bytes_per_ray = 32 + 4 + 8 + (80 if bvh8 else 64) * R["nodes_per_ray"] + 48 * R["tris_per_ray"]
     achieved = bytes_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e9
     peak, peak_kind = load_peaks()
-    traffic = profile_traffic()
+    traffic = None if bvh8 else profile_traffic()
     l2_gbs = l2_read_bandwidth(cr)
     line = {
         "metric": METRIC, "value": round(R["mrays"], 2), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
@@ -434,14 +441,14 @@ def run_ours(args):
         "gpu_launches": int(R["launches_per_step"] * args.steps),
         "roofline": {"bound": "alu", "achieved": round(achieved_ops, 3), "peak": round(peak_ops, 2),
                      "unit": "TOP/s (FP32 ALU operations)", "frac": round(achieved_ops / peak_ops, 4),
-                     "traffic": traffic, "kernel": "k_trace_bvh2 (secondary rays)",
+                     "traffic": traffic, "kernel": f"k_trace_{'bvh8' if bvh8 else 'bvh2'} (secondary rays)",
                      "ops_per_ray": round(ops_per_ray, 1),
                      "peak_source": f"152 SMs x 128 FP32 lanes x {clk:.0f} MHz (sampled)"},
         "roofline_hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "bytes_per_ray": round(bytes_per_ray, 1),
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                          "note": "algorithmic node+triangle bytes; mostly served by L1/L2 (DRAM traffic is the 'traffic' key)"},
-        "roofline_issue": issue_roof(R, clk),
+        "roofline_issue": None if bvh8 else issue_roof(R, clk),
         "roofline_l2": {"achieved": round(achieved, 1), "peak": round(l2_gbs, 1), "unit": "GB/s",
                         "frac": round(achieved / l2_gbs, 4),
                         "peak_source": "cr_measure_l2_read: read-only kernel over an L2-resident 48 MB buffer, CUDA events",
