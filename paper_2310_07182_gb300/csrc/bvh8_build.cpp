@@ -51,6 +51,9 @@ float decode(float origin, uint32_t q, float step) {
 #ifndef CR_BVH8_SPLIT_LEAVES
 #define CR_BVH8_SPLIT_LEAVES 1
 #endif
+// Fill a node's free child slots by splitting its multi-triangle leaves (0: leaves stay as
+// the BVH2 made them, the layout before this option existed).
+constexpr bool kSplitLeaves = CR_BVH8_SPLIT_LEAVES != 0;
 
 struct B8 {
     const HostBVH2& b2;
@@ -102,7 +105,7 @@ struct B8 {
         // Slots still free: split the leaf of largest area that holds several triangles,
         // one triangle off at a time.  All 8 slots of a node are tested together, so a free
         // slot costs nothing, and a ray that misses a single triangle's box skips its test.
-        while (CR_BVH8_SPLIT_LEAVES && ch.size() < 8) {
+        while (kSplitLeaves && ch.size() < 8) {
             int best = -1;
             double ba = -1.0;
             for (size_t i = 0; i < ch.size(); ++i)
