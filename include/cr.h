@@ -158,6 +158,14 @@ typedef struct {
     uint8_t* flags;  /* B * npx: bit0 alive at step b, bit1 spawned a secondary ray */
     float* local;    /* B * npx * 3: tangent-space exit direction */
     float* world;    /* B * npx * 3: world-space exit direction */
+    /* Optional replay capture (all three or none; NULL = off).  What trace b received and
+     * returned, so that a checker can recompute each later stage from the GPU's own inputs
+     * (a stage-by-stage comparison that one fragile decision cannot derail). */
+    float* ray;      /* (B+1) * npx * 8: the ray of trace b: origin.xyz, the skipped triangle's
+                        original index (int32 bits, -1 none), direction.xyz, tmax */
+    float* t;        /* (B+1) * npx: its hit distance in units of |d| (inf on a miss) */
+    float* beta;     /* (B+1) * npx * 4: the path throughput the ray carried (rgb) and, in w,
+                        the density of its direction (next-event estimation; 0 otherwise) */
 } cr_debug;
 
 enum {

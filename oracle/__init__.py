@@ -59,7 +59,18 @@ class _Params(C.Structure):
 class _Outputs(C.Structure):
     _fields_ = [("accum", C.c_void_p), ("taint", C.c_void_p), ("dbg_prim", C.c_void_p),
                 ("dbg_cat", C.c_void_p), ("dbg_cls", C.c_void_p), ("dbg_flags", C.c_void_p),
-                ("dbg_local", C.c_void_p), ("dbg_world", C.c_void_p), ("counters", C.c_void_p)]
+                ("dbg_local", C.c_void_p), ("dbg_world", C.c_void_p), ("counters", C.c_void_p),
+                ("dbg_ray", C.c_void_p), ("dbg_t", C.c_void_p), ("dbg_beta", C.c_void_p)]
+
+
+class _ReplayIn(C.Structure):
+    _fields_ = [("ray", C.c_void_p), ("prim", C.c_void_p), ("t", C.c_void_p), ("beta", C.c_void_p)]
+
+
+class _ReplayOut(C.Structure):
+    _fields_ = [("dL", C.c_void_p), ("next_o", C.c_void_p), ("next_beta", C.c_void_p), ("next_pdf", C.c_void_p),
+                ("next_alive", C.c_void_p), ("staint", C.c_void_p), ("cat", C.c_void_p), ("cls", C.c_void_p),
+                ("flags", C.c_void_p), ("local", C.c_void_p), ("world", C.c_void_p)]
 
 
 def lib():
@@ -96,6 +107,11 @@ def lib():
         L.orc_pdf_ggx.restype = C.c_double
         L.orc_render_tiles.argtypes = [vp, C.POINTER(_Camera), C.POINTER(_Params), u32, u32,
                                        C.POINTER(_Outputs)]
+        L.orc_trace_bound.argtypes = [vp, vp, vp, u32, i32, vp, vp, vp, vp]
+        L.orc_replay_step.argtypes = [vp, C.POINTER(_Camera), C.POINTER(_Params), u32, u32, u32, u32,
+                                      C.POINTER(_ReplayIn), C.POINTER(_ReplayOut)]
+        L.orc_camera_ray.argtypes = [C.POINTER(_Camera), u32, u32, C.c_float, C.c_float, vp]
+        L.orc_spawn_point.argtypes = [vp, vp, C.c_double, vp, C.c_double, vp]
         _lib = L
     return _lib
 
@@ -245,11 +261,98 @@ def trace(scene: Scene, rays, skip=None, use_bvh=True):
     return prim, t, fr
 
 
+def trace_bound(scene: Scene, rays, skip=None, use_bvh=True):
+    """trace() plus the FP32 error scale of each winning hit's t (0 on a miss)."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32)
+    n = rays.shape[0]
+    sk = None if skip is None else np.ascontiguousarray(skip, dtype=np.int32)
+    prim = np.zeros(n, dtype=np.int32)
+    t = np.zeros(n, dtype=np.float64)
+    fr = np.zeros(n, dtype=np.uint8)
+    terr = np.zeros(n, dtype=np.float64)
+    lib().orc_trace_bound(scene.h, _p(rays), _p(sk), n, int(use_bvh), _p(prim), _p(t), _p(fr), _p(terr))
+    return prim, t, fr, terr
+
+
+def _camc(cam):
+    return _Camera((C.c_float * 3)(*cam.pos), (C.c_float * 3)(*cam.look_at), (C.c_float * 3)(*cam.up),
+                   cam.vfov_deg, cam.width, cam.height)
+
+
+def camera_ray(cam, px, py, u, v):
+    """Primary ray direction (float32[3]) through pixel (px, py) jittered by (u, v)."""
+    d = np.zeros(3, dtype=np.float32)
+    lib().orc_camera_ray(C.byref(_camc(cam)), int(px), int(py), float(np.float32(u)), float(np.float32(v)), _p(d))
+    return d
+
+
+def spawn_point(o, d, t, n, side=1.0):
+    """Spawn point (float64[3]) of a ray leaving the surface hit at o + t d with normal n."""
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    n = np.ascontiguousarray(n, dtype=np.float32)
+    out = np.zeros(3, dtype=np.float64)
+    lib().orc_spawn_point(_p(o), _p(d), float(t), _p(n), float(side), _p(out))
+    return out
+
+
+def _params(spp, B, mode, tile, K, interleave, frame_base, reuse_depth, nee, hybrid_donor, nee_shared, seed,
+            diffuse_roughness):
+    W, H = tile
+    return _Params(spp, B, MODES[mode] if isinstance(mode, str) else mode, W, H, K, int(interleave),
+                   frame_base, reuse_depth, (1 if nee else 0) | (2 if hybrid_donor else 0) | (4 if nee_shared else 0),
+                   seed, float(diffuse_roughness))
+
+
+def replay_step(scene: Scene, cam, bounce, ray, prim, t, beta, *, max_bounces, mode="direction_reuse",
+                tile=(8, 8), k=None, interleave=True, seed=0, frame=0, reuse_depth=0, nee=False,
+                hybrid_donor=False, nee_shared=False, diffuse_roughness=0.0, tiles=None, threads=None):
+    """Replay mode: recompute shading step ``bounce`` (1..B; B + 1 = the end of the last ray)
+    of one frame from another renderer's captured inputs of trace bounce-1, per pixel:
+    ``ray`` (npx, 8) float32, ``prim`` (npx,) int32 (-2 = not traced), ``t`` (npx,) float32,
+    ``beta`` (npx, 4) float32.  Returns a dict of per-pixel arrays: dL, next_o, next_beta,
+    next_pdf, next_alive, staint, cat, cls, flags, local, world."""
+    W, H = tile
+    K = W * H if k is None else k
+    w, h = cam.width, cam.height
+    npx = w * h
+    ntiles = ((w + W - 1) // W) * ((h + H - 1) // H)
+    t0, t1 = (0, ntiles) if tiles is None else tiles
+    ray = np.ascontiguousarray(ray, dtype=np.float32).reshape(npx, 8)
+    prim = np.ascontiguousarray(prim, dtype=np.int32).reshape(npx)
+    t = np.ascontiguousarray(t, dtype=np.float32).reshape(npx)
+    beta = np.ascontiguousarray(beta, dtype=np.float32).reshape(npx, 4)
+    res = dict(dL=np.zeros((npx, 3)), next_o=np.full((npx, 3), np.nan), next_beta=np.full((npx, 3), np.nan, np.float32),
+               next_pdf=np.full(npx, np.nan), next_alive=np.zeros(npx, np.uint8), staint=np.zeros(npx, np.uint8),
+               cat=np.full(npx, 255, np.uint8), cls=np.zeros(npx, np.uint8), flags=np.zeros(npx, np.uint8),
+               local=np.zeros((npx, 3), np.float32), world=np.zeros((npx, 3), np.float32))
+    camc = _camc(cam)
+    par = _params(1, max_bounces, mode, tile, K, interleave, frame, reuse_depth, nee, hybrid_donor, nee_shared,
+                  seed, diffuse_roughness)
+    rin = _ReplayIn(_p(ray), _p(prim), _p(t), _p(beta))
+    rout = _ReplayOut(*[_p(res[key]) for key in ("dL", "next_o", "next_beta", "next_pdf", "next_alive", "staint",
+                                                 "cat", "cls", "flags", "local", "world")])
+    nthreads = threads or max(1, min(os.cpu_count() or 1, t1 - t0))
+    bounds = np.linspace(t0, t1, nthreads + 1).astype(int)
+
+    def work(i):
+        lib().orc_replay_step(scene.h, C.byref(camc), C.byref(par), frame, bounce, int(bounds[i]),
+                              int(bounds[i + 1]), C.byref(rin), C.byref(rout))
+
+    ths = [threading.Thread(target=work, args=(i,)) for i in range(nthreads) if bounds[i] < bounds[i + 1]]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    return res
+
+
 def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=None,
            interleave=True, seed=0, frame_base=0, reuse_depth=0, debug=False, threads=None,
            tiles=None, accum=None, nee=False, hybrid_donor=False, nee_shared=False, diffuse_roughness=0.0):
     """Run the oracle path tracer.  Returns a dict with ``rgb`` (mean radiance, float64 h x w x 3),
-    ``taint`` (h x w uint8), ``counters`` and, with debug=True (spp 1), per-bounce arrays.
+    ``taint`` (h x w uint8), ``counters`` and, with debug=True (spp 1), per-bounce arrays
+    (debug="replay" adds the replay capture: ray, t, beta of every trace).
     ``tiles`` = (begin, end) restricts the work to a tile range (other pixels stay 0).
     ``accum`` (npx x 3 float64) continues an earlier accumulation in place (progressive
     rendering resumed at ``frame_base``).  ``nee`` adds next-event estimation (one light
@@ -275,6 +378,9 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
         dbg = dict(prim=np.full((B + 1, npx), -2, dtype=np.int32), cat=np.full((B, npx), 255, np.uint8),
                    cls=np.zeros((B, npx), np.uint8), flags=np.zeros((B, npx), np.uint8),
                    local=np.zeros((B, npx, 3), np.float32), world=np.zeros((B, npx, 3), np.float32))
+        if debug == "replay":
+            dbg.update(ray=np.zeros((B + 1, npx, 8), np.float32), t=np.full((B + 1, npx), np.nan, np.float32),
+                       beta=np.zeros((B + 1, npx, 4), np.float32))
     camc = _Camera((C.c_float * 3)(*cam.pos), (C.c_float * 3)(*cam.look_at), (C.c_float * 3)(*cam.up),
                    cam.vfov_deg, w, h)
     par = _Params(spp, B, MODES[mode] if isinstance(mode, str) else mode, W, H, K, int(interleave),
@@ -286,7 +392,8 @@ def render(scene: Scene, cam, *, spp=1, max_bounces=1, mode="direction_reuse", t
 
     def work(i):
         o = _Outputs(_p(accum), _p(taint), _p(dbg.get("prim")), _p(dbg.get("cat")), _p(dbg.get("cls")),
-                     _p(dbg.get("flags")), _p(dbg.get("local")), _p(dbg.get("world")), _p(counters[i]))
+                     _p(dbg.get("flags")), _p(dbg.get("local")), _p(dbg.get("world")), _p(counters[i]),
+                     _p(dbg.get("ray")), _p(dbg.get("t")), _p(dbg.get("beta")))
         lib().orc_render_tiles(scene.h, C.byref(camc), C.byref(par), int(bounds[i]), int(bounds[i + 1]),
                                C.byref(o))
 

@@ -737,8 +737,8 @@ static void traverse(const orc_scene* s, const double* o, const double* d, int32
     *omax_out = omax;
 }
 
-static void trace_ray(const orc_scene* s, const double* o, const double* d, int32_t skip, int use_bvh,
-                      int32_t* prim, double* tout, uint8_t* fragile) {
+static void trace_ray_bound(const orc_scene* s, const double* o, const double* d, int32_t skip, int use_bvh,
+                            int32_t* prim, double* tout, uint8_t* fragile, double* terr) {
     tstate st;
     double omax;
     traverse(s, o, d, skip, use_bvh, &st, &omax);
@@ -760,6 +760,12 @@ static void trace_ray(const orc_scene* s, const double* o, const double* d, int3
      * ray origin relative to the coordinates' magnitude) */
     int tbad = st.found && st.terr_best > 1e-5 * st.tbest;
     *fragile = (uint8_t)((st.fragile ? 1 : 0) | (tbad ? 2 : 0));
+    if (terr) *terr = st.found ? st.terr_best : 0.0;
+}
+
+static void trace_ray(const orc_scene* s, const double* o, const double* d, int32_t skip, int use_bvh,
+                      int32_t* prim, double* tout, uint8_t* fragile) {
+    trace_ray_bound(s, o, d, skip, use_bvh, prim, tout, fragile, NULL);
 }
 
 /* Visibility of a shadow ray: occluded when some triangle other than `skip` is hit at
@@ -828,10 +834,16 @@ uint32_t orc_scene_lights(const orc_scene* s, float* total) {
 
 void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n, int use_bvh,
                int32_t* prim, double* t, uint8_t* fragile) {
+    orc_trace_bound(s, rays, skip_prim, n, use_bvh, prim, t, fragile, NULL);
+}
+
+void orc_trace_bound(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n, int use_bvh,
+                     int32_t* prim, double* t, uint8_t* fragile, double* terr) {
     for (uint32_t i = 0; i < n; ++i) {
         double o[3] = {rays[8 * i + 0], rays[8 * i + 1], rays[8 * i + 2]};
         double d[3] = {rays[8 * i + 4], rays[8 * i + 5], rays[8 * i + 6]};
-        trace_ray(s, o, d, skip_prim ? skip_prim[i] : -1, use_bvh, &prim[i], &t[i], &fragile[i]);
+        trace_ray_bound(s, o, d, skip_prim ? skip_prim[i] : -1, use_bvh, &prim[i], &t[i], &fragile[i],
+                        terr ? &terr[i] : NULL);
     }
 }
 
@@ -878,6 +890,14 @@ static f3 camera_dir(const cam_basis* b, uint32_t w, uint32_t h, uint32_t px, ui
     f3 d = f3m((b->fwd.x + sx * b->right.x) + sy * b->up.x, (b->fwd.y + sx * b->right.y) + sy * b->up.y,
                (b->fwd.z + sx * b->right.z) + sy * b->up.z);
     return f3normalize(d);
+}
+
+void orc_camera_ray(const orc_camera* cam, uint32_t px, uint32_t py, float u, float v, float* d) {
+    cam_basis b = make_camera(cam);
+    f3 r = camera_dir(&b, cam->width, cam->height, px, py, u, v);
+    d[0] = r.x;
+    d[1] = r.y;
+    d[2] = r.z;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -1082,16 +1102,19 @@ static double emit_weight(const orc_scene* s, const pstate* ps) {
 /* Spawn point of the next ray: p = o + t d in FP64, offset by 2^-18 max(1, |p|_inf) along
  * the shading normal times side (+1 for a ray leaving on the incoming side, -1 for a
  * transmitted one), so that the new ray clears the surface it leaves. */
-static void spawn_point(const pstate* ps, double side, double* out) {
+void orc_spawn_point(const double* o, const float* d, double t, const float* n, double side, double* out) {
     double pt[3], amax = 1.0;
-    double dd[3] = {ps->d.x, ps->d.y, ps->d.z};
     for (int k = 0; k < 3; ++k) {
-        pt[k] = ps->o[k] + ps->t * dd[k];
+        pt[k] = o[k] + t * (double)d[k];
         if (fabs(pt[k]) > amax) amax = fabs(pt[k]);
     }
     double eps = 0x1.0p-18 * amax;
-    double nn[3] = {ps->n.x, ps->n.y, ps->n.z};
-    for (int k = 0; k < 3; ++k) out[k] = pt[k] + (side * eps) * nn[k];
+    for (int k = 0; k < 3; ++k) out[k] = pt[k] + (side * eps) * (double)n[k];
+}
+
+static void spawn_point(const pstate* ps, double side, double* out) {
+    float d[3] = {ps->d.x, ps->d.y, ps->d.z}, n[3] = {ps->n.x, ps->n.y, ps->n.z};
+    orc_spawn_point(ps->o, d, ps->t, n, side, out);
 }
 
 #define SHADOW_TMAX (1.0 - 0x1.0p-10) /* shadow rays run to 1 - 2^-10 of the way to the light point */
@@ -1161,6 +1184,23 @@ static void next_event(const orc_scene* s, uint64_t seed, uint32_t frame, uint32
     for (int k = 0; k < 3; ++k) ps->L[k] += (double)ps->beta[k] * f[k] * (double)le[k] * g;
 }
 
+/* Replay capture of trace row di: the ray as a float record, its throughput and density. */
+static void capture_ray(const pstate* ps, orc_outputs* out, uint32_t di) {
+    if (!out->dbg_ray) return;
+    float* r = &out->dbg_ray[8 * (size_t)di];
+    int32_t skip = ps->hit;
+    r[0] = (float)ps->o[0];
+    r[1] = (float)ps->o[1];
+    r[2] = (float)ps->o[2];
+    memcpy(&r[3], &skip, sizeof(skip));
+    r[4] = ps->d.x;
+    r[5] = ps->d.y;
+    r[6] = ps->d.z;
+    r[7] = INFINITY;
+    for (int k = 0; k < 3; ++k) out->dbg_beta[4 * (size_t)di + k] = ps->beta[k];
+    out->dbg_beta[4 * (size_t)di + 3] = (float)ps->pdf;
+}
+
 static void trace_path(const orc_scene* s, pstate* ps, uint64_t* counters) {
     int32_t prim;
     double t;
@@ -1172,6 +1212,197 @@ static void trace_path(const orc_scene* s, pstate* ps, uint64_t* counters) {
     if (fr & 1) {
         ps->taint = 1;
         counters[2]++;
+    }
+}
+
+/* One shading step of the path (bounce b, Sec. 3.2) over the m slots of one tile, in the
+ * paper's order: the hits of trace b-1 are shaded (environment, emission, or a shading point
+ * with its frame and class), next-event estimation adds its light samples, then every group
+ * is classified and its members' exit directions are chosen (own samples, or the reused
+ * direction of the group's category), and each continuing path spawns its next ray and
+ * multiplies its throughput.  The per-pixel debug outputs, when requested, go to row
+ * dbg_row of out's per-bounce arrays. */
+static void shade_step(const orc_scene* s, const orc_params* p, uint32_t f, uint32_t b, uint32_t m, pstate* slot,
+                       f3* sumbuf, orc_outputs* out, uint32_t dbg_row, uint64_t* cnt_local) {
+    const uint32_t K = p->k;
+    /* shade the hits of trace b-1: environment, emission, or a shading point */
+    for (uint32_t j = 0; j < m; ++j) {
+        pstate* ps = &slot[j];
+        if (ps->pixel < 0 || !ps->alive) continue;
+        if (ps->hit < 0) {
+            for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
+            ps->alive = 0;
+            continue;
+        }
+        uint32_t mt = s->mat_type[s->tri_mat[ps->hit]];
+        if (mt == MAT_EMITTER) {
+            const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
+            double wb = (p->opts & ORC_OPT_NEE) ? emit_weight(s, ps) : 1.0;
+            for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
+            ps->alive = 0;
+            continue;
+        }
+        shade_setup(s, ps, p->diffuse_roughness,
+                    (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
+                        (p->reuse_depth == 0 || b <= p->reuse_depth));
+    }
+    /* next-event estimation at the shading points; with shared light samples
+     * every member of a group joins the point drawn from the stream of the
+     * group's first alive member (each member's point is still distributed by
+     * area, so every pixel's estimate keeps its mean) */
+    if (p->opts & ORC_OPT_NEE) {
+        for (uint32_t g = 0; g < m / K; ++g) {
+            pstate* G = &slot[g * K];
+            int32_t owner = -1;
+            for (uint32_t j = 0; j < K && owner < 0; ++j)
+                if (G[j].pixel >= 0 && G[j].alive) owner = G[j].pixel;
+            for (uint32_t j = 0; j < K; ++j) {
+                pstate* ps = &G[j];
+                if (ps->pixel < 0 || !ps->alive) continue;
+                uint32_t ty = s->mat_type[ps->mat];
+                if (ty == MAT_MIRROR || ty == MAT_DIELECTRIC) continue;
+                next_event(s, p->seed, f, b, ps, (p->opts & ORC_OPT_NEE_SHARED) ? owner : ps->pixel,
+                           cnt_local);
+            }
+        }
+    }
+    const int reuse_now = (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
+                          (p->reuse_depth == 0 || b <= p->reuse_depth);
+    for (uint32_t g = 0; g < m / K; ++g) {
+        pstate* G = &slot[g * K];
+        /* Sec. 3.2: classify the group by the materials of its shading points */
+        int nd = 0, ng = 0, taint = 0;
+        for (uint32_t j = 0; j < K; ++j) {
+            if (G[j].pixel < 0) continue;
+            taint |= G[j].taint;
+            if (!G[j].alive) continue;
+            if (G[j].cls == CLS_DIFFUSE) nd++;
+            else ng++;
+        }
+        int cat = nd && ng ? CAT_HYBRID : (nd ? CAT_DIFFUSE : (ng ? CAT_GLOSSY : CAT_EMPTY));
+        if (reuse_now && taint)
+            for (uint32_t j = 0; j < K; ++j)
+                if (G[j].pixel >= 0) G[j].taint = 1;
+        for (uint32_t j = 0; j < K; ++j)
+            if (G[j].pixel >= 0 && G[j].alive) own_sample(s, p->seed, f, b, &G[j]);
+        if (reuse_now && p->mode == ORC_WORLD_REUSE) {
+            /* Sec. 3.1 direct reuse: the first member's world-space exit direction,
+             * each member weighing it with its own material */
+            int donor = -1;
+            for (uint32_t j = 0; j < K && donor < 0; ++j)
+                if (G[j].pixel >= 0 && G[j].alive) donor = (int)j;
+            if (donor >= 0 && G[donor].valid) {
+                f3 wd = to_world(&G[donor], G[donor].wl);
+                for (uint32_t j = 0; j < K; ++j) {
+                    pstate* ps = &G[j];
+                    if (ps->pixel < 0 || !ps->alive || ps->cls != CLS_DIFFUSE) continue;
+                    f3 l = f3m(f3dot(wd, ps->T), f3dot(wd, ps->B), f3dot(wd, ps->n));
+                    take_direction(s, ps, l);
+                    if (!(ps->hemi * l.z > 0.0f)) ps->valid = 0; /* outside the lobe: f = 0 */
+                }
+            }
+        } else if (reuse_now && cat == CAT_DIFFUSE) {
+            /* diffuse group: every member reuses the first member's exit direction */
+            int donor = -1;
+            for (uint32_t j = 0; j < K && donor < 0; ++j)
+                if (G[j].pixel >= 0 && G[j].alive) donor = (int)j;
+            f3 wl = G[donor].wl;
+            for (uint32_t j = 0; j < K; ++j)
+                if (G[j].pixel >= 0 && G[j].alive) take_direction(s, &G[j], into_lobe(&G[j], wl));
+        } else if (reuse_now && cat == CAT_HYBRID && (p->opts & ORC_OPT_HYBRID_DONOR)) {
+            /* hybrid group, donor reading (an option, not the paper's rule): the
+             * diffuse members reuse the first diffuse member's own cosine sample,
+             * the glossy/specular members keep theirs; every direction keeps its
+             * sampling density, so the estimate stays unbiased */
+            int donor = -1;
+            for (uint32_t j = 0; j < K && donor < 0; ++j)
+                if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE) donor = (int)j;
+            f3 wl = G[donor].wl;
+            for (uint32_t j = 0; j < K; ++j)
+                if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE)
+                    take_direction(s, &G[j], into_lobe(&G[j], wl));
+        } else if (reuse_now && cat == CAT_HYBRID) {
+            /* hybrid group: diffuse members take the normalised tangent-space sum of
+             * the valid glossy/specular exit directions */
+            for (uint32_t j = 0; j < K; ++j) {
+                int use = G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_GLOSSY && G[j].valid;
+                sumbuf[j] = use ? G[j].wl : f3m(0.0f, 0.0f, 0.0f);
+            }
+            f3 v = tree_sum(sumbuf, K);
+            float l2 = f3dot(v, v);
+            f3 wl;
+            int keep_rough = 0;
+            if (l2 > 0.0f) {
+                float l = sqrtf(l2);
+                wl = f3m(v.x / l, v.y / l, v.z / l);
+                /* a rough GGX member (roughness threshold) keeps its own cosine
+                 * sample: its weight pi f at the glossy average, near its own
+                 * specular peak, would be far above 1 */
+                keep_rough = 1;
+            } else {
+                /* no valid glossy sample: fall back to the diffuse-group rule
+                 * among the diffuse members */
+                int donor = -1;
+                for (uint32_t j = 0; j < K && donor < 0; ++j)
+                    if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE) donor = (int)j;
+                wl = G[donor].wl;
+            }
+            for (uint32_t j = 0; j < K; ++j)
+                if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE &&
+                    !(keep_rough && G[j].cosgl))
+                    take_direction(s, &G[j], into_lobe(&G[j], wl));
+        }
+        /* glossy groups and the independent mode keep every member's own sample */
+        for (uint32_t j = 0; j < K; ++j) {
+            pstate* ps = &G[j];
+            if (ps->pixel < 0) continue;
+            uint32_t di = dbg_row + (uint32_t)ps->pixel;
+            if (out->dbg_cat) {
+                out->dbg_cat[di] = (uint8_t)cat;
+                out->dbg_cls[di] = (uint8_t)(!ps->alive ? CLS_NONE
+                                             : (ps->hemi < 0.0f ? DBG_CLS_TRANSLUCENT : ps->cls));
+                out->dbg_flags[di] = (uint8_t)((ps->alive ? 1 : 0) | (ps->alive && ps->valid ? 2 : 0) |
+                                               (ps->taint ? 4 : 0));
+                f3 wv = ps->alive ? to_world(ps, ps->wl) : f3m(0.0f, 0.0f, 0.0f);
+                f3 lv = ps->alive ? ps->wl : f3m(0.0f, 0.0f, 0.0f);
+                out->dbg_local[3 * di + 0] = lv.x;
+                out->dbg_local[3 * di + 1] = lv.y;
+                out->dbg_local[3 * di + 2] = lv.z;
+                out->dbg_world[3 * di + 0] = wv.x;
+                out->dbg_world[3 * di + 1] = wv.y;
+                out->dbg_world[3 * di + 2] = wv.z;
+            }
+            if (!ps->alive) continue;
+            if (!ps->valid) {
+                ps->alive = 0;
+                continue;
+            }
+            double o2[3];
+            spawn_point(ps, ps->wl.z < 0.0f ? -1.0 : 1.0, o2);
+            for (int k = 0; k < 3; ++k) ps->o[k] = o2[k];
+            ps->d = to_world(ps, ps->wl);
+            ps->pdf = bsdf_pdf(s, ps, ps->wl);
+            for (int k = 0; k < 3; ++k) ps->beta[k] = ps->beta[k] * ps->w[k];
+        }
+    }
+}
+
+/* After the last secondary ray of a path only the environment (miss) or an emitter's
+ * radiance where that ray ended is added. */
+static void final_step(const orc_scene* s, const orc_params* p, pstate* slot, uint32_t m) {
+    /* after the last secondary ray only the environment or an emitter is added */
+    for (uint32_t j = 0; j < m; ++j) {
+        pstate* ps = &slot[j];
+        if (ps->pixel < 0) continue;
+        if (ps->alive) {
+            if (ps->hit < 0) {
+                for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
+            } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER) {
+                const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
+                double wb = (p->opts & ORC_OPT_NEE) ? emit_weight(s, ps) : 1.0;
+                for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
+            }
+        }
     }
 }
 
@@ -1212,193 +1443,29 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
                 ps->o[1] = cb.pos.y;
                 ps->o[2] = cb.pos.z;
                 ps->hit = -1;
+                capture_ray(ps, out, (uint32_t)ps->pixel);
                 trace_path(s, ps, cnt_local);
                 cnt_local[0]++;
                 if (out->dbg_prim) out->dbg_prim[ps->pixel] = ps->hit;
+                if (out->dbg_t) out->dbg_t[ps->pixel] = (float)ps->t;
             }
             for (uint32_t b = 1; b <= B; ++b) {
-                /* shade the hits of trace b-1: environment, emission, or a shading point */
-                for (uint32_t j = 0; j < m; ++j) {
-                    pstate* ps = &slot[j];
-                    if (ps->pixel < 0 || !ps->alive) continue;
-                    if (ps->hit < 0) {
-                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
-                        ps->alive = 0;
-                        continue;
-                    }
-                    uint32_t mt = s->mat_type[s->tri_mat[ps->hit]];
-                    if (mt == MAT_EMITTER) {
-                        const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        double wb = (p->opts & ORC_OPT_NEE) ? emit_weight(s, ps) : 1.0;
-                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
-                        ps->alive = 0;
-                        continue;
-                    }
-                    shade_setup(s, ps, p->diffuse_roughness,
-                                (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
-                                    (p->reuse_depth == 0 || b <= p->reuse_depth));
-                }
-                /* next-event estimation at the shading points; with shared light samples
-                 * every member of a group joins the point drawn from the stream of the
-                 * group's first alive member (each member's point is still distributed by
-                 * area, so every pixel's estimate keeps its mean) */
-                if (p->opts & ORC_OPT_NEE) {
-                    for (uint32_t g = 0; g < m / K; ++g) {
-                        pstate* G = &slot[g * K];
-                        int32_t owner = -1;
-                        for (uint32_t j = 0; j < K && owner < 0; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive) owner = G[j].pixel;
-                        for (uint32_t j = 0; j < K; ++j) {
-                            pstate* ps = &G[j];
-                            if (ps->pixel < 0 || !ps->alive) continue;
-                            uint32_t ty = s->mat_type[ps->mat];
-                            if (ty == MAT_MIRROR || ty == MAT_DIELECTRIC) continue;
-                            next_event(s, p->seed, f, b, ps, (p->opts & ORC_OPT_NEE_SHARED) ? owner : ps->pixel,
-                                       cnt_local);
-                        }
-                    }
-                }
-                const int reuse_now = (p->mode == ORC_DIRECTION_REUSE || p->mode == ORC_WORLD_REUSE) &&
-                                      (p->reuse_depth == 0 || b <= p->reuse_depth);
-                for (uint32_t g = 0; g < m / K; ++g) {
-                    pstate* G = &slot[g * K];
-                    /* Sec. 3.2: classify the group by the materials of its shading points */
-                    int nd = 0, ng = 0, taint = 0;
-                    for (uint32_t j = 0; j < K; ++j) {
-                        if (G[j].pixel < 0) continue;
-                        taint |= G[j].taint;
-                        if (!G[j].alive) continue;
-                        if (G[j].cls == CLS_DIFFUSE) nd++;
-                        else ng++;
-                    }
-                    int cat = nd && ng ? CAT_HYBRID : (nd ? CAT_DIFFUSE : (ng ? CAT_GLOSSY : CAT_EMPTY));
-                    if (reuse_now && taint)
-                        for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0) G[j].taint = 1;
-                    for (uint32_t j = 0; j < K; ++j)
-                        if (G[j].pixel >= 0 && G[j].alive) own_sample(s, p->seed, f, b, &G[j]);
-                    if (reuse_now && p->mode == ORC_WORLD_REUSE) {
-                        /* Sec. 3.1 direct reuse: the first member's world-space exit direction,
-                         * each member weighing it with its own material */
-                        int donor = -1;
-                        for (uint32_t j = 0; j < K && donor < 0; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive) donor = (int)j;
-                        if (donor >= 0 && G[donor].valid) {
-                            f3 wd = to_world(&G[donor], G[donor].wl);
-                            for (uint32_t j = 0; j < K; ++j) {
-                                pstate* ps = &G[j];
-                                if (ps->pixel < 0 || !ps->alive || ps->cls != CLS_DIFFUSE) continue;
-                                f3 l = f3m(f3dot(wd, ps->T), f3dot(wd, ps->B), f3dot(wd, ps->n));
-                                take_direction(s, ps, l);
-                                if (!(ps->hemi * l.z > 0.0f)) ps->valid = 0; /* outside the lobe: f = 0 */
-                            }
-                        }
-                    } else if (reuse_now && cat == CAT_DIFFUSE) {
-                        /* diffuse group: every member reuses the first member's exit direction */
-                        int donor = -1;
-                        for (uint32_t j = 0; j < K && donor < 0; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive) donor = (int)j;
-                        f3 wl = G[donor].wl;
-                        for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive) take_direction(s, &G[j], into_lobe(&G[j], wl));
-                    } else if (reuse_now && cat == CAT_HYBRID && (p->opts & ORC_OPT_HYBRID_DONOR)) {
-                        /* hybrid group, donor reading (an option, not the paper's rule): the
-                         * diffuse members reuse the first diffuse member's own cosine sample,
-                         * the glossy/specular members keep theirs; every direction keeps its
-                         * sampling density, so the estimate stays unbiased */
-                        int donor = -1;
-                        for (uint32_t j = 0; j < K && donor < 0; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE) donor = (int)j;
-                        f3 wl = G[donor].wl;
-                        for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE)
-                                take_direction(s, &G[j], into_lobe(&G[j], wl));
-                    } else if (reuse_now && cat == CAT_HYBRID) {
-                        /* hybrid group: diffuse members take the normalised tangent-space sum of
-                         * the valid glossy/specular exit directions */
-                        for (uint32_t j = 0; j < K; ++j) {
-                            int use = G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_GLOSSY && G[j].valid;
-                            sumbuf[j] = use ? G[j].wl : f3m(0.0f, 0.0f, 0.0f);
-                        }
-                        f3 v = tree_sum(sumbuf, K);
-                        float l2 = f3dot(v, v);
-                        f3 wl;
-                        int keep_rough = 0;
-                        if (l2 > 0.0f) {
-                            float l = sqrtf(l2);
-                            wl = f3m(v.x / l, v.y / l, v.z / l);
-                            /* a rough GGX member (roughness threshold) keeps its own cosine
-                             * sample: its weight pi f at the glossy average, near its own
-                             * specular peak, would be far above 1 */
-                            keep_rough = 1;
-                        } else {
-                            /* no valid glossy sample: fall back to the diffuse-group rule
-                             * among the diffuse members */
-                            int donor = -1;
-                            for (uint32_t j = 0; j < K && donor < 0; ++j)
-                                if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE) donor = (int)j;
-                            wl = G[donor].wl;
-                        }
-                        for (uint32_t j = 0; j < K; ++j)
-                            if (G[j].pixel >= 0 && G[j].alive && G[j].cls == CLS_DIFFUSE &&
-                                !(keep_rough && G[j].cosgl))
-                                take_direction(s, &G[j], into_lobe(&G[j], wl));
-                    }
-                    /* glossy groups and the independent mode keep every member's own sample */
-                    for (uint32_t j = 0; j < K; ++j) {
-                        pstate* ps = &G[j];
-                        if (ps->pixel < 0) continue;
-                        uint32_t di = (b - 1) * npx + (uint32_t)ps->pixel;
-                        if (out->dbg_cat) {
-                            out->dbg_cat[di] = (uint8_t)cat;
-                            out->dbg_cls[di] = (uint8_t)(!ps->alive ? CLS_NONE
-                                                         : (ps->hemi < 0.0f ? DBG_CLS_TRANSLUCENT : ps->cls));
-                            out->dbg_flags[di] = (uint8_t)((ps->alive ? 1 : 0) | (ps->alive && ps->valid ? 2 : 0) |
-                                                           (ps->taint ? 4 : 0));
-                            f3 wv = ps->alive ? to_world(ps, ps->wl) : f3m(0.0f, 0.0f, 0.0f);
-                            f3 lv = ps->alive ? ps->wl : f3m(0.0f, 0.0f, 0.0f);
-                            out->dbg_local[3 * di + 0] = lv.x;
-                            out->dbg_local[3 * di + 1] = lv.y;
-                            out->dbg_local[3 * di + 2] = lv.z;
-                            out->dbg_world[3 * di + 0] = wv.x;
-                            out->dbg_world[3 * di + 1] = wv.y;
-                            out->dbg_world[3 * di + 2] = wv.z;
-                        }
-                        if (!ps->alive) continue;
-                        if (!ps->valid) {
-                            ps->alive = 0;
-                            continue;
-                        }
-                        double o2[3];
-                        spawn_point(ps, ps->wl.z < 0.0f ? -1.0 : 1.0, o2);
-                        for (int k = 0; k < 3; ++k) ps->o[k] = o2[k];
-                        ps->d = to_world(ps, ps->wl);
-                        ps->pdf = bsdf_pdf(s, ps, ps->wl);
-                        for (int k = 0; k < 3; ++k) ps->beta[k] = ps->beta[k] * ps->w[k];
-                    }
-                }
+                shade_step(s, p, f, b, m, slot, sumbuf, out, (b - 1) * npx, cnt_local);
                 /* trace the secondary rays of bounce b */
                 for (uint32_t j = 0; j < m; ++j) {
                     pstate* ps = &slot[j];
                     if (ps->pixel < 0 || !ps->alive) continue;
+                    capture_ray(ps, out, b * npx + (uint32_t)ps->pixel);
                     trace_path(s, ps, cnt_local);
                     cnt_local[1]++;
                     if (out->dbg_prim) out->dbg_prim[b * npx + (uint32_t)ps->pixel] = ps->hit;
+                    if (out->dbg_t) out->dbg_t[b * npx + (uint32_t)ps->pixel] = (float)ps->t;
                 }
             }
-            /* after the last secondary ray only the environment or an emitter is added */
+            final_step(s, p, slot, m);
             for (uint32_t j = 0; j < m; ++j) {
                 pstate* ps = &slot[j];
                 if (ps->pixel < 0) continue;
-                if (ps->alive) {
-                    if (ps->hit < 0) {
-                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * s->env[k]);
-                    } else if (s->mat_type[s->tri_mat[ps->hit]] == MAT_EMITTER) {
-                        const float* mp = &s->mat_params[7 * s->tri_mat[ps->hit]];
-                        double wb = (p->opts & ORC_OPT_NEE) ? emit_weight(s, ps) : 1.0;
-                        for (int k = 0; k < 3; ++k) ps->L[k] += (double)(ps->beta[k] * mp[4 + k]) * wb;
-                    }
-                }
                 for (int k = 0; k < 3; ++k) out->accum[3 * ps->pixel + k] += ps->L[k];
                 if (out->taint && (ps->taint || ps->staint)) out->taint[ps->pixel] = 1;
             }
@@ -1406,6 +1473,73 @@ void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_param
     }
     if (out->counters)
         for (int k = 0; k < 5; ++k) out->counters[k] += cnt_local[k];
+    free(sigma);
+    free(slot);
+    free(sumbuf);
+}
+
+/* Replay of one shading step on another renderer's captured state (see oracle.h): the tile's
+ * slots are filled from the inputs of trace b-1 (ray, hit, throughput), then the same
+ * shade_step (b <= B) or final_step (b = B + 1) as orc_render_tiles runs on them, so every
+ * stage after the trace is recomputed from exactly the state the other renderer had. */
+void orc_replay_step(const orc_scene* s, const orc_camera* cam, const orc_params* p, uint32_t frame, uint32_t bounce,
+                     uint32_t tile_begin, uint32_t tile_end, const orc_replay_in* in, orc_replay_out* out) {
+    const uint32_t W = p->tile_w, H = p->tile_h, m = W * H, K = p->k;
+    const uint32_t w = cam->width, h = cam->height;
+    const uint32_t ntx = (w + W - 1) / W;
+    uint32_t* sigma = (uint32_t*)malloc(sizeof(uint32_t) * m);
+    pstate* slot = (pstate*)malloc(sizeof(pstate) * m);
+    f3* sumbuf = (f3*)malloc(sizeof(f3) * K);
+    uint64_t cnt[5] = {0, 0, 0, 0, 0};
+    orc_outputs dbg;
+    memset(&dbg, 0, sizeof(dbg));
+    dbg.dbg_cat = out->cat;
+    dbg.dbg_cls = out->cls;
+    dbg.dbg_flags = out->flags;
+    dbg.dbg_local = out->local;
+    dbg.dbg_world = out->world;
+    for (uint32_t tile = tile_begin; tile < tile_end; ++tile) {
+        const uint32_t tx = tile % ntx, ty = tile / ntx;
+        orc_tile_sigma(W, H, tile, frame, p->seed, (int)p->interleave, sigma, NULL);
+        for (uint32_t j = 0; j < m; ++j) slot[j].pixel = -1;
+        for (uint32_t i = 0; i < m; ++i) {
+            uint32_t px = tx * W + i % W, py = ty * H + i / W;
+            if (px >= w || py >= h) continue;
+            pstate* ps = &slot[sigma[i]];
+            const uint32_t pix = py * w + px;
+            memset(ps, 0, sizeof(*ps));
+            ps->pixel = (int32_t)pix;
+            ps->alive = in->prim[pix] != -2; /* -2: the path ended before trace b-1 */
+            ps->hit = in->prim[pix];
+            ps->t = (double)in->t[pix];
+            for (int k = 0; k < 3; ++k) {
+                ps->o[k] = (double)in->ray[8 * pix + k];
+                ps->beta[k] = in->beta[4 * pix + k];
+            }
+            ps->d = f3m(in->ray[8 * pix + 4], in->ray[8 * pix + 5], in->ray[8 * pix + 6]);
+            ps->pdf = (double)in->beta[4 * pix + 3];
+            ps->hemi = 1.0f;
+        }
+        if (bounce <= p->max_bounces) {
+            shade_step(s, p, frame, bounce, m, slot, sumbuf, &dbg, 0, cnt);
+        } else {
+            final_step(s, p, slot, m);
+        }
+        for (uint32_t j = 0; j < m; ++j) {
+            const pstate* ps = &slot[j];
+            if (ps->pixel < 0) continue;
+            const uint32_t pix = (uint32_t)ps->pixel;
+            const int cont = bounce <= p->max_bounces && ps->alive;
+            for (int k = 0; k < 3; ++k) {
+                if (out->dL) out->dL[3 * pix + k] = ps->L[k];
+                if (out->next_o) out->next_o[3 * pix + k] = cont ? ps->o[k] : NAN;
+                if (out->next_beta) out->next_beta[3 * pix + k] = cont ? ps->beta[k] : NAN;
+            }
+            if (out->next_pdf) out->next_pdf[pix] = cont ? ps->pdf : NAN;
+            if (out->next_alive) out->next_alive[pix] = (uint8_t)cont;
+            if (out->staint) out->staint[pix] = (uint8_t)ps->staint;
+        }
+    }
     free(sigma);
     free(slot);
     free(sumbuf);

@@ -69,6 +69,12 @@ uint32_t orc_scene_nodes(const orc_scene* s);
 void orc_trace(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
                int use_bvh, int32_t* prim, double* t, uint8_t* fragile);
 
+/* orc_trace plus terr[i], the error scale an FP32 intersector's t can have for the winning
+ * hit: 4 * 2^-24 * (coordinate magnitude) / |d| / |cos| of the ray against the triangle's
+ * plane (0 on a miss). */
+void orc_trace_bound(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
+                     int use_bvh, int32_t* prim, double* t, uint8_t* fragile, double* terr);
+
 /* Shadow rays (n x 8 floats: origin, unused, direction, tmax): occluded if a triangle other
  * than skip_prim[i] is hit at 0 < t < tmax; fragile if FP32 could decide otherwise. */
 void orc_shadow(const orc_scene* s, const float* rays, const int32_t* skip_prim, uint32_t n,
@@ -129,11 +135,52 @@ typedef struct {
     float* dbg_world;   /* B*npx*3: world-space exit direction */
     uint64_t* counters; /* [0] primary rays, [1] secondary rays, [2] fragile decisions,
                            [3] shadow rays, [4] fragile shadow decisions */
+    /* optional replay capture (spp == 1), NULL to skip: what trace b received and returned */
+    float* dbg_ray;     /* (B+1)*npx*8: origin (rounded to float), skip id (int32 bits), direction, inf */
+    float* dbg_t;       /* (B+1)*npx: hit distance rounded to float (inf on a miss) */
+    float* dbg_beta;    /* (B+1)*npx*4: throughput rgb and the direction's density (rounded to float) */
 } orc_outputs;
 
 /* Render tiles [tile_begin, tile_end) of the image (Sec. 3, whole method). */
 void orc_render_tiles(const orc_scene* s, const orc_camera* cam, const orc_params* p,
                       uint32_t tile_begin, uint32_t tile_end, orc_outputs* out);
+
+/* Replay mode: one shading step recomputed from another renderer's captured state, so that
+ * each stage is checked on that renderer's own inputs (one fragile closest-hit decision then
+ * changes nothing downstream of it in the comparison).  Inputs, per pixel of the image (npx):
+ * what trace b-1 received and returned. */
+typedef struct {
+    const float* ray;     /* npx*8: o.xyz, (unused), d.xyz, (unused) of trace b-1 */
+    const int32_t* prim;  /* npx: its hit (original index), -1 miss, -2 not traced (path over) */
+    const float* t;       /* npx: its hit distance */
+    const float* beta;    /* npx*4: throughput rgb carried by the ray, w = its direction's density */
+} orc_replay_in;
+
+/* Outputs (each may be NULL), per pixel: what step b computes from those inputs. */
+typedef struct {
+    double* dL;           /* npx*3: radiance added at this step (environment, emission, light samples) */
+    double* next_o;       /* npx*3: origin of the spawned ray of trace b (FP64; NaN if none) */
+    float* next_beta;     /* npx*3: throughput it carries (NaN if none) */
+    double* next_pdf;     /* npx: density of its direction (MIS under next-event estimation) */
+    uint8_t* next_alive;  /* npx: 1 if the path spawned a ray */
+    uint8_t* staint;      /* npx: a fragile shadow-ray decision at this step */
+    uint8_t* cat, *cls, *flags; /* npx: as orc_outputs' per-bounce arrays, for step b */
+    float* local, *world; /* npx*3 */
+} orc_replay_out;
+
+/* Step `bounce` (1..B: shade, classify, reuse, spawn; B + 1: the environment or emission at
+ * the end of the last ray) of frame `frame` over tiles [tile_begin, tile_end). */
+void orc_replay_step(const orc_scene* s, const orc_camera* cam, const orc_params* p, uint32_t frame,
+                     uint32_t bounce, uint32_t tile_begin, uint32_t tile_end, const orc_replay_in* in,
+                     orc_replay_out* out);
+
+/* Primary ray direction through pixel (px, py) jittered by (u, v) in [0,1)^2 (pinhole camera,
+ * vertical field of view, row 0 at the top). */
+void orc_camera_ray(const orc_camera* cam, uint32_t px, uint32_t py, float u, float v, float* d);
+
+/* Spawn point of a ray leaving a surface: p = o + t d in FP64, then p + side eps n with
+ * eps = 2^-18 max(1, |p|_inf) (side +1: the incoming side of the surface, -1: through it). */
+void orc_spawn_point(const double* o, const float* d, double t, const float* n, double side, double* out);
 
 #ifdef __cplusplus
 }

@@ -84,7 +84,8 @@ class cr_bvh_report(C.Structure):
 
 class cr_debug(C.Structure):
     _fields_ = [("prim", C.c_void_p), ("cat", C.c_void_p), ("cls", C.c_void_p), ("flags", C.c_void_p),
-                ("local", C.c_void_p), ("world", C.c_void_p)]
+                ("local", C.c_void_p), ("world", C.c_void_p), ("ray", C.c_void_p), ("t", C.c_void_p),
+                ("beta", C.c_void_p)]
 
 
 class cr_job(C.Structure):
@@ -502,8 +503,9 @@ class Scene:
         return (prim, t, st.as_dict()) if stats else (prim, t)
 
 
-def debug_buffers(width, height, max_bounces, device="cuda"):
-    """Allocate (and pre-fill) the per-bounce capture buffers; returns (cr_debug, dict of tensors)."""
+def debug_buffers(width, height, max_bounces, device="cuda", replay=False):
+    """Allocate (and pre-fill) the per-bounce capture buffers; returns (cr_debug, dict of tensors).
+    replay=True adds the replay capture (ray, t, beta of every trace)."""
     import torch
     npx = width * height
     B = max_bounces
@@ -513,5 +515,11 @@ def debug_buffers(width, height, max_bounces, device="cuda"):
                 flags=torch.zeros((B, npx), dtype=torch.uint8, device=device),
                 local=torch.zeros((B, npx, 3), dtype=torch.float32, device=device),
                 world=torch.zeros((B, npx, 3), dtype=torch.float32, device=device))
-    d = cr_debug(*[bufs[k].data_ptr() for k in ("prim", "cat", "cls", "flags", "local", "world")])
+    names = ["prim", "cat", "cls", "flags", "local", "world"]
+    if replay:
+        bufs.update(ray=torch.zeros((B + 1, npx, 8), dtype=torch.float32, device=device),
+                    t=torch.full((B + 1, npx), float("nan"), dtype=torch.float32, device=device),
+                    beta=torch.zeros((B + 1, npx, 4), dtype=torch.float32, device=device))
+        names += ["ray", "t", "beta"]
+    d = cr_debug(*[bufs[k].data_ptr() for k in names])
     return d, bufs

@@ -828,6 +828,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     if (o.debug && spp != 1) return fail(CR_ERR_INVALID_ARG, "cr_render: debug capture needs spp == 1");
     if (o.debug && (!o.debug->prim || !o.debug->cat || !o.debug->cls || !o.debug->flags || !o.debug->local || !o.debug->world))
         return fail(CR_ERR_INVALID_ARG, "cr_render: debug capture needs all six buffers");
+    if (o.debug && (!o.debug->ray != !o.debug->t || !o.debug->ray != !o.debug->beta))
+        return fail(CR_ERR_INVALID_ARG, "cr_render: replay capture needs ray, t and beta together");
     cudaStream_t stream = static_cast<cudaStream_t>(o.stream);
     cr_status st = check_camera(cam);
     if (st != CR_OK) return st;

@@ -238,10 +238,21 @@ __device__ __forceinline__ void add_emission(const SceneDev& sc, const float4 v0
     L.z = fa(L.z, fm(fm(bt.z, m1.w), w));
 }
 
+// Replay capture: the ray trace b received (origin with its skip id, direction with tmax),
+// the distance it returned and the throughput it carried, at entry di = b * npx + pixel.
+__device__ __forceinline__ void capture_trace(const cr_debug& dbg, uint32_t di, const float4 o4, const float4 d4,
+                                              const int2 h, const float4 bt) {
+    reinterpret_cast<float4*>(dbg.ray)[2 * di + 0] = o4;
+    reinterpret_cast<float4*>(dbg.ray)[2 * di + 1] = d4;
+    dbg.t[di] = h.x >= 0 ? __int_as_float(h.y) : INFINITY;
+    reinterpret_cast<float4*>(dbg.beta)[di] = bt;
+}
+
 __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs& p, const SceneDev& sc, int slot,
                                              Member& mb, float3& L, const float4 bt, const int2 h, const float4 d4,
                                              const float tau) {
     if (a.dbg.prim) a.dbg.prim[(p.bounce - 1) * a.npx + mb.pix] = h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
+    if (a.dbg.ray) capture_trace(a.dbg, (p.bounce - 1) * a.npx + (uint32_t)mb.pix, a.ray_o[slot], d4, h, bt);
     if (h.x < 0) { // miss: environment
         add_environment(sc, bt, L);
         mb.alive = false;
@@ -1211,10 +1222,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // output, sum / spp, instead of the sum.
 __global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixel,
                                     const uint16_t* __restrict__ slot_job, const uint8_t* __restrict__ alive,
-                                    const int2* __restrict__ hit, const float4* __restrict__ ray_d,
-                                    const float4* __restrict__ beta, const float4* __restrict__ radiance,
-                                    uint32_t n_slots, float4* __restrict__ accum, int32_t* __restrict__ dbg_prim,
-                                    uint32_t dbg_npx) {
+                                    const int2* __restrict__ hit, const float4* __restrict__ ray_o,
+                                    const float4* __restrict__ ray_d, const float4* __restrict__ beta,
+                                    const float4* __restrict__ radiance, uint32_t n_slots,
+                                    float4* __restrict__ accum, cr_debug dbg, uint32_t dbg_npx) {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
     const int pix = pixel[s];
@@ -1227,9 +1238,10 @@ __global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixe
         const SceneDev& sc = p.scenes[J.scene];
         const int2 h = hit[s];
         const float4 bt = beta[s];
-        if (dbg_prim)
-            dbg_prim[(p.bounce - 1) * dbg_npx + (uint32_t)pix] =
+        if (dbg.prim)
+            dbg.prim[(p.bounce - 1) * dbg_npx + (uint32_t)pix] =
                 h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
+        if (dbg.ray) capture_trace(dbg, (p.bounce - 1) * dbg_npx + (uint32_t)pix, ray_o[s], ray_d[s], h, bt);
         if (h.x < 0) {
             add_environment(sc, bt, L);
         } else {
@@ -1379,7 +1391,7 @@ static ShadeArgs shade_args(const PassArgs& p, PathBuffers& b, bool first, bool 
     a.group_count = first ? nullptr : b.counts + 8 + 2 * (p.bounce - 1) + 1;
     a.n_groups_max = b.n_groups;
     if (dbg) a.dbg = *dbg;
-    else a.dbg = cr_debug{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    else a.dbg = cr_debug{};
     a.npx = p.npx;
     const bool nee = p.nee && b.shadow_d;
     a.shadow_o = nee ? b.shadow_o : nullptr;
@@ -1434,9 +1446,9 @@ void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t 
 void launch_finish_accumulate(const PassArgs& p, PathBuffers& b, const cr_debug* dbg, cudaStream_t st,
                               LaunchCount& lc) {
     const uint32_t n_slots = p.n_tiles * p.m;
-    k_finish_accumulate<<<(n_slots + 255) / 256, 256, 0, st>>>(p, b.pixel, b.slot_job, b.alive, b.hit, b.ray_d,
-                                                               b.beta, b.radiance, n_slots, b.accum,
-                                                               dbg ? dbg->prim : nullptr, p.npx);
+    k_finish_accumulate<<<(n_slots + 255) / 256, 256, 0, st>>>(p, b.pixel, b.slot_job, b.alive, b.hit, b.ray_o,
+                                                               b.ray_d, b.beta, b.radiance, n_slots, b.accum,
+                                                               dbg ? *dbg : cr_debug{}, p.npx);
     lc.n++;
 }
 

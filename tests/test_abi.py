@@ -36,7 +36,7 @@ def test_struct_layouts(cr):
     assert C.sizeof(cr.cr_material) == 32
     assert C.sizeof(cr.cr_camera) == 48
     assert C.sizeof(cr.cr_render_opts) == 72
-    assert C.sizeof(cr.cr_debug) == 48
+    assert C.sizeof(cr.cr_debug) == 72
 
 
 def test_struct_layouts_match_the_header(cr, tmp_path):
