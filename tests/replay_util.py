@@ -19,6 +19,11 @@ def spawn_tolerance(o, d, t, o_next):
     return 4.0 * U * (np.abs(o) + np.abs(t * d) + np.abs(np.asarray(o_next, np.float64)))
 
 
+def scenes_mat_ggx():
+    from paper_2310_07182_gb300 import scenes
+    return scenes.MAT_GGX
+
+
 def trace_threads(orc, O, rays, skip, nthreads=None):
     """oracle.trace_bound over chunks of rays on all host cores (the C routine releases the GIL)."""
     import os
@@ -109,9 +114,14 @@ def replay_check(cr, orc, S, O, cam, *, max_bounces, mode="direction_reuse", til
         if b > B:
             continue
         s = sel
-        for key in ("cat", "cls"):
-            bad = np.flatnonzero(s & (r[key] != g[key][b - 1]))
-            assert bad.size == 0, f"{label} step {b}: {key} differs at {bad.size} pixels, e.g. {bad[0]}"
+        # the GPU's shade visits only groups with a live member: a group with none keeps the
+        # capture's prefill (255) as its category where the oracle writes "empty"
+        live = g["prim"][b - 1] != -2
+        cat_ok = (r["cat"] == g["cat"][b - 1]) | (~live & (g["cat"][b - 1] == 255) & (r["cat"] == 0))
+        bad = np.flatnonzero(s & ~cat_ok)
+        assert bad.size == 0, f"{label} step {b}: cat differs at {bad.size} pixels, e.g. {bad[0]}"
+        bad = np.flatnonzero(s & (r["cls"] != g["cls"][b - 1]))
+        assert bad.size == 0, f"{label} step {b}: cls differs at {bad.size} pixels, e.g. {bad[0]}"
         assert np.array_equal(r["flags"][s] & 3, g["flags"][b - 1][s] & 3), f"{label} step {b}: flags"
         for key in ("local", "world"):
             bad = np.flatnonzero(s & (r[key].view(np.uint32) != g[key][b - 1].view(np.uint32)).any(axis=1))
@@ -120,15 +130,38 @@ def replay_check(cr, orc, S, O, cam, *, max_bounces, mode="direction_reuse", til
         assert np.array_equal(r["next_alive"][s].astype(bool), traced[s]), f"{label} step {b}: alive"
         tr = s & traced
         assert np.array_equal(r["world"][tr].view(np.uint32), g["ray"][b][tr, 4:7].view(np.uint32))
-        assert np.array_equal(r["next_beta"][tr].view(np.uint32), g["beta"][b][tr, :3].view(np.uint32)), \
-            f"{label} step {b}: throughput"
+        # throughput: bit-exact, except at GGX points of the rough diffuse class, whose weight
+        # pi f is a BRDF evaluation (FP32 on the GPU, FP64 here; ~20 roundings: 1e-5 relative)
+        same = (r["next_beta"].view(np.uint32) == g["beta"][b][:, :3].view(np.uint32)).all(axis=1)
+        rough = np.zeros(sel.shape, bool)
+        tau = kw.get("diffuse_roughness", 0.0)
+        if tau > 0:
+            src = O.src
+            hp = g["prim"][b - 1]
+            mat = src.tri_mat[np.maximum(hp, 0)]
+            rough = (hp >= 0) & (src.mat_type[mat] == scenes_mat_ggx()) & (src.mat_params[mat, 3] >= tau)
+        bad = tr & ~same & ~rough
+        assert not bad.any(), f"{label} step {b}: throughput differs at {bad.sum()} pixels"
+        rr = tr & rough
+        rel = np.abs(r["next_beta"][rr] - g["beta"][b][rr, :3]) / np.maximum(np.abs(r["next_beta"][rr]), 1e-30)
+        assert (rel <= 1e-5).all(), f"{label} step {b}: rough-class throughput off by {rel.max()}"
         prev = g["ray"][b - 1][tr]
         tol = spawn_tolerance(prev[:, :3], prev[:, 4:7], g["t"][b - 1][tr], g["ray"][b][tr, :3])
         off = np.abs(r["next_o"][tr] - g["ray"][b][tr, :3]) > tol
         assert not off.any(), f"{label} step {b}: {off.any(axis=1).sum()} spawn points off"
         if nee:
             pr, pg = r["next_pdf"][tr], g["beta"][b][tr, 3].astype(np.float64)
-            assert (np.abs(pg - pr) <= 1e-5 * np.abs(pr)).all(), f"{label} step {b}: direction densities"
+            # GGX's D(h) divides by c^2 (alpha^2 - 1) + 1, which is about alpha^2 at the lobe's
+            # peak: FP32 loses log2(1 / alpha^2) bits there, so its density is good to
+            # 8 u / alpha^2 (a few roundings of c^2 and of the sum, squared in D)
+            src = O.src
+            mat = src.tri_mat[np.maximum(g["prim"][b - 1][tr], 0)]
+            alpha = np.where(src.mat_type[mat] == scenes_mat_ggx(), src.mat_params[mat, 3], 1.0).astype(np.float64)
+            tol = 1e-5 + 8.0 * U / alpha ** 2
+            rel = np.abs(pg - pr) / np.maximum(np.abs(pr), 1e-30)
+            w = int(np.argmax(rel / tol)) if rel.size else 0
+            assert (rel <= tol).all(), (f"{label} step {b}: direction densities off at {(rel > tol).sum()} of "
+                                        f"{rel.size}, worst {rel[w]} (alpha {alpha[w]}): gpu {pg[w]} oracle {pr[w]}")
     ok = sel & ~staint
     good, excess, nbad = radiance_close(img, L, ok)
     assert good, f"{label}: {nbad} pixels' radiance off by up to {excess}"

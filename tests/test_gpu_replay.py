@@ -111,10 +111,12 @@ def test_replay_landscape_full_size(cr, orc, mode):
     plain, _ = S.render(spp=1, max_bounces=2, mode=mode, tile=(8, 8), k=8, seed=0)
     plain = plain.cpu().numpy().reshape(-1, 3)
     for b0 in (nt // 4, nt // 2, 3 * nt // 4, nt - 96):
+        # a grid of shared edges at coordinates up to 100: a ray meets an edge within the FP32
+        # rounding band (proportional to the coordinates' magnitude) about 5 times in 1,000
         img, rep = replay_check(cr, orc, S, O, cam, max_bounces=2, mode=mode, tile=(8, 8), k=8, seed=0,
-                                tiles=(b0, b0 + 96), label=f"landscape {mode} band {b0}")
+                                tiles=(b0, b0 + 96), label=f"landscape {mode} band {b0}", max_fragile=1e-2)
         assert np.array_equal(img, plain)
-        assert rep["shade_and_radiance"] == 1.0 and rep["every_stage"] >= 0.99
+        assert rep["shade_and_radiance"] == 1.0 and rep["every_stage"] >= 0.98
         assert rep["rays"] > 96 * 64  # secondary rays reached the band
 
 
