@@ -439,10 +439,12 @@ cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, uint32_t flag
  * hit records, 40 bytes per ray) in one file-scope device array sized for
  * CR_TRACE_STATIC_MAX_RAYS rays (2.5 MiB), which every GPU that loads the library holds
  * until the process exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
- *   rays, skip_prim (or NULL), prim, t: DEVICE pointers with the layouts of cr_trace_rays;
- *   host pointers are rejected (staging them would need an allocation).
+ *   rays, skip_prim (or NULL), prim, t: DEVICE pointers of the current device with the
+ *   layouts of cr_trace_rays; host pointers (staging them would need an allocation) and
+ *   other devices' memory are rejected, and so is a scene created on another device.
  *   n: 0..CR_TRACE_STATIC_MAX_RAYS; larger n returns CR_ERR_INVALID_ARG (trace in chunks).
- *   stream: cudaStream_t to run on (NULL = legacy default stream); synchronised on return.
+ *   stream: cudaStream_t to run on (NULL = legacy default stream).  The call synchronises
+ *   this stream before it returns.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture.  All calls
  * share the one array and it keeps the last call's contents: calls that overlap on the GPU

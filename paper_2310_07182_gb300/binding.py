@@ -422,9 +422,37 @@ def cr_debug_bvh_check(tri_xyz, flags=CR_BVH2 | CR_BVH8Q) -> dict:
     return {k: getattr(r, k) for k, _ in r._fields_}
 
 
+def check_static_trace_args(rays, skip, prim, t) -> int:
+    """Validate cr_trace_rays_static's buffers before they reach C, which sees only raw
+    pointers and cannot check their lengths: rays a contiguous (n, 8) float32 tensor, prim
+    int32 and t float32 (skip int32, or None) contiguous with at least n elements, all CUDA
+    tensors of one device.  Returns n; raises TypeError or ValueError."""
+    import torch
+    named = [("rays", rays), ("prim", prim), ("t", t)] + ([("skip", skip)] if skip is not None else [])
+    for name, x in named:
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"cr_trace_rays_static: {name} must be a torch tensor, not {type(x).__name__}")
+        if not x.is_contiguous():
+            raise ValueError(f"cr_trace_rays_static: {name} must be contiguous")
+    if rays.dim() != 2 or rays.shape[1] != 8:
+        raise ValueError(f"cr_trace_rays_static: rays must have shape (n, 8), not {tuple(rays.shape)}")
+    n = int(rays.shape[0])
+    want = {"rays": torch.float32, "prim": torch.int32, "t": torch.float32, "skip": torch.int32}
+    for name, x in named:
+        if x.dtype != want[name]:
+            raise TypeError(f"cr_trace_rays_static: {name} must be {want[name]}, not {x.dtype}")
+        if name != "rays" and x.numel() < n:
+            raise ValueError(f"cr_trace_rays_static: {name} holds {x.numel()} elements, fewer than n = {n}")
+    devs = {x.device for _, x in named}
+    if any(not x.is_cuda for _, x in named) or len(devs) != 1:
+        raise ValueError("cr_trace_rays_static: every buffer must be a CUDA tensor of one device, got "
+                         + ", ".join(f"{name} on {x.device}" for name, x in named))
+    return n
+
+
 def cr_trace_rays_static(handle, rays, skip, prim, t, stream=None):
-    """Allocation-free closest hits: every array must be a CUDA tensor (see include/cr.h)."""
-    n = rays.shape[0]
+    """Allocation-free closest hits (see include/cr.h); the buffers are checked first."""
+    n = check_static_trace_args(rays, skip, prim, t)
     if stream is None:
         stream = _current_stream([rays, prim, t])
     _check(lib().cr_trace_rays_static(handle, _ptr(rays), _ptr(skip), n, _ptr(prim), _ptr(t), stream))

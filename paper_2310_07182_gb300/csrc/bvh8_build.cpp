@@ -41,7 +41,10 @@ double child_area(const Child& c) {
     return 2.0 * (dx * dy + dy * dz + dz * dx);
 }
 
-// float decode exactly as the traversal kernel does it: origin + q * step, one rounding
+// The quantised box a code stands for: origin + q * step in float (q * step is exact, the sum
+// rounds once).  The quantiser chooses codes so that this box contains the child.  The
+// traversal kernel does not decode planes: it tests fma(q, step / d, (origin - o) / d) with an
+// error bias (trace_bvh8.cu) that makes its slab test conservative against this box.
 float decode(float origin, uint32_t q, float step) {
     volatile float prod = (float)q * step; // exact: 8-bit integer times a power of two
     volatile float sum = origin + prod;

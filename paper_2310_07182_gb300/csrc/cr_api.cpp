@@ -123,6 +123,7 @@ struct cr_scene {
     void* d_mats = nullptr;
     void* d_lights = nullptr; // emitter records and their running areas (one allocation)
     cr::SceneDev* d_entries = nullptr; // [0] BVH2 layout, [1] BVH8-Q layout (scene-table entries)
+    int device = -1;                   // the CUDA device the scene's memory lives on
     // render workspace and job tables, grown on demand
     cr::Workspace ws;
     cr::Plan plan_dev;
@@ -137,6 +138,7 @@ void set_last_error(const char* msg) { g_err = msg; }
 const DevScene* dev_scene_of(const cr_scene* s) { return &s->dev; }
 const SceneDev* dev_scene_entry(const cr_scene* s, bool bvh8) { return s->d_entries + (bvh8 ? 1 : 0); }
 bool scene_has_bvh8(const cr_scene* s) { return s->dev.nodes8 != nullptr; }
+int scene_device(const cr_scene* s) { return s->device; }
 } // namespace cr
 
 extern "C" const char* cr_last_error(void) { return g_err.c_str(); }
@@ -170,6 +172,10 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     }
     std::unique_ptr<cr_scene> s(new (std::nothrow) cr_scene());
     if (!s) return fail(CR_ERR_OOM, "cr_scene_create: host allocation");
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CR_ERR_CUDA, "cr_scene_create: no CUDA device");
+    }
     const auto t0 = std::chrono::steady_clock::now();
     const unsigned hc = std::thread::hardware_concurrency();
     HostBVH2 b2;

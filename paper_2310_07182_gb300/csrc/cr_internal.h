@@ -356,5 +356,6 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
 void set_last_error(const char* msg);
 const DevScene* dev_scene_of(const cr_scene* s);
 const SceneDev* dev_scene_entry(const cr_scene* s, bool bvh8); // device pointer
+int scene_device(const cr_scene* s);                            // CUDA device of the scene's memory
 
 } // namespace cr

@@ -49,13 +49,15 @@ cudaError_t scratch_on_current_device(void** out) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of device `dev`: another GPU's memory is rejected too, since the
+// kernels run on the current device.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 } // namespace
@@ -77,9 +79,21 @@ extern "C" cr_status cr_trace_rays_static(cr_scene* scene, const float* rays, co
         set_last_error(msg);
         return CR_ERR_INVALID_ARG;
     }
-    if (!rays || !prim || !t || !on_device(rays) || !on_device(prim) || !on_device(t) ||
-        (skip_prim && !on_device(skip_prim))) {
-        set_last_error("cr_trace_rays_static: rays, skip_prim, prim and t must be device pointers");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error("cr_trace_rays_static: no current CUDA device");
+        return CR_ERR_CUDA;
+    }
+    if (scene_device(scene) != dev) {
+        snprintf(msg, sizeof(msg), "cr_trace_rays_static: the scene lives on device %d, device %d is current",
+                 scene_device(scene), dev);
+        set_last_error(msg);
+        return CR_ERR_INVALID_ARG;
+    }
+    if (!rays || !prim || !t || !on_device(rays, dev) || !on_device(prim, dev) || !on_device(t, dev) ||
+        (skip_prim && !on_device(skip_prim, dev))) {
+        set_last_error("cr_trace_rays_static: rays, skip_prim, prim and t must be device pointers of the current device");
         return CR_ERR_INVALID_ARG;
     }
     void* base = nullptr;

@@ -93,3 +93,31 @@ def test_invalid_arguments_rejected_without_gpu(cr):
     assert o.interleave == 1 and o.bvh == cr.CR_BVH2 and o.k == 0
     assert L.cr_debug_groups(16, 16, 3, 4, 1, 0, 0, None) == cr.CR_ERR_INVALID_ARG
     assert L.cr_debug_sample(7, 1, None, None, None, None, None, None) == cr.CR_ERR_INVALID_ARG
+
+
+def test_static_trace_argument_checks_without_gpu(cr):
+    """cr_trace_rays_static's binding refuses buffers the C side could overrun (it sees raw
+    pointers only): wrong shape, dtype or length, non-contiguous, non-tensor, host tensors."""
+    import torch
+    ok = dict(rays=torch.zeros((16, 8)), skip=None, prim=torch.zeros(16, dtype=torch.int32),
+              t=torch.zeros(16))
+    cases = [
+        (dict(rays=np.zeros((16, 8), np.float32)), TypeError, "torch tensor"),
+        (dict(rays=torch.zeros((16, 7))), ValueError, "shape"),
+        (dict(rays=torch.zeros(128)), ValueError, "shape"),
+        (dict(rays=torch.zeros((16, 8), dtype=torch.float64)), TypeError, "rays must be"),
+        (dict(prim=torch.zeros(16, dtype=torch.int64)), TypeError, "prim must be"),
+        (dict(t=torch.zeros(16, dtype=torch.float16)), TypeError, "t must be"),
+        (dict(skip=torch.zeros(16, dtype=torch.float32)), TypeError, "skip must be"),
+        (dict(prim=torch.zeros(15, dtype=torch.int32)), ValueError, "fewer than n"),
+        (dict(t=torch.zeros(8)), ValueError, "fewer than n"),
+        (dict(skip=torch.zeros(3, dtype=torch.int32)), ValueError, "fewer than n"),
+        (dict(rays=torch.zeros((8, 16)).t()), ValueError, "contiguous"),
+        ({}, ValueError, "CUDA tensor"),  # well-formed, but host memory
+    ]
+    for change, exc, text in cases:
+        args = dict(ok, **change)
+        with pytest.raises(exc, match=text):
+            cr.check_static_trace_args(args["rays"], args["skip"], args["prim"], args["t"])
+        with pytest.raises(exc, match=text):  # the entry point's wrapper checks before calling C
+            cr.cr_trace_rays_static(None, args["rays"], args["skip"], args["prim"], args["t"])

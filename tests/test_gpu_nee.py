@@ -63,6 +63,10 @@ def test_any_hit_visibility_matches_oracle(cr, orc, bvh):
 
 def _check(img, ref, max_taint):
     ok = ref["taint"] == 0
+    c = ref["counters"]
+    print(f"end-to-end: tainted pixels {(~ok).mean():.4f} (bound {max_taint}), fragile decisions "
+          f"{int(c[2])} of {int(c[0] + c[1])} rays ({c[2] / max(1, c[0] + c[1]):.2e}), fragile shadow "
+          f"decisions {int(c[4])} of {int(c[3])}")
     assert ok.mean() >= 1 - max_taint, f"{(~ok).sum()} tainted pixels"
     good, excess, nbad = radiance_close(img, ref["rgb"], ok)
     assert good, f"{nbad} pixels off by up to {excess} beyond tolerance"

@@ -49,6 +49,10 @@ def _render_both(cr, orc, trio, mode, *, spp=1, B=1, tile=(4, 4), k=None, interl
 
 def _check(img, ref, max_taint=0.05):
     ok = ref["taint"] == 0
+    c = ref["counters"]
+    print(f"end-to-end: tainted pixels {(~ok).mean():.4f} (bound {max_taint}), fragile decisions "
+          f"{int(c[2])} of {int(c[0] + c[1])} rays ({c[2] / max(1, c[0] + c[1]):.2e}), fragile shadow "
+          f"decisions {int(c[4])} of {int(c[3])}")
     assert ok.mean() >= 1 - max_taint, f"{(~ok).sum()} tainted pixels"
     good, excess, nbad = radiance_close(img, ref["rgb"], ok)
     assert good, f"{nbad} pixels off by up to {excess} beyond tolerance"
@@ -183,6 +187,9 @@ def test_landscape_full_size_sampled_tiles(cr, orc, mode):
             tx, ty = t % ntx, t // ntx
             mask[ty * 8:(ty + 1) * 8, tx * 8:(tx + 1) * 8] = True
         ok = mask & (ref["taint"] == 0)
+        # an independent render cascades: one fragile decision taints its group for the rest of
+        # the path (the replay test checks every pixel stage by stage instead)
+        print(f"landscape band {b0}: {ok.sum() / mask.sum():.4f} of the band's pixels untainted")
         assert ok.sum() >= 0.85 * mask.sum()
         good, excess, nbad = radiance_close(img, ref["rgb"], ok)
         assert good, f"band {b0}: {nbad} pixels off by {excess}"
@@ -278,7 +285,9 @@ def test_interior_full_size_sampled_tiles(cr, orc, bvh):
             tx, ty = t % ntx, t // ntx
             mask[ty * 8:(ty + 1) * 8, tx * 8:(tx + 1) * 8] = True
         ok = mask & (ref["taint"] == 0)
-        # over 16 samples and 4 bounces a fragile ray anywhere in a group taints its pixels
+        # over 16 samples and 4 bounces a fragile ray anywhere in a group taints its pixels (the
+        # replay test checks every pixel of every frame stage by stage instead)
+        print(f"interior band {b0}: {ok.sum() / mask.sum():.4f} of the band's pixels untainted")
         assert ok.sum() >= 0.6 * mask.sum()
         good, excess, nbad = radiance_close(img, ref["rgb"], ok)
         assert good, f"band {b0}: {nbad} pixels off by {excess}"

@@ -1,10 +1,16 @@
 """GPU closest-hit traversal vs the FP64 oracle on the same fp32 rays: primitive ids bit-exact
-except decisions the oracle flags as fragile, t within 1e-5 relative."""
+except decisions the oracle flags as fragile, t within max(1e-5 t, T_ERR_K terr), terr being
+the oracle's FP32 error scale of the winning hit."""
 import numpy as np
 import pytest
 import torch
 
 from paper_2310_07182_gb300 import scenes
+from replay_util import T_ERR_K
+
+
+def _t_close(t, t_ref, terr):
+    return np.abs(t - t_ref) <= np.maximum(1e-5 * t_ref, T_ERR_K * terr)
 
 pytestmark = pytest.mark.gpu
 
@@ -16,17 +22,18 @@ def cr():
     return binding
 
 
-def _compare(orc, sc, S, rays, skip=None, max_fragile=2e-3, max_tflag=0.25, **kw):
+def _compare(orc, sc, S, rays, skip=None, max_fragile=2e-3, **kw):
     O = orc.Scene(sc)
-    p_ref, t_ref, fr = orc.trace(O, rays, skip=skip)
+    p_ref, t_ref, fr, terr = orc.trace_bound(O, rays, skip=skip)
     prim, t = S.trace(rays, skip, **kw)
     prim, t = np.asarray(prim), np.asarray(t)
     ok = (fr & 1) == 0
+    print(f"trace {sc.name}: {len(rays)} rays, fragile {(~ok).mean():.2e}, "
+          f"ill-conditioned t {((fr & 2) != 0).mean():.2e}")
     assert (~ok).mean() <= max_fragile
-    assert ((fr & 2) != 0).mean() <= max_tflag  # origins inside the scene: short, ill-conditioned t
     assert np.array_equal(prim[ok], p_ref[ok])
-    hit = (fr == 0) & (p_ref >= 0)
-    assert np.all(np.abs(t[hit] - t_ref[hit]) <= 1e-5 * t_ref[hit])
+    hit = ok & (p_ref >= 0)
+    assert np.all(_t_close(t[hit], t_ref[hit], terr[hit]))
     assert np.all(np.isinf(t[ok & (p_ref < 0)]))
     return prim, t
 
@@ -121,12 +128,14 @@ def test_landscape_full_size_sample(cr, orc):
     prim, t = prim.cpu().numpy(), t.cpu().numpy()
     sel = rng.choice(n, 3000, replace=False)
     O = orc.Scene(sc)
-    p_ref, t_ref, fr = orc.trace(O, rays[sel])
+    p_ref, t_ref, fr, terr = orc.trace_bound(O, rays[sel])
     ok = (fr & 1) == 0
+    print(f"landscape camera rays: fragile {(~ok).mean():.2e} of {len(sel)}")
+    # a grid of shared edges at coordinates up to 100 (FP32 rounding band of ~1e-4)
     assert (~ok).mean() < 1e-2
     assert np.array_equal(prim[sel][ok], p_ref[ok])
-    hit = (fr == 0) & (p_ref >= 0)
-    assert np.all(np.abs(t[sel][hit] - t_ref[hit]) <= 1e-5 * t_ref[hit])
+    hit = ok & (p_ref >= 0)
+    assert np.all(_t_close(t[sel][hit], t_ref[hit], terr[hit]))
 
 
 @pytest.mark.parametrize("name", ["tiny", "interior", "furnace"])
