@@ -395,6 +395,11 @@ def run_ours(args):
         extras["next_event_estimation"] = nee_leg(cr, scenes, rank, args)
         extras["transmission"] = transmission_leg(cr, scenes, rank, args)
         extras["quality"] = quality_leg(cr, S, cam, stream, results)
+        # the indoor stand-in, closer to the paper's Table 2 scenes (its 4 bounces)
+        si = scenes.interior()
+        Si = cr.Scene(si)
+        extras["quality_interior"] = quality_leg(cr, Si, si.camera, stream, results, bounces=4)
+        Si.close()
         if not args.no_batched:
             extras["batched"] = batched_leg(cr, scenes, rank, args)
         if not args.no_serving and rank == 0:
@@ -403,27 +408,45 @@ def run_ours(args):
     if rank != 0:
         return
     R = results[modes[0]]
-    # Roofline of the secondary trace kernel (k_trace_bvh2).  ncu shows it is bound by
-    # instruction issue (DRAM 2-3%, L2 6-11% of peak; 7-8 active lanes per warp instruction),
-    # so the bound is FP32 ALU: 24 operations per ray/box test (two per node visit) and 40 per
-    # watertight ray/triangle test, counted by the counting pass, against 152 SMs x 128 FP32
-    # lanes x the SM clock sampled during the timed region.  The node-byte rate against the
-    # measured HBM copy bandwidth is reported beside it.
-    # With "+bvh8q" first, the figures describe k_trace_bvh8 instead: 8 box tests and 80 B
-    # per node visit, and no ncu-derived keys (the committed summary is the BVH2 kernel's).
+    # Roofline of the secondary trace kernel (k_trace_bvh2): the algorithmic node + triangle
+    # bytes per secondary ray (32 ray + 4 queue + 8 hit + 64 per node visit + 48 per triangle
+    # test, visits and tests from the counting pass) times the rays of one launch, over the
+    # launch's CUDA-event time, against the measured HBM copy bandwidth (the headline) and
+    # the measured L2 read roof.  Above the HBM roof means caches serve node fetches again
+    # (coherence); the DRAM traffic the kernel really causes is the "traffic" key (ncu).
+    # ncu shows the kernel bound by instruction issue (7-8 active lanes per warp
+    # instruction), so the issue and FP32-ALU roofs are reported beside it.
+    # With "+bvh8q" first, the figures describe k_trace_bvh8 instead: 80 B and 8 box tests per
+    # node visit, and no ncu-derived keys (the committed summary is the BVH2 kernel's).
     bvh8 = parse(modes[0])[3] == cr.CR_BVH8Q
     launches = BOUNCES
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count  # cudaDevAttrMultiProcessorCount
+
+    def node_bytes_per_ray(res, wide=False):
+        return 32 + 4 + 8 + (80 if wide else 64) * res["nodes_per_ray"] + 48 * res["tris_per_ray"]
+
     rays_per_launch = R["secondary_rays_per_step"] / launches
     ms_per_launch = R["ms_trace_secondary"] / launches
     ops_per_ray = (8 if bvh8 else 2) * 24 * R["nodes_per_ray"] + 40 * R["tris_per_ray"]
     achieved_ops = ops_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e12
     clk = (clocks or {}).get("sm_mhz") or 2070.0
-    peak_ops = 152 * 128 * clk * 1e6 / 1e12
-    bytes_per_ray = 32 + 4 + 8 + (80 if bvh8 else 64) * R["nodes_per_ray"] + 48 * R["tris_per_ray"]
+    peak_ops = n_sm * 128 * clk * 1e6 / 1e12
+    bytes_per_ray = node_bytes_per_ray(R, bvh8)
     achieved = bytes_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e9
     peak, peak_kind = load_peaks()
     traffic = None if bvh8 else profile_traffic()
     l2_gbs = l2_read_bandwidth(cr)
+    # every mode's node-byte rate on the same roof (trace-only secondary rays/s x its own bytes
+    # per ray), and its ratio to independent sampling's: the coherence gain read off one roof
+    per_mode = {}
+    for m in modes:
+        wide = parse(m)[3] == cr.CR_BVH8Q
+        ach_m = node_bytes_per_ray(results[m], wide) * results[m]["trace_mrays"] * 1e6 / 1e9
+        per_mode[m] = {"achieved": round(ach_m, 1), "frac": round(ach_m / peak, 4),
+                       "bytes_per_ray": round(node_bytes_per_ray(results[m], wide), 1)}
+    if "independent" in per_mode:
+        for m in per_mode:
+            per_mode[m]["frac_vs_independent"] = round(per_mode[m]["frac"] / per_mode["independent"]["frac"], 4)
     line = {
         "metric": METRIC, "value": round(R["mrays"], 2), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(R["ms_per_step"], 4), "higher_is_better": True,
@@ -439,16 +462,20 @@ def run_ours(args):
                 "sync_value": round(e2e_rays / e2e["sync"] / 1e6, 2),
                 "sync_timing": "cr_render_ex into page-locked host memory, one synchronous call per step"},
         "gpu_launches": int(R["launches_per_step"] * args.steps),
-        "roofline": {"bound": "alu", "achieved": round(achieved_ops, 3), "peak": round(peak_ops, 2),
-                     "unit": "TOP/s (FP32 ALU operations)", "frac": round(achieved_ops / peak_ops, 4),
-                     "traffic": traffic, "kernel": f"k_trace_{'bvh8' if bvh8 else 'bvh2'} (secondary rays)",
-                     "ops_per_ray": round(ops_per_ray, 1),
-                     "peak_source": f"152 SMs x 128 FP32 lanes x {clk:.0f} MHz (sampled)"},
-        "roofline_hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "bytes_per_ray": round(bytes_per_ray, 1),
-                         "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                         "note": "algorithmic node+triangle bytes; mostly served by L1/L2 (DRAM traffic is the 'traffic' key)"},
-        "roofline_issue": None if bvh8 else issue_roof(R, clk),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": f"k_trace_{'bvh8' if bvh8 else 'bvh2'} (secondary rays)",
+                     "bytes_per_ray": round(bytes_per_ray, 1), "rays_per_launch": round(rays_per_launch),
+                     "ms_per_launch": round(ms_per_launch, 5),
+                     "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
+                     "note": "algorithmic node+triangle bytes per launch / CUDA-event launch time; mostly served by "
+                             "L1/L2, the DRAM bytes ncu counts per launch are 'traffic'",
+                     "modes": per_mode},
+        "roofline_alu": {"achieved": round(achieved_ops, 3), "peak": round(peak_ops, 2),
+                         "unit": "TOP/s (FP32 ALU operations)", "frac": round(achieved_ops / peak_ops, 4),
+                         "ops_per_ray": round(ops_per_ray, 1),
+                         "peak_source": f"{n_sm} SMs (device attribute) x 128 FP32 lanes x {clk:.0f} MHz (sampled)"},
+        "roofline_issue": None if bvh8 else issue_roof(R, clk, n_sm),
         "roofline_l2": {"achieved": round(achieved, 1), "peak": round(l2_gbs, 1), "unit": "GB/s",
                         "frac": round(achieved / l2_gbs, 4),
                         "peak_source": "cr_measure_l2_read: read-only kernel over an L2-resident 48 MB buffer, CUDA events",
@@ -481,12 +508,12 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def issue_roof(R, clk):
+def issue_roof(R, clk, n_sm):
     """The trace kernel's binding roof (ncu: issue-bound): warp instructions per second
-    against one instruction per scheduler per clock (152 SMs x 4 schedulers).  Instructions
+    against one instruction per scheduler per clock (n_sm SMs x 4 schedulers).  Instructions
     per ray come from the committed ncu capture; the ray rate is this run's."""
     ipr = profile_traffic("warp_instructions_per_ray")
-    peak = 152 * 4 * clk * 1e6 / 1e12
+    peak = n_sm * 4 * clk * 1e6 / 1e12
     if ipr is None:
         return {"achieved": None, "peak": round(peak, 3), "unit": "T warp instructions/s", "frac": None}
     ach = ipr * R["trace_mrays"] * 1e6 / 1e12
@@ -658,61 +685,123 @@ def sweep_leg(cr, S, cam, out, stream, rank, world, bounces=None):
     return {"independent_trace_only_mrays": round(base, 1), "direction_reuse": rows}
 
 
-def quality_leg(cr, S, cam, stream, results):
-    """MSE at equal time against a 4096-spp independent reference (Sec. 5.2 uses 4096
-    iterations), for budgets of 0.1/0.5/2 s of device time per mode, and PSNR at 128 spp
-    (the analogue of Table 2)."""
+T975 = {2: 12.706, 3: 4.303, 4: 3.182, 5: 2.776, 6: 2.571, 7: 2.447, 8: 2.365}  # Student t, 97.5%, by n samples
+
+
+def _mean_ci(xs):
+    """Mean and the half-width of its 95% confidence interval (Student t)."""
+    n = len(xs)
+    m = sum(xs) / n
+    if n < 2:
+        return m, None
+    sd = math.sqrt(sum((x - m) ** 2 for x in xs) / (n - 1))
+    return m, T975.get(n, 1.96) * sd / math.sqrt(n)
+
+
+def quality_leg(cr, S, cam, stream, results, bounces=None, seeds=5, budgets=(0.1, 0.5, 2.0)):
+    """MSE at equal time (Sec. 5.2) against a 4096-spp independent reference: for each mode
+    and each of `seeds` Philox keys, samples accumulate progressively (frame_base continues)
+    until each budget of device time per mode is spent; the mean MSE over keys and its 95%
+    confidence interval per budget.  PSNR at 128 spp per key (the analogue of Table 2).  The
+    fraction of live pixels in each group category per bounce (Sec. 3.2).  target_met: a mode
+    with more whole-step secondary Mrays/s than both comparators and a lower mean MSE at
+    every budget."""
     import torch
+    B = bounces or BOUNCES
     ref = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
     img = torch.empty_like(ref)
+    part = torch.empty_like(ref)
     n_ref = 4096
     for ci, c in enumerate(range(0, n_ref, 256)):  # mean of 16 chunks of 256 samples
-        o = cr.make_opts(k=K, frame_base=1_000_000 + c, stream=stream)
-        cr.cr_render_ex(S.handle, cam, 256, BOUNCES, "independent", TILE[0], TILE[1], img, o)
+        o = cr.make_opts(k=K, seed=1000, frame_base=c, stream=stream)
+        cr.cr_render_ex(S.handle, cam, 256, B, "independent", TILE[0], TILE[1], img, o)
         if ci == 0:
             ref.copy_(img)
         else:
             ref += img
     ref /= n_ref // 256
     torch.cuda.synchronize()
-    out = {"reference_spp": n_ref, "budgets_s": [0.1, 0.5, 2.0], "modes": {}}
     peak = float(ref.max())
+    out = {"reference_spp": n_ref, "reference": "independent sampling, Philox key 1000", "budgets_s": list(budgets),
+           "seeds": seeds, "ci": "95%, Student t over the keys", "modes": {}}
     donor = cr.CR_OPT_HYBRID_DONOR
-    # (name, mode, reuse depth, flags, K, roughness threshold of the diffuse class)
-    variants = (("direction_reuse", "direction_reuse", 0, 0, K, 0.0), ("independent", "independent", 0, 0, K, 0.0),
-                ("morton_sort", "morton_sort", 0, 0, K, 0.0),
-                ("direction_reuse_bounce1_only", "direction_reuse", 1, 0, K, 0.0),
-                ("direction_reuse_hybrid_donor", "direction_reuse", 0, donor, K, 0.0),
-                ("direction_reuse_hybrid_donor_k64", "direction_reuse", 0, donor, 64, 0.0),
-                ("direction_reuse_rough030", "direction_reuse", 0, 0, K, 0.3),
-                ("direction_reuse_rough030_hybrid_donor", "direction_reuse", 0, donor, K, 0.3))
-    for name, mode, depth, vflags, k, tau in variants:
-        ms_spp = results.get(name, {}).get("ms_per_step")
-        if ms_spp is None:
-            ms, tr, sec = _timed_renders(cr, S, cam, img, stream, 3, 1, mode=mode, k=k, reuse_depth=depth,
-                                         extra_flags=vflags, diffuse_roughness=tau)
-            ms_spp = ms / 3
-        row = {"ms_per_spp": round(ms_spp, 4), "mse": [], "spp": []}
-        if tau > 0:
-            row["diffuse_roughness"] = tau
-            row["trace_only_mrays"] = round(sec / (tr / 1e3) / 1e6, 1)
-        for T in out["budgets_s"]:
-            spp = max(1, int(T * 1e3 / ms_spp))
-            o = cr.make_opts(k=k, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags, diffuse_roughness=tau)
-            cr.cr_render_ex(S.handle, cam, spp, BOUNCES, mode, TILE[0], TILE[1], img, o)
-            row["mse"].append(float(((img - ref) ** 2).mean()))
-            row["spp"].append(spp)
-        o = cr.make_opts(k=k, frame_base=0, stream=stream, reuse_depth=depth, flags=vflags, diffuse_roughness=tau)
-        cr.cr_render_ex(S.handle, cam, 128, BOUNCES, mode, TILE[0], TILE[1], img, o)
-        mse128 = float(((img - ref) ** 2).mean())
-        row["psnr_128spp_db"] = round(10 * math.log10(peak * peak / mse128), 3)
-        # bias estimate: the 1024-spp mean of the mode against the reference
-        o = cr.make_opts(k=k, frame_base=2_000_000, stream=stream, reuse_depth=depth, flags=vflags,
-                         diffuse_roughness=tau)
-        cr.cr_render_ex(S.handle, cam, 1024, BOUNCES, mode, TILE[0], TILE[1], img, o)
+    variants = (("direction_reuse", "direction_reuse", 0), ("independent", "independent", 0),
+                ("morton_sort", "morton_sort", 0), ("direction_reuse_hybrid_donor", "direction_reuse", donor))
+
+    def render(spp, mode, flags, seed, frame, dst):
+        o = cr.make_opts(k=K, seed=seed, frame_base=frame, stream=stream, flags=flags)
+        cr.cr_render_ex(S.handle, cam, spp, B, mode, TILE[0], TILE[1], dst, o)
+
+    for name, mode, vflags in variants:
+        kw = {} if bounces is None else {"bounces": bounces}
+        ms, tr, sec = _timed_renders(cr, S, cam, img, stream, 5, 2, mode=mode, extra_flags=vflags, **kw)
+        ms_spp = ms / 5
+        mrays = sec / (ms / 1e3) / 1e6
+        row = {"ms_per_spp": round(ms_spp, 4), "whole_step_mrays": round(mrays, 1), "spp": [], "mse": [],
+               "mse_ci95": [], "psnr_128spp_db": None}
+        spps = [max(1, int(T * 1e3 / ms_spp)) for T in budgets]
+        row["spp"] = spps
+        per_budget = [[] for _ in budgets]
+        psnr = []
+        for seed in range(seeds):
+            done = 0
+            for bi, n in enumerate(spps):  # progressive: the next budget continues the frames
+                if n > done:
+                    render(n - done, mode, vflags, seed, done, part)
+                    if done == 0:
+                        img.copy_(part)
+                    else:
+                        img.mul_(done / n).add_(part, alpha=(n - done) / n)
+                    done = n
+                per_budget[bi].append(float(((img - ref) ** 2).mean()))
+            render(128, mode, vflags, seed, 50_000, img)
+            psnr.append(10 * math.log10(peak * peak / float(((img - ref) ** 2).mean())))
+        for vals in per_budget:
+            m, h = _mean_ci(vals)
+            row["mse"].append(m)
+            row["mse_ci95"].append(h)
+        pm, ph = _mean_ci(psnr)
+        row["psnr_128spp_db"] = round(pm, 3)
+        row["psnr_128spp_ci95_db"] = None if ph is None else round(ph, 3)
+        # bias estimate: a 1024-spp mean of the mode against the reference
+        render(1024, mode, vflags, 0, 2_000_000, img)
         row["mse_1024spp"] = float(((img - ref) ** 2).mean())
         out["modes"][name] = row
+    # the paper's target per mode: faster than both comparators and lower MSE at every budget
+    comps = ("independent", "morton_sort")
+    for name, row in out["modes"].items():
+        if name in comps:
+            continue
+        faster = all(row["whole_step_mrays"] > out["modes"][c]["whole_step_mrays"] for c in comps)
+        lower = all(row["mse"][i] < out["modes"][c]["mse"][i] for c in comps for i in range(len(budgets)))
+        separated = all(row["mse"][i] + (row["mse_ci95"][i] or 0) < out["modes"][c]["mse"][i]
+                        - (out["modes"][c]["mse_ci95"][i] or 0) for c in comps for i in range(len(budgets)))
+        row["target_met"] = bool(faster and lower)
+        row["faster_than_both"] = bool(faster)
+        row["lower_mse_than_both"] = bool(lower)
+        row["lower_mse_ci_separated"] = bool(separated)
+    out["category_fractions"] = category_fractions(cr, S, cam, stream, B)
     return out
+
+
+def category_fractions(cr, S, cam, stream, B):
+    """Fraction of the live pixels whose reuse group is diffuse / glossy / hybrid at each
+    bounce (Sec. 3.2), from one frame's per-bounce capture."""
+    import torch
+    dbg, bufs = cr.debug_buffers(cam.width, cam.height, B)
+    img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    o = cr.make_opts(k=K, seed=0, frame_base=0, stream=stream, debug=dbg)
+    cr.cr_render_ex(S.handle, cam, 1, B, "direction_reuse", TILE[0], TILE[1], img, o)
+    torch.cuda.synchronize()
+    rows = []
+    for b in range(B):
+        live = (bufs["flags"][b] & 1).bool()
+        n = max(1, int(live.sum()))
+        cat = bufs["cat"][b][live]
+        rows.append({"bounce": b + 1, "live_pixels": n,
+                     **{k: round(int((cat == v).sum()) / n, 4) for k, v in (("diffuse", 1), ("glossy", 2),
+                                                                           ("hybrid", 3))}})
+    return rows
 
 
 def batched_leg(cr, scenes, rank, args):
