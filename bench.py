@@ -492,6 +492,18 @@ def run_ours(args):
                         for m in modes if m != "direction_reuse"},
         "secondary_rays_per_step": int(R["secondary_rays_per_step"]),
     }
+    if "morton_sort" in results:
+        # the comparator's ray sort (key kernel + three radix passes, per step): algorithmic bytes
+        # per key = key kernel 38 in (queue 4, ray 32, scene 2) and 12 out (key, value, value
+        # copy), then 3 passes x (8 in + 8 out) = 98, against the measured HBM copy bandwidth
+        rm = results["morton_sort"]
+        keys = rm["secondary_rays_per_step"]
+        gbs = keys * 98 / (rm["ms_sort"] / 1e3) / 1e9 if rm["ms_sort"] > 0 else None
+        line["sort_roofline"] = {"ms_per_step": round(rm["ms_sort"], 4), "keys_per_step": int(keys),
+                                 "bytes_per_key": 98, "achieved": None if gbs is None else round(gbs, 1),
+                                 "peak": peak, "unit": "GB/s", "frac": None if gbs is None else round(gbs / peak, 4),
+                                 "share_of_step": round(rm["ms_sort"] / rm["ms_per_step"], 4),
+                                 "timing": "stage events of 3 untimed steps (events between all stages)"}
     line.update(extras)
     if not args.no_cpu_baseline:
         v, thr, sample, dt = cpu_oracle_rate(sc, args.cpu_seconds)

@@ -169,6 +169,8 @@ _SIGS = [
     ("cr_trace_rays_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
     ("cr_measure_l2_read", C.c_int, [C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]),
+    ("cr_debug_sort", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p,
+                                C.POINTER(C.c_double)]),
 ]
 CR_TRACE_STATIC_MAX_RAYS = 65536
 
@@ -461,6 +463,22 @@ def cr_trace_rays_static(handle, rays, skip, prim, t, stream=None):
 def cr_debug_groups(width, height, group_w, group_h, interleave, seed, frame, out):
     _check(lib().cr_debug_groups(width, height, group_w, group_h, int(interleave), seed, frame, _ptr(out)))
     return out
+
+
+def cr_debug_sort(keys, vals, reps=1):
+    """The ray sort on caller keys (numpy or CUDA tensors of uint32/int32 keys and int32 values)
+    -> (sorted keys, sorted values, mean ms per sort), outputs like the inputs."""
+    n = int(keys.shape[0])
+    if isinstance(keys, np.ndarray):
+        keys = np.ascontiguousarray(keys).view(np.uint32) if keys.dtype.itemsize == 4 else keys.astype(np.uint32)
+        vals = np.ascontiguousarray(vals, dtype=np.int32)
+        ko, vo = np.empty(n, np.uint32), np.empty(n, np.int32)
+    else:
+        import torch
+        ko, vo = torch.empty_like(keys), torch.empty(n, dtype=torch.int32, device=keys.device)
+    ms = C.c_double()
+    _check(lib().cr_debug_sort(_ptr(keys), _ptr(vals), n, reps, _ptr(ko), _ptr(vo), C.byref(ms)))
+    return ko, vo, ms.value
 
 
 def cr_debug_philox(seed, ctr, out):

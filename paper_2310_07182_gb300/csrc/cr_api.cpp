@@ -556,8 +556,9 @@ cr_status Workspace::ensure(uint32_t n_slots, uint32_t npx) {
 }
 
 cr_status queue_status(const uint64_t* host_counts) {
-    if (reinterpret_cast<const uint32_t*>(host_counts)[kQueueErrWord])
-        return fail(CR_ERR_CUDA, "queue compaction: an append would overflow a queue");
+    const uint32_t e = reinterpret_cast<const uint32_t*>(host_counts)[kQueueErrWord];
+    if (e & 1u) return fail(CR_ERR_CUDA, "queue compaction: an append would overflow a queue");
+    if (e & 2u) return fail(CR_ERR_TIMEOUT, "ray sort: a look-back wait ran out (the sorted order may be wrong)");
     return CR_OK;
 }
 
@@ -1118,6 +1119,57 @@ extern "C" cr_status cr_debug_philox(uint64_t seed, const uint32_t* ctr, uint32_
     CR_CUDA(cudaGetLastError());
     CR_CUDA(finish_out(co, 0));
     CR_CUDA(cudaStreamSynchronize(0));
+    return CR_OK;
+}
+
+extern "C" cr_status cr_debug_sort(const uint32_t* keys, const int32_t* vals, uint32_t n, uint32_t reps,
+                                   uint32_t* keys_out, int32_t* vals_out, double* ms) {
+    g_err.clear();
+    if (n == 0) return CR_OK;
+    if (!keys || !vals || !keys_out || !vals_out || reps == 0)
+        return fail(CR_ERR_INVALID_ARG, "cr_debug_sort: NULL argument or reps == 0");
+    if (n > (1u << 28)) return fail(CR_ERR_INVALID_ARG, "cr_debug_sort: n=%u above 2^28", n);
+    Staged ki, vi, ko, vo;
+    CR_CUDA(stage_in(ki, keys, 4 * (size_t)n, 0));
+    CR_CUDA(stage_in(vi, vals, 4 * (size_t)n, 0));
+    CR_CUDA(stage_out(ko, keys_out, 4 * (size_t)n));
+    CR_CUDA(stage_out(vo, vals_out, 4 * (size_t)n));
+    // the sort's own buffers: keys and values twice, the workspace, the count and error words
+    DevMem buf;
+    const size_t ws_words = sort_hist_len(n);
+    CR_CUDA(buf.alloc(16 * (size_t)n + 4 * ws_words + 64));
+    uint32_t* kk = static_cast<uint32_t*>(buf.p);
+    int32_t* vv = reinterpret_cast<int32_t*>(kk + 2 * (size_t)n);
+    uint32_t* ws = reinterpret_cast<uint32_t*>(vv + 2 * (size_t)n);
+    uint32_t* cnt = ws + ws_words;
+    const uint32_t host_cnt[2] = {n, 0u};
+    CR_CUDA(cudaMemcpy(cnt, host_cnt, 8, cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CR_CUDA(cudaEventCreate(&e0));
+    CR_CUDA(cudaEventCreate(&e1));
+    LaunchCount lc;
+    int32_t* sorted = nullptr;
+    cudaEventRecord(e0, 0);
+    for (uint32_t r = 0; r < reps; ++r)
+        sorted = launch_sort_only(static_cast<const uint32_t*>(ki.dev), static_cast<const int32_t*>(vi.dev), n, kk, vv,
+                                  ws, cnt, cnt + 1, 0, lc);
+    cudaEventRecord(e1, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float el = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CR_CUDA(e);
+    if (ms) *ms = (double)el / reps;
+    const uint32_t* sorted_keys = kk + (sorted - vv);
+    CR_CUDA(cudaMemcpyAsync(ko.dev, sorted_keys, 4 * (size_t)n, cudaMemcpyDeviceToDevice, 0));
+    CR_CUDA(cudaMemcpyAsync(vo.dev, sorted, 4 * (size_t)n, cudaMemcpyDeviceToDevice, 0));
+    CR_CUDA(finish_out(ko, 0));
+    CR_CUDA(finish_out(vo, 0));
+    uint32_t err = 0;
+    CR_CUDA(cudaMemcpy(&err, cnt + 1, 4, cudaMemcpyDeviceToHost));
+    if (err) return fail(CR_ERR_TIMEOUT, "cr_debug_sort: a look-back wait ran out");
     return CR_OK;
 }
 

@@ -256,6 +256,8 @@ void launch_compact(const PassArgs& p, PathBuffers& b, bool first, cudaStream_t 
 const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, uint32_t key_kind,
                                   cudaStream_t st, LaunchCount& lc);
 uint32_t sort_hist_len(uint32_t n_slots);
+int32_t* launch_sort_only(const uint32_t* key_in, const int32_t* val_in, uint32_t n, uint32_t* keys, int32_t* vals,
+                          uint32_t* ws, uint32_t* count, uint32_t* err, cudaStream_t st, LaunchCount& lc);
 uint32_t compact_blocks(uint32_t n_pos);
 void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, float4* ray_o, float4* ray_d,
                            cudaStream_t st, LaunchCount& lc);

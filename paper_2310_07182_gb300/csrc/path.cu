@@ -1032,14 +1032,10 @@ __device__ __forceinline__ uint32_t interleave(const uint32_t* q, int n, int bit
     return key;
 }
 
-__global__ void k_morton(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
-                         const int32_t* __restrict__ queue, const uint32_t* __restrict__ count, uint32_t n_max,
-                         const SceneDev* __restrict__ scenes, const uint16_t* __restrict__ slot_scene, uint32_t kind,
-                         uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
-    const uint32_t n = min(*count, n_max);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int slot = queue[i];
+// The reordering key of one queued ray (30 bits).
+__device__ __forceinline__ uint32_t morton_key(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
+                                               int slot, const SceneDev* __restrict__ scenes,
+                                               const uint16_t* __restrict__ slot_scene, uint32_t kind) {
     const SceneDev& sc = scenes[slot_scene[slot]];
     float l[3], s[3], emax = 0.0f;
 #pragma unroll
@@ -1090,126 +1086,262 @@ __global__ void k_morton(const float4* __restrict__ ray_o, const float4* __restr
             key = interleave(q5, 5, 6);
         }
     }
-    keys[i] = key;
-    vals[i] = slot;
+    return key;
 }
 
-constexpr uint32_t kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
+// ------------------------------------------------------------------------------------
+// Stable LSD radix sort of the 30-bit keys with their slots: three passes of 10-bit digits,
+// one launch each, in the style of a single-pass ("onesweep") sort with decoupled
+// look-back.  The key kernel also counts the digits of all three passes (global
+// histograms), so a pass needs no counting launch of its own: each block takes tiles of
+// kOsTile keys in ticket order, ranks its keys stably inside the tile (warp multisplit by
+// ballots), publishes its digit counts, finds the counts of all earlier tiles by looking back
+// over their published words, and scatters its keys through shared memory so that writes of
+// one digit are contiguous.  Every grid is a fixed number of blocks per SM; the live key
+// count is read on the device.
+constexpr uint32_t kRadixBits = 10, kRadix = 1u << kRadixBits, kRadixMask = kRadix - 1u, kRadixPasses = 3;
+constexpr uint32_t kOsThreads = 256, kOsWarps = kOsThreads / 32, kOsRounds = 16;
+constexpr uint32_t kOsWarpKeys = 32 * kOsRounds, kOsTile = kOsWarps * kOsWarpKeys; // 4096 keys per tile
+// sort workspace (uint32 words): [0, 3 kRadix) global digit counts per pass, then one tile
+// ticket per pass, then from kOsStatus the look-back words of each pass (stride: tiles x kRadix)
+constexpr uint32_t kOsHist = 0, kOsTicket = kRadixPasses * kRadix, kOsStatus = kRadixPasses * kRadix + 64;
+// look-back word: flag in the two top bits (0 nothing yet, aggregate = the tile's own count,
+// inclusive = the count of this and every earlier tile), count in the low 30 bits
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1u;
+constexpr uint32_t kLookbackSpins = 1u << 20; // look-back steps without progress before the wait is given up
+constexpr uint32_t kLookbackWindow = 4;       // earlier tiles read per look-back step
+constexpr uint32_t kSortErrBit = 2u;           // error word bit: a look-back wait ran out
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys,
-                                                            const uint32_t* __restrict__ count, uint32_t n_max,
-                                                            uint32_t shift, uint32_t n_blocks,
-                                                            uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[256];
-    const uint32_t n = min(*count, n_max);
-    h[threadIdx.x] = 0;
+__global__ void __launch_bounds__(512) k_morton(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
+                                                const int32_t* __restrict__ queue, const uint32_t* __restrict__ count,
+                                                uint32_t n_max, const SceneDev* __restrict__ scenes,
+                                                const uint16_t* __restrict__ slot_scene, uint32_t kind,
+                                                uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
+                                                int32_t* __restrict__ vals_alt, uint32_t* __restrict__ ws,
+                                                size_t status_stride) {
+    __shared__ uint32_t s_h[kRadixPasses * kRadix];
+    for (uint32_t i = threadIdx.x; i < kRadixPasses * kRadix; i += blockDim.x) s_h[i] = 0u;
     __syncthreads();
-    const uint32_t base = blockIdx.x * kSortTile;
-    for (uint32_t r = 0; r < kSortItems; ++r) {
-        const uint32_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[threadIdx.x * n_blocks + blockIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive scan of the digit-major histogram in chunks of kScanChunk entries: each block
-// scans its chunk in place (four contiguous entries per thread, loaded as one uint4) and
-// stores the chunk total; the scatter adds the exclusive prefix of the chunk totals.
-constexpr uint32_t kScanChunk = 4096;
-
-__global__ void __launch_bounds__(1024) k_sort_scan_chunks(uint32_t* __restrict__ hist, uint32_t len,
-                                                            uint32_t* __restrict__ chunk_totals) {
-    __shared__ uint32_t s_warp[32];
-    const uint32_t base = blockIdx.x * kScanChunk + 4 * threadIdx.x;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (base + 3 < len) {
-        v = *reinterpret_cast<const uint4*>(hist + base);
-    } else {
-        if (base < len) v.x = hist[base];
-        if (base + 1 < len) v.y = hist[base + 1];
-        if (base + 2 < len) v.z = hist[base + 2];
-    }
-    uint32_t total;
-    const uint32_t ex = block_excl_scan(v.x + v.y + v.z + v.w, s_warp, total);
-    const uint4 o = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
-    if (base + 3 < len) {
-        *reinterpret_cast<uint4*>(hist + base) = o;
-    } else {
-        if (base < len) hist[base] = o.x;
-        if (base + 1 < len) hist[base + 1] = o.y;
-        if (base + 2 < len) hist[base + 2] = o.z;
-    }
-    if (threadIdx.x == 0) chunk_totals[blockIdx.x] = total;
-}
-
-// Exclusive scan of the chunk totals in one block, 1024 at a time with a running carry.
-__global__ void __launch_bounds__(1024) k_sort_scan_totals(uint32_t* __restrict__ chunk_totals, uint32_t n) {
-    __shared__ uint32_t s_warp[32];
-    uint32_t carry = 0;
-    for (uint32_t base = 0; base < n; base += 1024) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < n ? chunk_totals[i] : 0u;
-        uint32_t total;
-        const uint32_t ex = block_excl_scan(v, s_warp, total);
-        if (i < n) chunk_totals[i] = carry + ex;
-        carry += total;
-    }
-}
-
-// Stable scatter: items are ranked in index order (round, warp, lane) within each digit.
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
-                                                               const int32_t* __restrict__ vin,
-                                                               const uint32_t* __restrict__ count, uint32_t n_max,
-                                                               uint32_t shift, uint32_t n_blocks,
-                                                               const uint32_t* __restrict__ hist,
-                                                               const uint32_t* __restrict__ chunk_prefix,
-                                                               uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_wc[kSortThreads / 32][256];
     const uint32_t n = min(*count, n_max);
-    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    {
-        const uint32_t h = threadIdx.x * n_blocks + blockIdx.x;
-        s_run[threadIdx.x] = hist[h] + chunk_prefix[h / kScanChunk];
-    }
-    const uint32_t base = blockIdx.x * kSortTile;
-    for (uint32_t r = 0; r < kSortItems; ++r) {
-        for (uint32_t ww = 0; ww < kSortThreads / 32; ++ww) s_wc[ww][threadIdx.x] = 0;
-        __syncthreads();
-        const uint32_t i = base + r * kSortThreads + threadIdx.x;
-        const bool ok = i < n;
-        uint32_t key = 0, dig = 256;
-        int32_t val = 0;
-        if (ok) {
-            key = kin[i];
-            val = vin[i];
-            dig = (key >> shift) & 255u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int slot;
+        uint32_t key;
+        if (ray_o) {
+            slot = queue[i];
+            key = morton_key(ray_o, ray_d, slot, scenes, slot_scene, kind);
+        } else { // a caller's keys (queue) and values (slot_scene): the sort alone
+            key = reinterpret_cast<const uint32_t*>(queue)[i] & ((1u << (kRadixBits * kRadixPasses)) - 1u);
+            slot = reinterpret_cast<const int32_t*>(slot_scene)[i];
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, dig);
-        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        if (ok && rank == 0) s_wc[w][dig] = __popc(peers);
+        keys[i] = key;
+        vals[i] = slot;
+        // the other value buffer starts as a copy, so every position a pass can leave
+        // unwritten (only after a look-back wait ran out) still holds a valid slot
+        vals_alt[i] = slot;
+        atomicAdd(&s_h[key & kRadixMask], 1u);
+        atomicAdd(&s_h[kRadix + ((key >> kRadixBits) & kRadixMask)], 1u);
+        atomicAdd(&s_h[2 * kRadix + ((key >> (2 * kRadixBits)) & kRadixMask)], 1u);
+    }
+    // clear the look-back words of the live tiles of every pass
+    const uint32_t n_tiles = (n + kOsTile - 1) / kOsTile;
+    const size_t per_pass = (size_t)n_tiles * kRadix;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < kRadixPasses * per_pass; i += stride) {
+        const size_t pass = i / per_pass;
+        ws[kOsStatus + pass * status_stride + (i - pass * per_pass)] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kRadixPasses * kRadix; i += blockDim.x)
+        if (s_h[i]) atomicAdd(&ws[kOsHist + i], s_h[i]);
+}
+
+__global__ void __launch_bounds__(kOsThreads, 3) k_onesweep(const uint32_t* __restrict__ kin,
+                                                            const int32_t* __restrict__ vin,
+                                                            uint32_t* __restrict__ kout, int32_t* __restrict__ vout,
+                                                            const uint32_t* __restrict__ count, uint32_t n_max,
+                                                            uint32_t pass, uint32_t* __restrict__ ws,
+                                                            uint32_t* status, uint32_t* __restrict__ err) {
+    // per-warp digit counts (then per-warp offsets); afterwards the tile's keys and values
+    // in sorted order (kOsTile each, the same 32 KB)
+    __shared__ uint32_t s_cnt[kOsWarps * kRadix];
+    __shared__ uint32_t s_gbase[kRadix]; // first output position of each digit (all tiles)
+    __shared__ uint32_t s_local[kRadix]; // first tile-local position of each digit
+    __shared__ uint32_t s_out[kRadix];   // the tile's digit counts, then output position - local position
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_tile;
+    const uint32_t n = min(*count, n_max);
+    const uint32_t n_tiles = (n + kOsTile - 1) / kOsTile;
+    const uint32_t shift = kRadixBits * pass;
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    {   // exclusive scan of the pass's global digit counts; thread t owns digits 4t..4t+3
+        const uint32_t d0 = 4 * threadIdx.x;
+        const uint32_t* h = ws + kOsHist + pass * kRadix + d0;
+        const uint32_t c0 = h[0], c1 = h[1], c2 = h[2], c3 = h[3];
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(c0 + c1 + c2 + c3, s_warp, tot);
+        s_gbase[d0] = ex;
+        s_gbase[d0 + 1] = ex + c0;
+        s_gbase[d0 + 2] = ex + c0 + c1;
+        s_gbase[d0 + 3] = ex + c0 + c1 + c2;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ws[kOsTicket + pass], 1u);
+        for (uint32_t i = threadIdx.x; i < kOsWarps * kRadix; i += kOsThreads) s_cnt[i] = 0u;
         __syncthreads();
-        // exclusive prefix over warps for digit d = threadIdx.x, then advance the running base
-        {
-            const uint32_t d = threadIdx.x;
+        const uint32_t tile = s_tile;
+        if (tile >= n_tiles) break;
+        // a warp ranks its 512 consecutive keys round by round (index order = round, lane):
+        // rank = keys of the same digit in earlier rounds + peers in lower lanes this round
+        const uint32_t wbase = tile * kOsTile + w * kOsWarpKeys;
+        uint32_t* wc = s_cnt + w * kRadix;
+        uint32_t key[kOsRounds], pos[kOsRounds];
+        int32_t val[kOsRounds];
+#pragma unroll
+        for (uint32_t r = 0; r < kOsRounds; ++r) {
+            const uint32_t i = wbase + r * 32 + lane;
+            key[r] = i < n ? kin[i] : 0u;
+            val[r] = i < n ? vin[i] : 0;
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < kOsRounds; ++r) {
+            const bool ok = wbase + r * 32 + lane < n;
+            const uint32_t dig = (key[r] >> shift) & kRadixMask;
+            // lanes with the same digit: one ballot per digit bit (a warp multisplit), far
+            // cheaper than a match instruction; lanes past the end join no group
+            uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+            for (uint32_t bit = 0; bit < kRadixBits; ++bit) {
+                const uint32_t b = __ballot_sync(0xffffffffu, (dig >> bit) & 1u);
+                peers &= ((dig >> bit) & 1u) ? b : ~b;
+            }
+            const uint32_t below = __popc(peers & ((1u << lane) - 1u));
+            const uint32_t before = ok ? wc[dig] : 0u;
+            __syncwarp();
+            if (ok && below == 0u) wc[dig] = before + __popc(peers);
+            __syncwarp();
+            pos[r] = before + below;
+        }
+        __syncthreads();
+        // per digit: exclusive offsets of the warps, and the tile's count
+        for (uint32_t d = threadIdx.x; d < kRadix; d += kOsThreads) {
             uint32_t acc = 0;
-            for (uint32_t ww = 0; ww < kSortThreads / 32; ++ww) {
-                const uint32_t c = s_wc[ww][d];
-                s_wc[ww][d] = acc;
+            for (uint32_t ww = 0; ww < kOsWarps; ++ww) {
+                const uint32_t c = s_cnt[ww * kRadix + d];
+                s_cnt[ww * kRadix + d] = acc;
                 acc += c;
             }
-            // s_run[d] still holds the base for this round; the total is added after use
-            __syncthreads();
-            if (ok) {
-                const uint32_t dst = s_run[dig] + s_wc[w][dig] + rank;
-                kout[dst] = key;
-                vout[dst] = val;
-            }
-            __syncthreads();
-            s_run[d] += acc;
+            s_out[d] = acc;
         }
         __syncthreads();
+        {   // tile-local exclusive scan over the digits (ends with a block barrier)
+            const uint32_t d0 = 4 * threadIdx.x;
+            const uint32_t c0 = s_out[d0], c1 = s_out[d0 + 1], c2 = s_out[d0 + 2], c3 = s_out[d0 + 3];
+            uint32_t tot;
+            const uint32_t ex = block_excl_scan(c0 + c1 + c2 + c3, s_warp, tot);
+            s_local[d0] = ex;
+            s_local[d0 + 1] = ex + c0;
+            s_local[d0 + 2] = ex + c0 + c1;
+            s_local[d0 + 3] = ex + c0 + c1 + c2;
+        }
+        __syncthreads(); // every digit's tile-local start is written
+        // decoupled look-back; thread t owns digits t, t + 256, t + 512, t + 768 (adjacent
+        // threads poll adjacent words).  All four digits walk back together, kLookbackWindow
+        // earlier tiles per step, so that many independent loads are in flight.  The walk of
+        // a digit stops at the first inclusive word and pauses at a word not yet published.
+        // Every wait is bounded: when it runs out the error word is set and the tile carries
+        // on with what it has (its writes stay in bounds).
+        {
+            constexpr uint32_t Q = kRadix / kOsThreads, Wn = kLookbackWindow;
+            uint32_t cnt[Q], excl[Q];
+            int32_t cur[Q]; // the next earlier tile to read, -1 once the digit is done
+#pragma unroll
+            for (uint32_t q = 0; q < Q; ++q) {
+                const uint32_t d = threadIdx.x + q * kOsThreads;
+                cnt[q] = s_out[d];
+                excl[q] = 0;
+                cur[q] = (int32_t)tile - 1;
+                if (tile > 0) *(volatile uint32_t*)(status + (size_t)tile * kRadix + d) = kFlagAgg | cnt[q];
+            }
+            uint32_t idle = 0;
+            bool pending = tile > 0;
+            while (pending) {
+                uint32_t v[Q][Wn];
+#pragma unroll
+                for (uint32_t q = 0; q < Q; ++q)
+#pragma unroll
+                    for (uint32_t k = 0; k < Wn; ++k) {
+                        const int32_t tp = cur[q] - (int32_t)k;
+                        v[q][k] = tp >= 0 ? *(volatile const uint32_t*)(status + (size_t)tp * kRadix + threadIdx.x +
+                                                                        q * kOsThreads)
+                                          : 0u;
+                    }
+                pending = false;
+                bool moved = false;
+#pragma unroll
+                for (uint32_t q = 0; q < Q; ++q) {
+                    bool go = cur[q] >= 0;
+#pragma unroll
+                    for (uint32_t k = 0; k < Wn; ++k) {
+                        if (go) {
+                            const uint32_t x = v[q][k];
+                            if ((x & ~kCountMask) == 0u) {
+                                go = false; // not published yet: read this tile again
+                            } else {
+                                excl[q] += x & kCountMask;
+                                cur[q] = (x & kFlagInc) ? -1 : cur[q] - 1;
+                                go = cur[q] >= 0;
+                                moved = true;
+                            }
+                        }
+                    }
+                    pending |= cur[q] >= 0;
+                }
+                if (pending && !moved) {
+                    if (++idle > kLookbackSpins) {
+                        atomicOr(err, kSortErrBit);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < Q; ++q) {
+                const uint32_t d = threadIdx.x + q * kOsThreads;
+                *(volatile uint32_t*)(status + (size_t)tile * kRadix + d) = kFlagInc | (excl[q] + cnt[q]);
+                s_out[d] = s_gbase[d] + excl[q] - s_local[d];
+            }
+        }
+        // tile-local positions: digit start in the tile + the warp's offset + rank in the warp
+#pragma unroll
+        for (uint32_t r = 0; r < kOsRounds; ++r) {
+            if (wbase + r * 32 + lane < n) {
+                const uint32_t dig = (key[r] >> shift) & kRadixMask;
+                pos[r] += s_local[dig] + s_cnt[w * kRadix + dig];
+            }
+        }
+        __syncthreads(); // the warp offsets are read: the same memory now stages the tile
+        uint32_t* s_key = s_cnt;
+        int32_t* s_val = reinterpret_cast<int32_t*>(s_cnt + kOsTile);
+#pragma unroll
+        for (uint32_t r = 0; r < kOsRounds; ++r) {
+            if (wbase + r * 32 + lane < n) {
+                s_key[pos[r]] = key[r];
+                s_val[pos[r]] = val[r];
+            }
+        }
+        __syncthreads();
+        const uint32_t tile_n = min(kOsTile, n - tile * kOsTile);
+        for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
+            const uint32_t k = s_key[j];
+            const uint32_t dst = s_out[(k >> shift) & kRadixMask] + j;
+            if (dst < n) {
+                kout[dst] = k;
+                vout[dst] = s_val[j];
+            } else {
+                atomicOr(err, kSortErrBit);
+            }
+        }
+        __syncthreads(); // shared memory is reused by the next tile
     }
 }
 
@@ -1477,7 +1609,32 @@ void launch_sample(uint32_t kind, uint32_t n, const float* wo, const float* u, c
     lc.n++;
 }
 
-// Sort the current bounce's ray queue by TwoPoint key; returns the sorted slot queue.
+// SMs of the current device (grids of a fixed number of blocks per SM).
+static int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// Resident k_onesweep blocks per SM (its grid: one wave of persistent blocks).
+static uint32_t onesweep_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_onesweep, kOsThreads, 0) != cudaSuccess || nb <= 0)
+            nb = 2;
+        cached = nb;
+    }
+    return (uint32_t)cached;
+}
+
+// Sort the current bounce's ray queue by its reordering key; returns the sorted slot queue.
 const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bounce, uint32_t key_kind,
                                   cudaStream_t st, LaunchCount& lc) {
     const uint32_t n_max = b.n_slots;
@@ -1486,21 +1643,20 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
     uint32_t* kb = b.keys + n_max;
     int32_t* va = b.vals;
     int32_t* vb = b.vals + n_max;
-    k_morton<<<(n_max + 255) / 256, 256, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max, p.scenes,
-                                                  b.slot_scene, key_kind, ka, va);
+    uint32_t* ws = b.sort_hist;
+    const uint32_t tiles_max = (n_max + kOsTile - 1) / kOsTile;
+    const size_t stride = (size_t)tiles_max * kRadix;
+    const uint32_t sms = (uint32_t)sm_count();
+    cudaMemsetAsync(ws, 0, 4 * (size_t)kOsStatus, st); // digit counts and tickets
+    k_morton<<<min((n_max + 511) / 512, 2 * sms), 512, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max,
+                                                                 p.scenes, b.slot_scene, key_kind, ka, va, vb, ws,
+                                                                 stride);
     lc.n++;
-    const uint32_t n_blocks = (n_max + kSortTile - 1) / kSortTile;
-    for (uint32_t pass = 0; pass < 4; ++pass) {
-        const uint32_t shift = 8 * pass;
-        const uint32_t len = 256 * n_blocks;
-        const uint32_t n_chunks = (len + kScanChunk - 1) / kScanChunk;
-        uint32_t* chunk_totals = b.sort_hist + len;
-        k_sort_hist<<<n_blocks, kSortThreads, 0, st>>>(ka, count, n_max, shift, n_blocks, b.sort_hist);
-        k_sort_scan_chunks<<<n_chunks, 1024, 0, st>>>(b.sort_hist, len, chunk_totals);
-        k_sort_scan_totals<<<1, 1024, 0, st>>>(chunk_totals, n_chunks);
-        k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ka, va, count, n_max, shift, n_blocks, b.sort_hist,
-                                                          chunk_totals, kb, vb);
-        lc.n += 4;
+    const uint32_t blocks = max(1u, min(tiles_max, onesweep_blocks_per_sm() * sms));
+    for (uint32_t pass = 0; pass < kRadixPasses; ++pass) {
+        k_onesweep<<<blocks, kOsThreads, 0, st>>>(ka, va, kb, vb, count, n_max, pass, ws,
+                                                  ws + kOsStatus + pass * stride, b.counts + kQueueErrWord);
+        lc.n++;
         uint32_t* tk = ka;
         ka = kb;
         kb = tk;
@@ -1508,18 +1664,50 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
         va = vb;
         vb = tv;
     }
-    return va; // after four passes the sorted pairs are back in the first buffers
+    return va; // the last pass's output
 }
 
-// histogram entries plus one chunk total per kScanChunk entries
+// The ray sort on a caller's n keys (low 30 bits) and values, in buffers of the sort's
+// layout: keys[0, 2n) and vals[0, 2n), ws of sort_hist_len(n) words; returns the sorted
+// values (the sorted keys are at the same offset of keys).  Used by cr_debug_sort.
+int32_t* launch_sort_only(const uint32_t* key_in, const int32_t* val_in, uint32_t n, uint32_t* keys, int32_t* vals,
+                          uint32_t* ws, uint32_t* count, uint32_t* err, cudaStream_t st, LaunchCount& lc) {
+    uint32_t* ka = keys;
+    uint32_t* kb = keys + n;
+    int32_t* va = vals;
+    int32_t* vb = vals + n;
+    const uint32_t tiles_max = (n + kOsTile - 1) / kOsTile;
+    const size_t stride = (size_t)tiles_max * kRadix;
+    const uint32_t sms = (uint32_t)sm_count();
+    cudaMemsetAsync(ws, 0, 4 * (size_t)kOsStatus, st);
+    k_morton<<<min((n + 511) / 512, 2 * sms), 512, 0, st>>>(nullptr, nullptr, reinterpret_cast<const int32_t*>(key_in),
+                                                             count, n, nullptr,
+                                                             reinterpret_cast<const uint16_t*>(val_in), 0, ka, va, vb,
+                                                             ws, stride);
+    lc.n++;
+    const uint32_t blocks = max(1u, min(tiles_max, onesweep_blocks_per_sm() * sms));
+    for (uint32_t pass = 0; pass < kRadixPasses; ++pass) {
+        k_onesweep<<<blocks, kOsThreads, 0, st>>>(ka, va, kb, vb, count, n, pass, ws, ws + kOsStatus + pass * stride,
+                                                  err);
+        lc.n++;
+        uint32_t* tk = ka;
+        ka = kb;
+        kb = tk;
+        int32_t* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    return va;
+}
+
 void launch_scan_counts(uint32_t* block_counts, uint32_t n_blocks, uint32_t* total, cudaStream_t st) {
     // k_compact_scan scans both columns; column 1 is zero here and its total lands in total[1]
     k_compact_scan<<<1, 1024, 0, st>>>(block_counts, n_blocks, total, nullptr);
 }
 
+// words of the sort workspace: digit counts, tickets and the look-back words of every pass
 uint32_t sort_hist_len(uint32_t n_slots) {
-    const uint32_t len = 256u * ((n_slots + kSortTile - 1) / kSortTile);
-    return len + (len + kScanChunk - 1) / kScanChunk + 4;
+    return kOsStatus + kRadixPasses * ((n_slots + kOsTile - 1) / kOsTile) * kRadix;
 }
 uint32_t compact_blocks(uint32_t n_pos) { return (n_pos + kCompactBlock - 1) / kCompactBlock; }
 

@@ -121,3 +121,12 @@ def test_static_trace_argument_checks_without_gpu(cr):
             cr.check_static_trace_args(args["rays"], args["skip"], args["prim"], args["t"])
         with pytest.raises(exc, match=text):  # the entry point's wrapper checks before calling C
             cr.cr_trace_rays_static(None, args["rays"], args["skip"], args["prim"], args["t"])
+
+
+def test_debug_sort_rejects_bad_arguments_without_gpu(cr):
+    L = cr.lib()
+    k = np.zeros(4, np.uint32)
+    assert L.cr_debug_sort(None, None, 0, 1, None, None, None) == cr.CR_OK  # nothing to sort
+    assert L.cr_debug_sort(k.ctypes.data, None, 4, 1, k.ctypes.data, k.ctypes.data, None) == cr.CR_ERR_INVALID_ARG
+    assert L.cr_debug_sort(k.ctypes.data, k.ctypes.data, 4, 0, k.ctypes.data, k.ctypes.data, None) == \
+        cr.CR_ERR_INVALID_ARG
