@@ -853,7 +853,11 @@ def batched_leg(cr, scenes, rank, args):
            "pixels": int(sum(sd * sd for _, sd, _ in specs)),
            "autotune": {"seconds": round(tune_s, 1), "candidates": rep["n_candidates"],
                         "best": f"{opts.group_w}x{opts.group_h} K={opts.k} interleave={'lcg' if opts.interleave else 'contiguous'} block={opts.block} stack={opts.stack}",
-                        "best_ms_spp1": round(rep["best_ms"], 3), "default_ms_spp1": round(rep["default_ms"], 3)}}
+                        "best_ms_spp1": round(rep["best_ms"], 3), "default_ms_spp1": round(rep["default_ms"], 3),
+                        "quality_guard": {"probe_job": rep["probe_job"], "best_block_mse": rep["best_mse"],
+                                          "default_block_mse": rep["default_mse"], "rejected": rep["n_rejected"],
+                                          "measure": "MSE of 4x4-pixel block means against a 64-spp independent "
+                                                     "reference; groupings above 1.1x the default's are not chosen"}}}
     variants = {"graph_autotuned": (opts, cr.CR_BATCH_GRAPH),
                 "graph_default": (cr.make_batch_opts(tile=(8, 8), k=8), cr.CR_BATCH_GRAPH),
                 "direct_autotuned": (opts, 0)}
@@ -905,7 +909,10 @@ def serving_leg(cr, scenes, args):
              "interior": scenes.interior(), "landscape": scenes.landscape(), "terrain": scenes.terrain()}
     S = {k: cr.Scene(v, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q) for k, v in world.items()}
     names = list(world)
-    out = {"window_s": args.serve_window, "rates": list(args.serve_rates), "configs": {}}
+    out = {"window_s": args.serve_window, "drain_s": args.serve_drain, "rates": list(args.serve_rates),
+           "latency": "submission to the result on the host, over the requests completed by the end of the drain; "
+                      "queue wait = admission - submission, render = completion - admission",
+           "configs": {}}
     for cfg, mode, bvh in (("reuse_bvh8q", "direction_reuse", cr.CR_BVH8Q), ("independent_bvh2", "independent", cr.CR_BVH2),
                            ("reuse_bvh2", "direction_reuse", cr.CR_BVH2)):
         rows = {}
@@ -935,13 +942,39 @@ def serving_leg(cr, scenes, args):
                 jid = cr.cr_server_submit(srv, cr.make_job(S[name].handle, cam, host, spp=spp, max_bounces=B,
                                                            mode=mode, seed=int(rng.integers(0, 1 << 30))))
                 reqs.append((jid, host))
-            lat = [cr.cr_server_wait(srv, jid, 600000)["latency_ms"] for jid, _ in reqs]
+            window_end_ms = args.serve_window * 1e3
+            # drain: at rates the GPU sustains every request finishes; under overload the
+            # backlog left after the drain is reported (and dropped with the server)
+            done, t_drain = {}, time.perf_counter()
+            while len(done) < len(reqs) and time.perf_counter() - t_drain < args.serve_drain:
+                for jid, _ in reqs:
+                    if jid not in done:
+                        r = cr.cr_server_poll(srv, jid)
+                        if r is not None:
+                            done[jid] = r
+                time.sleep(0.002)
             wall = time.perf_counter() - t0
             st = cr.cr_server_get_stats(srv)
             cr.cr_server_destroy(srv)
-            rows[str(lam)] = {"requests": len(reqs), "p50_ms": round(float(np.percentile(lat, 50)), 1),
-                              "p99_ms": round(float(np.percentile(lat, 99)), 1), "wall_s": round(wall, 2),
-                              "mrays": round(st["secondary_rays"] / wall / 1e6, 1), "passes": st["passes"]}
+            js = list(done.values())
+            lat = [j["latency_ms"] for j in js]
+            wait = [j["t_admit_ms"] - j["t_submit_ms"] for j in js]
+            rend = [j["t_done_ms"] - j["t_admit_ms"] for j in js]
+
+            def pct(v, q):
+                return round(float(np.percentile(v, q)), 1) if v else None
+
+            t_first = min((j["t_submit_ms"] for j in js), default=0.0)
+            rows[str(lam)] = {
+                "arrivals": len(reqs), "completed": len(js),
+                "completed_in_window": sum(1 for j in js if j["t_done_ms"] - t_first <= window_end_ms),
+                "admitted_in_window": sum(1 for j in js if j["t_admit_ms"] - t_first <= window_end_ms),
+                "unfinished_after_drain": len(reqs) - len(js),
+                "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "queue_wait_p50_ms": pct(wait, 50), "queue_wait_p99_ms": pct(wait, 99),
+                "render_p50_ms": pct(rend, 50), "render_p99_ms": pct(rend, 99),
+                "wall_s": round(wall, 2), "mrays": round(st["secondary_rays"] / wall / 1e6, 1),
+                "passes": st["passes"]}
         out["configs"][cfg] = rows
     for v in S.values():
         v.close()
@@ -959,7 +992,8 @@ def main():
     ap.add_argument("--core-only", action="store_true", help="skip the precision, sweep, quality, batched and serving legs")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-window", type=float, default=1.5, help="seconds of Poisson arrivals per rate")
+    ap.add_argument("--serve-window", type=float, default=10.0, help="seconds of Poisson arrivals per rate")
+    ap.add_argument("--serve-drain", type=float, default=5.0, help="seconds to wait for the requests after the window")
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[20.0, 50.0, 100.0, 200.0])
     ap.add_argument("--scene", default="landscape", choices=["landscape", "interior"],
                     help="workload scene; the headline metric is the landscape's")

@@ -215,6 +215,12 @@ typedef struct {
     void* stream;          /* cudaStream_t to run on; NULL = legacy default stream */
     cr_stats* stats;       /* optional, host */
     cr_debug* debug;       /* optional, host struct of device pointers */
+    /* Render only tiles [tile_begin, tile_end) of the image's group_w x group_h tiling
+     * (row-major tile order; 0, 0 = every tile).  Pixels outside the range are left as they
+     * are in out_rgb.  Every reuse group lies inside one tile (Sec. 3.3) and random numbers
+     * are keyed by pixel, so tile-aligned parts of an image rendered separately (on one or
+     * several devices) equal the whole render bit for bit. */
+    uint32_t tile_begin, tile_end;
 } cr_render_opts;
 
 /* Fill opts with the defaults: k = 0, interleave = 1, seed = 0, frame_base = 0,
@@ -327,13 +333,27 @@ cr_status cr_batch_device_bytes(const cr_job* jobs, uint32_t n_jobs, const cr_ba
  * quality, Sec. 5.3), interleave {LCG, contiguous} if allowed, and trace block {64, 128,
  * 256} on the given jobs (renders them), then the traversal stack depth in shared memory
  * {8, 16, 32} for the fastest of those, and writes the winner into *opts (its bvh and
- * flags are kept).  allow_contiguous = 0 keeps the LCG interleave of Sec. 3.3. */
+ * flags are kept).  allow_contiguous = 0 keeps the LCG interleave of Sec. 3.3.
+ * Quality guard: grouping changes which directions are shared, so speed alone could pick a
+ * grouping that shows the method's correlation artifacts (Sec. 3.3, 5.3).  When some job
+ * reuses directions, the largest such job of at most 512 x 512 pixels (the probe) is
+ * rendered once at 64 spp with independent sampling as a reference, and once per distinct
+ * (W, H, K, interleave) at its own spp, seed and frames.  The error measure is the MSE of
+ * 4x4-pixel block means: at a fixed spp, pixel-wise MSE is blind to how errors of
+ * neighbouring pixels correlate, and the block means are not.  A grouping whose error
+ * exceeds the default grouping's (8x8, K=8, LCG) by more than 10% is not chosen. */
 typedef struct {
     uint32_t n_candidates;
     uint32_t best_group_w, best_group_h, best_k, best_interleave, best_block, best_stack;
     double best_ms;   /* device ms of one run of the best candidate */
     double worst_ms;  /* slowest candidate */
     double default_ms;/* 8x8, K=8, LCG, block 128 */
+    /* Quality guard (when a job reuses directions): error of the probe job against its 64-spp
+     * independent reference (MSE of 4x4-pixel block means) for the chosen grouping and for
+     * the default one, the candidates rejected for an error more than 10% above the
+     * default's (not timed), and the probe job's index (all 0 when the guard is off). */
+    double best_mse, default_mse;
+    uint32_t n_rejected, probe_job;
 } cr_tune_report;
 
 cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint32_t allow_contiguous, cr_batch_opts* opts,

@@ -103,7 +103,9 @@ class cr_batch_opts(C.Structure):
 class cr_tune_report(C.Structure):
     _fields_ = [("n_candidates", C.c_uint32), ("best_group_w", C.c_uint32), ("best_group_h", C.c_uint32),
                 ("best_k", C.c_uint32), ("best_interleave", C.c_uint32), ("best_block", C.c_uint32),
-                ("best_stack", C.c_uint32), ("best_ms", C.c_double), ("worst_ms", C.c_double), ("default_ms", C.c_double)]
+                ("best_stack", C.c_uint32), ("best_ms", C.c_double), ("worst_ms", C.c_double), ("default_ms", C.c_double),
+                ("best_mse", C.c_double), ("default_mse", C.c_double), ("n_rejected", C.c_uint32),
+                ("probe_job", C.c_uint32)]
 
 
 class cr_server_opts(C.Structure):
@@ -128,7 +130,7 @@ class cr_render_opts(C.Structure):
                 ("reuse_depth", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32), ("flags", C.c_uint32),
                 ("sort_key", C.c_uint32), ("stack", C.c_uint32), ("diffuse_roughness", C.c_float),
                 ("stream", C.c_void_p), ("stats", C.POINTER(cr_stats)),
-                ("debug", C.POINTER(cr_debug))]
+                ("debug", C.POINTER(cr_debug)), ("tile_begin", C.c_uint32), ("tile_end", C.c_uint32)]
 
 
 _lib = None
@@ -269,7 +271,8 @@ SORT_KEYS = {"two_point": 0, "origin": 1, "reis": 2, "costa": 3, "aila_compact":
 
 
 def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_BVH2, block=0, flags=0,
-              stream=None, stats=None, debug=None, sort_key=0, stack=0, diffuse_roughness=0.0) -> cr_render_opts:
+              stream=None, stats=None, debug=None, sort_key=0, stack=0, diffuse_roughness=0.0,
+              tiles=None) -> cr_render_opts:
     o = cr_render_opts()
     _check(lib().cr_render_opts_default(C.byref(o)))
     o.k, o.interleave, o.seed, o.frame_base = k, int(interleave), seed, frame_base
@@ -282,6 +285,8 @@ def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_
         o.stats = C.pointer(stats)
     if debug is not None:
         o.debug = C.pointer(debug)
+    if tiles is not None:
+        o.tile_begin, o.tile_end = tiles
     return o
 
 
@@ -514,7 +519,7 @@ class Scene:
     def render(self, cam=None, *, spp=1, max_bounces=1, mode="direction_reuse", tile=(8, 8), k=0, interleave=True,
                seed=0, frame_base=0, reuse_depth=0, out=None, stats=False, flags=0, block=0, bvh=CR_BVH2,
                debug=None, stream=None, sort_key=0, nee=False, stack=0, hybrid_donor=False, nee_shared=False,
-               diffuse_roughness=0.0):
+               diffuse_roughness=0.0, tiles=None):
         """Render into ``out`` (torch CUDA tensor or numpy array of h x w x 3 float32; a new
         CUDA tensor by default).  Returns (out, stats dict or None)."""
         import torch
@@ -526,7 +531,7 @@ class Scene:
                       block=block, flags=flags | (CR_OPT_STATS if stats else 0) | (CR_OPT_NEE if nee else 0)
                       | (CR_OPT_HYBRID_DONOR if hybrid_donor else 0) | (CR_OPT_NEE_SHARED if nee_shared else 0),
                       stream=stream, stats=st, debug=debug, sort_key=sort_key, stack=stack,
-                      diffuse_roughness=diffuse_roughness)
+                      diffuse_roughness=diffuse_roughness, tiles=tiles)
         cr_render_ex(self.handle, cam, spp, max_bounces, mode, tile[0], tile[1], out, o)
         return out, (st.as_dict() if st is not None else None)
 

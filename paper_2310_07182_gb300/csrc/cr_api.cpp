@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <thread>
@@ -630,6 +631,14 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
         pxb[i] = px_base;
         px_base += jobs[i].camera.width * jobs[i].camera.height;
     }
+    if (po.tile_end != 0) {
+        const cr_job& j = jobs[0];
+        const uint64_t all = (uint64_t)((j.camera.width + po.tile_w - 1) / po.tile_w) *
+                             ((j.camera.height + po.tile_h - 1) / po.tile_h);
+        if (n_jobs != 1 || po.tile_begin >= po.tile_end || po.tile_end > all)
+            return fail(CR_ERR_INVALID_ARG, "tile range [%u, %u) is not within the image's %llu tiles", po.tile_begin,
+                        po.tile_end, (unsigned long long)all);
+    }
     for (uint32_t p = 0; p < max_spp; ++p) {
         Pass ps;
         ps.job_offset = (uint32_t)plan.jobs.size();
@@ -663,7 +672,12 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
             d.inv_spp = 1.0f / (float)j.spp;
             d.sample_flags = (p == 0 ? 1u : 0u) | (p + 1 == j.spp ? 2u : 0u);
             d.diffuse_rough = j.diffuse_roughness;
-            const uint64_t t64 = (uint64_t)tiles + (uint64_t)d.tiles_x * tiles_y;
+            uint64_t job_tiles = (uint64_t)d.tiles_x * tiles_y;
+            if (po.tile_end != 0) {
+                d.tile_first = po.tile_begin;
+                job_tiles = po.tile_end - po.tile_begin;
+            }
+            const uint64_t t64 = (uint64_t)tiles + job_tiles;
             if (t64 * m > (1ull << 27)) return fail(CR_ERR_INVALID_ARG, "pass %u: too many slots", p);
             tiles = (uint32_t)t64;
             plan.jobs.push_back(d);
@@ -872,6 +886,11 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     po.k = o.k;
     po.interleave = o.interleave;
     po.bvh8 = use8;
+    if (o.tile_begin != 0 || o.tile_end != 0) {
+        po.tile_begin = o.tile_begin;
+        po.tile_end = o.tile_end;
+        if (po.tile_end == 0) return fail(CR_ERR_INVALID_ARG, "cr_render: tile_end is 0 with tile_begin %u", o.tile_begin);
+    }
     RenderPlan plan;
     st = build_plan(&job, 1, po, plan);
     if (st != CR_OK) return st;
@@ -914,6 +933,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         CR_CUDA(cudaEventCreate(&e_all[1]));
         CR_CUDA(cudaEventRecord(e_all[0], stream));
     }
+    if (!out_dev && po.tile_end != 0) // pixels outside the range keep the caller's values
+        CR_CUDA(cudaMemcpyAsync(s->d_out, out_rgb, sizeof(float) * 3 * (size_t)npx, cudaMemcpyHostToDevice, stream));
     st = enqueue_plan(plan, dev, s->ws, eo, stream, lc,
                       (o.stats && (o.flags & (CR_OPT_STATS | CR_OPT_STATS_TRACES))) ? &times : nullptr);
     if (st != CR_OK) return st;
@@ -943,7 +964,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         stats.tri_tests = ctr[1];
         stats.shadow_rays = host_counts[kShadowWord / 2];
         stats.ms_trace_shadow = times.trace_shadow;
-        stats.h2d_bytes = sizeof(JobDev) * plan.jobs.size() + sizeof(SceneDev) * plan.scenes.size();
+        stats.h2d_bytes = sizeof(JobDev) * plan.jobs.size() + sizeof(SceneDev) * plan.scenes.size() +
+                          ((!out_dev && po.tile_end != 0) ? sizeof(float) * 3 * (size_t)npx : 0);
         stats.d2h_bytes = out_dev ? 0 : sizeof(float) * 3 * (uint64_t)npx;
         stats.primary_rays = (uint64_t)npx * spp;
         stats.kernel_launches = lc.n;
@@ -1400,6 +1422,101 @@ extern "C" cr_status cr_batch_destroy(cr_batch* b) {
     return CR_OK;
 }
 
+// Quality guard of the autotuner: a reference of the probe job (independent sampling,
+// kTuneRefSpp samples from frames no candidate uses) and each grouping's MSE against it.
+constexpr uint32_t kTuneRefSpp = 64;
+constexpr double kTuneMseMargin = 0.10;
+
+struct TuneProbe {
+    bool on = false;
+    uint32_t job = 0;
+    size_t n = 0;               // floats of the image
+    DevMem img;                 // device render target
+    std::vector<float> ref, host;
+    std::map<uint64_t, double> mse; // by (W, H, K, interleave)
+};
+
+static cr_status probe_render(const cr_job& j, uint32_t W, uint32_t H, uint32_t K, uint32_t il, uint32_t spp,
+                              uint32_t mode, uint64_t seed, uint32_t frame_base, float* out) {
+    cr_render_opts o;
+    cr_render_opts_default(&o);
+    o.k = K;
+    o.interleave = il;
+    o.seed = seed;
+    o.frame_base = frame_base;
+    o.reuse_depth = j.reuse_depth;
+    o.diffuse_roughness = j.diffuse_roughness;
+    o.flags = ((j.flags & CR_JOB_NEE) ? (uint32_t)CR_OPT_NEE : 0u) |
+              ((j.flags & CR_JOB_HYBRID_DONOR) ? (uint32_t)CR_OPT_HYBRID_DONOR : 0u) |
+              ((j.flags & CR_JOB_NEE_SHARED) ? (uint32_t)CR_OPT_NEE_SHARED : 0u);
+    return cr_render_ex(j.scene, &j.camera, spp, j.max_bounces, (cr_reuse_mode)mode, W, H, out, &o);
+}
+
+static cr_status probe_setup(const cr_job* jobs, uint32_t n_jobs, TuneProbe& pr) {
+    uint64_t best = 0;
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        if (jobs[i].mode != CR_DIRECTION_REUSE && jobs[i].mode != CR_WORLD_REUSE) continue;
+        const uint64_t px = (uint64_t)jobs[i].camera.width * jobs[i].camera.height;
+        const bool fits = px <= 512ull * 512ull;
+        const uint64_t cur = pr.on ? (uint64_t)jobs[pr.job].camera.width * jobs[pr.job].camera.height : 0;
+        const bool cur_fits = pr.on && cur <= 512ull * 512ull;
+        // the largest job that fits, else the smallest
+        if (!pr.on || (fits && (!cur_fits || px > best)) || (!fits && !cur_fits && px < best)) {
+            pr.on = true;
+            pr.job = i;
+            best = px;
+        }
+    }
+    if (!pr.on) return CR_OK;
+    const cr_job& j = jobs[pr.job];
+    pr.n = 3ull * j.camera.width * j.camera.height;
+    CR_CUDA(pr.img.alloc(4 * pr.n));
+    float* d = static_cast<float*>(pr.img.p);
+    cr_status st = probe_render(j, 8, 8, 8, 1, kTuneRefSpp, CR_INDEPENDENT, j.seed ^ 0x9e3779b97f4a7c15ull,
+                                j.frame_base + (1u << 24), d);
+    if (st != CR_OK) return st;
+    pr.ref.resize(pr.n);
+    pr.host.resize(pr.n);
+    CR_CUDA(cudaMemcpy(pr.ref.data(), d, 4 * pr.n, cudaMemcpyDeviceToHost));
+    return CR_OK;
+}
+
+static cr_status probe_mse(const cr_job* jobs, TuneProbe& pr, uint32_t W, uint32_t H, uint32_t K, uint32_t il,
+                           double& mse) {
+    const uint64_t key = ((uint64_t)W << 48) | ((uint64_t)H << 32) | ((uint64_t)K << 8) | il;
+    auto it = pr.mse.find(key);
+    if (it != pr.mse.end()) {
+        mse = it->second;
+        return CR_OK;
+    }
+    const cr_job& j = jobs[pr.job];
+    float* d = static_cast<float*>(pr.img.p);
+    cr_status st = probe_render(j, W, H, K, il, j.spp, j.mode, j.seed, j.frame_base, d);
+    if (st != CR_OK) return st;
+    CR_CUDA(cudaMemcpy(pr.host.data(), d, 4 * pr.n, cudaMemcpyDeviceToHost));
+    // MSE of the 4x4-pixel block means: independent pixel errors average down by 16 there,
+    // errors correlated within a block (directions shared by neighbouring pixels) do not
+    const uint32_t w = j.camera.width, h = j.camera.height;
+    double acc = 0.0;
+    uint64_t nb = 0;
+    for (uint32_t by = 0; by + 4 <= h; by += 4)
+        for (uint32_t bx = 0; bx + 4 <= w; bx += 4)
+            for (int c = 0; c < 3; ++c) {
+                double e = 0.0;
+                for (uint32_t y = by; y < by + 4; ++y)
+                    for (uint32_t x = bx; x < bx + 4; ++x) {
+                        const size_t i = 3 * ((size_t)y * w + x) + c;
+                        e += (double)pr.host[i] - (double)pr.ref[i];
+                    }
+                e /= 16.0;
+                acc += e * e;
+                ++nb;
+            }
+    mse = nb ? acc / (double)nb : 0.0;
+    pr.mse[key] = mse;
+    return CR_OK;
+}
+
 extern "C" cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint32_t allow_contiguous,
                                        cr_batch_opts* opts, cr_tune_report* report) {
     g_err.clear();
@@ -1408,6 +1525,16 @@ extern "C" cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint
     std::memset(&rep, 0, sizeof(rep));
     rep.best_ms = 1e30;
     const uint32_t tiles[3][2] = {{4, 4}, {8, 8}, {16, 16}};
+    TuneProbe probe;
+    {
+        cr_status pst = probe_setup(jobs, n_jobs, probe);
+        if (pst != CR_OK) return pst;
+    }
+    if (probe.on) {
+        rep.probe_job = probe.job;
+        cr_status pst = probe_mse(jobs, probe, 8, 8, 8, 1, rep.default_mse);
+        if (pst != CR_OK) return pst;
+    }
     auto time_one = [&](const cr_batch_opts& o, double& ms_out) -> cr_status {
         cr_batch* b = nullptr;
         cr_status st = cr_batch_create(jobs, n_jobs, &o, &b);
@@ -1428,7 +1555,17 @@ extern "C" cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint
         for (uint32_t k = 4; k <= m / 4 && k <= 64; k *= 2) {
             for (uint32_t il_i = 0; il_i < (allow_contiguous ? 2u : 1u); ++il_i) {
                 const uint32_t il = 1u - il_i;
+                double mse = 0.0;
+                if (probe.on) {
+                    cr_status pst = probe_mse(jobs, probe, t[0], t[1], k, il, mse);
+                    if (pst != CR_OK) return pst;
+                }
+                const bool rejected = probe.on && mse > rep.default_mse * (1.0 + kTuneMseMargin);
                 for (uint32_t block : {64u, 128u, 256u}) {
+                    if (rejected) { // not timed: its grouping fails the quality guard
+                        rep.n_rejected++;
+                        continue;
+                    }
                     cr_batch_opts o = *opts;
                     o.group_w = t[0];
                     o.group_h = t[1];
@@ -1443,6 +1580,7 @@ extern "C" cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint
                     rep.worst_ms = std::max(rep.worst_ms, ms);
                     if (t[0] == 8 && k == 8 && il == 1 && block == 128) rep.default_ms = ms;
                     if (ms < rep.best_ms) {
+                        rep.best_mse = mse;
                         rep.best_ms = ms;
                         rep.best_group_w = t[0];
                         rep.best_group_h = t[1];

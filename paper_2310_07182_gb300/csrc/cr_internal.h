@@ -119,6 +119,7 @@ struct JobDev {
     uint32_t hybrid_donor; // 1: hybrid groups reuse the first diffuse member's sample
     uint32_t sample_flags; // bit 0: this pass is the job's first sample, bit 1: its last
     float diffuse_rough;   // GGX of at least this roughness is in the diffuse class (0: off)
+    uint32_t tile_first;   // the job's first rendered tile of its image tiling (a tile range)
 };
 
 // Launch-uniform description of a pass.
@@ -301,6 +302,7 @@ size_t workspace_bytes(uint32_t n_slots, uint32_t npx);
 struct PlanOpts {
     uint32_t tile_w = 8, tile_h = 8, k = 0, interleave = 1;
     bool bvh8 = false;
+    uint32_t tile_begin = 0, tile_end = 0; // single-job plans: render only these tiles (0, 0 = all)
 };
 struct Pass {
     uint32_t job_offset = 0, n_jobs = 0, n_tiles = 0;

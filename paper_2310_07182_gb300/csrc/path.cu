@@ -91,7 +91,7 @@ __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __re
     if (in) {
         jid = job_of_tile(p.jobs, p.n_jobs, tile);
         const JobDev& J = p.jobs[jid];
-        const Lcg L = tile_lcg(J.seed, tile - J.tile_base, J.frame, m, J.interleave);
+        const Lcg L = tile_lcg(J.seed, tile - J.tile_base + J.tile_first, J.frame, m, J.interleave);
         const uint32_t s = sigma_of(L, j, m, J.interleave);
         inv[tl * m + s] = (uint16_t)j;
         if (primary_queue) primary_queue[tile * m + j] = (int32_t)(tile * m + s);
@@ -99,7 +99,7 @@ __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __re
     __syncthreads();
     if (!in) return;
     const JobDev& J = p.jobs[jid];
-    const uint32_t t = tile - J.tile_base;
+    const uint32_t t = tile - J.tile_base + J.tile_first;
     const uint32_t i = inv[tl * m + j];
     const uint32_t tx = t % J.tiles_x, ty = t / J.tiles_x;
     const uint32_t px = tx * p.tile_w + i % p.tile_w, py = ty * p.tile_h + i / p.tile_w;

@@ -35,7 +35,7 @@ def test_exports_every_declared_symbol(cr):
 def test_struct_layouts(cr):
     assert C.sizeof(cr.cr_material) == 32
     assert C.sizeof(cr.cr_camera) == 48
-    assert C.sizeof(cr.cr_render_opts) == 72
+    assert C.sizeof(cr.cr_render_opts) == 80
     assert C.sizeof(cr.cr_debug) == 72
 
 

@@ -79,7 +79,10 @@ def test_device_bytes_and_autotune(cr, world):
     three = cr.cr_batch_device_bytes(jobs, opts)
     assert 64 * 64 * 100 < one < three
     rep = cr.cr_batch_autotune(jobs, opts, allow_contiguous=True)
-    assert rep["n_candidates"] == 54 + 3  # then the stack depth of the winner
+    # every grouping is either timed or rejected by the quality guard; then the stack depth
+    assert rep["n_candidates"] + rep["n_rejected"] == 54 + 3
+    if any(j.mode == 2 for j in jobs):  # a direction-reuse job: the guard is on
+        assert rep["default_mse"] > 0 and rep["best_mse"] <= 1.1 * rep["default_mse"]
     assert rep["best_ms"] <= rep["default_ms"] <= rep["worst_ms"]
     assert opts.group_w in (4, 8, 16) and opts.k <= opts.group_w * opts.group_h // 4
     assert (opts.group_w, opts.k, opts.interleave, opts.block, opts.stack) == (

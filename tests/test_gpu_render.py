@@ -388,3 +388,31 @@ def test_hybrid_weight_reading_in_a_mixed_furnace_on_gpu(cr, hybrid_donor):
     glossy = cls == 2
     assert glossy.sum() > 20
     assert np.array_equal(rgb[glossy], ind.cpu().numpy().reshape(-1, 3)[glossy])
+
+
+@pytest.mark.parametrize("mode,nee", [("direction_reuse", False), ("independent", False), ("morton_sort", False),
+                                      ("direction_reuse", True)])
+def test_tile_aligned_parts_equal_the_whole_render(cr, mode, nee):
+    """The replica design of multi-GPU rendering: every reuse group lies inside one tile
+    (Sec. 3.3) and random numbers are keyed by pixel, so tile-aligned parts of an image
+    rendered separately (on one device here, on several in a sharded run) equal the whole
+    render bit for bit; also with uneven parts, ragged border tiles and a host output."""
+    sc = scenes.interior(width=200, height=84)  # 25 x 11 tiles of 8x8, the last row ragged
+    S = cr.Scene(sc)
+    kw = dict(spp=3, max_bounces=3, mode=mode, tile=(8, 8), k=8, seed=6, frame_base=2, nee=nee)
+    full, _ = S.render(**kw)
+    n_tiles = 25 * 11
+    for cuts in ((0, n_tiles // 2, n_tiles), (0, 1, 137, 138, n_tiles), (0, 24, 26, 250, n_tiles)):
+        out = torch.full_like(full, -1.0)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            S.render(out=out, tiles=(a, b), **kw)
+        assert torch.equal(out, full), (mode, cuts)
+    host = np.full(full.shape, 7.0, np.float32)
+    S.render(out=host, tiles=(0, 100), **kw)
+    py, px = np.mgrid[0:84, 0:200]
+    inside = (py // 8) * 25 + px // 8 < 100
+    assert np.array_equal(host[inside], full.cpu().numpy()[inside]) and (host[~inside] == 7.0).all()
+    with pytest.raises(cr.CrError):
+        S.render(tiles=(10, 10), **kw)
+    with pytest.raises(cr.CrError):
+        S.render(tiles=(0, n_tiles + 1), **kw)
