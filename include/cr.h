@@ -360,12 +360,16 @@ cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint32_t allow_
                             cr_tune_report* report);
 
 /* ---------------------------------------------------------------------------------- */
-/* Serving: a request loop with continuous batching.  A server thread renders one sample
- * pass of every admitted job at a time, all jobs merged into one wavefront; between passes
- * finished jobs are written out and queued jobs are admitted while their device footprint
- * (accumulation 16 B/px + output staging 12 B/px for host outputs + path state ~130 B per
- * slot) fits hbm_budget, so requests that arrive while others run join the next pass.
- * Results equal stand-alone renders with the same tile shape, K and interleave. */
+/* Serving: a request loop with continuous batching at bounce granularity.  A server thread
+ * runs a rolling wavefront: each iteration is one launch per stage (shade, light samples,
+ * sample sums, ray generation, trace) over the slots of every admitted job, whatever bounce
+ * each job is at, so a request joins at the next bounce launch after it is admitted and its
+ * buffers are free for others as soon as its last sample is summed.  Queued jobs are
+ * admitted first-come (later ones may backfill) while their device footprint fits the budget:
+ * path-state slots (whole tiles, ~170 B per slot), accumulation (16 B/px) and, for host
+ * outputs, staging (12 B/px), each a first-fit range of an arena allocated at creation (the
+ * loop allocates nothing).  Results equal stand-alone renders with the same tile shape, K and
+ * interleave. */
 typedef struct {
     uint64_t hbm_budget;       /* bytes of device memory the server may use (>= 64 MiB) */
     uint32_t group_w, group_h, k, interleave, bvh, block; /* as cr_batch_opts */
@@ -379,8 +383,10 @@ typedef struct {
 } cr_job_stats;
 
 typedef struct {
-    uint64_t jobs_submitted, jobs_done, passes, secondary_rays, kernel_launches, used_bytes;
-    double busy_ms;            /* wall time of the passes (device work + output copies) */
+    uint64_t jobs_submitted, jobs_done;
+    uint64_t passes;           /* iterations of the rolling wavefront (one bounce step of every active job) */
+    uint64_t secondary_rays, kernel_launches, used_bytes;
+    double busy_ms;            /* host time spent enqueueing iterations (up to four run ahead of the GPU) */
     uint32_t queued, active;
 } cr_server_stats;
 
@@ -396,7 +402,8 @@ cr_status cr_server_poll(cr_server* server, uint64_t job_id, cr_job_stats* stats
 /* As poll, but waits up to timeout_ms; CR_ERR_TIMEOUT if the job is still running. */
 cr_status cr_server_wait(cr_server* server, uint64_t job_id, uint32_t timeout_ms, cr_job_stats* stats);
 cr_status cr_server_get_stats(cr_server* server, cr_server_stats* stats);
-/* Stop the loop (jobs still queued are dropped) and free the server's memory. */
+/* Stop the loop (jobs not yet completed are dropped: their outputs are undefined) and free
+ * the server's memory. */
 cr_status cr_server_destroy(cr_server* server);
 
 /* ---------------------------------------------------------------------------------- */

@@ -589,6 +589,34 @@ cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h) {
 }
 
 // Build the per-pass job tables of a set of jobs that share the tile shape and K.
+// The device entry of sample `sample` of a job (tile_base, slot_tile and px_base are the
+// caller's: they place the job in a pass and its buffers).
+JobDev job_dev(const cr_job& j, const PlanOpts& po, uint32_t scene_idx, uint32_t sample) {
+    JobDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.cam = make_camera(j.camera);
+    d.tiles_x = (j.camera.width + po.tile_w - 1) / po.tile_w;
+    d.scene = scene_idx;
+    d.frame = j.frame_base + sample;
+    d.max_bounces = j.max_bounces;
+    d.reuse_mask = 0;
+    d.world_mask = 0;
+    for (uint32_t b = 1; b <= j.max_bounces; ++b)
+        if (j.reuse_depth == 0 || b <= j.reuse_depth) {
+            if (j.mode == CR_DIRECTION_REUSE) d.reuse_mask |= 1u << b;
+            if (j.mode == CR_WORLD_REUSE) d.world_mask |= 1u << b;
+        }
+    d.interleave = po.interleave ? 1u : 0u;
+    d.nee = (j.flags & CR_JOB_NEE) ? ((j.flags & CR_JOB_NEE_SHARED) ? 2u : 1u) : 0u;
+    d.hybrid_donor = (j.flags & CR_JOB_HYBRID_DONOR) ? 1u : 0u;
+    d.seed = j.seed;
+    d.out = j.out_rgb;
+    d.inv_spp = 1.0f / (float)j.spp;
+    d.sample_flags = (sample == 0 ? 1u : 0u) | (sample + 1 == j.spp ? 2u : 0u);
+    d.diffuse_rough = j.diffuse_roughness;
+    return d;
+}
+
 cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, RenderPlan& plan) {
     if (n_jobs == 0 || n_jobs > 65535) return fail(CR_ERR_INVALID_ARG, "n_jobs %u not in [1, 65535]", n_jobs);
     const uint32_t m = po.tile_w * po.tile_h;
@@ -646,32 +674,12 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
         for (uint32_t i = 0; i < n_jobs; ++i) {
             const cr_job& j = jobs[i];
             if (j.spp <= p) continue;
-            JobDev d;
-            std::memset(&d, 0, sizeof(d));
-            d.cam = make_camera(j.camera);
-            d.tiles_x = (j.camera.width + po.tile_w - 1) / po.tile_w;
+            JobDev d = job_dev(j, po, scene_idx[i], p);
             const uint32_t tiles_y = (j.camera.height + po.tile_h - 1) / po.tile_h;
             d.tile_base = tiles;
+            d.slot_tile = tiles;
             d.px_base = pxb[i];
-            d.scene = scene_idx[i];
-            d.frame = j.frame_base + p;
-            d.max_bounces = j.max_bounces;
-            d.reuse_mask = 0;
-            d.world_mask = 0;
-            for (uint32_t b = 1; b <= j.max_bounces; ++b)
-                if (j.reuse_depth == 0 || b <= j.reuse_depth) {
-                    if (j.mode == CR_DIRECTION_REUSE) d.reuse_mask |= 1u << b;
-                    if (j.mode == CR_WORLD_REUSE) d.world_mask |= 1u << b;
-                }
-            d.interleave = po.interleave ? 1u : 0u;
-            d.nee = (j.flags & CR_JOB_NEE) ? ((j.flags & CR_JOB_NEE_SHARED) ? 2u : 1u) : 0u;
-            d.hybrid_donor = (j.flags & CR_JOB_HYBRID_DONOR) ? 1u : 0u;
             if (d.nee) plan.nee = true;
-            d.seed = j.seed;
-            d.out = j.out_rgb;
-            d.inv_spp = 1.0f / (float)j.spp;
-            d.sample_flags = (p == 0 ? 1u : 0u) | (p + 1 == j.spp ? 2u : 0u);
-            d.diffuse_rough = j.diffuse_roughness;
             uint64_t job_tiles = (uint64_t)d.tiles_x * tiles_y;
             if (po.tile_end != 0) {
                 d.tile_first = po.tile_begin;

@@ -120,6 +120,11 @@ struct JobDev {
     uint32_t sample_flags; // bit 0: this pass is the job's first sample, bit 1: its last
     float diffuse_rough;   // GGX of at least this roughness is in the diffuse class (0: off)
     uint32_t tile_first;   // the job's first rendered tile of its image tiling (a tile range)
+    // rolling wavefront (the server): each job advances on its own.  step = the job's bounce
+    // at this iteration (0: ray generation, 1..B: shade + spawn, B + 1: last shade + sum);
+    // slot_tile = first tile of the job's slot range (slot = (slot_tile + t) m + i)
+    uint32_t step;
+    uint32_t slot_tile;
 };
 
 // Launch-uniform description of a pass.
@@ -135,6 +140,16 @@ struct PassArgs {
     // bit 0: a job's first sample writes its pixel sums without reading them (the buffer is
     // not cleared first); bit 1: its last sample writes the output instead of the sums
     uint32_t accum_mode = 0;
+    // rolling wavefront: every kernel takes a slot's bounce from its job (JobDev::step), and
+    // ray generation / the final sum run over launch lists: entry e covers job launch_job[e]
+    // from unit launch_prefix[e] (tiles for ray generation, slots for the sum) on
+    bool rolling = false;
+    const uint32_t* launch_job = nullptr;
+    const uint32_t* launch_prefix = nullptr;
+    uint32_t n_launch = 0;
+    uint32_t* queue_counts = nullptr;   // rolling ray generation: appends (rays, groups) here
+    int32_t* ray_queue = nullptr;       //   ... its slots to this queue
+    int32_t* group_queue_out = nullptr; //   ... and its groups to this one
 };
 
 // Per-call launch statistics.
@@ -264,6 +279,14 @@ void launch_rays_from_user(const float* rays, const int32_t* skip, uint32_t n, f
                            cudaStream_t st, LaunchCount& lc);
 // End of a pass (bounce B + 1): the environment or emission where each live path's last ray
 // ended, then every slot's radiance added to its pixel.
+// Rolling wavefront (the server): the stages over jobs at different bounces.  parity selects
+// the double-buffered group queue read at this iteration (the other one is appended to).
+void launch_raygen_rolling(const PassArgs& p, PathBuffers& b, uint32_t n_tiles, cudaStream_t st, LaunchCount& lc);
+void launch_shade_rolling(const PassArgs& p, PathBuffers& b, uint32_t parity, uint32_t n_groups_max,
+                          cudaStream_t st, LaunchCount& lc);
+void launch_shadow_rolling(const PassArgs& p, PathBuffers& b, uint32_t parity, uint32_t n_groups_max, bool bvh8,
+                           cudaStream_t st, LaunchCount& lc);
+void launch_finish_rolling(const PassArgs& p, PathBuffers& b, uint32_t n_slots, cudaStream_t st, LaunchCount& lc);
 void launch_finish_accumulate(const PassArgs& p, PathBuffers& b, const cr_debug* dbg, cudaStream_t st,
                               LaunchCount& lc);
 // out[job] = accum / spp for every job of the table (all pixels of all jobs, one launch).
@@ -349,6 +372,7 @@ struct StageTimes {
     double trace_shadow = 0;
 };
 cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, RenderPlan& plan);
+JobDev job_dev(const cr_job& j, const PlanOpts& po, uint32_t scene_idx, uint32_t sample);
 // CR_OK unless the queues of the run whose counts words these are overflowed (never expected)
 cr_status queue_status(const uint64_t* host_counts);
 cr_status check_job(const cr_job& j, uint32_t tile_w, uint32_t tile_h);

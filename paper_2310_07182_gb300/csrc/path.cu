@@ -59,6 +59,32 @@ __device__ __forceinline__ V3 camera_dir(const CamBasis& c, uint32_t px, uint32_
     return normalize3(d);
 }
 
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? s_warp[lane] : 0u;
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        if (lane < nw) s_warp[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t nw = blockDim.x >> 5;
+    total = s_warp[nw - 1];
+    const uint32_t excl = x - v + (w > 0 ? s_warp[w - 1] : 0u);
+    __syncthreads();
+    return excl;
+}
+
 // Job of a pass tile: the last job whose first tile is <= tile (jobs are in tile order).
 __device__ __forceinline__ uint32_t job_of_tile(const JobDev* jobs, uint32_t n_jobs, uint32_t tile) {
     uint32_t lo = 0, hi = n_jobs;
@@ -70,57 +96,104 @@ __device__ __forceinline__ uint32_t job_of_tile(const JobDev* jobs, uint32_t n_j
     return lo;
 }
 
+// Entry of a rolling launch list covering unit u (the last entry whose prefix is <= u).
+__device__ __forceinline__ uint32_t launch_entry(const uint32_t* prefix, uint32_t n, uint32_t u) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // One block covers blockDim / m whole tiles: every thread finds sigma of its pixel, the
 // inverse map is built in shared memory, then thread j writes slot j of its tile so the
 // slot arrays are written contiguously.
 // primary_queue (optional): entry tile * m + i = the slot of the tile's i-th pixel, so that the
 // primary trace can visit a tile's pixels in row-major order (compact pixel blocks per warp).
+// Rolling wavefront: the launch covers the tiles of the jobs that start a sample (launch
+// lists), their slots lie in each job's own slot range, and the block appends its live slots
+// to the ray queue and its groups with a live member to the next group queue.
 __global__ void k_raygen(PassArgs p, int32_t* __restrict__ pixel, uint16_t* __restrict__ slot_job,
                          uint16_t* __restrict__ slot_scene, float4* __restrict__ ray_o, float4* __restrict__ ray_d,
                          float4* __restrict__ beta, float4* __restrict__ radiance, uint8_t* __restrict__ alive,
                          int32_t* __restrict__ primary_queue, uint32_t* __restrict__ queue_counts) {
     extern __shared__ uint16_t inv[];
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_base[2];
     // the shade kernels append to the per-bounce queue counters: zero them for this pass
-    if (blockIdx.x == 0 && threadIdx.x < kQueueCountWords) queue_counts[threadIdx.x] = 0u;
+    if (!p.rolling && blockIdx.x == 0 && threadIdx.x < kQueueCountWords) queue_counts[threadIdx.x] = 0;
     const uint32_t m = p.m;
     const uint32_t tiles_per_block = blockDim.x / m;
     const uint32_t tl = threadIdx.x / m, j = threadIdx.x % m;
     const uint32_t tile = blockIdx.x * tiles_per_block + tl;
     const bool in = tl < tiles_per_block && tile < p.n_tiles;
-    uint32_t jid = 0;
+    uint32_t jid = 0, t = 0, slot_tile = tile;
     if (in) {
-        jid = job_of_tile(p.jobs, p.n_jobs, tile);
+        if (p.rolling) {
+            const uint32_t e = launch_entry(p.launch_prefix, p.n_launch, tile);
+            jid = p.launch_job[e];
+            t = tile - p.launch_prefix[e];
+            slot_tile = p.jobs[jid].slot_tile + t;
+        } else {
+            jid = job_of_tile(p.jobs, p.n_jobs, tile);
+            t = tile - p.jobs[jid].tile_base;
+        }
         const JobDev& J = p.jobs[jid];
-        const Lcg L = tile_lcg(J.seed, tile - J.tile_base + J.tile_first, J.frame, m, J.interleave);
+        const Lcg L = tile_lcg(J.seed, t + J.tile_first, J.frame, m, J.interleave);
         const uint32_t s = sigma_of(L, j, m, J.interleave);
         inv[tl * m + s] = (uint16_t)j;
-        if (primary_queue) primary_queue[tile * m + j] = (int32_t)(tile * m + s);
+        if (primary_queue && !p.rolling) primary_queue[tile * m + j] = (int32_t)(tile * m + s);
     }
     __syncthreads();
-    if (!in) return;
-    const JobDev& J = p.jobs[jid];
-    const uint32_t t = tile - J.tile_base + J.tile_first;
-    const uint32_t i = inv[tl * m + j];
-    const uint32_t tx = t % J.tiles_x, ty = t / J.tiles_x;
-    const uint32_t px = tx * p.tile_w + i % p.tile_w, py = ty * p.tile_h + i / p.tile_w;
-    const uint32_t slot = tile * m + j;
-    slot_job[slot] = (uint16_t)jid;
-    slot_scene[slot] = (uint16_t)J.scene;
-    if (px < J.cam.width && py < J.cam.height) {
-        const uint32_t pix = py * J.cam.width + px;
-        const uint4 h = philox_seed(J.seed, pix, J.frame, 0u, kTagCamera);
-        const V3 d = camera_dir(J.cam, px, py, unit24(h.x), unit24(h.y));
-        pixel[slot] = (int32_t)pix;
-        ray_o[slot] = make_float4(J.cam.pos[0], J.cam.pos[1], J.cam.pos[2], __int_as_float(-1));
-        ray_d[slot] = make_float4(d.x, d.y, d.z, INFINITY);
-        beta[slot] = make_float4(1.0f, 1.0f, 1.0f, 0.0f); // w: direction density, 0 for camera rays
-        radiance[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        alive[slot] = 1;
-    } else {
-        pixel[slot] = -1;
-        ray_d[slot] = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-        alive[slot] = 0;
+    bool live = false;
+    uint32_t slot = 0;
+    if (in) {
+        const JobDev& J = p.jobs[jid];
+        const uint32_t tt = t + J.tile_first;
+        const uint32_t i = inv[tl * m + j];
+        const uint32_t tx = tt % J.tiles_x, ty = tt / J.tiles_x;
+        const uint32_t px = tx * p.tile_w + i % p.tile_w, py = ty * p.tile_h + i / p.tile_w;
+        slot = slot_tile * m + j;
+        slot_job[slot] = (uint16_t)jid;
+        slot_scene[slot] = (uint16_t)J.scene;
+        if (px < J.cam.width && py < J.cam.height) {
+            const uint32_t pix = py * J.cam.width + px;
+            const uint4 h = philox_seed(J.seed, pix, J.frame, 0u, kTagCamera);
+            const V3 d = camera_dir(J.cam, px, py, unit24(h.x), unit24(h.y));
+            pixel[slot] = (int32_t)pix;
+            ray_o[slot] = make_float4(J.cam.pos[0], J.cam.pos[1], J.cam.pos[2], __int_as_float(-1));
+            ray_d[slot] = make_float4(d.x, d.y, d.z, INFINITY);
+            beta[slot] = make_float4(1.0f, 1.0f, 1.0f, 0.0f); // w: direction density, 0 for camera rays
+            radiance[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            alive[slot] = 1;
+            live = true;
+        } else {
+            pixel[slot] = -1;
+            ray_d[slot] = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+            alive[slot] = 0;
+        }
     }
+    if (!p.rolling) return;
+    // rolling: append the live slots (this iteration's trace) and the groups with a live member
+    // (the next iteration's shade); a group is K consecutive slots, i.e. K consecutive threads
+    uint32_t* grp_live = reinterpret_cast<uint32_t*>(inv + ((blockDim.x + 1) & ~1u));
+    if (threadIdx.x < blockDim.x / p.k) grp_live[threadIdx.x] = 0u;
+    __syncthreads();
+    if (live) grp_live[threadIdx.x / p.k] = 1u;
+    __syncthreads();
+    const bool head = in && j % p.k == 0 && grp_live[threadIdx.x / p.k] != 0u;
+    uint32_t tot_r, tot_g;
+    const uint32_t rr = block_excl_scan(live ? 1u : 0u, s_warp, tot_r);
+    const uint32_t rg = block_excl_scan(head ? 1u : 0u, s_warp, tot_g);
+    if (threadIdx.x == 0) {
+        s_base[0] = tot_r ? atomicAdd(&p.queue_counts[0], tot_r) : 0u;
+        s_base[1] = tot_g ? atomicAdd(&p.queue_counts[1], tot_g) : 0u;
+    }
+    __syncthreads();
+    if (live) p.ray_queue[s_base[0] + rr] = (int32_t)slot;
+    if (head) p.group_queue_out[s_base[1] + rg] = (int32_t)(slot / p.k);
 }
 
 __global__ void k_groups(CamBasis cam, uint32_t tile_w, uint32_t tile_h, uint32_t interleave, uint64_t seed,
@@ -184,6 +257,7 @@ struct Member {
     bool front;      // the incoming ray met the triangle's front face
     uint64_t seed;
     uint32_t frame;
+    uint32_t bounce; // this shading step's bounce (the launch's, or the job's own when rolling)
     int cls;
     V3 n, t, b, wo;
     float albedo[3];
@@ -298,7 +372,7 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
     mb.albedo[1] = m0.z;
     mb.albedo[2] = m0.w;
     // the member's own BSDF sample, drawn from its pixel's stream
-    const uint4 r = philox_seed(mb.seed, (uint32_t)mb.pix, mb.frame, p.bounce, kTagBsdf);
+    const uint4 r = philox_seed(mb.seed, (uint32_t)mb.pix, mb.frame, mb.bounce, kTagBsdf);
     const float u1 = unit24(r.x), u2 = unit24(r.y);
     if (type == kMatLambert) {
         mb.wl = sample_cosine(u1, u2);
@@ -397,7 +471,7 @@ __device__ __forceinline__ void next_event(const ShadeArgs& a, const PassArgs& p
     if (mb.alive && mb.nee && mb.type != kMatMirror && mb.type != kMatDielectric) {
         const SceneDev& sc = a.scenes[mb.scene];
         if (sc.n_lights > 0) {
-            const uint4 r = philox_seed(mb.seed, (uint32_t)light_pix, mb.frame, p.bounce, kTagLight);
+            const uint4 r = philox_seed(mb.seed, (uint32_t)light_pix, mb.frame, mb.bounce, kTagLight);
             const float u0 = unit24(r.x), u1 = unit24(r.y), u2 = unit24(r.z);
             // the first emitter whose running area exceeds u0 * A (the last if none)
             const float x = fm(u0, sc.light_total);
@@ -576,6 +650,7 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
     float4 bt = make_float4(0, 0, 0, 0);
     float3 L = make_float3(0, 0, 0);
     mb.final_pass = true;
+    mb.bounce = p.bounce;
     mb.reuse = false;
     mb.world = false;
     mb.nee = false;
@@ -600,9 +675,10 @@ __global__ void k_shade_warp(ShadeArgs a, PassArgs p) {
         const JobDev* Jp = nullptr;
         if (mb.pix >= 0) { // every valid slot knows whether its job is past its last bounce
             Jp = &a.jobs[jid];
-            mb.final_pass = p.bounce > Jp->max_bounces;
-            mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
-            mb.world = (Jp->world_mask >> p.bounce) & 1u;
+            mb.bounce = p.rolling ? Jp->step : p.bounce;
+            mb.final_pass = mb.bounce > Jp->max_bounces;
+            mb.reuse = (Jp->reuse_mask >> mb.bounce) & 1u;
+            mb.world = (Jp->world_mask >> mb.bounce) & 1u;
             mb.nee = Jp->nee != 0;
             mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
@@ -722,6 +798,7 @@ __global__ void __launch_bounds__(256, CR_SHADE_BLOCK_MIN_BLOCKS) k_shade_block(
     float4 bt = make_float4(0, 0, 0, 0);
     float3 L = make_float3(0, 0, 0);
     mb.final_pass = true;
+    mb.bounce = p.bounce;
     mb.reuse = false;
     mb.world = false;
     mb.nee = false;
@@ -746,9 +823,10 @@ __global__ void __launch_bounds__(256, CR_SHADE_BLOCK_MIN_BLOCKS) k_shade_block(
         const JobDev* Jp = nullptr;
         if (mb.pix >= 0) { // every valid slot knows whether its job is past its last bounce
             Jp = &a.jobs[jid];
-            mb.final_pass = p.bounce > Jp->max_bounces;
-            mb.reuse = (Jp->reuse_mask >> p.bounce) & 1u;
-            mb.world = (Jp->world_mask >> p.bounce) & 1u;
+            mb.bounce = p.rolling ? Jp->step : p.bounce;
+            mb.final_pass = mb.bounce > Jp->max_bounces;
+            mb.reuse = (Jp->reuse_mask >> mb.bounce) & 1u;
+            mb.world = (Jp->world_mask >> mb.bounce) & 1u;
             mb.nee = Jp->nee != 0;
             mb.nee_shared = Jp->nee == 2u;
             mb.hdonor = Jp->hybrid_donor != 0;
@@ -880,31 +958,6 @@ __device__ __forceinline__ void position_info(const int32_t* gq_in, uint32_t n_g
     }
 }
 
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
-    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    uint32_t x = v;
-    for (uint32_t off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        const uint32_t nw = blockDim.x >> 5;
-        uint32_t s = lane < nw ? s_warp[lane] : 0u;
-        for (uint32_t off = 1; off < 32; off <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, s, off);
-            if (lane >= off) s += y;
-        }
-        if (lane < nw) s_warp[lane] = s;
-    }
-    __syncthreads();
-    const uint32_t nw = blockDim.x >> 5;
-    total = s_warp[nw - 1];
-    const uint32_t excl = x - v + (w > 0 ? s_warp[w - 1] : 0u);
-    __syncthreads();
-    return excl;
-}
 
 __global__ void __launch_bounds__(kCompactBlock) k_compact_count(const int32_t* gq_in, const uint32_t* n_groups_ptr,
                                                                  uint32_t n_groups_max, uint32_t K,
@@ -1358,8 +1411,13 @@ __global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixe
                                     const float4* __restrict__ ray_d, const float4* __restrict__ beta,
                                     const float4* __restrict__ radiance, uint32_t n_slots,
                                     float4* __restrict__ accum, cr_debug dbg, uint32_t dbg_npx) {
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_slots) return;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_slots) return;
+    uint32_t s = u;
+    if (p.rolling) { // the slots of the jobs that end a sample now, from the launch lists
+        const uint32_t e = launch_entry(p.launch_prefix, p.n_launch, u);
+        s = p.jobs[p.launch_job[e]].slot_tile * p.m + (u - p.launch_prefix[e]);
+    }
     const int pix = pixel[s];
     if (pix < 0) return;
     const JobDev& J = p.jobs[slot_job[s]];
@@ -1556,6 +1614,65 @@ void launch_shade(const PassArgs& p, PathBuffers& b, bool first, bool compact, c
     } else {
         k_shade_block<<<(n_pos + 255) / 256, 256, 0, st>>>(a, p);
     }
+    lc.n++;
+}
+
+// Rolling wavefront.  Queue words: pair q = counts + 8 + 2 q holds (rays, groups) appended
+// for the iteration that reads group queue q; the caller zeroes the pair an iteration appends
+// to before its first launch.
+void launch_raygen_rolling(const PassArgs& p, PathBuffers& b, uint32_t n_tiles, cudaStream_t st, LaunchCount& lc) {
+    if (!n_tiles) return;
+    PassArgs q = p;
+    q.n_tiles = n_tiles;
+    const uint32_t block = p.m > 256 ? p.m : 256;
+    const uint32_t tiles_per_block = block / p.m;
+    const uint32_t grid = (n_tiles + tiles_per_block - 1) / tiles_per_block;
+    // shared memory: the inverse shuffle (2 B per thread), then one live flag per group
+    k_raygen<<<grid, block, block * (sizeof(uint16_t) + sizeof(uint32_t)) + 4, st>>>(
+        q, b.pixel, b.slot_job, b.slot_scene, b.ray_o, b.ray_d, b.beta, b.radiance, b.alive, nullptr, nullptr);
+    lc.n++;
+}
+
+static ShadeArgs shade_args_rolling(const PassArgs& p, PathBuffers& b, uint32_t parity, uint32_t n_groups_max) {
+    ShadeArgs a = shade_args(p, b, false, true, nullptr);
+    a.group_queue = b.group_queue + (size_t)parity * b.n_groups;
+    a.group_count = b.counts + 8 + 2 * parity + 1;
+    a.n_groups_max = n_groups_max;
+    a.group_queue_out = b.group_queue + (size_t)(parity ^ 1u) * b.n_groups;
+    a.queue_counts = b.counts + 8 + 2 * (parity ^ 1u);
+    a.rays_queued = reinterpret_cast<unsigned long long*>(b.counts + kStatWord) + 1;
+    a.ray_cap = b.n_groups * p.k;
+    a.group_cap = b.n_groups;
+    return a;
+}
+
+void launch_shade_rolling(const PassArgs& p, PathBuffers& b, uint32_t parity, uint32_t n_groups_max,
+                          cudaStream_t st, LaunchCount& lc) {
+    if (!n_groups_max) return;
+    ShadeArgs a = shade_args_rolling(p, b, parity, n_groups_max);
+    const uint32_t n_pos = n_groups_max * p.k;
+    if (p.k <= 32) {
+        k_shade_warp<<<(n_pos + CR_SHADE_WARP_BLOCK - 1) / CR_SHADE_WARP_BLOCK, CR_SHADE_WARP_BLOCK, 0, st>>>(a, p);
+    } else {
+        k_shade_block<<<(n_pos + 255) / 256, 256, 0, st>>>(a, p);
+    }
+    lc.n++;
+}
+
+void launch_shadow_rolling(const PassArgs& p, PathBuffers& b, uint32_t parity, uint32_t n_groups_max, bool bvh8,
+                           cudaStream_t st, LaunchCount& lc) {
+    if (!p.nee || !b.shadow_d || !n_groups_max) return;
+    const ShadeArgs a = shade_args_rolling(p, b, parity, n_groups_max);
+    launch_shadow_rays(p.scenes, b.slot_scene, b.shadow_o, b.shadow_d, b.shadow_c, a.group_queue, a.group_count,
+                       n_groups_max, p.k, b.radiance, reinterpret_cast<unsigned long long*>(b.counts + kShadowWord),
+                       bvh8, st, lc);
+}
+
+void launch_finish_rolling(const PassArgs& p, PathBuffers& b, uint32_t n_slots, cudaStream_t st, LaunchCount& lc) {
+    if (!n_slots) return;
+    k_finish_accumulate<<<(n_slots + 255) / 256, 256, 0, st>>>(p, b.pixel, b.slot_job, b.alive, b.hit, b.ray_o,
+                                                               b.ray_d, b.beta, b.radiance, n_slots, b.accum,
+                                                               cr_debug{}, 0);
     lc.n++;
 }
 

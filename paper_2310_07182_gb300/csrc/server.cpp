@@ -1,12 +1,17 @@
-// server.cpp -- render request loop with continuous batching.
+// server.cpp -- render request loop with continuous batching at bounce granularity.
 //
-// One host thread owns the device work.  Each iteration renders ONE sample pass of every
-// active job as a single merged wavefront (one launch per stage per bounce over the slots
-// of all jobs).  Between passes it retires jobs whose last sample is done (output, copy to
-// the host if needed, completion time) and admits queued jobs while their device
-// footprint fits the budget, so requests that arrive while others are on the GPU join the
-// next pass.  Accumulations live in one arena with a first-fit allocator, so jobs keep
-// their partial sums while others come and go.
+// One host thread owns the device work and runs a rolling wavefront: every iteration is one
+// launch per stage over the slots of all admitted jobs, whatever bounce each job is at.
+// An iteration shades (each job's own step; the step after a job's last bounce only adds
+// the end radiance), sums the samples of jobs that end one, generates the rays of jobs that
+// start one, and traces every queued ray.  A job therefore joins at the next bounce launch
+// after it is admitted, and leaves (its buffers free for others) right after its last sum.
+// Each sample of a job in flight is a "run" with its own entry in the device job table
+// (stable index, so slots keep pointing at it), which is how a job can end sample s and
+// start sample s + 1 in the same iteration.  Admission is by device footprint: path-state
+// slots (whole tiles), accumulation pixels and, for host outputs, staging pixels, each from
+// a first-fit arena allocated once, so the loop allocates nothing.  The host enqueues up to
+// kDepth iterations ahead of the GPU; events mark the iterations in which jobs complete.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,7 +20,9 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -26,25 +33,38 @@ namespace {
 
 // path state per slot, with the 48 bytes of shadow-ray records (jobs may use CR_JOB_NEE)
 constexpr uint64_t kSlotBytes = 4 + 2 + 2 + 16 + 16 + 8 + 16 + 16 + 1 + 4 + 8 + 8 + 8 + 48;
+constexpr uint32_t kMaxRuns = 16384;   // device job-table entries (runs in flight)
+constexpr uint32_t kMaxScenes = 256;   // distinct scenes the server may hold in its table
+constexpr uint32_t kListWords = 4 * kMaxRuns; // launch lists: finish (job, prefix), raygen (job, prefix)
+constexpr uint32_t kDepth = 4;        // iterations the host may enqueue ahead of the GPU (buffer sets)
 
 struct SJob {
     uint64_t id = 0;
     cr_job job;
     bool host_out = false;
     float* d_out = nullptr;   // output on the device (user buffer or staging)
-    uint32_t npx = 0, slots = 0;
+    uint32_t npx = 0, tiles = 0, slots = 0;
     uint64_t footprint = 0;
     uint32_t px_base = 0;     // in the accumulation arena
-    uint32_t done = 0;        // samples accumulated
+    uint32_t slot_tile = 0;   // first tile of its slot range
+    uint32_t stg_at = 0;      // first pixel of its staging range (host outputs)
+    uint32_t scene_idx = 0;
+    uint32_t done = 0;        // samples summed
+    uint32_t step = 0;        // bounce step of the current sample at the next iteration
+    uint32_t run = 0;         // job-table entry of the current sample
     double t_submit = 0, t_admit = -1, t_done = -1;
-    int state = 0;            // 0 queued, 1 active, 2 done, 3 failed
+    int state = 0;            // 0 queued, 1 active, 2 done, 3 failed, 4 waiting for its output
     cr_status status = CR_OK;
 };
 
-struct Arena { // first-fit ranges of float4 pixels
+struct Arena { // first-fit ranges of units
     std::vector<std::pair<uint32_t, uint32_t>> free_; // (start, length), sorted by start
     void init(uint32_t n) { free_.assign(1, {0u, n}); }
     bool alloc(uint32_t n, uint32_t& at) {
+        if (n == 0) {
+            at = 0;
+            return true;
+        }
         for (size_t i = 0; i < free_.size(); ++i)
             if (free_[i].second >= n) {
                 at = free_[i].first;
@@ -56,6 +76,7 @@ struct Arena { // first-fit ranges of float4 pixels
         return false;
     }
     void release(uint32_t at, uint32_t n) {
+        if (n == 0) return;
         auto it = std::lower_bound(free_.begin(), free_.end(), std::make_pair(at, 0u));
         it = free_.insert(it, {at, n});
         size_t i = it - free_.begin();
@@ -81,20 +102,37 @@ struct cr_server {
     ExecOpts eo;
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr; // job-table uploads, off the render stream
     Workspace ws;
-    Plan dev;
-    float4* arena = nullptr;
+    // device job tables and launch lists, kDepth sets used round robin by the iterations in
+    // flight, and their pinned host sources; the scene table
+    JobDev* d_table[kDepth] = {};
+    uint32_t* d_lists[kDepth] = {};
+    JobDev* h_table[kDepth] = {};
+    uint32_t* h_lists[kDepth] = {};
+    SceneDev* d_scenes = nullptr;
+    uint64_t* h_counts = nullptr; // pinned, per set: (rays traced at bounces >= 1, queue error word)
+    cudaEvent_t ev_iter[kDepth] = {};
+    cudaEvent_t ev_copied[kDepth] = {};
+    bool ev_used[kDepth] = {};
+    std::deque<std::pair<cudaEvent_t, std::vector<uint64_t>>> pending; // completion events
+    std::vector<cudaEvent_t> event_pool;
+    float4* arena = nullptr;  // accumulation (16 B per pixel)
     uint32_t arena_px = 0;
-    Arena alloc;
-    uint32_t slots_cap = 0, slots_used = 0;
+    float* staging = nullptr; // host-output staging (12 B per pixel)
+    uint32_t staging_px = 0;
+    Arena alloc, stg_alloc, tile_alloc;
+    uint32_t tiles_cap = 0;
+    std::vector<uint32_t> free_runs;
+    std::vector<const cr_scene*> scene_list;
+    bool scenes_dirty = false;
     uint64_t budget = 0, used = 0;
-    uint64_t staging_cap = 0, staging_used = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
     std::map<uint64_t, SJob> jobs;
     std::vector<uint64_t> active;
-    uint64_t next_id = 1;
+    uint64_t next_id = 1, iter = 0;
     bool stop = false;
     cr_status fatal = CR_OK;
     std::string fatal_msg;
@@ -106,148 +144,355 @@ struct cr_server {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     void loop();
-    bool admit_locked();
+    void admit_locked();
+    void poll_completions(bool wait_oldest);
+    void release_job_locked(SJob& j);
+    bool iterate(LaunchCount& lc);
 };
 
-// Admit queued jobs (in arrival order, later ones may backfill) while they fit.  Returns
-// true if anything is active.  Called with the lock held.
-bool cr_server::admit_locked() {
+// Admit queued jobs (in arrival order, later ones may backfill) while their slots,
+// accumulation and staging ranges and a job-table entry fit.  Called with the lock held.
+void cr_server::admit_locked() {
     for (auto it = queue.begin(); it != queue.end();) {
         SJob& j = jobs[*it];
-        const uint64_t stg = j.host_out ? 12ull * j.npx : 0;
-        const bool fits = slots_used + j.slots <= slots_cap && staging_used + stg <= staging_cap;
-        uint32_t at = 0;
-        if (fits && alloc.alloc(j.npx, at)) {
-            if (j.host_out) {
-                if (cudaMalloc(&j.d_out, 12ull * j.npx) != cudaSuccess) {
-                    cudaGetLastError();
-                    alloc.release(at, j.npx);
-                    ++it;
-                    continue; // retry when memory frees up
+        uint32_t scene_idx = 0;
+        while (scene_idx < scene_list.size() && scene_list[scene_idx] != j.job.scene) ++scene_idx;
+        if (scene_idx == scene_list.size() && scene_list.size() >= kMaxScenes) {
+            ++it; // the scene table is full: wait until it can be rebuilt
+            continue;
+        }
+        uint32_t st = 0, px = 0, sg = 0;
+        // at most half the job table is held by active jobs: a job that ends a sample takes a
+        // second entry for its next one in the same iteration
+        if (active.size() >= kMaxRuns / 2 || !tile_alloc.alloc(j.tiles, st)) {
+            ++it;
+            continue;
+        }
+        if (!alloc.alloc(j.npx, px)) {
+            tile_alloc.release(st, j.tiles);
+            ++it;
+            continue;
+        }
+        if (j.host_out && !stg_alloc.alloc(j.npx, sg)) {
+            tile_alloc.release(st, j.tiles);
+            alloc.release(px, j.npx);
+            ++it;
+            continue;
+        }
+        if (scene_idx == scene_list.size()) {
+            scene_list.push_back(j.job.scene);
+            scenes_dirty = true;
+        }
+        j.scene_idx = scene_idx;
+        j.slot_tile = st;
+        j.px_base = px;
+        j.stg_at = sg;
+        if (j.host_out) j.d_out = staging + 3ull * sg;
+        j.run = free_runs.back();
+        free_runs.pop_back();
+        j.step = 0;
+        j.done = 0;
+        j.state = 1;
+        j.t_admit = now_ms();
+        used += j.footprint;
+        active.push_back(j.id);
+        it = queue.erase(it);
+    }
+}
+
+// Free a job's slot, accumulation and staging ranges.  Later iterations on the stream run
+// after its last sum (and its output copy), so the ranges can go to other jobs at once.
+void cr_server::release_job_locked(SJob& j) {
+    tile_alloc.release(j.slot_tile, j.tiles);
+    alloc.release(j.px_base, j.npx);
+    if (j.host_out) stg_alloc.release(j.stg_at, j.npx);
+    used -= j.footprint;
+    free_runs.push_back(j.run);
+}
+
+// Mark the jobs of completed iterations done (their outputs are where the caller asked).
+void cr_server::poll_completions(bool wait_oldest) {
+    while (true) {
+        cudaEvent_t ev = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (pending.empty()) return;
+            ev = pending.front().first;
+        }
+        cudaError_t e = wait_oldest ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
+        wait_oldest = false;
+        if (e == cudaErrorNotReady) return;
+        std::vector<uint64_t> ids;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            ids = std::move(pending.front().second);
+            pending.pop_front();
+            event_pool.push_back(ev);
+            const double t = now_ms();
+            for (uint64_t id : ids) {
+                auto it = jobs.find(id);
+                if (it == jobs.end()) continue;
+                if (e == cudaSuccess) {
+                    it->second.state = 2;
+                } else {
+                    it->second.state = 3;
+                    it->second.status = CR_ERR_CUDA;
+                }
+                it->second.t_done = t;
+                stats.jobs_done++;
+            }
+            if (e != cudaSuccess && fatal == CR_OK) {
+                cudaGetLastError();
+                fatal = CR_ERR_CUDA;
+                fatal_msg = cudaGetErrorString(e);
+            }
+        }
+        cv_done.notify_all();
+    }
+}
+
+// One iteration of the rolling wavefront: shade (every job at its own step), sum the samples
+// that end, generate the rays of the samples that start, trace every queued ray.  Returns
+// false when no job is active.
+bool cr_server::iterate(LaunchCount& lc) {
+    const uint32_t par = (uint32_t)(iter & 1u);            // group queue read at this iteration
+    const uint32_t set = (uint32_t)(iter % kDepth);        // table, lists and counters of this iteration
+    if (ev_used[set]) cudaEventSynchronize(ev_iter[set]); // iteration iter - kDepth freed this set
+    const uint32_t m = po.tile_w * po.tile_h, K = po.k ? po.k : m;
+    JobDev* tab = h_table[set];
+    uint32_t* fin_job = h_lists[set];
+    uint32_t* fin_pre = fin_job + kMaxRuns;
+    uint32_t* st_job = fin_job + 2 * kMaxRuns;
+    uint32_t* st_pre = fin_job + 3 * kMaxRuns;
+    uint32_t n_fin = 0, n_start = 0, fin_slots = 0, start_tiles = 0, n_groups = 0, trace_max = 0, max_run = 0;
+    bool nee = false, sort = false, upload_scenes = false;
+    std::vector<SceneDev> scene_tab;
+    std::vector<uint64_t> completing, host_copies;
+    std::map<uint64_t, uint32_t> next_run;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (ev_used[set] && set == 0) { // what iteration iter - kDepth read back
+            stats.secondary_rays = std::max<uint64_t>(stats.secondary_rays, h_counts[0]);
+            const uint32_t err = (uint32_t)h_counts[1];
+            if (err != 0u && fatal == CR_OK) {
+                fatal = (err & 2u) ? CR_ERR_TIMEOUT : CR_ERR_CUDA;
+                fatal_msg = (err & 2u) ? "a ray-sort wait ran out" : "a ray or group queue overflowed";
+            }
+        }
+        if (fatal != CR_OK) { // fail what is left
+            for (uint64_t id : active) {
+                SJob& j = jobs[id];
+                j.state = 3;
+                j.status = fatal;
+                j.t_done = now_ms();
+                release_job_locked(j);
+            }
+            active.clear();
+            cv_done.notify_all();
+            return false;
+        }
+        if (active.empty()) return false;
+        if (scenes_dirty) {
+            for (const cr_scene* sc : scene_list) scene_tab.push_back(scene_entry(*dev_scene_of(sc), po.bvh8));
+            scenes_dirty = false;
+            upload_scenes = true;
+        }
+        for (uint64_t id : active) {
+            SJob& j = jobs[id];
+            const uint32_t B = j.job.max_bounces;
+            JobDev d = job_dev(j.job, po, j.scene_idx, j.done);
+            d.out = j.d_out;
+            d.px_base = j.px_base;
+            d.slot_tile = j.slot_tile;
+            d.step = j.step;
+            tab[j.run] = d;
+            max_run = std::max(max_run, j.run);
+            nee = nee || d.nee;
+            sort = sort || j.job.mode == CR_MORTON_SORT;
+            if (j.step >= 1) n_groups += j.slots / K; // its groups may be in the queue read now
+            if (j.step == 0) {
+                st_job[n_start] = j.run;
+                st_pre[n_start++] = start_tiles;
+                start_tiles += j.tiles;
+                trace_max += j.slots;
+            } else if (j.step <= B) {
+                trace_max += j.slots;
+            } else { // the sample ends here: its sum, and the next sample starts at once
+                fin_job[n_fin] = j.run;
+                fin_pre[n_fin++] = fin_slots;
+                fin_slots += j.slots;
+                if (j.done + 1 < j.job.spp) {
+                    const uint32_t nr = free_runs.back();
+                    free_runs.pop_back();
+                    JobDev d2 = job_dev(j.job, po, j.scene_idx, j.done + 1);
+                    d2.out = j.d_out;
+                    d2.px_base = j.px_base;
+                    d2.slot_tile = j.slot_tile;
+                    d2.step = 0;
+                    tab[nr] = d2;
+                    max_run = std::max(max_run, nr);
+                    st_job[n_start] = nr;
+                    st_pre[n_start++] = start_tiles;
+                    start_tiles += j.tiles;
+                    trace_max += j.slots;
+                    next_run[id] = nr;
+                } else {
+                    completing.push_back(id);
+                    if (j.host_out) host_copies.push_back(id);
                 }
             }
-            j.px_base = at;
-            j.state = 1;
-            j.t_admit = now_ms();
-            used += j.footprint;
-            slots_used += j.slots;
-            staging_used += stg;
-            cudaMemsetAsync(arena + at, 0, 16ull * j.npx, stream);
-            active.push_back(j.id);
-            it = queue.erase(it);
-        } else {
-            ++it;
         }
     }
-    return !active.empty();
+    PathBuffers& b = ws.pb;
+    b.n_groups = b.n_slots / K;
+    b.accum = arena;
+    // the uploads run on the copy stream (this set's device buffers were last read by
+    // iteration iter - kDepth, which has completed), overlapping the iterations in flight;
+    // the render stream waits for them before this iteration's first launch
+    cudaMemcpyAsync(d_table[set], tab, sizeof(JobDev) * (max_run + 1), cudaMemcpyHostToDevice, copy_stream);
+    if (n_fin) {
+        cudaMemcpyAsync(d_lists[set], fin_job, 4ull * n_fin, cudaMemcpyHostToDevice, copy_stream);
+        cudaMemcpyAsync(d_lists[set] + kMaxRuns, fin_pre, 4ull * n_fin, cudaMemcpyHostToDevice, copy_stream);
+    }
+    if (n_start) {
+        cudaMemcpyAsync(d_lists[set] + 2 * kMaxRuns, st_job, 4ull * n_start, cudaMemcpyHostToDevice, copy_stream);
+        cudaMemcpyAsync(d_lists[set] + 3 * kMaxRuns, st_pre, 4ull * n_start, cudaMemcpyHostToDevice, copy_stream);
+    }
+    cudaEventRecord(ev_copied[set], copy_stream);
+    cudaStreamWaitEvent(stream, ev_copied[set], 0);
+    if (upload_scenes) // append-only: entries in-flight iterations read do not change
+        cudaMemcpy(d_scenes, scene_tab.data(), sizeof(SceneDev) * scene_tab.size(), cudaMemcpyHostToDevice);
+    PassArgs P;
+    P.jobs = d_table[set];
+    P.n_jobs = max_run + 1;
+    P.scenes = d_scenes;
+    P.tile_w = po.tile_w;
+    P.tile_h = po.tile_h;
+    P.m = m;
+    P.k = K;
+    P.nee = nee;
+    P.rolling = true;
+    P.accum_mode = 3u;
+    uint32_t* qn = b.counts + 8 + 2 * (par ^ 1u); // (rays, groups) appended for the next iteration
+    cudaMemsetAsync(qn, 0, 8, stream);
+    launch_shade_rolling(P, b, par, n_groups, stream, lc);
+    launch_shadow_rolling(P, b, par, n_groups, po.bvh8, stream, lc);
+    if (n_fin) {
+        P.launch_job = d_lists[set];
+        P.launch_prefix = d_lists[set] + kMaxRuns;
+        P.n_launch = n_fin;
+        launch_finish_rolling(P, b, fin_slots, stream, lc);
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (uint64_t id : host_copies) {
+            SJob& j = jobs[id];
+            cudaMemcpyAsync(j.job.out_rgb, j.d_out, 12ull * j.npx, cudaMemcpyDeviceToHost, stream);
+        }
+    }
+    if (n_start) {
+        P.launch_job = d_lists[set] + 2 * kMaxRuns;
+        P.launch_prefix = d_lists[set] + 3 * kMaxRuns;
+        P.n_launch = n_start;
+        P.queue_counts = qn;
+        P.ray_queue = b.ray_queue;
+        P.group_queue_out = b.group_queue + (size_t)(par ^ 1u) * b.n_groups;
+        launch_raygen_rolling(P, b, start_tiles, stream, lc);
+    }
+    if (trace_max) {
+        TraceArgs ta;
+        ta.ray_o = b.ray_o;
+        ta.ray_d = b.ray_d;
+        ta.hit = b.hit;
+        ta.block = eo.block_secondary ? eo.block_secondary : eo.block;
+        ta.stack = eo.stack;
+        ta.bvh8 = po.bvh8;
+        ta.scenes = d_scenes;
+        ta.slot_scene = b.slot_scene;
+        ta.queue = b.ray_queue;
+        ta.queue_count = qn;
+        ta.n_max = trace_max;
+        if (sort) ta.queue = launch_morton_sort(P, b, par ^ 1u, eo.sort_key, stream, lc);
+        launch_trace(ta, stream, lc);
+    }
+    // the ray total and the error word, read back every kDepth-th iteration (the copies
+    // would otherwise sit between the kernels of consecutive iterations)
+    if (set == 0) {
+        cudaMemcpyAsync(&h_counts[0], reinterpret_cast<unsigned long long*>(b.counts + kStatWord) + 1, 8,
+                        cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(&h_counts[1], b.counts + kQueueErrWord, 4, cudaMemcpyDeviceToHost, stream);
+    }
+    cudaEventRecord(ev_iter[set], stream);
+    ev_used[set] = true;
+    cudaError_t e = cudaGetLastError();
+    std::lock_guard<std::mutex> lk(mu);
+    if (e != cudaSuccess && fatal == CR_OK) {
+        fatal = CR_ERR_CUDA;
+        fatal_msg = cudaGetErrorString(e);
+    }
+    if (!completing.empty()) {
+        cudaEvent_t ev = nullptr;
+        if (!event_pool.empty()) {
+            ev = event_pool.back();
+            event_pool.pop_back();
+        } else {
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        }
+        cudaEventRecord(ev, stream);
+        pending.push_back({ev, completing});
+    }
+    // advance every job by one bounce step
+    std::vector<uint64_t> keep;
+    for (uint64_t id : active) {
+        SJob& j = jobs[id];
+        if (j.step <= j.job.max_bounces) {
+            j.step++;
+            keep.push_back(id);
+            continue;
+        }
+        j.done++;
+        auto nr = next_run.find(id);
+        if (nr != next_run.end()) {
+            free_runs.push_back(j.run);
+            j.run = nr->second;
+            j.step = 1;
+            keep.push_back(id);
+        } else {
+            j.state = 4; // done on the device once its completion event has passed
+            release_job_locked(j);
+        }
+    }
+    active.swap(keep);
+    stats.passes++;
+    stats.kernel_launches = lc.n;
+    iter++;
+    return true;
 }
 
 void cr_server::loop() {
     cudaSetDevice(device);
     LaunchCount lc;
     while (true) {
-        std::vector<uint64_t> act;
+        poll_completions(false);
+        bool idle = false;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stop || !queue.empty() || !active.empty(); });
             if (stop) break;
-            admit_locked();
-            act = active;
-            if (act.empty()) { // nothing fits yet: wait for a completion or a new request
+            if (fatal == CR_OK) admit_locked();
+            idle = active.empty();
+            if (idle && pending.empty()) {
                 cv_work.wait_for(lk, std::chrono::milliseconds(5));
                 continue;
             }
         }
-        // one sample pass of every active job
-        std::vector<cr_job> pj;
-        std::vector<uint32_t> bases;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            for (uint64_t id : act) {
-                SJob& j = jobs[id];
-                cr_job c = j.job;
-                c.spp = 1;
-                c.frame_base = j.job.frame_base + j.done;
-                c.out_rgb = j.d_out;
-                pj.push_back(c);
-                bases.push_back(j.px_base);
-            }
+        if (idle) { // nothing to launch: wait for the oldest completion
+            poll_completions(true);
+            continue;
         }
-        RenderPlan plan;
-        cr_status st = build_plan(pj.data(), (uint32_t)pj.size(), po, plan);
-        if (st == CR_OK) {
-            for (size_t i = 0; i < plan.jobs.size(); ++i) plan.jobs[i].px_base = bases[i];
-            plan.npx_total = arena_px;
-            st = dev.upload(plan, stream);
-        }
-        if (st == CR_OK) {
-            ws.pb.accum = arena;
-            const double tb = now_ms();
-            st = enqueue_plan(plan, dev, ws, eo, stream, lc, nullptr);
-            uint64_t counts[kCountsWords / 2];
-            if (st == CR_OK) {
-                std::lock_guard<std::mutex> lk(mu);
-                for (uint64_t id : act) {
-                    SJob& j = jobs[id];
-                    if (j.done + 1 == j.job.spp) {
-                        launch_output_one(arena + j.px_base, j.npx, 1.0f / (float)j.job.spp, j.d_out, stream, lc);
-                        if (j.host_out)
-                            cudaMemcpyAsync(j.job.out_rgb, j.d_out, 12ull * j.npx, cudaMemcpyDeviceToHost, stream);
-                    }
-                }
-            }
-            cudaMemcpyAsync(counts, ws.pb.counts, 4 * kCountsWords, cudaMemcpyDeviceToHost, stream);
-            cudaError_t e = cudaStreamSynchronize(stream);
-            if (e == cudaSuccess) e = cudaGetLastError();
-            if (e != cudaSuccess && st == CR_OK) {
-                st = CR_ERR_CUDA;
-                std::lock_guard<std::mutex> lk(mu);
-                fatal_msg = cudaGetErrorString(e);
-            }
-            if (e == cudaSuccess && st == CR_OK && queue_status(counts) != CR_OK) {
-                st = CR_ERR_CUDA;
-                std::lock_guard<std::mutex> lk(mu);
-                fatal_msg = "queue compaction overflowed";
-            }
-            if (st == CR_OK) {
-                std::lock_guard<std::mutex> lk(mu);
-                stats.passes++;
-                stats.busy_ms += now_ms() - tb;
-                const uint64_t* stat = counts + kStatWord / 2;
-                for (uint32_t b = 1; b <= 16; ++b) stats.secondary_rays += stat[b];
-                stats.kernel_launches = lc.n;
-            }
-        }
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            const double t = now_ms();
-            std::vector<uint64_t> keep;
-            for (uint64_t id : act) {
-                SJob& j = jobs[id];
-                if (st != CR_OK) {
-                    j.state = 3;
-                    j.status = st;
-                } else if (++j.done < j.job.spp) {
-                    keep.push_back(id);
-                    continue;
-                } else {
-                    j.state = 2;
-                }
-                j.t_done = t;
-                alloc.release(j.px_base, j.npx);
-                used -= j.footprint;
-                slots_used -= j.slots;
-                if (j.host_out) staging_used -= 12ull * j.npx;
-                if (j.host_out && j.d_out) {
-                    cudaFree(j.d_out);
-                    j.d_out = nullptr;
-                }
-                stats.jobs_done++;
-            }
-            active = keep;
-            if (st != CR_OK) fatal = st;
-        }
-        cv_done.notify_all();
+        const double tb = now_ms();
+        iterate(lc);
+        std::lock_guard<std::mutex> lk(mu);
+        stats.busy_ms += now_ms() - tb;
     }
 }
 
@@ -258,6 +503,13 @@ extern "C" cr_status cr_server_create(const cr_server_opts* o, cr_server** out) 
         return CR_ERR_INVALID_ARG;
     }
     *out = nullptr;
+    const uint32_t m = o->group_w * o->group_h;
+    const uint32_t K = o->k ? o->k : m;
+    if (!o->group_w || !o->group_h || (m & (m - 1)) || m > 1024 || o->hbm_budget < (64ull << 20) || (K & (K - 1)) ||
+        m % K != 0 || K > 256) {
+        set_last_error("cr_server_create: bad tile shape or K, or budget below 64 MiB");
+        return CR_ERR_INVALID_ARG;
+    }
     std::unique_ptr<cr_server> s(new (std::nothrow) cr_server());
     if (!s) return CR_ERR_OOM;
     s->opts = *o;
@@ -268,41 +520,73 @@ extern "C" cr_status cr_server_create(const cr_server_opts* o, cr_server** out) 
     s->po.bvh8 = o->bvh == CR_BVH8Q;
     s->eo.block = o->block ? (int)o->block : 128;
     s->eo.block_secondary = o->block ? (int)o->block : kSecondaryBlock;
-    s->eo.clear_accum = false;
-    s->eo.write_output = false;
-    const uint32_t m = o->group_w * o->group_h;
-    if (!o->group_w || !o->group_h || (m & (m - 1)) || m > 1024 || o->hbm_budget < (64ull << 20)) {
-        set_last_error("cr_server_create: bad tile shape or budget below 64 MiB");
-        return CR_ERR_INVALID_ARG;
-    }
     s->budget = o->hbm_budget;
-    // the budget is split once: 60% path state (slots of the merged wavefront), 25% the
-    // accumulation arena (16 B per pixel of every admitted job), 15% output staging for
-    // jobs with host outputs (12 B per pixel)
-    s->slots_cap = (uint32_t)std::min<uint64_t>(o->hbm_budget * 6 / 10 / kSlotBytes, 1ull << 27);
+    // the budget is split once: 60% path state (whole tiles of slots), 25% the accumulation
+    // arena (16 B per pixel of every admitted job), 15% output staging for jobs with host
+    // outputs (12 B per pixel)
+    const uint64_t slots = std::min<uint64_t>(o->hbm_budget * 6 / 10 / kSlotBytes, 1ull << 27);
+    s->tiles_cap = (uint32_t)(slots / m);
     s->arena_px = (uint32_t)std::min<uint64_t>(o->hbm_budget / 4 / 16, 1ull << 28);
-    s->staging_cap = o->hbm_budget * 15 / 100;
+    s->staging_px = (uint32_t)std::min<uint64_t>(o->hbm_budget * 15 / 100 / 12, 1ull << 28);
     cudaGetDevice(&s->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&s->arena, 16ull * s->arena_px);
-    if (e != cudaSuccess) {
+    auto bad = [&](cudaError_t e, const char* what) {
         cudaGetLastError();
-        set_last_error("cr_server_create: device allocation failed");
-        if (s->stream) cudaStreamDestroy(s->stream);
+        set_last_error(what);
         return e == cudaErrorMemoryAllocation ? CR_ERR_OOM : CR_ERR_CUDA;
+    };
+    cr_server* r = s.get();
+    // releases whatever was allocated before a failure
+    auto cleanup = [r]() {
+        for (uint32_t p = 0; p < kDepth; ++p) {
+            if (r->d_table[p]) cudaFree(r->d_table[p]);
+            if (r->d_lists[p]) cudaFree(r->d_lists[p]);
+            if (r->h_table[p]) cudaFreeHost(r->h_table[p]);
+            if (r->h_lists[p]) cudaFreeHost(r->h_lists[p]);
+            if (r->ev_iter[p]) cudaEventDestroy(r->ev_iter[p]);
+            if (r->ev_copied[p]) cudaEventDestroy(r->ev_copied[p]);
+        }
+        if (r->d_scenes) cudaFree(r->d_scenes);
+        if (r->h_counts) cudaFreeHost(r->h_counts);
+        if (r->arena) cudaFree(r->arena);
+        if (r->staging) cudaFree(r->staging);
+        if (r->stream) cudaStreamDestroy(r->stream);
+        if (r->copy_stream) cudaStreamDestroy(r->copy_stream);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&r->arena, 16ull * r->arena_px);
+    if (e == cudaSuccess) e = cudaMalloc(&r->staging, 12ull * r->staging_px);
+    for (uint32_t p = 0; p < kDepth && e == cudaSuccess; ++p) {
+        e = cudaMalloc(&r->d_table[p], sizeof(JobDev) * kMaxRuns);
+        if (e == cudaSuccess) e = cudaMalloc(&r->d_lists[p], 4ull * kListWords);
+        if (e == cudaSuccess) e = cudaMallocHost(&r->h_table[p], sizeof(JobDev) * kMaxRuns);
+        if (e == cudaSuccess) e = cudaMallocHost(&r->h_lists[p], 4ull * kListWords);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_iter[p], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_copied[p], cudaEventDisableTiming);
     }
-    cr_status st = s->ws.ensure(s->slots_cap, 1);
-    if (st == CR_OK) st = s->ws.ensure_nee(s->slots_cap);
-    if (st != CR_OK) {
-        cudaFree(s->arena);
-        cudaStreamDestroy(s->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&r->d_scenes, sizeof(SceneDev) * kMaxScenes);
+    if (e == cudaSuccess) e = cudaMallocHost(&r->h_counts, 2 * kDepth * sizeof(uint64_t));
+    if (e != cudaSuccess) {
+        cr_status st = bad(e, "cr_server_create: device allocation failed");
+        cleanup();
         return st;
     }
-    s->alloc.init(s->arena_px);
-    std::memset(&s->stats, 0, sizeof(s->stats));
-    s->t0 = std::chrono::steady_clock::now();
-    cr_server* raw = s.get();
-    raw->th = std::thread([raw] { raw->loop(); });
+    std::memset(r->h_counts, 0, 2 * kDepth * sizeof(uint64_t));
+    cr_status st = r->ws.ensure(r->tiles_cap * m, 1);
+    if (st == CR_OK) st = r->ws.ensure_nee(r->tiles_cap * m);
+    if (st == CR_OK && cudaMemset(r->ws.pb.counts, 0, 4 * kCountsWords) != cudaSuccess)
+        st = bad(cudaErrorUnknown, "cr_server_create: clearing the counters failed");
+    if (st != CR_OK) {
+        cleanup();
+        return st;
+    }
+    r->alloc.init(r->arena_px);
+    r->stg_alloc.init(r->staging_px);
+    r->tile_alloc.init(r->tiles_cap);
+    for (uint32_t i = kMaxRuns; i-- > 0;) r->free_runs.push_back(i);
+    std::memset(&r->stats, 0, sizeof(r->stats));
+    r->t0 = std::chrono::steady_clock::now();
+    r->th = std::thread([r] { r->loop(); });
     *out = s.release();
     return CR_OK;
 }
@@ -331,16 +615,18 @@ extern "C" cr_status cr_server_submit(cr_server* s, const cr_job* job, uint64_t*
     cudaGetLastError();
     if (!j.host_out) j.d_out = job->out_rgb;
     j.npx = job->camera.width * job->camera.height;
+    const uint32_t m = s->po.tile_w * s->po.tile_h;
     const uint32_t tx = (job->camera.width + s->po.tile_w - 1) / s->po.tile_w;
     const uint32_t ty = (job->camera.height + s->po.tile_h - 1) / s->po.tile_h;
-    j.slots = tx * ty * s->po.tile_w * s->po.tile_h;
+    j.tiles = tx * ty;
+    j.slots = j.tiles * m;
     j.footprint = 16ull * j.npx + (j.host_out ? 12ull * j.npx : 0) + kSlotBytes * j.slots;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal != CR_OK) {
         set_last_error("cr_server_submit: the server stopped after a device error");
         return s->fatal;
     }
-    if (j.slots > s->slots_cap || j.npx > s->arena_px || (j.host_out && 12ull * j.npx > s->staging_cap)) {
+    if (j.tiles > s->tiles_cap || j.npx > s->arena_px || (j.host_out && j.npx > s->staging_px)) {
         set_last_error("cr_server_submit: job larger than the server's device budget");
         return CR_ERR_OOM;
     }
@@ -366,13 +652,15 @@ static cr_status fill_job_stats(const SJob& j, cr_job_stats* js) {
     return j.state == 2 ? CR_OK : j.status;
 }
 
+static bool finished(const SJob& j) { return j.state == 2 || j.state == 3; }
+
 extern "C" cr_status cr_server_poll(cr_server* s, uint64_t id, cr_job_stats* js) {
     set_last_error("");
     if (!s) return CR_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->jobs.find(id);
     if (it == s->jobs.end()) return CR_ERR_NOT_FOUND;
-    if (it->second.state < 2) return CR_ERR_BUSY;
+    if (!finished(it->second)) return CR_ERR_BUSY;
     cr_status st = fill_job_stats(it->second, js);
     s->jobs.erase(it);
     return st;
@@ -384,7 +672,7 @@ extern "C" cr_status cr_server_wait(cr_server* s, uint64_t id, uint32_t timeout_
     std::unique_lock<std::mutex> lk(s->mu);
     auto done = [&] {
         auto it = s->jobs.find(id);
-        return it == s->jobs.end() || it->second.state >= 2;
+        return it == s->jobs.end() || finished(it->second);
     };
     if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) return CR_ERR_TIMEOUT;
     auto it = s->jobs.find(id);
@@ -413,12 +701,24 @@ extern "C" cr_status cr_server_destroy(cr_server* s) {
     s->cv_work.notify_all();
     if (s->th.joinable()) s->th.join();
     cudaStreamSynchronize(s->stream);
-    for (auto& kv : s->jobs)
-        if (kv.second.host_out && kv.second.d_out) cudaFree(kv.second.d_out);
+    cudaStreamSynchronize(s->copy_stream);
+    for (auto& pe : s->pending) cudaEventDestroy(pe.first);
+    for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
+    for (uint32_t p = 0; p < kDepth; ++p) {
+        cudaFree(s->d_table[p]);
+        cudaFree(s->d_lists[p]);
+        cudaFreeHost(s->h_table[p]);
+        cudaFreeHost(s->h_lists[p]);
+        cudaEventDestroy(s->ev_iter[p]);
+        cudaEventDestroy(s->ev_copied[p]);
+    }
+    cudaFree(s->d_scenes);
+    cudaFreeHost(s->h_counts);
     s->ws.release();
-    s->dev.release();
     cudaFree(s->arena);
+    cudaFree(s->staging);
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->copy_stream);
     delete s;
     return CR_OK;
 }

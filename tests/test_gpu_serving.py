@@ -63,8 +63,10 @@ def test_results_equal_standalone_in_the_mix(cr, world, bvh):
                 time.sleep(0.002)  # requests keep arriving while earlier ones render
         lat = [cr.cr_server_wait(srv, jid, 60000) for jid in ids]
         st = cr.cr_server_get_stats(srv)
-        assert st["jobs_done"] == len(reqs) and st["passes"] >= max(r["spp"] for r in reqs)
-        assert st["passes"] < sum(r["spp"] for r in reqs)  # jobs shared passes
+        # "passes" counts bounce iterations: a job takes spp (B + 1) + 1 of them alone
+        steps = [r["spp"] * (r["B"] + 1) + 1 for r in reqs]
+        assert st["jobs_done"] == len(reqs) and st["passes"] >= max(steps)
+        assert st["passes"] < sum(steps)  # jobs shared launches
         for r, out, l in zip(reqs, outs, lat):
             cam = _cam(sc[r["name"]].camera, r["w"], r["h"])
             ref, _ = S[r["name"]].render(cam, spp=r["spp"], max_bounces=r["B"], mode=r["mode"], tile=(8, 8), k=8,
@@ -80,22 +82,59 @@ def test_results_equal_standalone_in_the_mix(cr, world, bvh):
 
 
 def test_admission_by_footprint(cr, world):
-    """A budget that holds only a few jobs at a time still completes all of them, and a job
-    larger than the whole budget is refused at submission."""
+    """A budget that holds only a few jobs at a time still completes all of them (equal to
+    their stand-alone renders), and a job larger than the whole budget is refused at
+    submission."""
     sc, S = world
-    srv = cr.cr_server_create(64 << 20, tile=(8, 8), k=8)
+    srv = cr.cr_server_create(64 << 20, tile=(8, 8), k=8)  # path state for 3 jobs of 256^2
     try:
         cam = _cam(sc["tiny"].camera, 256, 256)
         outs = [torch.empty((256, 256, 3), device="cuda") for _ in range(6)]
         ids = [cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, cam, o, spp=3, max_bounces=2, seed=i))
                for i, o in enumerate(outs)]
+        peak = 0
+        while cr.cr_server_get_stats(srv)["jobs_done"] < len(ids):
+            peak = max(peak, cr.cr_server_get_stats(srv)["active"])
+            time.sleep(0.0005)
         stats = [cr.cr_server_wait(srv, i, 60000) for i in ids]
-        admits = sorted(s["t_admit_ms"] for s in stats)
-        dones = sorted(s["t_done_ms"] for s in stats)
-        assert admits[-1] >= dones[0]  # the last admission waited for a completion
+        assert 1 <= peak <= 3 and all(s["samples"] == 3 for s in stats)
+        for i, o in enumerate(outs):
+            ref, _ = S["tiny"].render(cam, spp=3, max_bounces=2, tile=(8, 8), k=8, seed=i)
+            assert torch.equal(o, ref)
         big = cr.make_job(S["tiny"].handle, _cam(sc["tiny"].camera, 4096, 4096), torch.empty(1, device="cuda"))
         with pytest.raises(cr.CrError) as ei:
             cr.cr_server_submit(srv, big)
         assert ei.value.status == cr.CR_ERR_OOM
+    finally:
+        cr.cr_server_destroy(srv)
+
+
+def test_a_request_joins_between_bounce_launches(cr, world):
+    """Continuous batching at bounce granularity: a small request submitted while a large
+    many-bounce job renders is admitted within a fraction of one of that job's samples (it
+    joins at the next bounce launch instead of waiting for the sample to end), finishes
+    first, and equals its stand-alone render."""
+    sc, S = world
+    srv = cr.cr_server_create(2 << 30, tile=(8, 8), k=8)
+    try:
+        big_cam = _cam(sc["interior"].camera, 1024, 1024)
+        big = torch.empty((1024, 1024, 3), device="cuda")
+        spp, B = 48, 16
+        bid = cr.cr_server_submit(srv, cr.make_job(S["interior"].handle, big_cam, big, spp=spp, max_bounces=B,
+                                                   seed=3))
+        time.sleep(0.02)  # the big job is rendering
+        small_cam = _cam(sc["tiny"].camera, 32, 32)
+        small = torch.empty((32, 32, 3), device="cuda")
+        sid = cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, small_cam, small, spp=1, max_bounces=2, seed=5))
+        s_st = cr.cr_server_wait(srv, sid, 60000)
+        b_st = cr.cr_server_wait(srv, bid, 60000)
+        one_sample = (b_st["t_done_ms"] - b_st["t_admit_ms"]) / spp
+        assert b_st["t_admit_ms"] < s_st["t_submit_ms"] < b_st["t_done_ms"] - 4 * one_sample
+        assert s_st["t_admit_ms"] - s_st["t_submit_ms"] < 0.5 * one_sample
+        assert s_st["t_done_ms"] < b_st["t_done_ms"]
+        ref, _ = S["tiny"].render(small_cam, spp=1, max_bounces=2, tile=(8, 8), k=8, seed=5)
+        assert torch.equal(small, ref)
+        ref, _ = S["interior"].render(big_cam, spp=spp, max_bounces=B, tile=(8, 8), k=8, seed=3)
+        assert torch.equal(big, ref)
     finally:
         cr.cr_server_destroy(srv)
