@@ -981,6 +981,24 @@ def serving_leg(cr, scenes, args):
     return out
 
 
+def sort_only(args):
+    """The Morton comparator's ray sort alone (cr_debug_sort) on N random 30-bit keys: mean
+    device time of a sort over --sort-reps runs after one warm-up, as one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2310_07182_gb300 import binding as cr
+    from paper_2310_07182_gb300 import build as crbuild
+    crbuild.build()
+    n = args.sort_keys
+    rng = np.random.default_rng(1)
+    keys = torch.from_numpy(rng.integers(0, 1 << 30, n, dtype=np.int64).astype(np.uint32).view(np.int32)).cuda()
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    cr.cr_debug_sort(keys, vals, reps=1)
+    _, _, ms = cr.cr_debug_sort(keys, vals, reps=args.sort_reps)
+    print(json.dumps({"sort_keys": n, "reps": args.sort_reps, "ms_per_sort": round(ms, 5),
+                      "algorithmic_gbs": round(n * (8 + 12 + 3 * 16) / (ms * 1e-3) / 1e9, 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -992,6 +1010,8 @@ def main():
     ap.add_argument("--core-only", action="store_true", help="skip the precision, sweep, quality, batched and serving legs")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--sort-keys", type=int, default=0, help="time the ray sort alone on this many keys and exit")
+    ap.add_argument("--sort-reps", type=int, default=20)
     ap.add_argument("--serve-window", type=float, default=10.0, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-drain", type=float, default=5.0, help="seconds to wait for the requests after the window")
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[20.0, 50.0, 100.0, 200.0])
@@ -1001,7 +1021,9 @@ def main():
                     help="modes to time (the first is the headline); profiling runs use one")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
-    if args.impl == "reference":
+    if args.sort_keys:
+        sort_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
