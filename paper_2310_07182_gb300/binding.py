@@ -18,7 +18,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libcr.so")
+# CR_LIB selects another build of the library (the debug build, libcr_debug.so) for a process
+LIB_PATH = os.environ.get("CR_LIB") or os.path.join(_PKG, "libcr.so")
 
 CR_OK, CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT, CR_ERR_STACK_OVERFLOW, CR_ERR_BUSY, \
     CR_ERR_NOT_FOUND = range(8)

@@ -143,7 +143,30 @@ int scene_device(const cr_scene* s) { return s->device; }
 } // namespace cr
 
 extern "C" const char* cr_last_error(void) { return g_err.c_str(); }
-extern "C" const char* cr_version(void) { return "cr 0.1 sm_103a"; }
+#ifndef CR_DEBUG
+#define CR_DEBUG 0
+#endif
+extern "C" const char* cr_version(void) { return CR_DEBUG ? "cr 0.1 sm_103a debug" : "cr 0.1 sm_103a"; }
+
+namespace cr {
+// A debug build's verdict on a scene after a synchronised call: CR_OK, or CR_ERR_CUDA when a
+// kernel found a node, triangle or material index out of range (the word is then cleared).
+static cr_status debug_word_status(const cr_scene* s) {
+#if CR_DEBUG
+    uint32_t w = 0;
+    if (cudaMemcpy(&w, s->dev.err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(CR_ERR_CUDA, "debug build: reading the error word failed");
+    if (w) {
+        cudaMemset(s->dev.err, 0, 4);
+        return fail(CR_ERR_CUDA, "debug build: index checks failed (bits 0x%x: 1 node, 2 triangle, 4 hit, 8 material)",
+                    w);
+    }
+#else
+    (void)s;
+#endif
+    return CR_OK;
+}
+} // namespace cr
 
 extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const uint32_t* tri_mat,
                                      const cr_material* mats, uint32_t n_mat, const cr_env* env, uint32_t bvh_flags,
@@ -311,10 +334,15 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     }
     s->dev.n_tri = n_tri;
     s->dev.n_mat = n_mat;
+    s->dev.n_nodes2 = b2.n_nodes;
+    s->dev.n_nodes8 = (bvh_flags & CR_BVH8Q) ? b8.n_nodes : 0u;
     {
-        SceneDev ent[2] = {scene_entry(s->dev, false), scene_entry(s->dev, s->dev.nodes8 != nullptr)};
+        // the two scene-table entries, then the scene's error word (index checks of a debug build)
         DevMem de;
-        CR_CUDA(de.alloc(sizeof(ent)));
+        CR_CUDA(de.alloc(2 * sizeof(SceneDev) + 16));
+        s->dev.err = reinterpret_cast<uint32_t*>(static_cast<char*>(de.p) + 2 * sizeof(SceneDev));
+        CR_CUDA(cudaMemset(s->dev.err, 0, 4));
+        SceneDev ent[2] = {scene_entry(s->dev, false), scene_entry(s->dev, s->dev.nodes8 != nullptr)};
         CR_CUDA(cudaMemcpy(de.p, ent, sizeof(ent), cudaMemcpyHostToDevice));
         s->d_entries = static_cast<SceneDev*>(de.p);
         de.p = nullptr;
@@ -983,7 +1011,11 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
         st = queue_status(host_counts);
         if (st != CR_OK) return st;
     }
-    if (!(o.flags & CR_OPT_NO_SYNC)) CR_CUDA(cudaStreamSynchronize(stream));
+    if (!(o.flags & CR_OPT_NO_SYNC)) {
+        CR_CUDA(cudaStreamSynchronize(stream));
+        st = debug_word_status(s);
+        if (st != CR_OK) return st;
+    }
     CR_CUDA(cudaGetLastError());
     return CR_OK;
 }
@@ -1094,6 +1126,10 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     CR_CUDA(finish_out(p_out, stream));
     CR_CUDA(finish_out(t_out, stream));
     CR_CUDA(cudaStreamSynchronize(stream));
+    {
+        const cr_status dst = debug_word_status(s);
+        if (dst != CR_OK) return dst;
+    }
     if (o.stats) {
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);

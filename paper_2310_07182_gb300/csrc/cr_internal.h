@@ -74,6 +74,8 @@ struct DevScene {
     const float4* lights = nullptr;   // 4 per emitter: v0|orig, v1|0, v2|0, emission|0
     uint32_t n_lights = 0;
     float light_total = 0.0f;
+    uint32_t n_nodes2 = 0, n_nodes8 = 0;
+    uint32_t* err = nullptr; // device word: index checks that failed (debug builds)
 };
 
 // One entry of the device scene table a pass reads (tris in the order of the BVH traversed).
@@ -88,6 +90,9 @@ struct SceneDev {
     const float4* lights;
     uint32_t n_lights;
     float light_total;
+    // sizes of this entry's arrays and the scene's error word (bounds checks of a debug build)
+    uint32_t n_nodes, n_tris, n_mats;
+    uint32_t* err;
 };
 SceneDev scene_entry(const DevScene& s, bool bvh8);
 

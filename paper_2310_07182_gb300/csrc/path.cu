@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "cr_internal.h"
+#include "debug_checks.cuh"
 #include "device_math.cuh"
 
 namespace cr {
@@ -332,10 +333,18 @@ __device__ __forceinline__ void setup_member(const ShadeArgs& a, const PassArgs&
         mb.alive = false;
         return;
     }
+    CR_DBG(if (!dbg_in_range(&sc, (uint32_t)h.x, kDbgHit, sc.n_tris)) {
+        mb.alive = false;
+        return;
+    })
     const float4 v0 = __ldg(&sc.tris[3 * h.x + 0]);
     const float4 v1 = __ldg(&sc.tris[3 * h.x + 1]);
     const float4 v2 = __ldg(&sc.tris[3 * h.x + 2]);
     const int mat = __float_as_int(v1.w);
+    CR_DBG(if (!dbg_in_range(&sc, (uint32_t)mat, kDbgMat, sc.n_mats)) {
+        mb.alive = false;
+        return;
+    })
     const float4 m0 = __ldg(&sc.mats[2 * mat + 0]);
     const float4 m1 = __ldg(&sc.mats[2 * mat + 1]);
     const uint32_t type = (uint32_t)__float_as_int(m0.x);
@@ -1432,9 +1441,12 @@ __global__ void k_finish_accumulate(PassArgs p, const int32_t* __restrict__ pixe
             dbg.prim[(p.bounce - 1) * dbg_npx + (uint32_t)pix] =
                 h.x >= 0 ? __float_as_int(__ldg(&sc.tris[3 * h.x]).w) : -1;
         if (dbg.ray) capture_trace(dbg, (p.bounce - 1) * dbg_npx + (uint32_t)pix, ray_o[s], ray_d[s], h, bt);
+        bool ok = h.x >= 0;
+        CR_DBG(ok = ok && dbg_in_range(&sc, (uint32_t)h.x, kDbgHit, sc.n_tris) &&
+                    dbg_in_range(&sc, (uint32_t)__float_as_int(__ldg(&sc.tris[3 * h.x + 1]).w), kDbgMat, sc.n_mats);)
         if (h.x < 0) {
             add_environment(sc, bt, L);
-        } else {
+        } else if (ok) {
             const float4 v1 = __ldg(&sc.tris[3 * h.x + 1]);
             const int mat = __float_as_int(v1.w);
             const float4 m0 = __ldg(&sc.mats[2 * mat + 0]);

@@ -21,10 +21,11 @@ namespace {
 // kAny: visibility only; the traversal ends at the first triangle hit before the ray's tmax.
 // kSmemS: stack entries per thread kept in shared memory (8, 16 or 32; deeper ones go to a
 // local array), a launch-shape knob of the autotuner.
+// dsc: the scene-table entry, read only by the index checks of a debug build.
 template <bool kCount, bool kAny = false, int kSmemS = kSmemStack>
 __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
-                                               unsigned long long& n_tri) {
+                                               unsigned long long& n_tri, const SceneDev* dsc = nullptr) {
     const RayPre r = prep_ray(ro, rd);
     const int skip = __float_as_int(ro.w);
     Best best{rd.w, -1, 0x7fffffff};
@@ -37,6 +38,10 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
     while (true) {
         while (node >= 0) {
             if (kCount) ++n_node;
+            CR_DBG(if (!dbg_in_range(dsc, (uint32_t)node, kDbgNode, dsc->n_nodes)) {
+                node = 0x7fffffff;
+                break;
+            })
             const float4 n0 = __ldg(&nodes[4 * node + 0]);
             const float4 n1 = __ldg(&nodes[4 * node + 1]);
             const float4 n2 = __ldg(&nodes[4 * node + 2]);
@@ -60,6 +65,7 @@ __device__ __forceinline__ int2 trace_bvh2_one(const float4* __restrict__ nodes,
         if (node == 0x7fffffff) break;
         // leaf
         const uint32_t code = (uint32_t)(~node);
+        CR_DBG(if (!dbg_in_range(dsc, (code >> 2) + (code & 3u), kDbgTri, dsc->n_tris)) break;)
         test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, n_tri);
         if (kAny && best.leaf >= 0) break;
         tcull = __fmul_rn(best.t, kCullWiden);
@@ -90,7 +96,7 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_bvh2(const SceneDev* __res
         int2 h = make_int2(-1, __float_as_int(INFINITY));
         if (rd.w >= 0.0f)
             h = trace_bvh2_one<kCount, kAny, kSmemS>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node,
-                                                     n_tri);
+                                                     n_tri, &sc);
         hit[slot] = h;
     }
     if (kCount) {
@@ -579,7 +585,7 @@ __global__ void __maxnreg__(CR_TRACE_MAXNREG) k_trace_shadow(
             const float4 ro = sh_o[slot];
             const SceneDev& sc = scenes[slot_scene[slot]];
             unsigned long long dn = 0, dt = 0;
-            const int2 h = trace_bvh2_one<false, true>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt);
+            const int2 h = trace_bvh2_one<false, true>(sc.nodes2, sc.tris, ro, rd, smem_stack + threadIdx.x, dn, dt, &sc);
             if (h.x < 0) {
                 const float4 c = sh_c[slot];
                 const float4 L = radiance[slot];
@@ -654,6 +660,10 @@ SceneDev scene_entry(const DevScene& s, bool bvh8) {
     e.lights = s.lights;
     e.n_lights = s.n_lights;
     e.light_total = s.light_total;
+    e.n_nodes = bvh8 ? s.n_nodes8 : s.n_nodes2;
+    e.n_tris = s.n_tri;
+    e.n_mats = s.n_mat;
+    e.err = s.err;
     return e;
 }
 

@@ -47,7 +47,7 @@ __device__ __forceinline__ float qbyte(uint32_t lo, uint32_t hi) {
 template <bool kCount, bool kAny = false>
 __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, unsigned long long& n_node,
-                                               unsigned long long& n_tri) {
+                                               unsigned long long& n_tri, const SceneDev* dsc = nullptr) {
     const RayPre r = prep_ray(ro, rd);
     const int skip = __float_as_int(ro.w);
     const uint32_t oct = (rd.x < 0.0f ? 1u : 0u) | (rd.y < 0.0f ? 2u : 0u) | (rd.z < 0.0f ? 4u : 0u);
@@ -59,6 +59,7 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
     uint32_t node = 0;
     while (true) {
         if (kCount) ++n_node;
+        CR_DBG(if (!dbg_in_range(dsc, (uint32_t)node, kDbgNode, dsc->n_nodes)) break;)
         const uint4 w0 = __ldg(&nodes[5 * node + 0]);
         const uint4 w1 = __ldg(&nodes[5 * node + 1]);
         const uint4 w2 = __ldg(&nodes[5 * node + 2]);
@@ -143,6 +144,7 @@ __device__ __forceinline__ int2 trace_bvh8_one(const uint4* __restrict__ nodes, 
         while (trimask) {
             const uint32_t j = (uint32_t)__ffs(trimask) - 1u;
             trimask &= trimask - 1u;
+            CR_DBG(if (!dbg_in_range(dsc, tri_base + j, kDbgTri, dsc->n_tris)) break;)
             test_leaf(tris, r, skip, tri_base + j, 1u, best, n_tri);
         }
         if (kAny && best.leaf >= 0) break;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(128, CR_BVH8_MIN_BLOCKS) k_trace_bvh8(const Sc
         const float4 ro = ray_o[slot];
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
-        if (rd.w >= 0.0f) h = trace_bvh8_one<kCount, kAny>(sc.nodes8, sc.tris, ro, rd, n_node, n_tri);
+        if (rd.w >= 0.0f) h = trace_bvh8_one<kCount, kAny>(sc.nodes8, sc.tris, ro, rd, n_node, n_tri, &sc);
         hit[slot] = h;
     }
     if (kCount) {
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(128, CR_BVH8_MIN_BLOCKS) k_trace_shadow8(
             const float4 ro = sh_o[slot];
             const SceneDev& sc = scenes[slot_scene[slot]];
             unsigned long long dn = 0, dt = 0;
-            const int2 h = trace_bvh8_one<false, true>(sc.nodes8, sc.tris, ro, rd, dn, dt);
+            const int2 h = trace_bvh8_one<false, true>(sc.nodes8, sc.tris, ro, rd, dn, dt, &sc);
             if (h.x < 0) {
                 const float4 c = sh_c[slot];
                 const float4 L = radiance[slot];

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "cr_internal.h"
+#include "debug_checks.cuh"
 
 namespace cr {
 namespace {
