@@ -66,57 +66,135 @@ def barrier():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """SM clock and clock-event (throttle) reasons sampled while the timed region runs.
+
+    NVML is polled directly (the same read-only queries nvidia-smi makes) every ``period_s``
+    from a host thread, each sample stamped with ``time.perf_counter()``; ``summary(t0, t1)``
+    keeps the samples taken inside the timed region.  A timed region of a few tens of
+    milliseconds thus still gets a handful of samples, where nvidia-smi's 100 ms loop sees at
+    most one.  Without NVML the sampler falls back to an ``nvidia-smi -lms`` process, whose
+    lines are stamped on arrival."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of the NVML API (nvmlClocksEventReason*)
+    REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                   0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, uuid: str | None = None, period_s: float = 0.005):
         self.idx = gpu_index
+        self.uuid = uuid
+        self.period = period_s
+        self.samples = []  # (perf_counter, sm_mhz, reason names)
+        self.max_mhz = None
+        self.source = None
+        self._stop = threading.Event()
+        self._thread = None
         self.proc = None
-        self.lines = []
+
+    # ---- NVML ----
+    def _nvml_open(self):
+        import ctypes
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        rc = 1
+        if self.uuid:
+            rc = nv.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(self.uuid.encode()), ctypes.byref(h))
+        if rc != 0:
+            rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h))
+        if rc != 0:
+            nv.nvmlShutdown()
+            raise OSError("no NVML handle for the device")
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:  # 1 = NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        return nv, h, reasons
+
+    def _nvml_loop(self, nv, h, reasons):
+        import ctypes
+        clk, mask = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if nv.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(clk)) == 0:
+                names = []
+                if reasons(h, ctypes.byref(mask)) == 0:
+                    names = [n for bit, n in self.REASON_BITS.items() if mask.value & bit]
+                self.samples.append((t, float(clk.value), names))
+            self._stop.wait(self.period)
+        nv.nvmlShutdown()
+
+    # ---- nvidia-smi fallback ----
+    def _smi_loop(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm, self.max_mhz = float(f[1]), float(f[2])
+            except ValueError:
+                continue
+            self.samples.append((time.perf_counter(), sm,
+                                 [n for n, v in zip(names, f[5:9]) if v.lower().startswith("active")]))
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except OSError:
-            self.proc = None
+            nv, h, reasons = self._nvml_open()
+            self.source = f"NVML every {self.period * 1e3:g} ms"
+            self._thread = threading.Thread(target=self._nvml_loop, args=(nv, h, reasons), daemon=True)
+        except (OSError, AttributeError):
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "100"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except OSError:
+                return self
+            self.source = "nvidia-smi -lms 100"
+            self._thread = threading.Thread(target=self._smi_loop, daemon=True)
+        self._thread.start()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *a):
+        self._stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self._thread:
+            self._thread.join(timeout=5)
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+    def summary(self, t0: float | None = None, t1: float | None = None):
+        """Median SM clock and the union of reasons over the samples taken in [t0, t1] (all
+        samples when no window is given).  If none fell inside, the sample nearest to the
+        window stands in and ``samples`` says 0."""
+        inside = [x for x in self.samples if (t0 is None or x[0] >= t0) and (t1 is None or x[0] <= t1)]
+        use = inside
+        if not inside and self.samples and t0 is not None:
+            mid = 0.5 * (t0 + (t1 if t1 is not None else t0))
+            use = [min(self.samples, key=lambda x: abs(x[0] - mid))]
+        reasons = sorted({n for x in use for n in x[2]})
+        out = {"sm_mhz": statistics.median(x[1] for x in use) if use else None, "sm_max_mhz": self.max_mhz,
+               "reasons": reasons, "samples": len(inside), "source": self.source}
+        if t0 is not None and t1 is not None:
+            out["window_ms"] = round((t1 - t0) * 1e3, 1)
+        return out
+
+
+def gpu_uuid(index: int) -> str | None:
+    """NVML's name ("GPU-<uuid>") of torch's device ``index``, which need not be NVML's index."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(index).uuid)
+    except (AttributeError, RuntimeError):
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 def load_peaks():
@@ -287,15 +365,15 @@ def run_ours(args):
 
     results = {}
     clocks = None
+    sampler = None
     for mode in modes:
+        if mode == modes[0]:  # sampling starts before the warm-up so it is live when timing starts
+            sampler = ClockSampler(local, uuid=gpu_uuid(local)).__enter__()
         for w in range(args.warmup):
             step(mode, frame_of(rank, w, world))
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        sampler = ClockSampler(local) if mode == modes[0] else None
-        if sampler:
-            sampler.__enter__()
         stats = []
         t_wall = time.perf_counter()
         for s in range(args.steps):
@@ -304,10 +382,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall
-        if sampler:
+        t_end = time.perf_counter()
+        wall = t_end - t_wall
+        if sampler and mode == modes[0]:
             sampler.__exit__()
-            clocks = sampler.summary()
+            clocks = sampler.summary(t_wall, t_end)
         ms = sum(x["ms_total"] for x in stats)
         ms_max = aggregate(ms, "max")
         sec = sum(x["secondary_rays"] for x in stats)

@@ -432,14 +432,14 @@ cr_status cr_debug_groups(uint32_t width, uint32_t height, uint32_t group_w, uin
  * ctr, out: host or device, n*4 uint32. */
 cr_status cr_debug_philox(uint64_t seed, const uint32_t* ctr, uint32_t n, uint32_t* out);
 
-/* The ray sort of CR_MORTON_SORT (a stable LSD radix sort: three passes of 10-bit digits,
- * one launch each, decoupled look-back between tiles) on caller keys: keys_out, vals_out =
- * (keys & (2^30 - 1), vals) in ascending key order, equal keys in input order.  The sort runs
- * reps times on the same input and *ms (may be NULL) receives the mean device time of one
- * sort (CUDA events; the key kernel with its digit counts, and the three passes).
+/* The ray sort of CR_MORTON_SORT (a stable LSD radix sort: three passes of 10-bit digits in
+ * one cooperative launch, grid barriers between the phases of a pass) on caller keys:
+ * keys_out, vals_out = (keys & (2^30 - 1), vals) in ascending key order, equal keys in input
+ * order.  The sort runs reps times on the same input and *ms (may be NULL) receives the mean
+ * device time of one sort (CUDA events; the key kernel and the three passes).
  * keys, vals, keys_out, vals_out: host or device, n elements.  n <= 2^28.
- * Errors: CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT (a bounded look-back wait
- * ran out; the order may then be wrong). */
+ * Errors: CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT (a bounded grid-barrier
+ * wait ran out; the order may then be wrong). */
 cr_status cr_debug_sort(const uint32_t* keys, const int32_t* vals, uint32_t n, uint32_t reps, uint32_t* keys_out,
                         int32_t* vals_out, double* ms);
 

@@ -587,7 +587,7 @@ cr_status Workspace::ensure(uint32_t n_slots, uint32_t npx) {
 cr_status queue_status(const uint64_t* host_counts) {
     const uint32_t e = reinterpret_cast<const uint32_t*>(host_counts)[kQueueErrWord];
     if (e & 1u) return fail(CR_ERR_CUDA, "queue compaction: an append would overflow a queue");
-    if (e & 2u) return fail(CR_ERR_TIMEOUT, "ray sort: a look-back wait ran out (the sorted order may be wrong)");
+    if (e & 2u) return fail(CR_ERR_TIMEOUT, "ray sort: a grid-barrier wait ran out (the sorted order may be wrong)");
     return CR_OK;
 }
 
@@ -1235,7 +1235,7 @@ extern "C" cr_status cr_debug_sort(const uint32_t* keys, const int32_t* vals, ui
     CR_CUDA(finish_out(vo, 0));
     uint32_t err = 0;
     CR_CUDA(cudaMemcpy(&err, cnt + 1, 4, cudaMemcpyDeviceToHost));
-    if (err) return fail(CR_ERR_TIMEOUT, "cr_debug_sort: a look-back wait ran out");
+    if (err) return fail(CR_ERR_TIMEOUT, "cr_debug_sort: a grid-barrier wait ran out");
     return CR_OK;
 }
 

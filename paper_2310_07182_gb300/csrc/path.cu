@@ -1152,38 +1152,26 @@ __device__ __forceinline__ uint32_t morton_key(const float4* __restrict__ ray_o,
 }
 
 // ------------------------------------------------------------------------------------
-// Stable LSD radix sort of the 30-bit keys with their slots: three passes of 10-bit digits,
-// one launch each, in the style of a single-pass ("onesweep") sort with decoupled
-// look-back.  The key kernel also counts the digits of all three passes (global
-// histograms), so a pass needs no counting launch of its own: each block takes tiles of
-// kOsTile keys in ticket order, ranks its keys stably inside the tile (warp multisplit by
-// ballots), publishes its digit counts, finds the counts of all earlier tiles by looking back
-// over their published words, and scatters its keys through shared memory so that writes of
-// one digit are contiguous.  Every grid is a fixed number of blocks per SM; the live key
-// count is read on the device.
+// Stable LSD radix sort of the 30-bit keys with their slots: three passes of 10-bit digits
+// after the key kernel, all three in one cooperative launch (k_sort_coop below).  Tiles are
+// kOsTile keys; a block ranks a tile's keys stably (warp multisplit by ballots) and scatters
+// them through shared memory so that writes of one digit are contiguous.  The grid is one
+// wave of resident blocks; the live key count is read on the device.
 constexpr uint32_t kRadixBits = 10, kRadix = 1u << kRadixBits, kRadixMask = kRadix - 1u, kRadixPasses = 3;
 constexpr uint32_t kOsThreads = 256, kOsWarps = kOsThreads / 32, kOsRounds = 16;
 constexpr uint32_t kOsWarpKeys = 32 * kOsRounds, kOsTile = kOsWarps * kOsWarpKeys; // 4096 keys per tile
-// sort workspace (uint32 words): [0, 3 kRadix) global digit counts per pass, then one tile
-// ticket per pass, then from kOsStatus the look-back words of each pass (stride: tiles x kRadix)
-constexpr uint32_t kOsHist = 0, kOsTicket = kRadixPasses * kRadix, kOsStatus = kRadixPasses * kRadix + 64;
-// look-back word: flag in the two top bits (0 nothing yet, aggregate = the tile's own count,
-// inclusive = the count of this and every earlier tile), count in the low 30 bits
-constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1u;
-constexpr uint32_t kLookbackSpins = 1u << 20; // look-back steps without progress before the wait is given up
-constexpr uint32_t kLookbackWindow = 4;       // earlier tiles read per look-back step
-constexpr uint32_t kSortErrBit = 2u;           // error word bit: a look-back wait ran out
+constexpr uint32_t kCoopMaxGrid = 1024; // blocks of the sort launch at most (chunk sums kept in shared memory)
+// sort workspace (uint32 words): word 0 the grid-barrier counter (cleared before each sort),
+// from kSortF the digit counts F of the live tiles (tiles x kRadix), then kCoopMaxGrid chunk sums
+constexpr uint32_t kSortCtr = 0, kSortF = 64;
+constexpr uint32_t kSortErrBit = 2u; // error word bit: a grid-barrier wait ran out
 
 __global__ void __launch_bounds__(512) k_morton(const float4* __restrict__ ray_o, const float4* __restrict__ ray_d,
                                                 const int32_t* __restrict__ queue, const uint32_t* __restrict__ count,
                                                 uint32_t n_max, const SceneDev* __restrict__ scenes,
                                                 const uint16_t* __restrict__ slot_scene, uint32_t kind,
                                                 uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
-                                                int32_t* __restrict__ vals_alt, uint32_t* __restrict__ ws,
-                                                size_t status_stride) {
-    __shared__ uint32_t s_h[kRadixPasses * kRadix];
-    for (uint32_t i = threadIdx.x; i < kRadixPasses * kRadix; i += blockDim.x) s_h[i] = 0u;
-    __syncthreads();
+                                                int32_t* __restrict__ vals_alt) {
     const uint32_t n = min(*count, n_max);
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -1199,211 +1187,240 @@ __global__ void __launch_bounds__(512) k_morton(const float4* __restrict__ ray_o
         keys[i] = key;
         vals[i] = slot;
         // the other value buffer starts as a copy, so every position a pass can leave
-        // unwritten (only after a look-back wait ran out) still holds a valid slot
+        // unwritten (only after a grid-barrier wait ran out) still holds a valid slot
         vals_alt[i] = slot;
-        atomicAdd(&s_h[key & kRadixMask], 1u);
-        atomicAdd(&s_h[kRadix + ((key >> kRadixBits) & kRadixMask)], 1u);
-        atomicAdd(&s_h[2 * kRadix + ((key >> (2 * kRadixBits)) & kRadixMask)], 1u);
     }
-    // clear the look-back words of the live tiles of every pass
-    const uint32_t n_tiles = (n + kOsTile - 1) / kOsTile;
-    const size_t per_pass = (size_t)n_tiles * kRadix;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < kRadixPasses * per_pass; i += stride) {
-        const size_t pass = i / per_pass;
-        ws[kOsStatus + pass * status_stride + (i - pass * per_pass)] = 0u;
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kRadixPasses * kRadix; i += blockDim.x)
-        if (s_h[i]) atomicAdd(&ws[kOsHist + i], s_h[i]);
 }
 
-__global__ void __launch_bounds__(kOsThreads, 3) k_onesweep(const uint32_t* __restrict__ kin,
-                                                            const int32_t* __restrict__ vin,
-                                                            uint32_t* __restrict__ kout, int32_t* __restrict__ vout,
-                                                            const uint32_t* __restrict__ count, uint32_t n_max,
-                                                            uint32_t pass, uint32_t* __restrict__ ws,
-                                                            uint32_t* status, uint32_t* __restrict__ err) {
-    // per-warp digit counts (then per-warp offsets); afterwards the tile's keys and values
-    // in sorted order (kOsTile each, the same 32 KB)
-    __shared__ uint32_t s_cnt[kOsWarps * kRadix];
-    __shared__ uint32_t s_gbase[kRadix]; // first output position of each digit (all tiles)
-    __shared__ uint32_t s_local[kRadix]; // first tile-local position of each digit
-    __shared__ uint32_t s_out[kRadix];   // the tile's digit counts, then output position - local position
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_tile;
-    const uint32_t n = min(*count, n_max);
-    const uint32_t n_tiles = (n + kOsTile - 1) / kOsTile;
-    const uint32_t shift = kRadixBits * pass;
-    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    {   // exclusive scan of the pass's global digit counts; thread t owns digits 4t..4t+3
-        const uint32_t d0 = 4 * threadIdx.x;
-        const uint32_t* h = ws + kOsHist + pass * kRadix + d0;
-        const uint32_t c0 = h[0], c1 = h[1], c2 = h[2], c3 = h[3];
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan(c0 + c1 + c2 + c3, s_warp, tot);
-        s_gbase[d0] = ex;
-        s_gbase[d0 + 1] = ex + c0;
-        s_gbase[d0 + 2] = ex + c0 + c1;
-        s_gbase[d0 + 3] = ex + c0 + c1 + c2;
-    }
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ws[kOsTicket + pass], 1u);
-        for (uint32_t i = threadIdx.x; i < kOsWarps * kRadix; i += kOsThreads) s_cnt[i] = 0u;
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= n_tiles) break;
-        // a warp ranks its 512 consecutive keys round by round (index order = round, lane):
-        // rank = keys of the same digit in earlier rounds + peers in lower lanes this round
-        const uint32_t wbase = tile * kOsTile + w * kOsWarpKeys;
-        uint32_t* wc = s_cnt + w * kRadix;
-        uint32_t key[kOsRounds], pos[kOsRounds];
-        int32_t val[kOsRounds];
-#pragma unroll
-        for (uint32_t r = 0; r < kOsRounds; ++r) {
-            const uint32_t i = wbase + r * 32 + lane;
-            key[r] = i < n ? kin[i] : 0u;
-            val[r] = i < n ? vin[i] : 0;
-        }
-#pragma unroll
-        for (uint32_t r = 0; r < kOsRounds; ++r) {
-            const bool ok = wbase + r * 32 + lane < n;
-            const uint32_t dig = (key[r] >> shift) & kRadixMask;
-            // lanes with the same digit: one ballot per digit bit (a warp multisplit), far
-            // cheaper than a match instruction; lanes past the end join no group
-            uint32_t peers = __ballot_sync(0xffffffffu, ok);
-#pragma unroll
-            for (uint32_t bit = 0; bit < kRadixBits; ++bit) {
-                const uint32_t b = __ballot_sync(0xffffffffu, (dig >> bit) & 1u);
-                peers &= ((dig >> bit) & 1u) ? b : ~b;
-            }
-            const uint32_t below = __popc(peers & ((1u << lane) - 1u));
-            const uint32_t before = ok ? wc[dig] : 0u;
-            __syncwarp();
-            if (ok && below == 0u) wc[dig] = before + __popc(peers);
-            __syncwarp();
-            pos[r] = before + below;
-        }
-        __syncthreads();
-        // per digit: exclusive offsets of the warps, and the tile's count
-        for (uint32_t d = threadIdx.x; d < kRadix; d += kOsThreads) {
-            uint32_t acc = 0;
-            for (uint32_t ww = 0; ww < kOsWarps; ++ww) {
-                const uint32_t c = s_cnt[ww * kRadix + d];
-                s_cnt[ww * kRadix + d] = acc;
-                acc += c;
-            }
-            s_out[d] = acc;
-        }
-        __syncthreads();
-        {   // tile-local exclusive scan over the digits (ends with a block barrier)
-            const uint32_t d0 = 4 * threadIdx.x;
-            const uint32_t c0 = s_out[d0], c1 = s_out[d0 + 1], c2 = s_out[d0 + 2], c3 = s_out[d0 + 3];
-            uint32_t tot;
-            const uint32_t ex = block_excl_scan(c0 + c1 + c2 + c3, s_warp, tot);
-            s_local[d0] = ex;
-            s_local[d0 + 1] = ex + c0;
-            s_local[d0 + 2] = ex + c0 + c1;
-            s_local[d0 + 3] = ex + c0 + c1 + c2;
-        }
-        __syncthreads(); // every digit's tile-local start is written
-        // decoupled look-back; thread t owns digits t, t + 256, t + 512, t + 768 (adjacent
-        // threads poll adjacent words).  All four digits walk back together, kLookbackWindow
-        // earlier tiles per step, so that many independent loads are in flight.  The walk of
-        // a digit stops at the first inclusive word and pauses at a word not yet published.
-        // Every wait is bounded: when it runs out the error word is set and the tile carries
-        // on with what it has (its writes stay in bounds).
-        {
-            constexpr uint32_t Q = kRadix / kOsThreads, Wn = kLookbackWindow;
-            uint32_t cnt[Q], excl[Q];
-            int32_t cur[Q]; // the next earlier tile to read, -1 once the digit is done
-#pragma unroll
-            for (uint32_t q = 0; q < Q; ++q) {
-                const uint32_t d = threadIdx.x + q * kOsThreads;
-                cnt[q] = s_out[d];
-                excl[q] = 0;
-                cur[q] = (int32_t)tile - 1;
-                if (tile > 0) *(volatile uint32_t*)(status + (size_t)tile * kRadix + d) = kFlagAgg | cnt[q];
-            }
-            uint32_t idle = 0;
-            bool pending = tile > 0;
-            while (pending) {
-                uint32_t v[Q][Wn];
-#pragma unroll
-                for (uint32_t q = 0; q < Q; ++q)
-#pragma unroll
-                    for (uint32_t k = 0; k < Wn; ++k) {
-                        const int32_t tp = cur[q] - (int32_t)k;
-                        v[q][k] = tp >= 0 ? *(volatile const uint32_t*)(status + (size_t)tp * kRadix + threadIdx.x +
-                                                                        q * kOsThreads)
-                                          : 0u;
-                    }
-                pending = false;
-                bool moved = false;
-#pragma unroll
-                for (uint32_t q = 0; q < Q; ++q) {
-                    bool go = cur[q] >= 0;
-#pragma unroll
-                    for (uint32_t k = 0; k < Wn; ++k) {
-                        if (go) {
-                            const uint32_t x = v[q][k];
-                            if ((x & ~kCountMask) == 0u) {
-                                go = false; // not published yet: read this tile again
-                            } else {
-                                excl[q] += x & kCountMask;
-                                cur[q] = (x & kFlagInc) ? -1 : cur[q] - 1;
-                                go = cur[q] >= 0;
-                                moved = true;
-                            }
-                        }
-                    }
-                    pending |= cur[q] >= 0;
-                }
-                if (pending && !moved) {
-                    if (++idle > kLookbackSpins) {
-                        atomicOr(err, kSortErrBit);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-#pragma unroll
-            for (uint32_t q = 0; q < Q; ++q) {
-                const uint32_t d = threadIdx.x + q * kOsThreads;
-                *(volatile uint32_t*)(status + (size_t)tile * kRadix + d) = kFlagInc | (excl[q] + cnt[q]);
-                s_out[d] = s_gbase[d] + excl[q] - s_local[d];
-            }
-        }
-        // tile-local positions: digit start in the tile + the warp's offset + rank in the warp
-#pragma unroll
-        for (uint32_t r = 0; r < kOsRounds; ++r) {
-            if (wbase + r * 32 + lane < n) {
-                const uint32_t dig = (key[r] >> shift) & kRadixMask;
-                pos[r] += s_local[dig] + s_cnt[w * kRadix + dig];
-            }
-        }
-        __syncthreads(); // the warp offsets are read: the same memory now stages the tile
-        uint32_t* s_key = s_cnt;
-        int32_t* s_val = reinterpret_cast<int32_t*>(s_cnt + kOsTile);
-#pragma unroll
-        for (uint32_t r = 0; r < kOsRounds; ++r) {
-            if (wbase + r * 32 + lane < n) {
-                s_key[pos[r]] = key[r];
-                s_val[pos[r]] = val[r];
-            }
-        }
-        __syncthreads();
-        const uint32_t tile_n = min(kOsTile, n - tile * kOsTile);
-        for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
-            const uint32_t k = s_key[j];
-            const uint32_t dst = s_out[(k >> shift) & kRadixMask] + j;
-            if (dst < n) {
-                kout[dst] = k;
-                vout[dst] = s_val[j];
-            } else {
+// ------------------------------------------------------------------------------------
+// The three passes as one cooperative launch.  All blocks are resident at once (a
+// cooperative launch guarantees it), so the counts of earlier tiles come from a grid-wide
+// scan between two grid barriers; a look-back chain over the tiles' published counts, the
+// single-pass alternative, measured slower here (its walk, not the ranking, set a tile's
+// latency at ~1M keys).  Per pass:
+//   A  each block ranks its tiles' keys stably (warp multisplit, as above), keeps each
+//      tile in digit order and writes the tile's digit counts to F[d * T + t]
+//      (digit-major, T live tiles);
+//   -- grid barrier --
+//   B  exclusive scan of F: every block scans one chunk in place and publishes the chunk's
+//      sum.  In digit-major order the exclusive prefix of (d, t) is exactly the output
+//      position of the first key of digit d in tile t: all keys of smaller digits plus
+//      those of digit d in earlier tiles;
+//   -- grid barrier --
+//   C  each block adds the prefix of the chunk sums and scatters its tiles' keys.
+// A block that owns one tile keeps it in shared memory from A to C; with more tiles than
+// blocks, A writes each tile back in digit order over its own input range and C reads it
+// again.  A further barrier separates the passes.  Every barrier wait is bounded: when one
+// runs out the error word is set and the block returns, so the others run out too.
+constexpr uint32_t kBarrierSpins = 1u << 21;   // polls of a grid barrier before its wait is given up
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Arrive at the grid barrier whose completion is ctr == target and wait (bounded) for the
+// others.  Returns false, uniformly over the block, when the wait ran out.
+__device__ __forceinline__ bool grid_barrier(uint32_t* ctr, uint32_t target, uint32_t* err, uint32_t* s_flag) {
+    __syncthreads(); // every thread's writes precede thread 0's release
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        uint32_t spins = 0, ok = 1u;
+        while (ld_acquire_gpu(ctr) < target) {
+            if (++spins > kBarrierSpins) {
                 atomicOr(err, kSortErrBit);
+                ok = 0u;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0u;
+}
+
+__global__ void __launch_bounds__(kOsThreads, 3) k_sort_coop(uint32_t* __restrict__ ka, int32_t* __restrict__ va,
+                                                             uint32_t* __restrict__ kb, int32_t* __restrict__ vb,
+                                                             const uint32_t* __restrict__ count, uint32_t n_max,
+                                                             uint32_t* __restrict__ F, uint32_t* __restrict__ chunk_sum,
+                                                             uint32_t* __restrict__ ctr, uint32_t* __restrict__ err) {
+    // per-warp digit counts (then per-warp offsets); afterwards the tile's keys and values
+    // in digit order (kOsTile each, the same 32 KB)
+    __shared__ uint32_t s_cnt[kOsWarps * kRadix];
+    __shared__ uint32_t s_local[kRadix]; // first tile-local position of each digit
+    __shared__ uint32_t s_out[kRadix];   // the tile's digit counts, then its output positions
+    __shared__ uint32_t s_cpre[kCoopMaxGrid];
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_flag;
+    const uint32_t n = min(*count, n_max);
+    if (n == 0) return; // every block reads the same count: none waits at a barrier
+    const uint32_t T = (n + kOsTile - 1) / kOsTile;
+    const uint32_t G = gridDim.x;
+    const bool resident = T <= G; // at most one tile per block: it stays in shared memory
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const size_t L = (size_t)kRadix * T;
+    const uint32_t chunk = (uint32_t)((L + G - 1) / G);
+    uint32_t* s_key = s_cnt;
+    int32_t* s_val = reinterpret_cast<int32_t*>(s_cnt + kOsTile);
+    uint32_t barriers = 0;
+    for (uint32_t pass = 0; pass < kRadixPasses; ++pass) {
+        const uint32_t shift = kRadixBits * pass;
+        uint32_t* kin = pass & 1u ? kb : ka;
+        int32_t* vin = pass & 1u ? vb : va;
+        uint32_t* kout = pass & 1u ? ka : kb;
+        int32_t* vout = pass & 1u ? va : vb;
+        // ---- A: rank every tile of this block ----
+        for (uint32_t tile = blockIdx.x; tile < T; tile += G) {
+            for (uint32_t i = threadIdx.x; i < kOsWarps * kRadix; i += kOsThreads) s_cnt[i] = 0u;
+            __syncthreads();
+            const uint32_t wbase = tile * kOsTile + w * kOsWarpKeys;
+            uint32_t* wc = s_cnt + w * kRadix;
+            uint32_t key[kOsRounds], pos[kOsRounds];
+            int32_t val[kOsRounds];
+#pragma unroll
+            for (uint32_t r = 0; r < kOsRounds; ++r) {
+                const uint32_t i = wbase + r * 32 + lane;
+                key[r] = i < n ? __ldcg(kin + i) : 0u;
+                val[r] = i < n ? __ldcg(vin + i) : 0;
+            }
+#pragma unroll
+            for (uint32_t r = 0; r < kOsRounds; ++r) {
+                const bool ok = wbase + r * 32 + lane < n;
+                const uint32_t dig = (key[r] >> shift) & kRadixMask;
+                uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+                for (uint32_t bit = 0; bit < kRadixBits; ++bit) {
+                    const uint32_t b = __ballot_sync(0xffffffffu, (dig >> bit) & 1u);
+                    peers &= ((dig >> bit) & 1u) ? b : ~b;
+                }
+                const uint32_t below = __popc(peers & ((1u << lane) - 1u));
+                const uint32_t before = ok ? wc[dig] : 0u;
+                __syncwarp();
+                if (ok && below == 0u) wc[dig] = before + __popc(peers);
+                __syncwarp();
+                pos[r] = before + below;
+            }
+            __syncthreads();
+            for (uint32_t d = threadIdx.x; d < kRadix; d += kOsThreads) {
+                uint32_t acc = 0;
+                for (uint32_t ww = 0; ww < kOsWarps; ++ww) {
+                    const uint32_t c = s_cnt[ww * kRadix + d];
+                    s_cnt[ww * kRadix + d] = acc;
+                    acc += c;
+                }
+                s_out[d] = acc;
+                F[(size_t)d * T + tile] = acc;
+            }
+            __syncthreads();
+            {
+                const uint32_t d0 = 4 * threadIdx.x;
+                const uint32_t c0 = s_out[d0], c1 = s_out[d0 + 1], c2 = s_out[d0 + 2], c3 = s_out[d0 + 3];
+                uint32_t tot;
+                const uint32_t ex = block_excl_scan(c0 + c1 + c2 + c3, s_warp, tot);
+                s_local[d0] = ex;
+                s_local[d0 + 1] = ex + c0;
+                s_local[d0 + 2] = ex + c0 + c1;
+                s_local[d0 + 3] = ex + c0 + c1 + c2;
+            }
+            __syncthreads();
+#pragma unroll
+            for (uint32_t r = 0; r < kOsRounds; ++r) {
+                if (wbase + r * 32 + lane < n) {
+                    const uint32_t dig = (key[r] >> shift) & kRadixMask;
+                    pos[r] += s_local[dig] + s_cnt[w * kRadix + dig];
+                }
+            }
+            __syncthreads(); // the warp offsets are read: the same memory now stages the tile
+#pragma unroll
+            for (uint32_t r = 0; r < kOsRounds; ++r) {
+                if (wbase + r * 32 + lane < n) {
+                    s_key[pos[r]] = key[r];
+                    s_val[pos[r]] = val[r];
+                }
+            }
+            __syncthreads();
+            if (!resident) { // back over the tile's own input range, in digit order
+                const uint32_t tile_n = min(kOsTile, n - tile * kOsTile);
+                for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
+                    kin[tile * kOsTile + j] = s_key[j];
+                    vin[tile * kOsTile + j] = s_val[j];
+                }
+                __syncthreads();
             }
         }
-        __syncthreads(); // shared memory is reused by the next tile
+        if (!grid_barrier(ctr, ++barriers * G, err, &s_flag)) return;
+        // ---- B: exclusive scan of F, one chunk per block ----
+        {
+            const size_t c0 = (size_t)blockIdx.x * chunk;
+            const size_t c1 = min(L, c0 + chunk);
+            const uint32_t per = (chunk + kOsThreads - 1) / kOsThreads;
+            const size_t t0 = min(c1, c0 + (size_t)threadIdx.x * per);
+            const size_t t1 = min(c1, t0 + per);
+            uint32_t s = 0;
+            for (size_t i = t0; i < t1; ++i) s += __ldcg(F + i);
+            uint32_t tot;
+            uint32_t run = block_excl_scan(s, s_warp, tot);
+            for (size_t i = t0; i < t1; ++i) {
+                const uint32_t v = __ldcg(F + i);
+                F[i] = run;
+                run += v;
+            }
+            if (threadIdx.x == 0) chunk_sum[blockIdx.x] = tot;
+        }
+        if (!grid_barrier(ctr, ++barriers * G, err, &s_flag)) return;
+        // ---- C: output positions and the scatter ----
+        {   // exclusive prefix of the chunk sums; thread t owns chunks 4t..4t+3
+            const uint32_t q0 = 4 * threadIdx.x;
+            uint32_t c[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) c[k] = q0 + k < G ? __ldcg(chunk_sum + q0 + k) : 0u;
+            uint32_t tot;
+            const uint32_t ex = block_excl_scan(c[0] + c[1] + c[2] + c[3], s_warp, tot);
+            uint32_t acc = ex;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                if (q0 + k < kCoopMaxGrid) s_cpre[q0 + k] = acc;
+                acc += c[k];
+            }
+        }
+        __syncthreads();
+        for (uint32_t tile = blockIdx.x; tile < T; tile += G) {
+            const uint32_t tile_n = min(kOsTile, n - tile * kOsTile);
+            if (!resident) {
+                for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
+                    s_key[j] = __ldcg(kin + tile * kOsTile + j);
+                    s_val[j] = __ldcg(vin + tile * kOsTile + j);
+                }
+                __syncthreads();
+                // first tile-local position of each digit present in the tile
+                for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
+                    const uint32_t d = (s_key[j] >> shift) & kRadixMask;
+                    if (j == 0 || ((s_key[j - 1] >> shift) & kRadixMask) != d) s_local[d] = j;
+                }
+            }
+            for (uint32_t d = threadIdx.x; d < kRadix; d += kOsThreads) {
+                const size_t idx = (size_t)d * T + tile;
+                s_out[d] = __ldcg(F + idx) + s_cpre[idx / chunk];
+            }
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
+                const uint32_t k = s_key[j];
+                const uint32_t d = (k >> shift) & kRadixMask;
+                const uint32_t dst = s_out[d] + (j - s_local[d]);
+                if (dst < n) {
+                    kout[dst] = k;
+                    vout[dst] = s_val[j];
+                } else {
+                    atomicOr(err, kSortErrBit);
+                }
+            }
+            __syncthreads(); // shared memory is reused by the next tile or pass
+        }
+        if (pass + 1 < kRadixPasses && !grid_barrier(ctr, ++barriers * G, err, &s_flag)) return;
     }
 }
 
@@ -1751,16 +1768,41 @@ static int sm_count() {
     return cached[dev];
 }
 
-// Resident k_onesweep blocks per SM (its grid: one wave of persistent blocks).
-static uint32_t onesweep_blocks_per_sm() {
+// Resident k_sort_coop blocks per SM: its grid is one wave, every block resident at once.
+static uint32_t sort_blocks_per_sm() {
     static int cached = 0;
     if (!cached) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_onesweep, kOsThreads, 0) != cudaSuccess || nb <= 0)
-            nb = 2;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sort_coop, kOsThreads, 0) != cudaSuccess || nb <= 0)
+            nb = 1;
         cached = nb;
     }
     return (uint32_t)cached;
+}
+
+// The three radix passes over keys/values (ka, va) -> (kb, vb) -> (ka, va) -> (kb, vb) as one
+// cooperative launch; ws is the sort workspace (digit counts and the barrier counter
+// cleared, then F and the chunk sums).
+static void launch_radix_passes(uint32_t* ka, int32_t* va, uint32_t* kb, int32_t* vb, const uint32_t* count,
+                                uint32_t n_max, uint32_t* ws, uint32_t* err, cudaStream_t st, LaunchCount& lc) {
+    const uint32_t tiles_max = (n_max + kOsTile - 1) / kOsTile;
+    const size_t stride = (size_t)tiles_max * kRadix;
+    const uint32_t grid = max(1u, min(min(tiles_max, kCoopMaxGrid), sort_blocks_per_sm() * (uint32_t)sm_count()));
+    uint32_t* F = ws + kSortF;
+    uint32_t* chunk_sum = ws + kSortF + stride;
+    uint32_t* ctr = ws + kSortCtr;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kOsThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_sort_coop, ka, va, kb, vb, count, n_max, F, chunk_sum, ctr, err);
+    lc.n++;
 }
 
 // Sort the current bounce's ray queue by its reordering key; returns the sorted slot queue.
@@ -1768,32 +1810,16 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
                                   cudaStream_t st, LaunchCount& lc) {
     const uint32_t n_max = b.n_slots;
     const uint32_t* count = b.counts + 8 + 2 * bounce;
-    uint32_t* ka = b.keys;
-    uint32_t* kb = b.keys + n_max;
-    int32_t* va = b.vals;
-    int32_t* vb = b.vals + n_max;
     uint32_t* ws = b.sort_hist;
-    const uint32_t tiles_max = (n_max + kOsTile - 1) / kOsTile;
-    const size_t stride = (size_t)tiles_max * kRadix;
     const uint32_t sms = (uint32_t)sm_count();
-    cudaMemsetAsync(ws, 0, 4 * (size_t)kOsStatus, st); // digit counts and tickets
+    cudaMemsetAsync(ws, 0, 4 * (size_t)kSortF, st); // the barrier counter
     k_morton<<<min((n_max + 511) / 512, 2 * sms), 512, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max,
-                                                                 p.scenes, b.slot_scene, key_kind, ka, va, vb, ws,
-                                                                 stride);
+                                                                 p.scenes, b.slot_scene, key_kind, b.keys, b.vals,
+                                                                 b.vals + n_max);
     lc.n++;
-    const uint32_t blocks = max(1u, min(tiles_max, onesweep_blocks_per_sm() * sms));
-    for (uint32_t pass = 0; pass < kRadixPasses; ++pass) {
-        k_onesweep<<<blocks, kOsThreads, 0, st>>>(ka, va, kb, vb, count, n_max, pass, ws,
-                                                  ws + kOsStatus + pass * stride, b.counts + kQueueErrWord);
-        lc.n++;
-        uint32_t* tk = ka;
-        ka = kb;
-        kb = tk;
-        int32_t* tv = va;
-        va = vb;
-        vb = tv;
-    }
-    return va; // the last pass's output
+    launch_radix_passes(b.keys, b.vals, b.keys + n_max, b.vals + n_max, count, n_max, ws, b.counts + kQueueErrWord,
+                        st, lc);
+    return b.vals + n_max; // the last pass's output
 }
 
 // The ray sort on a caller's n keys (low 30 bits) and values, in buffers of the sort's
@@ -1801,32 +1827,15 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
 // values (the sorted keys are at the same offset of keys).  Used by cr_debug_sort.
 int32_t* launch_sort_only(const uint32_t* key_in, const int32_t* val_in, uint32_t n, uint32_t* keys, int32_t* vals,
                           uint32_t* ws, uint32_t* count, uint32_t* err, cudaStream_t st, LaunchCount& lc) {
-    uint32_t* ka = keys;
-    uint32_t* kb = keys + n;
-    int32_t* va = vals;
-    int32_t* vb = vals + n;
-    const uint32_t tiles_max = (n + kOsTile - 1) / kOsTile;
-    const size_t stride = (size_t)tiles_max * kRadix;
     const uint32_t sms = (uint32_t)sm_count();
-    cudaMemsetAsync(ws, 0, 4 * (size_t)kOsStatus, st);
+    cudaMemsetAsync(ws, 0, 4 * (size_t)kSortF, st);
     k_morton<<<min((n + 511) / 512, 2 * sms), 512, 0, st>>>(nullptr, nullptr, reinterpret_cast<const int32_t*>(key_in),
                                                              count, n, nullptr,
-                                                             reinterpret_cast<const uint16_t*>(val_in), 0, ka, va, vb,
-                                                             ws, stride);
+                                                             reinterpret_cast<const uint16_t*>(val_in), 0, keys, vals,
+                                                             vals + n);
     lc.n++;
-    const uint32_t blocks = max(1u, min(tiles_max, onesweep_blocks_per_sm() * sms));
-    for (uint32_t pass = 0; pass < kRadixPasses; ++pass) {
-        k_onesweep<<<blocks, kOsThreads, 0, st>>>(ka, va, kb, vb, count, n, pass, ws, ws + kOsStatus + pass * stride,
-                                                  err);
-        lc.n++;
-        uint32_t* tk = ka;
-        ka = kb;
-        kb = tk;
-        int32_t* tv = va;
-        va = vb;
-        vb = tv;
-    }
-    return va;
+    launch_radix_passes(keys, vals, keys + n, vals + n, count, n, ws, err, st, lc);
+    return vals + n;
 }
 
 void launch_scan_counts(uint32_t* block_counts, uint32_t n_blocks, uint32_t* total, cudaStream_t st) {
@@ -1834,9 +1843,9 @@ void launch_scan_counts(uint32_t* block_counts, uint32_t n_blocks, uint32_t* tot
     k_compact_scan<<<1, 1024, 0, st>>>(block_counts, n_blocks, total, nullptr);
 }
 
-// words of the sort workspace: digit counts, tickets and the look-back words of every pass
+// words of the sort workspace: the barrier counter, the digit counts of every tile, the chunk sums
 uint32_t sort_hist_len(uint32_t n_slots) {
-    return kOsStatus + kRadixPasses * ((n_slots + kOsTile - 1) / kOsTile) * kRadix;
+    return kSortF + ((n_slots + kOsTile - 1) / kOsTile) * kRadix + kCoopMaxGrid;
 }
 uint32_t compact_blocks(uint32_t n_pos) { return (n_pos + kCompactBlock - 1) / kCompactBlock; }
 

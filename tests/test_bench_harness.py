@@ -53,3 +53,33 @@ def test_single_process_aggregation_is_identity():
     import bench
     assert bench.aggregate(3.25, "max") == 3.25
     assert bench.frame_of(0, 7, 1) == 7
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """The clock record covers the timed region only: samples before and after it (warm-up,
+    the next leg) are left out, and their reasons too."""
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.max_mhz = 2070.0
+    cs.samples = [(0.90, 1500.0, ["sw_thermal_slowdown"]),  # warm-up, before the region
+                  (1.00, 2070.0, []), (1.01, 2055.0, ["sw_power_cap"]), (1.02, 2070.0, []),
+                  (1.20, 900.0, ["hw_slowdown"])]  # after the region
+    s = cs.summary(0.995, 1.025)
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["window_ms"] == 30.0
+    # a region shorter than the sampling period: the nearest sample stands in, samples = 0
+    s = cs.summary(1.05, 1.06)
+    assert s["samples"] == 0 and s["sm_mhz"] == 2070.0 and s["reasons"] == []
+    assert cs.summary()["samples"] == 5
+
+
+def test_clock_sampler_without_nvml_or_nvidia_smi(monkeypatch):
+    """On a host with neither NVML nor nvidia-smi the sampler records nothing and says so."""
+    import bench
+    monkeypatch.setenv("PATH", "/nonexistent")
+    cs = bench.ClockSampler(0)
+    monkeypatch.setattr(cs, "_nvml_open", lambda: (_ for _ in ()).throw(OSError("no NVML")))
+    with cs:
+        pass
+    s = cs.summary(0.0, 1.0)
+    assert s["sm_mhz"] is None and s["samples"] == 0 and s["source"] is None

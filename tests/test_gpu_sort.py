@@ -28,7 +28,7 @@ def _expect(keys, vals):
     return k[order], vals[order]
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 511, 512, 4095, 4096, 4097, 12289, 100_003, 1_463_294, 2_073_600])
+@pytest.mark.parametrize("n", [1, 2, 31, 511, 512, 4095, 4096, 4097, 12289, 100_003, 1_463_294, 2_073_600, 6_000_000])
 def test_sort_matches_a_stable_sort(cr, n):
     rng = np.random.default_rng(n)
     keys = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)  # bits above 30 are ignored
