@@ -1161,7 +1161,7 @@ constexpr uint32_t kRadixBits = 10, kRadix = 1u << kRadixBits, kRadixMask = kRad
 constexpr uint32_t kOsThreads = 256, kOsWarps = kOsThreads / 32, kOsRounds = 16;
 constexpr uint32_t kOsWarpKeys = 32 * kOsRounds, kOsTile = kOsWarps * kOsWarpKeys; // 4096 keys per tile
 constexpr uint32_t kCoopMaxGrid = 1024; // blocks of the sort launch at most (chunk sums kept in shared memory)
-// sort workspace (uint32 words): word 0 the grid-barrier counter (cleared before each sort),
+// sort workspace (uint32 words): word 0 the grid-barrier counter (cleared by the key kernel),
 // from kSortF the digit counts F of the live tiles (tiles x kRadix), then kCoopMaxGrid chunk sums
 constexpr uint32_t kSortCtr = 0, kSortF = 64;
 constexpr uint32_t kSortErrBit = 2u; // error word bit: a grid-barrier wait ran out
@@ -1171,7 +1171,8 @@ __global__ void __launch_bounds__(512) k_morton(const float4* __restrict__ ray_o
                                                 uint32_t n_max, const SceneDev* __restrict__ scenes,
                                                 const uint16_t* __restrict__ slot_scene, uint32_t kind,
                                                 uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
-                                                int32_t* __restrict__ vals_alt) {
+                                                int32_t* __restrict__ vals_alt, uint32_t* __restrict__ ctr) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ctr = 0u; // the sort launch's grid-barrier counter
     const uint32_t n = min(*count, n_max);
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -1221,12 +1222,13 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
 }
 
 // Arrive at the grid barrier whose completion is ctr == target and wait (bounded) for the
-// others.  Returns false, uniformly over the block, when the wait ran out.
+// others.  Returns false, uniformly over the block, when the wait ran out.  The arrival is a
+// release (it publishes every write the block made before its bar.sync, release being
+// cumulative) and the poll an acquire, so no full fence is needed on either side.
 __device__ __forceinline__ bool grid_barrier(uint32_t* ctr, uint32_t target, uint32_t* err, uint32_t* s_flag) {
     __syncthreads(); // every thread's writes precede thread 0's release
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
         uint32_t spins = 0, ok = 1u;
         while (ld_acquire_gpu(ctr) < target) {
             if (++spins > kBarrierSpins) {
@@ -1234,9 +1236,8 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* ctr, uint32_t target, uin
                 ok = 0u;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();
@@ -1373,6 +1374,14 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_sort_coop(uint32_t* __restric
         }
         if (!grid_barrier(ctr, ++barriers * G, err, &s_flag)) return;
         // ---- C: output positions and the scatter ----
+        // a block's only tile (the resident case) loads its scanned counts together with the
+        // chunk sums: one round trip instead of two
+        constexpr uint32_t Q = kRadix / kOsThreads;
+        uint32_t fv[Q];
+        if (resident && blockIdx.x < T) {
+#pragma unroll
+            for (uint32_t q = 0; q < Q; ++q) fv[q] = __ldcg(F + (size_t)(threadIdx.x + q * kOsThreads) * T + blockIdx.x);
+        }
         {   // exclusive prefix of the chunk sums; thread t owns chunks 4t..4t+3
             const uint32_t q0 = 4 * threadIdx.x;
             uint32_t c[4];
@@ -1402,9 +1411,11 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_sort_coop(uint32_t* __restric
                     if (j == 0 || ((s_key[j - 1] >> shift) & kRadixMask) != d) s_local[d] = j;
                 }
             }
-            for (uint32_t d = threadIdx.x; d < kRadix; d += kOsThreads) {
+#pragma unroll
+            for (uint32_t q = 0; q < Q; ++q) {
+                const uint32_t d = threadIdx.x + q * kOsThreads;
                 const size_t idx = (size_t)d * T + tile;
-                s_out[d] = __ldcg(F + idx) + s_cpre[idx / chunk];
+                s_out[d] = (resident ? fv[q] : __ldcg(F + idx)) + s_cpre[idx / chunk];
             }
             __syncthreads();
             for (uint32_t j = threadIdx.x; j < tile_n; j += kOsThreads) {
@@ -1812,10 +1823,9 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
     const uint32_t* count = b.counts + 8 + 2 * bounce;
     uint32_t* ws = b.sort_hist;
     const uint32_t sms = (uint32_t)sm_count();
-    cudaMemsetAsync(ws, 0, 4 * (size_t)kSortF, st); // the barrier counter
     k_morton<<<min((n_max + 511) / 512, 2 * sms), 512, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max,
                                                                  p.scenes, b.slot_scene, key_kind, b.keys, b.vals,
-                                                                 b.vals + n_max);
+                                                                 b.vals + n_max, ws + kSortCtr);
     lc.n++;
     launch_radix_passes(b.keys, b.vals, b.keys + n_max, b.vals + n_max, count, n_max, ws, b.counts + kQueueErrWord,
                         st, lc);
@@ -1828,11 +1838,10 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
 int32_t* launch_sort_only(const uint32_t* key_in, const int32_t* val_in, uint32_t n, uint32_t* keys, int32_t* vals,
                           uint32_t* ws, uint32_t* count, uint32_t* err, cudaStream_t st, LaunchCount& lc) {
     const uint32_t sms = (uint32_t)sm_count();
-    cudaMemsetAsync(ws, 0, 4 * (size_t)kSortF, st);
     k_morton<<<min((n + 511) / 512, 2 * sms), 512, 0, st>>>(nullptr, nullptr, reinterpret_cast<const int32_t*>(key_in),
                                                              count, n, nullptr,
                                                              reinterpret_cast<const uint16_t*>(val_in), 0, keys, vals,
-                                                             vals + n);
+                                                             vals + n, ws + kSortCtr);
     lc.n++;
     launch_radix_passes(keys, vals, keys + n, vals + n, count, n, ws, err, st, lc);
     return vals + n;
