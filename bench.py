@@ -358,7 +358,8 @@ def run_ours(args):
     # counting pass (untimed): node visits and triangle tests of the secondary traces
     modes = args.modes.split(",")
     if not args.core_only and "morton_sort" in modes:  # the other reordering keys of Table 1
-        modes += ["morton_sort:origin", "morton_sort:reis", "morton_sort:costa", "morton_sort:aila_compact"]
+        modes += ["morton_sort:origin", "morton_sort:reis", "morton_sort:costa", "morton_sort:aila_compact",
+                  "morton_sort:hierarchy_cut"]
     counts = {}
     for mode in modes:
         counts[mode] = step(mode, frame_of(rank, 0, world), flags=cr.CR_OPT_COUNT)

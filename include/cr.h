@@ -191,9 +191,13 @@ enum {
 /* Reordering keys of CR_MORTON_SORT (Table 1 comparators; 30-bit keys, layouts in path.cu):
  * TwoPoint interleaves origin and an estimated end point 0.25 x the largest scene extent
  * away; Origin is the origin's Morton code; Reis puts origin bits above direction bits,
- * Costa the reverse; AilaCompact interleaves origin and direction. */
+ * Costa the reverse; AilaCompact interleaves origin and direction.  HierarchyCut is a key
+ * from the BVH2 (a reading of MLHCC, of which the paper gives only the name, the code length
+ * and lambda = 0.125): the 15-level descent paths of the origin and of the point 0.125 x the
+ * largest scene extent along the ray, interleaved. */
 typedef enum {
-    CR_SORT_TWO_POINT = 0, CR_SORT_ORIGIN = 1, CR_SORT_REIS = 2, CR_SORT_COSTA = 3, CR_SORT_AILA_COMPACT = 4
+    CR_SORT_TWO_POINT = 0, CR_SORT_ORIGIN = 1, CR_SORT_REIS = 2, CR_SORT_COSTA = 3, CR_SORT_AILA_COMPACT = 4,
+    CR_SORT_HIERARCHY_CUT = 5
 } cr_sort_key;
 
 typedef struct {

@@ -268,7 +268,7 @@ def make_camera(cam) -> cr_camera:
                      float(cam.vfov_deg), int(cam.width), int(cam.height))
 
 
-SORT_KEYS = {"two_point": 0, "origin": 1, "reis": 2, "costa": 3, "aila_compact": 4}
+SORT_KEYS = {"two_point": 0, "origin": 1, "reis": 2, "costa": 3, "aila_compact": 4, "hierarchy_cut": 5}
 
 
 def make_opts(k=0, interleave=True, seed=0, frame_base=0, reuse_depth=0, bvh=CR_BVH2, block=0, flags=0,

@@ -950,7 +950,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     eo.packet_primary = (o.flags & CR_OPT_PACKET_PRIMARY) != 0;
     eo.packet_secondary = (o.flags & CR_OPT_PACKET_SECONDARY) != 0;
     eo.count = (o.flags & CR_OPT_COUNT) != 0;
-    if (o.sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "cr_render: sort_key %u", o.sort_key);
+    if (o.sort_key > CR_SORT_HIERARCHY_CUT) return fail(CR_ERR_INVALID_ARG, "cr_render: sort_key %u", o.sort_key);
     eo.sort_key = o.sort_key;
     if (o.flags & CR_OPT_TWO_PHASE) {
         eo.phase_budget = CR_PHASE_BUDGET;
@@ -1326,7 +1326,7 @@ static cr_status batch_opts_check(const cr_batch_opts* o, PlanOpts& po, ExecOpts
     eo.stack = o->stack ? o->stack : 16;
     eo.persistent = (o->flags & CR_OPT_PERSISTENT) != 0;
     eo.ordered_queues = (o->flags & CR_OPT_ORDERED_QUEUES) != 0;
-    if (o->sort_key > CR_SORT_AILA_COMPACT) return fail(CR_ERR_INVALID_ARG, "sort_key %u", o->sort_key);
+    if (o->sort_key > CR_SORT_HIERARCHY_CUT) return fail(CR_ERR_INVALID_ARG, "sort_key %u", o->sort_key);
     eo.sort_key = o->sort_key;
     return CR_OK;
 }

@@ -1081,6 +1081,56 @@ __global__ void __launch_bounds__(kCompactBlock) k_compact_scatter(const int32_t
 //                  octahedral coordinate, 2-D Morton)
 //   3 Costa        the same fields with the direction above the origin
 //   4 AilaCompact  origin and direction interleaved (5-D Morton, 6 bits per coordinate)
+//   5 HierarchyCut a key from the acceleration structure, our reading of MLHCC (the paper
+//                  describes it only as a code from cuts of the BVH, length 32, with
+//                  lambda = 0.125): the cut at depth l is the set of BVH2 nodes of depth l, and
+//                  a point's code at that level is the child its descent takes (1 bit).  The
+//                  origin and the point lambda x (largest scene extent) along the ray are
+//                  located by descending from the root to the nearest child box, and their
+//                  15-level paths are interleaved, origin first, top level most significant
+//                  (30 bits, the width of the sort's keys)
+constexpr uint32_t kHcutLevels = 15;
+constexpr float kHcutLambda = 0.125f;
+
+__device__ __forceinline__ float box_dist2(float px, float py, float pz, float lox, float hix, float loy, float hiy,
+                                           float loz, float hiz) {
+    const float dx = fmaxf(fmaxf(lox - px, px - hix), 0.0f);
+    const float dy = fmaxf(fmaxf(loy - py, py - hiy), 0.0f);
+    const float dz = fmaxf(fmaxf(loz - pz, pz - hiz), 0.0f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Path bits of point p through the BVH2 (root = node 0): at each node the child whose box is
+// nearer to p (distance 0 inside), ties (p in both) to the child whose box centre is nearer;
+// levels below a leaf add zero bits.
+__device__ __forceinline__ uint32_t hcut_path(const float4* __restrict__ nodes, float px, float py, float pz) {
+    uint32_t code = 0;
+    int node = 0;
+    for (uint32_t l = 0; l < kHcutLevels; ++l) {
+        code <<= 1;
+        if (node < 0) continue;
+        const float4 n0 = __ldg(&nodes[4 * node + 0]);
+        const float4 n1 = __ldg(&nodes[4 * node + 1]);
+        const float4 n2 = __ldg(&nodes[4 * node + 2]);
+        const float4 n3 = __ldg(&nodes[4 * node + 3]);
+        const float d0 = box_dist2(px, py, pz, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
+        const float d1 = box_dist2(px, py, pz, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
+        bool right;
+        if (d0 != d1) {
+            right = d1 < d0;
+        } else {
+            const float c0 = box_dist2(px, py, pz, 0.5f * (n0.x + n0.y), 0.5f * (n0.x + n0.y), 0.5f * (n0.z + n0.w),
+                                       0.5f * (n0.z + n0.w), 0.5f * (n2.x + n2.y), 0.5f * (n2.x + n2.y));
+            const float c1 = box_dist2(px, py, pz, 0.5f * (n1.x + n1.y), 0.5f * (n1.x + n1.y), 0.5f * (n1.z + n1.w),
+                                       0.5f * (n1.z + n1.w), 0.5f * (n2.z + n2.w), 0.5f * (n2.z + n2.w));
+            right = c1 < c0;
+        }
+        code |= right ? 1u : 0u;
+        node = __float_as_int(right ? n3.y : n3.x);
+    }
+    return code;
+}
+
 __device__ __forceinline__ uint32_t quant(float v, float lo, float scale, uint32_t bits) {
     const float m = (float)((1u << bits) - 1u);
     return (uint32_t)fminf(fmaxf((v - lo) * scale * m, 0.0f), m);
@@ -1110,6 +1160,13 @@ __device__ __forceinline__ uint32_t morton_key(const float4* __restrict__ ray_o,
     const float4 o = ray_o[slot], d = ray_d[slot];
     const float po[3] = {o.x, o.y, o.z};
     uint32_t key = 0;
+    if (kind == 5) {
+        const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z) * (kHcutLambda * emax);
+        const uint32_t a = hcut_path(sc.nodes2, o.x, o.y, o.z);
+        const uint32_t b = hcut_path(sc.nodes2, o.x + d.x * il, o.y + d.y * il, o.z + d.z * il);
+        const uint32_t q[2] = {a, b};
+        return interleave(q, 2, kHcutLevels);
+    }
     if (kind == 0) {
         const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z) * (0.25f * emax);
         const float pe[3] = {o.x + d.x * il, o.y + d.y * il, o.z + d.z * il};

@@ -209,7 +209,7 @@ def test_bvh8q_render_identical(cr, orc):
     _check(b.cpu().numpy(), ref, max_taint=0.1)
 
 
-@pytest.mark.parametrize("key", ["two_point", "origin", "reis", "costa", "aila_compact"])
+@pytest.mark.parametrize("key", ["two_point", "origin", "reis", "costa", "aila_compact", "hierarchy_cut"])
 def test_every_sort_key_gives_the_independent_image(cr, orc, key):
     """Reordering only changes the order rays are traced in (Table 1 comparators)."""
     sc, S, O = _scenes(cr, orc, "tiny", material_mix="mixed", n_soup=3000)
