@@ -68,12 +68,13 @@ def test_sixteen_bounces(cr, orc):
     assert st["secondary_rays"] > 0
 
 
-def test_every_camera_ray_misses(cr, orc):
+@pytest.mark.parametrize("mode", ["direction_reuse", "morton_sort"])
+def test_every_camera_ray_misses(cr, orc, mode):
     """Looking away from all geometry: the wavefront is empty after the primary trace and
-    every pixel is the environment."""
+    every pixel is the environment (under morton_sort the ray sort runs on zero keys)."""
     sc = scenes.tiny()
     cam = scenes.Camera((0.0, 0.0, -3.0), (0.0, 0.0, -10.0), (0.0, 1.0, 0.0), 30.0, 24, 16)
-    img, st, ref = _both(cr, orc, sc, cam, spp=2, max_bounces=3, mode="direction_reuse", tile=(8, 8), k=8, seed=1)
+    img, st, ref = _both(cr, orc, sc, cam, spp=2, max_bounces=3, mode=mode, tile=(8, 8), k=8, seed=1)
     assert st["secondary_rays"] == 0 and ref["counters"][1] == 0
     assert (img == 1.0).all() and (ref["rgb"] == 1.0).all()
 
