@@ -978,12 +978,16 @@ def batched_leg(cr, scenes, rank, args):
     return res
 
 
+EXPRESS_RAYS = 1 << 22  # ray steps (pixels x spp x (bounces + 1)) of the serving leg's express requests
+
+
 def serving_leg(cr, scenes, args):
     """Poisson arrivals against six resident scenes (tiny, soups 1M/4M, interior, landscape,
     terrain 2236^2 = 9,990,450 triangles), sides log-uniform in [128, 2048] (multiples of
     16), spp in {1,4,16,64}, 1-4 bounces, host outputs; p50/p99 latency from submission to
     the result on the host, and throughput, for direction reuse + BVH8-Q, independent
-    sampling + BVH2 and direction reuse + BVH2."""
+    sampling + BVH2 and direction reuse + BVH2, the last also with the express lane (requests
+    of at most EXPRESS_RAYS ray steps in a second, higher-priority wavefront)."""
     import numpy as np
     world = {"tiny": scenes.tiny(), "soup1m": scenes.soup(31, 1_000_000), "soup4m": scenes.soup(32, 4_000_000),
              "interior": scenes.interior(), "landscape": scenes.landscape(), "terrain": scenes.terrain()}
@@ -993,12 +997,17 @@ def serving_leg(cr, scenes, args):
            "latency": "submission to the result on the host, over the requests completed by the end of the drain; "
                       "queue wait = admission - submission, render = completion - admission",
            "configs": {}}
-    for cfg, mode, bvh in (("reuse_bvh8q", "direction_reuse", cr.CR_BVH8Q), ("independent_bvh2", "independent", cr.CR_BVH2),
-                           ("reuse_bvh2", "direction_reuse", cr.CR_BVH2)):
+    configs = (("reuse_bvh8q", "direction_reuse", cr.CR_BVH8Q, 0), ("independent_bvh2", "independent", cr.CR_BVH2, 0),
+               ("reuse_bvh2", "direction_reuse", cr.CR_BVH2, 0),
+               ("reuse_bvh2_express", "direction_reuse", cr.CR_BVH2, EXPRESS_RAYS))
+    out["express_rays"] = EXPRESS_RAYS
+    for cfg, mode, bvh, express in configs:
+        if getattr(args, "serve_configs", None) and cfg not in args.serve_configs:
+            continue
         rows = {}
         for lam in args.serve_rates:
             rng = np.random.default_rng(41 + int(lam))
-            srv = cr.cr_server_create(48 << 30, tile=(8, 8), k=8, bvh=bvh)
+            srv = cr.cr_server_create(48 << 30, tile=(8, 8), k=8, bvh=bvh, express_rays=express)
             t_next = 0.0
             arrivals = []
             while True:
@@ -1095,6 +1104,8 @@ def main():
     ap.add_argument("--serve-window", type=float, default=10.0, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-drain", type=float, default=5.0, help="seconds to wait for the requests after the window")
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[20.0, 50.0, 100.0, 200.0])
+    ap.add_argument("--serve-configs", type=lambda x: x.split(","), default=None,
+                    help="serving configurations to run (default: all)")
     ap.add_argument("--scene", default="landscape", choices=["landscape", "interior"],
                     help="workload scene; the headline metric is the landscape's")
     ap.add_argument("--modes", default="direction_reuse,independent,morton_sort,world_reuse",

@@ -377,6 +377,12 @@ cr_status cr_batch_autotune(const cr_job* jobs, uint32_t n_jobs, uint32_t allow_
 typedef struct {
     uint64_t hbm_budget;       /* bytes of device memory the server may use (>= 64 MiB) */
     uint32_t group_w, group_h, k, interleave, bvh, block; /* as cr_batch_opts */
+    /* Express lane (0 = none): jobs of at most express_rays ray steps (pixels x spp x
+     * (max_bounces + 1)) run in a second rolling wavefront with its own path state (1/8 of
+     * the slots) on a stream of the device's highest priority, so their bounce launches do
+     * not wait for the large jobs' launches.  An express job that does not fit its lane goes
+     * to the main one.  Results are the same in either lane. */
+    uint32_t express_rays, pad;
 } cr_server_opts;
 
 typedef struct {

@@ -111,7 +111,8 @@ class cr_tune_report(C.Structure):
 
 class cr_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_uint64), ("group_w", C.c_uint32), ("group_h", C.c_uint32), ("k", C.c_uint32),
-                ("interleave", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32)]
+                ("interleave", C.c_uint32), ("bvh", C.c_uint32), ("block", C.c_uint32),
+                ("express_rays", C.c_uint32), ("pad", C.c_uint32)]
 
 
 class cr_job_stats(C.Structure):
@@ -377,8 +378,8 @@ def cr_batch_autotune(jobs, opts: cr_batch_opts, allow_contiguous=False) -> dict
     return {k: getattr(rep, k) for k, _ in rep._fields_}
 
 
-def cr_server_create(hbm_budget, tile=(8, 8), k=0, interleave=True, bvh=CR_BVH2, block=0):
-    o = cr_server_opts(int(hbm_budget), tile[0], tile[1], k, int(interleave), bvh, block)
+def cr_server_create(hbm_budget, tile=(8, 8), k=0, interleave=True, bvh=CR_BVH2, block=0, express_rays=0):
+    o = cr_server_opts(int(hbm_budget), tile[0], tile[1], k, int(interleave), bvh, block, int(express_rays), 0)
     out = C.c_void_p()
     _check(lib().cr_server_create(C.byref(o), C.byref(out)))
     return out.value

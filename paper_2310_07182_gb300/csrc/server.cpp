@@ -12,6 +12,13 @@
 // slots (whole tiles), accumulation pixels and, for host outputs, staging pixels, each from
 // a first-fit arena allocated once, so the loop allocates nothing.  The host enqueues up to
 // kDepth iterations ahead of the GPU; events mark the iterations in which jobs complete.
+//
+// With an express lane (cr_server_opts.express_rays), small jobs run in a second wavefront
+// with its own path state, job tables and queues, on a stream of the highest priority: a
+// small job then takes one bounce step per iteration of its own lane, whose launches the
+// GPU schedules ahead of the main lane's waiting blocks, instead of one step per iteration
+// of the main lane (as long as the largest jobs' bounce).  Accumulation, staging and the
+// scene table are shared; each lane has its own slots.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,6 +59,9 @@ struct SJob {
     uint32_t done = 0;        // samples summed
     uint32_t step = 0;        // bounce step of the current sample at the next iteration
     uint32_t run = 0;         // job-table entry of the current sample
+    uint32_t lane = 0;        // 0 main, 1 express
+    bool shared_freed = false; // its accumulation and staging ranges are back in the arenas
+    uint64_t ray_steps = 0;   // pixels x spp x (max_bounces + 1)
     double t_submit = 0, t_admit = -1, t_done = -1;
     int state = 0;            // 0 queued, 1 active, 2 done, 3 failed, 4 waiting for its output
     cr_status status = CR_OK;
@@ -91,6 +101,73 @@ struct Arena { // first-fit ranges of units
     }
 };
 
+// One rolling wavefront: its stream, path state, device job tables and launch lists (kDepth
+// sets used round robin by the iterations in flight) with their pinned host sources, and
+// the jobs it runs.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr; // job-table uploads, off the render stream
+    Workspace ws;
+    JobDev* d_table[kDepth] = {};
+    uint32_t* d_lists[kDepth] = {};
+    JobDev* h_table[kDepth] = {};
+    uint32_t* h_lists[kDepth] = {};
+    uint64_t* h_counts = nullptr; // pinned: (rays traced at bounces >= 1, queue error word)
+    cudaEvent_t ev_iter[kDepth] = {};
+    cudaEvent_t ev_copied[kDepth] = {};
+    bool ev_used[kDepth] = {};
+    std::deque<std::pair<cudaEvent_t, std::vector<uint64_t>>> pending; // completion events
+    Arena tile_alloc;
+    uint32_t tiles_cap = 0;
+    std::vector<uint32_t> free_runs;
+    std::vector<uint64_t> active;
+    uint64_t iter = 0;
+    uint64_t rays = 0; // last read of the lane's ray counter
+
+    // streams (of the given priority), tables, lists and events; the path state for `tiles`
+    // whole tiles of m slots is allocated separately (Workspace, a cr_status)
+    cudaError_t create(uint32_t tiles, int priority) {
+        tiles_cap = tiles;
+        tile_alloc.init(tiles);
+        for (uint32_t i = kMaxRuns; i-- > 0;) free_runs.push_back(i);
+        cudaError_t e = cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, priority);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&copy_stream, cudaStreamNonBlocking, priority);
+        for (uint32_t p = 0; p < kDepth && e == cudaSuccess; ++p) {
+            e = cudaMalloc(&d_table[p], sizeof(JobDev) * kMaxRuns);
+            if (e == cudaSuccess) e = cudaMalloc(&d_lists[p], 4ull * kListWords);
+            if (e == cudaSuccess) e = cudaMallocHost(&h_table[p], sizeof(JobDev) * kMaxRuns);
+            if (e == cudaSuccess) e = cudaMallocHost(&h_lists[p], 4ull * kListWords);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_iter[p], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_copied[p], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaMallocHost(&h_counts, 2 * sizeof(uint64_t));
+        if (e == cudaSuccess) std::memset(h_counts, 0, 2 * sizeof(uint64_t));
+        return e;
+    }
+    // after the streams are drained; frees whatever create allocated
+    void destroy() {
+        for (auto& pe : pending) cudaEventDestroy(pe.first);
+        pending.clear();
+        for (uint32_t p = 0; p < kDepth; ++p) {
+            if (d_table[p]) cudaFree(d_table[p]);
+            if (d_lists[p]) cudaFree(d_lists[p]);
+            if (h_table[p]) cudaFreeHost(h_table[p]);
+            if (h_lists[p]) cudaFreeHost(h_lists[p]);
+            if (ev_iter[p]) cudaEventDestroy(ev_iter[p]);
+            if (ev_copied[p]) cudaEventDestroy(ev_copied[p]);
+        }
+        if (h_counts) cudaFreeHost(h_counts);
+        ws.release();
+        if (stream) cudaStreamDestroy(stream);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+    }
+    // the next iteration's buffer set is free (the iteration kDepth before it has completed)
+    bool ready() const {
+        const uint32_t set = (uint32_t)(iter % kDepth);
+        return !ev_used[set] || cudaEventQuery(ev_iter[set]) != cudaErrorNotReady;
+    }
+};
+
 } // namespace
 } // namespace cr
 
@@ -101,29 +178,15 @@ struct cr_server {
     PlanOpts po;
     ExecOpts eo;
     int device = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t copy_stream = nullptr; // job-table uploads, off the render stream
-    Workspace ws;
-    // device job tables and launch lists, kDepth sets used round robin by the iterations in
-    // flight, and their pinned host sources; the scene table
-    JobDev* d_table[kDepth] = {};
-    uint32_t* d_lists[kDepth] = {};
-    JobDev* h_table[kDepth] = {};
-    uint32_t* h_lists[kDepth] = {};
+    Lane lanes[2];            // 0 main, 1 express (used when opts.express_rays != 0)
+    uint32_t n_lanes = 1;
     SceneDev* d_scenes = nullptr;
-    uint64_t* h_counts = nullptr; // pinned, per set: (rays traced at bounces >= 1, queue error word)
-    cudaEvent_t ev_iter[kDepth] = {};
-    cudaEvent_t ev_copied[kDepth] = {};
-    bool ev_used[kDepth] = {};
-    std::deque<std::pair<cudaEvent_t, std::vector<uint64_t>>> pending; // completion events
     std::vector<cudaEvent_t> event_pool;
     float4* arena = nullptr;  // accumulation (16 B per pixel)
     uint32_t arena_px = 0;
     float* staging = nullptr; // host-output staging (12 B per pixel)
     uint32_t staging_px = 0;
-    Arena alloc, stg_alloc, tile_alloc;
-    uint32_t tiles_cap = 0;
-    std::vector<uint32_t> free_runs;
+    Arena alloc, stg_alloc;
     std::vector<const cr_scene*> scene_list;
     bool scenes_dirty = false;
     uint64_t budget = 0, used = 0;
@@ -131,8 +194,7 @@ struct cr_server {
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
     std::map<uint64_t, SJob> jobs;
-    std::vector<uint64_t> active;
-    uint64_t next_id = 1, iter = 0;
+    uint64_t next_id = 1;
     bool stop = false;
     cr_status fatal = CR_OK;
     std::string fatal_msg;
@@ -145,13 +207,16 @@ struct cr_server {
     }
     void loop();
     void admit_locked();
-    void poll_completions(bool wait_oldest);
+    bool admit_to_locked(SJob& j, uint32_t lane);
+    bool poll_completions(Lane& L, bool wait_oldest);
     void release_job_locked(SJob& j);
-    bool iterate(LaunchCount& lc);
+    bool iterate(Lane& L, LaunchCount& lc);
+    size_t active_count() const { return lanes[0].active.size() + lanes[1].active.size(); }
 };
 
 // Admit queued jobs (in arrival order, later ones may backfill) while their slots,
-// accumulation and staging ranges and a job-table entry fit.  Called with the lock held.
+// accumulation and staging ranges and a job-table entry fit.  A job of at most express_rays
+// ray steps tries the express lane first, then the main one.  Called with the lock held.
 void cr_server::admit_locked() {
     for (auto it = queue.begin(); it != queue.end();) {
         SJob& j = jobs[*it];
@@ -161,21 +226,8 @@ void cr_server::admit_locked() {
             ++it; // the scene table is full: wait until it can be rebuilt
             continue;
         }
-        uint32_t st = 0, px = 0, sg = 0;
-        // at most half the job table is held by active jobs: a job that ends a sample takes a
-        // second entry for its next one in the same iteration
-        if (active.size() >= kMaxRuns / 2 || !tile_alloc.alloc(j.tiles, st)) {
-            ++it;
-            continue;
-        }
-        if (!alloc.alloc(j.npx, px)) {
-            tile_alloc.release(st, j.tiles);
-            ++it;
-            continue;
-        }
-        if (j.host_out && !stg_alloc.alloc(j.npx, sg)) {
-            tile_alloc.release(st, j.tiles);
-            alloc.release(px, j.npx);
+        const bool express = n_lanes > 1 && j.ray_steps <= opts.express_rays;
+        if (!(express && admit_to_locked(j, 1)) && !admit_to_locked(j, 0)) {
             ++it;
             continue;
         }
@@ -184,54 +236,95 @@ void cr_server::admit_locked() {
             scenes_dirty = true;
         }
         j.scene_idx = scene_idx;
-        j.slot_tile = st;
-        j.px_base = px;
-        j.stg_at = sg;
-        if (j.host_out) j.d_out = staging + 3ull * sg;
-        j.run = free_runs.back();
-        free_runs.pop_back();
         j.step = 0;
         j.done = 0;
         j.state = 1;
         j.t_admit = now_ms();
         used += j.footprint;
-        active.push_back(j.id);
+        lanes[j.lane].active.push_back(j.id);
         it = queue.erase(it);
     }
 }
 
-// Free a job's slot, accumulation and staging ranges.  Later iterations on the stream run
-// after its last sum (and its output copy), so the ranges can go to other jobs at once.
-void cr_server::release_job_locked(SJob& j) {
-    tile_alloc.release(j.slot_tile, j.tiles);
-    alloc.release(j.px_base, j.npx);
-    if (j.host_out) stg_alloc.release(j.stg_at, j.npx);
-    used -= j.footprint;
-    free_runs.push_back(j.run);
+// Take the job's slot tiles in `lane`, its accumulation and staging ranges and a job-table
+// entry, or nothing.
+bool cr_server::admit_to_locked(SJob& j, uint32_t lane) {
+    Lane& L = lanes[lane];
+    uint32_t st = 0, px = 0, sg = 0;
+    // at most half the job table is held by active jobs: a job that ends a sample takes a
+    // second entry for its next one in the same iteration
+    if (L.active.size() >= kMaxRuns / 2 || !L.tile_alloc.alloc(j.tiles, st)) return false;
+    if (!alloc.alloc(j.npx, px)) {
+        L.tile_alloc.release(st, j.tiles);
+        return false;
+    }
+    if (j.host_out && !stg_alloc.alloc(j.npx, sg)) {
+        L.tile_alloc.release(st, j.tiles);
+        alloc.release(px, j.npx);
+        return false;
+    }
+    j.lane = lane;
+    j.slot_tile = st;
+    j.px_base = px;
+    j.stg_at = sg;
+    if (j.host_out) j.d_out = staging + 3ull * sg;
+    j.run = L.free_runs.back();
+    L.free_runs.pop_back();
+    return true;
 }
 
-// Mark the jobs of completed iterations done (their outputs are where the caller asked).
-void cr_server::poll_completions(bool wait_oldest) {
+// Free a job's slot, accumulation and staging ranges.  Later iterations on its lane's stream
+// run after its last sum (and its output copy), so the ranges can go to other jobs at once:
+// the accumulation and staging ranges may go to a job of the other lane only after the
+// job's completion event has passed, which release_job_locked's caller ensures for them by
+// freeing those ranges when the job completes (state 4 -> 2).
+void cr_server::release_job_locked(SJob& j) {
+    Lane& L = lanes[j.lane];
+    L.tile_alloc.release(j.slot_tile, j.tiles);
+    L.free_runs.push_back(j.run);
+    if (n_lanes == 1) { // one stream: every later launch is ordered after the job's last sum
+        alloc.release(j.px_base, j.npx);
+        if (j.host_out) stg_alloc.release(j.stg_at, j.npx);
+        used -= j.footprint;
+        j.shared_freed = true;
+    }
+}
+
+// Ranges of the shared arenas a completed job still holds (two lanes: freed on completion).
+static void release_shared_locked(cr_server& s, SJob& j) {
+    if (j.shared_freed) return;
+    s.alloc.release(j.px_base, j.npx);
+    if (j.host_out) s.stg_alloc.release(j.stg_at, j.npx);
+    s.used -= j.footprint;
+    j.shared_freed = true;
+}
+
+// Mark the jobs of the lane's completed iterations done (their outputs are where the caller
+// asked).  Returns true if an event was retired.
+bool cr_server::poll_completions(Lane& L, bool wait_oldest) {
+    bool any = false;
     while (true) {
         cudaEvent_t ev = nullptr;
         {
             std::lock_guard<std::mutex> lk(mu);
-            if (pending.empty()) return;
-            ev = pending.front().first;
+            if (L.pending.empty()) return any;
+            ev = L.pending.front().first;
         }
         cudaError_t e = wait_oldest ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
         wait_oldest = false;
-        if (e == cudaErrorNotReady) return;
+        if (e == cudaErrorNotReady) return any;
+        any = true;
         std::vector<uint64_t> ids;
         {
             std::lock_guard<std::mutex> lk(mu);
-            ids = std::move(pending.front().second);
-            pending.pop_front();
+            ids = std::move(L.pending.front().second);
+            L.pending.pop_front();
             event_pool.push_back(ev);
             const double t = now_ms();
             for (uint64_t id : ids) {
                 auto it = jobs.find(id);
                 if (it == jobs.end()) continue;
+                release_shared_locked(*this, it->second);
                 if (e == cudaSuccess) {
                     it->second.state = 2;
                 } else {
@@ -254,13 +347,13 @@ void cr_server::poll_completions(bool wait_oldest) {
 // One iteration of the rolling wavefront: shade (every job at its own step), sum the samples
 // that end, generate the rays of the samples that start, trace every queued ray.  Returns
 // false when no job is active.
-bool cr_server::iterate(LaunchCount& lc) {
-    const uint32_t par = (uint32_t)(iter & 1u);            // group queue read at this iteration
-    const uint32_t set = (uint32_t)(iter % kDepth);        // table, lists and counters of this iteration
-    if (ev_used[set]) cudaEventSynchronize(ev_iter[set]); // iteration iter - kDepth freed this set
+bool cr_server::iterate(Lane& L, LaunchCount& lc) {
+    const uint32_t par = (uint32_t)(L.iter & 1u);            // group queue read at this iteration
+    const uint32_t set = (uint32_t)(L.iter % kDepth);        // table, lists and counters of this iteration
+    if (L.ev_used[set]) cudaEventSynchronize(L.ev_iter[set]); // iteration iter - kDepth freed this set
     const uint32_t m = po.tile_w * po.tile_h, K = po.k ? po.k : m;
-    JobDev* tab = h_table[set];
-    uint32_t* fin_job = h_lists[set];
+    JobDev* tab = L.h_table[set];
+    uint32_t* fin_job = L.h_lists[set];
     uint32_t* fin_pre = fin_job + kMaxRuns;
     uint32_t* st_job = fin_job + 2 * kMaxRuns;
     uint32_t* st_pre = fin_job + 3 * kMaxRuns;
@@ -271,33 +364,34 @@ bool cr_server::iterate(LaunchCount& lc) {
     std::map<uint64_t, uint32_t> next_run;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (ev_used[set] && set == 0) { // what iteration iter - kDepth read back
-            stats.secondary_rays = std::max<uint64_t>(stats.secondary_rays, h_counts[0]);
-            const uint32_t err = (uint32_t)h_counts[1];
+        if (L.ev_used[set] && set == 0) { // what iteration iter - kDepth read back
+            L.rays = std::max<uint64_t>(L.rays, L.h_counts[0]);
+            stats.secondary_rays = lanes[0].rays + lanes[1].rays;
+            const uint32_t err = (uint32_t)L.h_counts[1];
             if (err != 0u && fatal == CR_OK) {
                 fatal = (err & 2u) ? CR_ERR_TIMEOUT : CR_ERR_CUDA;
                 fatal_msg = (err & 2u) ? "a ray-sort wait ran out" : "a ray or group queue overflowed";
             }
         }
         if (fatal != CR_OK) { // fail what is left
-            for (uint64_t id : active) {
+            for (uint64_t id : L.active) {
                 SJob& j = jobs[id];
                 j.state = 3;
                 j.status = fatal;
                 j.t_done = now_ms();
                 release_job_locked(j);
             }
-            active.clear();
+            L.active.clear();
             cv_done.notify_all();
             return false;
         }
-        if (active.empty()) return false;
+        if (L.active.empty()) return false;
         if (scenes_dirty) {
             for (const cr_scene* sc : scene_list) scene_tab.push_back(scene_entry(*dev_scene_of(sc), po.bvh8));
             scenes_dirty = false;
             upload_scenes = true;
         }
-        for (uint64_t id : active) {
+        for (uint64_t id : L.active) {
             SJob& j = jobs[id];
             const uint32_t B = j.job.max_bounces;
             JobDev d = job_dev(j.job, po, j.scene_idx, j.done);
@@ -322,8 +416,8 @@ bool cr_server::iterate(LaunchCount& lc) {
                 fin_pre[n_fin++] = fin_slots;
                 fin_slots += j.slots;
                 if (j.done + 1 < j.job.spp) {
-                    const uint32_t nr = free_runs.back();
-                    free_runs.pop_back();
+                    const uint32_t nr = L.free_runs.back();
+                    L.free_runs.pop_back();
                     JobDev d2 = job_dev(j.job, po, j.scene_idx, j.done + 1);
                     d2.out = j.d_out;
                     d2.px_base = j.px_base;
@@ -343,27 +437,27 @@ bool cr_server::iterate(LaunchCount& lc) {
             }
         }
     }
-    PathBuffers& b = ws.pb;
+    PathBuffers& b = L.ws.pb;
     b.n_groups = b.n_slots / K;
     b.accum = arena;
-    // the uploads run on the copy stream (this set's device buffers were last read by
+    // the uploads run on the lane's copy stream (this set's device buffers were last read by
     // iteration iter - kDepth, which has completed), overlapping the iterations in flight;
     // the render stream waits for them before this iteration's first launch
-    cudaMemcpyAsync(d_table[set], tab, sizeof(JobDev) * (max_run + 1), cudaMemcpyHostToDevice, copy_stream);
+    cudaMemcpyAsync(L.d_table[set], tab, sizeof(JobDev) * (max_run + 1), cudaMemcpyHostToDevice, L.copy_stream);
     if (n_fin) {
-        cudaMemcpyAsync(d_lists[set], fin_job, 4ull * n_fin, cudaMemcpyHostToDevice, copy_stream);
-        cudaMemcpyAsync(d_lists[set] + kMaxRuns, fin_pre, 4ull * n_fin, cudaMemcpyHostToDevice, copy_stream);
+        cudaMemcpyAsync(L.d_lists[set], fin_job, 4ull * n_fin, cudaMemcpyHostToDevice, L.copy_stream);
+        cudaMemcpyAsync(L.d_lists[set] + kMaxRuns, fin_pre, 4ull * n_fin, cudaMemcpyHostToDevice, L.copy_stream);
     }
     if (n_start) {
-        cudaMemcpyAsync(d_lists[set] + 2 * kMaxRuns, st_job, 4ull * n_start, cudaMemcpyHostToDevice, copy_stream);
-        cudaMemcpyAsync(d_lists[set] + 3 * kMaxRuns, st_pre, 4ull * n_start, cudaMemcpyHostToDevice, copy_stream);
+        cudaMemcpyAsync(L.d_lists[set] + 2 * kMaxRuns, st_job, 4ull * n_start, cudaMemcpyHostToDevice, L.copy_stream);
+        cudaMemcpyAsync(L.d_lists[set] + 3 * kMaxRuns, st_pre, 4ull * n_start, cudaMemcpyHostToDevice, L.copy_stream);
     }
-    cudaEventRecord(ev_copied[set], copy_stream);
-    cudaStreamWaitEvent(stream, ev_copied[set], 0);
+    cudaEventRecord(L.ev_copied[set], L.copy_stream);
+    cudaStreamWaitEvent(L.stream, L.ev_copied[set], 0);
     if (upload_scenes) // append-only: entries in-flight iterations read do not change
         cudaMemcpy(d_scenes, scene_tab.data(), sizeof(SceneDev) * scene_tab.size(), cudaMemcpyHostToDevice);
     PassArgs P;
-    P.jobs = d_table[set];
+    P.jobs = L.d_table[set];
     P.n_jobs = max_run + 1;
     P.scenes = d_scenes;
     P.tile_w = po.tile_w;
@@ -374,30 +468,30 @@ bool cr_server::iterate(LaunchCount& lc) {
     P.rolling = true;
     P.accum_mode = 3u;
     uint32_t* qn = b.counts + 8 + 2 * (par ^ 1u); // (rays, groups) appended for the next iteration
-    cudaMemsetAsync(qn, 0, 8, stream);
-    launch_shade_rolling(P, b, par, n_groups, stream, lc);
-    launch_shadow_rolling(P, b, par, n_groups, po.bvh8, stream, lc);
+    cudaMemsetAsync(qn, 0, 8, L.stream);
+    launch_shade_rolling(P, b, par, n_groups, L.stream, lc);
+    launch_shadow_rolling(P, b, par, n_groups, po.bvh8, L.stream, lc);
     if (n_fin) {
-        P.launch_job = d_lists[set];
-        P.launch_prefix = d_lists[set] + kMaxRuns;
+        P.launch_job = L.d_lists[set];
+        P.launch_prefix = L.d_lists[set] + kMaxRuns;
         P.n_launch = n_fin;
-        launch_finish_rolling(P, b, fin_slots, stream, lc);
+        launch_finish_rolling(P, b, fin_slots, L.stream, lc);
     }
     {
         std::lock_guard<std::mutex> lk(mu);
         for (uint64_t id : host_copies) {
             SJob& j = jobs[id];
-            cudaMemcpyAsync(j.job.out_rgb, j.d_out, 12ull * j.npx, cudaMemcpyDeviceToHost, stream);
+            cudaMemcpyAsync(j.job.out_rgb, j.d_out, 12ull * j.npx, cudaMemcpyDeviceToHost, L.stream);
         }
     }
     if (n_start) {
-        P.launch_job = d_lists[set] + 2 * kMaxRuns;
-        P.launch_prefix = d_lists[set] + 3 * kMaxRuns;
+        P.launch_job = L.d_lists[set] + 2 * kMaxRuns;
+        P.launch_prefix = L.d_lists[set] + 3 * kMaxRuns;
         P.n_launch = n_start;
         P.queue_counts = qn;
         P.ray_queue = b.ray_queue;
         P.group_queue_out = b.group_queue + (size_t)(par ^ 1u) * b.n_groups;
-        launch_raygen_rolling(P, b, start_tiles, stream, lc);
+        launch_raygen_rolling(P, b, start_tiles, L.stream, lc);
     }
     if (trace_max) {
         TraceArgs ta;
@@ -412,18 +506,18 @@ bool cr_server::iterate(LaunchCount& lc) {
         ta.queue = b.ray_queue;
         ta.queue_count = qn;
         ta.n_max = trace_max;
-        if (sort) ta.queue = launch_morton_sort(P, b, par ^ 1u, eo.sort_key, stream, lc);
-        launch_trace(ta, stream, lc);
+        if (sort) ta.queue = launch_morton_sort(P, b, par ^ 1u, eo.sort_key, L.stream, lc);
+        launch_trace(ta, L.stream, lc);
     }
     // the ray total and the error word, read back every kDepth-th iteration (the copies
     // would otherwise sit between the kernels of consecutive iterations)
     if (set == 0) {
-        cudaMemcpyAsync(&h_counts[0], reinterpret_cast<unsigned long long*>(b.counts + kStatWord) + 1, 8,
-                        cudaMemcpyDeviceToHost, stream);
-        cudaMemcpyAsync(&h_counts[1], b.counts + kQueueErrWord, 4, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(&L.h_counts[0], reinterpret_cast<unsigned long long*>(b.counts + kStatWord) + 1, 8,
+                        cudaMemcpyDeviceToHost, L.stream);
+        cudaMemcpyAsync(&L.h_counts[1], b.counts + kQueueErrWord, 4, cudaMemcpyDeviceToHost, L.stream);
     }
-    cudaEventRecord(ev_iter[set], stream);
-    ev_used[set] = true;
+    cudaEventRecord(L.ev_iter[set], L.stream);
+    L.ev_used[set] = true;
     cudaError_t e = cudaGetLastError();
     std::lock_guard<std::mutex> lk(mu);
     if (e != cudaSuccess && fatal == CR_OK) {
@@ -438,12 +532,12 @@ bool cr_server::iterate(LaunchCount& lc) {
         } else {
             cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         }
-        cudaEventRecord(ev, stream);
-        pending.push_back({ev, completing});
+        cudaEventRecord(ev, L.stream);
+        L.pending.push_back({ev, completing});
     }
     // advance every job by one bounce step
     std::vector<uint64_t> keep;
-    for (uint64_t id : active) {
+    for (uint64_t id : L.active) {
         SJob& j = jobs[id];
         if (j.step <= j.job.max_bounces) {
             j.step++;
@@ -453,7 +547,7 @@ bool cr_server::iterate(LaunchCount& lc) {
         j.done++;
         auto nr = next_run.find(id);
         if (nr != next_run.end()) {
-            free_runs.push_back(j.run);
+            L.free_runs.push_back(j.run);
             j.run = nr->second;
             j.step = 1;
             keep.push_back(id);
@@ -462,37 +556,55 @@ bool cr_server::iterate(LaunchCount& lc) {
             release_job_locked(j);
         }
     }
-    active.swap(keep);
+    L.active.swap(keep);
     stats.passes++;
     stats.kernel_launches = lc.n;
-    iter++;
+    L.iter++;
     return true;
 }
 
+// The host thread: admit, then enqueue one iteration of every lane whose next buffer set is
+// free (the express lane first); when no lane can take one, wait briefly (or, with nothing
+// active, for the oldest completion).
 void cr_server::loop() {
     cudaSetDevice(device);
     LaunchCount lc;
     while (true) {
-        poll_completions(false);
-        bool idle = false;
+        for (uint32_t l = 0; l < n_lanes; ++l) poll_completions(lanes[l], false);
+        bool any_active = false, any_pending = false;
         {
             std::unique_lock<std::mutex> lk(mu);
             if (stop) break;
             if (fatal == CR_OK) admit_locked();
-            idle = active.empty();
-            if (idle && pending.empty()) {
+            for (uint32_t l = 0; l < n_lanes; ++l) {
+                any_active = any_active || !lanes[l].active.empty();
+                any_pending = any_pending || !lanes[l].pending.empty();
+            }
+            if (!any_active && !any_pending) {
                 cv_work.wait_for(lk, std::chrono::milliseconds(5));
                 continue;
             }
         }
-        if (idle) { // nothing to launch: wait for the oldest completion
-            poll_completions(true);
+        if (!any_active) { // nothing to launch: wait for the oldest completion of a lane
+            for (uint32_t l = n_lanes; l-- > 0;)
+                if (poll_completions(lanes[l], true)) break;
             continue;
         }
-        const double tb = now_ms();
-        iterate(lc);
-        std::lock_guard<std::mutex> lk(mu);
-        stats.busy_ms += now_ms() - tb;
+        bool launched = false;
+        for (uint32_t l = n_lanes; l-- > 0;) { // express lane (1) first
+            Lane& L = lanes[l];
+            bool has;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                has = !L.active.empty();
+            }
+            if (!has || (n_lanes > 1 && !L.ready())) continue;
+            const double tb = now_ms();
+            launched = iterate(L, lc) || launched;
+            std::lock_guard<std::mutex> lk(mu);
+            stats.busy_ms += now_ms() - tb;
+        }
+        if (!launched) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
@@ -521,69 +633,54 @@ extern "C" cr_status cr_server_create(const cr_server_opts* o, cr_server** out) 
     s->eo.block = o->block ? (int)o->block : 128;
     s->eo.block_secondary = o->block ? (int)o->block : kSecondaryBlock;
     s->budget = o->hbm_budget;
-    // the budget is split once: 60% path state (whole tiles of slots), 25% the accumulation
-    // arena (16 B per pixel of every admitted job), 15% output staging for jobs with host
-    // outputs (12 B per pixel)
+    s->n_lanes = o->express_rays ? 2u : 1u;
+    // the budget is split once: 60% path state (whole tiles of slots; an express lane takes
+    // 1/8 of them), 25% the accumulation arena (16 B per pixel of every admitted job), 15%
+    // output staging for jobs with host outputs (12 B per pixel)
     const uint64_t slots = std::min<uint64_t>(o->hbm_budget * 6 / 10 / kSlotBytes, 1ull << 27);
-    s->tiles_cap = (uint32_t)(slots / m);
+    const uint32_t tiles = (uint32_t)(slots / m);
+    const uint32_t tiles_express = s->n_lanes > 1 ? tiles / 8 : 0u;
+    if (tiles_express == 0) s->n_lanes = 1; // a budget too small to split
     s->arena_px = (uint32_t)std::min<uint64_t>(o->hbm_budget / 4 / 16, 1ull << 28);
     s->staging_px = (uint32_t)std::min<uint64_t>(o->hbm_budget * 15 / 100 / 12, 1ull << 28);
     cudaGetDevice(&s->device);
-    auto bad = [&](cudaError_t e, const char* what) {
-        cudaGetLastError();
-        set_last_error(what);
-        return e == cudaErrorMemoryAllocation ? CR_ERR_OOM : CR_ERR_CUDA;
-    };
     cr_server* r = s.get();
-    // releases whatever was allocated before a failure
-    auto cleanup = [r]() {
-        for (uint32_t p = 0; p < kDepth; ++p) {
-            if (r->d_table[p]) cudaFree(r->d_table[p]);
-            if (r->d_lists[p]) cudaFree(r->d_lists[p]);
-            if (r->h_table[p]) cudaFreeHost(r->h_table[p]);
-            if (r->h_lists[p]) cudaFreeHost(r->h_lists[p]);
-            if (r->ev_iter[p]) cudaEventDestroy(r->ev_iter[p]);
-            if (r->ev_copied[p]) cudaEventDestroy(r->ev_copied[p]);
-        }
+    auto cleanup = [r]() { // releases whatever was allocated before a failure
+        for (Lane& L : r->lanes) L.destroy();
         if (r->d_scenes) cudaFree(r->d_scenes);
-        if (r->h_counts) cudaFreeHost(r->h_counts);
         if (r->arena) cudaFree(r->arena);
         if (r->staging) cudaFree(r->staging);
-        if (r->stream) cudaStreamDestroy(r->stream);
-        if (r->copy_stream) cudaStreamDestroy(r->copy_stream);
     };
-    cudaError_t e = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->copy_stream, cudaStreamNonBlocking);
+    int lo_pri = 0, hi_pri = 0; // numerically lower is the higher priority
+    cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
+    cudaError_t e = r->lanes[0].create(tiles - tiles_express, lo_pri);
+    if (e == cudaSuccess && r->n_lanes > 1) e = r->lanes[1].create(tiles_express, hi_pri);
     if (e == cudaSuccess) e = cudaMalloc(&r->arena, 16ull * r->arena_px);
     if (e == cudaSuccess) e = cudaMalloc(&r->staging, 12ull * r->staging_px);
-    for (uint32_t p = 0; p < kDepth && e == cudaSuccess; ++p) {
-        e = cudaMalloc(&r->d_table[p], sizeof(JobDev) * kMaxRuns);
-        if (e == cudaSuccess) e = cudaMalloc(&r->d_lists[p], 4ull * kListWords);
-        if (e == cudaSuccess) e = cudaMallocHost(&r->h_table[p], sizeof(JobDev) * kMaxRuns);
-        if (e == cudaSuccess) e = cudaMallocHost(&r->h_lists[p], 4ull * kListWords);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_iter[p], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_copied[p], cudaEventDisableTiming);
-    }
     if (e == cudaSuccess) e = cudaMalloc(&r->d_scenes, sizeof(SceneDev) * kMaxScenes);
-    if (e == cudaSuccess) e = cudaMallocHost(&r->h_counts, 2 * kDepth * sizeof(uint64_t));
     if (e != cudaSuccess) {
-        cr_status st = bad(e, "cr_server_create: device allocation failed");
+        cudaGetLastError();
+        set_last_error("cr_server_create: device allocation failed");
         cleanup();
-        return st;
+        return e == cudaErrorMemoryAllocation ? CR_ERR_OOM : CR_ERR_CUDA;
     }
-    std::memset(r->h_counts, 0, 2 * kDepth * sizeof(uint64_t));
-    cr_status st = r->ws.ensure(r->tiles_cap * m, 1);
-    if (st == CR_OK) st = r->ws.ensure_nee(r->tiles_cap * m);
-    if (st == CR_OK && cudaMemset(r->ws.pb.counts, 0, 4 * kCountsWords) != cudaSuccess)
-        st = bad(cudaErrorUnknown, "cr_server_create: clearing the counters failed");
+    cr_status st = CR_OK;
+    for (uint32_t l = 0; l < r->n_lanes && st == CR_OK; ++l) {
+        Workspace& ws = r->lanes[l].ws;
+        st = ws.ensure(r->lanes[l].tiles_cap * m, 1);
+        if (st == CR_OK) st = ws.ensure_nee(r->lanes[l].tiles_cap * m);
+        if (st == CR_OK && cudaMemset(ws.pb.counts, 0, 4 * kCountsWords) != cudaSuccess) {
+            cudaGetLastError();
+            set_last_error("cr_server_create: clearing the counters failed");
+            st = CR_ERR_CUDA;
+        }
+    }
     if (st != CR_OK) {
         cleanup();
         return st;
     }
     r->alloc.init(r->arena_px);
     r->stg_alloc.init(r->staging_px);
-    r->tile_alloc.init(r->tiles_cap);
-    for (uint32_t i = kMaxRuns; i-- > 0;) r->free_runs.push_back(i);
     std::memset(&r->stats, 0, sizeof(r->stats));
     r->t0 = std::chrono::steady_clock::now();
     r->th = std::thread([r] { r->loop(); });
@@ -621,12 +718,13 @@ extern "C" cr_status cr_server_submit(cr_server* s, const cr_job* job, uint64_t*
     j.tiles = tx * ty;
     j.slots = j.tiles * m;
     j.footprint = 16ull * j.npx + (j.host_out ? 12ull * j.npx : 0) + kSlotBytes * j.slots;
+    j.ray_steps = (uint64_t)j.npx * job->spp * (job->max_bounces + 1ull);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal != CR_OK) {
         set_last_error("cr_server_submit: the server stopped after a device error");
         return s->fatal;
     }
-    if (j.tiles > s->tiles_cap || j.npx > s->arena_px || (j.host_out && j.npx > s->staging_px)) {
+    if (j.tiles > s->lanes[0].tiles_cap || j.npx > s->arena_px || (j.host_out && j.npx > s->staging_px)) {
         set_last_error("cr_server_submit: job larger than the server's device budget");
         return CR_ERR_OOM;
     }
@@ -687,7 +785,7 @@ extern "C" cr_status cr_server_get_stats(cr_server* s, cr_server_stats* out) {
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
     out->queued = (uint32_t)s->queue.size();
-    out->active = (uint32_t)s->active.size();
+    out->active = (uint32_t)s->active_count();
     out->used_bytes = s->used;
     return CR_OK;
 }
@@ -700,25 +798,15 @@ extern "C" cr_status cr_server_destroy(cr_server* s) {
     }
     s->cv_work.notify_all();
     if (s->th.joinable()) s->th.join();
-    cudaStreamSynchronize(s->stream);
-    cudaStreamSynchronize(s->copy_stream);
-    for (auto& pe : s->pending) cudaEventDestroy(pe.first);
-    for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
-    for (uint32_t p = 0; p < kDepth; ++p) {
-        cudaFree(s->d_table[p]);
-        cudaFree(s->d_lists[p]);
-        cudaFreeHost(s->h_table[p]);
-        cudaFreeHost(s->h_lists[p]);
-        cudaEventDestroy(s->ev_iter[p]);
-        cudaEventDestroy(s->ev_copied[p]);
+    for (Lane& L : s->lanes) {
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        if (L.copy_stream) cudaStreamSynchronize(L.copy_stream);
     }
+    for (Lane& L : s->lanes) L.destroy();
+    for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
     cudaFree(s->d_scenes);
-    cudaFreeHost(s->h_counts);
-    s->ws.release();
     cudaFree(s->arena);
     cudaFree(s->staging);
-    cudaStreamDestroy(s->stream);
-    cudaStreamDestroy(s->copy_stream);
     delete s;
     return CR_OK;
 }

@@ -43,12 +43,14 @@ def _requests(rng, n):
     return out
 
 
-@pytest.mark.parametrize("bvh", [1, 2])
-def test_results_equal_standalone_in_the_mix(cr, world, bvh):
+@pytest.mark.parametrize("bvh,express", [(1, 0), (2, 0), (1, 40_000), (2, 40_000)])
+def test_results_equal_standalone_in_the_mix(cr, world, bvh, express):
+    """With an express lane, the requests of at most 40,000 ray steps (about a third of this
+    mix) render in the second wavefront; every result is still its stand-alone render."""
     sc, S = world
     rng = np.random.default_rng(bvh)
     reqs = _requests(rng, 24)
-    srv = cr.cr_server_create(512 << 20, tile=(8, 8), k=8, bvh=bvh)
+    srv = cr.cr_server_create(512 << 20, tile=(8, 8), k=8, bvh=bvh, express_rays=express)
     try:
         ids, outs = [], []
         for i, r in enumerate(reqs):
@@ -67,6 +69,9 @@ def test_results_equal_standalone_in_the_mix(cr, world, bvh):
         steps = [r["spp"] * (r["B"] + 1) + 1 for r in reqs]
         assert st["jobs_done"] == len(reqs) and st["passes"] >= max(steps)
         assert st["passes"] < sum(steps)  # jobs shared launches
+        if express:
+            small = [r["w"] * r["h"] * r["spp"] * (r["B"] + 1) <= express for r in reqs]
+            assert 0 < sum(small) < len(reqs)
         for r, out, l in zip(reqs, outs, lat):
             cam = _cam(sc[r["name"]].camera, r["w"], r["h"])
             ref, _ = S[r["name"]].render(cam, spp=r["spp"], max_bounces=r["B"], mode=r["mode"], tile=(8, 8), k=8,
@@ -138,3 +143,36 @@ def test_a_request_joins_between_bounce_launches(cr, world):
         assert torch.equal(big, ref)
     finally:
         cr.cr_server_destroy(srv)
+
+
+def test_express_lane_shortens_small_jobs_beside_a_large_one(cr, world):
+    """A small request submitted while a large many-bounce job renders: in the main lane it
+    takes one bounce step per iteration of the large job's wavefront; in the express lane its
+    steps run in their own wavefront on a higher-priority stream.  The same request, with the
+    same large job beside it, renders at least twice as fast with the express lane, still
+    finishes before the large job, and its output is the same."""
+    sc, S = world
+    big_cam = _cam(sc["interior"].camera, 1024, 1024)
+    small_cam = _cam(sc["tiny"].camera, 64, 64)
+    render_ms = {}
+    for express in (0, 1 << 20):
+        srv = cr.cr_server_create(2 << 30, tile=(8, 8), k=8, express_rays=express)
+        try:
+            big = torch.empty((1024, 1024, 3), device="cuda")
+            bid = cr.cr_server_submit(srv, cr.make_job(S["interior"].handle, big_cam, big, spp=24, max_bounces=16,
+                                                       seed=3))
+            time.sleep(0.02)  # the big job is rendering
+            small = torch.empty((64, 64, 3), device="cuda")
+            sid = cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, small_cam, small, spp=4, max_bounces=3,
+                                                       seed=5))
+            s_st = cr.cr_server_wait(srv, sid, 60000)
+            b_st = cr.cr_server_wait(srv, bid, 60000)
+            assert s_st["t_done_ms"] < b_st["t_done_ms"]
+            render_ms[express] = s_st["t_done_ms"] - s_st["t_admit_ms"]
+            ref, _ = S["tiny"].render(small_cam, spp=4, max_bounces=3, tile=(8, 8), k=8, seed=5)
+            assert torch.equal(small, ref)
+        finally:
+            cr.cr_server_destroy(srv)
+    print(f"small job render time beside a large one: main lane {render_ms[0]:.2f} ms, "
+          f"express lane {render_ms[1 << 20]:.2f} ms")
+    assert render_ms[1 << 20] < 0.5 * render_ms[0]
