@@ -394,7 +394,7 @@ typedef struct {
 
 typedef struct {
     uint64_t jobs_submitted, jobs_done;
-    uint64_t passes;           /* iterations of the rolling wavefront (one bounce step of every active job) */
+    uint64_t passes;           /* iterations of the rolling wavefronts (one bounce step of every active job of a lane) */
     uint64_t secondary_rays, kernel_launches, used_bytes;
     double busy_ms;            /* host time spent enqueueing iterations (up to four run ahead of the GPU) */
     uint32_t queued, active;

@@ -273,11 +273,11 @@ bool cr_server::admit_to_locked(SJob& j, uint32_t lane) {
     return true;
 }
 
-// Free a job's slot, accumulation and staging ranges.  Later iterations on its lane's stream
-// run after its last sum (and its output copy), so the ranges can go to other jobs at once:
-// the accumulation and staging ranges may go to a job of the other lane only after the
-// job's completion event has passed, which release_job_locked's caller ensures for them by
-// freeing those ranges when the job completes (state 4 -> 2).
+// Free a job's slots and job-table entry once its last sum is enqueued: later iterations on
+// its lane's stream run after that sum (and its output copy), so they can go to other jobs
+// of the lane at once.  The accumulation and staging ranges are shared by the lanes; with
+// one lane they are freed here too, with two only when the job's completion event has
+// passed (release_shared_locked), since the other lane's stream is not ordered after it.
 void cr_server::release_job_locked(SJob& j) {
     Lane& L = lanes[j.lane];
     L.tile_alloc.release(j.slot_tile, j.tiles);
