@@ -978,7 +978,7 @@ def batched_leg(cr, scenes, rank, args):
     return res
 
 
-EXPRESS_RAYS = 1 << 22  # ray steps (pixels x spp x (bounces + 1)) of the serving leg's express requests
+EXPRESS_RAYS = 1 << 26  # ray steps (pixels x spp x (bounces + 1)) of the serving leg's express requests
 
 
 def serving_leg(cr, scenes, args):
