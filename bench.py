@@ -317,8 +317,9 @@ def run_ours(args):
     # the headline metric is the landscape's
     sc = scenes.landscape() if args.scene == "landscape" else scenes.interior()
     workload = WORKLOAD if args.scene == "landscape" else "interior 1280x720 (512,014 tris), 1 spp, B=2, 8x8 K=8"
-    # a "+bvh8q" mode traces through the 8-wide quantised BVH (profiling its kernel)
-    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | (cr.CR_BVH8Q if "+bvh8q" in args.modes else 0))
+    # a "+bvh8q" ("+bvh4") mode traces through the 8-wide quantised (4-wide FP32) BVH
+    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | (cr.CR_BVH8Q if "+bvh8q" in args.modes else 0) |
+                 (cr.CR_BVH4 if "+bvh4" in args.modes else 0))
     cam = sc.camera
     out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
@@ -331,13 +332,16 @@ def run_ours(args):
 
     def parse(mode):
         # "morton_sort:<key>" selects a reordering key (Table 1 comparators); a "+<variant>"
-        # suffix selects a traversal variant of the secondary trace, "+bvh8q" the BVH8-Q
+        # suffix selects a traversal variant of the secondary trace, "+bvh8q" the BVH8-Q and
+        # "+bvh4" the BVH4 for every closest-hit trace
         mode, *variants = mode.split("+")
         m, _, key = mode.partition(":")
         flags, bvh = 0, cr.CR_BVH2
         for v in variants:
             if v == "bvh8q":
                 bvh = cr.CR_BVH8Q
+            elif v == "bvh4":
+                bvh = cr.CR_BVH4
             else:
                 flags |= variant_flags[v]
         return m, key or "two_point", flags, bvh
@@ -496,34 +500,38 @@ def run_ours(args):
     # (coherence); the DRAM traffic the kernel really causes is the "traffic" key (ncu).
     # ncu shows the kernel bound by instruction issue (7-8 active lanes per warp
     # instruction), so the issue and FP32-ALU roofs are reported beside it.
-    # With "+bvh8q" first, the figures describe k_trace_bvh8 instead: 80 B and 8 box tests per
-    # node visit, and no ncu-derived keys (the committed summary is the BVH2 kernel's).
-    bvh8 = parse(modes[0])[3] == cr.CR_BVH8Q
+    # With "+bvh8q" ("+bvh4") first, the figures describe k_trace_bvh8 (k_trace_bvh4) instead:
+    # 80 B and 8 box tests (112 B and 4) per node visit, and no ncu-derived keys (the committed
+    # summary is the BVH2 kernel's).
+    layout0 = parse(modes[0])[3]
+    plain = layout0 == cr.CR_BVH2
+    node_b = {cr.CR_BVH2: 64, cr.CR_BVH8Q: 80, cr.CR_BVH4: 112}
+    boxes = {cr.CR_BVH2: 2, cr.CR_BVH8Q: 8, cr.CR_BVH4: 4}
     launches = BOUNCES
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count  # cudaDevAttrMultiProcessorCount
 
-    def node_bytes_per_ray(res, wide=False):
-        return 32 + 4 + 8 + (80 if wide else 64) * res["nodes_per_ray"] + 48 * res["tris_per_ray"]
+    def node_bytes_per_ray(res, layout=cr.CR_BVH2):
+        return 32 + 4 + 8 + node_b[layout] * res["nodes_per_ray"] + 48 * res["tris_per_ray"]
 
     rays_per_launch = R["secondary_rays_per_step"] / launches
     ms_per_launch = R["ms_trace_secondary"] / launches
-    ops_per_ray = (8 if bvh8 else 2) * 24 * R["nodes_per_ray"] + 40 * R["tris_per_ray"]
+    ops_per_ray = boxes[layout0] * 24 * R["nodes_per_ray"] + 40 * R["tris_per_ray"]
     achieved_ops = ops_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e12
     clk = (clocks or {}).get("sm_mhz") or 2070.0
     peak_ops = n_sm * 128 * clk * 1e6 / 1e12
-    bytes_per_ray = node_bytes_per_ray(R, bvh8)
+    bytes_per_ray = node_bytes_per_ray(R, layout0)
     achieved = bytes_per_ray * rays_per_launch / (ms_per_launch / 1e3) / 1e9
     peak, peak_kind = load_peaks()
-    traffic = None if bvh8 else profile_traffic()
+    traffic = profile_traffic() if plain else None
     l2_gbs = l2_read_bandwidth(cr)
     # every mode's node-byte rate on the same roof (trace-only secondary rays/s x its own bytes
     # per ray), and its ratio to independent sampling's: the coherence gain read off one roof
     per_mode = {}
     for m in modes:
-        wide = parse(m)[3] == cr.CR_BVH8Q
-        ach_m = node_bytes_per_ray(results[m], wide) * results[m]["trace_mrays"] * 1e6 / 1e9
+        lay = parse(m)[3]
+        ach_m = node_bytes_per_ray(results[m], lay) * results[m]["trace_mrays"] * 1e6 / 1e9
         per_mode[m] = {"achieved": round(ach_m, 1), "frac": round(ach_m / peak, 4),
-                       "bytes_per_ray": round(node_bytes_per_ray(results[m], wide), 1)}
+                       "bytes_per_ray": round(node_bytes_per_ray(results[m], lay), 1)}
     if "independent" in per_mode:
         for m in per_mode:
             per_mode[m]["frac_vs_independent"] = round(per_mode[m]["frac"] / per_mode["independent"]["frac"], 4)
@@ -544,7 +552,7 @@ def run_ours(args):
         "gpu_launches": int(R["launches_per_step"] * args.steps),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": f"k_trace_{'bvh8' if bvh8 else 'bvh2'} (secondary rays)",
+                     "kernel": f"k_trace_{ {cr.CR_BVH2: 'bvh2', cr.CR_BVH8Q: 'bvh8', cr.CR_BVH4: 'bvh4'}[layout0]} (secondary rays)",
                      "bytes_per_ray": round(bytes_per_ray, 1), "rays_per_launch": round(rays_per_launch),
                      "ms_per_launch": round(ms_per_launch, 5),
                      "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
@@ -555,7 +563,7 @@ def run_ours(args):
                          "unit": "TOP/s (FP32 ALU operations)", "frac": round(achieved_ops / peak_ops, 4),
                          "ops_per_ray": round(ops_per_ray, 1),
                          "peak_source": f"{n_sm} SMs (device attribute) x 128 FP32 lanes x {clk:.0f} MHz (sampled)"},
-        "roofline_issue": None if bvh8 else issue_roof(R, clk, n_sm),
+        "roofline_issue": issue_roof(R, clk, n_sm) if plain else None,
         "roofline_l2": {"achieved": round(achieved, 1), "peak": round(l2_gbs, 1), "unit": "GB/s",
                         "frac": round(achieved / l2_gbs, 4),
                         "peak_source": "cr_measure_l2_read: read-only kernel over an L2-resident 48 MB buffer, CUDA events",
@@ -646,17 +654,18 @@ def _timed_renders(cr, S, cam, out, stream, steps, warmup, frame0=0, **kw):
 
 def precision_leg(cr, scenes, rank, world, args):
     """Interior (1280x720, 512,014 triangles, 16 spp, 4 bounces, direction reuse): FP32 BVH2
-    vs the 8-bit quantised BVH8-Q; the images must be identical bit for bit."""
+    vs the 8-bit quantised BVH8-Q and the FP32 4-wide BVH4; the images must be identical bit
+    for bit."""
     import torch
     sc = scenes.interior()
-    S8 = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
+    S8 = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q | cr.CR_BVH4)
     cam = sc.camera
     out = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     res = {"workload": "interior 1280x720, 2,000 UV spheres + room + ceiling light (512,014 tris), 16 spp, "
                        "4 bounces, direction_reuse 8x8 K=8", "scene_bytes": S8.info["device_bytes"]}
     imgs = {}
-    for name, bvh in (("bvh2", cr.CR_BVH2), ("bvh8q", cr.CR_BVH8Q)):
+    for name, bvh in (("bvh2", cr.CR_BVH2), ("bvh8q", cr.CR_BVH8Q), ("bvh4", cr.CR_BVH4)):
         ms, tr, sec = _timed_renders(cr, S8, cam, out, stream, 3, 2, frame0=rank * 100, spp=16, bounces=4, k=K,
                                      bvh=bvh)
         ms = aggregate(ms, "max")
@@ -666,8 +675,8 @@ def precision_leg(cr, scenes, rank, world, args):
         o = cr.make_opts(k=K, frame_base=0, bvh=bvh, stream=stream)
         cr.cr_render_ex(S8.handle, cam, 16, 4, "direction_reuse", 8, 8, out, o)
         imgs[name] = out.clone()
-    res["images_bit_identical"] = bool(torch.equal(imgs["bvh2"], imgs["bvh8q"]))
-    res["nodes"] = {"bvh2": S8.info["n_nodes2"], "bvh8q": S8.info["n_nodes8"]}
+    res["images_bit_identical"] = bool(torch.equal(imgs["bvh2"], imgs["bvh8q"]) and torch.equal(imgs["bvh2"], imgs["bvh4"]))
+    res["nodes"] = {"bvh2": S8.info["n_nodes2"], "bvh8q": S8.info["n_nodes8"], "bvh4": S8.info["n_nodes4"]}
     S8.close()
     return res
 

@@ -80,19 +80,20 @@ typedef struct {
     float radiance[3]; /* constant environment radiance seen by rays that miss */
 } cr_env;
 
-enum { CR_BVH2 = 1u, CR_BVH8Q = 2u };
+enum { CR_BVH2 = 1u, CR_BVH8Q = 2u, CR_BVH4 = 4u };
 
 typedef struct cr_scene cr_scene;
 
 /* Build a device-resident scene: an SAH BVH2 (exact sweep up to 1024 triangles, 32 bins
  * above, SAH-chosen leaves of <= 4 triangles, depth <= 64) on the host, optionally collapsed into 8-wide nodes with 8-bit
  * conservatively quantised child boxes (bvh_flags & CR_BVH8Q; Ylitie et al. 2017, cited
- * in Sec. 2.3), then uploaded once.
+ * in Sec. 2.3) and/or into 4-wide nodes that keep the BVH2's FP32 boxes (bvh_flags &
+ * CR_BVH4; both give the BVH2's closest hits), then uploaded once.
  *   tri_xyz  host, n_tri * 9 floats: v0.xyz v1.xyz v2.xyz per triangle; all finite.
  *   tri_mat  host, n_tri material indices < n_mat.
  *   mats     host, n_mat materials.
  *   env      host, may be NULL (black).
- *   bvh_flags CR_BVH2 (always built) | CR_BVH8Q.
+ *   bvh_flags CR_BVH2 (always built) | CR_BVH8Q | CR_BVH4.
  *   out      receives the handle; destroy it with cr_scene_destroy.
  * The inputs are copied; the caller may free them when the call returns.
  * Errors: CR_ERR_INVALID_ARG (n_tri == 0 or > 2^28, NaN/Inf vertex, material index or
@@ -113,6 +114,7 @@ typedef struct {
     double build_ms;           /* host build time */
     float bounds_lo[3], bounds_hi[3];
     float light_area;          /* total emitter area: float running sum of the areas (below) */
+    uint32_t n_nodes4, depth4; /* BVH4 nodes and depth (0 if not built) */
 } cr_scene_info;
 
 cr_status cr_scene_get_info(const cr_scene* scene, cr_scene_info* info);
@@ -206,7 +208,8 @@ typedef struct {
     uint64_t seed;         /* Philox key */
     uint32_t frame_base;   /* frame index of the first sample (progressive rendering) */
     uint32_t reuse_depth;  /* reuse at bounces b <= reuse_depth; 0 = every bounce */
-    uint32_t bvh;          /* CR_BVH2 (default) or CR_BVH8Q (scene must have it) */
+    uint32_t bvh;          /* CR_BVH2 (default), CR_BVH8Q or CR_BVH4 (scene must have it; with
+                              CR_BVH4 shadow rays stay on the BVH2) */
     uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 for
                             * primary rays and 64 for secondary rays */
     uint32_t flags;        /* CR_OPT_* */

@@ -24,7 +24,7 @@ LIB_PATH = os.environ.get("CR_LIB") or os.path.join(_PKG, "libcr.so")
 CR_OK, CR_ERR_INVALID_ARG, CR_ERR_OOM, CR_ERR_CUDA, CR_ERR_TIMEOUT, CR_ERR_STACK_OVERFLOW, CR_ERR_BUSY, \
     CR_ERR_NOT_FOUND = range(8)
 CR_MAT_LAMBERT, CR_MAT_GGX, CR_MAT_MIRROR, CR_MAT_EMITTER, CR_MAT_DIELECTRIC, CR_MAT_TRANSLUCENT = range(6)
-CR_BVH2, CR_BVH8Q = 1, 2
+CR_BVH2, CR_BVH8Q, CR_BVH4 = 1, 2, 4
 CR_INDEPENDENT, CR_MORTON_SORT, CR_DIRECTION_REUSE, CR_WORLD_REUSE = 0, 1, 2, 3
 CR_OPT_STATS, CR_OPT_COUNT, CR_OPT_NO_SYNC, CR_OPT_PERSISTENT, CR_OPT_SPECULATIVE = 1, 2, 4, 8, 16
 CR_OPT_PACKET_PRIMARY, CR_OPT_PACKET_SECONDARY, CR_OPT_TWO_PHASE = 32, 64, 128
@@ -55,7 +55,7 @@ class cr_scene_info(C.Structure):
     _fields_ = [("n_tri", C.c_uint32), ("n_mat", C.c_uint32), ("n_nodes2", C.c_uint32), ("depth2", C.c_uint32),
                 ("n_nodes8", C.c_uint32), ("n_lights", C.c_uint32), ("device_bytes", C.c_uint64),
                 ("build_ms", C.c_double), ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3),
-                ("light_area", C.c_float)]
+                ("light_area", C.c_float), ("n_nodes4", C.c_uint32), ("depth4", C.c_uint32)]
 
 
 class cr_camera(C.Structure):

@@ -15,7 +15,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcr.so")
 # the debug build: every node, triangle and material index checked in the kernels (CR_DEBUG=1)
 LIB_DEBUG = os.path.join(PKG, "libcr_debug.so")
-SOURCES = ["trace.cu", "trace_bvh8.cu", "path.cu", "cr_api.cpp", "bvh_build.cpp", "bvh8_build.cpp", "trace_static.cu", "server.cpp", "probe.cu"]
+SOURCES = ["trace.cu", "trace_bvh8.cu", "path.cu", "cr_api.cpp", "bvh_build.cpp", "bvh8_build.cpp", "trace_static.cu", "server.cpp", "probe.cu", "trace_bvh4.cu", "bvh4_build.cpp"]
 HEADERS = ["cr_internal.h", "device_math.cuh", "trace_common.cuh", "debug_checks.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -119,6 +119,7 @@ struct cr_scene {
     cr_scene_info info;
     void* d_nodes2 = nullptr;
     void* d_nodes8 = nullptr;
+    void* d_nodes4 = nullptr;
     void* d_tris = nullptr;
     void* d_tris8 = nullptr;
     void* d_mats = nullptr;
@@ -177,7 +178,8 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     if (!tri_xyz || !tri_mat || !mats) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: NULL array");
     if (n_tri == 0 || n_tri > (1u << 28)) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: n_tri=%u out of range", n_tri);
     if (n_mat == 0) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: n_mat is 0");
-    if (bvh_flags & ~(uint32_t)(CR_BVH2 | CR_BVH8Q)) return fail(CR_ERR_INVALID_ARG, "cr_scene_create: bad bvh_flags");
+    if (bvh_flags & ~(uint32_t)(CR_BVH2 | CR_BVH8Q | CR_BVH4))
+        return fail(CR_ERR_INVALID_ARG, "cr_scene_create: bad bvh_flags");
     for (size_t i = 0; i < 9 * (size_t)n_tri; ++i)
         if (!std::isfinite(tri_xyz[i]))
             return fail(CR_ERR_INVALID_ARG, "cr_scene_create: vertex coordinate %zu of triangle %zu is not finite", i % 9,
@@ -246,6 +248,17 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
             o[11] = 0.0f;
         }
     }
+    HostBVH4 b4;
+    if (bvh_flags & CR_BVH4) {
+        try {
+            b4 = build_bvh4(b2);
+        } catch (const std::bad_alloc&) {
+            return fail(CR_ERR_OOM, "cr_scene_create: host allocation during BVH4 build");
+        }
+        if (b4.stack_bound > kBvh4StackCapacity)
+            return fail(CR_ERR_STACK_OVERFLOW, "cr_scene_create: BVH4 needs a %u-entry stack (> %u)", b4.stack_bound,
+                        kBvh4StackCapacity);
+    }
     std::vector<float> mt(8 * (size_t)n_mat);
     for (uint32_t m = 0; m < n_mat; ++m) {
         int32_t ty = (int32_t)mats[m].type;
@@ -301,6 +314,11 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
         CR_CUDA(cudaMemcpy(dn8.p, b8.nodes.data(), dn8.bytes, cudaMemcpyHostToDevice));
         CR_CUDA(cudaMemcpy(dt8.p, tris8.data(), dt8.bytes, cudaMemcpyHostToDevice));
     }
+    DevMem dn4;
+    if (bvh_flags & CR_BVH4) {
+        CR_CUDA(dn4.alloc(b4.nodes.size() * sizeof(float)));
+        CR_CUDA(cudaMemcpy(dn4.p, b4.nodes.data(), dn4.bytes, cudaMemcpyHostToDevice));
+    }
     DevMem dl;
     const uint32_t n_lights = (uint32_t)lcdf.size();
     if (n_lights) {
@@ -321,7 +339,10 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     s->d_mats = dm.p;
     s->d_nodes8 = dn8.p;
     s->d_tris8 = dt8.p;
-    dn.p = dt.p = dm.p = dn8.p = dt8.p = nullptr;
+    s->d_nodes4 = dn4.p;
+    dn.p = dt.p = dm.p = dn8.p = dt8.p = dn4.p = nullptr;
+    s->dev.nodes4 = static_cast<const float4*>(s->d_nodes4);
+    s->dev.n_nodes4 = b4.n_nodes;
     s->dev.nodes8 = static_cast<const uint4*>(s->d_nodes8);
     s->dev.tris8 = static_cast<const float4*>(s->d_tris8);
     s->dev.nodes2 = static_cast<const float4*>(s->d_nodes2);
@@ -353,8 +374,10 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
     s->info.n_nodes2 = b2.n_nodes;
     s->info.depth2 = b2.depth;
     s->info.n_nodes8 = b8.n_nodes;
+    s->info.n_nodes4 = b4.n_nodes;
+    s->info.depth4 = b4.depth;
     s->info.device_bytes = b2.nodes.size() * 4 + tris.size() * 4 + mt.size() * 4 + b8.nodes.size() * 4 + tris8.size() * 4 +
-                           lrec.size() * 4 + lcdf.size() * 4;
+                           b4.nodes.size() * 4 + lrec.size() * 4 + lcdf.size() * 4;
     s->info.n_lights = n_lights;
     s->info.light_area = s->dev.light_total;
     s->info.build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -381,6 +404,7 @@ extern "C" cr_status cr_scene_destroy(cr_scene* s) {
     free_workspace(s);
     if (s->d_nodes2) cudaFree(s->d_nodes2);
     if (s->d_nodes8) cudaFree(s->d_nodes8);
+    if (s->d_nodes4) cudaFree(s->d_nodes4);
     if (s->d_tris) cudaFree(s->d_tris);
     if (s->d_tris8) cudaFree(s->d_tris8);
     if (s->d_mats) cudaFree(s->d_mats);
@@ -659,6 +683,7 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
     plan.m = m;
     plan.k = K;
     plan.bvh8 = po.bvh8;
+    plan.bvh4 = po.bvh4;
     // scene table
     std::vector<const cr_scene*> uniq;
     std::vector<uint32_t> scene_idx(n_jobs);
@@ -668,6 +693,8 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
         if (st != CR_OK) return st;
         if (po.bvh8 && !jobs[i].scene->dev.nodes8)
             return fail(CR_ERR_INVALID_ARG, "job %u: the scene has no BVH8-Q (create it with CR_BVH8Q)", i);
+        if (po.bvh4 && !jobs[i].scene->dev.nodes4)
+            return fail(CR_ERR_INVALID_ARG, "job %u: the scene has no BVH4 (create it with CR_BVH4)", i);
         uint32_t k = 0;
         while (k < uniq.size() && uniq[k] != jobs[i].scene) ++k;
         if (k == uniq.size()) uniq.push_back(jobs[i].scene);
@@ -784,6 +811,7 @@ cr_status enqueue_plan(const RenderPlan& p, const Plan& dev, Workspace& ws, cons
     ta.speculative = eo.speculative;
     ta.work_counter = b.counts + 2;
     ta.bvh8 = p.bvh8;
+    ta.bvh4 = p.bvh4;
     ta.scenes = dev.d_scenes;
     ta.slot_scene = b.slot_scene;
     double dummy = 0.0;
@@ -877,8 +905,8 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     cr_render_opts o;
     cr_render_opts_default(&o);
     if (opts_in) o = *opts_in;
-    const bool use8 = o.bvh == CR_BVH8Q;
-    if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8) || (use8 && !s->dev.nodes8))
+    const bool use8 = o.bvh == CR_BVH8Q, use4 = o.bvh == CR_BVH4;
+    if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8 && !use4) || (use8 && !s->dev.nodes8) || (use4 && !s->dev.nodes4))
         return fail(CR_ERR_INVALID_ARG, "cr_render: bvh %u not available for this scene", o.bvh);
     const int block = o.block ? (int)o.block : 128;
     if (block % 32 != 0 || block < 32 || block > 512) return fail(CR_ERR_INVALID_ARG, "cr_render: block %d", block);
@@ -922,6 +950,7 @@ extern "C" cr_status cr_render_ex(cr_scene* s, const cr_camera* cam, uint32_t sp
     po.k = o.k;
     po.interleave = o.interleave;
     po.bvh8 = use8;
+    po.bvh4 = use4;
     if (o.tile_begin != 0 || o.tile_end != 0) {
         po.tile_begin = o.tile_begin;
         po.tile_end = o.tile_end;
@@ -1077,8 +1106,8 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     cr_render_opts o;
     cr_render_opts_default(&o);
     if (opts_in) o = *opts_in;
-    const bool use8 = o.bvh == CR_BVH8Q;
-    if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8) || (use8 && !s->dev.nodes8))
+    const bool use8 = o.bvh == CR_BVH8Q, use4 = o.bvh == CR_BVH4;
+    if ((o.bvh != CR_BVH2 && o.bvh != 0 && !use8 && !use4) || (use8 && !s->dev.nodes8) || (use4 && !s->dev.nodes4))
         return fail(CR_ERR_INVALID_ARG, "cr_trace_rays: bvh %u not available", o.bvh);
     const float4* tris = use8 ? s->dev.tris8 : s->dev.tris;
     const int block = o.block ? (int)o.block : 128;
@@ -1109,6 +1138,7 @@ extern "C" cr_status cr_trace_rays(cr_scene* s, const float* rays, const int32_t
     ta.packet = (o.flags & (CR_OPT_PACKET_PRIMARY | CR_OPT_PACKET_SECONDARY)) != 0;
     ta.any_hit = (o.flags & CR_OPT_ANY_HIT) != 0;
     ta.bvh8 = use8;
+    ta.bvh4 = use4;
     ta.scenes = dev_scene_entry(s, use8);
     ta.slot_scene = nullptr;
     ta.work_counter = wc.as<uint32_t>();

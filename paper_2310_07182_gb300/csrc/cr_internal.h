@@ -53,6 +53,21 @@ struct HostBVH8 {
     uint32_t stack_bound = 0;         // largest traversal stack a ray can need (the depth)
 };
 HostBVH8 build_bvh8q(const HostBVH2& b2, const float* tri_xyz);
+// BVH4: the BVH2 collapsed into 4-wide nodes with FP32 child boxes, 32 floats (128 B) per node:
+//   floats 0-3 lo.x of children 0-3, 4-7 hi.x, 8-11 lo.y, 12-15 hi.y, 16-19 lo.z, 20-23 hi.z,
+//   24-27 child links as int bits (>= 0 BVH4 node, < 0 BVH2 leaf code, kBvh4Empty unused), 28-31 0.
+// Boxes and leaves are the BVH2's (same triangle records); the root is node 0.  An unused
+// slot's planes are NaN: the slab test's far distance is then NaN and the box is never entered.
+constexpr uint32_t kBvh4NodeFloats = 32;
+constexpr int32_t kBvh4Empty = 0x7fffffff;
+struct HostBVH4 {
+    std::vector<float> nodes;
+    uint32_t n_nodes = 0;
+    uint32_t depth = 0;
+    uint32_t stack_bound = 0; // largest traversal stack a ray can need (three per level)
+};
+HostBVH4 build_bvh4(const HostBVH2& b2);
+constexpr uint32_t kBvh4StackCapacity = 96; // traversal stack entries of the BVH4 kernel
 constexpr uint32_t kBvh2StackCapacity = 64; // traversal stack entries of the BVH2 kernels (> tree depth)
 constexpr uint32_t kBvh8StackCapacity = 48; // traversal stack entries of the BVH8-Q kernel (one per level)
 void check_bvh2(const HostBVH2& b, const float* v, uint32_t n_tri, uint32_t& covered, uint32_t& violations);
@@ -63,6 +78,7 @@ void check_bvh8(const HostBVH8& b, const float* v, uint32_t n_tri, uint32_t& cov
 struct DevScene {
     const float4* nodes2 = nullptr; // 4 per node
     const uint4* nodes8 = nullptr;  // 5 per node
+    const float4* nodes4 = nullptr; // 8 per node (BVH4, if built)
     const float4* tris = nullptr;   // 3 per triangle in leaf order: v0|orig, v1|mat, v2|0
     const float4* tris8 = nullptr;  // the same records in BVH8-Q leaf order (if built)
     const float4* mats = nullptr;   // 2 per material: (type bits, albedo), (roughness, emission)
@@ -74,7 +90,7 @@ struct DevScene {
     const float4* lights = nullptr;   // 4 per emitter: v0|orig, v1|0, v2|0, emission|0
     uint32_t n_lights = 0;
     float light_total = 0.0f;
-    uint32_t n_nodes2 = 0, n_nodes8 = 0;
+    uint32_t n_nodes2 = 0, n_nodes8 = 0, n_nodes4 = 0;
     uint32_t* err = nullptr; // device word: index checks that failed (debug builds)
 };
 
@@ -82,6 +98,7 @@ struct DevScene {
 struct SceneDev {
     const float4* nodes2;
     const uint4* nodes8;
+    const float4* nodes4; // BVH4 (with the BVH2's triangle records), or NULL
     const float4* tris;
     const float4* mats;
     float env[4];
@@ -203,8 +220,10 @@ struct TraceArgs {
     bool two_phase = false;   // budgeted traversal, compaction of unfinished rays, resume (BVH2)
     PhaseBuffers phase;
     bool bvh8 = false;
+    bool bvh4 = false; // closest hits through the BVH4 (any-hit queries stay on the BVH2)
 };
 void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
+void launch_trace_bvh4(const TraceArgs& a, cudaStream_t st, LaunchCount& lc);
 // Map leaf-order triangle indices of hits to original indices and split (prim, t).
 void launch_hits_to_user(const float4* tris, const int2* hit, uint32_t n, int32_t* prim, float* t,
                          cudaStream_t st, LaunchCount& lc);
@@ -330,6 +349,7 @@ size_t workspace_bytes(uint32_t n_slots, uint32_t npx);
 struct PlanOpts {
     uint32_t tile_w = 8, tile_h = 8, k = 0, interleave = 1;
     bool bvh8 = false;
+    bool bvh4 = false; // closest-hit traces through the BVH4 (single renders; shadow rays stay on the BVH2)
     uint32_t tile_begin = 0, tile_end = 0; // single-job plans: render only these tiles (0, 0 = all)
 };
 struct Pass {
@@ -338,6 +358,7 @@ struct Pass {
 struct RenderPlan {
     uint32_t tile_w = 0, tile_h = 0, m = 0, k = 0;
     bool bvh8 = false, sort = false;
+    bool bvh4 = false;
     bool nee = false; // some job uses next-event estimation
     uint32_t max_bounces = 0, max_slots = 0, npx_total = 0;
     std::vector<JobDev> jobs;     // all passes' tables, pass by pass

@@ -648,6 +648,7 @@ SceneDev scene_entry(const DevScene& s, bool bvh8) {
     SceneDev e;
     e.nodes2 = s.nodes2;
     e.nodes8 = s.nodes8;
+    e.nodes4 = s.nodes4;
     e.tris = bvh8 ? s.tris8 : s.tris;
     e.mats = s.mats;
     for (int k = 0; k < 3; ++k) {
@@ -674,6 +675,10 @@ void launch_trace(const TraceArgs& a, cudaStream_t st, LaunchCount& lc) {
     const size_t smem128 = (size_t)kSmemStack * 128 * sizeof(uint32_t);
     if (a.bvh8) { // BVH8-Q kernels (trace_bvh8.cu)
         launch_trace_bvh8(a, st, lc);
+        return;
+    }
+    if (a.bvh4 && !a.any_hit) { // BVH4 kernel (trace_bvh4.cu)
+        launch_trace_bvh4(a, st, lc);
         return;
     }
     if (a.any_hit) { // visibility queries (cr_trace_rays with CR_OPT_ANY_HIT)

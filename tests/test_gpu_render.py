@@ -209,6 +209,25 @@ def test_bvh8q_render_identical(cr, orc):
     _check(b.cpu().numpy(), ref, max_taint=0.1)
 
 
+@pytest.mark.parametrize("mode,nee", [("direction_reuse", False), ("direction_reuse", True), ("independent", False),
+                                      ("morton_sort", False), ("world_reuse", False)])
+def test_bvh4_render_identical(cr, mode, nee):
+    """The 4-wide BVH (the BVH2's FP32 boxes, four children per node) renders the same image
+    bit for bit as the BVH2 in every mode; with next-event estimation its shadow rays stay on
+    the BVH2.  A scene built without it refuses the option."""
+    sc = scenes.interior(width=160, height=96)
+    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH4)
+    assert 0 < S.info["n_nodes4"] < S.info["n_nodes2"] and 0 < S.info["depth4"] <= S.info["depth2"]
+    kw = dict(spp=3, max_bounces=4, mode=mode, tile=(8, 8), k=8, seed=5, nee=nee)
+    a, sa = S.render(bvh=cr.CR_BVH2, stats=True, **kw)
+    b, sb = S.render(bvh=cr.CR_BVH4, stats=True, **kw)
+    assert torch.equal(a, b) and sa["secondary_rays"] == sb["secondary_rays"]
+    plain = cr.Scene(scenes.tiny())
+    with pytest.raises(cr.CrError) as ei:
+        plain.render(bvh=cr.CR_BVH4)
+    assert ei.value.status == cr.CR_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("key", ["two_point", "origin", "reis", "costa", "aila_compact", "hierarchy_cut"])
 def test_every_sort_key_gives_the_independent_image(cr, orc, key):
     """Reordering only changes the order rays are traced in (Table 1 comparators)."""

@@ -138,13 +138,16 @@ def test_landscape_full_size_sample(cr, orc):
     assert np.all(_t_close(t[sel][hit], t_ref[hit], terr[hit]))
 
 
+@pytest.mark.parametrize("layout", ["bvh8q", "bvh4"])
 @pytest.mark.parametrize("name", ["tiny", "interior", "furnace"])
-def test_bvh8q_hits_identical_to_bvh2(cr, orc, name):
-    """The 8-bit quantised wide BVH only enlarges boxes (conservative rounding), so closest
-    hits equal the FP32 BVH2's bit for bit, on every ray."""
+def test_wide_bvh_hits_identical_to_bvh2(cr, orc, name, layout):
+    """The 8-bit quantised wide BVH only enlarges boxes (conservative rounding), and the
+    4-wide BVH keeps the BVH2's boxes and leaves, so closest hits equal the FP32 BVH2's bit
+    for bit, on every ray."""
     sc = getattr(scenes, name)() if name != "interior" else scenes.interior(n_spheres=400)
-    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
-    assert S.info["n_nodes8"] > 0
+    wide = cr.CR_BVH8Q if layout == "bvh8q" else cr.CR_BVH4
+    S = cr.Scene(sc, bvh_flags=cr.CR_BVH2 | wide)
+    assert S.info["n_nodes8" if layout == "bvh8q" else "n_nodes4"] > 0
     lo = np.min(sc.tri_xyz.reshape(-1, 3), axis=0)
     hi = np.max(sc.tri_xyz.reshape(-1, 3), axis=0)
     rng = np.random.default_rng(3)
@@ -160,12 +163,12 @@ def test_bvh8q_hits_identical_to_bvh2(cr, orc, name):
     rays_t = torch.from_numpy(rays).cuda()
     skip = torch.from_numpy(np.where(rng.random(n) < 0.2, rng.integers(0, sc.n_tri, n), -1).astype(np.int32)).cuda()
     p2, t2 = S.trace(rays_t, skip, bvh=cr.CR_BVH2)
-    p8, t8 = S.trace(rays_t, skip, bvh=cr.CR_BVH8Q)
+    p8, t8 = S.trace(rays_t, skip, bvh=wide)
     assert torch.equal(p2, p8) and torch.equal(t2.view(torch.int32), t8.view(torch.int32))
     assert 0.05 < float((p2 >= 0).float().mean()) < 0.99
     # and against the oracle on a sample of the unbounded rays (the oracle has no tmax)
     unb = np.isinf(rays[:, 7])
-    _compare(orc, sc, S, rays[unb][:4000], skip.cpu().numpy()[unb][:4000], bvh=cr.CR_BVH8Q)
+    _compare(orc, sc, S, rays[unb][:4000], skip.cpu().numpy()[unb][:4000], bvh=wide)
 
 
 def test_l2_read_probe(cr):
