@@ -465,15 +465,17 @@ cr_status cr_debug_sample(uint32_t kind, uint32_t n, const float* wo, const floa
                           float* wi, float* weight, uint8_t* valid);
 
 /* Host-only check of the BVH builders (no GPU needed): builds the BVH2 (and the BVH8-Q if
- * flags & CR_BVH8Q) for the triangles and verifies them by walking every root-to-leaf path:
- * each triangle must sit in exactly one leaf, and every box on its path (BVH8-Q boxes as the
- * kernel decodes them from 8-bit codes) must contain all three of its vertices. */
+ * flags & CR_BVH8Q, the BVH4 if flags & CR_BVH4) for the triangles and verifies them by
+ * walking every root-to-leaf path: each triangle must sit in a leaf, and every box on its
+ * path (BVH8-Q boxes as the kernel decodes them from 8-bit codes) must contain all three of
+ * its vertices; BVH4 slots must be used with finite planes or unused with NaN planes. */
 typedef struct {
     uint32_t n_nodes2, depth2, n_nodes8, depth8, stack_bound8;
-    uint32_t covered2, covered8;       /* triangles found in exactly one leaf */
+    uint32_t covered2, covered8;       /* triangles found in a leaf */
     uint32_t violations2, violations8; /* (triangle, ancestor box) pairs not containing it */
     uint32_t pad;
     double build_ms2, build_ms8;
+    uint32_t n_nodes4, depth4, stack_bound4, covered4, violations4, pad4;
 } cr_bvh_report;
 
 cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, uint32_t flags, cr_bvh_report* report);

@@ -80,7 +80,9 @@ class cr_bvh_report(C.Structure):
     _fields_ = [("n_nodes2", C.c_uint32), ("depth2", C.c_uint32), ("n_nodes8", C.c_uint32), ("depth8", C.c_uint32),
                 ("stack_bound8", C.c_uint32), ("covered2", C.c_uint32), ("covered8", C.c_uint32),
                 ("violations2", C.c_uint32), ("violations8", C.c_uint32), ("pad", C.c_uint32),
-                ("build_ms2", C.c_double), ("build_ms8", C.c_double)]
+                ("build_ms2", C.c_double), ("build_ms8", C.c_double), ("n_nodes4", C.c_uint32), ("depth4", C.c_uint32),
+                ("stack_bound4", C.c_uint32), ("covered4", C.c_uint32), ("violations4", C.c_uint32),
+                ("pad4", C.c_uint32)]
 
 
 class cr_debug(C.Structure):
@@ -424,7 +426,7 @@ def cr_measure_l2_read(nbytes=48 << 20, reps=100) -> float:
     return v.value
 
 
-def cr_debug_bvh_check(tri_xyz, flags=CR_BVH2 | CR_BVH8Q) -> dict:
+def cr_debug_bvh_check(tri_xyz, flags=CR_BVH2 | CR_BVH8Q | CR_BVH4) -> dict:
     tri_xyz = np.ascontiguousarray(tri_xyz, dtype=np.float32).reshape(-1, 9)
     r = cr_bvh_report()
     _check(lib().cr_debug_bvh_check(_ptr(tri_xyz), tri_xyz.shape[0], flags, C.byref(r)))

@@ -82,7 +82,72 @@ struct B4 {
     }
 };
 
+bool inside(const float* lo, const float* hi, const float* tri) {
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+            if (!(tri[3 * j + k] >= lo[k] && tri[3 * j + k] <= hi[k])) return false;
+    return true;
+}
+
 } // namespace
+
+// Walk every root-to-leaf path of the BVH4: each triangle must be reached (covered counts
+// the triangles reached at least once) and every box on its path must contain its three
+// vertices (violations counts the (triangle, box) pairs that do not); an unused slot must
+// carry kBvh4Empty and NaN planes, a used one finite planes (also counted as violations).
+void check_bvh4(const HostBVH4& b4, const HostBVH2& b2, const float* v, uint32_t n_tri, uint32_t& covered,
+                uint32_t& violations) {
+    std::vector<uint32_t> seen(n_tri, 0);
+    violations = 0;
+    std::vector<std::pair<uint32_t, std::vector<float>>> st;
+    if (b4.n_nodes) st.push_back({0u, {}});
+    while (!st.empty()) {
+        auto it = std::move(st.back());
+        st.pop_back();
+        const float* o = &b4.nodes[(size_t)it.first * kBvh4NodeFloats];
+        int32_t link[4];
+        std::memcpy(link, &o[24], sizeof(link));
+        for (int k = 0; k < 4; ++k) {
+            float lo[3], hi[3];
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = o[8 * a + k];
+                hi[a] = o[8 * a + 4 + k];
+            }
+            const bool planes_nan = std::isnan(lo[0]) && std::isnan(lo[1]) && std::isnan(lo[2]) && std::isnan(hi[0]) &&
+                                    std::isnan(hi[1]) && std::isnan(hi[2]);
+            if (link[k] == kBvh4Empty) {
+                if (!planes_nan) ++violations;
+                continue;
+            }
+            if (!(std::isfinite(lo[0]) && std::isfinite(lo[1]) && std::isfinite(lo[2]) && std::isfinite(hi[0]) &&
+                  std::isfinite(hi[1]) && std::isfinite(hi[2]))) {
+                ++violations;
+                continue;
+            }
+            std::vector<float> p = it.second;
+            p.insert(p.end(), lo, lo + 3);
+            p.insert(p.end(), hi, hi + 3);
+            if (link[k] >= 0) {
+                if ((uint32_t)link[k] >= b4.n_nodes) {
+                    ++violations;
+                    continue;
+                }
+                st.push_back({(uint32_t)link[k], std::move(p)});
+            } else {
+                const uint32_t code = (uint32_t)(~link[k]);
+                const uint32_t first = code >> 2, count = (code & 3u) + 1u;
+                for (uint32_t i = first; i < first + count && i < b2.leaf_order.size(); ++i) {
+                    const uint32_t t = b2.leaf_order[i];
+                    seen[t]++;
+                    for (size_t q = 0; q < p.size(); q += 6)
+                        if (!inside(&p[q], &p[q + 3], &v[9 * (size_t)t])) ++violations;
+                }
+            }
+        }
+    }
+    covered = 0;
+    for (uint32_t t = 0; t < n_tri; ++t) covered += seen[t] >= 1 ? 1u : 0u;
+}
 
 HostBVH4 build_bvh4(const HostBVH2& b2) {
     B4 b(b2);

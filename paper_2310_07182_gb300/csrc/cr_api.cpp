@@ -1318,6 +1318,13 @@ extern "C" cr_status cr_debug_bvh_check(const float* tri_xyz, uint32_t n_tri, ui
             rep->build_ms8 = std::chrono::duration<double, std::milli>(t3 - t2).count();
             check_bvh8(b8, tri_xyz, n_tri, rep->covered8, rep->violations8);
         }
+        if (flags & CR_BVH4) {
+            HostBVH4 b4 = build_bvh4(b2);
+            rep->n_nodes4 = b4.n_nodes;
+            rep->depth4 = b4.depth;
+            rep->stack_bound4 = b4.stack_bound;
+            check_bvh4(b4, b2, tri_xyz, n_tri, rep->covered4, rep->violations4);
+        }
     } catch (const std::bad_alloc&) {
         return fail(CR_ERR_OOM, "cr_debug_bvh_check: host allocation");
     }

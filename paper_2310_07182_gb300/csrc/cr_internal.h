@@ -67,6 +67,8 @@ struct HostBVH4 {
     uint32_t stack_bound = 0; // largest traversal stack a ray can need (three per level)
 };
 HostBVH4 build_bvh4(const HostBVH2& b2);
+void check_bvh4(const HostBVH4& b4, const HostBVH2& b2, const float* v, uint32_t n_tri, uint32_t& covered,
+                uint32_t& violations);
 constexpr uint32_t kBvh4StackCapacity = 96; // traversal stack entries of the BVH4 kernel
 constexpr uint32_t kBvh2StackCapacity = 64; // traversal stack entries of the BVH2 kernels (> tree depth)
 constexpr uint32_t kBvh8StackCapacity = 48; // traversal stack entries of the BVH8-Q kernel (one per level)
