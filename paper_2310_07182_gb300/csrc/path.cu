@@ -1279,7 +1279,7 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
 }
 
 // Arrive at the grid barrier whose completion is ctr == target and wait (bounded) for the
-// others.  Returns false, uniformly over the block, when the wait ran out.  The arrival is a
+// other participating blocks.  Returns false, uniformly over the block, when the wait ran out.  The arrival is a
 // release (it publishes every write the block made before its bar.sync, release being
 // cumulative) and the poll an acquire, so no full fence is needed on either side.
 __device__ __forceinline__ bool grid_barrier(uint32_t* ctr, uint32_t target, uint32_t* err, uint32_t* s_flag) {
@@ -1317,7 +1317,11 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_sort_coop(uint32_t* __restric
     const uint32_t n = min(*count, n_max);
     if (n == 0) return; // every block reads the same count: none waits at a barrier
     const uint32_t T = (n + kOsTile - 1) / kOsTile;
-    const uint32_t G = gridDim.x;
+    // the grid is sized for the largest count; with fewer live tiles the blocks past them
+    // leave at once (every block computes the same G), so they neither arrive at the
+    // barriers nor hold a chunk of the scan
+    const uint32_t G = min(gridDim.x, T);
+    if (blockIdx.x >= G) return;
     const bool resident = T <= G; // at most one tile per block: it stays in shared memory
     const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const size_t L = (size_t)kRadix * T;
