@@ -1883,10 +1883,9 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
     const uint32_t n_max = b.n_slots;
     const uint32_t* count = b.counts + 8 + 2 * bounce;
     uint32_t* ws = b.sort_hist;
-    const uint32_t sms = (uint32_t)sm_count();
-    k_morton<<<min((n_max + 511) / 512, 2 * sms), 512, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max,
-                                                                 p.scenes, b.slot_scene, key_kind, b.keys, b.vals,
-                                                                 b.vals + n_max, ws + kSortCtr);
+    // one thread per key: every queue entry's ray gather is in flight at once
+    k_morton<<<(n_max + 511) / 512, 512, 0, st>>>(b.ray_o, b.ray_d, b.ray_queue, count, n_max, p.scenes, b.slot_scene,
+                                                 key_kind, b.keys, b.vals, b.vals + n_max, ws + kSortCtr);
     lc.n++;
     launch_radix_passes(b.keys, b.vals, b.keys + n_max, b.vals + n_max, count, n_max, ws, b.counts + kQueueErrWord,
                         st, lc);
@@ -1898,8 +1897,7 @@ const int32_t* launch_morton_sort(const PassArgs& p, PathBuffers& b, uint32_t bo
 // values (the sorted keys are at the same offset of keys).  Used by cr_debug_sort.
 int32_t* launch_sort_only(const uint32_t* key_in, const int32_t* val_in, uint32_t n, uint32_t* keys, int32_t* vals,
                           uint32_t* ws, uint32_t* count, uint32_t* err, cudaStream_t st, LaunchCount& lc) {
-    const uint32_t sms = (uint32_t)sm_count();
-    k_morton<<<min((n + 511) / 512, 2 * sms), 512, 0, st>>>(nullptr, nullptr, reinterpret_cast<const int32_t*>(key_in),
+    k_morton<<<(n + 511) / 512, 512, 0, st>>>(nullptr, nullptr, reinterpret_cast<const int32_t*>(key_in),
                                                              count, n, nullptr,
                                                              reinterpret_cast<const uint16_t*>(val_in), 0, keys, vals,
                                                              vals + n, ws + kSortCtr);
