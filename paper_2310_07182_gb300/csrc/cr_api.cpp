@@ -364,6 +364,7 @@ extern "C" cr_status cr_scene_create(const float* tri_xyz, uint32_t n_tri, const
         s->dev.err = reinterpret_cast<uint32_t*>(static_cast<char*>(de.p) + 2 * sizeof(SceneDev));
         CR_CUDA(cudaMemset(s->dev.err, 0, 4));
         SceneDev ent[2] = {scene_entry(s->dev, false), scene_entry(s->dev, s->dev.nodes8 != nullptr)};
+        ent[0].n_nodes4 = ent[1].n_nodes4 = s->dev.n_nodes4;
         CR_CUDA(cudaMemcpy(de.p, ent, sizeof(ent), cudaMemcpyHostToDevice));
         s->d_entries = static_cast<SceneDev*>(de.p);
         de.p = nullptr;
@@ -705,7 +706,10 @@ cr_status build_plan(const cr_job* jobs, uint32_t n_jobs, const PlanOpts& po, Re
         px += jobs[i].camera.width * jobs[i].camera.height;
         if ((uint64_t)px > (1ull << 28)) return fail(CR_ERR_INVALID_ARG, "too many pixels in the batch");
     }
-    for (auto* sc : uniq) plan.scenes.push_back(scene_entry(sc->dev, po.bvh8));
+    for (auto* sc : uniq) {
+        plan.scenes.push_back(scene_entry(sc->dev, po.bvh8));
+        plan.scenes.back().n_nodes4 = sc->dev.n_nodes4;
+    }
     plan.npx_total = px;
     // passes: pass p renders sample p of every job with spp > p
     uint32_t px_base = 0;

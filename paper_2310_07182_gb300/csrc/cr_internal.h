@@ -112,6 +112,7 @@ struct SceneDev {
     // sizes of this entry's arrays and the scene's error word (bounds checks of a debug build)
     uint32_t n_nodes, n_tris, n_mats;
     uint32_t* err;
+    uint32_t n_nodes4 = 0; // BVH4 nodes (set where render and trace entries are made)
 };
 SceneDev scene_entry(const DevScene& s, bool bvh8);
 

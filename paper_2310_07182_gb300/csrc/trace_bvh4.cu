@@ -37,10 +37,11 @@ __device__ __forceinline__ void sort2(uint32_t& a, uint32_t& b) {
         (v) = __ldg(reinterpret_cast<const int*>(nodes + 8 * (size_t)(e_ >> 2) + 6) + (e_ & 3));      \
     } while (0)
 
+// dsc: the scene-table entry, read only by the index checks of a debug build.
 template <bool kCount>
 __device__ __forceinline__ int2 trace_bvh4_one(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                float4 ro, float4 rd, uint32_t* sstack, unsigned long long& n_node,
-                                               unsigned long long& n_tri) {
+                                               unsigned long long& n_tri, const SceneDev* dsc = nullptr) {
     constexpr int kSmemS = kSmemStack;
     const RayPre r = prep_ray(ro, rd);
     const int skip = __float_as_int(ro.w);
@@ -54,6 +55,10 @@ __device__ __forceinline__ int2 trace_bvh4_one(const float4* __restrict__ nodes,
     while (true) {
         while (node >= 0) {
             if (kCount) ++n_node;
+            CR_DBG(if (!dbg_in_range(dsc, (uint32_t)node, kDbgNode, dsc->n_nodes4)) {
+                node = 0x7fffffff;
+                break;
+            })
             const float4* q = nodes + 8 * (size_t)node;
             const float4 lx = __ldg(q + 0), hx = __ldg(q + 1), ly = __ldg(q + 2), hy = __ldg(q + 3);
             const float4 lz = __ldg(q + 4), hz = __ldg(q + 5), cc = __ldg(q + 6);
@@ -96,6 +101,7 @@ __device__ __forceinline__ int2 trace_bvh4_one(const float4* __restrict__ nodes,
         if (node == 0x7fffffff) break;
         // leaf: a BVH2 leaf code
         const uint32_t code = (uint32_t)(~node);
+        CR_DBG(if (!dbg_in_range(dsc, (code >> 2) + (code & 3u), kDbgTri, dsc->n_tris)) break;)
         test_leaf(tris, r, skip, code >> 2, (code & 3u) + 1u, best, n_tri);
         tcull = __fmul_rn(best.t, kCullWiden);
         if (sp == 0) break;
@@ -122,7 +128,8 @@ __global__ void __maxnreg__(CR_TRACE4_MAXNREG) k_trace_bvh4(const SceneDev* __re
         const float4 ro = ray_o[slot];
         const float4 rd = ray_d[slot];
         int2 h = make_int2(-1, __float_as_int(INFINITY));
-        if (rd.w >= 0.0f) h = trace_bvh4_one<kCount>(sc.nodes4, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri);
+        if (rd.w >= 0.0f)
+            h = trace_bvh4_one<kCount>(sc.nodes4, sc.tris, ro, rd, smem_stack + threadIdx.x, n_node, n_tri, &sc);
         hit[slot] = h;
     }
     if (kCount) {

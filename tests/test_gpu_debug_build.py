@@ -26,19 +26,19 @@ from paper_2310_07182_gb300 import binding as cr, scenes
 def run():
     out = {"version": np.array([cr.cr_version()])}
     tiny = scenes.tiny(material_mix="mixed", n_soup=3000)
-    S = cr.Scene(tiny, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
+    S = cr.Scene(tiny, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q | cr.CR_BVH4)
     for mode in ("direction_reuse", "independent", "morton_sort"):
         img, _ = S.render(spp=2, max_bounces=3, mode=mode, tile=(8, 4), k=8, seed=4)
         out["tiny_" + mode] = img.cpu().numpy()
     rays = scenes.random_rays(3, 20000)
-    for bvh, name in ((cr.CR_BVH2, "bvh2"), (cr.CR_BVH8Q, "bvh8q")):
+    for bvh, name in ((cr.CR_BVH2, "bvh2"), (cr.CR_BVH8Q, "bvh8q"), (cr.CR_BVH4, "bvh4")):
         p, t = S.trace(rays, bvh=bvh)
         out["trace_p_" + name], out["trace_t_" + name] = np.asarray(p), np.asarray(t)
         p, t = S.trace(rays, bvh=bvh, any_hit=True)
         out["any_p_" + name] = np.asarray(p)
     interior = scenes.interior(width=160, height=96)
-    I = cr.Scene(interior, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q)
-    for bvh, name in ((cr.CR_BVH2, "bvh2"), (cr.CR_BVH8Q, "bvh8q")):
+    I = cr.Scene(interior, bvh_flags=cr.CR_BVH2 | cr.CR_BVH8Q | cr.CR_BVH4)
+    for bvh, name in ((cr.CR_BVH2, "bvh2"), (cr.CR_BVH8Q, "bvh8q"), (cr.CR_BVH4, "bvh4")):
         img, _ = I.render(spp=3, max_bounces=4, tile=(8, 8), k=8, seed=2, bvh=bvh, nee=True)
         out["interior_nee_" + name] = img.cpu().numpy()
     return out
