@@ -150,7 +150,7 @@ extern "C" const char* cr_last_error(void) { return g_err.c_str(); }
 extern "C" const char* cr_version(void) { return CR_DEBUG ? "cr 0.1 sm_103a debug" : "cr 0.1 sm_103a"; }
 
 namespace cr {
-// A debug build's verdict on a scene after a synchronised call: CR_OK, or CR_ERR_CUDA when a
+// A debug build's finding on a scene after a synchronised call: CR_OK, or CR_ERR_CUDA when a
 // kernel found a node, triangle or material index out of range (the word is then cleared).
 static cr_status debug_word_status(const cr_scene* s) {
 #if CR_DEBUG
