@@ -467,7 +467,10 @@ def run_ours(args):
         e2e[name] = aggregate(time.perf_counter() - t0, "max")
 
     extras = {}
-    if not args.core_only:
+    # the legs beyond the headline (precision, sweeps, quality, batching, serving) run at
+    # N = 1; a multi-GPU run measures the headline step only, so its GPUs are not held for
+    # minutes of untimed work
+    if not args.core_only and world == 1:
         extras["precision_interior"] = precision_leg(cr, scenes, rank, world, args)
         extras["table3_sweep"] = sweep_leg(cr, S, cam, out, stream, rank, world)
         # the paper sweeps an indoor scene (Sibenik): the same sweep on the interior, 4 bounces
@@ -593,7 +596,7 @@ def run_ours(args):
                                  "share_of_step": round(rm["ms_sort"] / rm["ms_per_step"], 4),
                                  "timing": "stage events of 3 untimed steps (events between all stages)"}
     line.update(extras)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle's rate is a single-GPU context figure
         v, thr, sample, dt = cpu_oracle_rate(sc, args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                                 "sample": sample}
