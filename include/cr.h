@@ -209,7 +209,9 @@ typedef struct {
     uint32_t frame_base;   /* frame index of the first sample (progressive rendering) */
     uint32_t reuse_depth;  /* reuse at bounces b <= reuse_depth; 0 = every bounce */
     uint32_t bvh;          /* CR_BVH2 (default), CR_BVH8Q or CR_BVH4 (scene must have it; with
-                              CR_BVH4 shadow rays stay on the BVH2) */
+                              CR_BVH4 shadow rays stay on the BVH2, and the BVH2 traversal
+                              variants of flags -- persistent, packet, speculative, two-phase --
+                              do not apply) */
     uint32_t block;        /* trace block size, multiple of 32 in [32, 512]; 0 = 128 for
                             * primary rays and 64 for secondary rays */
     uint32_t flags;        /* CR_OPT_* */
