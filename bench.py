@@ -514,7 +514,7 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count  # cudaDevAttrMultiProcessorCount
 
     def node_bytes_per_ray(res, layout=cr.CR_BVH2):
-        return 32 + 4 + 8 + node_b[layout] * res["nodes_per_ray"] + 48 * res["tris_per_ray"]
+        return trace_bytes_per_ray(res["nodes_per_ray"], res["tris_per_ray"], node_b[layout])
 
     rays_per_launch = R["secondary_rays_per_step"] / launches
     ms_per_launch = R["ms_trace_secondary"] / launches
@@ -609,6 +609,13 @@ def run_ours(args):
                 extra[name] = {"mrays": round(v2, 4), "cores": thr2, "sample": sample2, "seconds": round(dt2, 2)}
             line["cpu_baseline"]["other_workloads"] = extra
     print(json.dumps(line), flush=True)
+
+
+def trace_bytes_per_ray(nodes_per_ray: float, tris_per_ray: float, node_bytes: int = 64) -> float:
+    """Algorithmic bytes one secondary ray moves through the trace kernel: its ray record
+    (32 B), the queue entry (4 B) and the hit (8 B), every node visited (64 B for a BVH2
+    node, 80 for BVH8-Q, 112 for BVH4) and every triangle tested (48 B)."""
+    return 32 + 4 + 8 + node_bytes * nodes_per_ray + 48 * tris_per_ray
 
 
 def issue_roof(R, clk, n_sm):

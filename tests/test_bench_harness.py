@@ -83,3 +83,26 @@ def test_clock_sampler_without_nvml_or_nvidia_smi(monkeypatch):
         pass
     s = cs.summary(0.0, 1.0)
     assert s["sm_mhz"] is None and s["samples"] == 0 and s["source"] is None
+
+
+def test_committed_trace_profile_matches_the_kernel_sources():
+    """The roofline's DRAM traffic and the issue roof's instructions per ray come from the
+    committed ncu summary of the BVH2 trace kernel; the summary names the sources it was
+    captured from by hash, and a changed kernel or tree builder must be recaptured."""
+    import bench
+    assert bench.profile_traffic() is not None, "trace kernel sources changed since profiles/ was captured"
+    assert 300 < bench.profile_traffic("warp_instructions_per_ray") < 500
+
+
+def test_roofline_arithmetic():
+    """Bytes per ray and the issue roof, recomputed by hand from the figures of a bench line
+    (40.17 BVH2 nodes and 4.32 triangles per secondary ray; 152 SMs at 2070 MHz)."""
+    import bench
+    assert abs(bench.trace_bytes_per_ray(40.17, 4.32) - (44 + 64 * 40.17 + 48 * 4.32)) < 1e-9
+    assert abs(bench.trace_bytes_per_ray(40.17, 4.32) - 2822.24) < 1e-6
+    assert bench.trace_bytes_per_ray(21.0, 4.4, 112) == 44 + 112 * 21.0 + 48 * 4.4
+    r = bench.issue_roof({"trace_mrays": 1850.0}, 2070.0, 152)
+    assert abs(r["peak"] - 152 * 4 * 2070e6 / 1e12) < 1e-3
+    ipr = bench.profile_traffic("warp_instructions_per_ray")
+    assert abs(r["achieved"] - round(ipr * 1850e6 / 1e12, 3)) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
