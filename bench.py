@@ -374,7 +374,8 @@ def run_ours(args):
     for mode in modes:
         if mode == modes[0]:  # sampling starts before the warm-up so it is live when timing starts
             sampler = ClockSampler(local, uuid=gpu_uuid(local)).__enter__()
-        for w in range(args.warmup):
+        for w in range(args.warmup):  # warm-up steps as the timed ones, L2 flush included
+            flush.fill_(float(w))
             step(mode, frame_of(rank, w, world))
         torch.cuda.synchronize()
         barrier()
