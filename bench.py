@@ -82,7 +82,7 @@ class ClockSampler:
     REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                    0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int, uuid: str | None = None, period_s: float = 0.005):
+    def __init__(self, gpu_index: int, uuid: str | None = None, period_s: float = 0.002):
         self.idx = gpu_index
         self.uuid = uuid
         self.period = period_s
