@@ -176,3 +176,39 @@ def test_express_lane_shortens_small_jobs_beside_a_large_one(cr, world):
     print(f"small job render time beside a large one: main lane {render_ms[0]:.2f} ms, "
           f"express lane {render_ms[1 << 20]:.2f} ms")
     assert render_ms[1 << 20] < 0.5 * render_ms[0]
+
+
+def test_express_lane_fallbacks(cr, world):
+    """A request under the express threshold whose tiles exceed the express lane's slots
+    runs in the main lane, and the express lane works at the smallest budget; every result is
+    its stand-alone render."""
+    sc, S = world
+    cam_small = _cam(sc["tiny"].camera, 48, 40)
+    # 512 MiB: ~2.05M slots of 157 B, an eighth of them (4,007 tiles of 8x8) in the express
+    # lane; a 640x640 request has 6,400 tiles but only 409,600 pixels x 1 spp x 2 = 819,200
+    # ray steps
+    srv = cr.cr_server_create(512 << 20, tile=(8, 8), k=8, express_rays=1 << 20)
+    try:
+        cam_wide = _cam(sc["tiny"].camera, 640, 640)
+        wide = torch.empty((640, 640, 3), device="cuda")
+        small = torch.empty((40, 48, 3), device="cuda")
+        ids = [cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, cam_wide, wide, spp=1, max_bounces=1, seed=7)),
+               cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, cam_small, small, spp=2, max_bounces=2, seed=8))]
+        for jid in ids:
+            cr.cr_server_wait(srv, jid, 60000)
+        ref, _ = S["tiny"].render(cam_wide, spp=1, max_bounces=1, tile=(8, 8), k=8, seed=7)
+        assert torch.equal(wide, ref)
+        ref, _ = S["tiny"].render(cam_small, spp=2, max_bounces=2, tile=(8, 8), k=8, seed=8)
+        assert torch.equal(small, ref)
+    finally:
+        cr.cr_server_destroy(srv)
+    # 64 MiB, the smallest budget: ~256k slots, an express lane of 500 tiles
+    srv = cr.cr_server_create(64 << 20, tile=(8, 8), k=8, express_rays=1 << 20)
+    try:
+        small = torch.empty((40, 48, 3), device="cuda")
+        jid = cr.cr_server_submit(srv, cr.make_job(S["tiny"].handle, cam_small, small, spp=2, max_bounces=2, seed=8))
+        cr.cr_server_wait(srv, jid, 60000)
+        ref, _ = S["tiny"].render(cam_small, spp=2, max_bounces=2, tile=(8, 8), k=8, seed=8)
+        assert torch.equal(small, ref)
+    finally:
+        cr.cr_server_destroy(srv)
