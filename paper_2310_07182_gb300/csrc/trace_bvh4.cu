@@ -1,8 +1,9 @@
 // trace_bvh4.cu -- closest-hit traversal of the BVH4 (4-wide nodes with FP32 child boxes,
 // collapsed from the BVH2 in bvh4_build.cpp), one ray per thread.
 //
-// A node visit loads the node's seven 16-byte words, tests the four child boxes with the
-// BVH2 kernel's conservative slab test (unused slots have NaN planes and never pass), and
+// A node visit loads the node's seven 16-byte words (the near and far plane words of each
+// axis picked by the ray's direction signs), tests the four child boxes with the BVH2
+// kernel's conservative slab test (unused slots have NaN planes and never pass), and
 // orders the hit children by entry distance: the distance bits with the child slot in the
 // two low bits, sorted by a five-exchange network (the slot bits only reorder children whose
 // distances agree to 21 bits, which changes the visit order, never the closest hit).  The
@@ -22,6 +23,17 @@ namespace {
 #ifndef CR_TRACE4_MAXNREG
 #define CR_TRACE4_MAXNREG 64
 #endif
+
+// The slab test of box_hit_fma with the near and far planes chosen by the ray: three min /
+// max operations per box instead of nine.  Unused slots (NaN planes) still miss: the exit
+// distance is NaN and the comparison fails.
+__device__ __forceinline__ bool box_hit_nf(const RayPre& r, float nx, float fx, float ny, float fy, float nz, float fz,
+                                           float onx, float ofx, float ony, float ofy, float onz, float ofz, float tcull,
+                                           float& tn) {
+    tn = fmaxf(max3f(fmaf(nx, r.ix, onx), fmaf(ny, r.iy, ony), fmaf(nz, r.iz, onz)), 0.0f);
+    const float tf = min3f(fmaf(fx, r.ix, ofx), fmaf(fy, r.iy, ofy), fmaf(fz, r.iz, ofz));
+    return tn <= __fmul_rn(tf, kFarWiden) && tn <= tcull;
+}
 
 __device__ __forceinline__ void sort2(uint32_t& a, uint32_t& b) {
     const uint32_t lo = min(a, b), hi = max(a, b);
@@ -52,6 +64,14 @@ __device__ __forceinline__ int2 trace_bvh4_one(const float4* __restrict__ nodes,
     int node = 0;
     float tcull = __fmul_rn(best.t, kCullWiden);
     uint32_t* top = sstack;
+    // the near and far plane of each axis follow from the sign of 1/d (the offsets are biased
+    // by that sign too, so this equals the min / max of the two plane distances): their word
+    // offsets in the node and their distance offsets, once per ray
+    const int sxn = r.ix < 0.0f, syn = r.iy < 0.0f, szn = r.iz < 0.0f;
+    const int wnx = sxn, wfx = 1 - sxn, wny = 2 + syn, wfy = 3 - syn, wnz = 4 + szn, wfz = 5 - szn;
+    const float onx = sxn ? r.hix : r.lox, ofx = sxn ? r.lox : r.hix;
+    const float ony = syn ? r.hiy : r.loy, ofy = syn ? r.loy : r.hiy;
+    const float onz = szn ? r.hiz : r.loz, ofz = szn ? r.loz : r.hiz;
     while (true) {
         while (node >= 0) {
             if (kCount) ++n_node;
@@ -60,15 +80,15 @@ __device__ __forceinline__ int2 trace_bvh4_one(const float4* __restrict__ nodes,
                 break;
             })
             const float4* q = nodes + 8 * (size_t)node;
-            const float4 lx = __ldg(q + 0), hx = __ldg(q + 1), ly = __ldg(q + 2), hy = __ldg(q + 3);
-            const float4 lz = __ldg(q + 4), hz = __ldg(q + 5), cc = __ldg(q + 6);
+            const float4 nx = __ldg(q + wnx), fx = __ldg(q + wfx), ny = __ldg(q + wny), fy = __ldg(q + wfy);
+            const float4 nz = __ldg(q + wnz), fz = __ldg(q + wfz), cc = __ldg(q + 6);
             const int c0 = __float_as_int(cc.x), c1 = __float_as_int(cc.y), c2 = __float_as_int(cc.z),
                       c3 = __float_as_int(cc.w);
             float t0, t1, t2, t3;
-            const bool h0 = box_hit_fma(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tcull, t0);
-            const bool h1 = box_hit_fma(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tcull, t1);
-            const bool h2 = box_hit_fma(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tcull, t2);
-            const bool h3 = box_hit_fma(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tcull, t3);
+            const bool h0 = box_hit_nf(r, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, onx, ofx, ony, ofy, onz, ofz, tcull, t0);
+            const bool h1 = box_hit_nf(r, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, onx, ofx, ony, ofy, onz, ofz, tcull, t1);
+            const bool h2 = box_hit_nf(r, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, onx, ofx, ony, ofy, onz, ofz, tcull, t2);
+            const bool h3 = box_hit_nf(r, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, onx, ofx, ony, ofy, onz, ofz, tcull, t3);
             // entry distances are >= 0, so their bits order like the floats; misses sort last
             uint32_t k0 = h0 ? (__float_as_uint(t0) & ~3u) : 0xffffffffu;
             uint32_t k1 = h1 ? ((__float_as_uint(t1) & ~3u) | 1u) : 0xffffffffu;
